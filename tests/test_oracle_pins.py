@@ -1,0 +1,473 @@
+"""Pins of the CPU oracle against facts fixed by mathematics and published
+definitions (not against the oracle itself).  CPU only.
+
+Each test names what it pins; a plausible slip in the oracle (a dropped term,
+a sign, a transposed index, a wrong root or slot order) fails one of them.
+"""
+import os
+
+import numpy as np
+import pytest
+import sympy
+import torch
+import torch.nn.functional as F
+
+import workloads
+from oracle import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def schoolbook(a, b, q):
+    """negacyclic product in Z_q[x]/(x^N+1), Python integers"""
+    N = len(a)
+    out = [0] * N
+    for i in range(N):
+        ai = int(a[i])
+        if ai == 0:
+            continue
+        for j in range(N):
+            k = i + j
+            if k < N:
+                out[k] += ai * int(b[j])
+            else:
+                out[k - N] -= ai * int(b[j])
+    return np.array([x % q for x in out], dtype=np.uint64)
+
+
+def centred(v, q):
+    v = np.asarray(v, dtype=np.int64) % q
+    return np.where(v > q // 2, v - q, v)
+
+
+@pytest.fixture(scope="module")
+def small():
+    return O.Params(6, 3, 1, 1)  # N = 64
+
+
+# --------------------------------------------------------------------------
+# parameters
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("log_n,L,K", [(4, 3, 1), (12, 3, 1), (13, 7, 1), (14, 11, 2)])
+def test_prime_chain(log_n, L, K):
+    P = O.Params(log_n, L, K, 1)
+    two_n = 2 << log_n
+    assert P.q == sorted(P.q, reverse=True) and len(set(P.primes)) == L + K
+    for q in P.q:
+        assert sympy.isprime(q) and q % two_n == 1 and q < 2**30 and q > 2**29
+    for p in P.p:
+        assert sympy.isprime(p) and p % two_n == 1 and p < 2**31 and p > 2**30
+    # nothing skipped: no prime = 1 (mod 2N) between consecutive chain primes
+    for bound, chain in ((2**30, P.q), (2**31, P.p)):
+        c = (bound - 1) // two_n * two_n + 1
+        for q in chain:
+            while c > q:
+                assert not sympy.isprime(c)
+                c -= two_n
+            c -= two_n
+
+
+@pytest.mark.parametrize("log_n", [4, 12, 14])
+def test_psi_is_primitive_2n_root(log_n):
+    P = O.Params(log_n, 2, 1, 1)
+    N = P.N
+    for t, q in enumerate(P.primes):
+        psi = P.psi(t)
+        assert pow(psi, N, q) == q - 1 and pow(psi, 2 * N, q) == 1
+
+
+# --------------------------------------------------------------------------
+# NTT
+# --------------------------------------------------------------------------
+def test_ntt_monomial_closed_form():
+    """NTT(x^m)_k = psi^{(2k+1) m}: evaluation at the odd powers of psi."""
+    P = O.Params(5, 2, 1, 1)
+    N = P.N
+    for t, q in enumerate(P.primes):
+        psi = P.psi(t)
+        for m in (0, 1, 7, N - 1):
+            a = np.zeros(N, dtype=np.uint32)
+            a[m] = 1
+            A = P.ntt_fwd(t, a)
+            want = [pow(psi, (2 * k + 1) * m, q) for k in range(N)]
+            assert A.tolist() == want
+
+
+@pytest.mark.parametrize("log_n", [4, 6, 8])
+def test_poly_mul_matches_schoolbook(log_n):
+    P = O.Params(log_n, 3, 2, 1)
+    rng = np.random.default_rng(log_n)
+    for t, q in enumerate(P.primes):
+        a = rng.integers(0, q, P.N, dtype=np.uint64).astype(np.uint32)
+        b = rng.integers(0, q, P.N, dtype=np.uint64).astype(np.uint32)
+        assert np.array_equal(P.poly_mul(t, a, b).astype(np.uint64), schoolbook(a, b, q))
+    # edge values 0, 1, q-1
+    q = P.primes[0]
+    a = np.array([0, 1, q - 1] * (P.N // 3) + [q - 1] * (P.N % 3), dtype=np.uint32)
+    b = np.full(P.N, q - 1, dtype=np.uint32)
+    assert np.array_equal(P.poly_mul(0, a, b).astype(np.uint64), schoolbook(a, b, q))
+
+
+@pytest.mark.parametrize("log_n", [12, 14])
+def test_ntt_roundtrip(log_n):
+    P = O.Params(log_n, 2, 1, 1)
+    rng = np.random.default_rng(1)
+    for t, q in enumerate(P.primes):
+        a = rng.integers(0, q, P.N, dtype=np.uint64).astype(np.uint32)
+        assert np.array_equal(P.ntt_inv(t, P.ntt_fwd(t, a)), a)
+
+
+# --------------------------------------------------------------------------
+# sampling
+# --------------------------------------------------------------------------
+def test_splitmix64_published_vectors():
+    blocks, cur = {}, None
+    for line in open(os.path.join(GOLDEN, "splitmix64.txt")):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        if line.startswith("state"):
+            cur = int(line.split()[1])
+            blocks[cur] = []
+        else:
+            blocks[cur].append(int(line))
+    for state, outs in blocks.items():
+        assert [O.splitmix_raw(state, k) for k in range(len(outs))] == outs
+    # a stream starts at mix64(seed + GAMMA*((tag<<40)+idx+1)); mix64(y) is the first raw output from y - GAMMA
+    G, M = 0x9E3779B97F4A7C15, (1 << 64) - 1
+    for seed, tag, idx in ((3, 1, 0), (4, 4, 5 * 256 + 2)):
+        start = O.splitmix_raw((seed + G * ((tag << 40) + idx + 1) - G) & M, 0)
+        assert [O.rng_output(seed, tag, idx, k) for k in range(3)] == [O.splitmix_raw(start, k) for k in range(3)]
+
+
+def test_keygen_secret_and_key_errors(small):
+    """evk_j = (-a s + e_j + P g_j s^2, a): removing a*s and P*g_j*s^2 leaves
+    the same small error e_j (|e| <= 21, centred binomial) on every prime."""
+    P = small
+    sk, evk = P.keygen(3)
+    assert set(np.unique(sk).tolist()) <= {-1, 0, 1}
+    Pprod = int(np.prod([int(p) for p in P.p], dtype=object))
+    for j in range(P.dnum(P.L)):
+        errs = []
+        for t, q in enumerate(P.primes):
+            s = (sk.astype(np.int64) % q).astype(np.uint32)
+            b, a = evk[j, 0, t], evk[j, 1, t]
+            v = (b.astype(np.uint64) + schoolbook(a, s, q)) % q
+            if t < P.L and j * P.alpha <= t < (j + 1) * P.alpha:
+                s2 = schoolbook(s, s, q)
+                v = (v + q - (Pprod % q) * s2 % q) % q
+            errs.append(centred(v, q))
+        for e in errs:
+            assert np.array_equal(e, errs[0])
+        assert np.abs(errs[0]).max() <= 21 and np.abs(errs[0]).max() > 0
+
+
+def test_encrypt_decrypt_error_is_small(small):
+    P = small
+    sk, _ = P.keygen(3)
+    rng = np.random.default_rng(0)
+    m = rng.integers(-(2**40), 2**40, size=(4, P.N))
+    ct = P.encrypt(sk, O.to_residues(m, P.q), P.L, 4)
+    d = O.crt_centered(P.decrypt(sk, ct, P.L), P.q)
+    e = (d - m).astype(np.int64)
+    assert np.abs(e).max() <= 21
+    assert abs(e.mean()) < 0.5 and 6 < e.var() < 15  # centred binomial eta=21: variance 10.5
+    # different ciphertexts use different randomness
+    assert not np.array_equal(ct[0, 1], ct[1, 1])
+
+
+# --------------------------------------------------------------------------
+# encoding and CRT
+# --------------------------------------------------------------------------
+def test_round_half_away():
+    x = np.array([0.5, -0.5, 1.5, 2.5, -2.5, 0.49999999999999994, 3.0, -0.0])
+    assert O.round_half_away(x).tolist() == [1, -1, 2, 3, -3, 0, 3, 0]
+
+
+def test_slot_exponents_are_the_odd_residues():
+    """{5^k, -5^k mod 2N} covers every odd residue mod 2N exactly once."""
+    for N in (16, 64, 4096):
+        e = O.slot_exponents(N)
+        allr = np.concatenate([e, (2 * N - e) % (2 * N)])
+        assert sorted(allr.tolist()) == list(range(1, 2 * N, 2))
+
+
+def test_encode_constant_closed_form():
+    """A constant vector c in all N/2 slots encodes to m_0 = round(S c), m_j = 0."""
+    N, S = 64, 2.0**20
+    m = O.encode_coeffs(np.full((1, N // 2), 0.3), N, S)[0]
+    assert m[0] == round(S * 0.3) and np.all(m[1:] == 0)
+
+
+def test_encode_is_multiplicative():
+    """decode(m1 * m2) ~ z1 * z2 slot-wise: the canonical embedding turns the
+    negacyclic product into the slot-wise product (App. A, Mult)."""
+    N, S = 64, 2.0**24
+    rng = np.random.default_rng(2)
+    z1, z2 = rng.uniform(-1, 1, (2, N // 2))
+    m1 = O.encode_coeffs(z1[None], N, S)[0]
+    m2 = O.encode_coeffs(z2[None], N, S)[0]
+    q = (1 << 127) - 1  # a large modulus so the product is exact in centred form
+    prod = centred_big(schoolbook_big(m1, m2), q)
+    z = O.decode(np.array(prod, dtype=np.float64)[None], N, N // 2, S * S)[0]
+    assert np.abs(z - z1 * z2).max() < 1e-5
+
+
+def schoolbook_big(a, b):
+    N = len(a)
+    out = [0] * N
+    for i in range(N):
+        for j in range(N):
+            k = i + j
+            v = int(a[i]) * int(b[j])
+            if k < N:
+                out[k] += v
+            else:
+                out[k - N] -= v
+    return out
+
+
+def centred_big(v, q):
+    return [((x % q) - q) if (x % q) > q // 2 else (x % q) for x in v]
+
+
+def test_decode_inverts_encode():
+    N, S, B = 4096, 2.0**40, 1000
+    z = np.random.default_rng(3).uniform(-2, 2, (3, B))
+    m = O.encode_coeffs(z, N, S)
+    assert np.abs(O.decode(m, N, B, S) - z).max() < 1e-9
+
+
+def test_crt_centered():
+    P = O.Params(12, 5, 1, 1)
+    Q = 1
+    for q in P.q:
+        Q *= q
+    rng = np.random.default_rng(4)
+    vals = [int(rng.integers(-(2**62), 2**62)) * int(rng.integers(0, 2**60)) for _ in range(64)]
+    vals += [Q // 2, -(Q // 2) + 1, 0, 1, -1]
+    res = np.array([[v % q for v in vals] for q in P.q], dtype=np.uint32)[None]
+    back = O.crt_centered(res, P.q)[0]
+    assert [int(x) for x in back] == vals
+
+
+# --------------------------------------------------------------------------
+# homomorphic operations
+# --------------------------------------------------------------------------
+def _rand_ct(P, n, level, seed):
+    return workloads.random_residues(P.q[:level], (n, 2), P.N, seed)
+
+
+def test_mac_decrypts_to_weighted_sum(small):
+    """Dec(sum_t w c_t + (pt, 0)) = sum_t w Dec(c_t) + pt, exactly (Mult(c,u), Add)."""
+    P = small
+    sk, _ = P.keygen(3)
+    level = 3
+    x = _rand_ct(P, 7, level, 5)
+    rng = np.random.default_rng(6)
+    idx = rng.integers(-1, 7, size=(5, 9)).astype(np.int32)
+    w = rng.integers(-127, 128, size=(5, 9)).astype(np.int8)
+    pt = workloads.random_residues(P.q[:level], (5,), P.N, 8)
+    out = P.mac(level, idx, w, x, pt)
+    dx = P.decrypt(sk, x, level).astype(np.int64)
+    dout = P.decrypt(sk, out, level).astype(np.int64)
+    for o in range(5):
+        for i, q in enumerate(P.q[:level]):
+            acc = pt[o, i].astype(np.int64)
+            for t in range(9):
+                if idx[o, t] >= 0:
+                    acc = acc + int(w[o, t]) * dx[idx[o, t], i]
+            assert np.array_equal(acc % q, dout[o, i])
+    # no pt: only the weighted sum; c1 of the output never sees pt
+    out2 = P.mac(level, idx, w, x, None)
+    assert np.array_equal(out2[:, 1], out[:, 1]) and not np.array_equal(out2[:, 0], out[:, 0])
+
+
+def test_square_decrypts_to_square(small):
+    """(c0 + c1 s)^2 = d0 + d1 s + d2 s^2 exactly (Mult(c1, c2) before relinearisation)."""
+    P = small
+    sk, _ = P.keygen(3)
+    ct = _rand_ct(P, 2, 3, 9)
+    d = P.square(3, ct)
+    m = P.decrypt(sk, ct, 3)
+    m3 = P.decrypt(sk, d, 3)
+    for c in range(2):
+        for i, q in enumerate(P.q):
+            assert np.array_equal(m3[c, i].astype(np.uint64), schoolbook(m[c, i], m[c, i], q))
+
+
+def _ks_bound(P, level, sk):
+    D = max(P.q) ** P.alpha
+    Pp = 1
+    for p in P.p:
+        Pp *= p
+    s1 = int(np.abs(sk).sum())
+    return P.dnum(level) * P.N * P.alpha * D / 2 * 21 / Pp + (P.K + 1) / 2 * (1 + s1) + 1
+
+
+@pytest.mark.parametrize("cfg", [(6, 3, 1, 1), (6, 5, 2, 2), (6, 5, 2, 1)])
+def test_keyswitch_noise_bound(cfg):
+    """k0 + k1 s - x s^2 (mod Q_level) is the key-switching noise, bounded by
+    dnum * N * alpha * D/2 * 21 / P + (K+1)/2 * (1 + ||s||_1) + 1 (digit value
+    times key error over P, plus the ModDown rounding)."""
+    P = O.Params(*cfg)
+    sk, evk = P.keygen(3)
+    for level in (P.L, P.L - 1):
+        x = workloads.random_residues(P.q[:level], (3,), P.N, 10 + level)
+        ks = P.keyswitch(level, evk, x)
+        ssq = [schoolbook((sk.astype(np.int64) % q), (sk.astype(np.int64) % q), q) for q in P.q[:level]]
+        m = P.decrypt(sk, ks, level).astype(np.uint64)
+        diff = np.zeros((3, level, P.N), dtype=np.uint32)
+        for c in range(3):
+            for i, q in enumerate(P.q[:level]):
+                xs2 = schoolbook(x[c, i], ssq[i], q)
+                diff[c, i] = (m[c, i] + q - xs2) % q
+        noise = np.array(O.crt_centered(diff, P.q[:level]), dtype=np.float64)
+        bound = _ks_bound(P, level, sk)
+        assert np.abs(noise).max() <= bound
+        # and it is genuinely small compared with Q_level
+        assert np.abs(noise).max() < 2.0**40
+
+
+def test_relin_keeps_the_message(small):
+    P = small
+    sk, evk = P.keygen(3)
+    ct = _rand_ct(P, 2, 3, 11)
+    d = P.square(3, ct)
+    r = P.relin(3, evk, d)
+    a = O.crt_centered(P.decrypt(sk, d, 3), P.q)
+    b = O.crt_centered(P.decrypt(sk, r, 3), P.q)
+    assert np.abs(np.array(b - a, dtype=np.float64)).max() <= _ks_bound(P, 3, sk)
+
+
+def test_rescale_divides_by_the_dropped_prime(small):
+    """Dec(rescale(c)) = Dec(c)/q_top + eps with |eps| <= (1 + ||s||_1)/2."""
+    P = small
+    sk, _ = P.keygen(3)
+    rng = np.random.default_rng(12)
+    m = rng.integers(-(2**55), 2**55, size=(3, P.N))
+    ct = P.encrypt(sk, O.to_residues(m, P.q), 3, 13)
+    before = O.crt_centered(P.decrypt(sk, ct, 3), P.q)
+    r = P.rescale(3, ct)
+    after = O.crt_centered(P.decrypt(sk, r, 2), P.q[:2])
+    qt = P.q[2]
+    err = np.array([[float(a) - float(b) / qt for a, b in zip(ra, rb)] for ra, rb in zip(after, before)])
+    assert np.abs(err).max() <= (1 + np.abs(sk).sum()) / 2 + 1e-6
+
+
+def test_square_relin_rescale_is_the_composition(small):
+    P = small
+    sk, evk = P.keygen(3)
+    ct = _rand_ct(P, 2, 3, 14)
+    a = P.square_relin_rescale(3, evk, ct)
+    b = P.rescale(3, P.relin(3, evk, P.square(3, ct)))
+    assert np.array_equal(a, b)
+
+
+# --------------------------------------------------------------------------
+# network pieces
+# --------------------------------------------------------------------------
+def test_quantize():
+    w = workloads.cipher_weights(workloads.get_config("cryptonets"))[1]
+    wi, s = O.quantize(w)
+    assert np.abs(wi).max() == 127 and s == pytest.approx(np.abs(w).max() / 127)
+    assert np.abs(wi.astype(np.float64) * s - w).max() <= s / 2 + 1e-12
+
+
+@pytest.mark.parametrize("name", ["cnn3_small", "cryptonets", "cifar_cnn"])
+def test_conv_tables_match_torch_conv2d(name):
+    """The gather tables compute exactly F.conv2d / F.linear (a library routine)."""
+    cfg = workloads.get_config(name)
+    rng = np.random.default_rng(15)
+    for layer, wf in zip(cfg["cipher"], workloads.cipher_weights(cfg)):
+        wi, s = O.quantize(wf)
+        idx, wt = O.layer_table(layer, wi)
+        n_in, n_out = workloads.cipher_layer_io(layer)
+        x = rng.standard_normal((n_in, 3))
+        y = O.fp64_network(dict(cipher=[dict(layer, add=False, square=False)]), x, [], [(idx, wt)], [s])
+        wr = torch.from_numpy(wi.astype(np.float64) * s)
+        if layer["type"] == "conv":
+            xt = torch.from_numpy(x.T.reshape(3, layer["cin"], layer["h"], layer["w"]))
+            ref = F.conv2d(xt, wr, stride=layer["stride"], padding=layer["pad"]).reshape(3, -1).numpy().T
+        else:
+            ref = F.linear(torch.from_numpy(x.T), wr).numpy().T
+        assert y.shape == (n_out, 3)
+        assert np.abs(y - ref).max() < 1e-12
+
+
+@pytest.mark.parametrize("name", ["cnn3_small", "cryptonets", "cifar_cnn"])
+def test_plain_branch_matches_torch(name):
+    cfg = workloads.with_batch(workloads.get_config(name), 5)
+    imgs, noise, pw = workloads.images(cfg), workloads.laplace_noise(cfg), workloads.plain_weights(cfg)
+    feats = O.plain_branch(cfg, imgs, noise, pw)
+    y0, x0, h, w = cfg["segment"]
+    x = torch.from_numpy(imgs.astype(np.float64) / 255.0 + noise.astype(np.float64)).permute(0, 3, 1, 2).clone()
+    x[:, :, y0:y0 + h, x0:x0 + w] = 0
+    ref = []
+    for st, wgt in zip(cfg["plain"], pw):
+        if st["op"] == "conv":
+            x = F.conv2d(x, torch.from_numpy(wgt.astype(np.float64)), stride=st["stride"], padding=st["pad"])
+            x = F.relu(x) if st["relu"] else x
+        elif st["op"] == "avgpool2":
+            x = F.avg_pool2d(x, 2)
+        elif st["op"] == "tap_crop_crot":
+            H = x.shape[2]
+            o = (H - st["hc"]) // 2
+            y = x[:, :, o:o + st["hc"], o:o + st["wc"]]
+            z = F.conv2d(y, torch.from_numpy(wgt.astype(np.float64))[:, :, None, None])  # 1x1 conv = CRot
+            ref.append(z.permute(1, 2, 3, 0).reshape(-1, 5).numpy())
+        else:
+            ref.append(F.linear(x.reshape(5, -1), torch.from_numpy(wgt.astype(np.float64))).numpy().T)
+    assert len(feats) == len(ref)
+    for a, b in zip(feats, ref):
+        assert np.abs(a - b).max() < 1e-12
+
+
+def test_level_and_scale_schedule():
+    cfg = workloads.get_config("cryptonets")
+    lv, out = workloads.level_schedule(cfg)
+    assert lv == [7, 6, 5] and out == 5
+    q = O.Params.from_config(cfg).q
+    adds, S = O.scale_schedule(cfg, q, [0.5, 0.25, 0.125])
+    S0 = 2.0**30
+    a1 = S0 / 0.5
+    a2 = (a1 * a1 / q[6]) / 0.25
+    assert adds == [a1, a2] and S == (a2 * a2 / q[5]) / 0.125
+
+
+# --------------------------------------------------------------------------
+# whole network
+# --------------------------------------------------------------------------
+def argmax_agrees(dec, ref, margin=2e-3):
+    top2 = np.sort(ref, axis=0)[-2:]
+    clear = (top2[1] - top2[0]) > margin
+    return np.all(np.argmax(dec, 0)[clear] == np.argmax(ref, 0)[clear]), int((~clear).sum())
+
+
+def test_whole_network_small_config():
+    """decrypt(eval(encrypt(x))) within 1e-3 of the fp64 network, same argmax."""
+    prob = O.Problem(workloads.get_config("cnn3_small"))
+    out = prob.evaluate()
+    assert out.shape == (10, 2, 2, 4096)
+    dec = prob.decode_output(out)
+    ref = prob.fp64_logits()
+    assert np.abs(dec - ref).max() < 1e-3
+    ok, ties = argmax_agrees(dec, ref)
+    assert ok and ties < 50
+
+
+def test_whole_network_catches_a_dropped_feature():
+    """Planted mistake: evaluating without the unidirectional add moves the
+    logits.  (With this shallow plaintext branch the centre crop of the small
+    config lies inside the zero-filled segment, so its own features are zero;
+    nonzero features are planted here.)"""
+    prob = O.Problem(workloads.with_batch(workloads.get_config("cnn3_small"), 64))
+    feats = [np.random.default_rng(20).normal(0, 0.3, f.shape) for f in prob.feats]
+    P = prob.params
+    pts = [O.encode(f, P.N, s, P.q[:lv]) for f, s, lv in zip(feats, prob.add_scales, prob.levels)]
+    ref = O.fp64_network(prob.cfg, prob.seg, feats, prob.tables, prob.s_w)
+    good = prob.decode_output(O.evaluate(P, prob.cfg, prob.tables, prob.evk, prob.cts, pts))
+    assert np.abs(good - ref).max() < 1e-3
+    zero = [np.zeros_like(p) for p in pts]
+    bad = prob.decode_output(O.evaluate(P, prob.cfg, prob.tables, prob.evk, prob.cts, zero))
+    assert np.abs(bad - ref).max() > 1e-2
