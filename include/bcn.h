@@ -1,0 +1,293 @@
+/*
+ * bcn.h -- C ABI of the GB300 ciphertext-branch engine for bi-CryptoNets
+ * ("Bi-CryptoNets: Leveraging Different-Level Privacy for Encrypted
+ * Inference", arXiv 2402.01296).
+ *
+ * The paper splits an image into a sensitive segment, encrypted with CKKS and
+ * evaluated by a ciphertext branch, and an insensitive segment, perturbed and
+ * evaluated in plaintext by a plaintext branch whose features enter the
+ * ciphertext branch through unidirectional additions (Sec. 3, Sec. 3.2).  The
+ * client holds the secret key and the server evaluates without it (Sec. 2,
+ * threat model).  This library implements, in that order of the problem:
+ *   keygen / encrypt of the sensitive segment       (client, host C++)
+ *   plaintext-branch forward on the perturbed image (device, CUDA fp32)
+ *   encode of its features                          (client, host C++, fp64)
+ *   ciphertext-branch evaluation                    (server, device, CUDA)
+ *   decrypt / decode                                (client, host C++)
+ * The scheme is levelled RNS-CKKS with one image per slot (batch packing,
+ * App. D); every step of the evaluation is exact modular integer arithmetic
+ * in hand-written sm_103a kernels.
+ *
+ * Conventions
+ *   - Every call returns a bcn_status; BCN_OK is 0, errors are negative.
+ *     bcn_last_error() gives a thread-local message for the last failure.
+ *     No exception and no device trap crosses this boundary.
+ *   - Ring degree N = 2^log_n.  Data primes q_0 > q_1 > ... > q_{L-1} are the
+ *     L largest primes below 2^30 with q = 1 (mod 2N); special primes
+ *     p_0..p_{K-1} are the K largest primes below 2^31 with p = 1 (mod 2N).
+ *     A ciphertext "at level l" lives modulo q_0 ... q_{l-1}.
+ *   - Interchange layout (host and device): uint32 residues, canonical in
+ *     [0, q), coefficient form, limbs in chain order:
+ *         ciphertexts  [n_ct][2][level][N]   (c0, c1)
+ *         plaintexts   [n_pt][level][N]
+ *         secret key   [N] int8 in {-1, 0, 1}
+ *         evk          [dnum][2][L+K][N]     (b, a) per digit, limbs q_0..q_{L-1}
+ *                                            then p_0..p_{K-1}; dnum = ceil(L/alpha)
+ *   - Buffers are owned by the caller.  The library owns only the opaque
+ *     bcn_ctx / bcn_model / bcn_plain_model objects (and the small device
+ *     tables inside them).  Device calls are asynchronous on the given CUDA
+ *     stream (NULL = legacy default stream); host calls are synchronous.
+ *   - A ctx created with device < 0 is host-only: client calls work, device
+ *     calls return BCN_E_INVAL.
+ */
+#ifndef BCN_H
+#define BCN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BCN_OK = 0,
+    BCN_E_INVAL = -1,   /* bad argument, shape or layout */
+    BCN_E_NOMEM = -2,   /* host or device allocation failed */
+    BCN_E_CUDA = -3,    /* a CUDA runtime call failed */
+    BCN_E_LEVEL = -4,   /* not enough levels left for the requested operation */
+    BCN_E_SCALE = -5,   /* an encoded coefficient does not fit in 63 bits */
+    BCN_E_TIMEOUT = -6, /* a bounded device-side wait gave up */
+    BCN_E_BUDGET = -7   /* the caller's workspace is too small */
+} bcn_status;
+
+typedef struct bcn_ctx bcn_ctx;
+typedef struct bcn_model bcn_model;
+typedef struct bcn_plain_model bcn_plain_model;
+
+typedef struct {
+    uint32_t log_n;        /* N = 2^log_n, 4 <= log_n <= 14 */
+    uint32_t n_data;       /* L data primes (< 2^30), 1 <= L <= 24 */
+    uint32_t n_special;    /* K special primes (< 2^31), 1 <= K <= 4 */
+    uint32_t alpha;        /* primes per key-switching digit, 1 <= alpha <= K */
+} bcn_params;
+
+typedef struct {
+    uint32_t N, L, K, alpha, dnum; /* dnum = ceil(L / alpha) */
+    int device;                    /* CUDA ordinal, or -1 for a host-only ctx */
+} bcn_ctx_info;
+
+/* Message of the last failure on this thread ("" if none). */
+const char *bcn_last_error(void);
+
+/* ---------------------------------------------------------------- context */
+/* Builds the prime chain and the NTT / basis-conversion tables; with
+ * device >= 0 also uploads the device tables to that GPU. */
+bcn_status bcn_ctx_create(const bcn_params *params, int device, bcn_ctx **out);
+bcn_status bcn_ctx_destroy(bcn_ctx *ctx);
+bcn_status bcn_ctx_get_info(const bcn_ctx *ctx, bcn_ctx_info *out);
+/* primes_out: L + K values, data primes then special primes. */
+bcn_status bcn_ctx_primes(const bcn_ctx *ctx, uint64_t *primes_out);
+/* number of uint32 words of an evaluation key: dnum * 2 * (L + K) * N */
+size_t bcn_evk_words(const bcn_ctx *ctx);
+
+/* ------------------------------------------------------------ client side */
+/* Secret key (uniform ternary) and relinearisation key for hybrid key
+ * switching (digit j covers q_{j*alpha} .. q_{j*alpha+alpha-1}):
+ *     evk_j = (-a_j s + e_j + P g_j s^2, a_j),  P = prod p_m,
+ *     g_j = 1 mod the primes of digit j, 0 mod every other prime,
+ * a_j uniform, e_j centred binomial (eta 21).  Randomness: SplitMix64; the
+ * stream (seed, tag, index) starts from state mix64(seed + G*((tag << 40) +
+ * index + 1)), G = 0x9E3779B97F4A7C15, and each draw is state += G,
+ * mix64(state).  Tags: 1 secret key (index 0; s = (r mod 3) - 1), 2 evk a_j
+ * (index j*256 + limb; low 32 bits rejected above floor(2^32/q)*q, then
+ * mod q), 3 evk e_j (index j; popcount of 21 bits minus popcount of the next
+ * 21), 4 encryption a (index ct*256 + limb), 5 encryption e (index ct).
+ * The key is what lets the server compute Mult(c1, c2) of App. A without the
+ * secret.  sk_out: [N] int8; evk_out: bcn_evk_words() uint32, host memory. */
+bcn_status bcn_keygen(const bcn_ctx *ctx, uint64_t seed, int8_t *sk_out, uint32_t *evk_out);
+
+/* Per-tensor symmetric int8 quantisation of float weights:
+ * s_w = max|w| / 127, w_int = round(w / s_w) (ties away from zero), computed
+ * in fp64.  The ciphertext branch multiplies by integers (Mult(c, u) with an
+ * integer u costs no level).  Host memory. */
+bcn_status bcn_quantize(const float *w, size_t n, int8_t *w_int_out, double *s_w_out);
+
+/* CKKS encode (App. A: N/2 slots per plaintext) of real vectors:
+ * values [n_vec][B] (B <= N/2; slots B..N/2-1 are zero) at `scale` ->
+ * pts_out [n_vec][level][N]: m_j = round(scale * (2/N) sum_k z_k cos(pi j 5^k / N)),
+ * computed with an FFT in fp64.  BCN_E_SCALE if |m_j| >= 2^63. Host memory. */
+bcn_status bcn_encode(const bcn_ctx *ctx, const double *values, int n_vec, int B, int level, double scale,
+                      uint32_t *pts_out);
+
+/* Symmetric encryption (the client holds the key, Sec. 2):
+ * ct = (-a s + e + m, a) with a uniform per limb and e centred binomial, drawn
+ * from SplitMix64 streams of `seed` indexed by the ciphertext's position in
+ * this call.  pts [n_ct][level][N] -> cts_out [n_ct][2][level][N].  Host. */
+bcn_status bcn_encrypt(const bcn_ctx *ctx, const int8_t *sk, const uint32_t *pts, int n_ct, int level,
+                       uint64_t seed, uint32_t *cts_out);
+
+/* Encrypt the sensitive segment (Sec. 3): images [B][H][W][C] uint8; seg =
+ * {y0, x0, h, w}.  Ciphertext (c, y, x) (row-major) holds pixel
+ * (y0+y, x0+x, c) / 255 of every image, image b in slot b, encoded at `scale`
+ * at the top level L and encrypted as bcn_encrypt does.
+ * cts_out: [C*h*w][2][L][N], host memory. */
+bcn_status bcn_encrypt_segment(const bcn_ctx *ctx, const int8_t *sk, const uint8_t *images, int B, int H, int W,
+                               int C, const int seg[4], double scale, uint64_t seed, uint32_t *cts_out);
+
+/* Decrypt m = c0 + c1 s (mod q_i), recombine the residues into the centred
+ * integer (balanced-digit Garner CRT, exact), decode the first B slots and
+ * divide by `scale`.  cts [n_ct][2][level][N] -> out [n_ct][B].  Host. */
+bcn_status bcn_decrypt_decode(const bcn_ctx *ctx, const int8_t *sk, const uint32_t *cts, int n_ct, int level,
+                              double scale, int B, double *out);
+
+/* ------------------------------------------------ plaintext branch (fp32) */
+/* The plaintext branch (Sec. 3.1) runs on the whole image with the sensitive
+ * segment set to zero and the insensitive segment perturbed by additive
+ * noise; its taps give the unidirectional-connection features of Sec. 3.2:
+ * Resize = centre crop (offset floor((h_p - h_c)/2)), CRot = a ch_c x ch_p
+ * channel mix, or a fully connected map of the flattened (c, y, x) map. */
+typedef enum {
+    BCN_PLAIN_CONV = 0,     /* 2-D cross-correlation, weights [cout][cin][k][k], optional ReLU */
+    BCN_PLAIN_AVGPOOL2 = 1, /* 2x2 average pool, stride 2 */
+    BCN_PLAIN_TAP_CROP_CROT = 2, /* tap: centre crop to hc x wc, CRot weights [ch_c][ch_p] */
+    BCN_PLAIN_TAP_FC = 3    /* tap: fully connected, weights [n_out][C*H*W] */
+} bcn_plain_op;
+
+typedef struct {
+    int op;               /* bcn_plain_op */
+    int cin, cout, k, stride, pad, relu; /* BCN_PLAIN_CONV */
+    int hc, wc, ch_c;     /* BCN_PLAIN_TAP_CROP_CROT */
+    int n_out;            /* BCN_PLAIN_TAP_FC */
+    const float *weights; /* host fp32, layout above (NULL for AVGPOOL2) */
+} bcn_plain_stage;
+
+bcn_status bcn_plain_model_create(bcn_ctx *ctx, const bcn_plain_stage *stages, int n_stages, int H, int W, int C,
+                                  const int seg[4], bcn_plain_model **out);
+bcn_status bcn_plain_model_destroy(bcn_plain_model *m);
+/* total number of features over all taps (the rows of feats_dev) */
+bcn_status bcn_plain_feature_count(const bcn_plain_model *m, int *n_feat);
+bcn_status bcn_plain_workspace_bytes(const bcn_plain_model *m, int B, size_t *bytes);
+/* images_dev [B][H][W][C] uint8, noise_dev [B][H][W][C] fp32 (the perturbation
+ * drawn by the client), feats_dev [n_feat][B] fp32: taps in order, each tap's
+ * features flattened (c, y, x).  Device memory; asynchronous on `stream`. */
+bcn_status bcn_plain_branch_forward(const bcn_plain_model *m, const uint8_t *images_dev, const float *noise_dev,
+                                    int B, float *feats_dev, void *workspace_dev, size_t workspace_bytes,
+                                    void *cuda_stream);
+
+/* -------------------------------------------------- ciphertext branch (server) */
+typedef enum { BCN_LAYER_CONV = 0, BCN_LAYER_DENSE = 1 } bcn_layer_type;
+
+/* One linear layer of the ciphertext branch: conv (weights [cout][cin][k][k],
+ * input map cin x h x w, stride, zero padding `pad`) or dense (weights
+ * [n_out][n_in]); int8 weights w_int with scale s_w.  Inputs and outputs are
+ * flattened in (channel, row, column) order.  add != 0: a plaintext-branch
+ * feature is added to every output (the unidirectional connection
+ * x_{c,l} + z_{p,l}, Sec. 3.2).  square != 0: square activation (App. B),
+ * i.e. tensor square, relinearisation and rescale (one level). */
+typedef struct {
+    int type;
+    int cin, h, w, cout, k, stride, pad; /* conv */
+    int n_in, n_out;                     /* dense */
+    int add, square;
+    const int8_t *w_int; /* host */
+    double s_w;
+} bcn_layer;
+
+typedef struct {
+    int n_layers;
+    int n_in;         /* input ciphertexts of layer 0 */
+    int n_out;        /* output ciphertexts of the last layer */
+    int out_level;    /* level of the output ciphertexts */
+    int n_add;        /* layers with add != 0 */
+} bcn_model_info;
+
+bcn_status bcn_model_create(bcn_ctx *ctx, const bcn_layer *layers, int n_layers, bcn_model **out);
+bcn_status bcn_model_destroy(bcn_model *m);
+bcn_status bcn_model_get_info(const bcn_model *m, bcn_model_info *out);
+/* per layer: live level at its input and its output count (arrays of n_layers) */
+bcn_status bcn_model_layers(const bcn_model *m, int *level_out, int *n_out_out);
+/* Scale bookkeeping (host fp64): the weights divide the scale by s_w, a square
+ * squares it, a rescale divides it by the dropped prime.  add_scales_out
+ * [n_add]: the scale each added feature must be encoded at; out_scale: the
+ * scale of the outputs, for bcn_decrypt_decode. */
+bcn_status bcn_model_scales(const bcn_model *m, double input_scale, double *add_scales_out, double *out_scale);
+
+/* Convert a boundary-layout evaluation key (coefficient form, device memory)
+ * into the evaluator's form (NTT domain, Montgomery representation) in
+ * evk_eval_dev (same size; may equal evk_dev for in-place). */
+bcn_status bcn_evk_prepare(const bcn_ctx *ctx, const uint32_t *evk_dev, uint32_t *evk_eval_dev, void *cuda_stream);
+
+bcn_status bcn_eval_workspace_bytes(const bcn_model *m, size_t *bytes);
+
+/* Ciphertext-branch evaluation (the hot path): for each layer the integer
+ * weight multiply-accumulate, the optional feature add, the optional
+ * square + relinearise + rescale.  cts_dev [n_in][2][L][N];
+ * pts_dev[a] [n_out of the a-th add layer][its level][N] encoded at the scale
+ * bcn_model_scales gives; out_dev [n_out][2][out_level][N].  All device
+ * memory; evk_eval_dev from bcn_evk_prepare; workspace of at least
+ * bcn_eval_workspace_bytes.  Asynchronous on `cuda_stream`. */
+bcn_status bcn_eval(const bcn_model *m, const uint32_t *evk_eval_dev, const uint32_t *cts_dev,
+                    const uint32_t *const *pts_dev, uint32_t *out_dev, void *workspace_dev, size_t workspace_bytes,
+                    void *cuda_stream);
+
+/* Same evaluation with host inputs and outputs: copies cts_host and pts_host
+ * to device staging buffers carved from the workspace (size:
+ * bcn_eval_host_workspace_bytes), evaluates, copies the result to out_host
+ * and synchronises the stream.  Page-locked host buffers give full-rate copies. */
+bcn_status bcn_eval_host_workspace_bytes(const bcn_model *m, size_t *bytes);
+bcn_status bcn_eval_host(const bcn_model *m, const uint32_t *evk_eval_dev, const uint32_t *cts_host,
+                         const uint32_t *const *pts_host, uint32_t *out_host, void *workspace_dev,
+                         size_t workspace_bytes, void *cuda_stream);
+
+/* ------------------------------------------------- kernel timing (device) */
+/* Classes of the kernels bcn_eval launches. */
+typedef enum {
+    BCN_KERNEL_MAC = 0,             /* integer-weight multiply-accumulate + feature add */
+    BCN_KERNEL_NTT_FWD = 1,         /* forward negacyclic NTT */
+    BCN_KERNEL_NTT_INV = 2,         /* inverse negacyclic NTT */
+    BCN_KERNEL_TENSOR_SQUARE = 3,   /* (c0, c1) -> (c0^2, 2 c0 c1, c1^2) */
+    BCN_KERNEL_MODUP = 4,           /* digit decomposition + fast basis conversion */
+    BCN_KERNEL_KS_INNER = 5,        /* inner product with the evaluation key */
+    BCN_KERNEL_MODDOWN_RESCALE = 6, /* ModDown by P, add, rescale */
+    BCN_KERNEL_COUNT = 7
+} bcn_kernel_class;
+
+/* With timing enabled, bcn_eval records a CUDA event pair around every kernel
+ * it launches (on the evaluation's stream) and the algorithmic bytes that
+ * launch must move (each input and output limb once).  Enabling resets the
+ * totals.  bcn_profile_read waits for the recorded events and returns, for
+ * one class, the summed device time in ms, the launch count and the bytes. */
+bcn_status bcn_profile_enable(bcn_model *m, int enable);
+bcn_status bcn_profile_read(bcn_model *m, int kernel_class, double *total_ms, long long *launches, double *bytes);
+
+/* ------------------------------------------- single operations (device) */
+/* Each runs the evaluator's kernels for one step, on device buffers in the
+ * interchange layout, for op-level checks and benchmarks. */
+
+/* In-place negacyclic NTT of n_poly polynomials at `level` ([n_poly][level][N]):
+ * forward gives the evaluator's internal (bit-reversed) order, inverse undoes it. */
+bcn_status bcn_op_ntt(const bcn_ctx *ctx, uint32_t *data_dev, int n_poly, int level, int inverse, void *cuda_stream);
+/* out[o] = sum_t w[o][t] * in[idx[o][t]] (+ (pt[o], 0)); idx < 0 = zero tap.
+ * idx_dev [n_out][K] int32, w_dev [n_out][K] int8, pt_dev may be NULL. */
+bcn_status bcn_op_mac(const bcn_ctx *ctx, int level, int n_in, int n_out, int K, const int32_t *idx_dev,
+                      const int8_t *w_dev, const uint32_t *in_dev, const uint32_t *pt_dev, uint32_t *out_dev,
+                      void *cuda_stream);
+/* workspace for bcn_op_square_relin_rescale on n_ct ciphertexts at level */
+bcn_status bcn_op_workspace_bytes(const bcn_ctx *ctx, int level, int n_ct, size_t *bytes);
+/* tensor square: [n_ct][2][level][N] -> [n_ct][3][level][N] (coefficient form) */
+bcn_status bcn_op_tensor_square(const bcn_ctx *ctx, int level, const uint32_t *in_dev, int n_ct, uint32_t *out_dev,
+                                void *workspace_dev, size_t workspace_bytes, void *cuda_stream);
+/* square activation: tensor square, relinearise, rescale:
+ * [n_ct][2][level][N] -> [n_ct][2][level-1][N] */
+bcn_status bcn_op_square_relin_rescale(const bcn_ctx *ctx, int level, const uint32_t *evk_eval_dev,
+                                       const uint32_t *in_dev, int n_ct, uint32_t *out_dev, void *workspace_dev,
+                                       size_t workspace_bytes, void *cuda_stream);
+/* rescale alone: [n_ct][2][level][N] -> [n_ct][2][level-1][N] */
+bcn_status bcn_op_rescale(const bcn_ctx *ctx, int level, const uint32_t *in_dev, int n_ct, uint32_t *out_dev,
+                          void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BCN_H */

@@ -448,19 +448,24 @@ def plain_branch(cfg: dict, imgs: np.ndarray, noise: np.ndarray, weights) -> lis
 def fp64_network(cfg: dict, seg_vals: np.ndarray, feats: list, tables: list, scales: list) -> np.ndarray:
     """The same quantised network in float64 (real weights w_int * s_w, the
     square activation, the unidirectional adds): [n_in][B] -> [n_out][B]."""
-    x = seg_vals
-    fi = 0
-    for layer, (idx, wt), s_w in zip(cfg["cipher"], tables, scales):
-        safe = np.where(idx < 0, 0, idx)
-        wr = wt.astype(np.float64) * s_w * (idx >= 0)
-        y = np.einsum("ot,otb->ob", wr, x[safe], optimize=True)
-        if layer["add"]:
-            y = y + feats[fi]
-            fi += 1
-        if layer["square"]:
-            y = y * y
-        x = y
-    return x
+    B = seg_vals.shape[1]
+    step = 256  # images are independent: evaluate them in groups to bound memory
+    outs = []
+    for b0 in range(0, B, step):
+        x = seg_vals[:, b0:b0 + step]
+        fi = 0
+        for layer, (idx, wt), s_w in zip(cfg["cipher"], tables, scales):
+            safe = np.where(idx < 0, 0, idx)
+            wr = wt.astype(np.float64) * s_w * (idx >= 0)
+            y = np.einsum("ot,otb->ob", wr, x[safe], optimize=True)
+            if layer["add"]:
+                y = y + feats[fi][:, b0:b0 + step]
+                fi += 1
+            if layer["square"]:
+                y = y * y
+            x = y
+        outs.append(x)
+    return np.concatenate(outs, axis=1)
 
 
 def scale_schedule(cfg: dict, q, scales: list):

@@ -1,0 +1,364 @@
+// Client-side calls (host C++): keygen, weight quantisation, CKKS encode,
+// symmetric encryption, decryption + decode.  The client holds the secret
+// key (Sec. 2 threat model of the paper); none of this runs on the server's
+// evaluation path.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <functional>
+#include <thread>
+
+#include "bcn_internal.h"
+
+namespace bcn {
+namespace {
+
+// ---------------------------------------------------------------- threads
+void parallel_for(int n, const std::function<void(int)> &fn) {
+    int hw = (int)std::thread::hardware_concurrency();
+    int nt = std::max(1, std::min(n, hw > 0 ? hw : 1));
+    if (nt <= 1) {
+        for (int i = 0; i < n; i++) fn(i);
+        return;
+    }
+    std::vector<std::thread> th;
+    for (int t = 0; t < nt; t++)
+        th.emplace_back([&, t] {
+            for (int i = t; i < n; i += nt) fn(i);
+        });
+    for (auto &x : th) x.join();
+}
+
+// ------------------------------------------------------ 32-bit modular math
+inline uint32_t shoup(uint32_t a, uint32_t w, uint32_t wp, uint32_t q) {
+    uint32_t hi = (uint32_t)(((uint64_t)a * wp) >> 32);
+    uint32_t r = a * w - hi * q;
+    return r >= q ? r - q : r;
+}
+inline uint32_t addq(uint32_t a, uint32_t b, uint32_t q) { uint32_t s = a + b; return s >= q ? s - q : s; }
+inline uint32_t subq(uint32_t a, uint32_t b, uint32_t q) { return a >= b ? a - b : a + q - b; }
+inline uint32_t mulq(uint32_t a, uint32_t b, uint32_t q) { return (uint32_t)((uint64_t)a * b % q); }
+inline uint32_t from_signed(int64_t v, uint32_t q) {
+    int64_t r = v % (int64_t)q;
+    return (uint32_t)(r < 0 ? r + q : r);
+}
+
+// negacyclic NTT, bit-reversed output (Cooley-Tukey) / input (Gentleman-Sande)
+void ntt_fwd(const bcn_ctx *c, int t, uint32_t *a) {
+    const uint32_t q = (uint32_t)c->primes[t];
+    const uint32_t *w = c->h_tw_fwd[t].data();
+    const int N = c->N;
+    for (int m = 1, len = N >> 1; m < N; m <<= 1, len >>= 1)
+        for (int i = 0; i < m; i++) {
+            uint32_t W = w[2 * (m + i)], Wp = w[2 * (m + i) + 1];
+            uint32_t *x = a + 2 * i * len, *y = x + len;
+            for (int j = 0; j < len; j++) {
+                uint32_t u = x[j], v = shoup(y[j], W, Wp, q);
+                x[j] = addq(u, v, q);
+                y[j] = subq(u, v, q);
+            }
+        }
+}
+void ntt_inv(const bcn_ctx *c, int t, uint32_t *a) {
+    const uint32_t q = (uint32_t)c->primes[t];
+    const uint32_t *w = c->h_tw_inv[t].data();
+    const int N = c->N;
+    for (int m = N >> 1, len = 1; m >= 1; m >>= 1, len <<= 1)
+        for (int i = 0; i < m; i++) {
+            uint32_t W = w[2 * (m + i)], Wp = w[2 * (m + i) + 1];
+            uint32_t *x = a + 2 * i * len, *y = x + len;
+            for (int j = 0; j < len; j++) {
+                uint32_t u = x[j], v = y[j];
+                x[j] = addq(u, v, q);
+                y[j] = shoup(subq(u, v, q), W, Wp, q);
+            }
+        }
+    const PrimeConst &pc = c->h_pc[t];
+    for (int j = 0; j < N; j++) a[j] = shoup(a[j], pc.ninv, pc.ninv_shoup, q);
+}
+
+// ----------------------------------------------------------------- sampling
+// SplitMix64 (Steele, Lea, Flood 2014) with per-object streams.
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
+inline uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+struct Stream {
+    uint64_t s;
+    Stream(uint64_t seed, uint64_t tag, uint64_t idx) : s(mix64(seed + kGamma * ((tag << 40) + idx + 1))) {}
+    uint64_t next() { s += kGamma; return mix64(s); }
+    uint32_t uniform(uint32_t q) {
+        uint64_t bound = ((1ull << 32) / q) * q;
+        for (;;) {
+            uint64_t w = next() & 0xFFFFFFFFull;
+            if (w < bound) return (uint32_t)(w % q);
+        }
+    }
+    int cbd21() {
+        uint64_t r = next(), m = (1ull << 21) - 1;
+        return __builtin_popcountll(r & m) - __builtin_popcountll((r >> 21) & m);
+    }
+};
+enum : uint64_t { kTagSk = 1, kTagEvkA = 2, kTagEvkE = 3, kTagEncA = 4, kTagEncE = 5 };
+
+// --------------------------------------------------------------------- FFT
+// Unnormalised DFT with positive exponent: F_j = sum_u Y_u exp(2 pi i j u / n).
+struct Fft {
+    int n, logn;
+    std::vector<std::complex<double>> root;  // exp(2 pi i k / n), k < n
+    std::vector<uint32_t> rev;
+    explicit Fft(int n_) : n(n_), logn(0), root(n_), rev(n_) {
+        while ((1 << logn) < n) logn++;
+        for (int k = 0; k < n; k++) {
+            double a = 2.0 * M_PI * (double)k / (double)n;
+            root[k] = {std::cos(a), std::sin(a)};
+        }
+        for (int k = 0; k < n; k++) {
+            uint32_t r = 0, x = (uint32_t)k;
+            for (int b = 0; b < logn; b++) { r = (r << 1) | (x & 1); x >>= 1; }
+            rev[k] = r;
+        }
+    }
+    void run(std::complex<double> *a) const {
+        for (int k = 0; k < n; k++)
+            if ((int)rev[k] > k) std::swap(a[k], a[rev[k]]);
+        for (int len = 2; len <= n; len <<= 1) {
+            int half = len >> 1, step = n / len;
+            for (int i = 0; i < n; i += len)
+                for (int j = 0; j < half; j++) {
+                    std::complex<double> u = a[i + j], v = a[i + j + half] * root[(size_t)j * step];
+                    a[i + j] = u + v;
+                    a[i + j + half] = u - v;
+                }
+        }
+    }
+};
+
+// slot k sits at the odd exponent e_k = 5^k mod 2N; its conjugate at 2N - e_k
+std::vector<uint32_t> slot_exponents(int N) {
+    std::vector<uint32_t> e(N / 2);
+    uint64_t v = 1;
+    for (int k = 0; k < N / 2; k++) { e[k] = (uint32_t)v; v = v * 5 % (2 * (uint64_t)N); }
+    return e;
+}
+
+}  // namespace
+}  // namespace bcn
+
+using namespace bcn;
+
+extern "C" {
+
+bcn_status bcn_keygen(const bcn_ctx *c, uint64_t seed, int8_t *sk, uint32_t *evk) {
+    if (!c || !sk || !evk) return fail(BCN_E_INVAL, "bcn_keygen: null argument");
+    const int N = c->N, L = c->L, K = c->K, P = L + K, A = c->alpha;
+    Stream rs(seed, kTagSk, 0);
+    for (int j = 0; j < N; j++) sk[j] = (int8_t)((int)(rs.next() % 3) - 1);
+    // s and s^2 in the NTT domain of every prime
+    std::vector<std::vector<uint32_t>> S(P, std::vector<uint32_t>(N)), S2(P, std::vector<uint32_t>(N));
+    parallel_for(P, [&](int t) {
+        uint32_t q = (uint32_t)c->primes[t];
+        for (int j = 0; j < N; j++) S[t][j] = from_signed(sk[j], q);
+        ntt_fwd(c, t, S[t].data());
+        for (int j = 0; j < N; j++) S2[t][j] = mulq(S[t][j], S[t][j], q);
+        ntt_inv(c, t, S2[t].data());  // s^2, coefficient form
+    });
+    std::vector<uint32_t> Pmod(P);
+    for (int t = 0; t < P; t++) {
+        uint64_t q = c->primes[t], v = 1 % q;
+        for (int m = 0; m < K; m++) v = mulmod64(v, c->primes[L + m] % q, q);
+        Pmod[t] = (uint32_t)v;
+    }
+    parallel_for(c->dnum * P, [&](int job) {
+        int j = job / P, t = job % P;
+        uint32_t q = (uint32_t)c->primes[t];
+        Stream re(seed, kTagEvkE, (uint64_t)j);
+        Stream ra(seed, kTagEvkA, (uint64_t)j * 256 + (uint64_t)t);
+        uint32_t *b = evk + ((size_t)(j * 2 + 0) * P + t) * N;
+        uint32_t *a = evk + ((size_t)(j * 2 + 1) * P + t) * N;
+        std::vector<uint32_t> as(N);
+        for (int k = 0; k < N; k++) a[k] = ra.uniform(q);
+        std::copy(a, a + N, as.begin());
+        ntt_fwd(c, t, as.data());
+        for (int k = 0; k < N; k++) as[k] = mulq(as[k], S[t][k], q);
+        ntt_inv(c, t, as.data());
+        bool in_digit = t < L && t >= j * A && t < std::min((j + 1) * A, L);
+        for (int k = 0; k < N; k++) {
+            uint32_t v = subq(from_signed(re.cbd21(), q), as[k], q);
+            if (in_digit) v = addq(v, mulq(Pmod[t], S2[t][k], q), q);
+            b[k] = v;
+        }
+    });
+    return BCN_OK;
+}
+
+bcn_status bcn_quantize(const float *w, size_t n, int8_t *w_int, double *s_w) {
+    if ((!w || !w_int) && n) return fail(BCN_E_INVAL, "bcn_quantize: null argument");
+    if (!s_w) return fail(BCN_E_INVAL, "bcn_quantize: null s_w");
+    double mx = 0.0;
+    for (size_t i = 0; i < n; i++) mx = std::max(mx, std::fabs((double)w[i]));
+    if (mx == 0.0) {
+        for (size_t i = 0; i < n; i++) w_int[i] = 0;
+        *s_w = 1.0;
+        return BCN_OK;
+    }
+    double s = mx / 127.0;
+    for (size_t i = 0; i < n; i++) {
+        long long r = std::llround((double)w[i] / s);
+        if (r > 127 || r < -127) return fail(BCN_E_INVAL, "bcn_quantize: value outside [-127, 127]");
+        w_int[i] = (int8_t)r;
+    }
+    *s_w = s;
+    return BCN_OK;
+}
+
+bcn_status bcn_encode(const bcn_ctx *c, const double *values, int n_vec, int B, int level, double scale,
+                      uint32_t *pts) {
+    if (!c || (!values && n_vec) || (!pts && n_vec)) return fail(BCN_E_INVAL, "bcn_encode: null argument");
+    const int N = c->N;
+    if (B < 0 || B > N / 2 || level < 1 || level > c->L || n_vec < 0)
+        return fail(BCN_E_INVAL, "bcn_encode: bad batch or level");
+    Fft fft(N);
+    std::vector<uint32_t> e = slot_exponents(N);
+    std::vector<std::complex<double>> twist(N);  // omega^j = exp(i pi j / N)
+    for (int j = 0; j < N; j++) twist[j] = {std::cos(M_PI * j / N), std::sin(M_PI * j / N)};
+    std::vector<int> bad(n_vec, 0);
+    parallel_for(n_vec, [&](int v) {
+        // Y_u = Z_{2u+1}: slot k at exponents e_k and 2N - e_k
+        std::vector<std::complex<double>> y(N, 0.0);
+        const double *z = values + (size_t)v * B;
+        for (int k = 0; k < B; k++) {
+            y[(e[k] - 1) / 2] += z[k];
+            y[(2 * N - e[k] - 1) / 2] += z[k];
+        }
+        fft.run(y.data());
+        uint32_t *out = pts + (size_t)v * level * N;
+        for (int j = 0; j < N; j++) {
+            double x = (twist[j] * y[j]).real() * (scale / N);
+            if (!(std::fabs(x) < 9.2e18)) { bad[v] = 1; return; }
+            long long m = std::llround(x);
+            for (int i = 0; i < level; i++) out[(size_t)i * N + j] = from_signed(m, (uint32_t)c->primes[i]);
+        }
+    });
+    for (int v = 0; v < n_vec; v++)
+        if (bad[v]) return fail(BCN_E_SCALE, "bcn_encode: a coefficient does not fit in 63 bits");
+    return BCN_OK;
+}
+
+bcn_status bcn_encrypt(const bcn_ctx *c, const int8_t *sk, const uint32_t *pts, int n_ct, int level,
+                       uint64_t seed, uint32_t *cts) {
+    if (!c || !sk || ((!pts || !cts) && n_ct)) return fail(BCN_E_INVAL, "bcn_encrypt: null argument");
+    if (level < 1 || level > c->L || n_ct < 0) return fail(BCN_E_INVAL, "bcn_encrypt: bad level or count");
+    const int N = c->N;
+    std::vector<std::vector<uint32_t>> S(level, std::vector<uint32_t>(N));
+    for (int i = 0; i < level; i++) {
+        uint32_t q = (uint32_t)c->primes[i];
+        for (int j = 0; j < N; j++) S[i][j] = from_signed(sk[j], q);
+        ntt_fwd(c, i, S[i].data());
+    }
+    parallel_for(n_ct, [&](int ci) {
+        std::vector<int> e(N);
+        Stream re(seed, kTagEncE, (uint64_t)ci);
+        for (int k = 0; k < N; k++) e[k] = re.cbd21();
+        std::vector<uint32_t> as(N);
+        for (int i = 0; i < level; i++) {
+            uint32_t q = (uint32_t)c->primes[i];
+            Stream ra(seed, kTagEncA, (uint64_t)ci * 256 + (uint64_t)i);
+            uint32_t *c0 = cts + (((size_t)ci * 2 + 0) * level + i) * N;
+            uint32_t *c1 = cts + (((size_t)ci * 2 + 1) * level + i) * N;
+            for (int k = 0; k < N; k++) c1[k] = ra.uniform(q);
+            std::copy(c1, c1 + N, as.begin());
+            ntt_fwd(c, i, as.data());
+            for (int k = 0; k < N; k++) as[k] = mulq(as[k], S[i][k], q);
+            ntt_inv(c, i, as.data());
+            const uint32_t *m = pts + ((size_t)ci * level + i) * N;
+            for (int k = 0; k < N; k++) c0[k] = addq(subq(from_signed(e[k], q), as[k], q), m[k] % q, q);
+        }
+    });
+    return BCN_OK;
+}
+
+bcn_status bcn_encrypt_segment(const bcn_ctx *c, const int8_t *sk, const uint8_t *images, int B, int H, int W,
+                               int C, const int seg[4], double scale, uint64_t seed, uint32_t *cts) {
+    if (!c || !sk || !images || !seg || !cts) return fail(BCN_E_INVAL, "bcn_encrypt_segment: null argument");
+    int y0 = seg[0], x0 = seg[1], h = seg[2], w = seg[3];
+    if (B < 1 || B > c->N / 2 || y0 < 0 || x0 < 0 || h < 1 || w < 1 || y0 + h > H || x0 + w > W || C < 1)
+        return fail(BCN_E_INVAL, "bcn_encrypt_segment: segment outside the image or bad batch");
+    int n_ct = C * h * w;
+    std::vector<double> vals((size_t)n_ct * B);
+    for (int ch = 0; ch < C; ch++)
+        for (int y = 0; y < h; y++)
+            for (int x = 0; x < w; x++) {
+                size_t ct = ((size_t)ch * h + y) * w + x;
+                for (int b = 0; b < B; b++)
+                    vals[ct * B + b] = images[(((size_t)b * H + y0 + y) * W + x0 + x) * C + ch] / 255.0;
+            }
+    std::vector<uint32_t> pts((size_t)n_ct * c->L * c->N);
+    bcn_status st = bcn_encode(c, vals.data(), n_ct, B, c->L, scale, pts.data());
+    if (st != BCN_OK) return st;
+    return bcn_encrypt(c, sk, pts.data(), n_ct, c->L, seed, cts);
+}
+
+bcn_status bcn_decrypt_decode(const bcn_ctx *c, const int8_t *sk, const uint32_t *cts, int n_ct, int level,
+                              double scale, int B, double *out) {
+    if (!c || !sk || ((!cts || !out) && n_ct)) return fail(BCN_E_INVAL, "bcn_decrypt_decode: null argument");
+    const int N = c->N;
+    if (level < 1 || level > c->L || B < 0 || B > N / 2 || n_ct < 0)
+        return fail(BCN_E_INVAL, "bcn_decrypt_decode: bad level or batch");
+    std::vector<std::vector<uint32_t>> S(level, std::vector<uint32_t>(N));
+    for (int i = 0; i < level; i++) {
+        uint32_t q = (uint32_t)c->primes[i];
+        for (int j = 0; j < N; j++) S[i][j] = from_signed(sk[j], q);
+        ntt_fwd(c, i, S[i].data());
+    }
+    // balanced-digit Garner: x = v_0 + v_1 M_1 + ... , M_i = q_0...q_{i-1}, |v_i| <= (q_i-1)/2
+    std::vector<std::vector<uint32_t>> Mmod(level, std::vector<uint32_t>(level));  // M_j mod q_i
+    std::vector<uint32_t> Minv(level);                                             // M_i^{-1} mod q_i
+    for (int i = 0; i < level; i++) {
+        uint64_t qi = c->primes[i];
+        for (int j = 0; j <= i; j++) {
+            uint64_t v = 1 % qi;
+            for (int k = 0; k < j; k++) v = mulmod64(v, c->primes[k] % qi, qi);
+            Mmod[i][j] = (uint32_t)v;
+        }
+        Minv[i] = (uint32_t)invmod64(Mmod[i][i], qi);
+    }
+    Fft fft(N);
+    std::vector<uint32_t> e = slot_exponents(N);
+    std::vector<double> cs(N), sn(N);  // omega^k = exp(i pi k / N)
+    for (int k = 0; k < N; k++) { cs[k] = std::cos(M_PI * k / N); sn[k] = std::sin(M_PI * k / N); }
+    parallel_for(n_ct, [&](int ci) {
+        std::vector<uint32_t> m((size_t)level * N), t(N);
+        for (int i = 0; i < level; i++) {
+            uint32_t q = (uint32_t)c->primes[i];
+            const uint32_t *c0 = cts + (((size_t)ci * 2 + 0) * level + i) * N;
+            const uint32_t *c1 = cts + (((size_t)ci * 2 + 1) * level + i) * N;
+            std::copy(c1, c1 + N, t.begin());
+            ntt_fwd(c, i, t.data());
+            for (int k = 0; k < N; k++) t[k] = mulq(t[k], S[i][k], q);
+            ntt_inv(c, i, t.data());
+            for (int k = 0; k < N; k++) m[(size_t)i * N + k] = addq(c0[k] % q, t[k], q);
+        }
+        std::vector<std::complex<double>> y(N);
+        std::vector<int64_t> v(level);
+        for (int k = 0; k < N; k++) {
+            for (int i = 0; i < level; i++) {
+                uint32_t qi = (uint32_t)c->primes[i];
+                uint32_t s = 0;  // x_{<i} mod q_i
+                for (int j = 0; j < i; j++) s = addq(s, mulq(from_signed(v[j], qi), Mmod[i][j], qi), qi);
+                uint32_t d = mulq(subq(m[(size_t)i * N + k], s, qi), Minv[i], qi);
+                v[i] = d <= (qi - 1) / 2 ? (int64_t)d : (int64_t)d - (int64_t)qi;
+            }
+            double x = 0.0;
+            for (int i = level - 1; i >= 0; i--) x = x * (double)c->primes[i] + (double)v[i];
+            y[k] = {x * cs[k], x * sn[k]};  // m_k * omega^k
+        }
+        fft.run(y.data());  // X_{2u+1} = sum_k m_k omega^{k (2u+1)}
+        for (int b = 0; b < B; b++) out[(size_t)ci * B + b] = y[(e[b] - 1) / 2].real() / scale;
+    });
+    return BCN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,853 @@
+// Ciphertext-branch evaluation on the device (the hot path).
+//
+// Per layer of the ciphertext branch (Sec. 3.2 and App. B of the paper):
+//   1. MAC      out[o] = sum_t w[o][t] * in[idx[o][t]]  (integer weights, exact)
+//   2. add      c0 += pt[o]                             (unidirectional connection)
+//   3. square   (c0, c1) -> (c0^2, 2 c0 c1, c1^2)        (tensor square, NTT domain)
+//   4. relin    key switching of c1^2: ModUp (digit decomposition + fast
+//               basis conversion), inner product with the evaluation key,
+//               ModDown by P
+//   5. rescale  divide by the last live prime
+// Steps 3-5 run over chunks of output ciphertexts whose intermediates fit in L2.
+#include <algorithm>
+#include <cuda_runtime.h>
+
+#include "device_api.h"
+#include "device_math.cuh"
+
+namespace bcn {
+
+struct KsDev {
+    const uint2 *dhat_inv, *dhat, *phat_inv, *phat, *pinv, *qtop_inv;
+    const uint32_t *dprod, *pmod;
+    int L, K, alpha, dnum_max, P;
+};
+
+static KsDev ks_dev(const bcn_ctx *c) {
+    const KsTables &t = c->ks;
+    KsDev k;
+    k.dhat_inv = reinterpret_cast<const uint2 *>(c->d_ks + t.off_dhat_inv);
+    k.dhat = reinterpret_cast<const uint2 *>(c->d_ks + t.off_dhat);
+    k.dprod = c->d_ks + t.off_dprod;
+    k.phat_inv = reinterpret_cast<const uint2 *>(c->d_ks + t.off_phat_inv);
+    k.phat = reinterpret_cast<const uint2 *>(c->d_ks + t.off_phat);
+    k.pmod = c->d_ks + t.off_pmod;
+    k.pinv = reinterpret_cast<const uint2 *>(c->d_ks + t.off_pinv);
+    k.qtop_inv = reinterpret_cast<const uint2 *>(c->d_ks + t.off_qtop_inv);
+    k.L = t.L; k.K = t.K; k.alpha = t.alpha; k.dnum_max = t.dnum_max; k.P = t.P;
+    return k;
+}
+
+// ------------------------------------------------------------------- kernels
+// MAC + feature add.  grid (N/4/256, 2*level, n_out), 256 threads, 4 coefficients each.
+__global__ void __launch_bounds__(256) k_mac(const uint32_t *__restrict__ in, uint32_t *__restrict__ out,
+                                             const int32_t *__restrict__ idx, const int8_t *__restrict__ w,
+                                             const uint32_t *__restrict__ pt, int K, int level, int N, int o_base,
+                                             const PrimeConst *__restrict__ pc) {
+    const int k4 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k4 * 4 >= N) return;
+    const int o = o_base + blockIdx.z;
+    const int poly = blockIdx.y / level, i = blockIdx.y % level;
+    const int32_t *id = idx + (size_t)o * K;
+    const int8_t *ww = w + (size_t)o * K;
+    long long a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    for (int t = 0; t < K; t++) {
+        const int src = __ldg(id + t);
+        if (src < 0) continue;
+        const long long wt = (long long)__ldg(ww + t);
+        const uint4 x = __ldg(reinterpret_cast<const uint4 *>(in + (((size_t)src * 2 + poly) * level + i) * N) + k4);
+        a0 += wt * x.x;
+        a1 += wt * x.y;
+        a2 += wt * x.z;
+        a3 += wt * x.w;
+    }
+    const uint32_t q = pc[i].q;
+    const uint64_t mu = pc[i].barrett;
+    const long long off = (long long)pc[i].mac_offset;
+    uint4 r;
+    r.x = barrett_reduce64((uint64_t)(a0 + off), q, mu);
+    r.y = barrett_reduce64((uint64_t)(a1 + off), q, mu);
+    r.z = barrett_reduce64((uint64_t)(a2 + off), q, mu);
+    r.w = barrett_reduce64((uint64_t)(a3 + off), q, mu);
+    if (pt != nullptr && poly == 0) {
+        const uint4 p = __ldg(reinterpret_cast<const uint4 *>(pt + ((size_t)o * level + i) * N) + k4);
+        r.x = add_mod(r.x, p.x, q);
+        r.y = add_mod(r.y, p.y, q);
+        r.z = add_mod(r.z, p.z, q);
+        r.w = add_mod(r.w, p.w, q);
+    }
+    reinterpret_cast<uint4 *>(out + (((size_t)blockIdx.z * 2 + poly) * level + i) * N)[k4] = r;
+}
+
+// Tensor square in the NTT domain: Y [C][2][n][N] -> D [C][3][n][N].
+// grid (N/4/256, n, C)
+__global__ void __launch_bounds__(256) k_tensor_square(const uint32_t *__restrict__ Y, uint32_t *__restrict__ D,
+                                                       int n, int N, const PrimeConst *__restrict__ pc) {
+    const int k4 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k4 * 4 >= N) return;
+    const int i = blockIdx.y, ct = blockIdx.z;
+    const PrimeConst P = pc[i];
+    const uint4 c0 = reinterpret_cast<const uint4 *>(Y + (((size_t)ct * 2 + 0) * n + i) * N)[k4];
+    const uint4 c1 = reinterpret_cast<const uint4 *>(Y + (((size_t)ct * 2 + 1) * n + i) * N)[k4];
+    uint4 d0, d1, d2;
+#define BCN_SQ(f)                                                             \
+    {                                                                         \
+        uint32_t a = shoup_mul(c0.f, P.r_mod, P.r_shoup, P.q);                \
+        uint32_t b = shoup_mul(c1.f, P.r_mod, P.r_shoup, P.q);                \
+        d0.f = mont_mul(a, c0.f, P.q, P.qneg_inv);                            \
+        uint32_t x = mont_mul(a, c1.f, P.q, P.qneg_inv);                      \
+        d1.f = add_mod(x, x, P.q);                                            \
+        d2.f = mont_mul(b, c1.f, P.q, P.qneg_inv);                            \
+    }
+    BCN_SQ(x) BCN_SQ(y) BCN_SQ(z) BCN_SQ(w)
+#undef BCN_SQ
+    reinterpret_cast<uint4 *>(D + (((size_t)ct * 3 + 0) * n + i) * N)[k4] = d0;
+    reinterpret_cast<uint4 *>(D + (((size_t)ct * 3 + 1) * n + i) * N)[k4] = d1;
+    reinterpret_cast<uint4 *>(D + (((size_t)ct * 3 + 2) * n + i) * N)[k4] = d2;
+}
+
+// ModUp of d2 (coefficient form) for every digit j into the extended basis
+// Q_n u P:  EXT [C][dnum][n+K][N].  On the digit's own primes the residue is
+// copied; elsewhere the centred fast basis conversion
+//     sum_u r_u * Dhat_u - cnt * D_j  (mod t),  r_u = [x_u Dhat_u^{-1}]_{q_u},
+// cnt = #{u : r_u > (q_u - 1)/2}.   grid (N/256, C)
+__global__ void __launch_bounds__(256) k_modup(const uint32_t *__restrict__ D, uint32_t *__restrict__ ext, int n,
+                                               int N, KsDev ks, const PrimeConst *__restrict__ pc) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const int ct = blockIdx.y;
+    const int A = ks.alpha, dnum = (n + A - 1) / A, nb = n + ks.K;
+    const uint32_t *x = D + ((size_t)ct * 3 + 2) * n * N;
+    uint32_t *e = ext + (size_t)ct * dnum * nb * N;
+    for (int j = 0; j < dnum; j++) {
+        const int lo = j * A, hi = min(lo + A, n);
+        uint32_t r[4];
+        int cnt = 0;
+        for (int u = 0; u < hi - lo; u++) {
+            const int i = lo + u;
+            const uint2 di = ks.dhat_inv[(size_t)(n * ks.dnum_max + j) * A + u];
+            r[u] = shoup_mul(__ldg(x + (size_t)i * N + k), di.x, di.y, pc[i].q);
+            cnt += r[u] > pc[i].half;
+        }
+        for (int t = 0; t < nb; t++) {
+            const int pt = t < n ? t : ks.L + (t - n);
+            const uint32_t qt = pc[pt].q;
+            uint32_t v;
+            if (t >= lo && t < hi) {
+                v = __ldg(x + (size_t)t * N + k);
+            } else {
+                v = 0;
+                for (int u = 0; u < hi - lo; u++) {
+                    const uint2 dh = ks.dhat[((size_t)(n * ks.dnum_max + j) * A + u) * ks.P + pt];
+                    v = add_mod(v, shoup_mul(r[u], dh.x, dh.y, qt), qt);
+                }
+                const uint32_t dp = ks.dprod[(size_t)(n * ks.dnum_max + j) * ks.P + pt];
+                for (int c = 0; c < cnt; c++) v = sub_mod(v, dp, qt);
+            }
+            e[((size_t)j * nb + t) * N + k] = v;
+        }
+    }
+}
+
+// Key-switching inner product in the NTT domain: ACC[b] = sum_j EXT_j * evk_j[b]
+// (evk in Montgomery form, so one Montgomery product gives the plain product).
+// EXT [C][dnum][n+K][N] -> ACC [C][2][n+K][N].  grid (N/4/256, n+K, C)
+__global__ void __launch_bounds__(256) k_ks_inner(const uint32_t *__restrict__ ext, const uint32_t *__restrict__ evk,
+                                                  uint32_t *__restrict__ acc, int n, int N, int L, int K,
+                                                  const PrimeConst *__restrict__ pc, int alpha) {
+    const int k4 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k4 * 4 >= N) return;
+    const int t = blockIdx.y, ct = blockIdx.z;
+    const int nb = n + K, dnum = (n + alpha - 1) / alpha, P = L + K;
+    const int pt = t < n ? t : L + (t - n);
+    const uint32_t q = pc[pt].q, qi = pc[pt].qneg_inv;
+    uint4 a0 = make_uint4(0, 0, 0, 0), a1 = make_uint4(0, 0, 0, 0);
+    for (int j = 0; j < dnum; j++) {
+        const uint4 e = reinterpret_cast<const uint4 *>(ext + (((size_t)ct * dnum + j) * nb + t) * N)[k4];
+        const uint4 k0 = __ldg(reinterpret_cast<const uint4 *>(evk + ((size_t)(j * 2 + 0) * P + pt) * N) + k4);
+        const uint4 k1 = __ldg(reinterpret_cast<const uint4 *>(evk + ((size_t)(j * 2 + 1) * P + pt) * N) + k4);
+        a0.x = add_mod(a0.x, mont_mul(e.x, k0.x, q, qi), q);
+        a0.y = add_mod(a0.y, mont_mul(e.y, k0.y, q, qi), q);
+        a0.z = add_mod(a0.z, mont_mul(e.z, k0.z, q, qi), q);
+        a0.w = add_mod(a0.w, mont_mul(e.w, k0.w, q, qi), q);
+        a1.x = add_mod(a1.x, mont_mul(e.x, k1.x, q, qi), q);
+        a1.y = add_mod(a1.y, mont_mul(e.y, k1.y, q, qi), q);
+        a1.z = add_mod(a1.z, mont_mul(e.z, k1.z, q, qi), q);
+        a1.w = add_mod(a1.w, mont_mul(e.w, k1.w, q, qi), q);
+    }
+    reinterpret_cast<uint4 *>(acc + (((size_t)ct * 2 + 0) * nb + t) * N)[k4] = a0;
+    reinterpret_cast<uint4 *>(acc + (((size_t)ct * 2 + 1) * nb + t) * N)[k4] = a1;
+}
+
+// ModDown by P, add to (d0, d1), then rescale by q_top -- the two roundings in
+// sequence.  D [C][3][n][N] and ACC [C][2][n+K][N] in coefficient form ->
+// out [C][2][n-1][N].   grid (N/256, 2, C)
+__global__ void __launch_bounds__(256) k_moddown_rescale(const uint32_t *__restrict__ D,
+                                                         const uint32_t *__restrict__ acc, uint32_t *__restrict__ out,
+                                                         int n, int N, KsDev ks, const PrimeConst *__restrict__ pc) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const int b = blockIdx.y, ct = blockIdx.z;
+    const int nb = n + ks.K, L = ks.L;
+    const uint32_t *db = D + ((size_t)ct * 3 + b) * n * N;
+    const uint32_t *ab = acc + ((size_t)ct * 2 + b) * nb * N;
+    uint32_t *ob = out + ((size_t)ct * 2 + b) * (n - 1) * N;
+    uint32_t r[4];
+    int cnt = 0;
+    for (int m = 0; m < ks.K; m++) {
+        const PrimeConst &pm = pc[L + m];
+        const uint2 hi = ks.phat_inv[m];
+        r[m] = shoup_mul(ab[(size_t)(n + m) * N + k], hi.x, hi.y, pm.q);
+        cnt += r[m] > pm.half;
+    }
+    auto limb = [&](int i) -> uint32_t {
+        const uint32_t q = pc[i].q;
+        uint32_t conv = 0;
+        for (int m = 0; m < ks.K; m++) {
+            const uint2 ph = ks.phat[(size_t)m * L + i];
+            conv = add_mod(conv, shoup_mul(r[m], ph.x, ph.y, q), q);
+        }
+        const uint32_t pmod = ks.pmod[i];
+        for (int c = 0; c < cnt; c++) conv = sub_mod(conv, pmod, q);
+        const uint2 pi = ks.pinv[i];
+        const uint32_t kv = shoup_mul(sub_mod(ab[(size_t)i * N + k], conv, q), pi.x, pi.y, q);
+        return add_mod(db[(size_t)i * N + k], kv, q);
+    };
+    const int top = n - 1;
+    const uint32_t ctop = limb(top), qtop = pc[top].q;
+    const bool neg = ctop > pc[top].half;
+    for (int i = 0; i < top; i++) {
+        const uint32_t q = pc[i].q;
+        uint32_t v = sub_mod(limb(i), ctop, q);
+        if (neg) v = add_mod(v, qtop, q);
+        const uint2 qi = ks.qtop_inv[(size_t)top * L + i];
+        ob[(size_t)i * N + k] = shoup_mul(v, qi.x, qi.y, q);
+    }
+}
+
+// Rescale alone: in [C][2][n][N] -> out [C][2][n-1][N] (coefficient form). grid (N/256, 2, C)
+__global__ void __launch_bounds__(256) k_rescale(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int n,
+                                                 int N, KsDev ks, const PrimeConst *__restrict__ pc) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const int b = blockIdx.y, ct = blockIdx.z, top = n - 1;
+    const uint32_t *ib = in + ((size_t)ct * 2 + b) * n * N;
+    uint32_t *ob = out + ((size_t)ct * 2 + b) * (n - 1) * N;
+    const uint32_t ctop = ib[(size_t)top * N + k], qtop = pc[top].q;
+    const bool neg = ctop > pc[top].half;
+    for (int i = 0; i < top; i++) {
+        const uint32_t q = pc[i].q;
+        uint32_t v = sub_mod(ib[(size_t)i * N + k], ctop, q);
+        if (neg) v = add_mod(v, qtop, q);
+        const uint2 qi = ks.qtop_inv[(size_t)top * ks.L + i];
+        ob[(size_t)i * N + k] = shoup_mul(v, qi.x, qi.y, q);
+    }
+}
+
+// x -> x * R mod q over rows of N words; row r uses prime pm.pidx[r % period]
+__global__ void k_to_mont(uint32_t *__restrict__ data, int N, PrimeMap pm, const PrimeConst *__restrict__ pc) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const int row = blockIdx.y;
+    const PrimeConst &P = pc[pm.pidx[row % pm.period]];
+    uint32_t *x = data + (size_t)row * N + k;
+    *x = shoup_mul(*x, P.r_mod, P.r_shoup, P.q);
+}
+
+// ------------------------------------------------------------- host helpers
+static bcn_status check_device(const bcn_ctx *c) {
+    if (!c) return fail(BCN_E_INVAL, "null ctx");
+    if (c->device < 0) return fail(BCN_E_INVAL, "host-only ctx (created with device < 0)");
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) return fail(BCN_E_CUDA, "cudaGetDevice failed");
+    if (cur != c->device)
+        return fail(BCN_E_INVAL, "ctx belongs to device " + std::to_string(c->device) + ", current device is " +
+                                     std::to_string(cur));
+    return BCN_OK;
+}
+
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
+
+static size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+#define BCN_TRY(x)                          \
+    do {                                    \
+        bcn_status _s = (x);                \
+        if (_s != BCN_OK) return _s;        \
+    } while (0)
+
+// CUDA-event pair around one launch when the model's profiler is on
+struct Timed {
+    Profiler *p;
+    cudaStream_t st;
+    int cls;
+    double bytes;
+    size_t e0 = 0;
+    Timed(Profiler *p_, cudaStream_t st_, int cls_, double bytes_)
+        : p(p_ && p_->on ? p_ : nullptr), st(st_), cls(cls_), bytes(bytes_) {
+        if (p) e0 = mark();
+    }
+    size_t mark() {
+        if (p->used == p->ev.size()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            p->ev.push_back(e);
+        }
+        cudaEventRecord(p->ev[p->used], st);
+        return p->used++;
+    }
+    ~Timed() {
+        if (p) {
+            size_t e1 = mark();
+            p->recs.push_back({cls, e0, e1, bytes});
+        }
+    }
+};
+
+// words of the chunk buffers per ciphertext at level n
+struct ChunkLayout {
+    size_t y, d, ext, acc;  // words per ciphertext
+};
+static ChunkLayout chunk_layout(const bcn_ctx *c, int n) {
+    const size_t N = c->N;
+    const int nb = n + c->K, dnum = (n + c->alpha - 1) / c->alpha;
+    return {2 * (size_t)n * N, 3 * (size_t)n * N, (size_t)dnum * nb * N, 2 * (size_t)nb * N};
+}
+static size_t chunk_bytes(const bcn_ctx *c, int n, int chunk) {
+    ChunkLayout l = chunk_layout(c, n);
+    return align_up(l.y * 4 * chunk) + align_up(l.d * 4 * chunk) + align_up(l.ext * 4 * chunk) +
+           align_up(l.acc * 4 * chunk);
+}
+static int default_chunk(const bcn_ctx *c, int n, int n_ct) {
+    const size_t target = 48ull << 20;  // keep the key-switching intermediates of a chunk L2-resident
+    ChunkLayout l = chunk_layout(c, n);
+    size_t per = (l.y + l.d + l.ext + l.acc) * 4;
+    int ch = (int)std::min<size_t>(4096, std::max<size_t>(1, target / per));
+    return std::max(1, std::min(ch, std::max(1, n_ct)));
+}
+
+struct ChunkBufs {
+    uint32_t *y, *d, *ext, *acc;
+};
+static ChunkBufs carve_chunk(const bcn_ctx *c, int n, int chunk, char *ws) {
+    ChunkLayout l = chunk_layout(c, n);
+    ChunkBufs b;
+    b.y = reinterpret_cast<uint32_t *>(ws);
+    ws += align_up(l.y * 4 * chunk);
+    b.d = reinterpret_cast<uint32_t *>(ws);
+    ws += align_up(l.d * 4 * chunk);
+    b.ext = reinterpret_cast<uint32_t *>(ws);
+    ws += align_up(l.ext * 4 * chunk);
+    b.acc = reinterpret_cast<uint32_t *>(ws);
+    return b;
+}
+
+static bcn_status launch_mac(const bcn_ctx *c, int level, int K, const int32_t *idx, const int8_t *w,
+                             const uint32_t *in, const uint32_t *pt, uint32_t *out, int o_base, int n_o,
+                             cudaStream_t st, Profiler *prof = nullptr, int n_distinct_in = 0) {
+    if (n_o <= 0) return BCN_OK;
+    const int N = c->N;
+    const double limb = (double)N * 4;
+    Timed tm(prof, st, BCN_KERNEL_MAC,
+             limb * ((double)n_distinct_in * 2 * level + (double)n_o * 2 * level + (pt ? (double)n_o * level : 0)));
+    for (int z0 = 0; z0 < n_o; z0 += 65535) {  // grid.z limit
+        const int nz = std::min(65535, n_o - z0);
+        dim3 grid((unsigned)((N / 4 + 255) / 256), (unsigned)(2 * level), (unsigned)nz);
+        k_mac<<<grid, 256, 0, st>>>(in, out + (size_t)z0 * 2 * level * N, idx, w, pt, K, level, N, o_base + z0,
+                                    c->d_pc);
+        BCN_TRY(check_launch("k_mac"));
+    }
+    return BCN_OK;
+}
+
+// steps 3-5 on a chunk: Y (MAC output, coefficient form, destroyed) -> out
+static bcn_status square_chunk(const bcn_ctx *c, int n, const uint32_t *evk, const ChunkBufs &b, int C,
+                               uint32_t *out, cudaStream_t st, Profiler *prof = nullptr) {
+    const int N = c->N, K = c->K, nb = n + K, dnum = (n + c->alpha - 1) / c->alpha;
+    const PrimeMap dm = data_map(n), em = ext_map(c, n);
+    const KsDev ks = ks_dev(c);
+    const double limb = (double)N * 4;
+    {
+        Timed tm(prof, st, BCN_KERNEL_NTT_FWD, limb * 2 * C * 2 * n);
+        BCN_TRY(launch_ntt(c, b.y, (size_t)C * 2 * n, dm, false, st));
+    }
+    {
+        Timed tm(prof, st, BCN_KERNEL_TENSOR_SQUARE, limb * C * 5 * n);
+        k_tensor_square<<<dim3((N / 4 + 255) / 256, n, C), 256, 0, st>>>(b.y, b.d, n, N, c->d_pc);
+        BCN_TRY(check_launch("k_tensor_square"));
+    }
+    {
+        Timed tm(prof, st, BCN_KERNEL_NTT_INV, limb * 2 * C * 3 * n);
+        BCN_TRY(launch_ntt(c, b.d, (size_t)C * 3 * n, dm, true, st));
+    }
+    {
+        Timed tm(prof, st, BCN_KERNEL_MODUP, limb * C * (n + (double)dnum * nb));
+        k_modup<<<dim3((N + 255) / 256, C), 256, 0, st>>>(b.d, b.ext, n, N, ks, c->d_pc);
+        BCN_TRY(check_launch("k_modup"));
+    }
+    {
+        Timed tm(prof, st, BCN_KERNEL_NTT_FWD, limb * 2 * C * dnum * nb);
+        BCN_TRY(launch_ntt(c, b.ext, (size_t)C * dnum * nb, em, false, st));
+    }
+    {
+        Timed tm(prof, st, BCN_KERNEL_KS_INNER, limb * ((double)C * (dnum * nb + 2 * nb) + 2.0 * dnum * nb));
+        k_ks_inner<<<dim3((N / 4 + 255) / 256, nb, C), 256, 0, st>>>(b.ext, evk, b.acc, n, N, c->L, K, c->d_pc,
+                                                                     c->alpha);
+        BCN_TRY(check_launch("k_ks_inner"));
+    }
+    {
+        Timed tm(prof, st, BCN_KERNEL_NTT_INV, limb * 2 * C * 2 * nb);
+        BCN_TRY(launch_ntt(c, b.acc, (size_t)C * 2 * nb, em, true, st));
+    }
+    Timed tm(prof, st, BCN_KERNEL_MODDOWN_RESCALE, limb * C * (2.0 * n + 2.0 * nb + 2.0 * (n - 1)));
+    k_moddown_rescale<<<dim3((N + 255) / 256, 2, C), 256, 0, st>>>(b.d, b.acc, out, n, N, ks, c->d_pc);
+    return check_launch("k_moddown_rescale");
+}
+
+// ----------------------------------------------------------- device context
+bcn_status device_ctx_init(bcn_ctx *c) {
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(BCN_E_CUDA, "cudaSetDevice failed");
+    const int P = c->L + c->K, N = c->N;
+    if (cudaMalloc(&c->d_pc, sizeof(PrimeConst) * P) != cudaSuccess ||
+        cudaMalloc(&c->d_tw_fwd, sizeof(uint2) * (size_t)P * N) != cudaSuccess ||
+        cudaMalloc(&c->d_tw_inv, sizeof(uint2) * (size_t)P * N) != cudaSuccess ||
+        cudaMalloc(&c->d_ks, sizeof(uint32_t) * c->ks.host.size()) != cudaSuccess)
+        return fail(BCN_E_NOMEM, "device allocation of the context tables failed");
+    bool ok = cudaMemcpy(c->d_pc, c->h_pc.data(), sizeof(PrimeConst) * P, cudaMemcpyHostToDevice) == cudaSuccess;
+    for (int t = 0; t < P && ok; t++) {
+        ok = cudaMemcpy(c->d_tw_fwd + (size_t)t * N, c->h_tw_fwd[t].data(), sizeof(uint2) * N,
+                        cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(c->d_tw_inv + (size_t)t * N, c->h_tw_inv[t].data(), sizeof(uint2) * N,
+                        cudaMemcpyHostToDevice) == cudaSuccess;
+    }
+    ok = ok && cudaMemcpy(c->d_ks, c->ks.host.data(), sizeof(uint32_t) * c->ks.host.size(),
+                          cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!ok) return fail(BCN_E_CUDA, "upload of the context tables failed");
+    return ntt_setup_kernels();
+}
+
+void device_ctx_free(bcn_ctx *c) {
+    cudaFree(c->d_pc);
+    cudaFree(c->d_tw_fwd);
+    cudaFree(c->d_tw_inv);
+    cudaFree(c->d_ks);
+    c->d_pc = nullptr;
+    c->d_tw_fwd = c->d_tw_inv = nullptr;
+    c->d_ks = nullptr;
+}
+
+}  // namespace bcn
+
+using namespace bcn;
+
+// ===================================================================== ABI
+extern "C" {
+
+// ------------------------------------------------------------------ model
+bcn_status bcn_model_create(bcn_ctx *c, const bcn_layer *layers, int n_layers, bcn_model **out) {
+    if (!c || !layers || !out || n_layers < 1) return fail(BCN_E_INVAL, "bcn_model_create: bad argument");
+    *out = nullptr;
+    BCN_TRY(check_device(c));
+    bcn_model *m = new bcn_model();
+    m->ctx = c;
+    int level = c->L, prev_out = -1;
+    size_t x_bytes = 0;
+    int max_sq_level = 0, max_sq_out = 0;
+    auto cleanup = [&](bcn_status s, const std::string &msg) {
+        bcn_model_destroy(m);
+        return fail(s, msg);
+    };
+    for (int l = 0; l < n_layers; l++) {
+        const bcn_layer &L = layers[l];
+        bcn_layer_plan p{};
+        p.type = L.type;
+        p.add = L.add != 0;
+        p.square = L.square != 0;
+        p.s_w = L.s_w;
+        p.level = level;
+        std::vector<int32_t> idx;
+        std::vector<int8_t> w;
+        if (!L.w_int) return cleanup(BCN_E_INVAL, "layer " + std::to_string(l) + ": null weights");
+        if (L.type == BCN_LAYER_CONV) {
+            if (L.cin < 1 || L.h < 1 || L.w < 1 || L.cout < 1 || L.k < 1 || L.stride < 1 || L.pad < 0 ||
+                L.h + 2 * L.pad < L.k || L.w + 2 * L.pad < L.k)
+                return cleanup(BCN_E_INVAL, "layer " + std::to_string(l) + ": bad conv geometry");
+            const int ho = (L.h + 2 * L.pad - L.k) / L.stride + 1, wo = (L.w + 2 * L.pad - L.k) / L.stride + 1;
+            p.n_in = L.cin * L.h * L.w;
+            p.n_out = L.cout * ho * wo;
+            p.K = L.cin * L.k * L.k;
+            idx.assign((size_t)p.n_out * p.K, -1);
+            w.assign((size_t)p.n_out * p.K, 0);
+            for (int co = 0; co < L.cout; co++)
+                for (int oy = 0; oy < ho; oy++)
+                    for (int ox = 0; ox < wo; ox++) {
+                        const size_t o = ((size_t)co * ho + oy) * wo + ox;
+                        for (int ci = 0; ci < L.cin; ci++)
+                            for (int ky = 0; ky < L.k; ky++)
+                                for (int kx = 0; kx < L.k; kx++) {
+                                    const int iy = oy * L.stride - L.pad + ky, ix = ox * L.stride - L.pad + kx;
+                                    if (iy < 0 || iy >= L.h || ix < 0 || ix >= L.w) continue;
+                                    const size_t t = ((size_t)ci * L.k + ky) * L.k + kx;
+                                    idx[o * p.K + t] = (ci * L.h + iy) * L.w + ix;
+                                    w[o * p.K + t] = L.w_int[(((size_t)co * L.cin + ci) * L.k + ky) * L.k + kx];
+                                }
+                    }
+        } else if (L.type == BCN_LAYER_DENSE) {
+            if (L.n_in < 1 || L.n_out < 1) return cleanup(BCN_E_INVAL, "layer " + std::to_string(l) + ": bad dense");
+            p.n_in = L.n_in;
+            p.n_out = L.n_out;
+            p.K = L.n_in;
+            idx.resize((size_t)p.n_out * p.K);
+            w.assign(L.w_int, L.w_int + (size_t)p.n_out * p.K);
+            for (int o = 0; o < p.n_out; o++)
+                for (int k = 0; k < p.K; k++) idx[(size_t)o * p.K + k] = k;
+        } else {
+            return cleanup(BCN_E_INVAL, "layer " + std::to_string(l) + ": unknown type");
+        }
+        if (p.K > (1 << 20)) return cleanup(BCN_E_INVAL, "layer fan-in above 2^20");
+        if (prev_out >= 0 && p.n_in != prev_out)
+            return cleanup(BCN_E_INVAL, "layer " + std::to_string(l) + ": input count does not match");
+        if (p.square && level < 2) return cleanup(BCN_E_LEVEL, "no level left for the square of layer " +
+                                                                   std::to_string(l));
+        if (cudaMalloc(&p.d_idx, idx.size() * 4) != cudaSuccess || cudaMalloc(&p.d_w, w.size()) != cudaSuccess) {
+            m->layers.push_back(p);
+            return cleanup(BCN_E_NOMEM, "device allocation of layer tables failed");
+        }
+        m->layers.push_back(p);
+        if (cudaMemcpy(p.d_idx, idx.data(), idx.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(p.d_w, w.data(), w.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            return cleanup(BCN_E_CUDA, "upload of layer tables failed");
+        if (p.square) {
+            max_sq_level = std::max(max_sq_level, level);
+            max_sq_out = std::max(max_sq_out, p.n_out);
+            level -= 1;
+        }
+        if (l + 1 < n_layers) x_bytes = std::max(x_bytes, (size_t)p.n_out * 2 * level * c->N * 4);
+        prev_out = p.n_out;
+    }
+    m->out_level = level;
+    m->ws_x_bytes = align_up(x_bytes);
+    m->chunk = max_sq_level ? default_chunk(c, max_sq_level, max_sq_out) : 1;
+    m->ws_chunk_bytes = max_sq_level ? chunk_bytes(c, max_sq_level, m->chunk) : 0;
+    // inputs each MAC launch reads (for the algorithmic byte count of the profiler)
+    for (size_t l = 0; l < m->layers.size(); l++) {
+        const bcn_layer_plan &p = m->layers[l];
+        std::vector<int> counts;
+        const int step = p.square ? m->chunk : p.n_out;
+        std::vector<int32_t> idx((size_t)p.n_out * p.K);
+        cudaMemcpy(idx.data(), p.d_idx, idx.size() * 4, cudaMemcpyDeviceToHost);
+        std::vector<char> seen(p.n_in);
+        for (int o0 = 0; o0 < p.n_out; o0 += step) {
+            std::fill(seen.begin(), seen.end(), 0);
+            int cnt = 0;
+            for (size_t i = (size_t)o0 * p.K; i < (size_t)std::min(p.n_out, o0 + step) * p.K; i++)
+                if (idx[i] >= 0 && !seen[idx[i]]) { seen[idx[i]] = 1; cnt++; }
+            counts.push_back(cnt);
+        }
+        m->distinct_inputs.push_back(counts);
+    }
+    *out = m;
+    return BCN_OK;
+}
+
+bcn_status bcn_model_destroy(bcn_model *m) {
+    if (!m) return BCN_OK;
+    for (auto &p : m->layers) {
+        cudaFree(p.d_idx);
+        cudaFree(p.d_w);
+    }
+    for (auto e : m->prof.ev) cudaEventDestroy(e);
+    delete m;
+    return BCN_OK;
+}
+
+bcn_status bcn_model_get_info(const bcn_model *m, bcn_model_info *o) {
+    if (!m || !o) return fail(BCN_E_INVAL, "bcn_model_get_info: null argument");
+    o->n_layers = (int)m->layers.size();
+    o->n_in = m->layers.front().n_in;
+    o->n_out = m->layers.back().n_out;
+    o->out_level = m->out_level;
+    o->n_add = 0;
+    for (auto &p : m->layers) o->n_add += p.add;
+    return BCN_OK;
+}
+
+bcn_status bcn_model_layers(const bcn_model *m, int *level_out, int *n_out_out) {
+    if (!m || !level_out || !n_out_out) return fail(BCN_E_INVAL, "bcn_model_layers: null argument");
+    for (size_t l = 0; l < m->layers.size(); l++) {
+        level_out[l] = m->layers[l].level;
+        n_out_out[l] = m->layers[l].n_out;
+    }
+    return BCN_OK;
+}
+
+bcn_status bcn_model_scales(const bcn_model *m, double input_scale, double *add_scales, double *out_scale) {
+    if (!m || !out_scale) return fail(BCN_E_INVAL, "bcn_model_scales: null argument");
+    double S = input_scale;
+    int a = 0;
+    for (auto &p : m->layers) {
+        S = S / p.s_w;
+        if (p.add) {
+            if (add_scales) add_scales[a] = S;
+            a++;
+        }
+        if (p.square) S = S * S / (double)m->ctx->primes[p.level - 1];
+    }
+    *out_scale = S;
+    return BCN_OK;
+}
+
+bcn_status bcn_evk_prepare(const bcn_ctx *c, const uint32_t *evk, uint32_t *evk_eval, void *stream) {
+    BCN_TRY(check_device(c));
+    if (!evk || !evk_eval || !aligned16(evk) || !aligned16(evk_eval))
+        return fail(BCN_E_INVAL, "bcn_evk_prepare: null or unaligned buffer");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t words = bcn_evk_words(c);
+    if (evk != evk_eval && cudaMemcpyAsync(evk_eval, evk, words * 4, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return fail(BCN_E_CUDA, "bcn_evk_prepare: copy failed");
+    const PrimeMap all = data_map(c->L + c->K);
+    const size_t rows = (size_t)c->dnum * 2 * (c->L + c->K);
+    BCN_TRY(launch_ntt(c, evk_eval, rows, all, false, st));
+    k_to_mont<<<dim3((c->N + 255) / 256, (unsigned)rows), 256, 0, st>>>(evk_eval, c->N, all, c->d_pc);
+    return check_launch("k_to_mont");
+}
+
+bcn_status bcn_eval_workspace_bytes(const bcn_model *m, size_t *bytes) {
+    if (!m || !bytes) return fail(BCN_E_INVAL, "bcn_eval_workspace_bytes: null argument");
+    *bytes = 2 * m->ws_x_bytes + m->ws_chunk_bytes;
+    return BCN_OK;
+}
+
+bcn_status bcn_eval(const bcn_model *m, const uint32_t *evk, const uint32_t *cts, const uint32_t *const *pts,
+                    uint32_t *out, void *ws, size_t ws_bytes, void *stream) {
+    if (!m) return fail(BCN_E_INVAL, "bcn_eval: null model");
+    const bcn_ctx *c = m->ctx;
+    BCN_TRY(check_device(c));
+    size_t need = 0;
+    bcn_eval_workspace_bytes(m, &need);
+    if (ws_bytes < need) return fail(BCN_E_BUDGET, "bcn_eval: workspace too small");
+    if (!cts || !out || (need && !ws) || !evk) return fail(BCN_E_INVAL, "bcn_eval: null buffer");
+    if (!aligned16(cts) || !aligned16(out) || !aligned16(ws) || !aligned16(evk))
+        return fail(BCN_E_INVAL, "bcn_eval: buffers must be 16-byte aligned");
+    cudaStream_t st = (cudaStream_t)stream;
+    char *w = reinterpret_cast<char *>(ws);
+    uint32_t *X[2] = {reinterpret_cast<uint32_t *>(w), reinterpret_cast<uint32_t *>(w + m->ws_x_bytes)};
+    char *chunk_ws = w + 2 * m->ws_x_bytes;
+    const uint32_t *x = cts;
+    int a = 0;
+    const size_t N = c->N;
+    for (size_t l = 0; l < m->layers.size(); l++) {
+        const bcn_layer_plan &p = m->layers[l];
+        const bool last = l + 1 == m->layers.size();
+        uint32_t *y = last ? out : X[l % 2];
+        const uint32_t *pt = nullptr;
+        if (p.add) {
+            if (!pts || !pts[a] || !aligned16(pts[a])) return fail(BCN_E_INVAL, "bcn_eval: missing feature plaintexts");
+            pt = pts[a++];
+        }
+        Profiler *prof = &m->prof;
+        if (!p.square) {
+            BCN_TRY(launch_mac(c, p.level, p.K, p.d_idx, p.d_w, x, pt, y, 0, p.n_out, st, prof,
+                               m->distinct_inputs[l][0]));
+        } else {
+            const int n = p.level;
+            ChunkBufs b = carve_chunk(c, n, m->chunk, chunk_ws);
+            for (int o0 = 0, ci = 0; o0 < p.n_out; o0 += m->chunk, ci++) {
+                const int C = std::min(m->chunk, p.n_out - o0);
+                BCN_TRY(launch_mac(c, n, p.K, p.d_idx, p.d_w, x, pt, b.y, o0, C, st, prof,
+                                   m->distinct_inputs[l][ci]));
+                BCN_TRY(square_chunk(c, n, evk, b, C, y + (size_t)o0 * 2 * (n - 1) * N, st, prof));
+            }
+        }
+        x = y;
+    }
+    return BCN_OK;
+}
+
+static size_t pts_words(const bcn_model *m, int a_idx) {
+    int a = 0;
+    for (auto &p : m->layers)
+        if (p.add) {
+            if (a == a_idx) return (size_t)p.n_out * p.level * m->ctx->N;
+            a++;
+        }
+    return 0;
+}
+
+bcn_status bcn_eval_host_workspace_bytes(const bcn_model *m, size_t *bytes) {
+    if (!m || !bytes) return fail(BCN_E_INVAL, "bcn_eval_host_workspace_bytes: null argument");
+    size_t b = 0;
+    bcn_eval_workspace_bytes(m, &b);
+    const bcn_ctx *c = m->ctx;
+    b = align_up(b);
+    b += align_up((size_t)m->layers.front().n_in * 2 * c->L * c->N * 4);
+    int n_add = 0;
+    for (auto &p : m->layers) n_add += p.add;
+    for (int a = 0; a < n_add; a++) b += align_up(pts_words(m, a) * 4);
+    b += align_up((size_t)m->layers.back().n_out * 2 * m->out_level * c->N * 4);
+    *bytes = b;
+    return BCN_OK;
+}
+
+bcn_status bcn_eval_host(const bcn_model *m, const uint32_t *evk, const uint32_t *cts_h,
+                         const uint32_t *const *pts_h, uint32_t *out_h, void *ws, size_t ws_bytes, void *stream) {
+    if (!m || !cts_h || !out_h) return fail(BCN_E_INVAL, "bcn_eval_host: null argument");
+    const bcn_ctx *c = m->ctx;
+    BCN_TRY(check_device(c));
+    size_t need = 0, eval_need = 0;
+    bcn_eval_host_workspace_bytes(m, &need);
+    bcn_eval_workspace_bytes(m, &eval_need);
+    if (ws_bytes < need || !ws) return fail(BCN_E_BUDGET, "bcn_eval_host: workspace too small");
+    cudaStream_t st = (cudaStream_t)stream;
+    char *w = reinterpret_cast<char *>(ws);
+    char *p = w + align_up(eval_need);
+    const size_t cts_b = (size_t)m->layers.front().n_in * 2 * c->L * c->N * 4;
+    uint32_t *cts_d = reinterpret_cast<uint32_t *>(p);
+    p += align_up(cts_b);
+    if (cudaMemcpyAsync(cts_d, cts_h, cts_b, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return fail(BCN_E_CUDA, "bcn_eval_host: input copy failed");
+    std::vector<const uint32_t *> pts_d;
+    int n_add = 0;
+    for (auto &l : m->layers) n_add += l.add;
+    for (int a = 0; a < n_add; a++) {
+        if (!pts_h || !pts_h[a]) return fail(BCN_E_INVAL, "bcn_eval_host: missing feature plaintexts");
+        const size_t b = pts_words(m, a) * 4;
+        if (cudaMemcpyAsync(p, pts_h[a], b, cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return fail(BCN_E_CUDA, "bcn_eval_host: feature copy failed");
+        pts_d.push_back(reinterpret_cast<const uint32_t *>(p));
+        p += align_up(b);
+    }
+    uint32_t *out_d = reinterpret_cast<uint32_t *>(p);
+    BCN_TRY(bcn_eval(m, evk, cts_d, pts_d.data(), out_d, ws, eval_need, stream));
+    const size_t out_b = (size_t)m->layers.back().n_out * 2 * m->out_level * c->N * 4;
+    if (cudaMemcpyAsync(out_h, out_d, out_b, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return fail(BCN_E_CUDA, "bcn_eval_host: output copy failed");
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(BCN_E_CUDA, std::string("bcn_eval_host: ") + cudaGetErrorString(e));
+    return BCN_OK;
+}
+
+// ------------------------------------------------------------- kernel timing
+bcn_status bcn_profile_enable(bcn_model *m, int enable) {
+    if (!m) return fail(BCN_E_INVAL, "bcn_profile_enable: null model");
+    Profiler &p = m->prof;
+    if (!p.recs.empty()) cudaDeviceSynchronize();
+    p.on = enable != 0;
+    p.recs.clear();
+    p.used = 0;
+    for (int k = 0; k < BCN_KERNEL_COUNT; k++) { p.ms[k] = 0; p.launches[k] = 0; p.bytes[k] = 0; }
+    return BCN_OK;
+}
+
+bcn_status bcn_profile_read(bcn_model *m, int cls, double *ms, long long *launches, double *bytes) {
+    if (!m || cls < 0 || cls >= BCN_KERNEL_COUNT) return fail(BCN_E_INVAL, "bcn_profile_read: bad argument");
+    Profiler &p = m->prof;
+    for (const auto &r : p.recs) {
+        if (cudaEventSynchronize(p.ev[r.e1]) != cudaSuccess) return fail(BCN_E_CUDA, "bcn_profile_read: event wait");
+        float t = 0;
+        cudaEventElapsedTime(&t, p.ev[r.e0], p.ev[r.e1]);
+        p.ms[r.cls] += t;
+        p.launches[r.cls] += 1;
+        p.bytes[r.cls] += r.bytes;
+    }
+    p.recs.clear();
+    p.used = 0;
+    if (ms) *ms = p.ms[cls];
+    if (launches) *launches = p.launches[cls];
+    if (bytes) *bytes = p.bytes[cls];
+    return BCN_OK;
+}
+
+// --------------------------------------------------------- single operations
+bcn_status bcn_op_ntt(const bcn_ctx *c, uint32_t *data, int n_poly, int level, int inverse, void *stream) {
+    BCN_TRY(check_device(c));
+    if (!data || !aligned16(data) || n_poly < 0 || level < 1 || level > c->L)
+        return fail(BCN_E_INVAL, "bcn_op_ntt: bad argument");
+    return launch_ntt(c, data, (size_t)n_poly * level, data_map(level), inverse != 0, (cudaStream_t)stream);
+}
+
+bcn_status bcn_op_mac(const bcn_ctx *c, int level, int n_in, int n_out, int K, const int32_t *idx, const int8_t *w,
+                      const uint32_t *in, const uint32_t *pt, uint32_t *out, void *stream) {
+    BCN_TRY(check_device(c));
+    if (!idx || !w || !in || !out || level < 1 || level > c->L || n_in < 0 || n_out < 0 || K < 0 || K > (1 << 20))
+        return fail(BCN_E_INVAL, "bcn_op_mac: bad argument");
+    if (!aligned16(in) || !aligned16(out) || (pt && !aligned16(pt)))
+        return fail(BCN_E_INVAL, "bcn_op_mac: buffers must be 16-byte aligned");
+    {  // every tap must name an input ciphertext or be a zero tap
+        std::vector<int32_t> h((size_t)n_out * K);
+        if (!h.empty() && cudaMemcpy(h.data(), idx, h.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return fail(BCN_E_CUDA, "bcn_op_mac: reading idx failed");
+        for (int32_t v : h)
+            if (v < -1 || v >= n_in) return fail(BCN_E_INVAL, "bcn_op_mac: idx entry outside [-1, n_in)");
+    }
+    return launch_mac(c, level, K, idx, w, in, pt, out, 0, n_out, (cudaStream_t)stream);
+}
+
+bcn_status bcn_op_workspace_bytes(const bcn_ctx *c, int level, int n_ct, size_t *bytes) {
+    if (!c || !bytes || level < 1 || level > c->L || n_ct < 0) return fail(BCN_E_INVAL, "bcn_op_workspace_bytes");
+    *bytes = chunk_bytes(c, level, default_chunk(c, level, n_ct));
+    return BCN_OK;
+}
+
+bcn_status bcn_op_tensor_square(const bcn_ctx *c, int level, const uint32_t *in, int n_ct, uint32_t *out, void *ws,
+                                size_t ws_bytes, void *stream) {
+    BCN_TRY(check_device(c));
+    size_t need = 0;
+    BCN_TRY(bcn_op_workspace_bytes(c, level, n_ct, &need));
+    if (ws_bytes < need || !ws) return fail(BCN_E_BUDGET, "bcn_op_tensor_square: workspace too small");
+    if (!in || !out || !aligned16(in) || !aligned16(out)) return fail(BCN_E_INVAL, "bcn_op_tensor_square: buffers");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int N = c->N, n = level, chunk = default_chunk(c, level, n_ct);
+    ChunkBufs b = carve_chunk(c, n, chunk, reinterpret_cast<char *>(ws));
+    for (int o0 = 0; o0 < n_ct; o0 += chunk) {
+        const int C = std::min(chunk, n_ct - o0);
+        if (cudaMemcpyAsync(b.y, in + (size_t)o0 * 2 * n * N, (size_t)C * 2 * n * N * 4, cudaMemcpyDeviceToDevice,
+                            st) != cudaSuccess)
+            return fail(BCN_E_CUDA, "copy failed");
+        BCN_TRY(launch_ntt(c, b.y, (size_t)C * 2 * n, data_map(n), false, st));
+        uint32_t *d = out + (size_t)o0 * 3 * n * N;
+        k_tensor_square<<<dim3((N / 4 + 255) / 256, n, C), 256, 0, st>>>(b.y, d, n, N, c->d_pc);
+        BCN_TRY(check_launch("k_tensor_square"));
+        BCN_TRY(launch_ntt(c, d, (size_t)C * 3 * n, data_map(n), true, st));
+    }
+    return BCN_OK;
+}
+
+bcn_status bcn_op_square_relin_rescale(const bcn_ctx *c, int level, const uint32_t *evk, const uint32_t *in,
+                                       int n_ct, uint32_t *out, void *ws, size_t ws_bytes, void *stream) {
+    BCN_TRY(check_device(c));
+    if (level < 2 || level > c->L) return fail(BCN_E_LEVEL, "bcn_op_square_relin_rescale: level must be >= 2");
+    size_t need = 0;
+    BCN_TRY(bcn_op_workspace_bytes(c, level, n_ct, &need));
+    if (ws_bytes < need || !ws) return fail(BCN_E_BUDGET, "bcn_op_square_relin_rescale: workspace too small");
+    if (!in || !out || !evk || !aligned16(in) || !aligned16(out) || !aligned16(evk))
+        return fail(BCN_E_INVAL, "bcn_op_square_relin_rescale: buffers");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int N = c->N, n = level, chunk = default_chunk(c, level, n_ct);
+    ChunkBufs b = carve_chunk(c, n, chunk, reinterpret_cast<char *>(ws));
+    for (int o0 = 0; o0 < n_ct; o0 += chunk) {
+        const int C = std::min(chunk, n_ct - o0);
+        if (cudaMemcpyAsync(b.y, in + (size_t)o0 * 2 * n * N, (size_t)C * 2 * n * N * 4, cudaMemcpyDeviceToDevice,
+                            st) != cudaSuccess)
+            return fail(BCN_E_CUDA, "copy failed");
+        BCN_TRY(square_chunk(c, n, evk, b, C, out + (size_t)o0 * 2 * (n - 1) * N, st));
+    }
+    return BCN_OK;
+}
+
+bcn_status bcn_op_rescale(const bcn_ctx *c, int level, const uint32_t *in, int n_ct, uint32_t *out, void *stream) {
+    BCN_TRY(check_device(c));
+    if (level < 2 || level > c->L) return fail(BCN_E_LEVEL, "bcn_op_rescale: level must be >= 2");
+    if (!in || !out || n_ct < 0) return fail(BCN_E_INVAL, "bcn_op_rescale: bad argument");
+    if (n_ct == 0) return BCN_OK;
+    const size_t N = c->N;
+    for (int z0 = 0; z0 < n_ct; z0 += 65535) {  // grid.z limit
+        const int nz = std::min(65535, n_ct - z0);
+        k_rescale<<<dim3((c->N + 255) / 256, 2, nz), 256, 0, (cudaStream_t)stream>>>(
+            in + (size_t)z0 * 2 * level * N, out + (size_t)z0 * 2 * (level - 1) * N, level, c->N, ks_dev(c), c->d_pc);
+        BCN_TRY(check_launch("k_rescale"));
+    }
+    return BCN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,162 @@
+"""Whole ciphertext-branch evaluation on the GPU (through the C ABI) against
+the oracle: bit-exact on every output limb for the small MNIST-shaped network,
+the CryptoNets-scale network (the benchmark's workload and launch
+configuration) and a CIFAR-shaped network on the full N = 16384 ring; at the
+CIFAR-shaped network's full size, decrypt(eval(encrypt(x))) within 1e-3 of the
+fp64 network with the same argmax.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from oracle import oracle as O
+from paper_2402_01296_gb300 import bcn
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-3  # decoded logits vs the fp64 plaintext network, max-abs
+
+
+def dev(a):
+    return bcn.to_device(a)
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return bcn.to_host_u32(t)
+
+
+def argmax_ok(dec, ref, margin=2e-3):
+    top2 = np.sort(ref, axis=0)[-2:]
+    clear = (top2[1] - top2[0]) > margin
+    return bool(np.all(np.argmax(dec, 0)[clear] == np.argmax(ref, 0)[clear])), int((~clear).sum())
+
+
+def run_gpu(cfg, w_int, s_w, evk, cts, pts):
+    ctx = bcn.Context.from_config(cfg)
+    model = bcn.Model(ctx, cfg["cipher"], w_int, s_w)
+    evk_eval = ctx.evk_prepare(dev(evk))
+    out = torch.empty(model.out_shape(), dtype=torch.int32, device="cuda")
+    ws = model.alloc_workspace()
+    model.eval(evk_eval, dev(cts), [dev(p) for p in pts], out, ws)
+    return ctx, model, evk_eval, host(out)
+
+
+CASES = {
+    "cnn3_small": lambda: workloads.get_config("cnn3_small"),
+    "cryptonets": lambda: workloads.get_config("cryptonets"),
+    "cifar_reduced": lambda: workloads.reduced_cifar(cout1=2, cout2=3, seg=8, batch=512),
+}
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def case(request):
+    cfg = CASES[request.param]()
+    prob = O.Problem(cfg)
+    trace = []
+    ref = prob.evaluate(trace)
+    return cfg, prob, ref
+
+
+def test_eval_bit_exact(case):
+    cfg, prob, ref = case
+    ctx, model, _, got = run_gpu(cfg, prob.w_int, prob.s_w, prob.evk, prob.cts, prob.pts)
+    assert got.shape == ref.shape
+    assert np.array_equal(got, ref), f"{np.mean(got != ref):.3%} of residues differ"
+    # scale schedule and levels agree with the oracle's bookkeeping
+    adds, out_scale = model.scales(2.0 ** cfg["log_scale"])
+    assert adds == prob.add_scales and out_scale == prob.out_scale
+    assert model.levels == prob.levels and model.out_level == prob.out_level
+    # decrypted logits: within TOL of the fp64 network, same argmax
+    dec = prob.decode_output(got)
+    fp = prob.fp64_logits()
+    assert np.abs(dec - fp).max() < TOL
+    ok, ties = argmax_ok(dec, fp)
+    assert ok
+
+
+def test_eval_host_path_matches_device_path(case):
+    cfg, prob, ref = case
+    ctx = bcn.Context.from_config(cfg)
+    model = bcn.Model(ctx, cfg["cipher"], prob.w_int, prob.s_w)
+    evk_eval = ctx.evk_prepare(dev(prob.evk))
+    ws = model.alloc_workspace(host=True)
+    out = np.zeros(model.out_shape(), dtype=np.uint32)
+    for _ in range(2):  # repeated calls reuse the workspace
+        out[:] = 0
+        model.eval_host(evk_eval, prob.cts, [np.ascontiguousarray(p) for p in prob.pts], out, ws)
+        assert np.array_equal(out, ref)
+
+
+def test_eval_is_deterministic_and_stream_ordered():
+    cfg = workloads.with_batch(workloads.get_config("cnn3_small"), 128)
+    prob = O.Problem(cfg)
+    ctx = bcn.Context.from_config(cfg)
+    model = bcn.Model(ctx, cfg["cipher"], prob.w_int, prob.s_w)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        evk_eval = ctx.evk_prepare(dev(prob.evk), stream=s)
+        cts, pts = dev(prob.cts), [dev(p) for p in prob.pts]
+        ws = model.alloc_workspace()
+        outs = []
+        for _ in range(3):
+            o = torch.empty(model.out_shape(), dtype=torch.int32, device="cuda")
+            model.eval(evk_eval, cts, pts, o, ws, stream=s)
+            outs.append(o)
+    s.synchronize()
+    ref = prob.evaluate()
+    for o in outs:
+        assert np.array_equal(bcn.to_host_u32(o), ref)
+
+
+@pytest.mark.parametrize("name", ["cnn3_small", "cryptonets", "cifar_cnn"])
+def test_plain_branch_forward(name):
+    """fp32 plaintext branch on the GPU vs the oracle's fp64 one."""
+    cfg = workloads.with_batch(workloads.get_config(name), 96)
+    imgs, noise, pw = workloads.images(cfg), workloads.laplace_noise(cfg), workloads.plain_weights(cfg)
+    ref = np.concatenate(O.plain_branch(cfg, imgs, noise, pw), axis=0)
+    ctx = bcn.Context.from_config(cfg)
+    pm = bcn.PlainModel(ctx, cfg["plain"], pw, cfg["image"], cfg["segment"])
+    assert pm.n_feat == ref.shape[0]
+    feats = torch.empty((pm.n_feat, cfg["batch"]), dtype=torch.float32, device="cuda")
+    ws = torch.empty(pm.workspace_bytes(cfg["batch"]) // 4 + 1, dtype=torch.int32, device="cuda")
+    pm.forward(torch.from_numpy(imgs).cuda(), torch.from_numpy(noise).cuda(), feats, ws)
+    got = feats.cpu().numpy().astype(np.float64)
+    scale = max(1.0, np.abs(ref).max())
+    assert np.abs(got - ref).max() <= 2e-5 * scale
+
+
+def test_full_size_cifar_within_tolerance_of_fp64():
+    """The CIFAR-shaped network at full size (8192 images, 768 input
+    ciphertexts, 4096 + 2048 features, N = 16384, 11 + 2 primes): client calls
+    of the library, GPU plaintext branch and GPU evaluation; the decrypted
+    logits against the fp64 network fed the same features."""
+    cfg = workloads.get_config("cifar_cnn")
+    B = cfg["batch"]
+    ctx = bcn.Context.from_config(cfg)
+    w_q = [bcn.quantize(w) for w in workloads.cipher_weights(cfg)]
+    w_int, s_w = [a for a, _ in w_q], [s for _, s in w_q]
+    model = bcn.Model(ctx, cfg["cipher"], w_int, s_w)
+    imgs, noise, pw = workloads.images(cfg), workloads.laplace_noise(cfg), workloads.plain_weights(cfg)
+    pm = bcn.PlainModel(ctx, cfg["plain"], pw, cfg["image"], cfg["segment"])
+    feats = torch.empty((pm.n_feat, B), dtype=torch.float32, device="cuda")
+    ws_p = torch.empty(pm.workspace_bytes(B) // 4 + 1, dtype=torch.int32, device="cuda")
+    pm.forward(torch.from_numpy(imgs).cuda(), torch.from_numpy(noise).cuda(), feats, ws_p)
+    f = feats.cpu().numpy().astype(np.float64)
+    f_split = [f[:4096], f[4096:]]
+    scale0 = 2.0 ** cfg["log_scale"]
+    adds, out_scale = model.scales(scale0)
+    sk, evk = ctx.keygen(workloads.SEED_KEYS)
+    cts = ctx.encrypt_segment(sk, imgs, cfg["segment"], scale0, workloads.SEED_ENC)
+    pts = [ctx.encode(fv, lv, sc) for fv, lv, sc in zip(f_split, [model.levels[i] for i in model.add_layers], adds)]
+    evk_eval = ctx.evk_prepare(dev(evk))
+    out = torch.empty(model.out_shape(), dtype=torch.int32, device="cuda")
+    ws = model.alloc_workspace()
+    model.eval(evk_eval, dev(cts), [dev(p) for p in pts], out, ws)
+    dec = ctx.decrypt_decode(sk, host(out), model.out_level, out_scale, B)
+    tables = [O.layer_table(l, w) for l, w in zip(cfg["cipher"], w_int)]
+    fp = O.fp64_network(cfg, O.segment_values(cfg, imgs), f_split, tables, s_w)
+    assert np.abs(dec - fp).max() < TOL
+    ok, ties = argmax_ok(dec, fp)
+    assert ok
