@@ -323,10 +323,10 @@ def run_ours(args, cfg, rank, world, local_rank):
     kernels = {k: {"launches": n, "ms_total": ms, "ms_per_step": ms / K, "share": ms / max(1e-9, sum(
         v[0] for v in prof.values())), "algorithmic_GBps": (b / (ms / 1e3) / 1e9) if ms else None}
                for k, (ms, n, b) in prof.items()}
-    ks_ms = sum(prof[k][0] for k in ("modup", "ks_inner", "moddown_rescale"))
-    ks_b = sum(prof[k][2] for k in ("modup", "ks_inner", "moddown_rescale"))
-    ntt_ms = prof["ntt_fwd"][0] + prof["ntt_inv"][0]
-    ntt_b = prof["ntt_fwd"][2] + prof["ntt_inv"][2]
+    ks_ms = sum(prof[k][0] for k in ("keyswitch", "moddown_rescale"))
+    ks_b = sum(prof[k][2] for k in ("keyswitch", "moddown_rescale"))
+    ntt_ms = prof["square"][0]
+    ntt_b = prof["square"][2]
 
     if rank != 0:
         if dist:

@@ -204,6 +204,10 @@ typedef struct {
 
 bcn_status bcn_model_create(bcn_ctx *ctx, const bcn_layer *layers, int n_layers, bcn_model **out);
 bcn_status bcn_model_destroy(bcn_model *m);
+/* Ciphertexts per key-switching chunk of the square layers (0: automatic, a
+ * chunk's intermediates bounded by 1 GiB).  Changes bcn_eval_workspace_bytes;
+ * results do not depend on it. */
+bcn_status bcn_model_set_chunk(bcn_model *m, int chunk);
 bcn_status bcn_model_get_info(const bcn_model *m, bcn_model_info *out);
 /* per layer: live level at its input and its output count (arrays of n_layers) */
 bcn_status bcn_model_layers(const bcn_model *m, int *level_out, int *n_out_out);
@@ -244,13 +248,10 @@ bcn_status bcn_eval_host(const bcn_model *m, const uint32_t *evk_eval_dev, const
 /* Classes of the kernels bcn_eval launches. */
 typedef enum {
     BCN_KERNEL_MAC = 0,             /* integer-weight multiply-accumulate + feature add */
-    BCN_KERNEL_NTT_FWD = 1,         /* forward negacyclic NTT */
-    BCN_KERNEL_NTT_INV = 2,         /* inverse negacyclic NTT */
-    BCN_KERNEL_TENSOR_SQUARE = 3,   /* (c0, c1) -> (c0^2, 2 c0 c1, c1^2) */
-    BCN_KERNEL_MODUP = 4,           /* digit decomposition + fast basis conversion */
-    BCN_KERNEL_KS_INNER = 5,        /* inner product with the evaluation key */
-    BCN_KERNEL_MODDOWN_RESCALE = 6, /* ModDown by P, add, rescale */
-    BCN_KERNEL_COUNT = 7
+    BCN_KERNEL_SQUARE = 1,          /* NTT of (c0, c1), tensor square, inverse NTT of the three products */
+    BCN_KERNEL_KEYSWITCH = 2,       /* ModUp + NTT + inner product with the evaluation key + inverse NTT */
+    BCN_KERNEL_MODDOWN_RESCALE = 3, /* ModDown by P, add, rescale */
+    BCN_KERNEL_COUNT = 4
 } bcn_kernel_class;
 
 /* With timing enabled, bcn_eval records a CUDA event pair around every kernel

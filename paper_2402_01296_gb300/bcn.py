@@ -73,6 +73,7 @@ _SIGS = {
     "bcn_plain_branch_forward": (_I, [_P, _P, _P, _I, _P, _P, _SZ, _P]),
     "bcn_model_create": (_I, [_P, _P, _I, ctypes.POINTER(_P)]),
     "bcn_model_destroy": (_I, [_P]),
+    "bcn_model_set_chunk": (_I, [_P, _I]),
     "bcn_model_get_info": (_I, [_P, ctypes.POINTER(_ModelInfo)]),
     "bcn_model_layers": (_I, [_P, _P, _P]),
     "bcn_model_scales": (_I, [_P, _D, _P, ctypes.POINTER(_D)]),
@@ -382,7 +383,10 @@ class Model:
         nb = self.host_workspace_bytes() if host else self.workspace_bytes()
         return torch.empty(max(1, (nb + 3) // 4), dtype=torch.int32, device=f"cuda:{self.ctx.device}")
 
-    KERNELS = ["mac", "ntt_fwd", "ntt_inv", "tensor_square", "modup", "ks_inner", "moddown_rescale"]
+    KERNELS = ["mac", "square", "keyswitch", "moddown_rescale"]
+
+    def set_chunk(self, chunk: int):
+        _check(lib().bcn_model_set_chunk(self._h, int(chunk)), "bcn_model_set_chunk")
 
     def profile_enable(self, on: bool = True):
         _check(lib().bcn_profile_enable(self._h, int(on)), "bcn_profile_enable")

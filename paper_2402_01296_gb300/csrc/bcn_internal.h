@@ -43,10 +43,10 @@ struct PrimeConst {
     uint64_t mac_offset; // a multiple of q >= 2^58 (makes a signed MAC sum non-negative)
 };
 
-// which prime each limb of a batched buffer uses: limb l -> pidx[l % period]
+// which prime each limb of a batched buffer uses: t = limb % period, then
+// prime index t if t < split, else t + offset
 struct PrimeMap {
-    int period;
-    uint8_t pidx[2 * kMaxPrimes];
+    int period, split, offset;
 };
 
 // basis-conversion constants, device resident (one blob) ----------------------
@@ -94,11 +94,16 @@ struct bcn_ctx {
     std::vector<bcn::PrimeConst> h_pc;
 };
 
+// A linear layer as output groups: the outputs of a group read the same taps
+// (one conv position with all its output channels; a whole dense layer).
 struct bcn_layer_plan {
     int type, n_in, n_out, K, level, add, square;
     double s_w;
-    int32_t *d_idx = nullptr;  // [n_out][K]
-    int8_t *d_w = nullptr;     // [n_out][K]
+    int n_groups, n_go;        // groups, outputs per group
+    int n_distinct_in;         // inputs the layer reads
+    int32_t *d_gidx = nullptr; // [n_groups][K] input index per tap (-1: zero padding)
+    int8_t *d_gw = nullptr;    // [n_groups][n_go][K]
+    int32_t *d_gout = nullptr; // [n_groups][n_go] output index
 };
 
 namespace bcn {
@@ -122,10 +127,11 @@ struct Profiler {
 struct bcn_model {
     bcn_ctx *ctx;
     std::vector<bcn_layer_plan> layers;
-    std::vector<std::vector<int>> distinct_inputs;  // [layer][chunk]: inputs a MAC chunk reads
     mutable bcn::Profiler prof;
     int chunk;          // ciphertexts per key-switching chunk
+    int chunk_request;  // 0: automatic
     size_t ws_x_bytes;  // one ping-pong activation buffer
+    size_t ws_y_bytes;  // MAC output of a square layer
     size_t ws_chunk_bytes;
     int out_level;
 };

@@ -1,0 +1,218 @@
+// Kernels built on the register-resident NTT core: the batched NTT, the
+// tensor-square core and the fused key-switching core.
+#pragma once
+
+#include "device_api.h"
+#include "ntt_core.cuh"
+
+namespace bcn {
+
+template <int LOGN, int R>
+__global__ void __launch_bounds__((1 << LOGN) / R) k_ntt_fwd(uint32_t *__restrict__ data, PrimeMap pm,
+                                                            const PrimeConst *__restrict__ pc,
+                                                            const uint2 *__restrict__ tw) {
+    using C = NttCore<LOGN, R>;
+    extern __shared__ __align__(16) uint32_t sm[];
+    const int limb = blockIdx.x, tid = threadIdx.x;
+    const int p = prime_of(pm, limb);
+    const uint32_t q = pc[p].q;
+    uint32_t *a = data + (size_t)limb * C::N;
+    uint32_t x[R];
+    C::load_natural(x, a, tid);
+    C::forward(x, sm, tid, q, tw + (size_t)p * C::N);
+    C::store_ntt(x, a, tid);
+}
+
+template <int LOGN, int R>
+__global__ void __launch_bounds__((1 << LOGN) / R) k_ntt_inv(uint32_t *__restrict__ data, PrimeMap pm,
+                                                            const PrimeConst *__restrict__ pc,
+                                                            const uint2 *__restrict__ tw) {
+    using C = NttCore<LOGN, R>;
+    extern __shared__ __align__(16) uint32_t sm[];
+    const int limb = blockIdx.x, tid = threadIdx.x;
+    const int p = prime_of(pm, limb);
+    const PrimeConst P = pc[p];
+    uint32_t *a = data + (size_t)limb * C::N;
+    uint32_t x[R];
+    C::load_ntt(x, a, tid);
+    C::inverse(x, sm, tid, P.q, tw + (size_t)p * C::N, P.ninv, P.ninv_shoup);
+    C::store_natural(x, a, tid);
+}
+
+// Square activation, first half: forward NTT of c0 and c1 of one limb,
+// tensor square (c0^2, 2 c0 c1, c1^2) in the NTT domain, inverse NTT of the
+// three products.  Y [C][2][n][N] -> D [C][3][n][N], coefficient form.
+// grid (n, C): one block per (limb, ciphertext).
+template <int LOGN, int R>
+__global__ void __launch_bounds__((1 << LOGN) / R) k_square_core(const uint32_t *__restrict__ Y,
+                                                                uint32_t *__restrict__ D, int n,
+                                                                const PrimeConst *__restrict__ pc,
+                                                                const uint2 *__restrict__ twf,
+                                                                const uint2 *__restrict__ twi) {
+    using C = NttCore<LOGN, R>;
+    constexpr int N = C::N, T = C::T;
+    extern __shared__ __align__(16) uint32_t sm[];
+    // exchange buffer, then two thread-private parking areas (slot u*T + tid)
+    uint32_t *s1 = sm + C::SMEM_WORDS, *s2 = s1 + N;
+    const int i = blockIdx.x, ct = blockIdx.y, tid = threadIdx.x;
+    const PrimeConst P = pc[i];
+    const uint2 *tf = twf + (size_t)i * N, *ti = twi + (size_t)i * N;
+    uint32_t a[R], b[R];
+    C::load_natural(a, Y + (((size_t)ct * 2 + 0) * n + i) * N, tid);
+    C::forward(a, sm, tid, P.q, tf);
+    C::load_natural(b, Y + (((size_t)ct * 2 + 1) * n + i) * N, tid);
+    C::forward(b, sm, tid, P.q, tf);
+#pragma unroll
+    for (int u = 0; u < R; u++) {
+        const uint32_t aR = shoup_mul(a[u], P.r_mod, P.r_shoup, P.q);
+        const uint32_t bR = shoup_mul(b[u], P.r_mod, P.r_shoup, P.q);
+        const uint32_t x = mont_mul(aR, b[u], P.q, P.qneg_inv);
+        s2[u * T + tid] = mont_mul(bR, b[u], P.q, P.qneg_inv);  // c1^2
+        s1[u * T + tid] = add_mod(x, x, P.q);                     // 2 c0 c1
+        a[u] = mont_mul(aR, a[u], P.q, P.qneg_inv);               // c0^2
+    }
+    C::inverse(a, sm, tid, P.q, ti, P.ninv, P.ninv_shoup);
+    C::store_natural(a, D + (((size_t)ct * 3 + 0) * n + i) * N, tid);
+#pragma unroll
+    for (int u = 0; u < R; u++) a[u] = s1[u * T + tid];
+    C::inverse(a, sm, tid, P.q, ti, P.ninv, P.ninv_shoup);
+    C::store_natural(a, D + (((size_t)ct * 3 + 1) * n + i) * N, tid);
+#pragma unroll
+    for (int u = 0; u < R; u++) a[u] = s2[u * T + tid];
+    C::inverse(a, sm, tid, P.q, ti, P.ninv, P.ninv_shoup);
+    C::store_natural(a, D + (((size_t)ct * 3 + 2) * n + i) * N, tid);
+}
+
+// Key switching of d2, fused per (target prime t, ciphertext): for every
+// digit j, ModUp of d2 into prime t (the residue itself on the digit's own
+// primes, else the centred fast basis conversion
+//     sum_u r_u * Dhat_u - #{u : r_u > (q_u-1)/2} * D_j,  r_u = [x_u Dhat_u^{-1}]_{q_u}),
+// forward NTT, and the product with evk_j accumulated for both key halves;
+// then the inverse NTT of the two sums.  No extended-basis limb is stored.
+// D [C][3][n][N] (d2 in coefficient form) -> ACC [C][2][n+K][N] (coefficient form).
+// grid (n+K, C).
+template <int LOGN, int R>
+__global__ void __launch_bounds__((1 << LOGN) / R) k_ks_core(const uint32_t *__restrict__ D,
+                                                            const uint32_t *__restrict__ evk,
+                                                            uint32_t *__restrict__ acc_out, int n, KsDev ks,
+                                                            const PrimeConst *__restrict__ pc,
+                                                            const uint2 *__restrict__ twf,
+                                                            const uint2 *__restrict__ twi) {
+    using C = NttCore<LOGN, R>;
+    constexpr int N = C::N, T = C::T;
+    extern __shared__ __align__(16) uint32_t sm[];
+    // exchange buffer, then the two running sums in thread-private slots u*T + tid
+    uint32_t *s0 = sm + C::SMEM_WORDS, *s1 = s0 + N;
+    const int t = blockIdx.x, ct = blockIdx.y, tid = threadIdx.x;
+    const int A = ks.alpha, dnum = (n + A - 1) / A, nb = n + ks.K;
+    const int pt = t < n ? t : ks.L + (t - n);
+    const PrimeConst P = pc[pt];
+    const uint2 *tf = twf + (size_t)pt * N, *ti = twi + (size_t)pt * N;
+    const uint32_t *x2 = D + ((size_t)ct * 3 + 2) * n * N;
+    uint32_t x[R];
+#pragma unroll
+    for (int u = 0; u < R; u++) s0[u * T + tid] = s1[u * T + tid] = 0;
+    for (int j = 0; j < dnum; j++) {
+        const int lo = j * A, hi = min(lo + A, n);
+        if (t >= lo && t < hi) {
+            C::load_natural(x, x2 + (size_t)t * N, tid);
+        } else {
+#pragma unroll
+            for (int u = 0; u < R; u++) x[u] = 0;
+            const uint32_t dp = ks.dprod[(size_t)(n * ks.dnum_max + j) * ks.P + pt];
+            for (int v = 0; v < hi - lo; v++) {
+                const int i = lo + v;
+                const uint32_t qi = pc[i].q, half = pc[i].half;
+                const uint2 di = ks.dhat_inv[(size_t)(n * ks.dnum_max + j) * A + v];
+                const uint2 dh = ks.dhat[((size_t)(n * ks.dnum_max + j) * A + v) * ks.P + pt];
+                const uint32_t *xi = x2 + (size_t)i * N;
+#pragma unroll
+                for (int u = 0; u < R; u++) {
+                    const uint32_t r = shoup_mul(__ldg(xi + tid + u * T), di.x, di.y, qi);
+                    uint32_t y = add_mod(x[u], shoup_mul(r, dh.x, dh.y, P.q), P.q);
+                    if (r > half) y = sub_mod(y, dp, P.q);
+                    x[u] = y;
+                }
+            }
+        }
+        C::forward(x, sm, tid, P.q, tf);
+        const uint32_t *k0 = evk + ((size_t)(j * 2 + 0) * ks.P + pt) * N;
+        const uint32_t *k1 = evk + ((size_t)(j * 2 + 1) * ks.P + pt) * N;
+        if constexpr (C::NTT_QUADS) {
+#pragma unroll
+            for (int u = 0; u < R; u += 4) {
+                const int e = C::ntt_elem(u, tid);
+                const uint4 v0 = __ldg(reinterpret_cast<const uint4 *>(k0 + e));
+                const uint4 v1 = __ldg(reinterpret_cast<const uint4 *>(k1 + e));
+                const uint32_t w0[4] = {v0.x, v0.y, v0.z, v0.w}, w1[4] = {v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+                for (int z = 0; z < 4; z++) {
+                    uint32_t &r0 = s0[(u + z) * T + tid], &r1 = s1[(u + z) * T + tid];
+                    r0 = add_mod(r0, mont_mul(x[u + z], w0[z], P.q, P.qneg_inv), P.q);
+                    r1 = add_mod(r1, mont_mul(x[u + z], w1[z], P.q, P.qneg_inv), P.q);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < R; u++) {
+                const int e = C::ntt_elem(u, tid);
+                uint32_t &r0 = s0[u * T + tid], &r1 = s1[u * T + tid];
+                r0 = add_mod(r0, mont_mul(x[u], __ldg(k0 + e), P.q, P.qneg_inv), P.q);
+                r1 = add_mod(r1, mont_mul(x[u], __ldg(k1 + e), P.q, P.qneg_inv), P.q);
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < R; u++) x[u] = s0[u * T + tid];
+    C::inverse(x, sm, tid, P.q, ti, P.ninv, P.ninv_shoup);
+    C::store_natural(x, acc_out + (((size_t)ct * 2 + 0) * nb + t) * N, tid);
+#pragma unroll
+    for (int u = 0; u < R; u++) x[u] = s1[u * T + tid];
+    C::inverse(x, sm, tid, P.q, ti, P.ninv, P.ninv_shoup);
+    C::store_natural(x, acc_out + (((size_t)ct * 2 + 1) * nb + t) * N, tid);
+}
+
+template <int LOGN, int R>
+struct CoreImpl {
+    using Core = NttCore<LOGN, R>;
+    static constexpr size_t SMEM = (size_t)Core::SMEM_WORDS * 4;            // NTT alone
+    static constexpr size_t SMEM3 = ((size_t)Core::SMEM_WORDS + 2 * Core::N) * 4;  // + two parking areas
+
+    static bcn_status ntt(const bcn_ctx *c, uint32_t *data, size_t n_limbs, PrimeMap pm, bool inverse,
+                          cudaStream_t st) {
+        if (inverse)
+            k_ntt_inv<LOGN, R><<<(unsigned)n_limbs, Core::T, SMEM, st>>>(data, pm, c->d_pc, c->d_tw_inv);
+        else
+            k_ntt_fwd<LOGN, R><<<(unsigned)n_limbs, Core::T, SMEM, st>>>(data, pm, c->d_pc, c->d_tw_fwd);
+        return check_launch("NTT");
+    }
+    static bcn_status square(const bcn_ctx *c, int n, const uint32_t *Y, uint32_t *D, int C, cudaStream_t st) {
+        k_square_core<LOGN, R><<<dim3(n, C), Core::T, SMEM3, st>>>(Y, D, n, c->d_pc, c->d_tw_fwd, c->d_tw_inv);
+        return check_launch("k_square_core");
+    }
+    static bcn_status keyswitch(const bcn_ctx *c, int n, const uint32_t *D, const uint32_t *evk, uint32_t *acc,
+                                int C, cudaStream_t st) {
+        k_ks_core<LOGN, R><<<dim3(n + c->K, C), Core::T, SMEM3, st>>>(D, evk, acc, n, ks_dev(c), c->d_pc,
+                                                                     c->d_tw_fwd, c->d_tw_inv);
+        return check_launch("k_ks_core");
+    }
+    static bcn_status setup() {
+        const int smem = (int)SMEM, smem3 = (int)SMEM3;
+        if (cudaFuncSetAttribute(k_ntt_fwd<LOGN, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+                cudaSuccess ||
+            cudaFuncSetAttribute(k_ntt_inv<LOGN, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+                cudaSuccess ||
+            cudaFuncSetAttribute(k_square_core<LOGN, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem3) !=
+                cudaSuccess ||
+            cudaFuncSetAttribute(k_ks_core<LOGN, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem3) !=
+                cudaSuccess)
+            return fail(BCN_E_CUDA, "cudaFuncSetAttribute failed for the NTT-based kernels");
+        return BCN_OK;
+    }
+    static const CoreFns *fns() {
+        static const CoreFns f = {&ntt, &square, &keyswitch, &setup};
+        return &f;
+    }
+};
+
+}  // namespace bcn

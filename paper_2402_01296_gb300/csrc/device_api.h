@@ -7,26 +7,14 @@
 
 namespace bcn {
 
-bcn_status ntt_setup_kernels();
-// In-place NTT of n_limbs consecutive limbs of N words; limb l uses prime
-// pm.pidx[l % pm.period].
-bcn_status launch_ntt(const bcn_ctx *c, uint32_t *data, size_t n_limbs, const PrimeMap &pm, bool inverse,
-                      cudaStream_t st);
-
 // prime map of a buffer whose limbs cycle through the data primes q_0..q_{level-1}
-inline PrimeMap data_map(int level) {
-    PrimeMap m{};
-    m.period = level;
-    for (int i = 0; i < level; i++) m.pidx[i] = (uint8_t)i;
-    return m;
-}
+inline PrimeMap data_map(int level) { return PrimeMap{level, level, 0}; }
 // prime map of the extended basis Q_level u P: q_0..q_{level-1}, p_0..p_{K-1}
-inline PrimeMap ext_map(const bcn_ctx *c, int level) {
-    PrimeMap m{};
-    m.period = level + c->K;
-    for (int i = 0; i < level; i++) m.pidx[i] = (uint8_t)i;
-    for (int k = 0; k < c->K; k++) m.pidx[level + k] = (uint8_t)(c->L + k);
-    return m;
+inline PrimeMap ext_map(const bcn_ctx *c, int level) { return PrimeMap{level + c->K, level, c->L - level}; }
+
+__host__ __device__ inline int prime_of(const PrimeMap &m, int limb) {
+    const int t = limb % m.period;
+    return t < m.split ? t : t + m.offset;
 }
 
 inline bcn_status check_launch(const char *what) {
@@ -34,5 +22,49 @@ inline bcn_status check_launch(const char *what) {
     if (e != cudaSuccess) return fail(BCN_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
     return BCN_OK;
 }
+
+// basis-conversion tables as the kernels see them (layout: KsTables)
+struct KsDev {
+    const uint2 *dhat_inv, *dhat, *phat_inv, *phat, *pinv, *qtop_inv;
+    const uint32_t *dprod, *pmod;
+    int L, K, alpha, dnum_max, P;
+};
+
+inline KsDev ks_dev(const bcn_ctx *c) {
+    const KsTables &t = c->ks;
+    KsDev k;
+    k.dhat_inv = reinterpret_cast<const uint2 *>(c->d_ks + t.off_dhat_inv);
+    k.dhat = reinterpret_cast<const uint2 *>(c->d_ks + t.off_dhat);
+    k.dprod = c->d_ks + t.off_dprod;
+    k.phat_inv = reinterpret_cast<const uint2 *>(c->d_ks + t.off_phat_inv);
+    k.phat = reinterpret_cast<const uint2 *>(c->d_ks + t.off_phat);
+    k.pmod = c->d_ks + t.off_pmod;
+    k.pinv = reinterpret_cast<const uint2 *>(c->d_ks + t.off_pinv);
+    k.qtop_inv = reinterpret_cast<const uint2 *>(c->d_ks + t.off_qtop_inv);
+    k.L = t.L; k.K = t.K; k.alpha = t.alpha; k.dnum_max = t.dnum_max; k.P = t.P;
+    return k;
+}
+
+// The NTT-based kernels of one ring degree (template instances live in
+// cores_*.cu so they compile in parallel).
+struct CoreFns {
+    // in-place NTT of n_limbs limbs; limb l uses prime prime_of(pm, l)
+    bcn_status (*ntt)(const bcn_ctx *, uint32_t *data, size_t n_limbs, PrimeMap pm, bool inverse, cudaStream_t);
+    // Y [C][2][n][N] -> D [C][3][n][N] (tensor square, coefficient form)
+    bcn_status (*square)(const bcn_ctx *, int n, const uint32_t *Y, uint32_t *D, int C, cudaStream_t);
+    // D (d2) -> ACC [C][2][n+K][N] (key-switching sums, coefficient form)
+    bcn_status (*keyswitch)(const bcn_ctx *, int n, const uint32_t *D, const uint32_t *evk, uint32_t *acc, int C,
+                            cudaStream_t);
+    bcn_status (*setup)();
+};
+const CoreFns *core_fns(int logN);  // nullptr if unsupported
+const CoreFns *core_fns_small(int logN);
+const CoreFns *core_fns_12();
+const CoreFns *core_fns_13();
+const CoreFns *core_fns_14();
+
+bcn_status launch_ntt(const bcn_ctx *c, uint32_t *data, size_t n_limbs, const PrimeMap &pm, bool inverse,
+                      cudaStream_t st);
+bcn_status cores_setup_all();
 
 }  // namespace bcn

@@ -17,166 +17,73 @@
 
 namespace bcn {
 
-struct KsDev {
-    const uint2 *dhat_inv, *dhat, *phat_inv, *phat, *pinv, *qtop_inv;
-    const uint32_t *dprod, *pmod;
-    int L, K, alpha, dnum_max, P;
-};
-
-static KsDev ks_dev(const bcn_ctx *c) {
-    const KsTables &t = c->ks;
-    KsDev k;
-    k.dhat_inv = reinterpret_cast<const uint2 *>(c->d_ks + t.off_dhat_inv);
-    k.dhat = reinterpret_cast<const uint2 *>(c->d_ks + t.off_dhat);
-    k.dprod = c->d_ks + t.off_dprod;
-    k.phat_inv = reinterpret_cast<const uint2 *>(c->d_ks + t.off_phat_inv);
-    k.phat = reinterpret_cast<const uint2 *>(c->d_ks + t.off_phat);
-    k.pmod = c->d_ks + t.off_pmod;
-    k.pinv = reinterpret_cast<const uint2 *>(c->d_ks + t.off_pinv);
-    k.qtop_inv = reinterpret_cast<const uint2 *>(c->d_ks + t.off_qtop_inv);
-    k.L = t.L; k.K = t.K; k.alpha = t.alpha; k.dnum_max = t.dnum_max; k.P = t.P;
-    return k;
-}
-
 // ------------------------------------------------------------------- kernels
-// MAC + feature add.  grid (N/4/256, 2*level, n_out), 256 threads, 4 coefficients each.
-__global__ void __launch_bounds__(256) k_mac(const uint32_t *__restrict__ in, uint32_t *__restrict__ out,
-                                             const int32_t *__restrict__ idx, const int8_t *__restrict__ w,
-                                             const uint32_t *__restrict__ pt, int K, int level, int N, int o_base,
-                                             const PrimeConst *__restrict__ pc) {
-    const int k4 = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k4 * 4 >= N) return;
-    const int o = o_base + blockIdx.z;
-    const int poly = blockIdx.y / level, i = blockIdx.y % level;
-    const int32_t *id = idx + (size_t)o * K;
-    const int8_t *ww = w + (size_t)o * K;
-    long long a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-    for (int t = 0; t < K; t++) {
-        const int src = __ldg(id + t);
-        if (src < 0) continue;
-        const long long wt = (long long)__ldg(ww + t);
-        const uint4 x = __ldg(reinterpret_cast<const uint4 *>(in + (((size_t)src * 2 + poly) * level + i) * N) + k4);
-        a0 += wt * x.x;
-        a1 += wt * x.y;
-        a2 += wt * x.z;
-        a3 += wt * x.w;
+// Integer-weight MAC + feature add over output groups.  A group is a set of
+// outputs that read the same taps (a conv position with all its output
+// channels; a whole dense layer); each thread keeps OT outputs x 4 columns of
+// signed 64-bit sums, so every input word it loads serves OT outputs.
+//   out[gout[g][o]][col] = sum_t gw[g][o][t] * in[gidx[g][t]][col]  (+ pt, poly 0)
+// Columns run over the (poly, limb, coefficient) words of a ciphertext.
+// grid (ceil(2*level*N/4/256), n_groups * ceil(n_go/OT)), 256 threads.
+template <int OT>
+__global__ void __launch_bounds__(256) k_mac_grouped(const uint32_t *__restrict__ in, uint32_t *__restrict__ out,
+                                                     const int32_t *__restrict__ gidx, const int8_t *__restrict__ gw,
+                                                     const int32_t *__restrict__ gout, const uint32_t *__restrict__ pt,
+                                                     int K, int n_go, int level, int N,
+                                                     const PrimeConst *__restrict__ pc) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    int32_t *sidx = reinterpret_cast<int32_t *>(smraw);
+    int8_t *sw = reinterpret_cast<int8_t *>(smraw + (size_t)K * 4);
+    const int tiles = (n_go + OT - 1) / OT;
+    const int g = blockIdx.y / tiles, o0 = (blockIdx.y % tiles) * OT;
+    const int no = min(OT, n_go - o0);
+    for (int t = threadIdx.x; t < K; t += blockDim.x) sidx[t] = gidx[(size_t)g * K + t];
+    for (int x = threadIdx.x; x < OT * K; x += blockDim.x) {
+        const int o = x / K, t = x % K;
+        sw[x] = o < no ? gw[((size_t)g * n_go + o0 + o) * K + t] : (int8_t)0;
     }
+    __syncthreads();
+    const size_t cols = (size_t)2 * level * N;
+    const size_t col = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    if (col >= cols) return;
+    long long acc[OT][4];
+#pragma unroll
+    for (int o = 0; o < OT; o++) acc[o][0] = acc[o][1] = acc[o][2] = acc[o][3] = 0;
+    for (int t = 0; t < K; t++) {
+        const int src = sidx[t];
+        if (src < 0) continue;
+        const uint4 x = __ldg(reinterpret_cast<const uint4 *>(in + (size_t)src * cols + col));
+#pragma unroll
+        for (int o = 0; o < OT; o++) {
+            const long long w = sw[o * K + t];
+            acc[o][0] += w * x.x;
+            acc[o][1] += w * x.y;
+            acc[o][2] += w * x.z;
+            acc[o][3] += w * x.w;
+        }
+    }
+    const int poly = (int)(col / ((size_t)level * N)), i = (int)((col / N) % level);
     const uint32_t q = pc[i].q;
     const uint64_t mu = pc[i].barrett;
     const long long off = (long long)pc[i].mac_offset;
-    uint4 r;
-    r.x = barrett_reduce64((uint64_t)(a0 + off), q, mu);
-    r.y = barrett_reduce64((uint64_t)(a1 + off), q, mu);
-    r.z = barrett_reduce64((uint64_t)(a2 + off), q, mu);
-    r.w = barrett_reduce64((uint64_t)(a3 + off), q, mu);
-    if (pt != nullptr && poly == 0) {
-        const uint4 p = __ldg(reinterpret_cast<const uint4 *>(pt + ((size_t)o * level + i) * N) + k4);
-        r.x = add_mod(r.x, p.x, q);
-        r.y = add_mod(r.y, p.y, q);
-        r.z = add_mod(r.z, p.z, q);
-        r.w = add_mod(r.w, p.w, q);
-    }
-    reinterpret_cast<uint4 *>(out + (((size_t)blockIdx.z * 2 + poly) * level + i) * N)[k4] = r;
-}
-
-// Tensor square in the NTT domain: Y [C][2][n][N] -> D [C][3][n][N].
-// grid (N/4/256, n, C)
-__global__ void __launch_bounds__(256) k_tensor_square(const uint32_t *__restrict__ Y, uint32_t *__restrict__ D,
-                                                       int n, int N, const PrimeConst *__restrict__ pc) {
-    const int k4 = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k4 * 4 >= N) return;
-    const int i = blockIdx.y, ct = blockIdx.z;
-    const PrimeConst P = pc[i];
-    const uint4 c0 = reinterpret_cast<const uint4 *>(Y + (((size_t)ct * 2 + 0) * n + i) * N)[k4];
-    const uint4 c1 = reinterpret_cast<const uint4 *>(Y + (((size_t)ct * 2 + 1) * n + i) * N)[k4];
-    uint4 d0, d1, d2;
-#define BCN_SQ(f)                                                             \
-    {                                                                         \
-        uint32_t a = shoup_mul(c0.f, P.r_mod, P.r_shoup, P.q);                \
-        uint32_t b = shoup_mul(c1.f, P.r_mod, P.r_shoup, P.q);                \
-        d0.f = mont_mul(a, c0.f, P.q, P.qneg_inv);                            \
-        uint32_t x = mont_mul(a, c1.f, P.q, P.qneg_inv);                      \
-        d1.f = add_mod(x, x, P.q);                                            \
-        d2.f = mont_mul(b, c1.f, P.q, P.qneg_inv);                            \
-    }
-    BCN_SQ(x) BCN_SQ(y) BCN_SQ(z) BCN_SQ(w)
-#undef BCN_SQ
-    reinterpret_cast<uint4 *>(D + (((size_t)ct * 3 + 0) * n + i) * N)[k4] = d0;
-    reinterpret_cast<uint4 *>(D + (((size_t)ct * 3 + 1) * n + i) * N)[k4] = d1;
-    reinterpret_cast<uint4 *>(D + (((size_t)ct * 3 + 2) * n + i) * N)[k4] = d2;
-}
-
-// ModUp of d2 (coefficient form) for every digit j into the extended basis
-// Q_n u P:  EXT [C][dnum][n+K][N].  On the digit's own primes the residue is
-// copied; elsewhere the centred fast basis conversion
-//     sum_u r_u * Dhat_u - cnt * D_j  (mod t),  r_u = [x_u Dhat_u^{-1}]_{q_u},
-// cnt = #{u : r_u > (q_u - 1)/2}.   grid (N/256, C)
-__global__ void __launch_bounds__(256) k_modup(const uint32_t *__restrict__ D, uint32_t *__restrict__ ext, int n,
-                                               int N, KsDev ks, const PrimeConst *__restrict__ pc) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= N) return;
-    const int ct = blockIdx.y;
-    const int A = ks.alpha, dnum = (n + A - 1) / A, nb = n + ks.K;
-    const uint32_t *x = D + ((size_t)ct * 3 + 2) * n * N;
-    uint32_t *e = ext + (size_t)ct * dnum * nb * N;
-    for (int j = 0; j < dnum; j++) {
-        const int lo = j * A, hi = min(lo + A, n);
-        uint32_t r[4];
-        int cnt = 0;
-        for (int u = 0; u < hi - lo; u++) {
-            const int i = lo + u;
-            const uint2 di = ks.dhat_inv[(size_t)(n * ks.dnum_max + j) * A + u];
-            r[u] = shoup_mul(__ldg(x + (size_t)i * N + k), di.x, di.y, pc[i].q);
-            cnt += r[u] > pc[i].half;
+#pragma unroll
+    for (int o = 0; o < OT; o++) {
+        if (o >= no) break;
+        const int og = gout != nullptr ? gout[(size_t)g * n_go + o0 + o] : g * n_go + o0 + o;
+        uint4 r;
+        r.x = barrett_reduce64((uint64_t)(acc[o][0] + off), q, mu);
+        r.y = barrett_reduce64((uint64_t)(acc[o][1] + off), q, mu);
+        r.z = barrett_reduce64((uint64_t)(acc[o][2] + off), q, mu);
+        r.w = barrett_reduce64((uint64_t)(acc[o][3] + off), q, mu);
+        if (pt != nullptr && poly == 0) {
+            const uint4 p = __ldg(reinterpret_cast<const uint4 *>(pt + (size_t)og * level * N + col));
+            r.x = add_mod(r.x, p.x, q);
+            r.y = add_mod(r.y, p.y, q);
+            r.z = add_mod(r.z, p.z, q);
+            r.w = add_mod(r.w, p.w, q);
         }
-        for (int t = 0; t < nb; t++) {
-            const int pt = t < n ? t : ks.L + (t - n);
-            const uint32_t qt = pc[pt].q;
-            uint32_t v;
-            if (t >= lo && t < hi) {
-                v = __ldg(x + (size_t)t * N + k);
-            } else {
-                v = 0;
-                for (int u = 0; u < hi - lo; u++) {
-                    const uint2 dh = ks.dhat[((size_t)(n * ks.dnum_max + j) * A + u) * ks.P + pt];
-                    v = add_mod(v, shoup_mul(r[u], dh.x, dh.y, qt), qt);
-                }
-                const uint32_t dp = ks.dprod[(size_t)(n * ks.dnum_max + j) * ks.P + pt];
-                for (int c = 0; c < cnt; c++) v = sub_mod(v, dp, qt);
-            }
-            e[((size_t)j * nb + t) * N + k] = v;
-        }
+        *reinterpret_cast<uint4 *>(out + (size_t)og * cols + col) = r;
     }
-}
-
-// Key-switching inner product in the NTT domain: ACC[b] = sum_j EXT_j * evk_j[b]
-// (evk in Montgomery form, so one Montgomery product gives the plain product).
-// EXT [C][dnum][n+K][N] -> ACC [C][2][n+K][N].  grid (N/4/256, n+K, C)
-__global__ void __launch_bounds__(256) k_ks_inner(const uint32_t *__restrict__ ext, const uint32_t *__restrict__ evk,
-                                                  uint32_t *__restrict__ acc, int n, int N, int L, int K,
-                                                  const PrimeConst *__restrict__ pc, int alpha) {
-    const int k4 = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k4 * 4 >= N) return;
-    const int t = blockIdx.y, ct = blockIdx.z;
-    const int nb = n + K, dnum = (n + alpha - 1) / alpha, P = L + K;
-    const int pt = t < n ? t : L + (t - n);
-    const uint32_t q = pc[pt].q, qi = pc[pt].qneg_inv;
-    uint4 a0 = make_uint4(0, 0, 0, 0), a1 = make_uint4(0, 0, 0, 0);
-    for (int j = 0; j < dnum; j++) {
-        const uint4 e = reinterpret_cast<const uint4 *>(ext + (((size_t)ct * dnum + j) * nb + t) * N)[k4];
-        const uint4 k0 = __ldg(reinterpret_cast<const uint4 *>(evk + ((size_t)(j * 2 + 0) * P + pt) * N) + k4);
-        const uint4 k1 = __ldg(reinterpret_cast<const uint4 *>(evk + ((size_t)(j * 2 + 1) * P + pt) * N) + k4);
-        a0.x = add_mod(a0.x, mont_mul(e.x, k0.x, q, qi), q);
-        a0.y = add_mod(a0.y, mont_mul(e.y, k0.y, q, qi), q);
-        a0.z = add_mod(a0.z, mont_mul(e.z, k0.z, q, qi), q);
-        a0.w = add_mod(a0.w, mont_mul(e.w, k0.w, q, qi), q);
-        a1.x = add_mod(a1.x, mont_mul(e.x, k1.x, q, qi), q);
-        a1.y = add_mod(a1.y, mont_mul(e.y, k1.y, q, qi), q);
-        a1.z = add_mod(a1.z, mont_mul(e.z, k1.z, q, qi), q);
-        a1.w = add_mod(a1.w, mont_mul(e.w, k1.w, q, qi), q);
-    }
-    reinterpret_cast<uint4 *>(acc + (((size_t)ct * 2 + 0) * nb + t) * N)[k4] = a0;
-    reinterpret_cast<uint4 *>(acc + (((size_t)ct * 2 + 1) * nb + t) * N)[k4] = a1;
 }
 
 // ModDown by P, add to (d0, d1), then rescale by q_top -- the two roundings in
@@ -244,12 +151,12 @@ __global__ void __launch_bounds__(256) k_rescale(const uint32_t *__restrict__ in
     }
 }
 
-// x -> x * R mod q over rows of N words; row r uses prime pm.pidx[r % period]
+// x -> x * R mod q over rows of N words; row r uses prime prime_of(pm, r)
 __global__ void k_to_mont(uint32_t *__restrict__ data, int N, PrimeMap pm, const PrimeConst *__restrict__ pc) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= N) return;
     const int row = blockIdx.y;
-    const PrimeConst &P = pc[pm.pidx[row % pm.period]];
+    const PrimeConst &P = pc[prime_of(pm, row)];
     uint32_t *x = data + (size_t)row * N + k;
     *x = shoup_mul(*x, P.r_mod, P.r_shoup, P.q);
 }
@@ -304,103 +211,69 @@ struct Timed {
     }
 };
 
-// words of the chunk buffers per ciphertext at level n
-struct ChunkLayout {
-    size_t y, d, ext, acc;  // words per ciphertext
-};
-static ChunkLayout chunk_layout(const bcn_ctx *c, int n) {
-    const size_t N = c->N;
-    const int nb = n + c->K, dnum = (n + c->alpha - 1) / c->alpha;
-    return {2 * (size_t)n * N, 3 * (size_t)n * N, (size_t)dnum * nb * N, 2 * (size_t)nb * N};
-}
+constexpr int kMaxMacTaps = 8192;
+
+// key-switching chunk buffers per ciphertext at level n (words): D and ACC
+static size_t chunk_words(const bcn_ctx *c, int n) { return (3 * (size_t)n + 2 * (size_t)(n + c->K)) * c->N; }
 static size_t chunk_bytes(const bcn_ctx *c, int n, int chunk) {
-    ChunkLayout l = chunk_layout(c, n);
-    return align_up(l.y * 4 * chunk) + align_up(l.d * 4 * chunk) + align_up(l.ext * 4 * chunk) +
-           align_up(l.acc * 4 * chunk);
+    return align_up(3 * (size_t)n * c->N * 4 * chunk) + align_up(2 * (size_t)(n + c->K) * c->N * 4 * chunk);
 }
 static int default_chunk(const bcn_ctx *c, int n, int n_ct) {
-    const size_t target = 48ull << 20;  // keep the key-switching intermediates of a chunk L2-resident
-    ChunkLayout l = chunk_layout(c, n);
-    size_t per = (l.y + l.d + l.ext + l.acc) * 4;
-    int ch = (int)std::min<size_t>(4096, std::max<size_t>(1, target / per));
+    const size_t target = 1ull << 30;
+    int ch = (int)std::min<size_t>(32768, std::max<size_t>(1, target / (chunk_words(c, n) * 4)));
     return std::max(1, std::min(ch, std::max(1, n_ct)));
 }
 
 struct ChunkBufs {
-    uint32_t *y, *d, *ext, *acc;
+    uint32_t *d, *acc;
 };
 static ChunkBufs carve_chunk(const bcn_ctx *c, int n, int chunk, char *ws) {
-    ChunkLayout l = chunk_layout(c, n);
     ChunkBufs b;
-    b.y = reinterpret_cast<uint32_t *>(ws);
-    ws += align_up(l.y * 4 * chunk);
     b.d = reinterpret_cast<uint32_t *>(ws);
-    ws += align_up(l.d * 4 * chunk);
-    b.ext = reinterpret_cast<uint32_t *>(ws);
-    ws += align_up(l.ext * 4 * chunk);
-    b.acc = reinterpret_cast<uint32_t *>(ws);
+    b.acc = reinterpret_cast<uint32_t *>(ws + align_up(3 * (size_t)n * c->N * 4 * chunk));
     return b;
 }
 
-static bcn_status launch_mac(const bcn_ctx *c, int level, int K, const int32_t *idx, const int8_t *w,
-                             const uint32_t *in, const uint32_t *pt, uint32_t *out, int o_base, int n_o,
-                             cudaStream_t st, Profiler *prof = nullptr, int n_distinct_in = 0) {
-    if (n_o <= 0) return BCN_OK;
+static bcn_status launch_mac(const bcn_ctx *c, int level, int K, int n_groups, int n_go, const int32_t *gidx,
+                             const int8_t *gw, const int32_t *gout, const uint32_t *in, const uint32_t *pt,
+                             uint32_t *out, cudaStream_t st, Profiler *prof = nullptr, double alg_bytes = 0) {
+    if (n_groups <= 0 || n_go <= 0) return BCN_OK;
+    if (K > kMaxMacTaps) return fail(BCN_E_INVAL, "MAC fan-in above 8192");
     const int N = c->N;
-    const double limb = (double)N * 4;
-    Timed tm(prof, st, BCN_KERNEL_MAC,
-             limb * ((double)n_distinct_in * 2 * level + (double)n_o * 2 * level + (pt ? (double)n_o * level : 0)));
-    for (int z0 = 0; z0 < n_o; z0 += 65535) {  // grid.z limit
-        const int nz = std::min(65535, n_o - z0);
-        dim3 grid((unsigned)((N / 4 + 255) / 256), (unsigned)(2 * level), (unsigned)nz);
-        k_mac<<<grid, 256, 0, st>>>(in, out + (size_t)z0 * 2 * level * N, idx, w, pt, K, level, N, o_base + z0,
-                                    c->d_pc);
-        BCN_TRY(check_launch("k_mac"));
-    }
-    return BCN_OK;
+    const int OT = std::min(8, n_go);
+    const int tiles = (n_go + OT - 1) / OT;
+    const size_t cols = (size_t)2 * level * N;
+    const size_t smem = (size_t)K * 4 + (size_t)OT * K;
+    if ((long long)n_groups * tiles > 65535) return fail(BCN_E_INVAL, "MAC layer with more than 65535 output tiles");
+    Timed tm(prof, st, BCN_KERNEL_MAC, alg_bytes);
+    dim3 grid((unsigned)((cols / 4 + 255) / 256), (unsigned)(n_groups * tiles));
+#define BCN_MAC(OTV)                                                                                          \
+    case OTV:                                                                                                 \
+        k_mac_grouped<OTV><<<grid, 256, smem, st>>>(in, out, gidx, gw, gout, pt, K, n_go, level, N, c->d_pc); \
+        break;
+    switch (OT) { BCN_MAC(1) BCN_MAC(2) BCN_MAC(3) BCN_MAC(4) BCN_MAC(5) BCN_MAC(6) BCN_MAC(7) BCN_MAC(8) }
+#undef BCN_MAC
+    return check_launch("k_mac_grouped");
 }
 
-// steps 3-5 on a chunk: Y (MAC output, coefficient form, destroyed) -> out
-static bcn_status square_chunk(const bcn_ctx *c, int n, const uint32_t *evk, const ChunkBufs &b, int C,
-                               uint32_t *out, cudaStream_t st, Profiler *prof = nullptr) {
+// Square activation on a chunk of C ciphertexts: Y [C][2][n][N] (coefficient
+// form) -> out [C][2][n-1][N].
+static bcn_status square_chunk(const bcn_ctx *c, int n, const uint32_t *evk, const uint32_t *Y, const ChunkBufs &b,
+                               int C, uint32_t *out, cudaStream_t st, Profiler *prof = nullptr) {
     const int N = c->N, K = c->K, nb = n + K, dnum = (n + c->alpha - 1) / c->alpha;
-    const PrimeMap dm = data_map(n), em = ext_map(c, n);
-    const KsDev ks = ks_dev(c);
     const double limb = (double)N * 4;
+    const CoreFns *f = core_fns(c->logN);
+    if (!f) return fail(BCN_E_INVAL, "unsupported ring degree");
     {
-        Timed tm(prof, st, BCN_KERNEL_NTT_FWD, limb * 2 * C * 2 * n);
-        BCN_TRY(launch_ntt(c, b.y, (size_t)C * 2 * n, dm, false, st));
+        Timed tm(prof, st, BCN_KERNEL_SQUARE, limb * C * 5 * n);
+        BCN_TRY(f->square(c, n, Y, b.d, C, st));
     }
     {
-        Timed tm(prof, st, BCN_KERNEL_TENSOR_SQUARE, limb * C * 5 * n);
-        k_tensor_square<<<dim3((N / 4 + 255) / 256, n, C), 256, 0, st>>>(b.y, b.d, n, N, c->d_pc);
-        BCN_TRY(check_launch("k_tensor_square"));
-    }
-    {
-        Timed tm(prof, st, BCN_KERNEL_NTT_INV, limb * 2 * C * 3 * n);
-        BCN_TRY(launch_ntt(c, b.d, (size_t)C * 3 * n, dm, true, st));
-    }
-    {
-        Timed tm(prof, st, BCN_KERNEL_MODUP, limb * C * (n + (double)dnum * nb));
-        k_modup<<<dim3((N + 255) / 256, C), 256, 0, st>>>(b.d, b.ext, n, N, ks, c->d_pc);
-        BCN_TRY(check_launch("k_modup"));
-    }
-    {
-        Timed tm(prof, st, BCN_KERNEL_NTT_FWD, limb * 2 * C * dnum * nb);
-        BCN_TRY(launch_ntt(c, b.ext, (size_t)C * dnum * nb, em, false, st));
-    }
-    {
-        Timed tm(prof, st, BCN_KERNEL_KS_INNER, limb * ((double)C * (dnum * nb + 2 * nb) + 2.0 * dnum * nb));
-        k_ks_inner<<<dim3((N / 4 + 255) / 256, nb, C), 256, 0, st>>>(b.ext, evk, b.acc, n, N, c->L, K, c->d_pc,
-                                                                     c->alpha);
-        BCN_TRY(check_launch("k_ks_inner"));
-    }
-    {
-        Timed tm(prof, st, BCN_KERNEL_NTT_INV, limb * 2 * C * 2 * nb);
-        BCN_TRY(launch_ntt(c, b.acc, (size_t)C * 2 * nb, em, true, st));
+        Timed tm(prof, st, BCN_KERNEL_KEYSWITCH, limb * ((double)C * (n + 2 * nb) + 2.0 * dnum * nb));
+        BCN_TRY(f->keyswitch(c, n, b.d, evk, b.acc, C, st));
     }
     Timed tm(prof, st, BCN_KERNEL_MODDOWN_RESCALE, limb * C * (2.0 * n + 2.0 * nb + 2.0 * (n - 1)));
-    k_moddown_rescale<<<dim3((N + 255) / 256, 2, C), 256, 0, st>>>(b.d, b.acc, out, n, N, ks, c->d_pc);
+    k_moddown_rescale<<<dim3((N + 255) / 256, 2, C), 256, 0, st>>>(b.d, b.acc, out, n, N, ks_dev(c), c->d_pc);
     return check_launch("k_moddown_rescale");
 }
 
@@ -423,7 +296,15 @@ bcn_status device_ctx_init(bcn_ctx *c) {
     ok = ok && cudaMemcpy(c->d_ks, c->ks.host.data(), sizeof(uint32_t) * c->ks.host.size(),
                           cudaMemcpyHostToDevice) == cudaSuccess;
     if (!ok) return fail(BCN_E_CUDA, "upload of the context tables failed");
-    return ntt_setup_kernels();
+    BCN_TRY(cores_setup_all());
+    const int mac_smem = kMaxMacTaps * 4 + 8 * kMaxMacTaps;
+#define BCN_MSETUP(OTV)                                                                                           \
+    if (cudaFuncSetAttribute(k_mac_grouped<OTV>, cudaFuncAttributeMaxDynamicSharedMemorySize, mac_smem) !=      \
+        cudaSuccess)                                                                                            \
+        return fail(BCN_E_CUDA, "cudaFuncSetAttribute failed for the MAC kernel");
+    BCN_MSETUP(1) BCN_MSETUP(2) BCN_MSETUP(3) BCN_MSETUP(4) BCN_MSETUP(5) BCN_MSETUP(6) BCN_MSETUP(7) BCN_MSETUP(8)
+#undef BCN_MSETUP
+    return BCN_OK;
 }
 
 void device_ctx_free(bcn_ctx *c) {
@@ -444,6 +325,27 @@ using namespace bcn;
 extern "C" {
 
 // ------------------------------------------------------------------ model
+static void model_layout(bcn_model *m) {
+    const bcn_ctx *c = m->ctx;
+    size_t x_bytes = 0, y_bytes = 0;
+    int max_sq_level = 0, max_sq_out = 0;
+    for (size_t l = 0; l < m->layers.size(); l++) {
+        const bcn_layer_plan &p = m->layers[l];
+        const int lout = p.square ? p.level - 1 : p.level;
+        if (p.square) {
+            max_sq_level = std::max(max_sq_level, p.level);
+            max_sq_out = std::max(max_sq_out, p.n_out);
+            y_bytes = std::max(y_bytes, (size_t)p.n_out * 2 * p.level * c->N * 4);
+        }
+        if (l + 1 < m->layers.size()) x_bytes = std::max(x_bytes, (size_t)p.n_out * 2 * lout * c->N * 4);
+    }
+    m->ws_x_bytes = align_up(x_bytes);
+    m->ws_y_bytes = align_up(y_bytes);
+    int ch = m->chunk_request > 0 ? m->chunk_request : (max_sq_level ? default_chunk(c, max_sq_level, max_sq_out) : 1);
+    m->chunk = std::max(1, std::min(ch, std::max(1, max_sq_out)));
+    m->ws_chunk_bytes = max_sq_level ? chunk_bytes(c, max_sq_level, m->chunk) : 0;
+}
+
 bcn_status bcn_model_create(bcn_ctx *c, const bcn_layer *layers, int n_layers, bcn_model **out) {
     if (!c || !layers || !out || n_layers < 1) return fail(BCN_E_INVAL, "bcn_model_create: bad argument");
     *out = nullptr;
@@ -451,8 +353,6 @@ bcn_status bcn_model_create(bcn_ctx *c, const bcn_layer *layers, int n_layers, b
     bcn_model *m = new bcn_model();
     m->ctx = c;
     int level = c->L, prev_out = -1;
-    size_t x_bytes = 0;
-    int max_sq_level = 0, max_sq_out = 0;
     auto cleanup = [&](bcn_status s, const std::string &msg) {
         bcn_model_destroy(m);
         return fail(s, msg);
@@ -465,8 +365,8 @@ bcn_status bcn_model_create(bcn_ctx *c, const bcn_layer *layers, int n_layers, b
         p.square = L.square != 0;
         p.s_w = L.s_w;
         p.level = level;
-        std::vector<int32_t> idx;
-        std::vector<int8_t> w;
+        std::vector<int32_t> gidx, gout;
+        std::vector<int8_t> gw;
         if (!L.w_int) return cleanup(BCN_E_INVAL, "layer " + std::to_string(l) + ": null weights");
         if (L.type == BCN_LAYER_CONV) {
             if (L.cin < 1 || L.h < 1 || L.w < 1 || L.cout < 1 || L.k < 1 || L.stride < 1 || L.pad < 0 ||
@@ -476,85 +376,87 @@ bcn_status bcn_model_create(bcn_ctx *c, const bcn_layer *layers, int n_layers, b
             p.n_in = L.cin * L.h * L.w;
             p.n_out = L.cout * ho * wo;
             p.K = L.cin * L.k * L.k;
-            idx.assign((size_t)p.n_out * p.K, -1);
-            w.assign((size_t)p.n_out * p.K, 0);
-            for (int co = 0; co < L.cout; co++)
-                for (int oy = 0; oy < ho; oy++)
-                    for (int ox = 0; ox < wo; ox++) {
-                        const size_t o = ((size_t)co * ho + oy) * wo + ox;
-                        for (int ci = 0; ci < L.cin; ci++)
-                            for (int ky = 0; ky < L.k; ky++)
-                                for (int kx = 0; kx < L.k; kx++) {
-                                    const int iy = oy * L.stride - L.pad + ky, ix = ox * L.stride - L.pad + kx;
-                                    if (iy < 0 || iy >= L.h || ix < 0 || ix >= L.w) continue;
-                                    const size_t t = ((size_t)ci * L.k + ky) * L.k + kx;
-                                    idx[o * p.K + t] = (ci * L.h + iy) * L.w + ix;
-                                    w[o * p.K + t] = L.w_int[(((size_t)co * L.cin + ci) * L.k + ky) * L.k + kx];
-                                }
-                    }
+            // one group per output position: its taps, then every output channel
+            p.n_groups = ho * wo;
+            p.n_go = L.cout;
+            gidx.assign((size_t)p.n_groups * p.K, -1);
+            gw.assign((size_t)p.n_groups * p.n_go * p.K, 0);
+            gout.resize((size_t)p.n_groups * p.n_go);
+            for (int oy = 0; oy < ho; oy++)
+                for (int ox = 0; ox < wo; ox++) {
+                    const size_t g = (size_t)oy * wo + ox;
+                    for (int ci = 0; ci < L.cin; ci++)
+                        for (int ky = 0; ky < L.k; ky++)
+                            for (int kx = 0; kx < L.k; kx++) {
+                                const int iy = oy * L.stride - L.pad + ky, ix = ox * L.stride - L.pad + kx;
+                                if (iy < 0 || iy >= L.h || ix < 0 || ix >= L.w) continue;
+                                const size_t t = ((size_t)ci * L.k + ky) * L.k + kx;
+                                gidx[g * p.K + t] = (ci * L.h + iy) * L.w + ix;
+                                for (int co = 0; co < L.cout; co++)
+                                    gw[(g * p.n_go + co) * p.K + t] =
+                                        L.w_int[(((size_t)co * L.cin + ci) * L.k + ky) * L.k + kx];
+                            }
+                    for (int co = 0; co < L.cout; co++) gout[g * p.n_go + co] = (int)((co * ho + oy) * wo + ox);
+                }
         } else if (L.type == BCN_LAYER_DENSE) {
             if (L.n_in < 1 || L.n_out < 1) return cleanup(BCN_E_INVAL, "layer " + std::to_string(l) + ": bad dense");
             p.n_in = L.n_in;
             p.n_out = L.n_out;
             p.K = L.n_in;
-            idx.resize((size_t)p.n_out * p.K);
-            w.assign(L.w_int, L.w_int + (size_t)p.n_out * p.K);
-            for (int o = 0; o < p.n_out; o++)
-                for (int k = 0; k < p.K; k++) idx[(size_t)o * p.K + k] = k;
+            p.n_groups = 1;
+            p.n_go = L.n_out;
+            gidx.resize(p.K);
+            for (int k = 0; k < p.K; k++) gidx[k] = k;
+            gw.assign(L.w_int, L.w_int + (size_t)p.n_out * p.K);
+            gout.resize(p.n_out);
+            for (int o = 0; o < p.n_out; o++) gout[o] = o;
         } else {
             return cleanup(BCN_E_INVAL, "layer " + std::to_string(l) + ": unknown type");
         }
-        if (p.K > (1 << 20)) return cleanup(BCN_E_INVAL, "layer fan-in above 2^20");
+        if (p.K > kMaxMacTaps) return cleanup(BCN_E_INVAL, "layer fan-in above 8192");
+        if ((long long)p.n_groups * ((p.n_go + 7) / 8) > 65535)
+            return cleanup(BCN_E_INVAL, "layer " + std::to_string(l) + ": too many output tiles");
         if (prev_out >= 0 && p.n_in != prev_out)
             return cleanup(BCN_E_INVAL, "layer " + std::to_string(l) + ": input count does not match");
-        if (p.square && level < 2) return cleanup(BCN_E_LEVEL, "no level left for the square of layer " +
-                                                                   std::to_string(l));
-        if (cudaMalloc(&p.d_idx, idx.size() * 4) != cudaSuccess || cudaMalloc(&p.d_w, w.size()) != cudaSuccess) {
-            m->layers.push_back(p);
-            return cleanup(BCN_E_NOMEM, "device allocation of layer tables failed");
-        }
+        if (p.square && level < 2)
+            return cleanup(BCN_E_LEVEL, "no level left for the square of layer " + std::to_string(l));
+        std::vector<char> used(p.n_in, 0);
+        for (int32_t v : gidx)
+            if (v >= 0) used[v] = 1;
+        p.n_distinct_in = 0;
+        for (char u : used) p.n_distinct_in += u;
         m->layers.push_back(p);
-        if (cudaMemcpy(p.d_idx, idx.data(), idx.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(p.d_w, w.data(), w.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        bcn_layer_plan &q = m->layers.back();
+        if (cudaMalloc(&q.d_gidx, gidx.size() * 4) != cudaSuccess || cudaMalloc(&q.d_gw, gw.size()) != cudaSuccess ||
+            cudaMalloc(&q.d_gout, gout.size() * 4) != cudaSuccess)
+            return cleanup(BCN_E_NOMEM, "device allocation of layer tables failed");
+        if (cudaMemcpy(q.d_gidx, gidx.data(), gidx.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(q.d_gw, gw.data(), gw.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(q.d_gout, gout.data(), gout.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
             return cleanup(BCN_E_CUDA, "upload of layer tables failed");
-        if (p.square) {
-            max_sq_level = std::max(max_sq_level, level);
-            max_sq_out = std::max(max_sq_out, p.n_out);
-            level -= 1;
-        }
-        if (l + 1 < n_layers) x_bytes = std::max(x_bytes, (size_t)p.n_out * 2 * level * c->N * 4);
+        if (p.square) level -= 1;
         prev_out = p.n_out;
     }
     m->out_level = level;
-    m->ws_x_bytes = align_up(x_bytes);
-    m->chunk = max_sq_level ? default_chunk(c, max_sq_level, max_sq_out) : 1;
-    m->ws_chunk_bytes = max_sq_level ? chunk_bytes(c, max_sq_level, m->chunk) : 0;
-    // inputs each MAC launch reads (for the algorithmic byte count of the profiler)
-    for (size_t l = 0; l < m->layers.size(); l++) {
-        const bcn_layer_plan &p = m->layers[l];
-        std::vector<int> counts;
-        const int step = p.square ? m->chunk : p.n_out;
-        std::vector<int32_t> idx((size_t)p.n_out * p.K);
-        cudaMemcpy(idx.data(), p.d_idx, idx.size() * 4, cudaMemcpyDeviceToHost);
-        std::vector<char> seen(p.n_in);
-        for (int o0 = 0; o0 < p.n_out; o0 += step) {
-            std::fill(seen.begin(), seen.end(), 0);
-            int cnt = 0;
-            for (size_t i = (size_t)o0 * p.K; i < (size_t)std::min(p.n_out, o0 + step) * p.K; i++)
-                if (idx[i] >= 0 && !seen[idx[i]]) { seen[idx[i]] = 1; cnt++; }
-            counts.push_back(cnt);
-        }
-        m->distinct_inputs.push_back(counts);
-    }
+    m->chunk_request = 0;
+    model_layout(m);
     *out = m;
+    return BCN_OK;
+}
+
+bcn_status bcn_model_set_chunk(bcn_model *m, int chunk) {
+    if (!m) return fail(BCN_E_INVAL, "bcn_model_set_chunk: null model");
+    m->chunk_request = chunk > 0 ? chunk : 0;
+    model_layout(m);
     return BCN_OK;
 }
 
 bcn_status bcn_model_destroy(bcn_model *m) {
     if (!m) return BCN_OK;
     for (auto &p : m->layers) {
-        cudaFree(p.d_idx);
-        cudaFree(p.d_w);
+        cudaFree(p.d_gidx);
+        cudaFree(p.d_gw);
+        cudaFree(p.d_gout);
     }
     for (auto e : m->prof.ev) cudaEventDestroy(e);
     delete m;
@@ -614,7 +516,7 @@ bcn_status bcn_evk_prepare(const bcn_ctx *c, const uint32_t *evk, uint32_t *evk_
 
 bcn_status bcn_eval_workspace_bytes(const bcn_model *m, size_t *bytes) {
     if (!m || !bytes) return fail(BCN_E_INVAL, "bcn_eval_workspace_bytes: null argument");
-    *bytes = 2 * m->ws_x_bytes + m->ws_chunk_bytes;
+    *bytes = 2 * m->ws_x_bytes + m->ws_y_bytes + m->ws_chunk_bytes;
     return BCN_OK;
 }
 
@@ -632,31 +534,35 @@ bcn_status bcn_eval(const bcn_model *m, const uint32_t *evk, const uint32_t *cts
     cudaStream_t st = (cudaStream_t)stream;
     char *w = reinterpret_cast<char *>(ws);
     uint32_t *X[2] = {reinterpret_cast<uint32_t *>(w), reinterpret_cast<uint32_t *>(w + m->ws_x_bytes)};
-    char *chunk_ws = w + 2 * m->ws_x_bytes;
+    uint32_t *Yfull = reinterpret_cast<uint32_t *>(w + 2 * m->ws_x_bytes);
+    char *chunk_ws = w + 2 * m->ws_x_bytes + m->ws_y_bytes;
     const uint32_t *x = cts;
     int a = 0;
     const size_t N = c->N;
+    Profiler *prof = &m->prof;
     for (size_t l = 0; l < m->layers.size(); l++) {
         const bcn_layer_plan &p = m->layers[l];
         const bool last = l + 1 == m->layers.size();
         uint32_t *y = last ? out : X[l % 2];
         const uint32_t *pt = nullptr;
         if (p.add) {
-            if (!pts || !pts[a] || !aligned16(pts[a])) return fail(BCN_E_INVAL, "bcn_eval: missing feature plaintexts");
+            if (!pts || !pts[a] || !aligned16(pts[a]))
+                return fail(BCN_E_INVAL, "bcn_eval: missing feature plaintexts");
             pt = pts[a++];
         }
-        Profiler *prof = &m->prof;
-        if (!p.square) {
-            BCN_TRY(launch_mac(c, p.level, p.K, p.d_idx, p.d_w, x, pt, y, 0, p.n_out, st, prof,
-                               m->distinct_inputs[l][0]));
-        } else {
+        const double limb = (double)N * 4;
+        const double mac_bytes = limb * ((double)p.n_distinct_in * 2 * p.level + (double)p.n_out * 2 * p.level +
+                                         (pt ? (double)p.n_out * p.level : 0.0));
+        uint32_t *mac_out = p.square ? Yfull : y;
+        BCN_TRY(launch_mac(c, p.level, p.K, p.n_groups, p.n_go, p.d_gidx, p.d_gw, p.d_gout, x, pt, mac_out, st, prof,
+                           mac_bytes));
+        if (p.square) {
             const int n = p.level;
             ChunkBufs b = carve_chunk(c, n, m->chunk, chunk_ws);
-            for (int o0 = 0, ci = 0; o0 < p.n_out; o0 += m->chunk, ci++) {
+            for (int o0 = 0; o0 < p.n_out; o0 += m->chunk) {
                 const int C = std::min(m->chunk, p.n_out - o0);
-                BCN_TRY(launch_mac(c, n, p.K, p.d_idx, p.d_w, x, pt, b.y, o0, C, st, prof,
-                                   m->distinct_inputs[l][ci]));
-                BCN_TRY(square_chunk(c, n, evk, b, C, y + (size_t)o0 * 2 * (n - 1) * N, st, prof));
+                BCN_TRY(square_chunk(c, n, evk, Yfull + (size_t)o0 * 2 * n * N, b, C, y + (size_t)o0 * 2 * (n - 1) * N,
+                                     st, prof));
             }
         }
         x = y;
@@ -769,7 +675,8 @@ bcn_status bcn_op_ntt(const bcn_ctx *c, uint32_t *data, int n_poly, int level, i
 bcn_status bcn_op_mac(const bcn_ctx *c, int level, int n_in, int n_out, int K, const int32_t *idx, const int8_t *w,
                       const uint32_t *in, const uint32_t *pt, uint32_t *out, void *stream) {
     BCN_TRY(check_device(c));
-    if (!idx || !w || !in || !out || level < 1 || level > c->L || n_in < 0 || n_out < 0 || K < 0 || K > (1 << 20))
+    if (!idx || !w || !in || !out || level < 1 || level > c->L || n_in < 0 || n_out < 0 || K < 0 ||
+        K > kMaxMacTaps)
         return fail(BCN_E_INVAL, "bcn_op_mac: bad argument");
     if (!aligned16(in) || !aligned16(out) || (pt && !aligned16(pt)))
         return fail(BCN_E_INVAL, "bcn_op_mac: buffers must be 16-byte aligned");
@@ -780,7 +687,8 @@ bcn_status bcn_op_mac(const bcn_ctx *c, int level, int n_in, int n_out, int K, c
         for (int32_t v : h)
             if (v < -1 || v >= n_in) return fail(BCN_E_INVAL, "bcn_op_mac: idx entry outside [-1, n_in)");
     }
-    return launch_mac(c, level, K, idx, w, in, pt, out, 0, n_out, (cudaStream_t)stream);
+    // every output is a group of one with its own taps
+    return launch_mac(c, level, K, n_out, 1, idx, w, nullptr, in, pt, out, (cudaStream_t)stream);
 }
 
 bcn_status bcn_op_workspace_bytes(const bcn_ctx *c, int level, int n_ct, size_t *bytes) {
@@ -792,23 +700,17 @@ bcn_status bcn_op_workspace_bytes(const bcn_ctx *c, int level, int n_ct, size_t 
 bcn_status bcn_op_tensor_square(const bcn_ctx *c, int level, const uint32_t *in, int n_ct, uint32_t *out, void *ws,
                                 size_t ws_bytes, void *stream) {
     BCN_TRY(check_device(c));
-    size_t need = 0;
-    BCN_TRY(bcn_op_workspace_bytes(c, level, n_ct, &need));
-    if (ws_bytes < need || !ws) return fail(BCN_E_BUDGET, "bcn_op_tensor_square: workspace too small");
-    if (!in || !out || !aligned16(in) || !aligned16(out)) return fail(BCN_E_INVAL, "bcn_op_tensor_square: buffers");
+    if (!in || !out || !aligned16(in) || !aligned16(out) || n_ct < 0 || level < 1 || level > c->L)
+        return fail(BCN_E_INVAL, "bcn_op_tensor_square: bad argument");
+    (void)ws;
+    (void)ws_bytes;
     cudaStream_t st = (cudaStream_t)stream;
-    const int N = c->N, n = level, chunk = default_chunk(c, level, n_ct);
-    ChunkBufs b = carve_chunk(c, n, chunk, reinterpret_cast<char *>(ws));
-    for (int o0 = 0; o0 < n_ct; o0 += chunk) {
-        const int C = std::min(chunk, n_ct - o0);
-        if (cudaMemcpyAsync(b.y, in + (size_t)o0 * 2 * n * N, (size_t)C * 2 * n * N * 4, cudaMemcpyDeviceToDevice,
-                            st) != cudaSuccess)
-            return fail(BCN_E_CUDA, "copy failed");
-        BCN_TRY(launch_ntt(c, b.y, (size_t)C * 2 * n, data_map(n), false, st));
-        uint32_t *d = out + (size_t)o0 * 3 * n * N;
-        k_tensor_square<<<dim3((N / 4 + 255) / 256, n, C), 256, 0, st>>>(b.y, d, n, N, c->d_pc);
-        BCN_TRY(check_launch("k_tensor_square"));
-        BCN_TRY(launch_ntt(c, d, (size_t)C * 3 * n, data_map(n), true, st));
+    const size_t N = c->N;
+    const CoreFns *f = core_fns(c->logN);
+    if (!f) return fail(BCN_E_INVAL, "unsupported ring degree");
+    for (int o0 = 0; o0 < n_ct; o0 += 32768) {
+        const int C = std::min(32768, n_ct - o0);
+        BCN_TRY(f->square(c, level, in + (size_t)o0 * 2 * level * N, out + (size_t)o0 * 3 * level * N, C, st));
     }
     return BCN_OK;
 }
@@ -823,14 +725,12 @@ bcn_status bcn_op_square_relin_rescale(const bcn_ctx *c, int level, const uint32
     if (!in || !out || !evk || !aligned16(in) || !aligned16(out) || !aligned16(evk))
         return fail(BCN_E_INVAL, "bcn_op_square_relin_rescale: buffers");
     cudaStream_t st = (cudaStream_t)stream;
-    const int N = c->N, n = level, chunk = default_chunk(c, level, n_ct);
+    const int n = level, chunk = default_chunk(c, level, n_ct);
+    const size_t N = c->N;
     ChunkBufs b = carve_chunk(c, n, chunk, reinterpret_cast<char *>(ws));
     for (int o0 = 0; o0 < n_ct; o0 += chunk) {
         const int C = std::min(chunk, n_ct - o0);
-        if (cudaMemcpyAsync(b.y, in + (size_t)o0 * 2 * n * N, (size_t)C * 2 * n * N * 4, cudaMemcpyDeviceToDevice,
-                            st) != cudaSuccess)
-            return fail(BCN_E_CUDA, "copy failed");
-        BCN_TRY(square_chunk(c, n, evk, b, C, out + (size_t)o0 * 2 * (n - 1) * N, st));
+        BCN_TRY(square_chunk(c, n, evk, in + (size_t)o0 * 2 * n * N, b, C, out + (size_t)o0 * 2 * (n - 1) * N, st));
     }
     return BCN_OK;
 }
@@ -839,7 +739,6 @@ bcn_status bcn_op_rescale(const bcn_ctx *c, int level, const uint32_t *in, int n
     BCN_TRY(check_device(c));
     if (level < 2 || level > c->L) return fail(BCN_E_LEVEL, "bcn_op_rescale: level must be >= 2");
     if (!in || !out || n_ct < 0) return fail(BCN_E_INVAL, "bcn_op_rescale: bad argument");
-    if (n_ct == 0) return BCN_OK;
     const size_t N = c->N;
     for (int z0 = 0; z0 < n_ct; z0 += 65535) {  // grid.z limit
         const int nz = std::min(65535, n_ct - z0);

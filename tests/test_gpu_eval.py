@@ -76,6 +76,19 @@ def test_eval_bit_exact(case):
     assert ok
 
 
+def test_eval_chunk_size_does_not_change_results(case):
+    """The key-switching chunk (ciphertexts per launch of the square kernels)
+    is a performance knob: a ragged chunk gives the same residues."""
+    cfg, prob, ref = case
+    ctx = bcn.Context.from_config(cfg)
+    model = bcn.Model(ctx, cfg["cipher"], prob.w_int, prob.s_w)
+    model.set_chunk(7)
+    evk_eval = ctx.evk_prepare(dev(prob.evk))
+    out = torch.empty(model.out_shape(), dtype=torch.int32, device="cuda")
+    model.eval(evk_eval, dev(prob.cts), [dev(p) for p in prob.pts], out, model.alloc_workspace())
+    assert np.array_equal(host(out), ref)
+
+
 def test_eval_host_path_matches_device_path(case):
     cfg, prob, ref = case
     ctx = bcn.Context.from_config(cfg)
