@@ -284,6 +284,25 @@ bcn_status bcn_op_tensor_square(const bcn_ctx *ctx, int level, const uint32_t *i
 bcn_status bcn_op_square_relin_rescale(const bcn_ctx *ctx, int level, const uint32_t *evk_eval_dev,
                                        const uint32_t *in_dev, int n_ct, uint32_t *out_dev, void *workspace_dev,
                                        size_t workspace_bytes, void *cuda_stream);
+/* The square activation above without any allocation.  The paper has no
+ * counterpart: this is a service for callers that may not allocate device
+ * memory themselves (a serving process whose device memory is budgeted by an
+ * admission controller, code under a framework allocator that forbids
+ * allocations behind its back; cudaMalloc/cudaFree would also synchronise the
+ * device mid-request).  The caller passes only inputs and outputs; the key-
+ * switching intermediates live in one file-scope device array of 32 MiB that
+ * every GPU loading the library holds until exit.  Ciphertexts are processed in
+ * chunks that fit it; BCN_E_BUDGET if a single ciphertext at `level` does not.
+ * The first call on a device looks the array's device address up (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call shares the array, so calls that overlap on the GPU (other
+ * streams, other threads) race; nothing in it has to start at zero (each word is
+ * written before it is read within a call).  Same layouts, results and errors
+ * as bcn_op_square_relin_rescale; allocates nothing (no cudaMalloc/cudaFree, no
+ * allocating library routine). */
+bcn_status bcn_op_square_relin_rescale_noalloc(const bcn_ctx *ctx, int level, const uint32_t *evk_eval_dev,
+                                               const uint32_t *in_dev, int n_ct, uint32_t *out_dev,
+                                               void *cuda_stream);
 /* rescale alone: [n_ct][2][level][N] -> [n_ct][2][level-1][N] */
 bcn_status bcn_op_rescale(const bcn_ctx *ctx, int level, const uint32_t *in_dev, int n_ct, uint32_t *out_dev,
                           void *cuda_stream);

@@ -90,6 +90,7 @@ _SIGS = {
     "bcn_op_tensor_square": (_I, [_P, _I, _P, _I, _P, _P, _SZ, _P]),
     "bcn_op_square_relin_rescale": (_I, [_P, _I, _P, _P, _I, _P, _P, _SZ, _P]),
     "bcn_op_rescale": (_I, [_P, _I, _P, _I, _P, _P]),
+    "bcn_op_square_relin_rescale_noalloc": (_I, [_P, _I, _P, _P, _I, _P, _P]),
 }
 
 _lock = threading.Lock()
@@ -304,6 +305,15 @@ class Context:
                                                  _dev_ptr(in_dev, n_ct * 2 * level * self.N), n_ct,
                                                  _dev_ptr(out_dev, n_ct * 2 * (level - 1) * self.N), ws.data_ptr(),
                                                  nb, _stream(stream)), "bcn_op_square_relin_rescale")
+
+    def op_square_relin_rescale_noalloc(self, level, evk_eval, in_dev, n_ct, out_dev, stream=None):
+        """bcn_op_square_relin_rescale_noalloc: the same square activation for
+        callers that may not allocate device memory; its intermediates live in the
+        library's fixed 32 MiB device array, so no workspace is passed (or made)."""
+        _check(lib().bcn_op_square_relin_rescale_noalloc(
+            self._h, level, _dev_ptr(evk_eval, self.evk_words()), _dev_ptr(in_dev, n_ct * 2 * level * self.N), n_ct,
+            _dev_ptr(out_dev, n_ct * 2 * (level - 1) * self.N), _stream(stream)),
+            "bcn_op_square_relin_rescale_noalloc")
 
     def op_rescale(self, level, in_dev, n_ct, out_dev, stream=None):
         _check(lib().bcn_op_rescale(self._h, level, _dev_ptr(in_dev, n_ct * 2 * level * self.N), n_ct,

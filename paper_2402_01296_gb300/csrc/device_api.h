@@ -63,6 +63,11 @@ const CoreFns *core_fns_12();
 const CoreFns *core_fns_13();
 const CoreFns *core_fns_14();
 
+// square + relinearise + rescale of C ciphertexts Y [C][2][n][N] -> out [C][2][n-1][N],
+// intermediates in d [C][3][n][N] and acc [C][2][n+K][N]
+bcn_status square_relin_rescale_chunk(const bcn_ctx *c, int n, const uint32_t *evk, const uint32_t *Y, uint32_t *d,
+                                      uint32_t *acc, int C, uint32_t *out, cudaStream_t st);
+
 bcn_status launch_ntt(const bcn_ctx *c, uint32_t *data, size_t n_limbs, const PrimeMap &pm, bool inverse,
                       cudaStream_t st);
 bcn_status cores_setup_all();

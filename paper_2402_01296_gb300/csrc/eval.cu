@@ -277,6 +277,14 @@ static bcn_status square_chunk(const bcn_ctx *c, int n, const uint32_t *evk, con
     return check_launch("k_moddown_rescale");
 }
 
+// Square activation of C ciphertexts with the intermediates in caller-chosen
+// memory: d [C][3][n][N], acc [C][2][n+K][N].
+bcn_status square_relin_rescale_chunk(const bcn_ctx *c, int n, const uint32_t *evk, const uint32_t *Y, uint32_t *d,
+                                      uint32_t *acc, int C, uint32_t *out, cudaStream_t st) {
+    ChunkBufs b{d, acc};
+    return square_chunk(c, n, evk, Y, b, C, out, st);
+}
+
 // ----------------------------------------------------------- device context
 bcn_status device_ctx_init(bcn_ctx *c) {
     if (cudaSetDevice(c->device) != cudaSuccess) return fail(BCN_E_CUDA, "cudaSetDevice failed");
