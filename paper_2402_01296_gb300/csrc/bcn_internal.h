@@ -38,6 +38,8 @@ struct PrimeConst {
     uint32_t ninv;       // N^{-1} mod q
     uint32_t ninv_shoup;
     uint32_t half;       // (q - 1) / 2: the largest residue whose centred value is >= 0
+    uint32_t rn;         // R * N^{-1} mod q: Montgomery form of N^{-1}
+    uint32_t rn_shoup;   // Shoup companion of rn
     uint32_t pad_;
     uint64_t barrett;    // floor(2^64 / q)
     uint64_t mac_offset; // a multiple of q >= 2^58 (makes a signed MAC sum non-negative)

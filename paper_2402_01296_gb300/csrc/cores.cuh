@@ -39,17 +39,28 @@ __global__ void __launch_bounds__((1 << LOGN) / R) k_ntt_inv(uint32_t *__restric
     C::store_natural(x, a, tid);
 }
 
+// Register budget per thread of the fused kernels (sets their blocks per SM).
+#ifndef BCN_CORE_REGS
+#define BCN_CORE_REGS 128
+#endif
+template <int T>
+struct CoreOcc {
+    static constexpr int B = 65536 / (T * BCN_CORE_REGS);
+    static constexpr int MIN_BLOCKS = B > 32 ? 32 : (B < 1 ? 1 : B);
+};
+
 // Square activation, first half: forward NTT of c0 and c1 of one limb,
 // tensor square (c0^2, 2 c0 c1, c1^2) in the NTT domain, inverse NTT of the
-// three products.  Y [C][2][n][N] -> D [C][3][n][N], coefficient form.
-// grid (n, C): one block per (limb, ciphertext).
+// three products.  Y [C][2][n][N] -> D [C][3][n][N], coefficient form; with
+// D2N != nullptr also c1^2 in the NTT domain (last-pass layout of the NTT) to
+// D2N [C][n][N], which the key-switching kernel reuses on the digit's own prime.
+// The products are formed with R*N^{-1} in place of R, so they carry the
+// inverse transform's N^{-1} already.  grid (n, C): one block per (limb, ct).
 template <int LOGN, int R>
-__global__ void __launch_bounds__((1 << LOGN) / R) k_square_core(const uint32_t *__restrict__ Y,
-                                                                uint32_t *__restrict__ D, int n,
-                                                                const PrimeConst *__restrict__ pc,
-                                                                const uint2 *__restrict__ twf,
-                                                                const uint2 *__restrict__ twi) {
-    using C = NttCore<LOGN, R>;
+__global__ void __launch_bounds__((1 << LOGN) / R, CoreOcc<(1 << LOGN) / R>::MIN_BLOCKS)
+    k_square_core(const uint32_t *__restrict__ Y, uint32_t *__restrict__ D, uint32_t *__restrict__ D2N, int n,
+                  const PrimeConst *__restrict__ pc, const uint2 *__restrict__ twf, const uint2 *__restrict__ twi) {
+    using C = NttCore<LOGN, R, true>;  // data primes only (q < 2^30): lazy butterflies
     constexpr int N = C::N, T = C::T;
     extern __shared__ __align__(16) uint32_t sm[];
     // exchange buffer, then two thread-private parking areas (slot u*T + tid)
@@ -57,48 +68,62 @@ __global__ void __launch_bounds__((1 << LOGN) / R) k_square_core(const uint32_t 
     const int i = blockIdx.x, ct = blockIdx.y, tid = threadIdx.x;
     const PrimeConst P = pc[i];
     const uint2 *tf = twf + (size_t)i * N, *ti = twi + (size_t)i * N;
-    uint32_t a[R], b[R];
-    C::load_natural(a, Y + (((size_t)ct * 2 + 0) * n + i) * N, tid);
-    C::forward(a, sm, tid, P.q, tf);
-    C::load_natural(b, Y + (((size_t)ct * 2 + 1) * n + i) * N, tid);
-    C::forward(b, sm, tid, P.q, tf);
+    uint32_t x[R];
+    // c0 -> NTT, parked in s1
+    C::load_natural(x, Y + (((size_t)ct * 2 + 0) * n + i) * N, tid);
+    C::forward(x, sm, tid, P.q, tf);
+#pragma unroll
+    for (int u = 0; u < R; u++) s1[u * T + tid] = x[u];
+    // c1 -> NTT; c0^2/N in registers, 2 c0 c1/N in s1, c1^2/N in s2 (inputs in [0, 4q))
+    C::load_natural(x, Y + (((size_t)ct * 2 + 1) * n + i) * N, tid);
+    C::forward(x, sm, tid, P.q, tf);
+    if (D2N != nullptr) {
+        uint32_t y[R];
+#pragma unroll
+        for (int u = 0; u < R; u++) {
+            const uint32_t bR = shoup_mul(x[u], P.r_mod, P.r_shoup, P.q);
+            y[u] = mont_mul(bR, x[u], P.q, P.qneg_inv);  // c1^2, canonical
+        }
+        C::store_ntt(y, D2N + ((size_t)ct * n + i) * N, tid);
+    }
 #pragma unroll
     for (int u = 0; u < R; u++) {
-        const uint32_t aR = shoup_mul(a[u], P.r_mod, P.r_shoup, P.q);
-        const uint32_t bR = shoup_mul(b[u], P.r_mod, P.r_shoup, P.q);
-        const uint32_t x = mont_mul(aR, b[u], P.q, P.qneg_inv);
-        s2[u * T + tid] = mont_mul(bR, b[u], P.q, P.qneg_inv);  // c1^2
-        s1[u * T + tid] = add_mod(x, x, P.q);                     // 2 c0 c1
-        a[u] = mont_mul(aR, a[u], P.q, P.qneg_inv);               // c0^2
+        const uint32_t a = s1[u * T + tid], b = x[u];
+        const uint32_t aRN = shoup_mul(a, P.rn, P.rn_shoup, P.q);
+        const uint32_t bRN = shoup_mul(b, P.rn, P.rn_shoup, P.q);
+        const uint32_t ab = mont_mul(aRN, b, P.q, P.qneg_inv);
+        s1[u * T + tid] = add_mod(ab, ab, P.q);
+        s2[u * T + tid] = mont_mul(bRN, b, P.q, P.qneg_inv);
+        x[u] = mont_mul(aRN, a, P.q, P.qneg_inv);
     }
-    C::inverse(a, sm, tid, P.q, ti, P.ninv, P.ninv_shoup);
-    C::store_natural(a, D + (((size_t)ct * 3 + 0) * n + i) * N, tid);
+    C::inverse_unscaled(x, sm, tid, P.q, ti);
+    C::store_natural(x, D + (((size_t)ct * 3 + 0) * n + i) * N, tid);
 #pragma unroll
-    for (int u = 0; u < R; u++) a[u] = s1[u * T + tid];
-    C::inverse(a, sm, tid, P.q, ti, P.ninv, P.ninv_shoup);
-    C::store_natural(a, D + (((size_t)ct * 3 + 1) * n + i) * N, tid);
+    for (int u = 0; u < R; u++) x[u] = s1[u * T + tid];
+    C::inverse_unscaled(x, sm, tid, P.q, ti);
+    C::store_natural(x, D + (((size_t)ct * 3 + 1) * n + i) * N, tid);
 #pragma unroll
-    for (int u = 0; u < R; u++) a[u] = s2[u * T + tid];
-    C::inverse(a, sm, tid, P.q, ti, P.ninv, P.ninv_shoup);
-    C::store_natural(a, D + (((size_t)ct * 3 + 2) * n + i) * N, tid);
+    for (int u = 0; u < R; u++) x[u] = s2[u * T + tid];
+    C::inverse_unscaled(x, sm, tid, P.q, ti);
+    C::store_natural(x, D + (((size_t)ct * 3 + 2) * n + i) * N, tid);
 }
 
 // Key switching of d2, fused per (target prime t, ciphertext): for every
 // digit j, ModUp of d2 into prime t (the residue itself on the digit's own
-// primes, else the centred fast basis conversion
-//     sum_u r_u * Dhat_u - #{u : r_u > (q_u-1)/2} * D_j,  r_u = [x_u Dhat_u^{-1}]_{q_u}),
-// forward NTT, and the product with evk_j accumulated for both key halves;
-// then the inverse NTT of the two sums.  No extended-basis limb is stored.
+// primes -- taken from D2N in the NTT domain when given -- else the centred
+// fast basis conversion
+//     sum_u r_u * Dhat_u - #{u : r_u > (q_u-1)/2} * D_j,  r_u = [x_u Dhat_u^{-1}]_{q_u},
+// which for one-prime digits is d mod t, less q_j mod t when d > (q_j-1)/2),
+// forward NTT, and the product with evk_j (prepared as k*R*N^{-1}, so one
+// Montgomery product gives k*x/N) accumulated for both key halves; then the
+// inverse NTT of the two sums.  No extended-basis limb is stored.
 // D [C][3][n][N] (d2 in coefficient form) -> ACC [C][2][n+K][N] (coefficient form).
-// grid (n+K, C).
-template <int LOGN, int R>
-__global__ void __launch_bounds__((1 << LOGN) / R) k_ks_core(const uint32_t *__restrict__ D,
-                                                            const uint32_t *__restrict__ evk,
-                                                            uint32_t *__restrict__ acc_out, int n, KsDev ks,
-                                                            const PrimeConst *__restrict__ pc,
-                                                            const uint2 *__restrict__ twf,
-                                                            const uint2 *__restrict__ twi) {
-    using C = NttCore<LOGN, R>;
+template <int LOGN, int R, bool LAZY>
+__device__ __forceinline__ void ks_core_body(const uint32_t *__restrict__ D, const uint32_t *__restrict__ D2N,
+                                             const uint32_t *__restrict__ evk, uint32_t *__restrict__ acc_out,
+                                             int n, const KsDev &ks, const PrimeConst *__restrict__ pc,
+                                             const uint2 *__restrict__ twf, const uint2 *__restrict__ twi) {
+    using C = NttCore<LOGN, R, LAZY>;
     constexpr int N = C::N, T = C::T;
     extern __shared__ __align__(16) uint32_t sm[];
     // exchange buffer, then the two running sums in thread-private slots u*T + tid
@@ -114,28 +139,43 @@ __global__ void __launch_bounds__((1 << LOGN) / R) k_ks_core(const uint32_t *__r
     for (int u = 0; u < R; u++) s0[u * T + tid] = s1[u * T + tid] = 0;
     for (int j = 0; j < dnum; j++) {
         const int lo = j * A, hi = min(lo + A, n);
-        if (t >= lo && t < hi) {
-            C::load_natural(x, x2 + (size_t)t * N, tid);
+        if (t >= lo && t < hi && D2N != nullptr) {
+            C::load_ntt(x, D2N + ((size_t)ct * n + t) * N, tid);
         } else {
-#pragma unroll
-            for (int u = 0; u < R; u++) x[u] = 0;
-            const uint32_t dp = ks.dprod[(size_t)(n * ks.dnum_max + j) * ks.P + pt];
-            for (int v = 0; v < hi - lo; v++) {
-                const int i = lo + v;
-                const uint32_t qi = pc[i].q, half = pc[i].half;
-                const uint2 di = ks.dhat_inv[(size_t)(n * ks.dnum_max + j) * A + v];
-                const uint2 dh = ks.dhat[((size_t)(n * ks.dnum_max + j) * A + v) * ks.P + pt];
-                const uint32_t *xi = x2 + (size_t)i * N;
+            if (t >= lo && t < hi) {
+                C::load_natural(x, x2 + (size_t)t * N, tid);
+            } else if (A == 1) {
+                const uint32_t half = pc[j].half;
+                const uint32_t dp = ks.dprod[(size_t)(n * ks.dnum_max + j) * ks.P + pt];  // q_j mod t
+                const uint32_t *xj = x2 + (size_t)j * N;
 #pragma unroll
                 for (int u = 0; u < R; u++) {
-                    const uint32_t r = shoup_mul(__ldg(xi + tid + u * T), di.x, di.y, qi);
-                    uint32_t y = add_mod(x[u], shoup_mul(r, dh.x, dh.y, P.q), P.q);
-                    if (r > half) y = sub_mod(y, dp, P.q);
+                    const uint32_t d = __ldg(xj + tid + u * T);
+                    uint32_t y = reduce_once(d, P.q);  // d < q_j < 2t
+                    if (d > half) y = sub_mod(y, dp, P.q);
                     x[u] = y;
                 }
+            } else {
+#pragma unroll
+                for (int u = 0; u < R; u++) x[u] = 0;
+                const uint32_t dp = ks.dprod[(size_t)(n * ks.dnum_max + j) * ks.P + pt];
+                for (int v = 0; v < hi - lo; v++) {
+                    const int i = lo + v;
+                    const uint32_t qi = pc[i].q, half = pc[i].half;
+                    const uint2 di = ks.dhat_inv[(size_t)(n * ks.dnum_max + j) * A + v];
+                    const uint2 dh = ks.dhat[((size_t)(n * ks.dnum_max + j) * A + v) * ks.P + pt];
+                    const uint32_t *xi = x2 + (size_t)i * N;
+#pragma unroll
+                    for (int u = 0; u < R; u++) {
+                        const uint32_t r = shoup_mul(__ldg(xi + tid + u * T), di.x, di.y, qi);
+                        uint32_t y = add_mod(x[u], shoup_mul(r, dh.x, dh.y, P.q), P.q);
+                        if (r > half) y = sub_mod(y, dp, P.q);
+                        x[u] = y;
+                    }
+                }
             }
+            C::forward(x, sm, tid, P.q, tf);
         }
-        C::forward(x, sm, tid, P.q, tf);
         const uint32_t *k0 = evk + ((size_t)(j * 2 + 0) * ks.P + pt) * N;
         const uint32_t *k1 = evk + ((size_t)(j * 2 + 1) * ks.P + pt) * N;
         if constexpr (C::NTT_QUADS) {
@@ -164,12 +204,27 @@ __global__ void __launch_bounds__((1 << LOGN) / R) k_ks_core(const uint32_t *__r
     }
 #pragma unroll
     for (int u = 0; u < R; u++) x[u] = s0[u * T + tid];
-    C::inverse(x, sm, tid, P.q, ti, P.ninv, P.ninv_shoup);
+    C::inverse_unscaled(x, sm, tid, P.q, ti);
     C::store_natural(x, acc_out + (((size_t)ct * 2 + 0) * nb + t) * N, tid);
 #pragma unroll
     for (int u = 0; u < R; u++) x[u] = s1[u * T + tid];
-    C::inverse(x, sm, tid, P.q, ti, P.ninv, P.ninv_shoup);
+    C::inverse_unscaled(x, sm, tid, P.q, ti);
     C::store_natural(x, acc_out + (((size_t)ct * 2 + 1) * nb + t) * N, tid);
+}
+
+// grid (n+K, C); lazy butterflies for the data primes (< 2^30), strict ones for
+// the special primes (< 2^31)
+template <int LOGN, int R>
+__global__ void __launch_bounds__((1 << LOGN) / R, CoreOcc<(1 << LOGN) / R>::MIN_BLOCKS)
+    k_ks_core(const uint32_t *__restrict__ D, const uint32_t *__restrict__ D2N, const uint32_t *__restrict__ evk,
+              uint32_t *__restrict__ acc_out, int n, KsDev ks, const PrimeConst *__restrict__ pc,
+              const uint2 *__restrict__ twf, const uint2 *__restrict__ twi) {
+    const int t = blockIdx.x;
+    const int pt = t < n ? t : ks.L + (t - n);
+    if (pc[pt].q < (1u << 30))
+        ks_core_body<LOGN, R, true>(D, D2N, evk, acc_out, n, ks, pc, twf, twi);
+    else
+        ks_core_body<LOGN, R, false>(D, D2N, evk, acc_out, n, ks, pc, twf, twi);
 }
 
 template <int LOGN, int R>
@@ -186,13 +241,15 @@ struct CoreImpl {
             k_ntt_fwd<LOGN, R><<<(unsigned)n_limbs, Core::T, SMEM, st>>>(data, pm, c->d_pc, c->d_tw_fwd);
         return check_launch("NTT");
     }
-    static bcn_status square(const bcn_ctx *c, int n, const uint32_t *Y, uint32_t *D, int C, cudaStream_t st) {
-        k_square_core<LOGN, R><<<dim3(n, C), Core::T, SMEM3, st>>>(Y, D, n, c->d_pc, c->d_tw_fwd, c->d_tw_inv);
+    static bcn_status square(const bcn_ctx *c, int n, const uint32_t *Y, uint32_t *D, uint32_t *D2N, int C,
+                             cudaStream_t st) {
+        k_square_core<LOGN, R><<<dim3(n, C), Core::T, SMEM3, st>>>(Y, D, D2N, n, c->d_pc, c->d_tw_fwd,
+                                                                   c->d_tw_inv);
         return check_launch("k_square_core");
     }
-    static bcn_status keyswitch(const bcn_ctx *c, int n, const uint32_t *D, const uint32_t *evk, uint32_t *acc,
-                                int C, cudaStream_t st) {
-        k_ks_core<LOGN, R><<<dim3(n + c->K, C), Core::T, SMEM3, st>>>(D, evk, acc, n, ks_dev(c), c->d_pc,
+    static bcn_status keyswitch(const bcn_ctx *c, int n, const uint32_t *D, const uint32_t *D2N,
+                                const uint32_t *evk, uint32_t *acc, int C, cudaStream_t st) {
+        k_ks_core<LOGN, R><<<dim3(n + c->K, C), Core::T, SMEM3, st>>>(D, D2N, evk, acc, n, ks_dev(c), c->d_pc,
                                                                      c->d_tw_fwd, c->d_tw_inv);
         return check_launch("k_ks_core");
     }
@@ -205,6 +262,10 @@ struct CoreImpl {
             cudaFuncSetAttribute(k_square_core<LOGN, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem3) !=
                 cudaSuccess ||
             cudaFuncSetAttribute(k_ks_core<LOGN, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem3) !=
+                cudaSuccess ||
+            cudaFuncSetAttribute(k_square_core<LOGN, R>, cudaFuncAttributePreferredSharedMemoryCarveout, 100) !=
+                cudaSuccess ||
+            cudaFuncSetAttribute(k_ks_core<LOGN, R>, cudaFuncAttributePreferredSharedMemoryCarveout, 100) !=
                 cudaSuccess)
             return fail(BCN_E_CUDA, "cudaFuncSetAttribute failed for the NTT-based kernels");
         return BCN_OK;

@@ -1,6 +1,10 @@
-// NTT-based kernels for N = 2^12 (16 residues per thread).
+// NTT-based kernels for N = 2^12.
 #include "cores.cuh"
 
+#ifndef BCN_R12
+#define BCN_R12 16  // residues per thread
+#endif
+
 namespace bcn {
-const CoreFns *core_fns_12() { return CoreImpl<12, 16>::fns(); }
+const CoreFns *core_fns_12() { return CoreImpl<12, BCN_R12>::fns(); }
 }  // namespace bcn

@@ -1,6 +1,10 @@
-// NTT-based kernels for N = 2^13 (16 residues per thread).
+// NTT-based kernels for N = 2^13.
 #include "cores.cuh"
 
+#ifndef BCN_R13
+#define BCN_R13 16  // residues per thread
+#endif
+
 namespace bcn {
-const CoreFns *core_fns_13() { return CoreImpl<13, 16>::fns(); }
+const CoreFns *core_fns_13() { return CoreImpl<13, BCN_R13>::fns(); }
 }  // namespace bcn

@@ -50,11 +50,13 @@ inline KsDev ks_dev(const bcn_ctx *c) {
 struct CoreFns {
     // in-place NTT of n_limbs limbs; limb l uses prime prime_of(pm, l)
     bcn_status (*ntt)(const bcn_ctx *, uint32_t *data, size_t n_limbs, PrimeMap pm, bool inverse, cudaStream_t);
-    // Y [C][2][n][N] -> D [C][3][n][N] (tensor square, coefficient form)
-    bcn_status (*square)(const bcn_ctx *, int n, const uint32_t *Y, uint32_t *D, int C, cudaStream_t);
-    // D (d2) -> ACC [C][2][n+K][N] (key-switching sums, coefficient form)
-    bcn_status (*keyswitch)(const bcn_ctx *, int n, const uint32_t *D, const uint32_t *evk, uint32_t *acc, int C,
-                            cudaStream_t);
+    // Y [C][2][n][N] -> D [C][3][n][N] (tensor square, coefficient form) and, if
+    // D2N is not null, d2 in the NTT domain [C][n][N]
+    bcn_status (*square)(const bcn_ctx *, int n, const uint32_t *Y, uint32_t *D, uint32_t *D2N, int C,
+                         cudaStream_t);
+    // D (d2; D2N optional) -> ACC [C][2][n+K][N] (key-switching sums, coefficient form)
+    bcn_status (*keyswitch)(const bcn_ctx *, int n, const uint32_t *D, const uint32_t *D2N, const uint32_t *evk,
+                            uint32_t *acc, int C, cudaStream_t);
     bcn_status (*setup)();
 };
 const CoreFns *core_fns(int logN);  // nullptr if unsupported
@@ -67,6 +69,10 @@ const CoreFns *core_fns_14();
 // intermediates in d [C][3][n][N] and acc [C][2][n+K][N]
 bcn_status square_relin_rescale_chunk(const bcn_ctx *c, int n, const uint32_t *evk, const uint32_t *Y, uint32_t *d,
                                       uint32_t *acc, int C, uint32_t *out, cudaStream_t st);
+// the same with d2 also kept in the NTT domain in d2n [C][n][N] (saves one
+// forward NTT per key-switching target)
+bcn_status square_relin_rescale_chunk2(const bcn_ctx *c, int n, const uint32_t *evk, const uint32_t *Y, uint32_t *d,
+                                       uint32_t *d2n, uint32_t *acc, int C, uint32_t *out, cudaStream_t st);
 
 bcn_status launch_ntt(const bcn_ctx *c, uint32_t *data, size_t n_limbs, const PrimeMap &pm, bool inverse,
                       cudaStream_t st);

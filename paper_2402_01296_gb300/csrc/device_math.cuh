@@ -13,36 +13,40 @@
 
 namespace bcn {
 
+// x - m if x >= m else x, for x < 2m <= 2^32 (one subtraction and one unsigned min)
+__device__ __forceinline__ uint32_t reduce_once(uint32_t x, uint32_t m) { return min(x, x - m); }
+
 __device__ __forceinline__ uint32_t add_mod(uint32_t a, uint32_t b, uint32_t q) {
-    uint32_t s = a + b;  // < 2q < 2^32
-    return s >= q ? s - q : s;
+    return reduce_once(a + b, q);  // a + b < 2q <= 2^32
 }
 
 __device__ __forceinline__ uint32_t sub_mod(uint32_t a, uint32_t b, uint32_t q) {
-    uint32_t d = a - b;
-    return a >= b ? d : d + q;
+    return reduce_once(a + q - b, q);  // a + q - b in (0, 2q)
+}
+
+// a * w mod q up to one q: result in [0, 2q), for any a < 2^32
+__device__ __forceinline__ uint32_t shoup_mul_lazy(uint32_t a, uint32_t w, uint32_t wp, uint32_t q) {
+    return a * w - __umulhi(a, wp) * q;
 }
 
 // a * w mod q for any a < 2^32, w < q, wp = floor(w * 2^32 / q)
 __device__ __forceinline__ uint32_t shoup_mul(uint32_t a, uint32_t w, uint32_t wp, uint32_t q) {
-    uint32_t hi = __umulhi(a, wp);
-    uint32_t r = a * w - hi * q;  // in [0, 2q)
-    return r >= q ? r - q : r;
+    return reduce_once(shoup_mul_lazy(a, w, wp, q), q);
 }
 
-// a * b * 2^-32 mod q for a, b < q (< 2^31)
+// a * b * 2^-32 mod q for a < 4q, b < q, q < 2^30; or a, b < q < 2^31
 __device__ __forceinline__ uint32_t mont_mul(uint32_t a, uint32_t b, uint32_t q, uint32_t qneg_inv) {
     uint64_t t = (uint64_t)a * b;
     uint32_t m = (uint32_t)t * qneg_inv;
     uint32_t u = (uint32_t)((t + (uint64_t)m * q) >> 32);  // < 2q
-    return u >= q ? u - q : u;
+    return reduce_once(u, q);
 }
 
 // x mod q for any x < 2^64 (mu = floor(2^64 / q))
 __device__ __forceinline__ uint32_t barrett_reduce64(uint64_t x, uint32_t q, uint64_t mu) {
     uint64_t qh = __umul64hi(x, mu);
-    uint64_t r = x - qh * q;  // in [0, 2q)
-    return (uint32_t)(r >= q ? r - q : r);
+    uint32_t r = (uint32_t)(x - qh * q);  // in [0, 2q)
+    return reduce_once(r, q);
 }
 
 }  // namespace bcn

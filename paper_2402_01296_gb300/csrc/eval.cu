@@ -31,35 +31,60 @@ __global__ void __launch_bounds__(256) k_mac_grouped(const uint32_t *__restrict_
                                                      const int32_t *__restrict__ gout, const uint32_t *__restrict__ pt,
                                                      int K, int n_go, int level, int N,
                                                      const PrimeConst *__restrict__ pc) {
+    constexpr int OTP = (OT + 3) / 4 * 4;  // weight row padded to whole int4 loads
     extern __shared__ __align__(16) unsigned char smraw[];
-    int32_t *sidx = reinterpret_cast<int32_t *>(smraw);
-    int8_t *sw = reinterpret_cast<int8_t *>(smraw + (size_t)K * 4);
+    int32_t *sw = reinterpret_cast<int32_t *>(smraw);               // [K][OTP] weights (0 for padding taps)
+    int32_t *sidx = reinterpret_cast<int32_t *>(smraw) + (size_t)K * OTP;  // [K] input index (0 for padding)
     const int tiles = (n_go + OT - 1) / OT;
     const int g = blockIdx.y / tiles, o0 = (blockIdx.y % tiles) * OT;
     const int no = min(OT, n_go - o0);
-    for (int t = threadIdx.x; t < K; t += blockDim.x) sidx[t] = gidx[(size_t)g * K + t];
-    for (int x = threadIdx.x; x < OT * K; x += blockDim.x) {
-        const int o = x / K, t = x % K;
-        sw[x] = o < no ? gw[((size_t)g * n_go + o0 + o) * K + t] : (int8_t)0;
+    for (int t = threadIdx.x; t < K; t += blockDim.x) {
+        const int src = gidx[(size_t)g * K + t];
+        sidx[t] = src < 0 ? 0 : src;
+    }
+    for (int x = threadIdx.x; x < OTP * K; x += blockDim.x) {
+        const int t = x / OTP, o = x % OTP;
+        const bool live = o < no && gidx[(size_t)g * K + t] >= 0;
+        sw[x] = live ? (int32_t)gw[((size_t)g * n_go + o0 + o) * K + t] : 0;
     }
     __syncthreads();
     const size_t cols = (size_t)2 * level * N;
     const size_t col = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
     if (col >= cols) return;
+    // residues are below 2^31, so signed 32 x 32 -> 64 products are exact
     long long acc[OT][4];
 #pragma unroll
     for (int o = 0; o < OT; o++) acc[o][0] = acc[o][1] = acc[o][2] = acc[o][3] = 0;
-    for (int t = 0; t < K; t++) {
-        const int src = sidx[t];
-        if (src < 0) continue;
-        const uint4 x = __ldg(reinterpret_cast<const uint4 *>(in + (size_t)src * cols + col));
+    const uint32_t *base = in + col;
+    constexpr int U = 4;  // taps in flight per thread
+    int t = 0;
+    for (; t + U <= K; t += U) {
+        uint4 x[U];
+#pragma unroll
+        for (int k = 0; k < U; k++) x[k] = __ldg(reinterpret_cast<const uint4 *>(base + (size_t)sidx[t + k] * cols));
+#pragma unroll
+        for (int k = 0; k < U; k++) {
+            const int32_t *wr = sw + (t + k) * OTP;
+#pragma unroll
+            for (int o = 0; o < OT; o++) {
+                const long long w = wr[o];
+                acc[o][0] += w * (int)x[k].x;
+                acc[o][1] += w * (int)x[k].y;
+                acc[o][2] += w * (int)x[k].z;
+                acc[o][3] += w * (int)x[k].w;
+            }
+        }
+    }
+    for (; t < K; t++) {
+        const uint4 x = __ldg(reinterpret_cast<const uint4 *>(base + (size_t)sidx[t] * cols));
+        const int32_t *wr = sw + t * OTP;
 #pragma unroll
         for (int o = 0; o < OT; o++) {
-            const long long w = sw[o * K + t];
-            acc[o][0] += w * x.x;
-            acc[o][1] += w * x.y;
-            acc[o][2] += w * x.z;
-            acc[o][3] += w * x.w;
+            const long long w = wr[o];
+            acc[o][0] += w * (int)x.x;
+            acc[o][1] += w * (int)x.y;
+            acc[o][2] += w * (int)x.z;
+            acc[o][3] += w * (int)x.w;
         }
     }
     const int poly = (int)(col / ((size_t)level * N)), i = (int)((col / N) % level);
@@ -151,14 +176,17 @@ __global__ void __launch_bounds__(256) k_rescale(const uint32_t *__restrict__ in
     }
 }
 
-// x -> x * R mod q over rows of N words; row r uses prime prime_of(pm, r)
-__global__ void k_to_mont(uint32_t *__restrict__ data, int N, PrimeMap pm, const PrimeConst *__restrict__ pc) {
+// x -> x * R * N^{-1} mod q over rows of N words; row r uses prime prime_of(pm, r).
+// The evaluation key in this form makes one Montgomery product per digit give
+// the key product already divided by N, which the key-switching kernel's
+// inverse NTT then needs no longer apply.
+__global__ void k_key_form(uint32_t *__restrict__ data, int N, PrimeMap pm, const PrimeConst *__restrict__ pc) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= N) return;
     const int row = blockIdx.y;
     const PrimeConst &P = pc[prime_of(pm, row)];
     uint32_t *x = data + (size_t)row * N + k;
-    *x = shoup_mul(*x, P.r_mod, P.r_shoup, P.q);
+    *x = shoup_mul(*x, P.rn, P.rn_shoup, P.q);
 }
 
 // ------------------------------------------------------------- host helpers
@@ -211,12 +239,13 @@ struct Timed {
     }
 };
 
-constexpr int kMaxMacTaps = 8192;
+constexpr int kMaxMacTaps = 4096;
 
-// key-switching chunk buffers per ciphertext at level n (words): D and ACC
-static size_t chunk_words(const bcn_ctx *c, int n) { return (3 * (size_t)n + 2 * (size_t)(n + c->K)) * c->N; }
+// key-switching chunk buffers per ciphertext at level n (words): D, D2N and ACC
+static size_t chunk_words(const bcn_ctx *c, int n) { return (4 * (size_t)n + 2 * (size_t)(n + c->K)) * c->N; }
 static size_t chunk_bytes(const bcn_ctx *c, int n, int chunk) {
-    return align_up(3 * (size_t)n * c->N * 4 * chunk) + align_up(2 * (size_t)(n + c->K) * c->N * 4 * chunk);
+    return align_up(3 * (size_t)n * c->N * 4 * chunk) + align_up((size_t)n * c->N * 4 * chunk) +
+           align_up(2 * (size_t)(n + c->K) * c->N * 4 * chunk);
 }
 static int default_chunk(const bcn_ctx *c, int n, int n_ct) {
     const size_t target = 1ull << 30;
@@ -225,12 +254,14 @@ static int default_chunk(const bcn_ctx *c, int n, int n_ct) {
 }
 
 struct ChunkBufs {
-    uint32_t *d, *acc;
+    uint32_t *d, *acc, *d2n;
 };
 static ChunkBufs carve_chunk(const bcn_ctx *c, int n, int chunk, char *ws) {
     ChunkBufs b;
+    const size_t d_b = align_up(3 * (size_t)n * c->N * 4 * chunk), d2n_b = align_up((size_t)n * c->N * 4 * chunk);
     b.d = reinterpret_cast<uint32_t *>(ws);
-    b.acc = reinterpret_cast<uint32_t *>(ws + align_up(3 * (size_t)n * c->N * 4 * chunk));
+    b.d2n = reinterpret_cast<uint32_t *>(ws + d_b);
+    b.acc = reinterpret_cast<uint32_t *>(ws + d_b + d2n_b);
     return b;
 }
 
@@ -238,12 +269,12 @@ static bcn_status launch_mac(const bcn_ctx *c, int level, int K, int n_groups, i
                              const int8_t *gw, const int32_t *gout, const uint32_t *in, const uint32_t *pt,
                              uint32_t *out, cudaStream_t st, Profiler *prof = nullptr, double alg_bytes = 0) {
     if (n_groups <= 0 || n_go <= 0) return BCN_OK;
-    if (K > kMaxMacTaps) return fail(BCN_E_INVAL, "MAC fan-in above 8192");
+    if (K > kMaxMacTaps) return fail(BCN_E_INVAL, "MAC fan-in above 4096");
     const int N = c->N;
     const int OT = std::min(8, n_go);
     const int tiles = (n_go + OT - 1) / OT;
     const size_t cols = (size_t)2 * level * N;
-    const size_t smem = (size_t)K * 4 + (size_t)OT * K;
+    const size_t smem = (size_t)K * 4 + (size_t)((OT + 3) / 4 * 4) * K * 4;
     if ((long long)n_groups * tiles > 65535) return fail(BCN_E_INVAL, "MAC layer with more than 65535 output tiles");
     Timed tm(prof, st, BCN_KERNEL_MAC, alg_bytes);
     dim3 grid((unsigned)((cols / 4 + 255) / 256), (unsigned)(n_groups * tiles));
@@ -266,11 +297,11 @@ static bcn_status square_chunk(const bcn_ctx *c, int n, const uint32_t *evk, con
     if (!f) return fail(BCN_E_INVAL, "unsupported ring degree");
     {
         Timed tm(prof, st, BCN_KERNEL_SQUARE, limb * C * 5 * n);
-        BCN_TRY(f->square(c, n, Y, b.d, C, st));
+        BCN_TRY(f->square(c, n, Y, b.d, b.d2n, C, st));
     }
     {
         Timed tm(prof, st, BCN_KERNEL_KEYSWITCH, limb * ((double)C * (n + 2 * nb) + 2.0 * dnum * nb));
-        BCN_TRY(f->keyswitch(c, n, b.d, evk, b.acc, C, st));
+        BCN_TRY(f->keyswitch(c, n, b.d, b.d2n, evk, b.acc, C, st));
     }
     Timed tm(prof, st, BCN_KERNEL_MODDOWN_RESCALE, limb * C * (2.0 * n + 2.0 * nb + 2.0 * (n - 1)));
     k_moddown_rescale<<<dim3((N + 255) / 256, 2, C), 256, 0, st>>>(b.d, b.acc, out, n, N, ks_dev(c), c->d_pc);
@@ -281,7 +312,12 @@ static bcn_status square_chunk(const bcn_ctx *c, int n, const uint32_t *evk, con
 // memory: d [C][3][n][N], acc [C][2][n+K][N].
 bcn_status square_relin_rescale_chunk(const bcn_ctx *c, int n, const uint32_t *evk, const uint32_t *Y, uint32_t *d,
                                       uint32_t *acc, int C, uint32_t *out, cudaStream_t st) {
-    ChunkBufs b{d, acc};
+    ChunkBufs b{d, acc, nullptr};
+    return square_chunk(c, n, evk, Y, b, C, out, st);
+}
+bcn_status square_relin_rescale_chunk2(const bcn_ctx *c, int n, const uint32_t *evk, const uint32_t *Y, uint32_t *d,
+                                       uint32_t *d2n, uint32_t *acc, int C, uint32_t *out, cudaStream_t st) {
+    ChunkBufs b{d, acc, d2n};
     return square_chunk(c, n, evk, Y, b, C, out, st);
 }
 
@@ -305,7 +341,7 @@ bcn_status device_ctx_init(bcn_ctx *c) {
                           cudaMemcpyHostToDevice) == cudaSuccess;
     if (!ok) return fail(BCN_E_CUDA, "upload of the context tables failed");
     BCN_TRY(cores_setup_all());
-    const int mac_smem = kMaxMacTaps * 4 + 8 * kMaxMacTaps;
+    const int mac_smem = kMaxMacTaps * 4 + 8 * kMaxMacTaps * 4;
 #define BCN_MSETUP(OTV)                                                                                           \
     if (cudaFuncSetAttribute(k_mac_grouped<OTV>, cudaFuncAttributeMaxDynamicSharedMemorySize, mac_smem) !=      \
         cudaSuccess)                                                                                            \
@@ -421,7 +457,7 @@ bcn_status bcn_model_create(bcn_ctx *c, const bcn_layer *layers, int n_layers, b
         } else {
             return cleanup(BCN_E_INVAL, "layer " + std::to_string(l) + ": unknown type");
         }
-        if (p.K > kMaxMacTaps) return cleanup(BCN_E_INVAL, "layer fan-in above 8192");
+        if (p.K > kMaxMacTaps) return cleanup(BCN_E_INVAL, "layer fan-in above 4096");
         if ((long long)p.n_groups * ((p.n_go + 7) / 8) > 65535)
             return cleanup(BCN_E_INVAL, "layer " + std::to_string(l) + ": too many output tiles");
         if (prev_out >= 0 && p.n_in != prev_out)
@@ -518,8 +554,8 @@ bcn_status bcn_evk_prepare(const bcn_ctx *c, const uint32_t *evk, uint32_t *evk_
     const PrimeMap all = data_map(c->L + c->K);
     const size_t rows = (size_t)c->dnum * 2 * (c->L + c->K);
     BCN_TRY(launch_ntt(c, evk_eval, rows, all, false, st));
-    k_to_mont<<<dim3((c->N + 255) / 256, (unsigned)rows), 256, 0, st>>>(evk_eval, c->N, all, c->d_pc);
-    return check_launch("k_to_mont");
+    k_key_form<<<dim3((c->N + 255) / 256, (unsigned)rows), 256, 0, st>>>(evk_eval, c->N, all, c->d_pc);
+    return check_launch("k_key_form");
 }
 
 bcn_status bcn_eval_workspace_bytes(const bcn_model *m, size_t *bytes) {
@@ -718,7 +754,8 @@ bcn_status bcn_op_tensor_square(const bcn_ctx *c, int level, const uint32_t *in,
     if (!f) return fail(BCN_E_INVAL, "unsupported ring degree");
     for (int o0 = 0; o0 < n_ct; o0 += 32768) {
         const int C = std::min(32768, n_ct - o0);
-        BCN_TRY(f->square(c, level, in + (size_t)o0 * 2 * level * N, out + (size_t)o0 * 3 * level * N, C, st));
+        BCN_TRY(f->square(c, level, in + (size_t)o0 * 2 * level * N, out + (size_t)o0 * 3 * level * N, nullptr, C,
+                          st));
     }
     return BCN_OK;
 }

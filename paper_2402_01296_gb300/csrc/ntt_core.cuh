@@ -19,13 +19,18 @@
 // Pass 0 is therefore e = tid + u * T (coalesced loads of natural order) and a
 // full last pass gives each thread R consecutive elements.  Everything that
 // selects a register is a template parameter, so the limb stays in registers.
+//
+// LAZY (only for q < 2^30, so 4q < 2^32): Harvey's lazy butterflies.  The
+// forward transform keeps residues in [0, 4q) (input [0, 4q), output [0, 4q));
+// the inverse keeps them in [0, 2q) (input [0, 2q)) and its final N^{-1}
+// product returns canonical residues.  Otherwise every value stays in [0, q).
 #pragma once
 
 #include "device_math.cuh"
 
 namespace bcn {
 
-template <int LOGN, int R>
+template <int LOGN, int R, bool LAZY = false>
 struct NttCore {
     static constexpr int N = 1 << LOGN;
     static constexpr int T = N / R;
@@ -40,24 +45,45 @@ struct NttCore {
     __host__ __device__ static constexpr int rp_of(int p) { return s1_of(p) - s0_of(p); }
     static constexpr int LAST_RP = rp_of(PASSES - 1);
 
-    // element held in register u during pass P
+    // element held in register u during pass P (the defining formula)
     template <int P>
-    __device__ __forceinline__ static int elem(int u, int tid) {
-        constexpr int rp = rp_of(P), logtmin = LOGN - s1_of(P);
+    __host__ __device__ static constexpr int elem_def(int u, int tid) {
+        const int rp = rp_of(P), logtmin = LOGN - s1_of(P);
         const int g = u >> rp, v = u & ((1 << rp) - 1);
         const int gidx = g * T + tid;
         const int lo = gidx & ((1 << logtmin) - 1), hi = gidx >> logtmin;
         return (hi << (logtmin + rp)) + lo + (v << logtmin);
     }
-    __device__ __forceinline__ static int padded(int e) { return e + (e >> 5); }
+    __host__ __device__ static constexpr int padded(int e) { return e + (e >> 5); }
+    // For every supported (LOGN, R, pass) both maps are linear in the thread:
+    //   elem(u, tid)         = elem(0, tid)         + elem(u, 0)
+    //   padded(elem(u, tid)) = padded(elem(0, tid)) + padded(elem(u, 0))
+    // (checked exhaustively on the host), so a thread needs one base per pass
+    // and every register sits at a constant offset from it.
+    template <int P>
+    __device__ __forceinline__ static int elem(int u, int tid) { return elem_def<P>(0, tid) + elem_def<P>(u, 0); }
+    template <int P>
+    __device__ __forceinline__ static int pad_base(int tid) { return padded(elem_def<P>(0, tid)); }
+    template <int P>
+    __host__ __device__ static constexpr int pad_off(int u) { return padded(elem_def<P>(u, 0)); }
+
+    // Twiddle load that the compiler may not merge with the same load of another
+    // transform in the same kernel (merging keeps whole tables live in registers).
+    __device__ __forceinline__ static uint2 load_tw(const uint2 *p) {
+        uint2 v;
+        asm volatile("ld.global.nc.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+        return v;
+    }
 
     template <int PF, int PT>
     __device__ __forceinline__ static void exchange(uint32_t (&x)[R], uint32_t *sm, int tid) {
+        uint32_t *wf = sm + pad_base<PF>(tid);
 #pragma unroll
-        for (int u = 0; u < R; u++) sm[padded(elem<PF>(u, tid))] = x[u];
+        for (int u = 0; u < R; u++) wf[pad_off<PF>(u)] = x[u];
         __syncthreads();
+        const uint32_t *rt = sm + pad_base<PT>(tid);
 #pragma unroll
-        for (int u = 0; u < R; u++) x[u] = sm[padded(elem<PT>(u, tid))];
+        for (int u = 0; u < R; u++) x[u] = rt[pad_off<PT>(u)];
         __syncthreads();
     }
 
@@ -68,13 +94,20 @@ struct NttCore {
         constexpr int rp = rp_of(P), s = s0_of(P) + KS, d = 1 << (rp - 1 - KS);
 #pragma unroll
         for (int b = 0; b < (1 << KS); b++) {
-            const uint2 W = __ldg(&tw[(1 << s) + (hi << KS) + b]);
+            const uint2 W = load_tw(&tw[(1 << s) + (hi << KS) + b]);
 #pragma unroll
             for (int w = 0; w < d; w++) {
                 const int u = (g << rp) + b * 2 * d + w;
-                const uint32_t U = x[u], V = shoup_mul(x[u + d], W.x, W.y, q);
-                x[u] = add_mod(U, V, q);
-                x[u + d] = sub_mod(U, V, q);
+                if constexpr (LAZY) {
+                    const uint32_t q2 = 2 * q;
+                    const uint32_t U = reduce_once(x[u], q2), V = shoup_mul_lazy(x[u + d], W.x, W.y, q);
+                    x[u] = U + V;           // [0, 4q)
+                    x[u + d] = U - V + q2;  // [0, 4q)
+                } else {
+                    const uint32_t U = x[u], V = shoup_mul(x[u + d], W.x, W.y, q);
+                    x[u] = add_mod(U, V, q);
+                    x[u + d] = sub_mod(U, V, q);
+                }
             }
         }
         if constexpr (KS + 1 < rp) stage_fwd<P, KS + 1>(x, g, hi, q, tw);
@@ -87,13 +120,19 @@ struct NttCore {
         constexpr int rp = rp_of(P), s = s0_of(P) + KS, d = 1 << (rp - 1 - KS);
 #pragma unroll
         for (int b = 0; b < (1 << KS); b++) {
-            const uint2 W = __ldg(&tw[(1 << s) + (hi << KS) + b]);
+            const uint2 W = load_tw(&tw[(1 << s) + (hi << KS) + b]);
 #pragma unroll
             for (int w = 0; w < d; w++) {
                 const int u = (g << rp) + b * 2 * d + w;
                 const uint32_t U = x[u], V = x[u + d];
-                x[u] = add_mod(U, V, q);
-                x[u + d] = shoup_mul(sub_mod(U, V, q), W.x, W.y, q);
+                if constexpr (LAZY) {
+                    const uint32_t q2 = 2 * q;
+                    x[u] = reduce_once(U + V, q2);                             // [0, 2q)
+                    x[u + d] = shoup_mul_lazy(U - V + q2, W.x, W.y, q);        // [0, 2q)
+                } else {
+                    x[u] = add_mod(U, V, q);
+                    x[u + d] = shoup_mul(sub_mod(U, V, q), W.x, W.y, q);
+                }
             }
         }
         if constexpr (KS > 0) stage_inv<P, KS - 1>(x, g, hi, q, tw);
@@ -149,6 +188,16 @@ struct NttCore {
         inverse_from<PASSES - 1>(x, sm, tid, q, tw);
 #pragma unroll
         for (int u = 0; u < R; u++) x[u] = shoup_mul(x[u], ninv, ninv_shoup, q);
+    }
+    // the same without the N^{-1} factor (callers that folded it into their
+    // inputs); the result is canonical
+    __device__ __forceinline__ static void inverse_unscaled(uint32_t (&x)[R], uint32_t *sm, int tid, uint32_t q,
+                                                            const uint2 *__restrict__ tw) {
+        inverse_from<PASSES - 1>(x, sm, tid, q, tw);
+        if constexpr (LAZY) {
+#pragma unroll
+            for (int u = 0; u < R; u++) x[u] = reduce_once(x[u], q);
+        }
     }
 
     // natural-order limb <-> pass-0 distribution (coalesced)
