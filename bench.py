@@ -44,7 +44,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default=WORKLOAD, choices=list(workloads.CONFIGS))
+    ap.add_argument("--workload", default=WORKLOAD, choices=list(workloads.CONFIGS) + ["uneven64", "serve"])
+    ap.add_argument("--rates", default="50,100,200,500,1000,2000", help="serve: request rates (req/s)")
+    ap.add_argument("--serve-seconds", type=float, default=5.0, help="serve: seconds of arrivals per rate")
+    ap.add_argument("--lanes", type=int, default=8, help="serve: lanes (concurrent requests)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-budget-s", type=float, default=150.0, help="wall budget of the reference arm")
     return ap.parse_args()
@@ -113,6 +116,21 @@ class ClockSampler:
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def replica_summary(mean_ms: float, images_per_rank: int, dist=None, device="cpu"):
+    """Replicas only: every rank evaluated its own batch.  The job takes as long
+    as the slowest rank, so the whole-job throughput is world * images / max ms.
+    Returns (images/s, max ms)."""
+    world = 1
+    if dist is not None and dist.is_initialized():
+        import torch
+
+        world = dist.get_world_size()
+        t = torch.tensor([mean_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        mean_ms = float(t.item())
+    return world * images_per_rank / (mean_ms / 1e3), mean_ms
 
 
 def measured_peaks():
@@ -276,11 +294,7 @@ def run_ours(args, cfg, rank, world, local_rank):
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     prof = model.profile_read()
     model.profile_enable(False)
-    mean_ms = statistics.mean(step_ms)
-    if dist:
-        t = torch.tensor([mean_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        mean_ms = float(t.item())
+    value, mean_ms = replica_summary(statistics.mean(step_ms), cfg["batch"], dist, dev)
 
     # decrypt once to make sure the timed result is the real one
     res = bcn.to_host_u32(out)
@@ -302,17 +316,12 @@ def run_ours(args, cfg, rank, world, local_rank):
         t0 = time.perf_counter()
         model.eval_host(evk_eval, as_u32(cts_h), [as_u32(p) for p in pts_h], as_u32(out_h), ws_h)
         e2e_s.append(time.perf_counter() - t0)
-    e2e_mean = statistics.mean(e2e_s)
-    if dist:
-        t = torch.tensor([e2e_mean], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_mean = float(t.item())
+    e2e_value, e2e_ms = replica_summary(statistics.mean(e2e_s) * 1e3, cfg["batch"], dist, dev)
     assert np.array_equal(as_u32(out_h), res), "host-buffer evaluation differs from the device evaluation"
     h2d = cts.nbytes + sum(p.nbytes for p in pts)
     d2h = out_h.numel() * 4
 
     B = cfg["batch"]
-    value = world * B / (mean_ms / 1e3)
     launches = sum(v[1] for v in prof.values())
     # roofline of the dominant kernel (largest device time)
     dom = max(prof, key=lambda k: prof[k][0])
@@ -344,8 +353,8 @@ def run_ours(args, cfg, rank, world, local_rank):
         "data": "synthetic", "config": {**config_desc(cfg), "parallelism": f"replicas x{world}",
                                         "l2": "flushed (512 MiB write) between timed steps, outside the events"},
         "p50_ms": statistics.median(step_ms), "p99_ms": float(np.percentile(step_ms, 99)),
-        "e2e": {"value": world * B / e2e_mean, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_mean * 1e3},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms},
         "gpu_launches": int(launches),
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src},
@@ -361,11 +370,205 @@ def run_ours(args, cfg, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------
+# the batched uneven workload (64 evaluations, one graph)
+# ---------------------------------------------------------------------------
+def _dev_residues(torch, primes, lead, N, gen, device):
+    """uniform residues [*lead][len(primes)][N] generated on the device"""
+    t = torch.empty(tuple(lead) + (len(primes), N), dtype=torch.int32, device=device)
+    for i, q in enumerate(primes):
+        t[..., i, :] = torch.randint(0, int(q), tuple(lead) + (N,), generator=gen, device=device, dtype=torch.int32)
+    return t
+
+
+def run_uneven(args, rank, world, local_rank):
+    import torch
+
+    from paper_2402_01296_gb300 import bcn, tuner
+
+    device = local_rank
+    torch.cuda.set_device(device)
+    dev = f"cuda:{device}"
+    cfgs = workloads.uneven_batch(64)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(workloads.SEED_ENC + 1000 * rank)
+    # contexts and keys per ring degree; alpha tuned where the chain allows a choice
+    ctxs, evks, alpha_note = {}, {}, {}
+    for cfg in cfgs:
+        if cfg["log_n"] in ctxs:
+            continue
+        alphas = list(range(1, cfg["n_special"] + 1))
+        best_alpha = cfg["alpha"]
+        if len(alphas) > 1:
+            probe = [c for c in cfgs if c["log_n"] == cfg["log_n"]][0]
+
+            def make_eval(a, probe=probe):
+                cx = bcn.Context(probe["log_n"], probe["n_data"], probe["n_special"], a, device)
+                _, ek = cx.keygen(workloads.SEED_KEYS)
+                ev = cx.evk_prepare(bcn.to_device(ek, dev))
+                wq = [bcn.quantize(w) for w in workloads.cipher_weights(probe)]
+                m = bcn.Model(cx, probe["cipher"], [x for x, _ in wq], [y for _, y in wq])
+                c_ = _dev_residues(torch, cx.q, (m.n_in, 2), cx.N, gen, dev)
+                p_ = [_dev_residues(torch, cx.q[:sh[1]], (sh[0],), cx.N, gen, dev) for sh in m.pt_shapes()]
+                o_ = torch.empty(m.out_shape(), dtype=torch.int32, device=dev)
+                ws_ = m.alloc_workspace()
+                keep = (cx, ev, m, c_, p_, o_, ws_)
+                return lambda: keep[2].eval(keep[1], keep[3], keep[4], keep[5], keep[6])
+
+            best_alpha, _, res = tuner.tune_alpha(make_eval, alphas)
+            alpha_note[cfg["log_n"]] = {str(a): round(v, 3) for a, v in res.items()}
+            torch.cuda.empty_cache()
+        cx = bcn.Context(cfg["log_n"], cfg["n_data"], cfg["n_special"], best_alpha, device)
+        _, ek = cx.keygen(workloads.SEED_KEYS)
+        ctxs[cfg["log_n"]] = cx
+        evks[cfg["log_n"]] = cx.evk_prepare(bcn.to_device(ek, dev))
+    items, images = [], 0
+    for cfg in cfgs:
+        cx = ctxs[cfg["log_n"]]
+        wq = [bcn.quantize(w) for w in workloads.cipher_weights(cfg)]
+        m = bcn.Model(cx, cfg["cipher"], [x for x, _ in wq], [y for _, y in wq])
+        cts = _dev_residues(torch, cx.q, (m.n_in, 2), cx.N, gen, dev)
+        pts = [_dev_residues(torch, cx.q[:sh[1]], (sh[0],), cx.N, gen, dev) for sh in m.pt_shapes()]
+        out = torch.empty(m.out_shape(), dtype=torch.int32, device=dev)
+        items.append((m, evks[cfg["log_n"]], cts, pts, out))
+        images += cfg["batch"]
+    torch.cuda.synchronize()
+    free, total = torch.cuda.mem_get_info()
+    budget = max(0, free - (8 << 30))
+    lanes, _, lane_res = tuner.tune_lanes(items, candidates=(1, 2, 4, 8), budget_bytes=budget)
+    batch = bcn.Batch(items, lanes)
+    for _ in range(max(1, args.warmup)):
+        batch.launch()
+    torch.cuda.synchronize()
+    K = args.steps
+    st = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    en = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    clocks = ClockSampler(device)
+    clocks.start()
+    for i in range(K):
+        st[i].record()
+        batch.launch()
+        en[i].record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = [a.elapsed_time(b) for a, b in zip(st, en)]
+    batch.close()
+    del batch
+    torch.cuda.empty_cache()
+    # the plain per-request path: the same 64 evaluations one after another, no graph
+    big = max((it[0] for it in items), key=lambda m: m.workspace_bytes())
+    ws = big.alloc_workspace()
+    plain_ms = []
+    for rep in range(2):
+        s0, e0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        s0.record()
+        for (m, evk, cts, pts, out) in items:
+            m.eval(evk, cts, pts, out, ws)
+        e0.record()
+        torch.cuda.synchronize()
+        plain_ms.append(s0.elapsed_time(e0))
+    value, mean_ms = replica_summary(statistics.mean(ms), images, None)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": max(1, args.warmup),
+        "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic (uniform residues as ciphertexts and encoded features)",
+        "config": {"workload": "uneven64: 64 evaluations, N in {4096, 8192, 16384}, sensitive fraction 10-60%, "
+                               "slot occupancy 25-100%, one CUDA graph",
+                   "images_per_step": images, "lanes": lanes,
+                   "counts": {str(k): sum(1 for c in cfgs if c["log_n"] == k) for k in (12, 13, 14)}},
+        "p50_ms": statistics.median(ms), "p99_ms": float(np.percentile(ms, 99)),
+        "tuning": {"lanes_ms": {str(k): round(v, 3) for k, v in lane_res.items()}, "alpha_ms": alpha_note},
+        "plain_sequential": {"value": images / (min(plain_ms) / 1e3), "ms_per_step": min(plain_ms)},
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# serving: Poisson arrivals, continuous batching over lanes, 16 clients
+# ---------------------------------------------------------------------------
+def run_serve(args, rank, world, local_rank):
+    import torch
+
+    from paper_2402_01296_gb300 import bcn, serve
+
+    device = local_rank
+    torch.cuda.set_device(device)
+    dev = f"cuda:{device}"
+    n_clients, budget = 16, 120 << 30
+    models, images = {}, {}
+    for name in ("cnn3_small", "cryptonets"):
+        cfg = workloads.get_config(name)
+        ctx = bcn.Context.from_config(cfg, device)
+        wq = [bcn.quantize(w) for w in workloads.cipher_weights(cfg)]
+        model = bcn.Model(ctx, cfg["cipher"], [a for a, _ in wq], [s_ for _, s_ in wq])
+        evks = [ctx.evk_prepare(bcn.to_device(ctx.keygen(1000 + c)[1], dev)) for c in range(n_clients)]
+        models[name] = (model, evks)
+        images[name] = cfg["batch"]
+    # one seeded payload per (model, client), page-locked on the host
+    g = np.random.default_rng(workloads.SEED_ENC)
+    payload = {}
+    for name, (model, _) in models.items():
+        ctx = model.ctx
+        for c in range(n_clients):
+            def res(primes, lead):
+                a = np.empty(tuple(lead) + (len(primes), ctx.N), dtype=np.uint32)
+                for i, q in enumerate(primes):
+                    a[..., i, :] = g.integers(0, q, size=tuple(lead) + (ctx.N,), dtype=np.uint32)
+                t = torch.from_numpy(a.view(np.int32)).pin_memory()
+                return t.numpy().view(np.uint32)
+            payload[(name, c)] = (res(ctx.q, (model.n_in, 2)),
+                                  [res(ctx.q[:sh[1]], (sh[0],)) for sh in model.pt_shapes()])
+    srv = serve.Server(models, lanes=args.lanes, budget_bytes=budget, device=device)
+    rates = [float(r) for r in args.rates.split(",")]
+    results = []
+    for rate in rates:
+        arr = serve.poisson_arrivals(rate, args.serve_seconds, seed=int(rate))
+        gg = np.random.default_rng(int(rate) + 1)
+        def make():
+            out = []
+            for i, t in enumerate(arr):
+                name = "cnn3_small" if gg.random() < 0.7 else "cryptonets"
+                c = int(gg.integers(0, n_clients))
+                cts, pts = payload[(name, c)]
+                out.append(serve.Request(rid=i, client=c, model=name, arrival=float(t), cts=cts, pts=pts))
+            return out
+        reqs = make()
+        srv.run(reqs[: min(20, len(reqs))])  # warm-up
+        torch.cuda.synchronize()
+        clocks = ClockSampler(device)
+        clocks.start()
+        done = srv.run(reqs)
+        clk = clocks.stop()
+        st = serve.latency_stats(done, images)
+        gg = np.random.default_rng(int(rate) + 1)
+        plain = serve.latency_stats(serve.run_plain(models, make(), device), images)
+        results.append({"rate_req_per_s": rate, "served": st, "plain": plain, "clocks": clk})
+    best = max(r["served"]["throughput_inferences_per_s"] for r in results)
+    line = {
+        "metric": METRIC, "value": best, "unit": UNIT, "n_gpus": world, "steps": len(rates), "warmup": 1,
+        "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic (uniform residues as request ciphertexts and encoded features)",
+        "config": {"workload": "serve: Poisson arrivals, 70% cnn3_small (N=4096, 2048 images) / 30% cryptonets "
+                               "(N=8192, 4096 images), 16 clients with resident keys, 120 GiB budget",
+                   "lanes": len(srv.lanes), "seconds_per_rate": args.serve_seconds},
+        "rates": results,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.workload == "uneven64":
+        return run_uneven(args, rank, world, local_rank)
+    if args.workload == "serve":
+        return run_serve(args, rank, world, local_rank)
     cfg = workloads.get_config(args.workload)
     if args.impl == "reference":
         run_reference(args, cfg, rank, world)

@@ -244,6 +244,40 @@ bcn_status bcn_eval_host(const bcn_model *m, const uint32_t *evk_eval_dev, const
                          const uint32_t *const *pts_host, uint32_t *out_host, void *workspace_dev,
                          size_t workspace_bytes, void *cuda_stream);
 
+/* ------------------------------------------------ batched evaluation (device) */
+/* Many evaluations of different models (ring degrees, segment sizes) replayed
+ * as one CUDA graph: items are spread over `lanes` streams by the longest-
+ * processing-time rule on bcn_model_cost, each lane evaluates its items in
+ * turn on its own workspace slice, the lanes run concurrently.  This is the
+ * batched form of the ciphertext-branch evaluation (one launch for all items);
+ * every item's output equals that of bcn_eval on the same inputs.  All
+ * pointers are device memory on one device except `pts`, a host array of
+ * device pointers (copied at creation). */
+typedef struct bcn_batch bcn_batch;
+typedef struct {
+    const bcn_model *model;
+    const uint32_t *evk_eval;     /* from bcn_evk_prepare on the model's ctx */
+    const uint32_t *cts;          /* [n_in][2][L][N] */
+    const uint32_t *const *pts;   /* one per add layer, as for bcn_eval */
+    uint32_t *out;                /* [n_out][2][out_level][N] */
+} bcn_batch_item;
+
+/* workspace bytes the batch needs with this many lanes (sum over lanes of the
+ * largest bcn_eval_workspace_bytes among the lane's items) */
+bcn_status bcn_batch_plan(const bcn_batch_item *items, int n_items, int lanes, size_t *workspace_bytes);
+/* Capture the launch sequence into a graph (the items' device must be
+ * current; the workspace and every item buffer are baked into the graph). */
+bcn_status bcn_batch_create(const bcn_batch_item *items, int n_items, int lanes, void *workspace_dev,
+                            size_t workspace_bytes, bcn_batch **out);
+/* one graph launch on `cuda_stream` (asynchronous) */
+bcn_status bcn_batch_launch(bcn_batch *b, void *cuda_stream);
+/* lane of every item, [n_items] */
+bcn_status bcn_batch_lanes(const bcn_batch *b, int *lane_of_item);
+bcn_status bcn_batch_destroy(bcn_batch *b);
+/* the analytic cost the lane assignment uses: MAC products plus about four
+ * products per NTT butterfly of the square layers */
+bcn_status bcn_model_cost(const bcn_model *m, double *cost);
+
 /* ------------------------------------------------- kernel timing (device) */
 /* Classes of the kernels bcn_eval launches. */
 typedef enum {

@@ -47,6 +47,10 @@ class _ModelInfo(ctypes.Structure):
     _fields_ = [("n_layers", _I), ("n_in", _I), ("n_out", _I), ("out_level", _I), ("n_add", _I)]
 
 
+class _BatchItem(ctypes.Structure):
+    _fields_ = [("model", _P), ("evk_eval", _P), ("cts", _P), ("pts", _P), ("out", _P)]
+
+
 class _PlainStage(ctypes.Structure):
     _fields_ = [("op", _I), ("cin", _I), ("cout", _I), ("k", _I), ("stride", _I), ("pad", _I), ("relu", _I),
                 ("hc", _I), ("wc", _I), ("ch_c", _I), ("n_out", _I), ("weights", _P)]
@@ -82,6 +86,12 @@ _SIGS = {
     "bcn_eval": (_I, [_P, _P, _P, _P, _P, _P, _SZ, _P]),
     "bcn_eval_host_workspace_bytes": (_I, [_P, ctypes.POINTER(_SZ)]),
     "bcn_eval_host": (_I, [_P, _P, _P, _P, _P, _P, _SZ, _P]),
+    "bcn_batch_plan": (_I, [_P, _I, _I, ctypes.POINTER(_SZ)]),
+    "bcn_batch_create": (_I, [_P, _I, _I, _P, _SZ, ctypes.POINTER(_P)]),
+    "bcn_batch_launch": (_I, [_P, _P]),
+    "bcn_batch_lanes": (_I, [_P, _P]),
+    "bcn_batch_destroy": (_I, [_P]),
+    "bcn_model_cost": (_I, [_P, ctypes.POINTER(_D)]),
     "bcn_profile_enable": (_I, [_P, _I]),
     "bcn_profile_read": (_I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D)]),
     "bcn_op_ntt": (_I, [_P, _P, _I, _I, _I, _P]),
@@ -429,6 +439,76 @@ class Model:
         _check(lib().bcn_eval_host(self._h, _dev_ptr(evk_eval, self.ctx.evk_words()), cts_host.ctypes.data,
                                    ctypes.cast(arr, _P), out_host.ctypes.data, workspace.data_ptr(),
                                    workspace.numel() * workspace.element_size(), _stream(stream)), "bcn_eval_host")
+
+
+class Batch:
+    """bcn_batch: many evaluations replayed as one CUDA graph over `lanes` streams.
+
+    items: list of (model, evk_eval, cts_dev, [pts_dev...], out_dev)."""
+
+    def __init__(self, items, lanes: int, workspace=None):
+        self._keep = items
+        n = len(items)
+        arr = (_BatchItem * n)()
+        self._pts_arrays = []
+        for a, (model, evk, cts, pts, out) in zip(arr, items):
+            pa = (_P * max(1, len(pts)))(*[_dev_ptr(p) for p in pts])
+            self._pts_arrays.append(pa)
+            a.model = model._h
+            a.evk_eval = _dev_ptr(evk, model.ctx.evk_words())
+            a.cts = _dev_ptr(cts, model.n_in * 2 * model.ctx.L * model.ctx.N)
+            a.pts = ctypes.cast(pa, _P)
+            a.out = _dev_ptr(out, int(np.prod(model.out_shape())))
+        self._arr = arr
+        self.workspace_bytes = Batch.plan(arr, n, lanes)
+        if workspace is None:
+            import torch
+
+            dev = items[0][0].ctx.device
+            workspace = torch.empty(max(1, (self.workspace_bytes + 3) // 4), dtype=torch.int32, device=f"cuda:{dev}")
+        self.workspace = workspace
+        h = _P()
+        _check(lib().bcn_batch_create(ctypes.cast(arr, _P), n, lanes, workspace.data_ptr(),
+                                      workspace.numel() * workspace.element_size(), ctypes.byref(h)),
+               "bcn_batch_create")
+        self._h = h
+        lanes_of = np.zeros(n, dtype=np.int32)
+        _check(lib().bcn_batch_lanes(self._h, _np_ptr(lanes_of, np.int32)), "bcn_batch_lanes")
+        self.lane_of_item = lanes_of.tolist()
+
+    @staticmethod
+    def plan(arr, n, lanes) -> int:
+        b = _SZ()
+        _check(lib().bcn_batch_plan(ctypes.cast(arr, _P), n, lanes, ctypes.byref(b)), "bcn_batch_plan")
+        return b.value
+
+    @staticmethod
+    def plan_items(items, lanes: int) -> int:
+        arr = (_BatchItem * len(items))()
+        for a, (model, evk, cts, pts, out) in zip(arr, items):
+            a.model = model._h
+            a.evk_eval, a.cts, a.out = _dev_ptr(evk), _dev_ptr(cts), _dev_ptr(out)
+        return Batch.plan(arr, len(items), lanes)
+
+    def launch(self, stream=None):
+        _check(lib().bcn_batch_launch(self._h, _stream(stream)), "bcn_batch_launch")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().bcn_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def model_cost(model: "Model") -> float:
+    c = _D()
+    _check(lib().bcn_model_cost(model._h, ctypes.byref(c)), "bcn_model_cost")
+    return c.value
 
 
 PLAIN_OPS = {"conv": 0, "avgpool2": 1, "tap_crop_crot": 2, "tap_fc": 3}

@@ -22,21 +22,24 @@ namespace bcn {
 // outputs that read the same taps (a conv position with all its output
 // channels; a whole dense layer); each thread keeps OT outputs x 4 columns of
 // signed 64-bit sums, so every input word it loads serves OT outputs.
-//   out[gout[g][o]][col] = sum_t gw[g][o][t] * in[gidx[g][t]][col]  (+ pt, poly 0)
+//   out[store(g, o)][col] = sum_t gw[g][o][t] * in[gidx[g][t]][col]  (+ pt[gout[g][o]], poly 0)
+// store(g, o) is the output's natural (channel, row, column) index gout[g][o]
+// when store_natural, else its group-major position (g - g_base) * n_go + o
+// (the order kept between layers, so a chunk of outputs is a run of groups).
 // Columns run over the (poly, limb, coefficient) words of a ciphertext.
-// grid (ceil(2*level*N/4/256), n_groups * ceil(n_go/OT)), 256 threads.
+// grid (ceil(2*level*N/4/256), groups in this launch * ceil(n_go/OT)), 256 threads.
 template <int OT>
 __global__ void __launch_bounds__(256) k_mac_grouped(const uint32_t *__restrict__ in, uint32_t *__restrict__ out,
                                                      const int32_t *__restrict__ gidx, const int8_t *__restrict__ gw,
                                                      const int32_t *__restrict__ gout, const uint32_t *__restrict__ pt,
-                                                     int K, int n_go, int level, int N,
-                                                     const PrimeConst *__restrict__ pc) {
+                                                     int K, int n_go, int level, int N, int g_base,
+                                                     int store_natural, const PrimeConst *__restrict__ pc) {
     constexpr int OTP = (OT + 3) / 4 * 4;  // weight row padded to whole int4 loads
     extern __shared__ __align__(16) unsigned char smraw[];
     int32_t *sw = reinterpret_cast<int32_t *>(smraw);               // [K][OTP] weights (0 for padding taps)
     int32_t *sidx = reinterpret_cast<int32_t *>(smraw) + (size_t)K * OTP;  // [K] input index (0 for padding)
     const int tiles = (n_go + OT - 1) / OT;
-    const int g = blockIdx.y / tiles, o0 = (blockIdx.y % tiles) * OT;
+    const int g = g_base + blockIdx.y / tiles, o0 = (blockIdx.y % tiles) * OT;
     const int no = min(OT, n_go - o0);
     for (int t = threadIdx.x; t < K; t += blockDim.x) {
         const int src = gidx[(size_t)g * K + t];
@@ -95,6 +98,7 @@ __global__ void __launch_bounds__(256) k_mac_grouped(const uint32_t *__restrict_
     for (int o = 0; o < OT; o++) {
         if (o >= no) break;
         const int og = gout != nullptr ? gout[(size_t)g * n_go + o0 + o] : g * n_go + o0 + o;
+        const int os = store_natural ? og : (g - g_base) * n_go + o0 + o;
         uint4 r;
         r.x = barrett_reduce64((uint64_t)(acc[o][0] + off), q, mu);
         r.y = barrett_reduce64((uint64_t)(acc[o][1] + off), q, mu);
@@ -107,53 +111,77 @@ __global__ void __launch_bounds__(256) k_mac_grouped(const uint32_t *__restrict_
             r.z = add_mod(r.z, p.z, q);
             r.w = add_mod(r.w, p.w, q);
         }
-        *reinterpret_cast<uint4 *>(out + (size_t)og * cols + col) = r;
+        *reinterpret_cast<uint4 *>(out + (size_t)os * cols + col) = r;
     }
 }
 
 // ModDown by P, add to (d0, d1), then rescale by q_top -- the two roundings in
 // sequence.  D [C][3][n][N] and ACC [C][2][n+K][N] in coefficient form ->
-// out [C][2][n-1][N].   grid (N/256, 2, C)
+// out [C][2][n-1][N].  Four coefficients per thread.   grid (N/4/256, 2, C)
 __global__ void __launch_bounds__(256) k_moddown_rescale(const uint32_t *__restrict__ D,
                                                          const uint32_t *__restrict__ acc, uint32_t *__restrict__ out,
                                                          int n, int N, KsDev ks, const PrimeConst *__restrict__ pc) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= N) return;
+    const int k4 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k4 * 4 >= N) return;
     const int b = blockIdx.y, ct = blockIdx.z;
     const int nb = n + ks.K, L = ks.L;
-    const uint32_t *db = D + ((size_t)ct * 3 + b) * n * N;
-    const uint32_t *ab = acc + ((size_t)ct * 2 + b) * nb * N;
-    uint32_t *ob = out + ((size_t)ct * 2 + b) * (n - 1) * N;
-    uint32_t r[4];
-    int cnt = 0;
-    for (int m = 0; m < ks.K; m++) {
+    const uint4 *db = reinterpret_cast<const uint4 *>(D + ((size_t)ct * 3 + b) * n * N) + k4;
+    const uint4 *ab = reinterpret_cast<const uint4 *>(acc + ((size_t)ct * 2 + b) * nb * N) + k4;
+    uint4 *ob = reinterpret_cast<uint4 *>(out + ((size_t)ct * 2 + b) * (n - 1) * N) + k4;
+    const size_t stride = (size_t)N / 4;  // one limb, in uint4
+    uint32_t r[4][4];                      // [special prime][coefficient]
+    int cnt[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int m = 0; m < 4; m++) {  // K <= 4; constant indices keep r in registers
+        if (m >= ks.K) break;
         const PrimeConst &pm = pc[L + m];
         const uint2 hi = ks.phat_inv[m];
-        r[m] = shoup_mul(ab[(size_t)(n + m) * N + k], hi.x, hi.y, pm.q);
-        cnt += r[m] > pm.half;
+        const uint4 v = __ldg(ab + (size_t)(n + m) * stride);
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int z = 0; z < 4; z++) {
+            r[m][z] = shoup_mul(w[z], hi.x, hi.y, pm.q);
+            cnt[z] += r[m][z] > pm.half;
+        }
     }
-    auto limb = [&](int i) -> uint32_t {
+    auto limb = [&](int i, uint32_t (&res)[4]) {
         const uint32_t q = pc[i].q;
-        uint32_t conv = 0;
-        for (int m = 0; m < ks.K; m++) {
+        uint32_t conv[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int m = 0; m < 4; m++) {
+            if (m >= ks.K) break;
             const uint2 ph = ks.phat[(size_t)m * L + i];
-            conv = add_mod(conv, shoup_mul(r[m], ph.x, ph.y, q), q);
+#pragma unroll
+            for (int z = 0; z < 4; z++) conv[z] = add_mod(conv[z], shoup_mul(r[m][z], ph.x, ph.y, q), q);
         }
         const uint32_t pmod = ks.pmod[i];
-        for (int c = 0; c < cnt; c++) conv = sub_mod(conv, pmod, q);
         const uint2 pi = ks.pinv[i];
-        const uint32_t kv = shoup_mul(sub_mod(ab[(size_t)i * N + k], conv, q), pi.x, pi.y, q);
-        return add_mod(db[(size_t)i * N + k], kv, q);
+        const uint4 av = __ldg(ab + (size_t)i * stride), dv = __ldg(db + (size_t)i * stride);
+        const uint32_t a[4] = {av.x, av.y, av.z, av.w}, d[4] = {dv.x, dv.y, dv.z, dv.w};
+#pragma unroll
+        for (int z = 0; z < 4; z++) {
+            for (int c = 0; c < cnt[z]; c++) conv[z] = sub_mod(conv[z], pmod, q);
+            const uint32_t kv = shoup_mul(sub_mod(a[z], conv[z], q), pi.x, pi.y, q);
+            res[z] = add_mod(d[z], kv, q);
+        }
     };
     const int top = n - 1;
-    const uint32_t ctop = limb(top), qtop = pc[top].q;
-    const bool neg = ctop > pc[top].half;
+    uint32_t ctop[4];
+    limb(top, ctop);
+    const uint32_t qtop = pc[top].q, htop = pc[top].half;
     for (int i = 0; i < top; i++) {
         const uint32_t q = pc[i].q;
-        uint32_t v = sub_mod(limb(i), ctop, q);
-        if (neg) v = add_mod(v, qtop, q);
         const uint2 qi = ks.qtop_inv[(size_t)top * L + i];
-        ob[(size_t)i * N + k] = shoup_mul(v, qi.x, qi.y, q);
+        uint32_t ci[4];
+        limb(i, ci);
+        uint32_t o[4];
+#pragma unroll
+        for (int z = 0; z < 4; z++) {
+            uint32_t v = sub_mod(ci[z], ctop[z], q);
+            if (ctop[z] > htop) v = add_mod(v, qtop, q);
+            o[z] = shoup_mul(v, qi.x, qi.y, q);
+        }
+        ob[(size_t)i * stride] = make_uint4(o[0], o[1], o[2], o[3]);
     }
 }
 
@@ -242,11 +270,13 @@ struct Timed {
 constexpr int kMaxMacTaps = 4096;
 
 // key-switching chunk buffers per ciphertext at level n (words): D, D2N and ACC
-static size_t chunk_words(const bcn_ctx *c, int n) { return (4 * (size_t)n + 2 * (size_t)(n + c->K)) * c->N; }
+// (plus the MAC output Y of the chunk for an evaluation)
+static size_t chunk_words(const bcn_ctx *c, int n) { return (6 * (size_t)n + 2 * (size_t)(n + c->K)) * c->N; }
 static size_t chunk_bytes(const bcn_ctx *c, int n, int chunk) {
     return align_up(3 * (size_t)n * c->N * 4 * chunk) + align_up((size_t)n * c->N * 4 * chunk) +
            align_up(2 * (size_t)(n + c->K) * c->N * 4 * chunk);
 }
+static size_t y_chunk_bytes(const bcn_ctx *c, int n, int chunk) { return align_up(2 * (size_t)n * c->N * 4 * chunk); }
 static int default_chunk(const bcn_ctx *c, int n, int n_ct) {
     const size_t target = 1ull << 30;
     int ch = (int)std::min<size_t>(32768, std::max<size_t>(1, target / (chunk_words(c, n) * 4)));
@@ -265,9 +295,11 @@ static ChunkBufs carve_chunk(const bcn_ctx *c, int n, int chunk, char *ws) {
     return b;
 }
 
+// MAC over groups [g_base, g_base + n_groups) of a layer
 static bcn_status launch_mac(const bcn_ctx *c, int level, int K, int n_groups, int n_go, const int32_t *gidx,
                              const int8_t *gw, const int32_t *gout, const uint32_t *in, const uint32_t *pt,
-                             uint32_t *out, cudaStream_t st, Profiler *prof = nullptr, double alg_bytes = 0) {
+                             uint32_t *out, cudaStream_t st, Profiler *prof = nullptr, double alg_bytes = 0,
+                             int g_base = 0, bool store_natural = true) {
     if (n_groups <= 0 || n_go <= 0) return BCN_OK;
     if (K > kMaxMacTaps) return fail(BCN_E_INVAL, "MAC fan-in above 4096");
     const int N = c->N;
@@ -280,7 +312,8 @@ static bcn_status launch_mac(const bcn_ctx *c, int level, int K, int n_groups, i
     dim3 grid((unsigned)((cols / 4 + 255) / 256), (unsigned)(n_groups * tiles));
 #define BCN_MAC(OTV)                                                                                          \
     case OTV:                                                                                                 \
-        k_mac_grouped<OTV><<<grid, 256, smem, st>>>(in, out, gidx, gw, gout, pt, K, n_go, level, N, c->d_pc); \
+        k_mac_grouped<OTV><<<grid, 256, smem, st>>>(in, out, gidx, gw, gout, pt, K, n_go, level, N, g_base, \
+                                                    store_natural ? 1 : 0, c->d_pc);                          \
         break;
     switch (OT) { BCN_MAC(1) BCN_MAC(2) BCN_MAC(3) BCN_MAC(4) BCN_MAC(5) BCN_MAC(6) BCN_MAC(7) BCN_MAC(8) }
 #undef BCN_MAC
@@ -304,7 +337,7 @@ static bcn_status square_chunk(const bcn_ctx *c, int n, const uint32_t *evk, con
         BCN_TRY(f->keyswitch(c, n, b.d, b.d2n, evk, b.acc, C, st));
     }
     Timed tm(prof, st, BCN_KERNEL_MODDOWN_RESCALE, limb * C * (2.0 * n + 2.0 * nb + 2.0 * (n - 1)));
-    k_moddown_rescale<<<dim3((N + 255) / 256, 2, C), 256, 0, st>>>(b.d, b.acc, out, n, N, ks_dev(c), c->d_pc);
+    k_moddown_rescale<<<dim3((N / 4 + 255) / 256, 2, C), 256, 0, st>>>(b.d, b.acc, out, n, N, ks_dev(c), c->d_pc);
     return check_launch("k_moddown_rescale");
 }
 
@@ -371,22 +404,23 @@ extern "C" {
 // ------------------------------------------------------------------ model
 static void model_layout(bcn_model *m) {
     const bcn_ctx *c = m->ctx;
-    size_t x_bytes = 0, y_bytes = 0;
-    int max_sq_level = 0, max_sq_out = 0;
+    size_t x_bytes = 0;
+    int max_sq_level = 0, max_sq_out = 0, max_go = 1;
     for (size_t l = 0; l < m->layers.size(); l++) {
         const bcn_layer_plan &p = m->layers[l];
         const int lout = p.square ? p.level - 1 : p.level;
         if (p.square) {
             max_sq_level = std::max(max_sq_level, p.level);
             max_sq_out = std::max(max_sq_out, p.n_out);
-            y_bytes = std::max(y_bytes, (size_t)p.n_out * 2 * p.level * c->N * 4);
+            max_go = std::max(max_go, p.n_go);
         }
         if (l + 1 < m->layers.size()) x_bytes = std::max(x_bytes, (size_t)p.n_out * 2 * lout * c->N * 4);
     }
     m->ws_x_bytes = align_up(x_bytes);
-    m->ws_y_bytes = align_up(y_bytes);
     int ch = m->chunk_request > 0 ? m->chunk_request : (max_sq_level ? default_chunk(c, max_sq_level, max_sq_out) : 1);
-    m->chunk = std::max(1, std::min(ch, std::max(1, max_sq_out)));
+    ch = std::max(ch, max_go);  // a chunk holds whole output groups
+    m->chunk = std::max(1, std::min(ch, std::max(max_go, max_sq_out)));
+    m->ws_y_bytes = max_sq_level ? y_chunk_bytes(c, max_sq_level, m->chunk) : 0;
     m->ws_chunk_bytes = max_sq_level ? chunk_bytes(c, max_sq_level, m->chunk) : 0;
 }
 
@@ -397,6 +431,7 @@ bcn_status bcn_model_create(bcn_ctx *c, const bcn_layer *layers, int n_layers, b
     bcn_model *m = new bcn_model();
     m->ctx = c;
     int level = c->L, prev_out = -1;
+    std::vector<int32_t> prev_perm;
     auto cleanup = [&](bcn_status s, const std::string &msg) {
         bcn_model_destroy(m);
         return fail(s, msg);
@@ -464,6 +499,11 @@ bcn_status bcn_model_create(bcn_ctx *c, const bcn_layer *layers, int n_layers, b
             return cleanup(BCN_E_INVAL, "layer " + std::to_string(l) + ": input count does not match");
         if (p.square && level < 2)
             return cleanup(BCN_E_LEVEL, "no level left for the square of layer " + std::to_string(l));
+        if (p.square && l + 1 == n_layers)
+            return cleanup(BCN_E_INVAL, "the last layer gives the outputs and must not square");
+        if (!prev_perm.empty())  // inputs live in the previous layer's group-major order
+            for (int32_t &v : gidx)
+                if (v >= 0) v = prev_perm[v];
         std::vector<char> used(p.n_in, 0);
         for (int32_t v : gidx)
             if (v >= 0) used[v] = 1;
@@ -480,6 +520,8 @@ bcn_status bcn_model_create(bcn_ctx *c, const bcn_layer *layers, int n_layers, b
             return cleanup(BCN_E_CUDA, "upload of layer tables failed");
         if (p.square) level -= 1;
         prev_out = p.n_out;
+        prev_perm.assign(p.n_out, 0);  // natural index -> group-major position
+        for (size_t k = 0; k < gout.size(); k++) prev_perm[gout[k]] = (int32_t)k;
     }
     m->out_level = level;
     m->chunk_request = 0;
@@ -578,7 +620,7 @@ bcn_status bcn_eval(const bcn_model *m, const uint32_t *evk, const uint32_t *cts
     cudaStream_t st = (cudaStream_t)stream;
     char *w = reinterpret_cast<char *>(ws);
     uint32_t *X[2] = {reinterpret_cast<uint32_t *>(w), reinterpret_cast<uint32_t *>(w + m->ws_x_bytes)};
-    uint32_t *Yfull = reinterpret_cast<uint32_t *>(w + 2 * m->ws_x_bytes);
+    uint32_t *Ychunk = reinterpret_cast<uint32_t *>(w + 2 * m->ws_x_bytes);
     char *chunk_ws = w + 2 * m->ws_x_bytes + m->ws_y_bytes;
     const uint32_t *x = cts;
     int a = 0;
@@ -595,18 +637,22 @@ bcn_status bcn_eval(const bcn_model *m, const uint32_t *evk, const uint32_t *cts
             pt = pts[a++];
         }
         const double limb = (double)N * 4;
-        const double mac_bytes = limb * ((double)p.n_distinct_in * 2 * p.level + (double)p.n_out * 2 * p.level +
-                                         (pt ? (double)p.n_out * p.level : 0.0));
-        uint32_t *mac_out = p.square ? Yfull : y;
-        BCN_TRY(launch_mac(c, p.level, p.K, p.n_groups, p.n_go, p.d_gidx, p.d_gw, p.d_gout, x, pt, mac_out, st, prof,
-                           mac_bytes));
-        if (p.square) {
+        if (!p.square) {
+            const double mac_bytes = limb * ((double)p.n_distinct_in * 2 * p.level + (double)p.n_out * 2 * p.level +
+                                             (pt ? (double)p.n_out * p.level : 0.0));
+            BCN_TRY(launch_mac(c, p.level, p.K, p.n_groups, p.n_go, p.d_gidx, p.d_gw, p.d_gout, x, pt, y, st, prof,
+                               mac_bytes, 0, last));
+        } else {
             const int n = p.level;
+            const int gpc = std::max(1, m->chunk / p.n_go);  // whole groups per chunk
             ChunkBufs b = carve_chunk(c, n, m->chunk, chunk_ws);
-            for (int o0 = 0; o0 < p.n_out; o0 += m->chunk) {
-                const int C = std::min(m->chunk, p.n_out - o0);
-                BCN_TRY(square_chunk(c, n, evk, Yfull + (size_t)o0 * 2 * n * N, b, C, y + (size_t)o0 * 2 * (n - 1) * N,
-                                     st, prof));
+            for (int g0 = 0; g0 < p.n_groups; g0 += gpc) {
+                const int ng = std::min(gpc, p.n_groups - g0), C = ng * p.n_go, o0 = g0 * p.n_go;
+                const double mac_bytes = limb * ((double)p.n_distinct_in * 2 * n * ng / p.n_groups +
+                                                 (double)C * 2 * n + (pt ? (double)C * n : 0.0));
+                BCN_TRY(launch_mac(c, n, p.K, ng, p.n_go, p.d_gidx, p.d_gw, p.d_gout, x, pt, Ychunk, st, prof,
+                                   mac_bytes, g0, false));
+                BCN_TRY(square_chunk(c, n, evk, Ychunk, b, C, y + (size_t)o0 * 2 * (n - 1) * N, st, prof));
             }
         }
         x = y;

@@ -217,3 +217,57 @@ def random_residues(primes, shape_before_limb, n: int, seed: int):
     q = np.asarray(primes, dtype=np.uint64).reshape((1,) * len(shape_before_limb) + (len(primes), 1))
     r = g.integers(0, 2**62, size=tuple(shape_before_limb) + (len(primes), n), dtype=np.uint64)
     return (r % q).astype(np.uint32)
+
+
+# ---------------------------------------------------------------------------
+# the batched uneven workload: many evaluations of different ring degrees,
+# segment sizes and slot occupancies
+# ---------------------------------------------------------------------------
+_BY_N = {12: "cnn3_small", 13: "cryptonets", 14: "cifar_cnn"}
+
+
+def segment_network(base: dict, h: int, w: int) -> dict:
+    """The network of `base` on a centred h x w sensitive segment: the same
+    layers, with the first conv reading h x w and every later layer sized to
+    follow; plaintext-branch crops follow the ciphertext-branch maps."""
+    cfg = copy.deepcopy(base)
+    H, W, C = cfg["image"]
+    cfg["segment"] = ((H - h) // 2, (W - w) // 2, h, w)
+    ch, hh, ww = C, h, w
+    cipher = []
+    for layer in cfg["cipher"]:
+        layer = dict(layer)
+        if layer["type"] == "conv":
+            layer.update(cin=ch, h=hh, w=ww)
+            hh, ww = conv_out_hw(hh, ww, layer["k"], layer["stride"], layer["pad"])
+            ch = layer["cout"]
+        else:
+            layer["n_in"] = ch * hh * ww
+            ch, hh, ww = layer["n_out"], 1, 1
+        cipher.append(layer)
+    cfg["cipher"] = cipher
+    return cfg
+
+
+def uneven_batch(n_eval: int = 64, seed: int = 11, log_ns=(12, 13, 14)):
+    """Seeded list of evaluations: ring degree uniform over `log_ns` (with the
+    matching parameter set and network), sensitive fraction f uniform in
+    [0.10, 0.60] of the pixels as a centred h x w block (h = round(sqrt(f H W)),
+    w = round(f H W / h), at least the first kernel size), slot occupancy
+    uniform in [0.25, 1.0] of the N/2 slots.  Returns a list of configs with
+    "occupancy" (images counted) added."""
+    g = _rng(seed, 3)
+    out = []
+    for i in range(n_eval):
+        base = get_config(_BY_N[int(log_ns[g.integers(0, len(log_ns))])])
+        H, W, C = base["image"]
+        f = g.uniform(0.10, 0.60)
+        k = base["cipher"][0]["k"]
+        h = max(k, min(H, int(round(np.sqrt(f * H * W)))))
+        w = max(k, min(W, int(round(f * H * W / h))))
+        cfg = segment_network(base, h, w)
+        cfg["name"] = f"{base['name']}_{h}x{w}_{i}"
+        slots = 1 << (cfg["log_n"] - 1)
+        cfg["batch"] = max(1, int(round(g.uniform(0.25, 1.0) * slots)))
+        out.append(cfg)
+    return out
