@@ -17,6 +17,9 @@
 
 namespace bcn {
 
+// taps whose weights and indices a MAC block holds in shared memory at a time
+constexpr int kMacTapChunk = 2048;
+
 // ------------------------------------------------------------------- kernels
 // Integer-weight MAC + feature add over output groups.  A group is a set of
 // outputs that read the same taps (a conv position with all its output
@@ -36,60 +39,67 @@ __global__ void __launch_bounds__(256) k_mac_grouped(const uint32_t *__restrict_
                                                      int store_natural, const PrimeConst *__restrict__ pc) {
     constexpr int OTP = (OT + 3) / 4 * 4;  // weight row padded to whole int4 loads
     extern __shared__ __align__(16) unsigned char smraw[];
-    int32_t *sw = reinterpret_cast<int32_t *>(smraw);               // [K][OTP] weights (0 for padding taps)
-    int32_t *sidx = reinterpret_cast<int32_t *>(smraw) + (size_t)K * OTP;  // [K] input index (0 for padding)
+    int32_t *sw = reinterpret_cast<int32_t *>(smraw);                        // [KC][OTP] weights (0: padding tap)
+    int32_t *sidx = reinterpret_cast<int32_t *>(smraw) + (size_t)kMacTapChunk * OTP;  // [KC] input (0: padding)
     const int tiles = (n_go + OT - 1) / OT;
     const int g = g_base + blockIdx.y / tiles, o0 = (blockIdx.y % tiles) * OT;
     const int no = min(OT, n_go - o0);
-    for (int t = threadIdx.x; t < K; t += blockDim.x) {
-        const int src = gidx[(size_t)g * K + t];
-        sidx[t] = src < 0 ? 0 : src;
-    }
-    for (int x = threadIdx.x; x < OTP * K; x += blockDim.x) {
-        const int t = x / OTP, o = x % OTP;
-        const bool live = o < no && gidx[(size_t)g * K + t] >= 0;
-        sw[x] = live ? (int32_t)gw[((size_t)g * n_go + o0 + o) * K + t] : 0;
-    }
-    __syncthreads();
     const size_t cols = (size_t)2 * level * N;
     const size_t col = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
-    if (col >= cols) return;
+    const bool active = col < cols;
     // residues are below 2^31, so signed 32 x 32 -> 64 products are exact
     long long acc[OT][4];
 #pragma unroll
     for (int o = 0; o < OT; o++) acc[o][0] = acc[o][1] = acc[o][2] = acc[o][3] = 0;
-    const uint32_t *base = in + col;
-    constexpr int U = 4;  // taps in flight per thread
-    int t = 0;
-    for (; t + U <= K; t += U) {
-        uint4 x[U];
+    const uint32_t *base = in + (active ? col : 0);
+    for (int t0 = 0; t0 < K; t0 += kMacTapChunk) {  // taps in chunks that fit shared memory
+        const int KC = min(kMacTapChunk, K - t0);
+        __syncthreads();  // the previous chunk's taps are no longer read
+        for (int t = threadIdx.x; t < KC; t += blockDim.x) {
+            const int src = gidx[(size_t)g * K + t0 + t];
+            sidx[t] = src < 0 ? 0 : src;
+        }
+        for (int x = threadIdx.x; x < OTP * KC; x += blockDim.x) {
+            const int t = x / OTP, o = x % OTP;
+            const bool live = o < no && gidx[(size_t)g * K + t0 + t] >= 0;
+            sw[x] = live ? (int32_t)gw[((size_t)g * n_go + o0 + o) * K + t0 + t] : 0;
+        }
+        __syncthreads();
+        if (!active) continue;
+        constexpr int U = 4;  // taps in flight per thread
+        int t = 0;
+        for (; t + U <= KC; t += U) {
+            uint4 x[U];
 #pragma unroll
-        for (int k = 0; k < U; k++) x[k] = __ldg(reinterpret_cast<const uint4 *>(base + (size_t)sidx[t + k] * cols));
+            for (int k = 0; k < U; k++)
+                x[k] = __ldg(reinterpret_cast<const uint4 *>(base + (size_t)sidx[t + k] * cols));
 #pragma unroll
-        for (int k = 0; k < U; k++) {
-            const int32_t *wr = sw + (t + k) * OTP;
+            for (int k = 0; k < U; k++) {
+                const int32_t *wr = sw + (t + k) * OTP;
+#pragma unroll
+                for (int o = 0; o < OT; o++) {
+                    const long long w = wr[o];
+                    acc[o][0] += w * (int)x[k].x;
+                    acc[o][1] += w * (int)x[k].y;
+                    acc[o][2] += w * (int)x[k].z;
+                    acc[o][3] += w * (int)x[k].w;
+                }
+            }
+        }
+        for (; t < KC; t++) {
+            const uint4 x = __ldg(reinterpret_cast<const uint4 *>(base + (size_t)sidx[t] * cols));
+            const int32_t *wr = sw + t * OTP;
 #pragma unroll
             for (int o = 0; o < OT; o++) {
                 const long long w = wr[o];
-                acc[o][0] += w * (int)x[k].x;
-                acc[o][1] += w * (int)x[k].y;
-                acc[o][2] += w * (int)x[k].z;
-                acc[o][3] += w * (int)x[k].w;
+                acc[o][0] += w * (int)x.x;
+                acc[o][1] += w * (int)x.y;
+                acc[o][2] += w * (int)x.z;
+                acc[o][3] += w * (int)x.w;
             }
         }
     }
-    for (; t < K; t++) {
-        const uint4 x = __ldg(reinterpret_cast<const uint4 *>(base + (size_t)sidx[t] * cols));
-        const int32_t *wr = sw + t * OTP;
-#pragma unroll
-        for (int o = 0; o < OT; o++) {
-            const long long w = wr[o];
-            acc[o][0] += w * (int)x.x;
-            acc[o][1] += w * (int)x.y;
-            acc[o][2] += w * (int)x.z;
-            acc[o][3] += w * (int)x.w;
-        }
-    }
+    if (!active) return;
     const int poly = (int)(col / ((size_t)level * N)), i = (int)((col / N) % level);
     const uint32_t q = pc[i].q;
     const uint64_t mu = pc[i].barrett;
@@ -267,7 +277,7 @@ struct Timed {
     }
 };
 
-constexpr int kMaxMacTaps = 4096;
+constexpr int kMaxMacTaps = 1 << 20;  // keeps |sum| < 2^58, the MAC offset
 
 // key-switching chunk buffers per ciphertext at level n (words): D, D2N and ACC
 // (plus the MAC output Y of the chunk for an evaluation)
@@ -301,12 +311,12 @@ static bcn_status launch_mac(const bcn_ctx *c, int level, int K, int n_groups, i
                              uint32_t *out, cudaStream_t st, Profiler *prof = nullptr, double alg_bytes = 0,
                              int g_base = 0, bool store_natural = true) {
     if (n_groups <= 0 || n_go <= 0) return BCN_OK;
-    if (K > kMaxMacTaps) return fail(BCN_E_INVAL, "MAC fan-in above 4096");
+    if (K > kMaxMacTaps) return fail(BCN_E_INVAL, "MAC fan-in above 2^20");
     const int N = c->N;
     const int OT = std::min(8, n_go);
     const int tiles = (n_go + OT - 1) / OT;
     const size_t cols = (size_t)2 * level * N;
-    const size_t smem = (size_t)K * 4 + (size_t)((OT + 3) / 4 * 4) * K * 4;
+    const size_t smem = (size_t)kMacTapChunk * 4 * (1 + (OT + 3) / 4 * 4);
     if ((long long)n_groups * tiles > 65535) return fail(BCN_E_INVAL, "MAC layer with more than 65535 output tiles");
     Timed tm(prof, st, BCN_KERNEL_MAC, alg_bytes);
     dim3 grid((unsigned)((cols / 4 + 255) / 256), (unsigned)(n_groups * tiles));
@@ -374,7 +384,7 @@ bcn_status device_ctx_init(bcn_ctx *c) {
                           cudaMemcpyHostToDevice) == cudaSuccess;
     if (!ok) return fail(BCN_E_CUDA, "upload of the context tables failed");
     BCN_TRY(cores_setup_all());
-    const int mac_smem = kMaxMacTaps * 4 + 8 * kMaxMacTaps * 4;
+    const int mac_smem = kMacTapChunk * 4 * (1 + 8);
 #define BCN_MSETUP(OTV)                                                                                           \
     if (cudaFuncSetAttribute(k_mac_grouped<OTV>, cudaFuncAttributeMaxDynamicSharedMemorySize, mac_smem) !=      \
         cudaSuccess)                                                                                            \
@@ -492,7 +502,7 @@ bcn_status bcn_model_create(bcn_ctx *c, const bcn_layer *layers, int n_layers, b
         } else {
             return cleanup(BCN_E_INVAL, "layer " + std::to_string(l) + ": unknown type");
         }
-        if (p.K > kMaxMacTaps) return cleanup(BCN_E_INVAL, "layer fan-in above 4096");
+        if (p.K > kMaxMacTaps) return cleanup(BCN_E_INVAL, "layer fan-in above 2^20");
         if ((long long)p.n_groups * ((p.n_go + 7) / 8) > 65535)
             return cleanup(BCN_E_INVAL, "layer " + std::to_string(l) + ": too many output tiles");
         if (prev_out >= 0 && p.n_in != prev_out)

@@ -94,6 +94,22 @@ def test_mac_large_fan_in():
     assert np.array_equal(host(out), P.mac(2, idx, w, x, None))
 
 
+def test_mac_fan_in_spanning_tap_chunks():
+    """Fan-in 5000 (above the 2048 taps a block stages at a time: two full
+    chunks and a ragged third) with zero taps and repeated inputs, as in a dense
+    layer over a large segment."""
+    c, P = pair((12, 3, 1, 1))
+    rng = np.random.default_rng(17)
+    n_in, n_out, K = 700, 5, 5000
+    x = workloads.random_residues(P.q[:2], (n_in, 2), P.N, 18)
+    idx = rng.integers(-1, n_in, size=(n_out, K)).astype(np.int32)
+    w = rng.integers(-127, 128, size=(n_out, K)).astype(np.int8)
+    w[0] = -127
+    out = torch.empty((n_out, 2, 2, P.N), dtype=torch.int32, device="cuda")
+    c.op_mac(2, n_in, torch.from_numpy(idx).cuda(), torch.from_numpy(w).cuda(), dev(x), None, out)
+    assert np.array_equal(host(out), P.mac(2, idx, w, x, None))
+
+
 @pytest.mark.parametrize("p", PARAMS)
 def test_rescale(p):
     c, P = pair(p)
