@@ -192,6 +192,20 @@ __device__ __forceinline__ void ks_core_body(const uint32_t *__restrict__ D, con
                     r1 = add_mod(r1, mont_mul(x[u + z], w1[z], P.q, P.qneg_inv), P.q);
                 }
             }
+        } else if constexpr (C::NTT_PAIRS) {
+#pragma unroll
+            for (int u = 0; u < R; u += 2) {
+                const int e = C::ntt_elem(u, tid);
+                const uint2 v0 = __ldg(reinterpret_cast<const uint2 *>(k0 + e));
+                const uint2 v1 = __ldg(reinterpret_cast<const uint2 *>(k1 + e));
+                const uint32_t w0[2] = {v0.x, v0.y}, w1[2] = {v1.x, v1.y};
+#pragma unroll
+                for (int z = 0; z < 2; z++) {
+                    uint32_t &r0 = s0[(u + z) * T + tid], &r1 = s1[(u + z) * T + tid];
+                    r0 = add_mod(r0, mont_mul(x[u + z], w0[z], P.q, P.qneg_inv), P.q);
+                    r1 = add_mod(r1, mont_mul(x[u + z], w1[z], P.q, P.qneg_inv), P.q);
+                }
+            }
         } else {
 #pragma unroll
             for (int u = 0; u < R; u++) {

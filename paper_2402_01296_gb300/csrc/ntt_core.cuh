@@ -14,11 +14,24 @@
 // Distribution of pass P covering stages [s0, s1): rp = s1 - s0 stages,
 // stride tmin = N >> s1, G = R >> rp groups of 2^rp residues per thread;
 // register u = g * 2^rp + v holds element
-//     e = hi * (tmin << rp) + lo + v * tmin,   gidx = g * T + tid,
+//     e = hi * (tmin << rp) + lo + v * tmin,
+//     gidx = (tid / W) * W * G + g * W + tid mod W   (W = min(32, T)),
 //     lo = gidx mod tmin,  hi = gidx / tmin.
-// Pass 0 is therefore e = tid + u * T (coalesced loads of natural order) and a
-// full last pass gives each thread R consecutive elements.  Everything that
-// selects a register is a template parameter, so the limb stays in registers.
+// Only the last pass can have G > 1; there the groups of a warp interleave by
+// lane, so one register across a warp is a contiguous run (coalesced NTT-domain
+// loads and stores).  Pass 0 is e = tid + u * T (coalesced loads of natural
+// order).  Everything that selects a register is a template parameter, so the
+// limb stays in registers.
+//
+// A pass is warp-local when every warp holds the contiguous block of 32 R
+// elements [32 R w, 32 R (w + 1)): the last pass, and every pass with
+// tmin <= 32.  The exchange between two warp-local passes never crosses a
+// warp, so it synchronises with __syncwarp; only exchanges from or to a
+// spread-out distribution (pass 0 and, for large N, pass 1) need the whole
+// block.  Since every read of a spread-out distribution ends with a block
+// barrier, a warp may write its own block whenever its own earlier reads are
+// done; a spread-out write waits for the block unless the previous exchange of
+// the same transform already ended with a block barrier.
 //
 // LAZY (only for q < 2^30, so 4q < 2^32): Harvey's lazy butterflies.  The
 // forward transform keeps residues in [0, 4q) (input [0, 4q), output [0, 4q));
@@ -37,6 +50,7 @@ struct NttCore {
     static constexpr int LOGR = (R == 2) ? 1 : (R == 4) ? 2 : (R == 8) ? 3 : (R == 16) ? 4 : (R == 32) ? 5 : 6;
     static constexpr int PASSES = (LOGN + LOGR - 1) / LOGR;
     static constexpr int SMEM_WORDS = N + N / 32;  // padded exchange buffer
+    static constexpr int WS = T < 32 ? T : 32;     // threads of one warp
     static_assert((1 << LOGR) == R, "R must be a power of two");
     static_assert(LOGN >= LOGR, "R must not exceed N");
 
@@ -45,14 +59,23 @@ struct NttCore {
     __host__ __device__ static constexpr int rp_of(int p) { return s1_of(p) - s0_of(p); }
     static constexpr int LAST_RP = rp_of(PASSES - 1);
 
+    // butterfly-group index of group g of thread tid in pass P
+    template <int P>
+    __host__ __device__ static constexpr int gidx_of(int g, int tid) {
+        return (tid / WS) * WS * (R >> rp_of(P)) + g * WS + tid % WS;
+    }
     // element held in register u during pass P (the defining formula)
     template <int P>
     __host__ __device__ static constexpr int elem_def(int u, int tid) {
         const int rp = rp_of(P), logtmin = LOGN - s1_of(P);
         const int g = u >> rp, v = u & ((1 << rp) - 1);
-        const int gidx = g * T + tid;
+        const int gidx = gidx_of<P>(g, tid);
         const int lo = gidx & ((1 << logtmin) - 1), hi = gidx >> logtmin;
         return (hi << (logtmin + rp)) + lo + (v << logtmin);
+    }
+    template <int P>
+    __host__ __device__ static constexpr bool warp_local() {
+        return T >= 32 && (T == 32 || P == PASSES - 1 || (N >> s1_of(P)) <= 32);  // full warps only
     }
     __host__ __device__ static constexpr int padded(int e) { return e + (e >> 5); }
     // For every supported (LOGN, R, pass) both maps are linear in the thread:
@@ -75,16 +98,25 @@ struct NttCore {
         return v;
     }
 
-    template <int PF, int PT>
+    // FIRST: the first exchange of a transform (what ran before is unknown)
+    template <int PF, int PT, bool FIRST>
     __device__ __forceinline__ static void exchange(uint32_t (&x)[R], uint32_t *sm, int tid) {
+        constexpr bool WF = warp_local<PF>(), WT = warp_local<PT>();
+        if constexpr (FIRST && !WF) __syncthreads();
         uint32_t *wf = sm + pad_base<PF>(tid);
 #pragma unroll
         for (int u = 0; u < R; u++) wf[pad_off<PF>(u)] = x[u];
-        __syncthreads();
+        if constexpr (WF && WT)
+            __syncwarp();
+        else
+            __syncthreads();
         const uint32_t *rt = sm + pad_base<PT>(tid);
 #pragma unroll
         for (int u = 0; u < R; u++) x[u] = rt[pad_off<PT>(u)];
-        __syncthreads();
+        if constexpr (WT)
+            __syncwarp();
+        else
+            __syncthreads();
     }
 
     // stage s0 + KS of pass P (forward) for group g
@@ -144,7 +176,7 @@ struct NttCore {
         constexpr int rp = rp_of(P);
 #pragma unroll
         for (int g = 0; g < (R >> rp); g++) {
-            const int hi = (g * T + tid) >> (LOGN - s1_of(P));
+            const int hi = gidx_of<P>(g, tid) >> (LOGN - s1_of(P));
             stage_fwd<P, 0>(x, g, hi, q, tw);
         }
     }
@@ -154,7 +186,7 @@ struct NttCore {
         constexpr int rp = rp_of(P);
 #pragma unroll
         for (int g = 0; g < (R >> rp); g++) {
-            const int hi = (g * T + tid) >> (LOGN - s1_of(P));
+            const int hi = gidx_of<P>(g, tid) >> (LOGN - s1_of(P));
             stage_inv<P, rp - 1>(x, g, hi, q, tw);
         }
     }
@@ -162,7 +194,7 @@ struct NttCore {
     template <int P>
     __device__ __forceinline__ static void forward_from(uint32_t (&x)[R], uint32_t *sm, int tid, uint32_t q,
                                                         const uint2 *__restrict__ tw) {
-        if constexpr (P > 0) exchange<P - 1, P>(x, sm, tid);
+        if constexpr (P > 0) exchange<P - 1, P, P == 1>(x, sm, tid);
         pass_fwd<P>(x, tid, q, tw);
         if constexpr (P + 1 < PASSES) forward_from<P + 1>(x, sm, tid, q, tw);
     }
@@ -171,7 +203,7 @@ struct NttCore {
                                                         const uint2 *__restrict__ tw) {
         pass_inv<P>(x, tid, q, tw);
         if constexpr (P > 0) {
-            exchange<P, P - 1>(x, sm, tid);
+            exchange<P, P - 1, P == PASSES - 1>(x, sm, tid);
             inverse_from<P - 1>(x, sm, tid, q, tw);
         }
     }
@@ -214,6 +246,8 @@ struct NttCore {
     // at least 2 stages
     __device__ __forceinline__ static int ntt_elem(int u, int tid) { return elem<PASSES - 1>(u, tid); }
     static constexpr bool NTT_QUADS = LAST_RP >= 2 && R >= 4;
+    // registers 2k, 2k+1 hold 2 consecutive elements
+    static constexpr bool NTT_PAIRS = LAST_RP >= 1 && R >= 2;
 
     // NTT-domain limb <-> last-pass distribution
     __device__ __forceinline__ static void load_ntt(uint32_t (&x)[R], const uint32_t *__restrict__ g, int tid) {
@@ -222,6 +256,12 @@ struct NttCore {
             for (int u = 0; u < R; u += 4) {
                 const uint4 v = __ldg(reinterpret_cast<const uint4 *>(g + ntt_elem(u, tid)));
                 x[u] = v.x; x[u + 1] = v.y; x[u + 2] = v.z; x[u + 3] = v.w;
+            }
+        } else if constexpr (NTT_PAIRS) {
+#pragma unroll
+            for (int u = 0; u < R; u += 2) {
+                const uint2 v = __ldg(reinterpret_cast<const uint2 *>(g + ntt_elem(u, tid)));
+                x[u] = v.x; x[u + 1] = v.y;
             }
         } else {
 #pragma unroll
@@ -233,6 +273,10 @@ struct NttCore {
 #pragma unroll
             for (int u = 0; u < R; u += 4)
                 *reinterpret_cast<uint4 *>(g + ntt_elem(u, tid)) = make_uint4(x[u], x[u + 1], x[u + 2], x[u + 3]);
+        } else if constexpr (NTT_PAIRS) {
+#pragma unroll
+            for (int u = 0; u < R; u += 2)
+                *reinterpret_cast<uint2 *>(g + ntt_elem(u, tid)) = make_uint2(x[u], x[u + 1]);
         } else {
 #pragma unroll
             for (int u = 0; u < R; u++) g[ntt_elem(u, tid)] = x[u];
