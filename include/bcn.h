@@ -91,6 +91,12 @@ bcn_status bcn_ctx_primes(const bcn_ctx *ctx, uint64_t *primes_out);
 /* number of uint32 words of an evaluation key: dnum * 2 * (L + K) * N */
 size_t bcn_evk_words(const bcn_ctx *ctx);
 
+/* Reads and clears the context's device status word (synchronous): 0 when no
+ * kernel gave up a bounded wait since the last call; otherwise a bit set by
+ * the kernel that gave up (1: the tensor-core MAC's wait for its MMAs), whose
+ * outputs are then unspecified. */
+bcn_status bcn_device_status(const bcn_ctx *ctx, uint32_t *status);
+
 /* ------------------------------------------------------------ client side */
 /* Secret key (uniform ternary) and relinearisation key for hybrid key
  * switching (digit j covers q_{j*alpha} .. q_{j*alpha+alpha-1}):
@@ -208,6 +214,11 @@ bcn_status bcn_model_destroy(bcn_model *m);
  * chunk's intermediates bounded by 1 GiB).  Changes bcn_eval_workspace_bytes;
  * results do not depend on it. */
 bcn_status bcn_model_set_chunk(bcn_model *m, int chunk);
+/* MAC implementation: 0 (default) runs the layer groups with at least 32
+ * outputs and at most 512 taps on the tensor cores (the residues split into
+ * byte planes, fp16 operands, exact fp32 sums), the rest on the CUDA cores;
+ * 1 runs every MAC on the CUDA cores.  Results are identical either way. */
+bcn_status bcn_model_set_mac_impl(bcn_model *m, int impl);
 bcn_status bcn_model_get_info(const bcn_model *m, bcn_model_info *out);
 /* per layer: live level at its input and its output count (arrays of n_layers) */
 bcn_status bcn_model_layers(const bcn_model *m, int *level_out, int *n_out_out);

@@ -64,6 +64,7 @@ _SIGS = {
     "bcn_ctx_get_info": (_I, [_P, ctypes.POINTER(_CtxInfo)]),
     "bcn_ctx_primes": (_I, [_P, _P]),
     "bcn_evk_words": (_SZ, [_P]),
+    "bcn_device_status": (_I, [_P, _P]),
     "bcn_keygen": (_I, [_P, _U64, _P, _P]),
     "bcn_quantize": (_I, [_P, _SZ, _P, ctypes.POINTER(_D)]),
     "bcn_encode": (_I, [_P, _P, _I, _I, _I, _D, _P]),
@@ -78,6 +79,7 @@ _SIGS = {
     "bcn_model_create": (_I, [_P, _P, _I, ctypes.POINTER(_P)]),
     "bcn_model_destroy": (_I, [_P]),
     "bcn_model_set_chunk": (_I, [_P, _I]),
+    "bcn_model_set_mac_impl": (_I, [_P, _I]),
     "bcn_model_get_info": (_I, [_P, ctypes.POINTER(_ModelInfo)]),
     "bcn_model_layers": (_I, [_P, _P, _P]),
     "bcn_model_scales": (_I, [_P, _D, _P, ctypes.POINTER(_D)]),
@@ -225,6 +227,12 @@ class Context:
 
     def evk_shape(self):
         return (self.dnum, 2, self.L + self.K, self.N)
+
+    def device_status(self) -> int:
+        """Reads and clears the device status word (0: no bounded wait gave up)."""
+        v = ctypes.c_uint32(0)
+        _check(lib().bcn_device_status(self._h, ctypes.byref(v)), "bcn_device_status")
+        return int(v.value)
 
     # -- client side (host) ---------------------------------------------
     def keygen(self, seed: int):
@@ -407,6 +415,10 @@ class Model:
 
     def set_chunk(self, chunk: int):
         _check(lib().bcn_model_set_chunk(self._h, int(chunk)), "bcn_model_set_chunk")
+
+    def set_mac_impl(self, impl: int):
+        """0: tensor cores where eligible (default); 1: CUDA cores only."""
+        _check(lib().bcn_model_set_mac_impl(self._h, int(impl)), "bcn_model_set_mac_impl")
 
     def profile_enable(self, on: bool = True):
         _check(lib().bcn_profile_enable(self._h, int(on)), "bcn_profile_enable")

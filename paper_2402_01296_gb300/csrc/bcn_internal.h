@@ -78,6 +78,16 @@ struct KsTables {
 }  // namespace bcn
 
 // the opaque objects -------------------------------------------------------------
+namespace bcn {
+// Tensor-core MAC of a layer: fp16 weight tables per output tile and launch shape.
+struct MacTcPlan {
+    uint16_t *w16 = nullptr;  // [tiles][NT][Kpad] canonical K-major layout
+    int tiles = 0, tile_out = 0, NT = 0, Kpad = 0;
+    uint32_t tmem_cols = 0;
+    size_t smem = 0;
+};
+}  // namespace bcn
+
 struct bcn_ctx {
     bcn_params params;
     int N, logN, L, K, alpha, dnum;
@@ -92,6 +102,7 @@ struct bcn_ctx {
     uint2 *d_tw_fwd = nullptr;        // [P][N] (psi^{brv(k)}, shoup)
     uint2 *d_tw_inv = nullptr;        // [P][N] (psi^{-brv(k)}, shoup)
     uint32_t *d_ks = nullptr;         // KsTables blob
+    uint32_t *d_status = nullptr;     // device status word (bounded waits that gave up)
     bcn::KsTables ks;
     std::vector<bcn::PrimeConst> h_pc;
 };
@@ -106,6 +117,7 @@ struct bcn_layer_plan {
     int32_t *d_gidx = nullptr; // [n_groups][K] input index per tap (-1: zero padding)
     int8_t *d_gw = nullptr;    // [n_groups][n_go][K]
     int32_t *d_gout = nullptr; // [n_groups][n_go] output index
+    bcn::MacTcPlan tc;         // tensor-core MAC (tc.w16 == nullptr: not used)
 };
 
 namespace bcn {
@@ -132,6 +144,7 @@ struct bcn_model {
     mutable bcn::Profiler prof;
     int chunk;          // ciphertexts per key-switching chunk
     int chunk_request;  // 0: automatic
+    int mac_impl = 0;   // 0: tensor cores where eligible, 1: CUDA cores only
     size_t ws_x_bytes;  // one ping-pong activation buffer
     size_t ws_y_bytes;  // MAC output of a square layer
     size_t ws_chunk_bytes;

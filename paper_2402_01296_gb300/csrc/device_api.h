@@ -76,6 +76,17 @@ bcn_status square_relin_rescale_chunk2(const bcn_ctx *c, int n, const uint32_t *
 
 bcn_status launch_ntt(const bcn_ctx *c, uint32_t *data, size_t n_limbs, const PrimeMap &pm, bool inverse,
                       cudaStream_t st);
+
+// Tensor-core MAC (mac_tc.cu): used for groups of at least kMacTcMinOutputs
+// outputs and at most kMacTcMaxTaps taps (the fp32 sums stay exact).
+constexpr int kMacTcMaxTaps = 512, kMacTcMinOutputs = 32;
+bool mac_tc_eligible(const bcn_ctx *c, int K, int n_go);
+// w: [n_go][K] int8 weights shared by every group
+bcn_status mac_tc_plan(const bcn_ctx *c, int K, int n_go, const int8_t *w, MacTcPlan *p);
+bcn_status mac_tc_setup();
+bcn_status launch_mac_tc(const bcn_ctx *c, const MacTcPlan &p, int level, int K, int n_groups, int n_go,
+                         const int32_t *gidx, const int32_t *gout, const uint32_t *in, const uint32_t *pt,
+                         uint32_t *out, cudaStream_t st, int g_base, bool store_natural);
 bcn_status cores_setup_all();
 
 }  // namespace bcn

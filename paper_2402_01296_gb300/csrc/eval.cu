@@ -309,9 +309,13 @@ static ChunkBufs carve_chunk(const bcn_ctx *c, int n, int chunk, char *ws) {
 static bcn_status launch_mac(const bcn_ctx *c, int level, int K, int n_groups, int n_go, const int32_t *gidx,
                              const int8_t *gw, const int32_t *gout, const uint32_t *in, const uint32_t *pt,
                              uint32_t *out, cudaStream_t st, Profiler *prof = nullptr, double alg_bytes = 0,
-                             int g_base = 0, bool store_natural = true) {
+                             int g_base = 0, bool store_natural = true, const MacTcPlan *tc = nullptr) {
     if (n_groups <= 0 || n_go <= 0) return BCN_OK;
     if (K > kMaxMacTaps) return fail(BCN_E_INVAL, "MAC fan-in above 2^20");
+    if (tc != nullptr && tc->w16 != nullptr) {
+        Timed tm(prof, st, BCN_KERNEL_MAC, alg_bytes);
+        return launch_mac_tc(c, *tc, level, K, n_groups, n_go, gidx, gout, in, pt, out, st, g_base, store_natural);
+    }
     const int N = c->N;
     const int OT = std::min(8, n_go);
     const int tiles = (n_go + OT - 1) / OT;
@@ -371,8 +375,11 @@ bcn_status device_ctx_init(bcn_ctx *c) {
     if (cudaMalloc(&c->d_pc, sizeof(PrimeConst) * P) != cudaSuccess ||
         cudaMalloc(&c->d_tw_fwd, sizeof(uint2) * (size_t)P * N) != cudaSuccess ||
         cudaMalloc(&c->d_tw_inv, sizeof(uint2) * (size_t)P * N) != cudaSuccess ||
-        cudaMalloc(&c->d_ks, sizeof(uint32_t) * c->ks.host.size()) != cudaSuccess)
+        cudaMalloc(&c->d_ks, sizeof(uint32_t) * c->ks.host.size()) != cudaSuccess ||
+        cudaMalloc(&c->d_status, sizeof(uint32_t)) != cudaSuccess)
         return fail(BCN_E_NOMEM, "device allocation of the context tables failed");
+    if (cudaMemset(c->d_status, 0, sizeof(uint32_t)) != cudaSuccess)
+        return fail(BCN_E_CUDA, "clearing the device status word failed");
     bool ok = cudaMemcpy(c->d_pc, c->h_pc.data(), sizeof(PrimeConst) * P, cudaMemcpyHostToDevice) == cudaSuccess;
     for (int t = 0; t < P && ok; t++) {
         ok = cudaMemcpy(c->d_tw_fwd + (size_t)t * N, c->h_tw_fwd[t].data(), sizeof(uint2) * N,
@@ -384,6 +391,7 @@ bcn_status device_ctx_init(bcn_ctx *c) {
                           cudaMemcpyHostToDevice) == cudaSuccess;
     if (!ok) return fail(BCN_E_CUDA, "upload of the context tables failed");
     BCN_TRY(cores_setup_all());
+    BCN_TRY(mac_tc_setup());
     const int mac_smem = kMacTapChunk * 4 * (1 + 8);
 #define BCN_MSETUP(OTV)                                                                                           \
     if (cudaFuncSetAttribute(k_mac_grouped<OTV>, cudaFuncAttributeMaxDynamicSharedMemorySize, mac_smem) !=      \
@@ -399,6 +407,8 @@ void device_ctx_free(bcn_ctx *c) {
     cudaFree(c->d_tw_fwd);
     cudaFree(c->d_tw_inv);
     cudaFree(c->d_ks);
+    cudaFree(c->d_status);
+    c->d_status = nullptr;
     c->d_pc = nullptr;
     c->d_tw_fwd = c->d_tw_inv = nullptr;
     c->d_ks = nullptr;
@@ -528,6 +538,11 @@ bcn_status bcn_model_create(bcn_ctx *c, const bcn_layer *layers, int n_layers, b
             cudaMemcpy(q.d_gw, gw.data(), gw.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(q.d_gout, gout.data(), gout.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
             return cleanup(BCN_E_CUDA, "upload of layer tables failed");
+        if (mac_tc_eligible(c, q.K, q.n_go)) {
+            // conv and dense weights are [n_go][K] in tap order, the same for every group
+            bcn_status s = mac_tc_plan(c, q.K, q.n_go, L.w_int, &q.tc);
+            if (s != BCN_OK) return cleanup(s, bcn_last_error());
+        }
         if (p.square) level -= 1;
         prev_out = p.n_out;
         prev_perm.assign(p.n_out, 0);  // natural index -> group-major position
@@ -547,12 +562,28 @@ bcn_status bcn_model_set_chunk(bcn_model *m, int chunk) {
     return BCN_OK;
 }
 
+bcn_status bcn_model_set_mac_impl(bcn_model *m, int impl) {
+    if (!m || impl < 0 || impl > 1) return fail(BCN_E_INVAL, "bcn_model_set_mac_impl: bad argument");
+    m->mac_impl = impl;
+    return BCN_OK;
+}
+
+bcn_status bcn_device_status(const bcn_ctx *c, uint32_t *status) {
+    if (!c || !status) return fail(BCN_E_INVAL, "bcn_device_status: null argument");
+    BCN_TRY(check_device(c));
+    if (cudaMemcpy(status, c->d_status, 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemset(c->d_status, 0, 4) != cudaSuccess)
+        return fail(BCN_E_CUDA, "bcn_device_status: reading the status word failed");
+    return BCN_OK;
+}
+
 bcn_status bcn_model_destroy(bcn_model *m) {
     if (!m) return BCN_OK;
     for (auto &p : m->layers) {
         cudaFree(p.d_gidx);
         cudaFree(p.d_gw);
         cudaFree(p.d_gout);
+        cudaFree(p.tc.w16);
     }
     for (auto e : m->prof.ev) cudaEventDestroy(e);
     delete m;
@@ -651,7 +682,7 @@ bcn_status bcn_eval(const bcn_model *m, const uint32_t *evk, const uint32_t *cts
             const double mac_bytes = limb * ((double)p.n_distinct_in * 2 * p.level + (double)p.n_out * 2 * p.level +
                                              (pt ? (double)p.n_out * p.level : 0.0));
             BCN_TRY(launch_mac(c, p.level, p.K, p.n_groups, p.n_go, p.d_gidx, p.d_gw, p.d_gout, x, pt, y, st, prof,
-                               mac_bytes, 0, last));
+                               mac_bytes, 0, last, m->mac_impl == 0 ? &p.tc : nullptr));
         } else {
             const int n = p.level;
             const int gpc = std::max(1, m->chunk / p.n_go);  // whole groups per chunk
@@ -661,7 +692,7 @@ bcn_status bcn_eval(const bcn_model *m, const uint32_t *evk, const uint32_t *cts
                 const double mac_bytes = limb * ((double)p.n_distinct_in * 2 * n * ng / p.n_groups +
                                                  (double)C * 2 * n + (pt ? (double)C * n : 0.0));
                 BCN_TRY(launch_mac(c, n, p.K, ng, p.n_go, p.d_gidx, p.d_gw, p.d_gout, x, pt, Ychunk, st, prof,
-                                   mac_bytes, g0, false));
+                                   mac_bytes, g0, false, m->mac_impl == 0 ? &p.tc : nullptr));
                 BCN_TRY(square_chunk(c, n, evk, Ychunk, b, C, y + (size_t)o0 * 2 * (n - 1) * N, st, prof));
             }
         }

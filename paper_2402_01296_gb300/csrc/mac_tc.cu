@@ -1,0 +1,307 @@
+// Integer-weight MAC on the fifth-generation tensor cores (tcgen05).
+//
+// The MAC of a layer group is a dense contraction
+//     out[o][col] = sum_t w[o][t] * x[t][col]   (exact, then mod q),
+// int8 weights times residues below 2^30 (Sec. 3.2: the ciphertext branch's
+// linear layers use integer weights, so a MAC is plain integer arithmetic on
+// the residues).  The tensor cores have no exact wide-integer path here, so a
+// residue is split into its 4 bytes and each byte plane is one fp16 GEMM:
+// bytes (0..255) and weights (-127..127) are exact in fp16, their products are
+// exact, and every partial sum of at most 512 taps stays below
+// 512 * 255 * 127 < 2^24 in magnitude, so the fp32 accumulation in tensor
+// memory is exact.  The epilogue recombines the planes in int64
+// (sum_b plane_b * 2^{8b}), adds a multiple of q that makes the sum
+// non-negative and reduces mod q (Barrett), then adds the feature plaintext.
+//
+// One CTA: 128 coefficient columns (the MMA's M, one tensor-memory lane
+// each) x one tile of at most 64 outputs (N, padded to a multiple of 16) of
+// one group, all taps.  The weights of the tile are staged once in shared
+// memory (B, K-major); the residues pass through shared memory in slabs of 64
+// taps (A, K-major, 4 planes), written by the thread that owns the column.
+// One elected thread issues the MMAs and commits them to an mbarrier; the
+// wait on it is bounded and records a status word on timeout.  Operand layout
+// is the no-swizzle canonical K-major form: 8 rows x 16 bytes per core matrix,
+// core matrices 128 bytes apart along K (LBO) and one row group apart along
+// M/N (SBO).
+#include <algorithm>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "device_api.h"
+#include "device_math.cuh"
+
+namespace bcn {
+
+namespace {
+
+constexpr int kRows = 128;     // columns per CTA (MMA M)
+constexpr int kSlab = 64;      // taps per A slab
+constexpr int kPlanes = 4;     // bytes of a residue
+constexpr int kPlaneBytes = kRows * kSlab * 2;
+constexpr int kABytes = kPlanes * kPlaneBytes;  // 64 KiB
+constexpr uint32_t kSboA = (kSlab / 8) * 128;   // bytes between row groups of a slab
+constexpr int kWaitLimit = 1 << 20;             // mbarrier polls before giving up
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: start, LBO, SBO (bytes, 16-byte units),
+// descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t mat_desc(uint32_t start, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((start >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+// instruction descriptor, kind::f16: fp32 accumulator, fp16 A and B, both K-major
+__host__ __device__ constexpr uint32_t instr_desc(int M, int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// two residues' byte b as fp16 pair (tap k in the low half, tap k+1 in the high)
+__device__ __forceinline__ uint32_t byte_pair(uint32_t x0, uint32_t x1, int b) {
+    const uint32_t sel = (uint32_t)b | ((uint32_t)b << 4) | ((uint32_t)(4 + b) << 8) | ((uint32_t)(4 + b) << 12);
+    uint32_t v = (__byte_perm(x0, x1, sel) & 0x00FF00FFu) | 0x64006400u;  // 1024 + byte
+    __half2 h = *reinterpret_cast<__half2 *>(&v);
+    h = __hsub2(h, __half2(__ushort_as_half(0x6400), __ushort_as_half(0x6400)));  // exact byte
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+    for (int i = 0; i < kWaitLimit; i++) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t addr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(addr));
+}
+
+}  // namespace
+
+// grid (2 level N / 128, n_groups * tiles), 128 threads.  w16: per output tile
+// the fp16 weights [NT][Kpad] in the canonical K-major layout (zero rows past
+// the tile's outputs, zero columns past K).
+__global__ void __launch_bounds__(kRows) k_mac_tc(const uint32_t *__restrict__ in, uint32_t *__restrict__ out,
+                                                  const int32_t *__restrict__ gidx, const uint4 *__restrict__ w16,
+                                                  const int32_t *__restrict__ gout, const uint32_t *__restrict__ pt,
+                                                  int K, int Kpad, int n_go, int tile_out, int NT, int tiles,
+                                                  int level, int N, int g_base, int store_natural,
+                                                  const PrimeConst *__restrict__ pc, uint32_t tmem_cols,
+                                                  uint32_t *__restrict__ status) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned char *A = sm;
+    unsigned char *B = sm + kABytes;
+    int32_t *sidx = reinterpret_cast<int32_t *>(B + (size_t)NT * Kpad * 2);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(sidx + Kpad + (Kpad & 1));
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
+    volatile int *flag = reinterpret_cast<volatile int *>(tslot + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int g = g_base + (int)blockIdx.y / tiles, tile = (int)blockIdx.y % tiles;
+    const int o0 = tile * tile_out, no = min(tile_out, n_go - o0);
+    const size_t cols = (size_t)2 * level * N;
+    const size_t col = (size_t)blockIdx.x * kRows + tid;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
+                     "r"(tmem_cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        *flag = 0;
+    }
+    {
+        const uint4 *src = w16 + (size_t)tile * ((size_t)NT * Kpad * 2 / 16);
+        uint4 *dst = reinterpret_cast<uint4 *>(B);
+        for (int i = tid; i < NT * Kpad * 2 / 16; i += kRows) dst[i] = __ldg(src + i);
+        for (int t = tid; t < Kpad; t += kRows) sidx[t] = t < K ? gidx[(size_t)g * K + t] : -1;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = *tslot;
+    const uint32_t a_base = smem_addr(A), b_base = smem_addr(B), mb = smem_addr(mbar);
+    const uint32_t idesc = instr_desc(kRows, NT);
+    const uint32_t sbo_b = (uint32_t)(Kpad / 8) * 128;
+    uint32_t parity = 0;
+
+    for (int t0 = 0; t0 < Kpad; t0 += kSlab) {
+        const int ks = min(kSlab, Kpad - t0);  // a multiple of 16
+        // this thread's column, 16 taps at a time, into the 4 planes of the slab
+        for (int t16 = 0; t16 < ks; t16 += 16) {
+            uint32_t x[16];
+#pragma unroll
+            for (int j = 0; j < 16; j++) {
+                const int s = sidx[t0 + t16 + j];
+                x[j] = s >= 0 ? __ldg(in + (size_t)s * cols + col) : 0u;
+            }
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int t8 = t16 + 8 * h;
+                const uint32_t off = (uint32_t)(tid >> 3) * kSboA + (uint32_t)(t8 >> 3) * 128 + (tid & 7) * 16;
+#pragma unroll
+                for (int b = 0; b < kPlanes; b++) {
+                    uint4 v;
+                    v.x = byte_pair(x[8 * h + 0], x[8 * h + 1], b);
+                    v.y = byte_pair(x[8 * h + 2], x[8 * h + 3], b);
+                    v.z = byte_pair(x[8 * h + 4], x[8 * h + 5], b);
+                    v.w = byte_pair(x[8 * h + 6], x[8 * h + 7], b);
+                    *reinterpret_cast<uint4 *>(A + b * kPlaneBytes + off) = v;
+                }
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll 1
+            for (int b = 0; b < kPlanes; b++) {
+#pragma unroll 1
+                for (int j = 0; j < ks / 16; j++) {
+                    const uint64_t ad = mat_desc(a_base + b * kPlaneBytes + j * 256, 128, kSboA);
+                    const uint64_t bd = mat_desc(b_base + (uint32_t)(t0 / 16 + j) * 256, 128, sbo_b);
+                    const uint32_t d = tmem + (uint32_t)(b * NT);
+                    const uint32_t acc = (t0 > 0 || j > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\t"
+                        "setp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb));
+            if (!mbar_wait(mb, parity)) *flag = 1;
+        }
+        parity ^= 1;
+        __syncthreads();  // the slab is free again (or the wait gave up)
+        if (*flag) break;
+    }
+
+    if (*flag == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t lanes = tmem + ((uint32_t)(warp * 32) << 16);
+        const int i = (int)((col / N) % level), poly = (int)(col / ((size_t)level * N));
+        const uint32_t q = pc[i].q;
+        const uint64_t mu = pc[i].barrett;
+        const long long offs = (long long)pc[i].mac_offset;
+        for (int ob = 0; ob < NT; ob += 16) {
+            uint32_t f[kPlanes][16];
+#pragma unroll
+            for (int b = 0; b < kPlanes; b++) tmem_ld16(lanes + (uint32_t)(b * NT + ob), f[b]);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int o = 0; o < 16; o++) {
+                if (ob + o >= no) break;
+                long long v = offs;
+#pragma unroll
+                for (int b = 0; b < kPlanes; b++)
+                    v += (long long)__float2int_rn(__uint_as_float(f[b][o])) << (8 * b);
+                uint32_t r = barrett_reduce64((uint64_t)v, q, mu);
+                const int og = gout != nullptr ? gout[(size_t)g * n_go + o0 + ob + o] : g * n_go + o0 + ob + o;
+                const int os = store_natural ? og : (g - g_base) * n_go + o0 + ob + o;
+                if (pt != nullptr && poly == 0) r = add_mod(r, __ldg(pt + (size_t)og * level * N + col), q);
+                out[(size_t)os * cols + col] = r;
+            }
+        }
+    } else if (tid == 0) {
+        atomicOr(status, 1u);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
+    }
+}
+
+// ------------------------------------------------------------------ host side
+static uint16_t half_of_int(int v) {  // exact for |v| < 2048
+    if (v == 0) return 0;
+    const uint16_t s = v < 0 ? 0x8000 : 0;
+    int a = v < 0 ? -v : v, e = 0;
+    while ((a >> (e + 1)) != 0) e++;
+    const uint16_t mant = (uint16_t)(((uint32_t)a << (10 - e)) & 0x3FF);
+    return (uint16_t)(s | ((e + 15) << 10) | mant);
+}
+
+bool mac_tc_eligible(const bcn_ctx *c, int K, int n_go) {
+    return K >= 1 && K <= kMacTcMaxTaps && n_go >= kMacTcMinOutputs && c->N >= kRows && c->N % kRows == 0;
+}
+
+size_t mac_tc_smem(int NT, int Kpad) {
+    return (size_t)kABytes + (size_t)NT * Kpad * 2 + (size_t)(Kpad + 2) * 4 + 1024;
+}
+
+bcn_status mac_tc_plan(const bcn_ctx *c, int K, int n_go, const int8_t *w, MacTcPlan *p) {
+    const int tiles = (n_go + 63) / 64;
+    const int tile_out = (n_go + tiles - 1) / tiles;
+    const int NT = (tile_out + 15) / 16 * 16, Kpad = (K + 15) / 16 * 16;
+    uint32_t cols = 32;
+    while (cols < (uint32_t)(kPlanes * NT)) cols *= 2;
+    // weights per tile in the canonical K-major layout
+    std::vector<uint16_t> h((size_t)tiles * NT * Kpad, 0);
+    for (int tt = 0; tt < tiles; tt++) {
+        const int o0 = tt * tile_out, no = std::min(tile_out, n_go - o0);
+        uint16_t *dst = h.data() + (size_t)tt * NT * Kpad;
+        for (int n = 0; n < no; n++)
+            for (int k = 0; k < K; k++)
+                dst[((size_t)(n / 8) * (Kpad / 8) + k / 8) * 64 + (n % 8) * 8 + (k % 8)] =
+                    half_of_int(w[(size_t)(o0 + n) * K + k]);
+    }
+    if (cudaMalloc(&p->w16, h.size() * 2) != cudaSuccess) return fail(BCN_E_NOMEM, "MAC weight tables");
+    if (cudaMemcpy(p->w16, h.data(), h.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(BCN_E_CUDA, "upload of the MAC weight tables failed");
+    // co-resident CTAs must fit the 512 tensor-memory columns of an SM: grow
+    // the shared-memory request until they do
+    size_t smem = mac_tc_smem(NT, Kpad);
+    for (;;) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_mac_tc, kRows, smem) != cudaSuccess)
+            return fail(BCN_E_CUDA, "occupancy query for the tensor-core MAC failed");
+        if (nb < 1) return fail(BCN_E_INVAL, "tensor-core MAC: shared memory does not fit");
+        if ((uint32_t)nb * cols <= 512) break;
+        smem += 4096;
+    }
+    p->tiles = tiles;
+    p->tile_out = tile_out;
+    p->NT = NT;
+    p->Kpad = Kpad;
+    p->tmem_cols = cols;
+    p->smem = smem;
+    return BCN_OK;
+}
+
+bcn_status mac_tc_setup() {
+    if (cudaFuncSetAttribute(k_mac_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) != cudaSuccess)
+        return fail(BCN_E_CUDA, "cudaFuncSetAttribute failed for the tensor-core MAC");
+    return BCN_OK;
+}
+
+bcn_status launch_mac_tc(const bcn_ctx *c, const MacTcPlan &p, int level, int K, int n_groups, int n_go,
+                         const int32_t *gidx, const int32_t *gout, const uint32_t *in, const uint32_t *pt,
+                         uint32_t *out, cudaStream_t st, int g_base, bool store_natural) {
+    const size_t cols = (size_t)2 * level * c->N;
+    if ((long long)n_groups * p.tiles > 65535) return fail(BCN_E_INVAL, "MAC layer with more than 65535 output tiles");
+    dim3 grid((unsigned)(cols / kRows), (unsigned)(n_groups * p.tiles));
+    k_mac_tc<<<grid, kRows, p.smem, st>>>(in, out, gidx, reinterpret_cast<const uint4 *>(p.w16), gout, pt, K, p.Kpad,
+                                          n_go, p.tile_out, p.NT, p.tiles, level, c->N, g_base,
+                                          store_natural ? 1 : 0, c->d_pc, p.tmem_cols, c->d_status);
+    return check_launch("k_mac_tc");
+}
+
+}  // namespace bcn
