@@ -125,6 +125,20 @@ __device__ __forceinline__ void ks_core_body(const uint32_t *__restrict__ D, con
                                              const uint2 *__restrict__ twf, const uint2 *__restrict__ twi) {
     using C = NttCore<LOGN, R, LAZY>;
     constexpr int N = C::N, T = C::T;
+    // running sums r0 += x k0 / R, r1 += x k1 / R: kept in [0, 2q) with lazy
+    // Montgomery products on the data primes (the lazy inverse NTT takes
+    // [0, 2q)), canonical on the special primes
+    auto ks_accumulate = [](uint32_t &r0, uint32_t &r1, uint32_t xv, uint32_t w0, uint32_t w1,
+                            const PrimeConst &P) {
+        if constexpr (LAZY) {
+            const uint32_t q2 = 2 * P.q;
+            r0 = reduce_once(r0 + mont_mul_lazy(xv, w0, P.q, P.qneg_inv), q2);
+            r1 = reduce_once(r1 + mont_mul_lazy(xv, w1, P.q, P.qneg_inv), q2);
+        } else {
+            r0 = add_mod(r0, mont_mul(xv, w0, P.q, P.qneg_inv), P.q);
+            r1 = add_mod(r1, mont_mul(xv, w1, P.q, P.qneg_inv), P.q);
+        }
+    };
     extern __shared__ __align__(16) uint32_t sm[];
     // exchange buffer, then the two running sums in thread-private slots u*T + tid
     uint32_t *s0 = sm + C::SMEM_WORDS, *s1 = s0 + N;
@@ -186,11 +200,8 @@ __device__ __forceinline__ void ks_core_body(const uint32_t *__restrict__ D, con
                 const uint4 v1 = __ldg(reinterpret_cast<const uint4 *>(k1 + e));
                 const uint32_t w0[4] = {v0.x, v0.y, v0.z, v0.w}, w1[4] = {v1.x, v1.y, v1.z, v1.w};
 #pragma unroll
-                for (int z = 0; z < 4; z++) {
-                    uint32_t &r0 = s0[(u + z) * T + tid], &r1 = s1[(u + z) * T + tid];
-                    r0 = add_mod(r0, mont_mul(x[u + z], w0[z], P.q, P.qneg_inv), P.q);
-                    r1 = add_mod(r1, mont_mul(x[u + z], w1[z], P.q, P.qneg_inv), P.q);
-                }
+                for (int z = 0; z < 4; z++) ks_accumulate(s0[(u + z) * T + tid], s1[(u + z) * T + tid], x[u + z],
+                                                          w0[z], w1[z], P);
             }
         } else if constexpr (C::NTT_PAIRS) {
 #pragma unroll
@@ -200,19 +211,14 @@ __device__ __forceinline__ void ks_core_body(const uint32_t *__restrict__ D, con
                 const uint2 v1 = __ldg(reinterpret_cast<const uint2 *>(k1 + e));
                 const uint32_t w0[2] = {v0.x, v0.y}, w1[2] = {v1.x, v1.y};
 #pragma unroll
-                for (int z = 0; z < 2; z++) {
-                    uint32_t &r0 = s0[(u + z) * T + tid], &r1 = s1[(u + z) * T + tid];
-                    r0 = add_mod(r0, mont_mul(x[u + z], w0[z], P.q, P.qneg_inv), P.q);
-                    r1 = add_mod(r1, mont_mul(x[u + z], w1[z], P.q, P.qneg_inv), P.q);
-                }
+                for (int z = 0; z < 2; z++) ks_accumulate(s0[(u + z) * T + tid], s1[(u + z) * T + tid], x[u + z],
+                                                          w0[z], w1[z], P);
             }
         } else {
 #pragma unroll
             for (int u = 0; u < R; u++) {
                 const int e = C::ntt_elem(u, tid);
-                uint32_t &r0 = s0[u * T + tid], &r1 = s1[u * T + tid];
-                r0 = add_mod(r0, mont_mul(x[u], __ldg(k0 + e), P.q, P.qneg_inv), P.q);
-                r1 = add_mod(r1, mont_mul(x[u], __ldg(k1 + e), P.q, P.qneg_inv), P.q);
+                ks_accumulate(s0[u * T + tid], s1[u * T + tid], x[u], __ldg(k0 + e), __ldg(k1 + e), P);
             }
         }
     }

@@ -79,7 +79,10 @@ bcn_status launch_ntt(const bcn_ctx *c, uint32_t *data, size_t n_limbs, const Pr
 
 // Tensor-core MAC (mac_tc.cu): used for groups of at least kMacTcMinOutputs
 // outputs and at most kMacTcMaxTaps taps (the fp32 sums stay exact).
-constexpr int kMacTcMaxTaps = 512, kMacTcMinOutputs = 32;
+#ifndef BCN_TC_MIN_OUTPUTS
+#define BCN_TC_MIN_OUTPUTS 32
+#endif
+constexpr int kMacTcMaxTaps = 512, kMacTcMinOutputs = BCN_TC_MIN_OUTPUTS;
 bool mac_tc_eligible(const bcn_ctx *c, int K, int n_go);
 // w: [n_go][K] int8 weights shared by every group
 bcn_status mac_tc_plan(const bcn_ctx *c, int K, int n_go, const int8_t *w, MacTcPlan *p);

@@ -42,6 +42,13 @@ __device__ __forceinline__ uint32_t mont_mul(uint32_t a, uint32_t b, uint32_t q,
     return reduce_once(u, q);
 }
 
+// a * b * 2^-32 mod q up to one q: result in [0, 2q), for a < 4q, b < q, q < 2^30
+__device__ __forceinline__ uint32_t mont_mul_lazy(uint32_t a, uint32_t b, uint32_t q, uint32_t qneg_inv) {
+    uint64_t t = (uint64_t)a * b;
+    uint32_t m = (uint32_t)t * qneg_inv;
+    return (uint32_t)((t + (uint64_t)m * q) >> 32);
+}
+
 // x mod q for any x < 2^64 (mu = floor(2^64 / q))
 __device__ __forceinline__ uint32_t barrett_reduce64(uint64_t x, uint32_t q, uint64_t mu) {
     uint64_t qh = __umul64hi(x, mu);

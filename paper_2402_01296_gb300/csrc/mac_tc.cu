@@ -16,8 +16,9 @@
 // One CTA: 128 coefficient columns (the MMA's M, one tensor-memory lane
 // each) x one tile of at most 64 outputs (N, padded to a multiple of 16) of
 // one group, all taps.  The weights of the tile are staged once in shared
-// memory (B, K-major); the residues pass through shared memory in slabs of 64
-// taps (A, K-major, 4 planes), written by the thread that owns the column.
+// memory (B, K-major); the residues of 32 taps at a time arrive by cp.async in
+// a ring of 3 stages (two slabs load while one converts) and are split into
+// the 4 fp16 planes of A (K-major) by the two threads that own the column.
 // One elected thread issues the MMAs and commits them to an mbarrier; the
 // wait on it is bounded and records a status word on timeout.  Operand layout
 // is the no-swizzle canonical K-major form: 8 rows x 16 bytes per core matrix,
@@ -34,13 +35,16 @@ namespace bcn {
 
 namespace {
 
-constexpr int kRows = 128;     // columns per CTA (MMA M)
-constexpr int kSlab = 64;      // taps per A slab
-constexpr int kPlanes = 4;     // bytes of a residue
-constexpr int kPlaneBytes = kRows * kSlab * 2;
-constexpr int kABytes = kPlanes * kPlaneBytes;  // 64 KiB
-constexpr uint32_t kSboA = (kSlab / 8) * 128;   // bytes between row groups of a slab
-constexpr int kWaitLimit = 1 << 20;             // mbarrier polls before giving up
+constexpr int kRows = 128;                       // columns per CTA (MMA M)
+constexpr int kThreads = 256;                    // two threads per column
+constexpr int kSlab = 32;                        // taps per slab
+constexpr int kPlanes = 4;                       // bytes of a residue
+constexpr int kStages = 3;                       // raw slabs in shared memory
+constexpr int kStageBytes = kSlab * kRows * 4;   // raw residues of one slab (16 KiB)
+constexpr int kPlaneBytes = kRows * kSlab * 2;   // one fp16 plane of a slab (8 KiB)
+constexpr int kABytes = kPlanes * kPlaneBytes;   // 32 KiB
+constexpr uint32_t kSboA = (kSlab / 8) * 128;    // bytes between row groups of a plane
+constexpr int kWaitLimit = 1 << 20;              // mbarrier polls before giving up
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -65,6 +69,15 @@ __device__ __forceinline__ uint32_t byte_pair(uint32_t x0, uint32_t x1, int b) {
     return *reinterpret_cast<uint32_t *>(&h);
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t addr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(addr));
+}
+
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
     for (int i = 0; i < kWaitLimit; i++) {
         uint32_t done;
@@ -80,40 +93,55 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
     return false;
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t addr, uint32_t (&r)[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(addr));
+// 16-byte asynchronous copy global -> shared; zero-filled when !valid
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool valid) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+
+// residues of slab taps [t0, t0 + kSlab) of columns [col0, col0 + 128) into a
+// stage ([tap][column] words), as one cp.async group
+__device__ __forceinline__ void stage_slab(uint32_t stage, const uint32_t *__restrict__ in, const int32_t *sidx,
+                                           int t0, size_t cols, size_t col0, int tid) {
+#pragma unroll
+    for (int i = 0; i < kStageBytes / 16 / kThreads; i++) {
+        const int c = tid + i * kThreads, tap = c >> 5, q4 = c & 31;
+        const int s = sidx[t0 + tap];
+        const uint32_t *src = s >= 0 ? in + (size_t)s * cols + col0 + 4 * q4 : in;
+        cp_async16(stage + (uint32_t)(tap * kRows * 4 + q4 * 16), src, s >= 0);
+    }
 }
 
 }  // namespace
 
-// grid (2 level N / 128, n_groups * tiles), 128 threads.  w16: per output tile
+// grid (2 level N / 128, n_groups * tiles), 256 threads.  w16: per output tile
 // the fp16 weights [NT][Kpad] in the canonical K-major layout (zero rows past
-// the tile's outputs, zero columns past K).
-__global__ void __launch_bounds__(kRows) k_mac_tc(const uint32_t *__restrict__ in, uint32_t *__restrict__ out,
-                                                  const int32_t *__restrict__ gidx, const uint4 *__restrict__ w16,
-                                                  const int32_t *__restrict__ gout, const uint32_t *__restrict__ pt,
-                                                  int K, int Kpad, int n_go, int tile_out, int NT, int tiles,
-                                                  int level, int N, int g_base, int store_natural,
-                                                  const PrimeConst *__restrict__ pc, uint32_t tmem_cols,
-                                                  uint32_t *__restrict__ status) {
+// the tile's outputs, zero columns past K).  Kpad is a multiple of kSlab.
+// Shared memory: kStages raw stages (cp.async, kStages - 1 slabs in flight
+// ahead of the one being converted), the fp16 planes of one slab (A), the
+// tile's weights (B), the tap indices, the mbarrier.
+__global__ void __launch_bounds__(kThreads) k_mac_tc(const uint32_t *__restrict__ in, uint32_t *__restrict__ out,
+                                                     const int32_t *__restrict__ gidx, const uint4 *__restrict__ w16,
+                                                     const int32_t *__restrict__ gout,
+                                                     const uint32_t *__restrict__ pt, int K, int Kpad, int n_go,
+                                                     int tile_out, int NT, int tiles, int level, int N, int g_base,
+                                                     int store_natural, const PrimeConst *__restrict__ pc,
+                                                     uint32_t tmem_cols, uint32_t *__restrict__ status) {
     extern __shared__ __align__(1024) unsigned char sm[];
-    unsigned char *A = sm;
-    unsigned char *B = sm + kABytes;
+    unsigned char *S = sm;                          // [kStages][kSlab][kRows] u32
+    unsigned char *A = sm + kStages * kStageBytes;  // [kPlanes] planes
+    unsigned char *B = A + kABytes;                 // [NT][Kpad] fp16
     int32_t *sidx = reinterpret_cast<int32_t *>(B + (size_t)NT * Kpad * 2);
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(sidx + Kpad + (Kpad & 1));
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(sidx + Kpad);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
     volatile int *flag = reinterpret_cast<volatile int *>(tslot + 1);
 
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, r = tid & (kRows - 1), half = tid >> 7;
     const int g = g_base + (int)blockIdx.y / tiles, tile = (int)blockIdx.y % tiles;
     const int o0 = tile * tile_out, no = min(tile_out, n_go - o0);
     const size_t cols = (size_t)2 * level * N;
-    const size_t col = (size_t)blockIdx.x * kRows + tid;
+    const size_t col0 = (size_t)blockIdx.x * kRows, col = col0 + r;
+    const int n_slabs = Kpad / kSlab;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
@@ -125,11 +153,18 @@ __global__ void __launch_bounds__(kRows) k_mac_tc(const uint32_t *__restrict__ i
         asm volatile("fence.mbarrier_init.release.cluster;");
         *flag = 0;
     }
+    for (int t = tid; t < Kpad; t += kThreads) sidx[t] = t < K ? gidx[(size_t)g * K + t] : -1;
+    __syncthreads();  // sidx
+    const uint32_t s_base = smem_addr(S);
+#pragma unroll
+    for (int k = 0; k < kStages - 1; k++) {  // the first slabs, one cp.async group each
+        if (k < n_slabs) stage_slab(s_base + (uint32_t)(k * kStageBytes), in, sidx, k * kSlab, cols, col0, tid);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
     {
         const uint4 *src = w16 + (size_t)tile * ((size_t)NT * Kpad * 2 / 16);
         uint4 *dst = reinterpret_cast<uint4 *>(B);
-        for (int i = tid; i < NT * Kpad * 2 / 16; i += kRows) dst[i] = __ldg(src + i);
-        for (int t = tid; t < Kpad; t += kRows) sidx[t] = t < K ? gidx[(size_t)g * K + t] : -1;
+        for (int i = tid; i < NT * Kpad * 2 / 16; i += kThreads) dst[i] = __ldg(src + i);
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -138,22 +173,28 @@ __global__ void __launch_bounds__(kRows) k_mac_tc(const uint32_t *__restrict__ i
     const uint32_t a_base = smem_addr(A), b_base = smem_addr(B), mb = smem_addr(mbar);
     const uint32_t idesc = instr_desc(kRows, NT);
     const uint32_t sbo_b = (uint32_t)(Kpad / 8) * 128;
-    uint32_t parity = 0;
 
-    for (int t0 = 0; t0 < Kpad; t0 += kSlab) {
-        const int ks = min(kSlab, Kpad - t0);  // a multiple of 16
-        // this thread's column, 16 taps at a time, into the 4 planes of the slab
-        for (int t16 = 0; t16 < ks; t16 += 16) {
+    for (int sl = 0; sl < n_slabs; sl++) {
+        // keep kStages - 1 slabs in flight: issue slab sl + kStages - 1 (its
+        // stage was converted at iteration sl - 1), then wait for slab sl
+        {
+            const int nx = sl + kStages - 1;
+            if (nx < n_slabs)
+                stage_slab(s_base + (uint32_t)((nx % kStages) * kStageBytes), in, sidx, nx * kSlab, cols, col0,
+                           tid);
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            asm volatile("cp.async.wait_group %0;" ::"n"(kStages - 1) : "memory");
+        }
+        __syncthreads();  // slab sl is in its stage for every thread; A is free
+        {
+            const uint32_t *st = reinterpret_cast<const uint32_t *>(S + (sl % kStages) * kStageBytes);
             uint32_t x[16];
 #pragma unroll
-            for (int j = 0; j < 16; j++) {
-                const int s = sidx[t0 + t16 + j];
-                x[j] = s >= 0 ? __ldg(in + (size_t)s * cols + col) : 0u;
-            }
+            for (int j = 0; j < 16; j++) x[j] = st[(16 * half + j) * kRows + r];
 #pragma unroll
             for (int h = 0; h < 2; h++) {
-                const int t8 = t16 + 8 * h;
-                const uint32_t off = (uint32_t)(tid >> 3) * kSboA + (uint32_t)(t8 >> 3) * 128 + (tid & 7) * 16;
+                const int t8 = 16 * half + 8 * h;
+                const uint32_t off = (uint32_t)(r >> 3) * kSboA + (uint32_t)(t8 >> 3) * 128 + (r & 7) * 16;
 #pragma unroll
                 for (int b = 0; b < kPlanes; b++) {
                     uint4 v;
@@ -169,14 +210,14 @@ __global__ void __launch_bounds__(kRows) k_mac_tc(const uint32_t *__restrict__ i
         __syncthreads();
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;");
-#pragma unroll 1
+#pragma unroll
             for (int b = 0; b < kPlanes; b++) {
-#pragma unroll 1
-                for (int j = 0; j < ks / 16; j++) {
+#pragma unroll
+                for (int j = 0; j < kSlab / 16; j++) {
                     const uint64_t ad = mat_desc(a_base + b * kPlaneBytes + j * 256, 128, kSboA);
-                    const uint64_t bd = mat_desc(b_base + (uint32_t)(t0 / 16 + j) * 256, 128, sbo_b);
+                    const uint64_t bd = mat_desc(b_base + (uint32_t)(sl * (kSlab / 16) + j) * 256, 128, sbo_b);
                     const uint32_t d = tmem + (uint32_t)(b * NT);
-                    const uint32_t acc = (t0 > 0 || j > 0) ? 1u : 0u;
+                    const uint32_t acc = (sl > 0 || j > 0) ? 1u : 0u;
                     asm volatile(
                         "{\n\t.reg .pred p;\n\t"
                         "setp.ne.b32 p, %4, 0;\n\t"
@@ -185,21 +226,23 @@ __global__ void __launch_bounds__(kRows) k_mac_tc(const uint32_t *__restrict__ i
                 }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb));
-            if (!mbar_wait(mb, parity)) *flag = 1;
+            if (!mbar_wait(mb, (uint32_t)(sl & 1))) *flag = 1;
         }
-        parity ^= 1;
-        __syncthreads();  // the slab is free again (or the wait gave up)
+        __syncthreads();  // the MMAs of this slab are done (or the wait gave up)
         if (*flag) break;
     }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
 
     if (*flag == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t lanes = tmem + ((uint32_t)(warp * 32) << 16);
+        // warp w reads tensor-memory lanes 32 (w mod 4) ..; the two warp halves
+        // take alternate blocks of 16 outputs
+        const uint32_t lanes = tmem + ((uint32_t)((warp & 3) * 32) << 16);
         const int i = (int)((col / N) % level), poly = (int)(col / ((size_t)level * N));
         const uint32_t q = pc[i].q;
         const uint64_t mu = pc[i].barrett;
         const long long offs = (long long)pc[i].mac_offset;
-        for (int ob = 0; ob < NT; ob += 16) {
+        for (int ob = 16 * half; ob < NT; ob += 32) {
             uint32_t f[kPlanes][16];
 #pragma unroll
             for (int b = 0; b < kPlanes; b++) tmem_ld16(lanes + (uint32_t)(b * NT + ob), f[b]);
@@ -211,11 +254,11 @@ __global__ void __launch_bounds__(kRows) k_mac_tc(const uint32_t *__restrict__ i
 #pragma unroll
                 for (int b = 0; b < kPlanes; b++)
                     v += (long long)__float2int_rn(__uint_as_float(f[b][o])) << (8 * b);
-                uint32_t r = barrett_reduce64((uint64_t)v, q, mu);
+                uint32_t res = barrett_reduce64((uint64_t)v, q, mu);
                 const int og = gout != nullptr ? gout[(size_t)g * n_go + o0 + ob + o] : g * n_go + o0 + ob + o;
                 const int os = store_natural ? og : (g - g_base) * n_go + o0 + ob + o;
-                if (pt != nullptr && poly == 0) r = add_mod(r, __ldg(pt + (size_t)og * level * N + col), q);
-                out[(size_t)os * cols + col] = r;
+                if (pt != nullptr && poly == 0) res = add_mod(res, __ldg(pt + (size_t)og * level * N + col), q);
+                out[(size_t)os * cols + col] = res;
             }
         }
     } else if (tid == 0) {
@@ -244,13 +287,13 @@ bool mac_tc_eligible(const bcn_ctx *c, int K, int n_go) {
 }
 
 size_t mac_tc_smem(int NT, int Kpad) {
-    return (size_t)kABytes + (size_t)NT * Kpad * 2 + (size_t)(Kpad + 2) * 4 + 1024;
+    return (size_t)kStages * kStageBytes + kABytes + (size_t)NT * Kpad * 2 + (size_t)Kpad * 4 + 16 + 1024;
 }
 
 bcn_status mac_tc_plan(const bcn_ctx *c, int K, int n_go, const int8_t *w, MacTcPlan *p) {
     const int tiles = (n_go + 63) / 64;
     const int tile_out = (n_go + tiles - 1) / tiles;
-    const int NT = (tile_out + 15) / 16 * 16, Kpad = (K + 15) / 16 * 16;
+    const int NT = (tile_out + 15) / 16 * 16, Kpad = (K + kSlab - 1) / kSlab * kSlab;
     uint32_t cols = 32;
     while (cols < (uint32_t)(kPlanes * NT)) cols *= 2;
     // weights per tile in the canonical K-major layout
@@ -271,7 +314,7 @@ bcn_status mac_tc_plan(const bcn_ctx *c, int K, int n_go, const int8_t *w, MacTc
     size_t smem = mac_tc_smem(NT, Kpad);
     for (;;) {
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_mac_tc, kRows, smem) != cudaSuccess)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_mac_tc, kThreads, smem) != cudaSuccess)
             return fail(BCN_E_CUDA, "occupancy query for the tensor-core MAC failed");
         if (nb < 1) return fail(BCN_E_INVAL, "tensor-core MAC: shared memory does not fit");
         if ((uint32_t)nb * cols <= 512) break;
@@ -298,7 +341,7 @@ bcn_status launch_mac_tc(const bcn_ctx *c, const MacTcPlan &p, int level, int K,
     const size_t cols = (size_t)2 * level * c->N;
     if ((long long)n_groups * p.tiles > 65535) return fail(BCN_E_INVAL, "MAC layer with more than 65535 output tiles");
     dim3 grid((unsigned)(cols / kRows), (unsigned)(n_groups * p.tiles));
-    k_mac_tc<<<grid, kRows, p.smem, st>>>(in, out, gidx, reinterpret_cast<const uint4 *>(p.w16), gout, pt, K, p.Kpad,
+    k_mac_tc<<<grid, kThreads, p.smem, st>>>(in, out, gidx, reinterpret_cast<const uint4 *>(p.w16), gout, pt, K, p.Kpad,
                                           n_go, p.tile_out, p.NT, p.tiles, level, c->N, g_base,
                                           store_natural ? 1 : 0, c->d_pc, p.tmem_cols, c->d_status);
     return check_launch("k_mac_tc");

@@ -90,12 +90,36 @@ struct NttCore {
     template <int P>
     __host__ __device__ static constexpr int pad_off(int u) { return padded(elem_def<P>(u, 0)); }
 
-    // Twiddle load that the compiler may not merge with the same load of another
-    // transform in the same kernel (merging keeps whole tables live in registers).
+    // Twiddle loads that the compiler may not merge with the same load of another
+    // transform in the same kernel (merging keeps whole tables live in registers);
+    // load_tw2 reads two consecutive entries (p 16-byte aligned).
     __device__ __forceinline__ static uint2 load_tw(const uint2 *p) {
         uint2 v;
         asm volatile("ld.global.nc.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
         return v;
+    }
+    __device__ __forceinline__ static uint4 load_tw2(const uint2 *p) {
+        uint4 v;
+        asm volatile("ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                     : "l"(p));
+        return v;
+    }
+    // twiddle of butterfly group b of stage KS: entries (1 << s) + (hi << KS) + b;
+    // for KS >= 1 the pair (b, b + 1), b even, is one 16-byte load
+    template <int KS>
+    __device__ __forceinline__ static void load_stage_tw(uint2 (&W)[1 << KS], const uint2 *tw, int s, int hi) {
+        const uint2 *p = tw + (1 << s) + (hi << KS);
+        if constexpr (KS == 0) {
+            W[0] = load_tw(p);
+        } else {
+#pragma unroll
+            for (int b = 0; b < (1 << KS); b += 2) {
+                const uint4 v = load_tw2(p + b);
+                W[b] = make_uint2(v.x, v.y);
+                W[b + 1] = make_uint2(v.z, v.w);
+            }
+        }
     }
 
     // FIRST: the first exchange of a transform (what ran before is unknown)
@@ -124,9 +148,11 @@ struct NttCore {
     __device__ __forceinline__ static void stage_fwd(uint32_t (&x)[R], int g, int hi, uint32_t q,
                                                      const uint2 *__restrict__ tw) {
         constexpr int rp = rp_of(P), s = s0_of(P) + KS, d = 1 << (rp - 1 - KS);
+        uint2 Wt[1 << KS];
+        load_stage_tw<KS>(Wt, tw, s, hi);
 #pragma unroll
         for (int b = 0; b < (1 << KS); b++) {
-            const uint2 W = load_tw(&tw[(1 << s) + (hi << KS) + b]);
+            const uint2 W = Wt[b];
 #pragma unroll
             for (int w = 0; w < d; w++) {
                 const int u = (g << rp) + b * 2 * d + w;
@@ -150,9 +176,11 @@ struct NttCore {
     __device__ __forceinline__ static void stage_inv(uint32_t (&x)[R], int g, int hi, uint32_t q,
                                                      const uint2 *__restrict__ tw) {
         constexpr int rp = rp_of(P), s = s0_of(P) + KS, d = 1 << (rp - 1 - KS);
+        uint2 Wt[1 << KS];
+        load_stage_tw<KS>(Wt, tw, s, hi);
 #pragma unroll
         for (int b = 0; b < (1 << KS); b++) {
-            const uint2 W = load_tw(&tw[(1 << s) + (hi << KS) + b]);
+            const uint2 W = Wt[b];
 #pragma unroll
             for (int w = 0; w < d; w++) {
                 const int u = (g << rp) + b * 2 * d + w;
