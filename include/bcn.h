@@ -122,7 +122,9 @@ bcn_status bcn_quantize(const float *w, size_t n, int8_t *w_int_out, double *s_w
 /* CKKS encode (App. A: N/2 slots per plaintext) of real vectors:
  * values [n_vec][B] (B <= N/2; slots B..N/2-1 are zero) at `scale` ->
  * pts_out [n_vec][level][N]: m_j = round(scale * (2/N) sum_k z_k cos(pi j 5^k / N)),
- * computed with an FFT in fp64.  BCN_E_SCALE if |m_j| >= 2^63. Host memory. */
+ * computed with an FFT in fp64; beyond 2^52 in magnitude m_j is the integer
+ * value of the fp64 product itself (which has no fractional part), reduced mod
+ * each prime.  BCN_E_SCALE if a product is not finite. Host memory. */
 bcn_status bcn_encode(const bcn_ctx *ctx, const double *values, int n_vec, int B, int level, double scale,
                       uint32_t *pts_out);
 
@@ -157,14 +159,23 @@ typedef enum {
     BCN_PLAIN_CONV = 0,     /* 2-D cross-correlation, weights [cout][cin][k][k], optional ReLU */
     BCN_PLAIN_AVGPOOL2 = 1, /* 2x2 average pool, stride 2 */
     BCN_PLAIN_TAP_CROP_CROT = 2, /* tap: centre crop to hc x wc, CRot weights [ch_c][ch_p] */
-    BCN_PLAIN_TAP_FC = 3    /* tap: fully connected, weights [n_out][C*H*W] */
+    BCN_PLAIN_TAP_FC = 3,   /* tap: fully connected, weights [n_out][C*H*W], then [n_out] bias if bias != 0 */
+    /* tap: the plaintext neurons of the two-layer feature integration (Sec. 3.3)
+     * and their contribution to the ciphertext neurons of the second layer:
+     *     h = sigma(W'_1 x_p + b'_1),  feature = W_2 h + b_2,
+     * x_p the flattened (c, y, x) map, sigma the square activation; weights
+     * W'_1 [n_hidden][C*H*W], b'_1 [n_hidden], W_2 [n_out][n_hidden], b_2 [n_out]
+     * back to back */
+    BCN_PLAIN_TAP_INTEGRATE = 4
 } bcn_plain_op;
 
 typedef struct {
     int op;               /* bcn_plain_op */
     int cin, cout, k, stride, pad, relu; /* BCN_PLAIN_CONV */
     int hc, wc, ch_c;     /* BCN_PLAIN_TAP_CROP_CROT */
-    int n_out;            /* BCN_PLAIN_TAP_FC */
+    int n_out;            /* BCN_PLAIN_TAP_FC, BCN_PLAIN_TAP_INTEGRATE */
+    int n_hidden;         /* BCN_PLAIN_TAP_INTEGRATE */
+    int bias;             /* BCN_PLAIN_TAP_FC: the weights are followed by a bias */
     const float *weights; /* host fp32, layout above (NULL for AVGPOOL2) */
 } bcn_plain_stage;
 

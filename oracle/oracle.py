@@ -277,29 +277,39 @@ def _cos_block(N: int, j0: int, j1: int, B: int) -> np.ndarray:
 
 def encode_coeffs(values: np.ndarray, N: int, scale: float) -> np.ndarray:
     """Real slot values z [n_vec][B] (B <= N/2, other slots 0) -> integer
-    coefficients m [n_vec][N] (int64) with
+    coefficients m [n_vec][N] with
         m_j = round(scale * (2/N) * sum_k z_k cos(pi j e_k / N)),
-    the inverse canonical embedding of a real vector, rounded half away from 0."""
+    the inverse canonical embedding of a real vector, rounded half away from 0.
+    int64 when every |m_j| < 2^63; otherwise an object array of Python ints,
+    each the exact integer value of the fp64 product (beyond 2^52 an fp64
+    number has no fractional part)."""
     values = np.atleast_2d(np.asarray(values, dtype=np.float64))
     n_vec, B = values.shape
     assert B <= N // 2
-    out = np.zeros((n_vec, N), dtype=np.int64)
+    out = np.zeros((n_vec, N), dtype=np.float64)
     step = 1024
     for j0 in range(0, N, step):
         j1 = min(N, j0 + step)
         M = _cos_block(N, j0, j1, B)  # [j][k]
         x = scale * (2.0 / N) * (values @ M.T)
-        r = round_half_away(x)
-        if np.any(np.abs(r) >= 2.0**63):
-            raise OverflowError("encoded coefficient beyond int64")
-        out[:, j0:j1] = r.astype(np.int64)
-    return out
+        out[:, j0:j1] = round_half_away(x)
+    if not np.all(np.isfinite(out)):
+        raise OverflowError("encoded coefficient is not finite")
+    if np.all(np.abs(out) < 2.0**63):
+        return out.astype(np.int64)
+    big = np.empty(out.shape, dtype=object)
+    big.flat[:] = [int(v) for v in out.flat]
+    return big
 
 
 def to_residues(m: np.ndarray, primes) -> np.ndarray:
-    """int64 coefficients [..][N] -> uint32 residues [..][len(primes)][N]."""
-    m = np.asarray(m, dtype=np.int64)
-    res = [np.mod(m, np.int64(q)).astype(np.uint32) for q in primes]
+    """Integer coefficients [..][N] (int64, or Python ints in an object array)
+    -> uint32 residues [..][len(primes)][N]."""
+    if m.dtype == object:
+        res = [np.mod(m, int(q)).astype(np.uint32) for q in primes]
+    else:
+        m = np.asarray(m, dtype=np.int64)
+        res = [np.mod(m, np.int64(q)).astype(np.uint32) for q in primes]
     return np.stack(res, axis=-2)
 
 
@@ -419,7 +429,9 @@ def plain_branch(cfg: dict, imgs: np.ndarray, noise: np.ndarray, weights) -> lis
     """fp64 plaintext branch with its unidirectional-connection taps:
     Resize = centre crop (offset floor((h_p - h_c)/2)), then CRot
     z^i = sum_j W^{i,j} y^j (Sec. 3.2); a dense tap is a fully connected map of
-    the flattened (c, y, x) trunk output.  Returns features [n][B] per tap."""
+    the flattened (c, y, x) trunk output (with an optional bias); an
+    integration tap is the plaintext half of the two-layer feature integration
+    (Sec. 3.3).  Returns features [n][B] per tap."""
     x = perturbed_input(cfg, imgs, noise)
     feats = []
     for st, wgt in zip(cfg["plain"], weights):
@@ -439,7 +451,20 @@ def plain_branch(cfg: dict, imgs: np.ndarray, noise: np.ndarray, weights) -> lis
             feats.append(np.ascontiguousarray(z.reshape(-1, B)))
         elif st["op"] == "tap_fc":
             B = x.shape[0]
-            feats.append(np.ascontiguousarray(wgt.astype(np.float64) @ x.reshape(B, -1).T))
+            wm, bias = wgt if isinstance(wgt, tuple) else (wgt, None)
+            z = wm.astype(np.float64) @ x.reshape(B, -1).T
+            if bias is not None:
+                z = z + bias.astype(np.float64)[:, None]
+            feats.append(np.ascontiguousarray(z))
+        elif st["op"] == "tap_integrate":
+            # Sec. 3.3: plaintext neurons x_p^<1> = sigma(W'_1 x_p + b'_1) of the
+            # first integration layer (sigma: the square activation), and their
+            # term W_2 x_p^<1> + b_2 of the second layer
+            B = x.shape[0]
+            w1, b1, w2, b2 = (a.astype(np.float64) for a in wgt)
+            h = w1 @ x.reshape(B, -1).T + b1[:, None]
+            h = h * h
+            feats.append(np.ascontiguousarray(w2 @ h + b2[:, None]))
         else:
             raise ValueError(st["op"])
     return feats

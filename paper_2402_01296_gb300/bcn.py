@@ -53,7 +53,8 @@ class _BatchItem(ctypes.Structure):
 
 class _PlainStage(ctypes.Structure):
     _fields_ = [("op", _I), ("cin", _I), ("cout", _I), ("k", _I), ("stride", _I), ("pad", _I), ("relu", _I),
-                ("hc", _I), ("wc", _I), ("ch_c", _I), ("n_out", _I), ("weights", _P)]
+                ("hc", _I), ("wc", _I), ("ch_c", _I), ("n_out", _I), ("n_hidden", _I), ("bias", _I),
+                ("weights", _P)]
 
 
 # name -> (restype, argtypes); restype _I means a bcn_status
@@ -523,7 +524,7 @@ def model_cost(model: "Model") -> float:
     return c.value
 
 
-PLAIN_OPS = {"conv": 0, "avgpool2": 1, "tap_crop_crot": 2, "tap_fc": 3}
+PLAIN_OPS = {"conv": 0, "avgpool2": 1, "tap_crop_crot": 2, "tap_fc": 3, "tap_integrate": 4}
 
 
 class PlainModel:
@@ -531,13 +532,17 @@ class PlainModel:
 
     def __init__(self, ctx: Context, stages: list, weights: list, image_hwc, seg):
         self.ctx = ctx
-        self._keep = [None if w is None else np.ascontiguousarray(w, dtype=np.float32) for w in weights]
+        # a stage's weights: one array, or a tuple of arrays laid out back to back
+        self._keep = [None if w is None else np.ascontiguousarray(
+            np.concatenate([np.ravel(a) for a in w]) if isinstance(w, tuple) else w, dtype=np.float32)
+            for w in weights]
         arr = (_PlainStage * len(stages))()
         for i, (s, w) in enumerate(zip(stages, self._keep)):
             a = arr[i]
             a.op = PLAIN_OPS[s["op"]]
-            for f in ("cin", "cout", "k", "stride", "pad", "hc", "wc", "ch_c", "n_out"):
+            for f in ("cin", "cout", "k", "stride", "pad", "hc", "wc", "ch_c", "n_out", "n_hidden"):
                 setattr(a, f, int(s.get(f, 0)))
+            a.bias = int(bool(s.get("bias", False)))
             a.relu = int(bool(s.get("relu", False)))
             a.weights = None if w is None else w.ctypes.data
         H, W, C = image_hwc

@@ -43,6 +43,20 @@ inline uint32_t from_signed(int64_t v, uint32_t q) {
     return (uint32_t)(r < 0 ? r + q : r);
 }
 
+// The integer a finite double x >= 2^52 in magnitude stands for (it has no
+// fractional part), mod q: x = mant * 2^e with an integer mant < 2^53.
+inline uint32_t big_mod(double x, uint32_t q) {
+    int e2 = 0;
+    const double f = std::frexp(std::fabs(x), &e2);  // |x| = f 2^e2, f in [0.5, 1)
+    const uint64_t mant = (uint64_t)std::ldexp(f, 53);
+    uint64_t r = mant % q, p2 = 2 % q;
+    for (int e = e2 - 53; e > 0; e >>= 1) {  // r * 2^(e2 - 53) mod q
+        if (e & 1) r = (uint64_t)(((unsigned __int128)r * p2) % q);
+        p2 = (uint64_t)(((unsigned __int128)p2 * p2) % q);
+    }
+    return x < 0 && r ? (uint32_t)(q - r) : (uint32_t)r;
+}
+
 // negacyclic NTT, bit-reversed output (Cooley-Tukey) / input (Gentleman-Sande)
 void ntt_fwd(const bcn_ctx *c, int t, uint32_t *a) {
     const uint32_t q = (uint32_t)c->primes[t];
@@ -237,13 +251,17 @@ bcn_status bcn_encode(const bcn_ctx *c, const double *values, int n_vec, int B, 
         uint32_t *out = pts + (size_t)v * level * N;
         for (int j = 0; j < N; j++) {
             double x = (twist[j] * y[j]).real() * (scale / N);
-            if (!(std::fabs(x) < 9.2e18)) { bad[v] = 1; return; }
-            long long m = std::llround(x);
-            for (int i = 0; i < level; i++) out[(size_t)i * N + j] = from_signed(m, (uint32_t)c->primes[i]);
+            if (!std::isfinite(x)) { bad[v] = 1; return; }
+            if (std::fabs(x) < 4503599627370496.0) {  // 2^52: round half away from zero
+                long long m = std::llround(x);
+                for (int i = 0; i < level; i++) out[(size_t)i * N + j] = from_signed(m, (uint32_t)c->primes[i]);
+            } else {  // already an integer
+                for (int i = 0; i < level; i++) out[(size_t)i * N + j] = big_mod(x, (uint32_t)c->primes[i]);
+            }
         }
     });
     for (int v = 0; v < n_vec; v++)
-        if (bad[v]) return fail(BCN_E_SCALE, "bcn_encode: a coefficient does not fit in 63 bits");
+        if (bad[v]) return fail(BCN_E_SCALE, "bcn_encode: a coefficient is not finite");
     return BCN_OK;
 }
 

@@ -4,7 +4,9 @@
 // to zero and the insensitive segment carries the client's perturbation
 // (Sec. 3.1 of the paper).  Each tap resizes a feature map to the ciphertext
 // branch's size by a centre crop and mixes channels with CRot,
-// z^i = sum_j W^{i,j} y^j (Sec. 3.2), or applies a fully connected map.
+// z^i = sum_j W^{i,j} y^j (Sec. 3.2), applies a fully connected map (with an
+// optional bias), or computes the plaintext half of the two-layer feature
+// integration (Sec. 3.3): W_2 sigma(W'_1 x_p + b'_1) + b_2.
 // Feature rows are written as [n_feat][B] so each row is one slot vector.
 #include <algorithm>
 #include <cuda_runtime.h>
@@ -88,15 +90,28 @@ __global__ void k_crop_crot(const float *__restrict__ act, const float *__restri
     feats[((size_t)row0 + f) * B + b] = acc;
 }
 
-// feats[row0 + o][b] = sum_k W[o][k] * act[b][k]
-__global__ void k_fc(const float *__restrict__ act, const float *__restrict__ wt, float *__restrict__ feats, int B,
-                     int K, int n_out, int row0) {
+// feats[row0 + o][b] = sum_k W[o][k] * act[b][k] (+ bias[o])
+__global__ void k_fc(const float *__restrict__ act, const float *__restrict__ wt, const float *__restrict__ bias,
+                     float *__restrict__ feats, int B, int K, int n_out, int row0) {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (size_t)n_out * B) return;
     const int b = (int)(i % B), o = (int)(i / B);
-    float acc = 0.0f;
+    float acc = bias != nullptr ? __ldg(bias + o) : 0.0f;
     for (int k = 0; k < K; k++) acc = fmaf(__ldg(wt + (size_t)o * K + k), act[(size_t)b * K + k], acc);
     feats[((size_t)row0 + o) * B + b] = acc;
+}
+
+// hidden[b][j] = (sum_k W[j][k] * act[b][k] + bias[j])^2: the plaintext neurons
+// of the first integration layer, square activation
+__global__ void k_fc_square(const float *__restrict__ act, const float *__restrict__ wt,
+                            const float *__restrict__ bias, float *__restrict__ hidden, int B, int K, int n_hidden) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)n_hidden * B) return;
+    const int j = (int)(i % n_hidden);
+    const size_t b = i / n_hidden;
+    float acc = __ldg(bias + j);
+    for (int k = 0; k < K; k++) acc = fmaf(__ldg(wt + (size_t)j * K + k), act[b * K + k], acc);
+    hidden[b * n_hidden + j] = acc * acc;
 }
 
 static unsigned blocks_for(size_t n) { return (unsigned)((n + 255) / 256); }
@@ -159,7 +174,16 @@ bcn_status bcn_plain_model_create(bcn_ctx *c, const bcn_plain_stage *st, int n, 
             s.feat_row = m->n_feat;
             s.n_feat = st[i].n_out;
             m->n_feat += s.n_feat;
-            nw = (size_t)st[i].n_out * ch * h * w;
+            nw = (size_t)st[i].n_out * ch * h * w + (st[i].bias ? (size_t)st[i].n_out : 0);
+            break;
+        case BCN_PLAIN_TAP_INTEGRATE:
+            if (st[i].n_out < 1 || st[i].n_hidden < 1) return bad("integration tap: bad size");
+            s.feat_row = m->n_feat;
+            s.n_feat = st[i].n_out;
+            m->n_feat += s.n_feat;
+            nw = (size_t)st[i].n_hidden * ch * h * w + st[i].n_hidden + (size_t)st[i].n_out * st[i].n_hidden +
+                 st[i].n_out;
+            m->max_act = std::max(m->max_act, (size_t)st[i].n_hidden);  // the hidden layer's scratch
             break;
         default:
             return bad("unknown plain stage op");
@@ -241,9 +265,20 @@ bcn_status bcn_plain_branch_forward(const bcn_plain_model *m, const uint8_t *img
             break;
         }
         case BCN_PLAIN_TAP_FC: {
+            const int K = s.cin * s.hin * s.win;
             size_t n = (size_t)s.n_feat * B;
-            k_fc<<<blocks_for(n), 256, 0, st>>>(buf[cur], s.d_w, feats, B, s.cin * s.hin * s.win, x.n_out,
-                                                s.feat_row);
+            k_fc<<<blocks_for(n), 256, 0, st>>>(buf[cur], s.d_w, x.bias ? s.d_w + (size_t)x.n_out * K : nullptr,
+                                                feats, B, K, x.n_out, s.feat_row);
+            break;
+        }
+        case BCN_PLAIN_TAP_INTEGRATE: {
+            const int K = s.cin * s.hin * s.win, nh = x.n_hidden;
+            const float *w1 = s.d_w, *b1 = w1 + (size_t)nh * K, *w2 = b1 + nh, *b2 = w2 + (size_t)x.n_out * nh;
+            float *hidden = buf[1 - cur];  // scratch; the trunk stays in buf[cur]
+            k_fc_square<<<blocks_for((size_t)nh * B), 256, 0, st>>>(buf[cur], w1, b1, hidden, B, K, nh);
+            if (check_launch("k_fc_square") != BCN_OK) return BCN_E_CUDA;
+            k_fc<<<blocks_for((size_t)s.n_feat * B), 256, 0, st>>>(hidden, w2, b2, feats, B, nh, x.n_out,
+                                                                    s.feat_row);
             break;
         }
         }

@@ -1,7 +1,8 @@
 """Whole ciphertext-branch evaluation on the GPU (through the C ABI) against
 the oracle: bit-exact on every output limb for the small MNIST-shaped network,
 the CryptoNets-scale network (the benchmark's workload and launch
-configuration) and a CIFAR-shaped network on the full N = 16384 ring; at the
+configuration), the same with the two-layer feature-integration head (Sec.
+3.3), and a CIFAR-shaped network on the full N = 16384 ring; at the
 CIFAR-shaped network's full size, decrypt(eval(encrypt(x))) within 1e-3 of the
 fp64 network with the same argmax.
 """
@@ -46,6 +47,7 @@ def run_gpu(cfg, w_int, s_w, evk, cts, pts):
 CASES = {
     "cnn3_small": lambda: workloads.get_config("cnn3_small"),
     "cryptonets": lambda: workloads.get_config("cryptonets"),
+    "cryptonets_fi": lambda: workloads.get_config("cryptonets_fi"),
     "cifar_reduced": lambda: workloads.reduced_cifar(cout1=2, cout2=3, seg=8, batch=512),
 }
 
@@ -123,7 +125,7 @@ def test_eval_is_deterministic_and_stream_ordered():
         assert np.array_equal(bcn.to_host_u32(o), ref)
 
 
-@pytest.mark.parametrize("name", ["cnn3_small", "cryptonets", "cifar_cnn"])
+@pytest.mark.parametrize("name", ["cnn3_small", "cryptonets", "cifar_cnn", "cryptonets_fi"])
 def test_plain_branch_forward(name):
     """fp32 plaintext branch on the GPU vs the oracle's fp64 one."""
     cfg = workloads.with_batch(workloads.get_config(name), 96)

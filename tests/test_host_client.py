@@ -65,7 +65,8 @@ def test_encode_matches_direct_sum(pair):
     differs, so |delta m_j| <= 1 + 2^-40 * scale * max|z| (fp64 on both sides)."""
     c, P = pair
     rng = np.random.default_rng(1)
-    for B, scale in ((P.N // 2, 2.0**25), (P.N // 4 + 3, 2.0**40)):
+    # 2^80: coefficients beyond int64, taken as the exact integers of the fp64 products
+    for B, scale in ((P.N // 2, 2.0**25), (P.N // 4 + 3, 2.0**40), (P.N // 8 + 1, 2.0**80)):
         z = rng.uniform(-1.5, 1.5, (3, B))
         a = c.encode(z, P.L, scale)
         m = O.encode_coeffs(z, P.N, scale)
@@ -119,4 +120,4 @@ def test_bad_arguments_are_errors():
     with pytest.raises(bcn.BcnError):
         c.encode(np.zeros((1, 4096)), 3, 1.0)  # B > N/2
     with pytest.raises(bcn.BcnError):
-        c.encode(np.full((1, 8), 1.0), 3, 2.0**80)  # does not fit in 63 bits
+        c.encode(np.full((1, 8), 1.0), 3, float("inf"))  # not finite

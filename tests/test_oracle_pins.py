@@ -395,7 +395,7 @@ def test_conv_tables_match_torch_conv2d(name):
         assert np.abs(y - ref).max() < 1e-12
 
 
-@pytest.mark.parametrize("name", ["cnn3_small", "cryptonets", "cifar_cnn"])
+@pytest.mark.parametrize("name", ["cnn3_small", "cryptonets", "cifar_cnn", "cryptonets_fi"])
 def test_plain_branch_matches_torch(name):
     cfg = workloads.with_batch(workloads.get_config(name), 5)
     imgs, noise, pw = workloads.images(cfg), workloads.laplace_noise(cfg), workloads.plain_weights(cfg)
@@ -416,11 +416,68 @@ def test_plain_branch_matches_torch(name):
             y = x[:, :, o:o + st["hc"], o:o + st["wc"]]
             z = F.conv2d(y, torch.from_numpy(wgt.astype(np.float64))[:, :, None, None])  # 1x1 conv = CRot
             ref.append(z.permute(1, 2, 3, 0).reshape(-1, 5).numpy())
-        else:
-            ref.append(F.linear(x.reshape(5, -1), torch.from_numpy(wgt.astype(np.float64))).numpy().T)
+        elif st["op"] == "tap_fc":
+            wm, b = wgt if isinstance(wgt, tuple) else (wgt, None)
+            bt = None if b is None else torch.from_numpy(b.astype(np.float64))
+            ref.append(F.linear(x.reshape(5, -1), torch.from_numpy(wm.astype(np.float64)), bt).numpy().T)
+        else:  # tap_integrate: a Linear, the square activation, a Linear
+            w1, b1, w2, b2 = (torch.from_numpy(a.astype(np.float64)) for a in wgt)
+            ref.append(F.linear(F.linear(x.reshape(5, -1), w1, b1).pow(2), w2, b2).numpy().T)
     assert len(feats) == len(ref)
     for a, b in zip(feats, ref):
         assert np.abs(a - b).max() < 1e-12
+
+
+def test_feature_integration_is_the_two_layer_head():
+    """Sec. 3.3: with the ciphertext branch's output x_c and the plaintext
+    branch's output x_p, the integration head computes
+        x_c1 = sigma(W_c1 x_c + W_p1 x_p + b_1),  x_p1 = sigma(W'_p1 x_p + b'_1),
+        x_out = W_c2 x_c1 + W_p2 x_p1 + b_2       (sigma: the square activation;
+    the logits are left without a final activation).  The feature-integration
+    config expresses it as two ciphertext dense layers fed by two plaintext
+    taps; its fp64 network must equal the head written out with torch layers
+    on the branch outputs built from the images (conv2d / avg_pool2d)."""
+    cfg = workloads.with_batch(workloads.get_config("cryptonets_fi"), 6)
+    imgs, noise, pw = workloads.images(cfg), workloads.laplace_noise(cfg), workloads.plain_weights(cfg)
+    feats = O.plain_branch(cfg, imgs, noise, pw)
+    wf = workloads.cipher_weights(cfg)
+    q = [O.quantize(w) for w in wf]
+    tables = [O.layer_table(l, a) for l, (a, _) in zip(cfg["cipher"], q)]
+    seg = O.segment_values(cfg, imgs)
+    got = O.fp64_network(cfg, seg, feats, tables, [s for _, s in q])
+    t = lambda a: torch.from_numpy(np.asarray(a, dtype=np.float64))  # noqa: E731
+    # plaintext branch output x_p: perturbed image, segment zeroed, conv3x3, 2x2 average pool
+    y0, x0, h, w = cfg["segment"]
+    xp = t(imgs.astype(np.float64) / 255.0 + noise.astype(np.float64)).permute(0, 3, 1, 2).clone()
+    xp[:, :, y0:y0 + h, x0:x0 + w] = 0
+    xp = F.avg_pool2d(F.conv2d(xp, t(pw[0]), padding=1), 2)
+    # ciphertext branch output x_c: conv5x5/2 on the segment, plus the crop/CRot feature, squared
+    wc = [t(a.astype(np.float64) * s) for a, s in q]
+    seg_img = t(seg.T.reshape(6, 1, 16, 16))
+    z = F.conv2d(xp[:, :, 4:10, 4:10], t(pw[2])[:, :, None, None])  # centre crop 14 -> 6, CRot
+    xc = (F.conv2d(seg_img, wc[0], stride=2) + z).pow(2).reshape(6, -1)
+    W_p1, b_1 = pw[3]
+    Wq1, bq1, W_p2, b_2 = pw[4]
+    xp_flat = xp.reshape(6, -1)
+    xc1 = (F.linear(xc, wc[1]) + F.linear(xp_flat, t(W_p1), t(b_1))).pow(2)
+    xp1 = F.linear(xp_flat, t(Wq1), t(bq1)).pow(2)
+    x_out = F.linear(xc1, wc[2]) + F.linear(xp1, t(W_p2), t(b_2))
+    assert np.abs(got - x_out.numpy().T).max() < 1e-9 * max(1.0, float(x_out.abs().max()))
+
+
+def test_encode_beyond_int64_roundtrips():
+    """Scales past 2^63 (the feature added after the last MAC of the
+    integration head sits near 2^90): the coefficients become Python ints, the
+    residues reduce them exactly, and CRT + decode return the values."""
+    P = O.Params(10, 4, 1, 1)
+    z = np.random.default_rng(31).uniform(-1, 1, (2, 100))
+    scale = 2.0**90
+    m = O.encode_coeffs(z, P.N, scale)
+    assert m.dtype == object and max(abs(int(v)) for v in m.flat) > 2**63
+    res = O.to_residues(m, P.q)
+    back = O.crt_centered(res, P.q)
+    assert all(int(a) == int(b) for a, b in zip(back.flat, m.flat))
+    assert np.abs(O.decode(back, P.N, 100, scale) - z).max() < 1e-9
 
 
 def test_level_and_scale_schedule():

@@ -63,6 +63,29 @@ CONFIGS = {
             dict(op="tap_fc", n_out=100),
         ],
     ),
+    # The CryptoNets-scale network with the two-layer feature integration of
+    # Sec. 3.3 as its head: the ciphertext neurons of integration layer 1 are
+    # a dense layer on the ciphertext branch plus W_p1 x_p + b_1 from the
+    # plaintext branch (a tap), squared; integration layer 2 is a dense layer
+    # on them plus W_p2 x_p^<1> + b_2, the plaintext neurons' contribution
+    # (a tap).  n_1 = 100 (50 + 50 neurons), n_2 = 10.
+    "cryptonets_fi": dict(
+        name="cryptonets_fi",
+        log_n=13, n_data=7, n_special=1, alpha=1, log_scale=30.0,
+        image=(28, 28, 1), batch=4096, segment=(6, 6, 16, 16),
+        cipher=[
+            dict(type="conv", cin=1, h=16, w=16, cout=5, k=5, stride=2, pad=0, add=True, square=True),
+            dict(type="dense", n_in=180, n_out=50, add=True, square=True),
+            dict(type="dense", n_in=50, n_out=10, add=True, square=False),
+        ],
+        plain=[
+            dict(op="conv", cin=1, cout=4, k=3, stride=1, pad=1, relu=False),
+            dict(op="avgpool2"),
+            dict(op="tap_crop_crot", hc=6, wc=6, ch_c=5),
+            dict(op="tap_fc", n_out=50, bias=True),
+            dict(op="tap_integrate", n_hidden=50, n_out=10),
+        ],
+    ),
     "cifar_cnn": dict(
         name="cifar_cnn",
         log_n=14, n_data=11, n_special=2, alpha=2, log_scale=30.0,
@@ -195,17 +218,24 @@ def cipher_weights(cfg: dict, seed: int = SEED_WEIGHTS):
 
 
 def plain_weights(cfg: dict, seed: int = SEED_WEIGHTS):
-    """float32 N(0, 0.1) weights for every plain-branch stage that has any:
-    conv [cout][cin][k][k]; tap_crop_crot CRot [ch_c][ch_p]; tap_fc [n_out][C*H*W]."""
+    """float32 N(0, 0.1) weights (and biases) for every plain-branch stage that
+    has any: conv [cout][cin][k][k]; tap_crop_crot CRot [ch_c][ch_p]; tap_fc
+    [n_out][C*H*W], or the tuple (W, b) with bias; tap_integrate the tuple
+    (W'_1 [n_hidden][C*H*W], b'_1 [n_hidden], W_2 [n_out][n_hidden], b_2 [n_out])."""
     out = []
     for i, (st, (C, H, W)) in enumerate(plain_shapes(cfg)):
         g = _rng(seed, 2, i)
+        nrm = lambda *shape: (g.standard_normal(shape) * 0.1).astype(np.float32)  # noqa: E731
         if st["op"] == "conv":
-            out.append((g.standard_normal((st["cout"], st["cin"], st["k"], st["k"])) * 0.1).astype(np.float32))
+            out.append(nrm(st["cout"], st["cin"], st["k"], st["k"]))
         elif st["op"] == "tap_crop_crot":
-            out.append((g.standard_normal((st["ch_c"], C)) * 0.1).astype(np.float32))
+            out.append(nrm(st["ch_c"], C))
         elif st["op"] == "tap_fc":
-            out.append((g.standard_normal((st["n_out"], C * H * W)) * 0.1).astype(np.float32))
+            w = nrm(st["n_out"], C * H * W)
+            out.append((w, nrm(st["n_out"])) if st.get("bias") else w)
+        elif st["op"] == "tap_integrate":
+            nh, no = st["n_hidden"], st["n_out"]
+            out.append((nrm(nh, C * H * W), nrm(nh), nrm(no, nh), nrm(no)))
         else:
             out.append(None)
     return out
