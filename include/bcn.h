@@ -360,6 +360,23 @@ bcn_status bcn_op_square_relin_rescale_noalloc(const bcn_ctx *ctx, int level, co
                                                const uint32_t *in_dev, int n_ct, uint32_t *out_dev,
                                                void *cuda_stream);
 /* rescale alone: [n_ct][2][level][N] -> [n_ct][2][level-1][N] */
+/* Rotation of the slots (App. A: D(Rot(c, k)) is D(c) rotated by k slots; App.
+ * D builds its packed convolutions and dense layers from rotations).  With slot k
+ * at the root zeta^{5^k}, a rotation by r slots (slot k + r moves to slot k,
+ * cyclically over the N/2 slots) is the automorphism sigma_g: a(X) -> a(X^g),
+ * g = 5^r mod 2N, followed by key switching from sigma_g(s) back to s:
+ *     Rot(c0, c1) = (sigma_g(c0) + k0, k1),  (k0, k1) = KeySwitch_gk(sigma_g(c1)).
+ * bcn_galois_elt: g for `steps` (taken mod N/2).  bcn_galois_keygen (client,
+ * host): gk_j = (-a_j s + e_j + P g_j sigma_g(s), a_j) in the layout of the
+ * relinearisation key (bcn_evk_words words; streams: tag 6 a (index
+ * (g << 20) + j*256 + limb), tag 7 e (index (g << 20) + j)); make it device-ready
+ * with bcn_evk_prepare.  bcn_op_rotate: n_ct ciphertexts in/out
+ * [n_ct][2][level][N] (device, coefficient form; no level is used), workspace
+ * bcn_op_workspace_bytes(level, n_ct); in and out must not overlap. */
+uint32_t bcn_galois_elt(const bcn_ctx *ctx, int steps);
+bcn_status bcn_galois_keygen(const bcn_ctx *ctx, const int8_t *sk, int steps, uint64_t seed, uint32_t *gk_out);
+bcn_status bcn_op_rotate(const bcn_ctx *ctx, int level, const uint32_t *gk_eval_dev, int steps, const uint32_t *in_dev,
+                         int n_ct, uint32_t *out_dev, void *workspace_dev, size_t workspace_bytes, void *cuda_stream);
 bcn_status bcn_op_rescale(const bcn_ctx *ctx, int level, const uint32_t *in_dev, int n_ct, uint32_t *out_dev,
                           void *cuda_stream);
 

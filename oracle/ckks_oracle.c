@@ -301,7 +301,7 @@ uint64_t oc_rng_first(uint64_t seed, uint64_t tag, uint64_t idx, uint64_t k) {
     return v;
 }
 
-enum { TAG_SK = 1, TAG_EVK_A = 2, TAG_EVK_E = 3, TAG_ENC_A = 4, TAG_ENC_E = 5 };
+enum { TAG_SK = 1, TAG_EVK_A = 2, TAG_EVK_E = 3, TAG_ENC_A = 4, TAG_ENC_E = 5, TAG_GK_A = 6, TAG_GK_E = 7 };
 
 /* ternary secret coefficient: (r mod 3) - 1 */
 static int ternary(uint64_t r) { return (int)(r % 3) - 1; }
@@ -708,5 +708,118 @@ int oc_square_relin_rescale(const oc_ctx *c, int level, const uint32_t *evk, con
         free(d); free(ks);
     }
     free(evk_ntt);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* rotations (App. A: Rot(c, k) rotates the slots of D(c) by k positions;  */
+/* App. D builds convolutions and dense layers from them)                  */
+/* ------------------------------------------------------------------ */
+/* The automorphism sigma_g: a(X) -> a(X^g) of Z_q[X]/(X^N + 1), g odd.
+ * Coefficient i moves to position i*g mod 2N and changes sign when that
+ * position is N or more (X^N = -1).  With slot k at the root zeta^{5^k}
+ * (the encoding of App. A as read here), sigma_g with g = 5^r mod 2N moves the
+ * value of slot k + r into slot k: a rotation by r slots. */
+static void automorph(int N, uint64_t g, const uint64_t *a, uint64_t *out, uint64_t q) {
+    uint64_t two_n = 2 * (uint64_t)N;
+    for (int i = 0; i < N; i++) {
+        uint64_t j = ((uint64_t)i * g) % two_n;
+        if (j < (uint64_t)N)
+            out[j] = a[i];
+        else
+            out[j - N] = (q - a[i]) % q;
+    }
+}
+
+/* in [n_poly][level][N] -> out [n_poly][level][N], limb i mod q_i */
+int oc_automorphism(const oc_ctx *c, int level, uint64_t g, const uint32_t *in, int n_poly, uint32_t *out) {
+    int N = c->N;
+    if (level < 1 || level > c->L + c->K || (g & 1) == 0 || g >= 2 * (uint64_t)N) return -1;
+#pragma omp parallel for schedule(dynamic)
+    for (int p = 0; p < n_poly; p++) {
+        uint64_t *a = (uint64_t *)malloc(8 * N), *b = (uint64_t *)malloc(8 * N);
+        for (int i = 0; i < level; i++) {
+            const uint32_t *src = in + ((size_t)p * level + i) * N;
+            for (int k = 0; k < N; k++) a[k] = src[k];
+            automorph(N, g, a, b, c->q[i]);
+            for (int k = 0; k < N; k++) out[((size_t)p * level + i) * N + k] = (uint32_t)b[k];
+        }
+        free(a); free(b);
+    }
+    return 0;
+}
+
+/* Galois key of sigma_g: key switching from sigma_g(s) to s in the same hybrid
+ * form as the relinearisation key, with s^2 replaced by sigma_g(s):
+ *     gk_j = (-a_j s + e_j + P g_j sigma_g(s), a_j)   over Q_L u P.
+ * Streams: a_j per limb (TAG_GK_A, (g << 20) + j*256 + limb), e_j
+ * (TAG_GK_E, (g << 20) + j).  Layout [dnum][2][L+K][N] like the relinearisation key. */
+int oc_galois_keygen(const oc_ctx *c, const int8_t *sk, uint64_t g, uint64_t seed, uint32_t *gk) {
+    int N = c->N, L = c->L, K = c->K, nb = L + K, dnum = oc_dnum(c, L);
+    if ((g & 1) == 0 || g >= 2 * (uint64_t)N) return -1;
+    uint64_t *s = (uint64_t *)malloc(8 * N), *sg = (uint64_t *)malloc(8 * N), *as = (uint64_t *)malloc(8 * N);
+    uint64_t *a = (uint64_t *)malloc(8 * N);
+    int64_t *e = (int64_t *)malloc(8 * N);
+    for (int dj = 0; dj < dnum; dj++) {
+        oc_rng re;
+        rng_init(&re, seed, TAG_GK_E, (g << 20) + (uint64_t)dj);
+        for (int k = 0; k < N; k++) e[k] = cbd21(rng_next(&re));
+        for (int t = 0; t < nb; t++) {
+            uint64_t q = c->q[t];
+            oc_rng ra;
+            rng_init(&ra, seed, TAG_GK_A, (g << 20) + (uint64_t)dj * 256 + (uint64_t)t);
+            for (int k = 0; k < N; k++) a[k] = uniform_mod(&ra, q);
+            for (int k = 0; k < N; k++) s[k] = smod(sk[k], q);
+            poly_mul(c, t, a, s, as);
+            automorph(N, g, s, sg, q);
+            uint64_t Pm = 1 % q;
+            for (int m = 0; m < K; m++) Pm = mulmod(Pm, c->q[L + m] % q, q);
+            int in_digit = (t < L) && t >= digit_lo(c, dj) && t < digit_hi(c, dj, L);
+            uint32_t *bo = gk + ((size_t)(dj * 2 + 0) * nb + t) * N;
+            uint32_t *ao = gk + ((size_t)(dj * 2 + 1) * nb + t) * N;
+            for (int k = 0; k < N; k++) {
+                uint64_t b = submod(smod(e[k], q), as[k], q);
+                if (in_digit) b = addmod(b, mulmod(Pm, sg[k], q), q);
+                bo[k] = (uint32_t)b;
+                ao[k] = (uint32_t)a[k];
+            }
+        }
+    }
+    free(s); free(sg); free(as); free(a); free(e);
+    return 0;
+}
+
+/* Rotation by the automorphism sigma_g: (c0, c1) -> (sigma_g(c0) + k0, k1) with
+ * (k0, k1) = KeySwitch_gk(sigma_g(c1)), so that k0 + k1 s ~= sigma_g(c1) sigma_g(s)
+ * and the result decrypts under s to sigma_g(m).  No rescale (no level used).
+ * ct [n_ct][2][level][N] -> out [n_ct][2][level][N]. */
+int oc_rotate(const oc_ctx *c, int level, const uint32_t *gk, uint64_t g, const uint32_t *ct, int n_ct,
+              uint32_t *out) {
+    int N = c->N;
+    if (level < 1 || level > c->L || c->K < 1 || (g & 1) == 0 || g >= 2 * (uint64_t)N) return -1;
+    uint64_t *gk_ntt = evk_to_ntt(c, level, gk);
+#pragma omp parallel for schedule(dynamic)
+    for (int ci = 0; ci < n_ct; ci++) {
+        size_t ln = (size_t)level * N;
+        uint64_t *a = (uint64_t *)malloc(8 * N), *r0 = (uint64_t *)malloc(8 * ln), *r1 = (uint64_t *)malloc(8 * ln);
+        uint64_t *ks = (uint64_t *)malloc(8 * 2 * ln);
+        const uint32_t *cc = ct + (size_t)ci * 2 * ln;
+        for (int i = 0; i < level; i++) {
+            for (int k = 0; k < N; k++) a[k] = cc[(size_t)i * N + k];
+            automorph(N, g, a, r0 + (size_t)i * N, c->q[i]);
+            for (int k = 0; k < N; k++) a[k] = cc[ln + (size_t)i * N + k];
+            automorph(N, g, a, r1 + (size_t)i * N, c->q[i]);
+        }
+        keyswitch_one(c, level, gk_ntt, r1, ks);
+        uint32_t *o = out + (size_t)ci * 2 * ln;
+        for (int i = 0; i < level; i++)
+            for (int k = 0; k < N; k++) {
+                size_t x = (size_t)i * N + k;
+                o[x] = (uint32_t)addmod(r0[x], ks[x], c->q[i]);
+                o[ln + x] = (uint32_t)ks[ln + x];
+            }
+        free(a); free(r0); free(r1); free(ks);
+    }
+    free(gk_ntt);
     return 0;
 }

@@ -78,6 +78,9 @@ def lib():
                 "oc_relin": (I, [P, I, P, P, I, P]),
                 "oc_rescale": (I, [P, I, P, I, P]),
                 "oc_square_relin_rescale": (I, [P, I, P, P, I, P]),
+                "oc_automorphism": (I, [P, I, U64, P, I, P]),
+                "oc_galois_keygen": (I, [P, P, U64, U64, P]),
+                "oc_rotate": (I, [P, I, P, U64, P, I, P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -234,6 +237,33 @@ class Params:
         ct = np.ascontiguousarray(ct, dtype=np.uint32)
         out = np.zeros((ct.shape[0], 2, level - 1, self.N), dtype=np.uint32)
         assert lib().oc_rescale(self._c, level, _p(ct), ct.shape[0], _p(out)) == 0
+        return out
+
+    # -- rotations (App. A Rot; App. D) ----------------------------------
+    def galois_elt(self, steps: int) -> int:
+        """g = 5^steps mod 2N: sigma_g rotates the N/2 slots by `steps`."""
+        return pow(5, steps % (self.N // 2), 2 * self.N)
+
+    def automorphism(self, level: int, g: int, a: np.ndarray) -> np.ndarray:
+        """a [..][level][N] -> a(X^g), limb i mod q_i."""
+        a = np.ascontiguousarray(a, dtype=np.uint32)
+        out = np.zeros_like(a)
+        n_poly = int(np.prod(a.shape[:-2])) if a.ndim > 2 else 1
+        assert lib().oc_automorphism(self._c, level, g, _p(a), n_poly, _p(out)) == 0
+        return out
+
+    def galois_keygen(self, sk: np.ndarray, steps: int, seed: int) -> np.ndarray:
+        gk = np.zeros(self.evk_shape(), dtype=np.uint32)
+        rc = lib().oc_galois_keygen(self._c, _p(np.ascontiguousarray(sk)), self.galois_elt(steps), seed, _p(gk))
+        assert rc == 0
+        return gk
+
+    def rotate(self, level: int, gk: np.ndarray, steps: int, ct: np.ndarray) -> np.ndarray:
+        ct = np.ascontiguousarray(ct, dtype=np.uint32)
+        out = np.zeros_like(ct)
+        rc = lib().oc_rotate(self._c, level, _p(np.ascontiguousarray(gk)), self.galois_elt(steps), _p(ct),
+                             ct.shape[0], _p(out))
+        assert rc == 0
         return out
 
     def square_relin_rescale(self, level: int, evk: np.ndarray, ct: np.ndarray) -> np.ndarray:

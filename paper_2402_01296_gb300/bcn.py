@@ -103,6 +103,9 @@ _SIGS = {
     "bcn_op_tensor_square": (_I, [_P, _I, _P, _I, _P, _P, _SZ, _P]),
     "bcn_op_square_relin_rescale": (_I, [_P, _I, _P, _P, _I, _P, _P, _SZ, _P]),
     "bcn_op_rescale": (_I, [_P, _I, _P, _I, _P, _P]),
+    "bcn_galois_elt": (ctypes.c_uint32, [_P, _I]),
+    "bcn_galois_keygen": (_I, [_P, _P, _I, _U64, _P]),
+    "bcn_op_rotate": (_I, [_P, _I, _P, _I, _P, _I, _P, _P, _SZ, _P]),
     "bcn_op_square_relin_rescale_noalloc": (_I, [_P, _I, _P, _P, _I, _P, _P]),
 }
 
@@ -242,6 +245,15 @@ class Context:
         _check(lib().bcn_keygen(self._h, seed, _np_ptr(sk, np.int8), _np_ptr(evk, np.uint32)), "bcn_keygen")
         return sk, evk
 
+    def galois_elt(self, steps: int) -> int:
+        return int(lib().bcn_galois_elt(self._h, int(steps)))
+
+    def galois_keygen(self, sk: np.ndarray, steps: int, seed: int) -> np.ndarray:
+        gk = np.zeros(self.evk_shape(), dtype=np.uint32)
+        _check(lib().bcn_galois_keygen(self._h, _np_ptr(np.ascontiguousarray(sk, dtype=np.int8), np.int8),
+                                       int(steps), seed, _np_ptr(gk, np.uint32)), "bcn_galois_keygen")
+        return gk
+
     def encode(self, values: np.ndarray, level: int, scale: float) -> np.ndarray:
         v = np.ascontiguousarray(np.atleast_2d(values), dtype=np.float64)
         n_vec, B = v.shape
@@ -333,6 +345,14 @@ class Context:
             self._h, level, _dev_ptr(evk_eval, self.evk_words()), _dev_ptr(in_dev, n_ct * 2 * level * self.N), n_ct,
             _dev_ptr(out_dev, n_ct * 2 * (level - 1) * self.N), _stream(stream)),
             "bcn_op_square_relin_rescale_noalloc")
+
+    def op_rotate(self, level, gk_eval, steps, in_dev, n_ct, out_dev, stream=None):
+        """Slot rotation by `steps` (automorphism + key switch with the prepared Galois key)."""
+        ws, nb = self._ws(level, n_ct)
+        _check(lib().bcn_op_rotate(self._h, level, _dev_ptr(gk_eval, self.evk_words()), int(steps),
+                                   _dev_ptr(in_dev, n_ct * 2 * level * self.N), n_ct,
+                                   _dev_ptr(out_dev, n_ct * 2 * level * self.N), ws.data_ptr(), nb, _stream(stream)),
+               "bcn_op_rotate")
 
     def op_rescale(self, level, in_dev, n_ct, out_dev, stream=None):
         _check(lib().bcn_op_rescale(self._h, level, _dev_ptr(in_dev, n_ct * 2 * level * self.N), n_ct,

@@ -115,7 +115,7 @@ struct Stream {
         return __builtin_popcountll(r & m) - __builtin_popcountll((r >> 21) & m);
     }
 };
-enum : uint64_t { kTagSk = 1, kTagEvkA = 2, kTagEvkE = 3, kTagEncA = 4, kTagEncE = 5 };
+enum : uint64_t { kTagSk = 1, kTagEvkA = 2, kTagEvkE = 3, kTagEncA = 4, kTagEncE = 5, kTagGkA = 6, kTagGkE = 7 };
 
 // --------------------------------------------------------------------- FFT
 // Unnormalised DFT with positive exponent: F_j = sum_u Y_u exp(2 pi i j u / n).
@@ -202,6 +202,66 @@ bcn_status bcn_keygen(const bcn_ctx *c, uint64_t seed, int8_t *sk, uint32_t *evk
         for (int k = 0; k < N; k++) {
             uint32_t v = subq(from_signed(re.cbd21(), q), as[k], q);
             if (in_digit) v = addq(v, mulq(Pmod[t], S2[t][k], q), q);
+            b[k] = v;
+        }
+    });
+    return BCN_OK;
+}
+
+uint32_t bcn_galois_elt(const bcn_ctx *c, int steps) {
+    if (!c) return 0;
+    const uint64_t two_n = 2 * (uint64_t)c->N, half = (uint64_t)c->N / 2;
+    const uint64_t e = (uint64_t)(((long long)steps % (long long)half + (long long)half) % (long long)half);
+    uint64_t g = 1, b = 5;
+    for (uint64_t k = e; k; k >>= 1) {
+        if (k & 1) g = g * b % two_n;
+        b = b * b % two_n;
+    }
+    return (uint32_t)g;
+}
+
+bcn_status bcn_galois_keygen(const bcn_ctx *c, const int8_t *sk, int steps, uint64_t seed, uint32_t *gk) {
+    if (!c || !sk || !gk) return fail(BCN_E_INVAL, "bcn_galois_keygen: null argument");
+    const int N = c->N, L = c->L, K = c->K, P = L + K, A = c->alpha;
+    const uint64_t g = bcn_galois_elt(c, steps), two_n = 2 * (uint64_t)N;
+    // s in the NTT domain and sigma_g(s) in coefficient form, every prime
+    std::vector<std::vector<uint32_t>> S(P, std::vector<uint32_t>(N)), SG(P, std::vector<uint32_t>(N));
+    parallel_for(P, [&](int t) {
+        uint32_t q = (uint32_t)c->primes[t];
+        for (int i = 0; i < N; i++) {
+            const uint32_t v = from_signed(sk[i], q);
+            const uint64_t j = (uint64_t)i * g % two_n;  // X^i -> X^{i g}, X^N = -1
+            if (j < (uint64_t)N)
+                SG[t][j] = v;
+            else
+                SG[t][j - N] = v ? q - v : 0;
+            S[t][i] = v;
+        }
+        ntt_fwd(c, t, S[t].data());
+    });
+    std::vector<uint32_t> Pmod(P);
+    for (int t = 0; t < P; t++) {
+        uint64_t q = c->primes[t], v = 1 % q;
+        for (int m = 0; m < K; m++) v = mulmod64(v, c->primes[L + m] % q, q);
+        Pmod[t] = (uint32_t)v;
+    }
+    parallel_for(c->dnum * P, [&](int job) {
+        int j = job / P, t = job % P;
+        uint32_t q = (uint32_t)c->primes[t];
+        Stream re(seed, kTagGkE, (g << 20) + (uint64_t)j);
+        Stream ra(seed, kTagGkA, (g << 20) + (uint64_t)j * 256 + (uint64_t)t);
+        uint32_t *b = gk + ((size_t)(j * 2 + 0) * P + t) * N;
+        uint32_t *a = gk + ((size_t)(j * 2 + 1) * P + t) * N;
+        std::vector<uint32_t> as(N);
+        for (int k = 0; k < N; k++) a[k] = ra.uniform(q);
+        std::copy(a, a + N, as.begin());
+        ntt_fwd(c, t, as.data());
+        for (int k = 0; k < N; k++) as[k] = mulq(as[k], S[t][k], q);
+        ntt_inv(c, t, as.data());
+        bool in_digit = t < L && t >= j * A && t < std::min((j + 1) * A, L);
+        for (int k = 0; k < N; k++) {
+            uint32_t v = subq(from_signed(re.cbd21(), q), as[k], q);
+            if (in_digit) v = addq(v, mulq(Pmod[t], SG[t][k], q), q);
             b[k] = v;
         }
     });

@@ -17,6 +17,13 @@ __host__ __device__ inline int prime_of(const PrimeMap &m, int limb) {
     return t < m.split ? t : t + m.offset;
 }
 
+// return the status of a call that fails
+#define BCN_TRY(x)                          \
+    do {                                    \
+        bcn_status _s = (x);                \
+        if (_s != BCN_OK) return _s;        \
+    } while (0)
+
 inline bcn_status check_launch(const char *what) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(BCN_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
@@ -76,6 +83,12 @@ bcn_status square_relin_rescale_chunk2(const bcn_ctx *c, int n, const uint32_t *
 
 bcn_status launch_ntt(const bcn_ctx *c, uint32_t *data, size_t n_limbs, const PrimeMap &pm, bool inverse,
                       cudaStream_t st);
+
+// key-switching chunk of the op entry points (eval.cu): ciphertexts per chunk
+// at level n for n_ct ciphertexts, and the chunk's buffers in a workspace of
+// bcn_op_workspace_bytes: D [C][3][n][N], D2N [C][n][N], ACC [C][2][n+K][N]
+int ks_default_chunk(const bcn_ctx *c, int n, int n_ct);
+void ks_carve(const bcn_ctx *c, int n, int chunk, char *ws, uint32_t **d, uint32_t **d2n, uint32_t **acc);
 
 // Tensor-core MAC (mac_tc.cu): used for groups of at least kMacTcMinOutputs
 // outputs and at most kMacTcMaxTaps taps (the fp32 sums stay exact).

@@ -243,12 +243,6 @@ static bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 
 static size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 
-#define BCN_TRY(x)                          \
-    do {                                    \
-        bcn_status _s = (x);                \
-        if (_s != BCN_OK) return _s;        \
-    } while (0)
-
 // CUDA-event pair around one launch when the model's profiler is on
 struct Timed {
     Profiler *p;
@@ -303,6 +297,14 @@ static ChunkBufs carve_chunk(const bcn_ctx *c, int n, int chunk, char *ws) {
     b.d2n = reinterpret_cast<uint32_t *>(ws + d_b);
     b.acc = reinterpret_cast<uint32_t *>(ws + d_b + d2n_b);
     return b;
+}
+
+int ks_default_chunk(const bcn_ctx *c, int n, int n_ct) { return default_chunk(c, n, n_ct); }
+void ks_carve(const bcn_ctx *c, int n, int chunk, char *ws, uint32_t **d, uint32_t **d2n, uint32_t **acc) {
+    ChunkBufs b = carve_chunk(c, n, chunk, ws);
+    *d = b.d;
+    *d2n = b.d2n;
+    *acc = b.acc;
 }
 
 // MAC over groups [g_base, g_base + n_groups) of a layer

@@ -1,0 +1,144 @@
+// Slot rotation (App. A: D(Rot(c, k)) is D(c) rotated by k slots; App. D
+// builds packed convolutions and dense layers from rotations).
+//
+// With slot k at the root zeta^{5^k}, the rotation by r slots is the
+// automorphism sigma_g: a(X) -> a(X^g), g = 5^r mod 2N, followed by key
+// switching from sigma_g(s) back to s with the Galois key of g:
+//     Rot(c0, c1) = (sigma_g(c0) + k0, k1),  (k0, k1) = KeySwitch_gk(sigma_g(c1)).
+// Per chunk of ciphertexts: sigma_g(c1) into the key-switching input, the fused
+// key-switching core (ModUp, NTT, key product, iNTT -- the same kernel as the
+// relinearisation), then ModDown with sigma_g(c0) added (no rescale).
+#include <algorithm>
+#include <cuda_runtime.h>
+
+#include "device_api.h"
+#include "device_math.cuh"
+
+namespace bcn {
+namespace {
+
+// coefficient j of a(X^g): a_i with i = j g^{-1} mod 2N when i < N, else
+// -a_{i-N} (X^N = -1); ginv = g^{-1} mod 2N, N a power of two
+__device__ __forceinline__ uint32_t auto_coeff(const uint32_t *__restrict__ a, int j, uint32_t ginv, int N,
+                                               uint32_t q) {
+    const uint32_t i = (uint32_t)(((uint64_t)j * ginv) & (uint64_t)(2 * N - 1));
+    if (i < (uint32_t)N) return __ldg(a + i);
+    const uint32_t v = __ldg(a + (i - N));
+    return v ? q - v : 0u;
+}
+
+// D [C][3][n][N] slot 2 <- sigma_g(c1) of in [C][2][n][N].  grid (N/256, n, C)
+__global__ void __launch_bounds__(256) k_automorph_c1(const uint32_t *__restrict__ in, uint32_t *__restrict__ D,
+                                                      int n, int N, uint32_t ginv,
+                                                      const PrimeConst *__restrict__ pc) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    const int i = blockIdx.y, ct = blockIdx.z;
+    const uint32_t *a = in + (((size_t)ct * 2 + 1) * n + i) * N;
+    D[(((size_t)ct * 3 + 2) * n + i) * N + j] = auto_coeff(a, j, ginv, N, pc[i].q);
+}
+
+// ModDown by P of the key-switching sums ACC [C][2][n+K][N] (centred fast
+// basis conversion of the P part), plus sigma_g(c0) on the first polynomial:
+// out [C][2][n][N].  Four coefficients per thread.  grid (N/4/256, 2, C)
+__global__ void __launch_bounds__(256) k_moddown_rotate(const uint32_t *__restrict__ in,
+                                                        const uint32_t *__restrict__ acc,
+                                                        uint32_t *__restrict__ out, int n, int N, uint32_t ginv,
+                                                        KsDev ks, const PrimeConst *__restrict__ pc) {
+    const int k4 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k4 * 4 >= N) return;
+    const int b = blockIdx.y, ct = blockIdx.z;
+    const int nb = n + ks.K, L = ks.L;
+    const uint4 *ab = reinterpret_cast<const uint4 *>(acc + ((size_t)ct * 2 + b) * nb * N) + k4;
+    uint4 *ob = reinterpret_cast<uint4 *>(out + ((size_t)ct * 2 + b) * n * N) + k4;
+    const size_t stride = (size_t)N / 4;
+    uint32_t r[4][4];  // [special prime][coefficient]
+    int cnt[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int m = 0; m < 4; m++) {  // K <= 4
+        if (m >= ks.K) break;
+        const PrimeConst &pm = pc[L + m];
+        const uint2 hi = ks.phat_inv[m];
+        const uint4 v = __ldg(ab + (size_t)(n + m) * stride);
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int z = 0; z < 4; z++) {
+            r[m][z] = shoup_mul(w[z], hi.x, hi.y, pm.q);
+            cnt[z] += r[m][z] > pm.half;
+        }
+    }
+    for (int i = 0; i < n; i++) {
+        const uint32_t q = pc[i].q;
+        uint32_t conv[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int m = 0; m < 4; m++) {
+            if (m >= ks.K) break;
+            const uint2 ph = ks.phat[(size_t)m * L + i];
+#pragma unroll
+            for (int z = 0; z < 4; z++) conv[z] = add_mod(conv[z], shoup_mul(r[m][z], ph.x, ph.y, q), q);
+        }
+        const uint32_t pmod = ks.pmod[i];
+        const uint2 pi = ks.pinv[i];
+        const uint4 av = __ldg(ab + (size_t)i * stride);
+        const uint32_t a[4] = {av.x, av.y, av.z, av.w};
+        const uint32_t *c0 = in + (((size_t)ct * 2 + 0) * n + i) * N;
+        uint32_t o[4];
+#pragma unroll
+        for (int z = 0; z < 4; z++) {
+            for (int c = 0; c < cnt[z]; c++) conv[z] = sub_mod(conv[z], pmod, q);
+            const uint32_t kv = shoup_mul(sub_mod(a[z], conv[z], q), pi.x, pi.y, q);
+            o[z] = b == 0 ? add_mod(kv, auto_coeff(c0, 4 * k4 + z, ginv, N, q), q) : kv;
+        }
+        ob[(size_t)i * stride] = make_uint4(o[0], o[1], o[2], o[3]);
+    }
+}
+
+}  // namespace
+}  // namespace bcn
+
+using namespace bcn;
+
+extern "C" bcn_status bcn_op_rotate(const bcn_ctx *c, int level, const uint32_t *gk, int steps, const uint32_t *in,
+                                    int n_ct, uint32_t *out, void *ws, size_t ws_bytes, void *stream) {
+    if (!c) return fail(BCN_E_INVAL, "bcn_op_rotate: null context");
+    if (c->device < 0) return fail(BCN_E_INVAL, "bcn_op_rotate: host-only ctx");
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess || cur != c->device)
+        return fail(BCN_E_INVAL, "bcn_op_rotate: the ctx's device must be current");
+    if (level < 1 || level > c->L || n_ct < 0 || c->K < 1) return fail(BCN_E_INVAL, "bcn_op_rotate: bad level");
+    if (n_ct == 0) return BCN_OK;
+    size_t need = 0;
+    BCN_TRY(bcn_op_workspace_bytes(c, level, n_ct, &need));
+    if (!ws || ws_bytes < need) return fail(BCN_E_BUDGET, "bcn_op_rotate: workspace too small");
+    auto a16 = [](const void *p) { return ((uintptr_t)p & 15) == 0; };
+    if (!gk || !in || !out || !a16(gk) || !a16(in) || !a16(out) || !a16(ws))
+        return fail(BCN_E_INVAL, "bcn_op_rotate: null or unaligned buffer");
+    const size_t N = c->N, ct_words = 2 * (size_t)level * N;
+    const uint32_t *in_end = in + (size_t)n_ct * ct_words, *out_end = out + (size_t)n_ct * ct_words;
+    if (in < out_end && out < in_end) return fail(BCN_E_INVAL, "bcn_op_rotate: in and out overlap");
+    const CoreFns *f = core_fns(c->logN);
+    if (!f) return fail(BCN_E_INVAL, "unsupported ring degree");
+    // g^{-1} mod 2N: the odd residues mod 2N form a group of order N, so g^{N-1}
+    const uint64_t g = bcn_galois_elt(c, steps), two_n = 2 * N;
+    uint64_t ginv = 1, base = g;
+    for (uint64_t e = N - 1; e; e >>= 1) {
+        if (e & 1) ginv = ginv * base % two_n;
+        base = base * base % two_n;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = level, chunk = ks_default_chunk(c, level, n_ct);
+    uint32_t *d, *d2n, *acc;
+    ks_carve(c, n, chunk, reinterpret_cast<char *>(ws), &d, &d2n, &acc);
+    for (int o0 = 0; o0 < n_ct; o0 += chunk) {
+        const int C = std::min(chunk, n_ct - o0);
+        const uint32_t *x = in + (size_t)o0 * ct_words;
+        k_automorph_c1<<<dim3((unsigned)((N + 255) / 256), n, C), 256, 0, st>>>(x, d, n, (int)N, (uint32_t)ginv,
+                                                                             c->d_pc);
+        BCN_TRY(check_launch("k_automorph_c1"));
+        BCN_TRY(f->keyswitch(c, n, d, nullptr, gk, acc, C, st));
+        k_moddown_rotate<<<dim3((unsigned)((N / 4 + 255) / 256), 2, C), 256, 0, st>>>(
+            x, acc, out + (size_t)o0 * ct_words, n, (int)N, (uint32_t)ginv, ks_dev(c), c->d_pc);
+        BCN_TRY(check_launch("k_moddown_rotate"));
+    }
+    return BCN_OK;
+}

@@ -50,6 +50,16 @@ def test_keygen_bit_exact(pair):
         assert np.array_equal(sk, sk2) and np.array_equal(evk, evk2)
 
 
+def test_galois_keygen_bit_exact(pair):
+    """Galois keys (rotation keys, App. A Rot) from the library's client call
+    equal the oracle's, residue by residue, for rotations left and right."""
+    c, P = pair
+    sk, _ = P.keygen(3)
+    for steps in (1, 5, -2):
+        assert c.galois_elt(steps) == P.galois_elt(steps)
+        assert np.array_equal(c.galois_keygen(sk, steps, 12), P.galois_keygen(sk, steps, 12))
+
+
 def test_encrypt_bit_exact(pair):
     c, P = pair
     sk, _ = P.keygen(3)

@@ -528,3 +528,93 @@ def test_whole_network_catches_a_dropped_feature():
     zero = [np.zeros_like(p) for p in pts]
     bad = prob.decode_output(O.evaluate(P, prob.cfg, prob.tables, prob.evk, prob.cts, zero))
     assert np.abs(bad - ref).max() > 1e-2
+
+
+# --------------------------------------------------------------------------
+# rotations (App. A Rot(c, k); App. D builds conv and dense layers from them)
+# --------------------------------------------------------------------------
+def automorph_by_definition(a, g, q):
+    """a(X^g) mod (X^N + 1, q) by expanding every monomial (brute force)."""
+    N = len(a)
+    out = [0] * N
+    for i in range(N):
+        e = i * g
+        sign = -1 if (e // N) % 2 else 1  # X^N = -1
+        out[e % N] += sign * int(a[i])
+    return np.array([v % q for v in out], dtype=np.uint32)
+
+
+def test_automorphism_is_the_substitution_and_a_ring_map(small):
+    P = small
+    rng = np.random.default_rng(40)
+    q = P.q[0]
+    for steps in (1, 3, 17):
+        g = P.galois_elt(steps)
+        a = rng.integers(0, q, P.N).astype(np.uint32)
+        b = rng.integers(0, q, P.N).astype(np.uint32)
+        ga = P.automorphism(1, g, a[None, None, :])[0, 0]
+        assert np.array_equal(ga, automorph_by_definition(a, g, q))
+        gb = P.automorphism(1, g, b[None, None, :])[0, 0]
+        ab = np.array(schoolbook(a, b, q), dtype=np.uint32)
+        gab = P.automorphism(1, g, ab[None, None, :])[0, 0]
+        assert np.array_equal(gab, np.array(schoolbook(ga, gb, q), dtype=np.uint32))
+    # sigma_g o sigma_h = sigma_{gh mod 2N}
+    a = rng.integers(0, q, P.N).astype(np.uint32)[None, None, :]
+    g, h = P.galois_elt(3), P.galois_elt(5)
+    assert np.array_equal(P.automorphism(1, g, P.automorphism(1, h, a)),
+                          P.automorphism(1, g * h % (2 * P.N), a))
+
+
+def test_automorphism_rotates_the_slots():
+    """With slot k at zeta^{5^k}, sigma_{5^r} moves slot k + r to slot k
+    (cyclically over the N/2 slots): checked through encode and decode alone."""
+    P = O.Params(10, 3, 1, 1)
+    z = np.random.default_rng(41).uniform(-1, 1, (2, P.N // 2))
+    S = 2.0**40
+    m = O.encode_coeffs(z, P.N, S)
+    res = O.to_residues(m, P.q)
+    for steps in (1, 7, P.N // 2 - 1):
+        rot = P.automorphism(P.L, P.galois_elt(steps), res)
+        back = O.decode(O.crt_centered(rot, P.q), P.N, P.N // 2, S)
+        assert np.abs(back - np.roll(z, -steps, axis=1)).max() < 1e-9
+
+
+def test_galois_key_errors(small):
+    """gk_j = (-a s + e_j + P g_j sigma_g(s), a): removing a*s and
+    P*g_j*sigma_g(s) leaves the same small error on every prime."""
+    P = small
+    sk, _ = P.keygen(3)
+    steps = 5
+    g = P.galois_elt(steps)
+    gk = P.galois_keygen(sk, steps, 8)
+    Pprod = int(np.prod([int(p) for p in P.p], dtype=object))
+    for j in range(P.dnum(P.L)):
+        errs = []
+        for t, q in enumerate(P.primes):
+            s = (sk.astype(np.int64) % q).astype(np.uint32)
+            b, a = gk[j, 0, t], gk[j, 1, t]
+            v = (b.astype(np.uint64) + schoolbook(a, s, q)) % q
+            if t < P.L and j * P.alpha <= t < (j + 1) * P.alpha:
+                sg = automorph_by_definition(s, g, q)
+                v = (v + q - (Pprod % q) * sg.astype(np.uint64) % q) % q
+            errs.append(centred(v, q))
+        for e in errs:
+            assert np.array_equal(e, errs[0])
+        assert np.abs(errs[0]).max() <= 21 and np.abs(errs[0]).max() > 0
+
+
+@pytest.mark.parametrize("cfg", [(10, 3, 1, 1), (10, 5, 2, 2)])
+def test_rotation_of_an_encryption_decrypts_to_the_rotated_slots(cfg):
+    P = O.Params(*cfg)
+    sk, _ = P.keygen(3)
+    z = np.random.default_rng(42).uniform(-1, 1, (2, P.N // 2))
+    S = 2.0**30
+    ct = P.encrypt(sk, O.encode(z, P.N, S, P.q), P.L, 4)
+    for steps in (1, 33):
+        gk = P.galois_keygen(sk, steps, 7)
+        for level in (P.L, P.L - 1):
+            c = ct[:, :, :level]
+            r = P.rotate(level, gk, steps, c)
+            dec = O.decode(O.crt_centered(P.decrypt(sk, r, level), P.q[:level]), P.N, P.N // 2, S)
+            # noise: the key switch (well below 2^20 here) over the scale
+            assert np.abs(dec - np.roll(z, -steps, axis=1)).max() < 2.0**20 / S
