@@ -49,7 +49,8 @@ def test_rotate_decrypts_to_rotated_slots():
     out = torch.empty(ct.shape, dtype=torch.int32, device="cuda")
     c.op_rotate(P.L, gk_eval, steps, bcn.to_device(ct), 2, out)
     dec = c.decrypt_decode(sk, bcn.to_host_u32(out), P.L, S, P.N // 2)
-    assert np.abs(dec - np.roll(z, -steps, axis=1)).max() < 1e-5
+    # key-switching noise of one-prime digits over one special prime: well below 2^20
+    assert np.abs(dec - np.roll(z, -steps, axis=1)).max() < 2.0**20 / S
 
 
 def test_rotate_rejects_overlap_and_bad_level():
