@@ -44,7 +44,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default=WORKLOAD, choices=list(workloads.CONFIGS) + ["uneven64", "serve"])
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=list(workloads.CONFIGS) + ["uneven64", "serve", "rotate"])
     ap.add_argument("--rates", default="50,100,200,500,1000,2000", help="serve: request rates (req/s)")
     ap.add_argument("--serve-seconds", type=float, default=5.0, help="serve: seconds of arrivals per rate")
     ap.add_argument("--lanes", type=int, default=8, help="serve: lanes (concurrent requests)")
@@ -623,6 +624,60 @@ def run_serve(args, rank, world, local_rank):
         print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# slot rotations (automorphism + key switch with a Galois key)
+# ---------------------------------------------------------------------------
+def run_rotate(args, rank, world, local_rank):
+    """Rotations of the CryptoNets-scale ciphertexts (N = 8192, 7 + 1 primes,
+    the 256 ciphertexts of a slot batch at the top level) and of the CIFAR-shaped
+    ones (N = 16384, 11 + 2 primes, alpha 2, 768 ciphertexts): rotations/s, L2
+    flushed between timed steps."""
+    import torch
+
+    from paper_2402_01296_gb300 import bcn
+
+    device = local_rank
+    torch.cuda.set_device(device)
+    dev = f"cuda:{device}"
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(workloads.SEED_ENC)
+    res = {}
+    for name, n_ct in (("cryptonets", 256), ("cifar_cnn", 768)):
+        cfg = workloads.get_config(name)
+        ctx = bcn.Context.from_config(cfg, device)
+        sk, _ = ctx.keygen(workloads.SEED_KEYS)
+        gk = ctx.evk_prepare(bcn.to_device(ctx.galois_keygen(sk, 1, workloads.SEED_KEYS), dev))
+        x = _dev_residues(torch, ctx.q, (n_ct, 2), ctx.N, gen, dev)
+        out = torch.empty_like(x)
+        ws, nb = ctx._ws(ctx.L, n_ct)
+        run = lambda: bcn.lib().bcn_op_rotate(ctx.handle, ctx.L, gk.data_ptr(), 1, x.data_ptr(), n_ct,  # noqa: E731
+                                              out.data_ptr(), ws.data_ptr(), nb,
+                                              torch.cuda.current_stream().cuda_stream)
+        for _ in range(max(3, args.warmup)):
+            assert run() == 0
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(args.steps):
+            flush.zero_()
+            s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s_.record()
+            assert run() == 0
+            e_.record()
+            torch.cuda.synchronize()
+            ms.append(s_.elapsed_time(e_))
+        t = statistics.mean(ms)
+        res[name] = {"ciphertexts": n_ct, "level": ctx.L, "ms_per_step": t, "rotations_per_s": n_ct / (t / 1e3)}
+        del ctx
+    if rank == 0:
+        print(json.dumps({"metric": "rotations/s", "value": res["cryptonets"]["rotations_per_s"],
+                          "unit": "rotations/s", "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup),
+                          "higher_is_better": True, "dtype": "u32", "data": "synthetic (uniform residues)",
+                          "config": {"workload": "rotate: one-slot rotations of a slot batch's ciphertexts",
+                                     "l2": "flushed (512 MiB write) between timed steps, outside the events"},
+                          "rotations": res}), flush=True)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", 0))
@@ -632,6 +687,8 @@ def main():
         return run_uneven(args, rank, world, local_rank)
     if args.workload == "serve":
         return run_serve(args, rank, world, local_rank)
+    if args.workload == "rotate":
+        return run_rotate(args, rank, world, local_rank)
     cfg = workloads.get_config(args.workload)
     if args.impl == "reference":
         run_reference(args, cfg, rank, world)

@@ -377,6 +377,15 @@ uint32_t bcn_galois_elt(const bcn_ctx *ctx, int steps);
 bcn_status bcn_galois_keygen(const bcn_ctx *ctx, const int8_t *sk, int steps, uint64_t seed, uint32_t *gk_out);
 bcn_status bcn_op_rotate(const bcn_ctx *ctx, int level, const uint32_t *gk_eval_dev, int steps, const uint32_t *in_dev,
                          int n_ct, uint32_t *out_dev, void *workspace_dev, size_t workspace_bytes, void *cuda_stream);
+/* Ciphertext-plaintext product then rescale (App. A Mult(c, u) with an encoded
+ * u -- the masks of App. D's packed layers): (c0 u, c1 u) in R_{Q_level}, then
+ * the rescale by q_{level-1}.  Encode u at scale q_{level-1} to keep the
+ * ciphertext's scale.  in [n_ct][2][level][N], pt [level][N] (coefficient form),
+ * out [n_ct][2][level-1][N], device; workspace bcn_op_workspace_bytes(level,
+ * n_ct).  level >= 2. */
+bcn_status bcn_op_mul_plain_rescale(const bcn_ctx *ctx, int level, const uint32_t *in_dev, int n_ct,
+                                    const uint32_t *pt_dev, uint32_t *out_dev, void *workspace_dev,
+                                    size_t workspace_bytes, void *cuda_stream);
 bcn_status bcn_op_rescale(const bcn_ctx *ctx, int level, const uint32_t *in_dev, int n_ct, uint32_t *out_dev,
                           void *cuda_stream);
 

@@ -823,3 +823,28 @@ int oc_rotate(const oc_ctx *c, int level, const uint32_t *gk, uint64_t g, const 
     free(gk_ntt);
     return 0;
 }
+
+/* Ciphertext-plaintext product (App. A Mult(c, u) with an encoded u, e.g. the
+ * masks of App. D): (c0 u, c1 u) in R_{Q_level}, negacyclic products per prime;
+ * ct [n_ct][2][level][N], pt [level][N] -> out [n_ct][2][level][N].  The
+ * caller rescales afterwards (the mask carries a scale). */
+int oc_mul_plain(const oc_ctx *c, int level, const uint32_t *ct, int n_ct, const uint32_t *pt, uint32_t *out) {
+    int N = c->N;
+    if (level < 1 || level > c->L) return -1;
+#pragma omp parallel for schedule(dynamic)
+    for (int ci = 0; ci < n_ct; ci++) {
+        uint64_t *a = (uint64_t *)malloc(8 * N), *u = (uint64_t *)malloc(8 * N), *o = (uint64_t *)malloc(8 * N);
+        for (int b = 0; b < 2; b++)
+            for (int i = 0; i < level; i++) {
+                const uint32_t *src = ct + (((size_t)ci * 2 + b) * level + i) * N;
+                for (int k = 0; k < N; k++) {
+                    a[k] = src[k];
+                    u[k] = pt[(size_t)i * N + k];
+                }
+                poly_mul(c, i, a, u, o);
+                for (int k = 0; k < N; k++) out[(((size_t)ci * 2 + b) * level + i) * N + k] = (uint32_t)o[k];
+            }
+        free(a); free(u); free(o);
+    }
+    return 0;
+}

@@ -81,6 +81,7 @@ def lib():
                 "oc_automorphism": (I, [P, I, U64, P, I, P]),
                 "oc_galois_keygen": (I, [P, P, U64, U64, P]),
                 "oc_rotate": (I, [P, I, P, U64, P, I, P]),
+                "oc_mul_plain": (I, [P, I, P, I, P, P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -264,6 +265,15 @@ class Params:
         rc = lib().oc_rotate(self._c, level, _p(np.ascontiguousarray(gk)), self.galois_elt(steps), _p(ct),
                              ct.shape[0], _p(out))
         assert rc == 0
+        return out
+
+    def mul_plain(self, level: int, ct: np.ndarray, pt: np.ndarray) -> np.ndarray:
+        """(c0 u, c1 u) mod Q_level for an encoded plaintext u [level][N]."""
+        ct = np.ascontiguousarray(ct, dtype=np.uint32)
+        pt = np.ascontiguousarray(pt, dtype=np.uint32)
+        assert pt.shape == (level, self.N)
+        out = np.zeros_like(ct)
+        assert lib().oc_mul_plain(self._c, level, _p(ct), ct.shape[0], _p(pt), _p(out)) == 0
         return out
 
     def square_relin_rescale(self, level: int, evk: np.ndarray, ct: np.ndarray) -> np.ndarray:
@@ -609,3 +619,41 @@ class Problem:
 
     def fp64_logits(self) -> np.ndarray:
         return fp64_network(self.cfg, self.seg, self.feats, self.tables, self.s_w)
+
+
+# ---------------------------------------------------------------------------
+# BHW packing (App. D): one channel of n images' h x w segments per ciphertext
+# ---------------------------------------------------------------------------
+def pack_bhw(x: np.ndarray, N: int) -> np.ndarray:
+    """x [n_img][C][h][w] -> slot vectors [C][N/2]: image b's pixel (y, x) of
+    channel c in slot b*h*w + y*w + x; unused slots zero."""
+    n, C, h, w = x.shape
+    assert n * h * w <= N // 2
+    out = np.zeros((C, N // 2))
+    for c in range(C):
+        out[c, :n * h * w] = x[:, c].reshape(-1)
+    return out
+
+
+def unpack_bhw(z: np.ndarray, n: int, h: int, w: int) -> np.ndarray:
+    """slot vectors [C][N/2] -> [n][C][h][w] (the inverse of pack_bhw)."""
+    C = z.shape[0]
+    return z[:, :n * h * w].reshape(C, n, h, w).transpose(1, 0, 2, 3)
+
+
+def conv_bhw(P: "Params", level: int, gks: dict, w_int: np.ndarray, cts: np.ndarray, w_img: int) -> np.ndarray:
+    """Convolution of BHW-packed ciphertexts by rotations (App. D, homomorphic
+    convolutional layer): out[co] = sum_{ci,i,j} w[co][ci][i][j] Rot(ct[ci], i w_img + j),
+    k x k kernel, stride 1.  Output (y, x) of each image sits in the input's slot
+    of (y, x); slots with y > h-k or x > w_img-k hold neighbours' values (mask them).
+    gks: {steps: Galois key}; cts [cin][2][level][N] -> [cout][2][level][N]."""
+    cout, cin, k, _ = w_int.shape
+    rots = []
+    for ci in range(cin):
+        for i in range(k):
+            for j in range(k):
+                r = i * w_img + j
+                rots.append(cts[ci] if r == 0 else P.rotate(level, gks[r], r, cts[ci:ci + 1])[0])
+    x = np.stack(rots)
+    idx = np.tile(np.arange(cin * k * k, dtype=np.int32), (cout, 1))
+    return P.mac(level, idx, w_int.reshape(cout, -1).astype(np.int8), x)

@@ -104,6 +104,7 @@ _SIGS = {
     "bcn_op_square_relin_rescale": (_I, [_P, _I, _P, _P, _I, _P, _P, _SZ, _P]),
     "bcn_op_rescale": (_I, [_P, _I, _P, _I, _P, _P]),
     "bcn_galois_elt": (ctypes.c_uint32, [_P, _I]),
+    "bcn_op_mul_plain_rescale": (_I, [_P, _I, _P, _I, _P, _P, _P, _SZ, _P]),
     "bcn_galois_keygen": (_I, [_P, _P, _I, _U64, _P]),
     "bcn_op_rotate": (_I, [_P, _I, _P, _I, _P, _I, _P, _P, _SZ, _P]),
     "bcn_op_square_relin_rescale_noalloc": (_I, [_P, _I, _P, _P, _I, _P, _P]),
@@ -353,6 +354,14 @@ class Context:
                                    _dev_ptr(in_dev, n_ct * 2 * level * self.N), n_ct,
                                    _dev_ptr(out_dev, n_ct * 2 * level * self.N), ws.data_ptr(), nb, _stream(stream)),
                "bcn_op_rotate")
+
+    def op_mul_plain_rescale(self, level, in_dev, n_ct, pt_dev, out_dev, stream=None):
+        """(c0 u, c1 u), then rescale: in [n_ct][2][level][N], pt [level][N] -> out at level - 1."""
+        ws, nb = self._ws(level, n_ct)
+        _check(lib().bcn_op_mul_plain_rescale(self._h, level, _dev_ptr(in_dev, n_ct * 2 * level * self.N), n_ct,
+                                              _dev_ptr(pt_dev, level * self.N),
+                                              _dev_ptr(out_dev, n_ct * 2 * (level - 1) * self.N), ws.data_ptr(), nb,
+                                              _stream(stream)), "bcn_op_mul_plain_rescale")
 
     def op_rescale(self, level, in_dev, n_ct, out_dev, stream=None):
         _check(lib().bcn_op_rescale(self._h, level, _dev_ptr(in_dev, n_ct * 2 * level * self.N), n_ct,

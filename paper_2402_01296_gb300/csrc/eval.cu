@@ -195,6 +195,17 @@ __global__ void __launch_bounds__(256) k_moddown_rescale(const uint32_t *__restr
     }
 }
 
+// Pointwise product in the NTT domain (both operands canonical):
+// data[r][k] <- data[r][k] * u[r mod level][k] mod q_{r mod level}.  grid (N/256, rows)
+__global__ void __launch_bounds__(256) k_mul_ntt(uint32_t *__restrict__ data, const uint32_t *__restrict__ u,
+                                                 int level, int N, const PrimeConst *__restrict__ pc) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const int row = blockIdx.y, i = row % level;
+    uint32_t *x = data + (size_t)row * N + k;
+    *x = barrett_reduce64((uint64_t)*x * __ldg(u + (size_t)i * N + k), pc[i].q, pc[i].barrett);
+}
+
 // Rescale alone: in [C][2][n][N] -> out [C][2][n-1][N] (coefficient form). grid (N/256, 2, C)
 __global__ void __launch_bounds__(256) k_rescale(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int n,
                                                  int N, KsDev ks, const PrimeConst *__restrict__ pc) {
@@ -865,6 +876,45 @@ bcn_status bcn_op_square_relin_rescale(const bcn_ctx *c, int level, const uint32
     for (int o0 = 0; o0 < n_ct; o0 += chunk) {
         const int C = std::min(chunk, n_ct - o0);
         BCN_TRY(square_chunk(c, n, evk, in + (size_t)o0 * 2 * n * N, b, C, out + (size_t)o0 * 2 * (n - 1) * N, st));
+    }
+    return BCN_OK;
+}
+
+bcn_status bcn_op_mul_plain_rescale(const bcn_ctx *c, int level, const uint32_t *in, int n_ct, const uint32_t *pt,
+                                    uint32_t *out, void *ws, size_t ws_bytes, void *stream) {
+    BCN_TRY(check_device(c));
+    if (level < 2 || level > c->L) return fail(BCN_E_LEVEL, "bcn_op_mul_plain_rescale: level must be >= 2");
+    if (n_ct < 0) return fail(BCN_E_INVAL, "bcn_op_mul_plain_rescale: bad count");
+    if (n_ct == 0) return BCN_OK;
+    size_t need = 0;
+    BCN_TRY(bcn_op_workspace_bytes(c, level, n_ct, &need));
+    if (!ws || ws_bytes < need) return fail(BCN_E_BUDGET, "bcn_op_mul_plain_rescale: workspace too small");
+    if (!in || !out || !pt || !aligned16(in) || !aligned16(out) || !aligned16(pt) || !aligned16(ws))
+        return fail(BCN_E_INVAL, "bcn_op_mul_plain_rescale: null or unaligned buffer");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t N = c->N, ct_words = 2 * (size_t)level * N;
+    const size_t u_bytes = align_up((size_t)level * N * 4);
+    uint32_t *U = reinterpret_cast<uint32_t *>(ws);
+    uint32_t *X = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(ws) + u_bytes);
+    const size_t fit = (ws_bytes - u_bytes) / (ct_words * 4);
+    const int chunk = (int)std::min<size_t>({fit, (size_t)n_ct, (size_t)(65535 / (2 * level))});
+    if (chunk < 1) return fail(BCN_E_BUDGET, "bcn_op_mul_plain_rescale: workspace too small");
+    if (cudaMemcpyAsync(U, pt, (size_t)level * N * 4, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return fail(BCN_E_CUDA, "bcn_op_mul_plain_rescale: copy failed");
+    BCN_TRY(launch_ntt(c, U, (size_t)level, data_map(level), false, st));
+    for (int o0 = 0; o0 < n_ct; o0 += chunk) {
+        const int C = std::min(chunk, n_ct - o0);
+        if (cudaMemcpyAsync(X, in + (size_t)o0 * ct_words, (size_t)C * ct_words * 4, cudaMemcpyDeviceToDevice, st) !=
+            cudaSuccess)
+            return fail(BCN_E_CUDA, "bcn_op_mul_plain_rescale: copy failed");
+        const size_t rows = (size_t)2 * level * C;
+        BCN_TRY(launch_ntt(c, X, rows, data_map(level), false, st));
+        k_mul_ntt<<<dim3((unsigned)((N + 255) / 256), (unsigned)rows), 256, 0, st>>>(X, U, level, (int)N, c->d_pc);
+        BCN_TRY(check_launch("k_mul_ntt"));
+        BCN_TRY(launch_ntt(c, X, rows, data_map(level), true, st));
+        k_rescale<<<dim3((unsigned)((N + 255) / 256), 2, C), 256, 0, st>>>(
+            X, out + (size_t)o0 * 2 * (level - 1) * N, level, (int)N, ks_dev(c), c->d_pc);
+        BCN_TRY(check_launch("k_rescale"));
     }
     return BCN_OK;
 }

@@ -618,3 +618,35 @@ def test_rotation_of_an_encryption_decrypts_to_the_rotated_slots(cfg):
             dec = O.decode(O.crt_centered(P.decrypt(sk, r, level), P.q[:level]), P.N, P.N // 2, S)
             # noise: the key switch (well below 2^20 here) over the scale
             assert np.abs(dec - np.roll(z, -steps, axis=1)).max() < 2.0**20 / S
+
+
+def test_bhw_conv_by_rotations_is_the_convolution():
+    """App. D: with n images' h x w segments of a channel in one ciphertext, the
+    sum of rotated copies weighted by the kernel computes the convolution in the
+    valid slots; a 0/1 mask encoded at the top prime's scale, multiplied in and
+    rescaled away, zeroes the other slots.  Against torch conv2d."""
+    P = O.Params(10, 4, 1, 1)
+    n, cin, cout, h, w, k = 4, 2, 3, 10, 10, 3
+    rng = np.random.default_rng(50)
+    x = rng.uniform(-1, 1, (n, cin, h, w))
+    wi = rng.integers(-127, 128, (cout, cin, k, k)).astype(np.int8)
+    sk, _ = P.keygen(3)
+    S = 2.0**30
+    cts = P.encrypt(sk, O.encode(O.pack_bhw(x, P.N), P.N, S, P.q), P.L, 4)
+    steps = {i * w + j for i in range(k) for j in range(k)} - {0}
+    gks = {r: P.galois_keygen(sk, r, 60 + r) for r in steps}
+    out = O.conv_bhw(P, P.L, gks, wi, cts, w)
+    ref = F.conv2d(torch.from_numpy(x), torch.from_numpy(wi.astype(np.float64))).numpy()  # valid, stride 1
+    dec = O.decode(O.crt_centered(P.decrypt(sk, out, P.L), P.q), P.N, P.N // 2, S)
+    got = O.unpack_bhw(dec, n, h, w)[:, :, :h - k + 1, :w - k + 1]
+    assert np.abs(got - ref).max() < 1e-3
+    # mask the invalid slots: multiply by the 0/1 mask at scale q_top, rescale
+    m = np.zeros((n, 1, h, w))
+    m[:, :, :h - k + 1, :w - k + 1] = 1
+    mask = O.encode(O.pack_bhw(m, P.N), P.N, float(P.q[P.L - 1]), P.q)[0]
+    masked = P.rescale(P.L, P.mul_plain(P.L, out, mask))
+    dm = O.unpack_bhw(O.decode(O.crt_centered(P.decrypt(sk, masked, P.L - 1), P.q[:P.L - 1]), P.N, P.N // 2, S),
+                      n, h, w)
+    assert np.abs(dm[:, :, :h - k + 1, :w - k + 1] - ref).max() < 1e-3
+    dm[:, :, :h - k + 1, :w - k + 1] = 0
+    assert np.abs(dm).max() < 1e-3
