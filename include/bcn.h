@@ -265,6 +265,14 @@ bcn_status bcn_eval_host_workspace_bytes(const bcn_model *m, size_t *bytes);
 bcn_status bcn_eval_host(const bcn_model *m, const uint32_t *evk_eval_dev, const uint32_t *cts_host,
                          const uint32_t *const *pts_host, uint32_t *out_host, void *workspace_dev,
                          size_t workspace_bytes, void *cuda_stream);
+/* The same without the final synchronisation: every copy and kernel is queued
+ * behind the earlier work on `cuda_stream` and out_host holds the result once
+ * that stream has passed this call (synchronise it or record an event).  The
+ * host buffers must stay valid and unchanged until then.  With two workspaces
+ * on two streams, one evaluation's copies overlap another's kernels. */
+bcn_status bcn_eval_host_async(const bcn_model *m, const uint32_t *evk_eval_dev, const uint32_t *cts_host,
+                               const uint32_t *const *pts_host, uint32_t *out_host, void *workspace_dev,
+                               size_t workspace_bytes, void *cuda_stream);
 
 /* ------------------------------------------------ batched evaluation (device) */
 /* Many evaluations of different models (ring degrees, segment sizes) replayed

@@ -89,6 +89,7 @@ _SIGS = {
     "bcn_eval": (_I, [_P, _P, _P, _P, _P, _P, _SZ, _P]),
     "bcn_eval_host_workspace_bytes": (_I, [_P, ctypes.POINTER(_SZ)]),
     "bcn_eval_host": (_I, [_P, _P, _P, _P, _P, _P, _SZ, _P]),
+    "bcn_eval_host_async": (_I, [_P, _P, _P, _P, _P, _P, _SZ, _P]),
     "bcn_batch_plan": (_I, [_P, _I, _I, ctypes.POINTER(_SZ)]),
     "bcn_batch_create": (_I, [_P, _I, _I, _P, _SZ, ctypes.POINTER(_P)]),
     "bcn_batch_launch": (_I, [_P, _P]),
@@ -481,6 +482,19 @@ class Model:
         _check(lib().bcn_eval_host(self._h, _dev_ptr(evk_eval, self.ctx.evk_words()), cts_host.ctypes.data,
                                    ctypes.cast(arr, _P), out_host.ctypes.data, workspace.data_ptr(),
                                    workspace.numel() * workspace.element_size(), _stream(stream)), "bcn_eval_host")
+
+    def eval_host_async(self, evk_eval, cts_host: np.ndarray, pts_host: list, out_host: np.ndarray, workspace,
+                        stream=None):
+        """eval_host without the final synchronisation: out_host is ready once
+        `stream` has passed this call; the host buffers must stay alive until then."""
+        for a in [cts_host, out_host, *pts_host]:
+            assert a.dtype == np.uint32 and a.flags["C_CONTIGUOUS"]
+        assert out_host.shape == self.out_shape()
+        arr = (_P * max(1, len(pts_host)))(*[p.ctypes.data for p in pts_host])
+        _check(lib().bcn_eval_host_async(self._h, _dev_ptr(evk_eval, self.ctx.evk_words()), cts_host.ctypes.data,
+                                         ctypes.cast(arr, _P), out_host.ctypes.data, workspace.data_ptr(),
+                                         workspace.numel() * workspace.element_size(), _stream(stream)),
+               "bcn_eval_host_async")
 
 
 class Batch:

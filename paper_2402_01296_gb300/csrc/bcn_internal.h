@@ -5,6 +5,7 @@
 #include <cstdint>
 #include <cstring>
 #include <string>
+#include <mutex>
 #include <vector>
 
 #include <cuda_runtime_api.h>
@@ -145,6 +146,9 @@ struct bcn_model {
     int chunk;          // ciphertexts per key-switching chunk
     int chunk_request;  // 0: automatic
     int mac_impl = 0;   // 0: tensor cores where eligible, 1: CUDA cores only
+    // copy streams of bcn_eval_host (created on first use, guarded by copy_mu)
+    std::mutex copy_mu;
+    std::vector<cudaStream_t> copy_streams;
     size_t ws_x_bytes;  // one ping-pong activation buffer
     size_t ws_y_bytes;  // MAC output of a square layer
     size_t ws_chunk_bytes;

@@ -599,6 +599,7 @@ bcn_status bcn_model_destroy(bcn_model *m) {
         cudaFree(p.tc.w16);
     }
     for (auto e : m->prof.ev) cudaEventDestroy(e);
+    for (auto s2 : m->copy_streams) cudaStreamDestroy(s2);
     delete m;
     return BCN_OK;
 }
@@ -660,8 +661,20 @@ bcn_status bcn_eval_workspace_bytes(const bcn_model *m, size_t *bytes) {
     return BCN_OK;
 }
 
+// The evaluation; with layer_ready, the stream waits for layer_ready[l] (when
+// not null) before layer l's first launch (bcn_eval_host: feature copies).
+static bcn_status eval_impl(const bcn_model *m, const uint32_t *evk, const uint32_t *cts, const uint32_t *const *pts,
+                            uint32_t *out, void *ws, size_t ws_bytes, void *stream,
+                            const std::vector<std::vector<cudaEvent_t>> *layer_ready);
+
 bcn_status bcn_eval(const bcn_model *m, const uint32_t *evk, const uint32_t *cts, const uint32_t *const *pts,
                     uint32_t *out, void *ws, size_t ws_bytes, void *stream) {
+    return eval_impl(m, evk, cts, pts, out, ws, ws_bytes, stream, nullptr);
+}
+
+static bcn_status eval_impl(const bcn_model *m, const uint32_t *evk, const uint32_t *cts, const uint32_t *const *pts,
+                            uint32_t *out, void *ws, size_t ws_bytes, void *stream,
+                            const std::vector<std::vector<cudaEvent_t>> *layer_ready) {
     if (!m) return fail(BCN_E_INVAL, "bcn_eval: null model");
     const bcn_ctx *c = m->ctx;
     BCN_TRY(check_device(c));
@@ -684,6 +697,9 @@ bcn_status bcn_eval(const bcn_model *m, const uint32_t *evk, const uint32_t *cts
         const bcn_layer_plan &p = m->layers[l];
         const bool last = l + 1 == m->layers.size();
         uint32_t *y = last ? out : X[l % 2];
+        if (layer_ready != nullptr)
+            for (cudaEvent_t e : (*layer_ready)[l])
+                if (cudaStreamWaitEvent(st, e, 0) != cudaSuccess) return fail(BCN_E_CUDA, "bcn_eval: event wait");
         const uint32_t *pt = nullptr;
         if (p.add) {
             if (!pts || !pts[a] || !aligned16(pts[a]))
@@ -741,6 +757,15 @@ bcn_status bcn_eval_host_workspace_bytes(const bcn_model *m, size_t *bytes) {
 
 bcn_status bcn_eval_host(const bcn_model *m, const uint32_t *evk, const uint32_t *cts_h,
                          const uint32_t *const *pts_h, uint32_t *out_h, void *ws, size_t ws_bytes, void *stream) {
+    BCN_TRY(bcn_eval_host_async(m, evk, cts_h, pts_h, out_h, ws, ws_bytes, stream));
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return fail(BCN_E_CUDA, std::string("bcn_eval_host: ") + cudaGetErrorString(e));
+    return BCN_OK;
+}
+
+bcn_status bcn_eval_host_async(const bcn_model *m, const uint32_t *evk, const uint32_t *cts_h,
+                               const uint32_t *const *pts_h, uint32_t *out_h, void *ws, size_t ws_bytes,
+                               void *stream) {
     if (!m || !cts_h || !out_h) return fail(BCN_E_INVAL, "bcn_eval_host: null argument");
     const bcn_ctx *c = m->ctx;
     BCN_TRY(check_device(c));
@@ -748,33 +773,79 @@ bcn_status bcn_eval_host(const bcn_model *m, const uint32_t *evk, const uint32_t
     bcn_eval_host_workspace_bytes(m, &need);
     bcn_eval_workspace_bytes(m, &eval_need);
     if (ws_bytes < need || !ws) return fail(BCN_E_BUDGET, "bcn_eval_host: workspace too small");
+    int n_add = 0;
+    for (auto &l : m->layers) n_add += l.add;
+    for (int a = 0; a < n_add; a++)
+        if (!pts_h || !pts_h[a]) return fail(BCN_E_INVAL, "bcn_eval_host: missing feature plaintexts");
     cudaStream_t st = (cudaStream_t)stream;
-    char *w = reinterpret_cast<char *>(ws);
-    char *p = w + align_up(eval_need);
+    // Host-to-device copies go out in kCopyLanes parts on as many streams (the
+    // copies run side by side), each after the caller's earlier work on `st`
+    // (the workspace may still be in use); layer l waits only for its inputs,
+    // so the later layers' features copy while the first layers compute.
+    constexpr int kCopyLanes = 4;
+    bcn_model *mm = const_cast<bcn_model *>(m);
+    std::lock_guard<std::mutex> lock(mm->copy_mu);
+    if (mm->copy_streams.empty()) {
+        for (int i = 0; i < kCopyLanes; i++) {
+            cudaStream_t s2 = nullptr;
+            if (cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking) != cudaSuccess)
+                return fail(BCN_E_CUDA, "bcn_eval_host: stream creation failed");
+            mm->copy_streams.push_back(s2);
+        }
+    }
+    std::vector<cudaEvent_t> events;
+    auto new_event = [&](cudaEvent_t *e) {
+        if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return false;
+        events.push_back(*e);
+        return true;
+    };
+    auto cleanup = [&](bcn_status s, const char *msg) {
+        for (cudaEvent_t e : events) cudaEventDestroy(e);
+        return s == BCN_OK ? BCN_OK : fail(s, msg);
+    };
+    cudaEvent_t start;
+    if (!new_event(&start) || cudaEventRecord(start, st) != cudaSuccess)
+        return cleanup(BCN_E_CUDA, "bcn_eval_host: event failed");
+    for (cudaStream_t s2 : mm->copy_streams)
+        if (cudaStreamWaitEvent(s2, start, 0) != cudaSuccess) return cleanup(BCN_E_CUDA, "bcn_eval_host: event wait");
+    // one buffer: kCopyLanes parts, one event per part
+    auto copy_in = [&](void *dst, const void *src, size_t bytes, std::vector<cudaEvent_t> &ready) {
+        const size_t part = (bytes / kCopyLanes + 255) / 256 * 256;
+        for (int i = 0; i < kCopyLanes; i++) {
+            const size_t off = (size_t)i * part;
+            if (off >= bytes) break;
+            const size_t nb = std::min(part, bytes - off);
+            cudaEvent_t e;
+            if (cudaMemcpyAsync((char *)dst + off, (const char *)src + off, nb, cudaMemcpyHostToDevice,
+                                mm->copy_streams[i]) != cudaSuccess ||
+                !new_event(&e) || cudaEventRecord(e, mm->copy_streams[i]) != cudaSuccess)
+                return false;
+            ready.push_back(e);
+        }
+        return true;
+    };
+    char *p = reinterpret_cast<char *>(ws) + align_up(eval_need);
     const size_t cts_b = (size_t)m->layers.front().n_in * 2 * c->L * c->N * 4;
     uint32_t *cts_d = reinterpret_cast<uint32_t *>(p);
     p += align_up(cts_b);
-    if (cudaMemcpyAsync(cts_d, cts_h, cts_b, cudaMemcpyHostToDevice, st) != cudaSuccess)
-        return fail(BCN_E_CUDA, "bcn_eval_host: input copy failed");
+    std::vector<std::vector<cudaEvent_t>> ready(m->layers.size());
+    if (!copy_in(cts_d, cts_h, cts_b, ready[0])) return cleanup(BCN_E_CUDA, "bcn_eval_host: input copy failed");
     std::vector<const uint32_t *> pts_d;
-    int n_add = 0;
-    for (auto &l : m->layers) n_add += l.add;
-    for (int a = 0; a < n_add; a++) {
-        if (!pts_h || !pts_h[a]) return fail(BCN_E_INVAL, "bcn_eval_host: missing feature plaintexts");
-        const size_t b = pts_words(m, a) * 4;
-        if (cudaMemcpyAsync(p, pts_h[a], b, cudaMemcpyHostToDevice, st) != cudaSuccess)
-            return fail(BCN_E_CUDA, "bcn_eval_host: feature copy failed");
+    for (size_t l = 0, a = 0; l < m->layers.size(); l++) {
+        if (!m->layers[l].add) continue;
+        const size_t b = pts_words(m, (int)a) * 4;
+        if (!copy_in(p, pts_h[a], b, ready[l])) return cleanup(BCN_E_CUDA, "bcn_eval_host: feature copy failed");
         pts_d.push_back(reinterpret_cast<const uint32_t *>(p));
         p += align_up(b);
+        a++;
     }
     uint32_t *out_d = reinterpret_cast<uint32_t *>(p);
-    BCN_TRY(bcn_eval(m, evk, cts_d, pts_d.data(), out_d, ws, eval_need, stream));
+    bcn_status s = eval_impl(m, evk, cts_d, pts_d.data(), out_d, ws, eval_need, stream, &ready);
+    if (s != BCN_OK) return cleanup(s, bcn_last_error());
     const size_t out_b = (size_t)m->layers.back().n_out * 2 * m->out_level * c->N * 4;
     if (cudaMemcpyAsync(out_h, out_d, out_b, cudaMemcpyDeviceToHost, st) != cudaSuccess)
-        return fail(BCN_E_CUDA, "bcn_eval_host: output copy failed");
-    cudaError_t e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return fail(BCN_E_CUDA, std::string("bcn_eval_host: ") + cudaGetErrorString(e));
-    return BCN_OK;
+        return cleanup(BCN_E_CUDA, "bcn_eval_host: output copy failed");
+    return cleanup(BCN_OK, "");  // events are released once the device has passed them
 }
 
 // ------------------------------------------------------------- kernel timing

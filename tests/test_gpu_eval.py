@@ -104,6 +104,27 @@ def test_eval_host_path_matches_device_path(case):
         assert np.array_equal(out, ref)
 
 
+def test_eval_host_async_two_in_flight(case):
+    """Two host-buffer evaluations in flight on two streams (their copies share
+    the model's copy streams): both results equal the oracle's."""
+    cfg, prob, ref = case
+    ctx = bcn.Context.from_config(cfg)
+    model = bcn.Model(ctx, cfg["cipher"], prob.w_int, prob.s_w)
+    evk_eval = ctx.evk_prepare(dev(prob.evk))
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).pin_memory()  # noqa: E731
+    u32 = lambda t: t.numpy().view(np.uint32)  # noqa: E731
+    cts_h, pts_h = pin(prob.cts), [pin(p) for p in prob.pts]
+    outs = [torch.zeros(model.out_shape(), dtype=torch.int32).pin_memory() for _ in range(2)]
+    wss = [model.alloc_workspace(host=True) for _ in range(2)]
+    sts = [torch.cuda.Stream(), torch.cuda.Stream()]
+    for rep in range(3):
+        for i in range(2):
+            model.eval_host_async(evk_eval, u32(cts_h), [u32(p) for p in pts_h], u32(outs[i]), wss[i], sts[i])
+    torch.cuda.synchronize()
+    for o in outs:
+        assert np.array_equal(u32(o), ref)
+
+
 def test_eval_is_deterministic_and_stream_ordered():
     cfg = workloads.with_batch(workloads.get_config("cnn3_small"), 128)
     prob = O.Problem(cfg)
