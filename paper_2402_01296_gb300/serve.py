@@ -143,8 +143,10 @@ class Server:
                 if lane.req is None and queue:
                     self._start(lane, queue.pop(0), now)
                     progressed = True
-            if not progressed:
-                if sleep and not queue and nxt < len(pending):
+            if not progressed and sleep and not queue and nxt < len(pending):
+                # idle until the next arrival -- unless a lane is busy, whose
+                # completion must be seen (and its lane reused) when it happens
+                if not any(lane.req is not None for lane in self.lanes):
                     wait = pending[nxt].arrival - (time.perf_counter() - t0)
                     if wait > 2e-4:
                         time.sleep(wait - 1e-4)
