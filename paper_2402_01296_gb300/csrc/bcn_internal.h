@@ -41,7 +41,7 @@ struct PrimeConst {
     uint32_t half;       // (q - 1) / 2: the largest residue whose centred value is >= 0
     uint32_t rn;         // R * N^{-1} mod q: Montgomery form of N^{-1}
     uint32_t rn_shoup;   // Shoup companion of rn
-    uint32_t pad_;
+    uint32_t one;        // 1, read at run time: multiply-adds by it stay on the FMA pipe
     uint64_t barrett;    // floor(2^64 / q)
     uint64_t mac_offset; // a multiple of q >= 2^58 (makes a signed MAC sum non-negative)
 };

@@ -39,6 +39,12 @@ __global__ void __launch_bounds__((1 << LOGN) / R) k_ntt_inv(uint32_t *__restric
     C::store_natural(x, a, tid);
 }
 
+// The lazy butterflies' additions go through the FMA pipe (ModQ::one read at
+// run time) where registers are plentiful; at N = 16384 (1024-thread blocks,
+// 64 registers) the compile-time 1 folds them back into plain additions.
+template <int LOGN>
+constexpr bool kFmaOne = LOGN <= 13;
+
 // Register budget per thread of the fused kernels (sets their blocks per SM).
 #ifndef BCN_CORE_REGS
 #define BCN_CORE_REGS 128
@@ -71,12 +77,12 @@ __global__ void __launch_bounds__((1 << LOGN) / R, CoreOcc<(1 << LOGN) / R>::MIN
     uint32_t x[R];
     // c0 -> NTT, parked in s1
     C::load_natural(x, Y + (((size_t)ct * 2 + 0) * n + i) * N, tid);
-    C::forward(x, sm, tid, P.q, tf);
+    C::forward(x, sm, tid, ModQ(P.q, kFmaOne<LOGN> ? P.one : 1u), tf);
 #pragma unroll
     for (int u = 0; u < R; u++) s1[u * T + tid] = x[u];
     // c1 -> NTT; c0^2/N in registers, 2 c0 c1/N in s1, c1^2/N in s2 (inputs in [0, 4q))
     C::load_natural(x, Y + (((size_t)ct * 2 + 1) * n + i) * N, tid);
-    C::forward(x, sm, tid, P.q, tf);
+    C::forward(x, sm, tid, ModQ(P.q, kFmaOne<LOGN> ? P.one : 1u), tf);
     if (D2N != nullptr) {
         uint32_t y[R];
 #pragma unroll
@@ -96,15 +102,15 @@ __global__ void __launch_bounds__((1 << LOGN) / R, CoreOcc<(1 << LOGN) / R>::MIN
         s2[u * T + tid] = mont_mul(bRN, b, P.q, P.qneg_inv);
         x[u] = mont_mul(aRN, a, P.q, P.qneg_inv);
     }
-    C::inverse_unscaled(x, sm, tid, P.q, ti);
+    C::inverse_unscaled(x, sm, tid, ModQ(P.q, kFmaOne<LOGN> ? P.one : 1u), ti);
     C::store_natural(x, D + (((size_t)ct * 3 + 0) * n + i) * N, tid);
 #pragma unroll
     for (int u = 0; u < R; u++) x[u] = s1[u * T + tid];
-    C::inverse_unscaled(x, sm, tid, P.q, ti);
+    C::inverse_unscaled(x, sm, tid, ModQ(P.q, kFmaOne<LOGN> ? P.one : 1u), ti);
     C::store_natural(x, D + (((size_t)ct * 3 + 1) * n + i) * N, tid);
 #pragma unroll
     for (int u = 0; u < R; u++) x[u] = s2[u * T + tid];
-    C::inverse_unscaled(x, sm, tid, P.q, ti);
+    C::inverse_unscaled(x, sm, tid, ModQ(P.q, kFmaOne<LOGN> ? P.one : 1u), ti);
     C::store_natural(x, D + (((size_t)ct * 3 + 2) * n + i) * N, tid);
 }
 
@@ -128,12 +134,16 @@ __device__ __forceinline__ void ks_core_body(const uint32_t *__restrict__ D, con
     // running sums r0 += x k0 / R, r1 += x k1 / R: kept in [0, 2q) with lazy
     // Montgomery products on the data primes (the lazy inverse NTT takes
     // [0, 2q)), canonical on the special primes
-    auto ks_accumulate = [](uint32_t &r0, uint32_t &r1, uint32_t xv, uint32_t w0, uint32_t w1,
-                            const PrimeConst &P) {
+    // (additions through the FMA pipe as in the lazy butterflies)
+    const uint32_t one = kFmaOne<LOGN> ? pc[0].one : 1u;
+    auto ks_accumulate = [one](uint32_t &r0, uint32_t &r1, uint32_t xv, uint32_t w0, uint32_t w1,
+                               const PrimeConst &P) {
         if constexpr (LAZY) {
-            const uint32_t q2 = 2 * P.q;
-            r0 = reduce_once(r0 + mont_mul_lazy(xv, w0, P.q, P.qneg_inv), q2);
-            r1 = reduce_once(r1 + mont_mul_lazy(xv, w1, P.q, P.qneg_inv), q2);
+            const uint32_t nq2 = 0u - 2 * P.q;
+            const uint32_t a0 = mont_mul_lazy(xv, w0, P.q, P.qneg_inv) * one + r0;
+            const uint32_t a1 = mont_mul_lazy(xv, w1, P.q, P.qneg_inv) * one + r1;
+            r0 = min(a0, a0 * one + nq2);
+            r1 = min(a1, a1 * one + nq2);
         } else {
             r0 = add_mod(r0, mont_mul(xv, w0, P.q, P.qneg_inv), P.q);
             r1 = add_mod(r1, mont_mul(xv, w1, P.q, P.qneg_inv), P.q);
@@ -162,12 +172,23 @@ __device__ __forceinline__ void ks_core_body(const uint32_t *__restrict__ D, con
                 const uint32_t half = pc[j].half;
                 const uint32_t dp = ks.dprod[(size_t)(n * ks.dnum_max + j) * ks.P + pt];  // q_j mod t
                 const uint32_t *xj = x2 + (size_t)j * N;
+                if constexpr (LAZY) {
+                    // d - [d > (q_j-1)/2] q_j as d + (t - q_j mod t): below q_j + t < 3t (the
+                    // data primes are within a factor 2), a valid lazy NTT input
+                    const uint32_t tmq = P.q - dp;
 #pragma unroll
-                for (int u = 0; u < R; u++) {
-                    const uint32_t d = __ldg(xj + tid + u * T);
-                    uint32_t y = reduce_once(d, P.q);  // d < q_j < 2t
-                    if (d > half) y = sub_mod(y, dp, P.q);
-                    x[u] = y;
+                    for (int u = 0; u < R; u++) {
+                        const uint32_t d = __ldg(xj + tid + u * T);
+                        x[u] = d * one + (d > half ? tmq : 0u);
+                    }
+                } else {
+#pragma unroll
+                    for (int u = 0; u < R; u++) {
+                        const uint32_t d = __ldg(xj + tid + u * T);
+                        uint32_t y = reduce_once(d, P.q);  // d < q_j < 2t
+                        if (d > half) y = sub_mod(y, dp, P.q);
+                        x[u] = y;
+                    }
                 }
             } else {
 #pragma unroll
@@ -188,7 +209,7 @@ __device__ __forceinline__ void ks_core_body(const uint32_t *__restrict__ D, con
                     }
                 }
             }
-            C::forward(x, sm, tid, P.q, tf);
+            C::forward(x, sm, tid, ModQ(P.q, kFmaOne<LOGN> ? P.one : 1u), tf);
         }
         const uint32_t *k0 = evk + ((size_t)(j * 2 + 0) * ks.P + pt) * N;
         const uint32_t *k1 = evk + ((size_t)(j * 2 + 1) * ks.P + pt) * N;
@@ -224,11 +245,11 @@ __device__ __forceinline__ void ks_core_body(const uint32_t *__restrict__ D, con
     }
 #pragma unroll
     for (int u = 0; u < R; u++) x[u] = s0[u * T + tid];
-    C::inverse_unscaled(x, sm, tid, P.q, ti);
+    C::inverse_unscaled(x, sm, tid, ModQ(P.q, kFmaOne<LOGN> ? P.one : 1u), ti);
     C::store_natural(x, acc_out + (((size_t)ct * 2 + 0) * nb + t) * N, tid);
 #pragma unroll
     for (int u = 0; u < R; u++) x[u] = s1[u * T + tid];
-    C::inverse_unscaled(x, sm, tid, P.q, ti);
+    C::inverse_unscaled(x, sm, tid, ModQ(P.q, kFmaOne<LOGN> ? P.one : 1u), ti);
     C::store_natural(x, acc_out + (((size_t)ct * 2 + 1) * nb + t) * N, tid);
 }
 

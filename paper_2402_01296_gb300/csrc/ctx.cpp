@@ -213,7 +213,7 @@ bcn_status bcn_ctx_create(const bcn_params *p, int device, bcn_ctx **out) {
         pc.half = (uint32_t)((q - 1) / 2);
         pc.rn = (uint32_t)mulmod64(pc.r_mod, pc.ninv, q);
         pc.rn_shoup = shoup_companion(pc.rn, pc.q);
-        pc.pad_ = 0;
+        pc.one = 1;
         pc.barrett = (uint64_t)(((unsigned __int128)1 << 64) / q);
         pc.mac_offset = ((1ull << 58) / q + 1) * q;
     }

@@ -43,6 +43,15 @@
 
 namespace bcn {
 
+// A prime and the value 1 read at run time.  The lazy butterflies add through
+// multiply-adds by `one`, which the compiler cannot fold into plain additions:
+// they issue on the FMA pipe and leave the half-rate ALU pipe to the min and
+// three-input add that remain.  Constructed from q alone, one is the constant 1.
+struct ModQ {
+    uint32_t q, one;
+    __device__ __forceinline__ ModQ(uint32_t q_, uint32_t one_ = 1u) : q(q_), one(one_) {}
+};
+
 template <int LOGN, int R, bool LAZY = false>
 struct NttCore {
     static constexpr int N = 1 << LOGN;
@@ -145,9 +154,10 @@ struct NttCore {
 
     // stage s0 + KS of pass P (forward) for group g
     template <int P, int KS>
-    __device__ __forceinline__ static void stage_fwd(uint32_t (&x)[R], int g, int hi, uint32_t q,
+    __device__ __forceinline__ static void stage_fwd(uint32_t (&x)[R], int g, int hi, ModQ m,
                                                      const uint2 *__restrict__ tw) {
         constexpr int rp = rp_of(P), s = s0_of(P) + KS, d = 1 << (rp - 1 - KS);
+        const uint32_t q = m.q;
         uint2 Wt[1 << KS];
         load_stage_tw<KS>(Wt, tw, s, hi);
 #pragma unroll
@@ -157,9 +167,10 @@ struct NttCore {
             for (int w = 0; w < d; w++) {
                 const int u = (g << rp) + b * 2 * d + w;
                 if constexpr (LAZY) {
-                    const uint32_t q2 = 2 * q;
-                    const uint32_t U = reduce_once(x[u], q2), V = shoup_mul_lazy(x[u + d], W.x, W.y, q);
-                    x[u] = U + V;           // [0, 4q)
+                    const uint32_t q2 = 2 * q, nq2 = 0u - q2, xu = x[u];
+                    const uint32_t U = min(xu, xu * m.one + nq2);  // [0, 2q)
+                    const uint32_t V = shoup_mul_lazy(x[u + d], W.x, W.y, q);
+                    x[u] = V * m.one + U;   // [0, 4q)
                     x[u + d] = U - V + q2;  // [0, 4q)
                 } else {
                     const uint32_t U = x[u], V = shoup_mul(x[u + d], W.x, W.y, q);
@@ -168,14 +179,15 @@ struct NttCore {
                 }
             }
         }
-        if constexpr (KS + 1 < rp) stage_fwd<P, KS + 1>(x, g, hi, q, tw);
+        if constexpr (KS + 1 < rp) stage_fwd<P, KS + 1>(x, g, hi, m, tw);
     }
 
     // stage s0 + KS of pass P (inverse), then the stages below it
     template <int P, int KS>
-    __device__ __forceinline__ static void stage_inv(uint32_t (&x)[R], int g, int hi, uint32_t q,
+    __device__ __forceinline__ static void stage_inv(uint32_t (&x)[R], int g, int hi, ModQ m,
                                                      const uint2 *__restrict__ tw) {
         constexpr int rp = rp_of(P), s = s0_of(P) + KS, d = 1 << (rp - 1 - KS);
+        const uint32_t q = m.q;
         uint2 Wt[1 << KS];
         load_stage_tw<KS>(Wt, tw, s, hi);
 #pragma unroll
@@ -186,8 +198,8 @@ struct NttCore {
                 const int u = (g << rp) + b * 2 * d + w;
                 const uint32_t U = x[u], V = x[u + d];
                 if constexpr (LAZY) {
-                    const uint32_t q2 = 2 * q;
-                    x[u] = reduce_once(U + V, q2);                             // [0, 2q)
+                    const uint32_t q2 = 2 * q, nq2 = 0u - q2, sum = V * m.one + U;
+                    x[u] = min(sum, sum * m.one + nq2);                        // [0, 2q)
                     x[u + d] = shoup_mul_lazy(U - V + q2, W.x, W.y, q);        // [0, 2q)
                 } else {
                     x[u] = add_mod(U, V, q);
@@ -195,68 +207,68 @@ struct NttCore {
                 }
             }
         }
-        if constexpr (KS > 0) stage_inv<P, KS - 1>(x, g, hi, q, tw);
+        if constexpr (KS > 0) stage_inv<P, KS - 1>(x, g, hi, m, tw);
     }
 
     template <int P>
-    __device__ __forceinline__ static void pass_fwd(uint32_t (&x)[R], int tid, uint32_t q,
+    __device__ __forceinline__ static void pass_fwd(uint32_t (&x)[R], int tid, ModQ m,
                                                     const uint2 *__restrict__ tw) {
         constexpr int rp = rp_of(P);
 #pragma unroll
         for (int g = 0; g < (R >> rp); g++) {
             const int hi = gidx_of<P>(g, tid) >> (LOGN - s1_of(P));
-            stage_fwd<P, 0>(x, g, hi, q, tw);
+            stage_fwd<P, 0>(x, g, hi, m, tw);
         }
     }
     template <int P>
-    __device__ __forceinline__ static void pass_inv(uint32_t (&x)[R], int tid, uint32_t q,
+    __device__ __forceinline__ static void pass_inv(uint32_t (&x)[R], int tid, ModQ m,
                                                     const uint2 *__restrict__ tw) {
         constexpr int rp = rp_of(P);
 #pragma unroll
         for (int g = 0; g < (R >> rp); g++) {
             const int hi = gidx_of<P>(g, tid) >> (LOGN - s1_of(P));
-            stage_inv<P, rp - 1>(x, g, hi, q, tw);
+            stage_inv<P, rp - 1>(x, g, hi, m, tw);
         }
     }
 
     template <int P>
-    __device__ __forceinline__ static void forward_from(uint32_t (&x)[R], uint32_t *sm, int tid, uint32_t q,
+    __device__ __forceinline__ static void forward_from(uint32_t (&x)[R], uint32_t *sm, int tid, ModQ m,
                                                         const uint2 *__restrict__ tw) {
         if constexpr (P > 0) exchange<P - 1, P, P == 1>(x, sm, tid);
-        pass_fwd<P>(x, tid, q, tw);
-        if constexpr (P + 1 < PASSES) forward_from<P + 1>(x, sm, tid, q, tw);
+        pass_fwd<P>(x, tid, m, tw);
+        if constexpr (P + 1 < PASSES) forward_from<P + 1>(x, sm, tid, m, tw);
     }
     template <int P>
-    __device__ __forceinline__ static void inverse_from(uint32_t (&x)[R], uint32_t *sm, int tid, uint32_t q,
+    __device__ __forceinline__ static void inverse_from(uint32_t (&x)[R], uint32_t *sm, int tid, ModQ m,
                                                         const uint2 *__restrict__ tw) {
-        pass_inv<P>(x, tid, q, tw);
+        pass_inv<P>(x, tid, m, tw);
         if constexpr (P > 0) {
             exchange<P, P - 1, P == PASSES - 1>(x, sm, tid);
-            inverse_from<P - 1>(x, sm, tid, q, tw);
+            inverse_from<P - 1>(x, sm, tid, m, tw);
         }
     }
 
     // x: pass-0 distribution (natural order) -> last-pass distribution (NTT domain)
-    __device__ __forceinline__ static void forward(uint32_t (&x)[R], uint32_t *sm, int tid, uint32_t q,
+    __device__ __forceinline__ static void forward(uint32_t (&x)[R], uint32_t *sm, int tid, ModQ m,
                                                    const uint2 *__restrict__ tw) {
-        forward_from<0>(x, sm, tid, q, tw);
+        forward_from<0>(x, sm, tid, m, tw);
     }
 
     // x: last-pass distribution (NTT domain) -> pass-0 distribution, times N^{-1}
-    __device__ __forceinline__ static void inverse(uint32_t (&x)[R], uint32_t *sm, int tid, uint32_t q,
+    __device__ __forceinline__ static void inverse(uint32_t (&x)[R], uint32_t *sm, int tid, ModQ m,
                                                    const uint2 *__restrict__ tw, uint32_t ninv, uint32_t ninv_shoup) {
-        inverse_from<PASSES - 1>(x, sm, tid, q, tw);
+        inverse_from<PASSES - 1>(x, sm, tid, m, tw);
 #pragma unroll
-        for (int u = 0; u < R; u++) x[u] = shoup_mul(x[u], ninv, ninv_shoup, q);
+        for (int u = 0; u < R; u++) x[u] = shoup_mul(x[u], ninv, ninv_shoup, m.q);
     }
     // the same without the N^{-1} factor (callers that folded it into their
     // inputs); the result is canonical
-    __device__ __forceinline__ static void inverse_unscaled(uint32_t (&x)[R], uint32_t *sm, int tid, uint32_t q,
+    __device__ __forceinline__ static void inverse_unscaled(uint32_t (&x)[R], uint32_t *sm, int tid, ModQ m,
                                                             const uint2 *__restrict__ tw) {
-        inverse_from<PASSES - 1>(x, sm, tid, q, tw);
+        inverse_from<PASSES - 1>(x, sm, tid, m, tw);
         if constexpr (LAZY) {
 #pragma unroll
-            for (int u = 0; u < R; u++) x[u] = reduce_once(x[u], q);
+            for (int u = 0; u < R; u++) x[u] = reduce_once(x[u], m.q);
         }
     }
 
