@@ -265,11 +265,15 @@ bcn_status bcn_eval_host_workspace_bytes(const bcn_model *m, size_t *bytes);
 bcn_status bcn_eval_host(const bcn_model *m, const uint32_t *evk_eval_dev, const uint32_t *cts_host,
                          const uint32_t *const *pts_host, uint32_t *out_host, void *workspace_dev,
                          size_t workspace_bytes, void *cuda_stream);
-/* The same without the final synchronisation: every copy and kernel is queued
- * behind the earlier work on `cuda_stream` and out_host holds the result once
- * that stream has passed this call (synchronise it or record an event).  The
- * host buffers must stay valid and unchanged until then.  With two workspaces
- * on two streams, one evaluation's copies overlap another's kernels. */
+/* The same without the final synchronisation: the kernels and the result read
+ * are queued on `cuda_stream` and out_host holds the result once that stream
+ * has passed this call (synchronise it or record an event).  The host-to-device
+ * copies run on the library's own streams and wait only for the previous
+ * host-buffer evaluation that used the same workspace (the first time, for the
+ * work queued on `cuda_stream`), so with two workspaces on one stream the next
+ * evaluation's inputs copy while this one computes.  The host buffers must
+ * stay valid and unchanged until the result is read, and earlier work must not
+ * write the host input buffers. */
 bcn_status bcn_eval_host_async(const bcn_model *m, const uint32_t *evk_eval_dev, const uint32_t *cts_host,
                                const uint32_t *const *pts_host, uint32_t *out_host, void *workspace_dev,
                                size_t workspace_bytes, void *cuda_stream);

@@ -6,6 +6,7 @@
 #include <cstring>
 #include <string>
 #include <mutex>
+#include <unordered_map>
 #include <vector>
 
 #include <cuda_runtime_api.h>
@@ -146,9 +147,12 @@ struct bcn_model {
     int chunk;          // ciphertexts per key-switching chunk
     int chunk_request;  // 0: automatic
     int mac_impl = 0;   // 0: tensor cores where eligible, 1: CUDA cores only
-    // copy streams of bcn_eval_host (created on first use, guarded by copy_mu)
+    // copy streams of bcn_eval_host (created on first use) and, per workspace,
+    // the event after the last evaluation that read its staged inputs; guarded
+    // by copy_mu
     std::mutex copy_mu;
     std::vector<cudaStream_t> copy_streams;
+    std::unordered_map<const void *, cudaEvent_t> staging_free;
     size_t ws_x_bytes;  // one ping-pong activation buffer
     size_t ws_y_bytes;  // MAC output of a square layer
     size_t ws_chunk_bytes;

@@ -600,6 +600,7 @@ bcn_status bcn_model_destroy(bcn_model *m) {
     }
     for (auto e : m->prof.ev) cudaEventDestroy(e);
     for (auto s2 : m->copy_streams) cudaStreamDestroy(s2);
+    for (auto &kv : m->staging_free) cudaEventDestroy(kv.second);
     delete m;
     return BCN_OK;
 }
@@ -803,9 +804,16 @@ bcn_status bcn_eval_host_async(const bcn_model *m, const uint32_t *evk, const ui
         for (cudaEvent_t e : events) cudaEventDestroy(e);
         return s == BCN_OK ? BCN_OK : fail(s, msg);
     };
+    // The copies overwrite the workspace's staging area: they wait for the last
+    // evaluation that read it (its event), or, the first time a workspace is
+    // seen, for everything queued on `st` so far.
     cudaEvent_t start;
-    if (!new_event(&start) || cudaEventRecord(start, st) != cudaSuccess)
+    auto it = mm->staging_free.find(ws);
+    if (it != mm->staging_free.end()) {
+        start = it->second;
+    } else if (!new_event(&start) || cudaEventRecord(start, st) != cudaSuccess) {
         return cleanup(BCN_E_CUDA, "bcn_eval_host: event failed");
+    }
     for (cudaStream_t s2 : mm->copy_streams)
         if (cudaStreamWaitEvent(s2, start, 0) != cudaSuccess) return cleanup(BCN_E_CUDA, "bcn_eval_host: event wait");
     // one buffer: kCopyLanes parts, one event per part
@@ -842,6 +850,15 @@ bcn_status bcn_eval_host_async(const bcn_model *m, const uint32_t *evk, const ui
     uint32_t *out_d = reinterpret_cast<uint32_t *>(p);
     bcn_status s = eval_impl(m, evk, cts_d, pts_d.data(), out_d, ws, eval_need, stream, &ready);
     if (s != BCN_OK) return cleanup(s, bcn_last_error());
+    {  // the staging area is free again once this evaluation has run
+        cudaEvent_t done;
+        if (cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventRecord(done, st) != cudaSuccess)
+            return cleanup(BCN_E_CUDA, "bcn_eval_host: event failed");
+        auto old_it = mm->staging_free.find(ws);
+        if (old_it != mm->staging_free.end()) cudaEventDestroy(old_it->second);
+        mm->staging_free[ws] = done;
+    }
     const size_t out_b = (size_t)m->layers.back().n_out * 2 * m->out_level * c->N * 4;
     if (cudaMemcpyAsync(out_h, out_d, out_b, cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return cleanup(BCN_E_CUDA, "bcn_eval_host: output copy failed");

@@ -123,6 +123,15 @@ def test_eval_host_async_two_in_flight(case):
     torch.cuda.synchronize()
     for o in outs:
         assert np.array_equal(u32(o), ref)
+    # two workspaces in turn on one stream: copies wait only for their workspace
+    for o in outs:
+        o.zero_()
+    for rep in range(5):
+        i = rep % 2
+        model.eval_host_async(evk_eval, u32(cts_h), [u32(p) for p in pts_h], u32(outs[i]), wss[i])
+    torch.cuda.synchronize()
+    for o in outs:
+        assert np.array_equal(u32(o), ref)
 
 
 def test_eval_is_deterministic_and_stream_ordered():
