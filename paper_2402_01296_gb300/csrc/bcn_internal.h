@@ -153,6 +153,10 @@ struct bcn_model {
     std::mutex copy_mu;
     std::vector<cudaStream_t> copy_streams;
     std::unordered_map<const void *, cudaEvent_t> staging_free;
+    // second stream of bcn_eval's square layers (created on first use, guarded
+    // by split_mu): a chunk's two halves run side by side
+    std::mutex split_mu;
+    cudaStream_t split_stream = nullptr;
     size_t ws_x_bytes;  // one ping-pong activation buffer
     size_t ws_y_bytes;  // MAC output of a square layer
     size_t ws_chunk_bytes;

@@ -601,6 +601,7 @@ bcn_status bcn_model_destroy(bcn_model *m) {
     for (auto e : m->prof.ev) cudaEventDestroy(e);
     for (auto s2 : m->copy_streams) cudaStreamDestroy(s2);
     for (auto &kv : m->staging_free) cudaEventDestroy(kv.second);
+    if (m->split_stream) cudaStreamDestroy(m->split_stream);
     delete m;
     return BCN_OK;
 }
@@ -686,6 +687,29 @@ static bcn_status eval_impl(const bcn_model *m, const uint32_t *evk, const uint3
     if (!aligned16(cts) || !aligned16(out) || !aligned16(ws) || !aligned16(evk))
         return fail(BCN_E_INVAL, "bcn_eval: buffers must be 16-byte aligned");
     cudaStream_t st = (cudaStream_t)stream;
+    // square layers split their chunks over `st` and the model's split stream,
+    // unless kernel timing is on (its events are on `st` alone)
+    cudaStream_t split = nullptr;
+    cudaEvent_t split_ev[2] = {nullptr, nullptr};
+    struct EventPair {
+        cudaEvent_t *e;
+        ~EventPair() {
+            for (int i = 0; i < 2; i++)
+                if (e[i]) cudaEventDestroy(e[i]);
+        }
+    } split_guard{split_ev};
+    bool has_square = false;
+    for (auto &l : m->layers) has_square |= l.square != 0;
+    if (!m->prof.on && has_square) {
+        bcn_model *mm = const_cast<bcn_model *>(m);
+        std::lock_guard<std::mutex> lock(mm->split_mu);
+        if (!mm->split_stream && cudaStreamCreateWithFlags(&mm->split_stream, cudaStreamNonBlocking) != cudaSuccess)
+            return fail(BCN_E_CUDA, "bcn_eval: stream creation failed");
+        split = mm->split_stream;
+        if (cudaEventCreateWithFlags(&split_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&split_ev[1], cudaEventDisableTiming) != cudaSuccess)
+            return fail(BCN_E_CUDA, "bcn_eval: event creation failed");
+    }
     char *w = reinterpret_cast<char *>(ws);
     uint32_t *X[2] = {reinterpret_cast<uint32_t *>(w), reinterpret_cast<uint32_t *>(w + m->ws_x_bytes)};
     uint32_t *Ychunk = reinterpret_cast<uint32_t *>(w + 2 * m->ws_x_bytes);
@@ -723,7 +747,27 @@ static bcn_status eval_impl(const bcn_model *m, const uint32_t *evk, const uint3
                                                  (double)C * 2 * n + (pt ? (double)C * n : 0.0));
                 BCN_TRY(launch_mac(c, n, p.K, ng, p.n_go, p.d_gidx, p.d_gw, p.d_gout, x, pt, Ychunk, st, prof,
                                    mac_bytes, g0, false, m->mac_impl == 0 ? &p.tc : nullptr));
-                BCN_TRY(square_chunk(c, n, evk, Ychunk, b, C, y + (size_t)o0 * 2 * (n - 1) * N, st, prof));
+                uint32_t *yo = y + (size_t)o0 * 2 * (n - 1) * N;
+                if (split == nullptr || C < 2) {
+                    BCN_TRY(square_chunk(c, n, evk, Ychunk, b, C, yo, st, prof));
+                    continue;
+                }
+                // the chunk's two halves side by side: the second on the split
+                // stream (forked from and joined back to `st`), each on its own
+                // slices of the chunk buffers, so one half's blocks fill the
+                // other's last wave
+                const int C0 = (C + 1) / 2, C1 = C - C0;
+                ChunkBufs b1{b.d + (size_t)C0 * 3 * n * N, b.acc + (size_t)C0 * 2 * (n + c->K) * N,
+                             b.d2n + (size_t)C0 * n * N};
+                if (cudaEventRecord(split_ev[0], st) != cudaSuccess ||
+                    cudaStreamWaitEvent(split, split_ev[0], 0) != cudaSuccess)
+                    return fail(BCN_E_CUDA, "bcn_eval: fork failed");
+                BCN_TRY(square_chunk(c, n, evk, Ychunk, b, C0, yo, st, nullptr));
+                BCN_TRY(square_chunk(c, n, evk, Ychunk + (size_t)C0 * 2 * n * N, b1, C1,
+                                     yo + (size_t)C0 * 2 * (n - 1) * N, split, nullptr));
+                if (cudaEventRecord(split_ev[1], split) != cudaSuccess ||
+                    cudaStreamWaitEvent(st, split_ev[1], 0) != cudaSuccess)
+                    return fail(BCN_E_CUDA, "bcn_eval: join failed");
             }
         }
         x = y;
