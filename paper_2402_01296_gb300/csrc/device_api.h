@@ -102,7 +102,7 @@ bcn_status mac_tc_plan(const bcn_ctx *c, int K, int n_go, const int8_t *w, MacTc
 bcn_status mac_tc_setup();
 bcn_status launch_mac_tc(const bcn_ctx *c, const MacTcPlan &p, int level, int K, int n_groups, int n_go,
                          const int32_t *gidx, const int32_t *gout, const uint32_t *in, const uint32_t *pt,
-                         uint32_t *out, cudaStream_t st, int g_base, bool store_natural);
+                         uint32_t *out, cudaStream_t st, int g_base, bool store_natural, int t_lo, int n_tl);
 bcn_status cores_setup_all();
 
 }  // namespace bcn

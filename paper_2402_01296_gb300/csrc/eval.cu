@@ -36,13 +36,14 @@ __global__ void __launch_bounds__(256) k_mac_grouped(const uint32_t *__restrict_
                                                      const int32_t *__restrict__ gidx, const int8_t *__restrict__ gw,
                                                      const int32_t *__restrict__ gout, const uint32_t *__restrict__ pt,
                                                      int K, int n_go, int level, int N, int g_base,
-                                                     int store_natural, const PrimeConst *__restrict__ pc) {
+                                                     int store_natural, int t_lo, int n_tl,
+                                                     const PrimeConst *__restrict__ pc) {
     constexpr int OTP = (OT + 3) / 4 * 4;  // weight row padded to whole int4 loads
     extern __shared__ __align__(16) unsigned char smraw[];
     int32_t *sw = reinterpret_cast<int32_t *>(smraw);                        // [KC][OTP] weights (0: padding tap)
     int32_t *sidx = reinterpret_cast<int32_t *>(smraw) + (size_t)kMacTapChunk * OTP;  // [KC] input (0: padding)
-    const int tiles = (n_go + OT - 1) / OT;
-    const int g = g_base + blockIdx.y / tiles, o0 = (blockIdx.y % tiles) * OT;
+    // output tiles [t_lo, t_lo + n_tl) of every group
+    const int g = g_base + blockIdx.y / n_tl, o0 = (t_lo + (int)blockIdx.y % n_tl) * OT;
     const int no = min(OT, n_go - o0);
     const size_t cols = (size_t)2 * level * N;
     const size_t col = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
@@ -322,29 +323,38 @@ void ks_carve(const bcn_ctx *c, int n, int chunk, char *ws, uint32_t **d, uint32
 static bcn_status launch_mac(const bcn_ctx *c, int level, int K, int n_groups, int n_go, const int32_t *gidx,
                              const int8_t *gw, const int32_t *gout, const uint32_t *in, const uint32_t *pt,
                              uint32_t *out, cudaStream_t st, Profiler *prof = nullptr, double alg_bytes = 0,
-                             int g_base = 0, bool store_natural = true, const MacTcPlan *tc = nullptr) {
+                             int g_base = 0, bool store_natural = true, const MacTcPlan *tc = nullptr,
+                             int o_lo = 0, int o_hi = -1) {
     if (n_groups <= 0 || n_go <= 0) return BCN_OK;
     if (K > kMaxMacTaps) return fail(BCN_E_INVAL, "MAC fan-in above 2^20");
+    if (o_hi < 0) o_hi = n_go;  // outputs [o_lo, o_hi) of every group, o_lo on a tile boundary
     if (tc != nullptr && tc->w16 != nullptr) {
         Timed tm(prof, st, BCN_KERNEL_MAC, alg_bytes);
-        return launch_mac_tc(c, *tc, level, K, n_groups, n_go, gidx, gout, in, pt, out, st, g_base, store_natural);
+        const int t_lo = o_lo / tc->tile_out, t_hi = (o_hi + tc->tile_out - 1) / tc->tile_out;
+        return launch_mac_tc(c, *tc, level, K, n_groups, n_go, gidx, gout, in, pt, out, st, g_base, store_natural,
+                             t_lo, t_hi - t_lo);
     }
     const int N = c->N;
     const int OT = std::min(8, n_go);
-    const int tiles = (n_go + OT - 1) / OT;
+    const int t_lo = o_lo / OT, n_tl = (o_hi + OT - 1) / OT - t_lo;
     const size_t cols = (size_t)2 * level * N;
     const size_t smem = (size_t)kMacTapChunk * 4 * (1 + (OT + 3) / 4 * 4);
-    if ((long long)n_groups * tiles > 65535) return fail(BCN_E_INVAL, "MAC layer with more than 65535 output tiles");
+    if ((long long)n_groups * n_tl > 65535) return fail(BCN_E_INVAL, "MAC layer with more than 65535 output tiles");
     Timed tm(prof, st, BCN_KERNEL_MAC, alg_bytes);
-    dim3 grid((unsigned)((cols / 4 + 255) / 256), (unsigned)(n_groups * tiles));
+    dim3 grid((unsigned)((cols / 4 + 255) / 256), (unsigned)(n_groups * n_tl));
 #define BCN_MAC(OTV)                                                                                          \
     case OTV:                                                                                                 \
         k_mac_grouped<OTV><<<grid, 256, smem, st>>>(in, out, gidx, gw, gout, pt, K, n_go, level, N, g_base, \
-                                                    store_natural ? 1 : 0, c->d_pc);                          \
+                                                    store_natural ? 1 : 0, t_lo, n_tl, c->d_pc);              \
         break;
     switch (OT) { BCN_MAC(1) BCN_MAC(2) BCN_MAC(3) BCN_MAC(4) BCN_MAC(5) BCN_MAC(6) BCN_MAC(7) BCN_MAC(8) }
 #undef BCN_MAC
     return check_launch("k_mac_grouped");
+}
+
+// outputs per tile of the MAC kernel a layer runs (splits fall on tile boundaries)
+static int mac_out_tile(const bcn_layer_plan &p, bool use_tc) {
+    return use_tc && p.tc.w16 != nullptr ? p.tc.tile_out : std::min(8, p.n_go);
 }
 
 // Square activation on a chunk of C ciphertexts: Y [C][2][n][N] (coefficient
@@ -741,30 +751,47 @@ static bcn_status eval_impl(const bcn_model *m, const uint32_t *evk, const uint3
             const int n = p.level;
             const int gpc = std::max(1, m->chunk / p.n_go);  // whole groups per chunk
             ChunkBufs b = carve_chunk(c, n, m->chunk, chunk_ws);
+            const MacTcPlan *tc = m->mac_impl == 0 ? &p.tc : nullptr;
+            const int ts = mac_out_tile(p, tc != nullptr);
             for (int g0 = 0; g0 < p.n_groups; g0 += gpc) {
                 const int ng = std::min(gpc, p.n_groups - g0), C = ng * p.n_go, o0 = g0 * p.n_go;
                 const double mac_bytes = limb * ((double)p.n_distinct_in * 2 * n * ng / p.n_groups +
                                                  (double)C * 2 * n + (pt ? (double)C * n : 0.0));
-                BCN_TRY(launch_mac(c, n, p.K, ng, p.n_go, p.d_gidx, p.d_gw, p.d_gout, x, pt, Ychunk, st, prof,
-                                   mac_bytes, g0, false, m->mac_impl == 0 ? &p.tc : nullptr));
                 uint32_t *yo = y + (size_t)o0 * 2 * (n - 1) * N;
-                if (split == nullptr || C < 2) {
+                // Two halves side by side (MAC, then square, key switch, ModDown
+                // and rescale), the second on the split stream forked from and
+                // joined back to `st`, each on its own slices of the chunk
+                // buffers: one half's MAC overlaps the other's NTT kernels and
+                // their blocks fill each other's last waves.  Halves of several
+                // groups split by groups, of one group by output tiles.
+                const int ngA = (ng + 1) / 2;
+                const int oA = ng >= 2 ? ngA * p.n_go : std::min(p.n_go, (((p.n_go + ts - 1) / ts + 1) / 2) * ts);
+                if (split == nullptr || oA >= C) {
+                    BCN_TRY(launch_mac(c, n, p.K, ng, p.n_go, p.d_gidx, p.d_gw, p.d_gout, x, pt, Ychunk, st, prof,
+                                       mac_bytes, g0, false, tc));
                     BCN_TRY(square_chunk(c, n, evk, Ychunk, b, C, yo, st, prof));
                     continue;
                 }
-                // the chunk's two halves side by side: the second on the split
-                // stream (forked from and joined back to `st`), each on its own
-                // slices of the chunk buffers, so one half's blocks fill the
-                // other's last wave
-                const int C0 = (C + 1) / 2, C1 = C - C0;
-                ChunkBufs b1{b.d + (size_t)C0 * 3 * n * N, b.acc + (size_t)C0 * 2 * (n + c->K) * N,
-                             b.d2n + (size_t)C0 * n * N};
+                const int C1 = C - oA;
+                ChunkBufs b1{b.d + (size_t)oA * 3 * n * N, b.acc + (size_t)oA * 2 * (n + c->K) * N,
+                             b.d2n + (size_t)oA * n * N};
                 if (cudaEventRecord(split_ev[0], st) != cudaSuccess ||
                     cudaStreamWaitEvent(split, split_ev[0], 0) != cudaSuccess)
                     return fail(BCN_E_CUDA, "bcn_eval: fork failed");
-                BCN_TRY(square_chunk(c, n, evk, Ychunk, b, C0, yo, st, nullptr));
-                BCN_TRY(square_chunk(c, n, evk, Ychunk + (size_t)C0 * 2 * n * N, b1, C1,
-                                     yo + (size_t)C0 * 2 * (n - 1) * N, split, nullptr));
+                if (ng >= 2) {
+                    BCN_TRY(launch_mac(c, n, p.K, ngA, p.n_go, p.d_gidx, p.d_gw, p.d_gout, x, pt, Ychunk, st, nullptr,
+                                       0, g0, false, tc));
+                    BCN_TRY(launch_mac(c, n, p.K, ng - ngA, p.n_go, p.d_gidx, p.d_gw, p.d_gout, x, pt,
+                                       Ychunk + (size_t)oA * 2 * n * N, split, nullptr, 0, g0 + ngA, false, tc));
+                } else {  // one group: outputs [0, oA) and [oA, n_go), both stored at their group positions
+                    BCN_TRY(launch_mac(c, n, p.K, 1, p.n_go, p.d_gidx, p.d_gw, p.d_gout, x, pt, Ychunk, st, nullptr,
+                                       0, g0, false, tc, 0, oA));
+                    BCN_TRY(launch_mac(c, n, p.K, 1, p.n_go, p.d_gidx, p.d_gw, p.d_gout, x, pt, Ychunk, split, nullptr,
+                                       0, g0, false, tc, oA, p.n_go));
+                }
+                BCN_TRY(square_chunk(c, n, evk, Ychunk, b, oA, yo, st, nullptr));
+                BCN_TRY(square_chunk(c, n, evk, Ychunk + (size_t)oA * 2 * n * N, b1, C1,
+                                     yo + (size_t)oA * 2 * (n - 1) * N, split, nullptr));
                 if (cudaEventRecord(split_ev[1], split) != cudaSuccess ||
                     cudaStreamWaitEvent(st, split_ev[1], 0) != cudaSuccess)
                     return fail(BCN_E_CUDA, "bcn_eval: join failed");

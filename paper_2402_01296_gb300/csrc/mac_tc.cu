@@ -124,8 +124,8 @@ __global__ void __launch_bounds__(kThreads) k_mac_tc(const uint32_t *__restrict_
                                                      const int32_t *__restrict__ gidx, const uint4 *__restrict__ w16,
                                                      const int32_t *__restrict__ gout,
                                                      const uint32_t *__restrict__ pt, int K, int Kpad, int n_go,
-                                                     int tile_out, int NT, int tiles, int level, int N, int g_base,
-                                                     int store_natural, const PrimeConst *__restrict__ pc,
+                                                     int tile_out, int NT, int t_lo, int n_tl, int level, int N,
+                                                     int g_base, int store_natural, const PrimeConst *__restrict__ pc,
                                                      uint32_t tmem_cols, uint32_t *__restrict__ status) {
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char *S = sm;                          // [kStages][kSlab][kRows] u32
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(kThreads) k_mac_tc(const uint32_t *__restrict_
     volatile int *flag = reinterpret_cast<volatile int *>(tslot + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, r = tid & (kRows - 1), half = tid >> 7;
-    const int g = g_base + (int)blockIdx.y / tiles, tile = (int)blockIdx.y % tiles;
+    const int g = g_base + (int)blockIdx.y / n_tl, tile = t_lo + (int)blockIdx.y % n_tl;
     const int o0 = tile * tile_out, no = min(tile_out, n_go - o0);
     const size_t cols = (size_t)2 * level * N;
     const size_t col0 = (size_t)blockIdx.x * kRows, col = col0 + r;
@@ -337,12 +337,13 @@ bcn_status mac_tc_setup() {
 
 bcn_status launch_mac_tc(const bcn_ctx *c, const MacTcPlan &p, int level, int K, int n_groups, int n_go,
                          const int32_t *gidx, const int32_t *gout, const uint32_t *in, const uint32_t *pt,
-                         uint32_t *out, cudaStream_t st, int g_base, bool store_natural) {
+                         uint32_t *out, cudaStream_t st, int g_base, bool store_natural, int t_lo, int n_tl) {
     const size_t cols = (size_t)2 * level * c->N;
-    if ((long long)n_groups * p.tiles > 65535) return fail(BCN_E_INVAL, "MAC layer with more than 65535 output tiles");
-    dim3 grid((unsigned)(cols / kRows), (unsigned)(n_groups * p.tiles));
+    if (t_lo < 0 || n_tl < 1 || t_lo + n_tl > p.tiles) return fail(BCN_E_INVAL, "MAC tile range");
+    if ((long long)n_groups * n_tl > 65535) return fail(BCN_E_INVAL, "MAC layer with more than 65535 output tiles");
+    dim3 grid((unsigned)(cols / kRows), (unsigned)(n_groups * n_tl));
     k_mac_tc<<<grid, kThreads, p.smem, st>>>(in, out, gidx, reinterpret_cast<const uint4 *>(p.w16), gout, pt, K, p.Kpad,
-                                          n_go, p.tile_out, p.NT, p.tiles, level, c->N, g_base,
+                                          n_go, p.tile_out, p.NT, t_lo, n_tl, level, c->N, g_base,
                                           store_natural ? 1 : 0, c->d_pc, p.tmem_cols, c->d_status);
     return check_launch("k_mac_tc");
 }
