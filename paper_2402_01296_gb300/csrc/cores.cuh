@@ -45,6 +45,12 @@ __global__ void __launch_bounds__((1 << LOGN) / R) k_ntt_inv(uint32_t *__restric
 template <int LOGN>
 constexpr bool kFmaOne = LOGN <= 13;
 
+// Pairs of independent transforms run in lockstep (shared twiddle loads and
+// barriers, twice the independent work per thread) where the registers allow
+// it: up to N = 8192.
+template <int LOGN>
+constexpr bool kDual = LOGN <= 13;
+
 // Register budget per thread of the fused kernels (sets their blocks per SM).
 #ifndef BCN_CORE_REGS
 #define BCN_CORE_REGS 128
@@ -69,11 +75,56 @@ __global__ void __launch_bounds__((1 << LOGN) / R, CoreOcc<(1 << LOGN) / R>::MIN
     using C = NttCore<LOGN, R, true>;  // data primes only (q < 2^30): lazy butterflies
     constexpr int N = C::N, T = C::T;
     extern __shared__ __align__(16) uint32_t sm[];
-    // exchange buffer, then two thread-private parking areas (slot u*T + tid)
-    uint32_t *s1 = sm + C::SMEM_WORDS, *s2 = s1 + N;
     const int i = blockIdx.x, ct = blockIdx.y, tid = threadIdx.x;
     const PrimeConst P = pc[i];
     const uint2 *tf = twf + (size_t)i * N, *ti = twi + (size_t)i * N;
+    if constexpr (kDual<LOGN>) {
+        // c0 and c1 transformed together (two exchange buffers), then d0 and d1
+        // back together; d2 waits in a thread-private parking area (u*T + tid)
+        uint32_t *s2 = sm + 2 * C::SMEM_WORDS;
+        const ModQ mq(P.q, kFmaOne<LOGN> ? P.one : 1u);
+        uint32_t x[2][R];
+        C::load_natural(x[0], Y + (((size_t)ct * 2 + 0) * n + i) * N, tid);
+        C::load_natural(x[1], Y + (((size_t)ct * 2 + 1) * n + i) * N, tid);
+        C::forward_n(x, sm, tid, mq, tf);
+        uint32_t *d2n = D2N != nullptr ? D2N + ((size_t)ct * n + i) * N : nullptr;
+        constexpr int V = C::NTT_QUADS ? 4 : (C::NTT_PAIRS ? 2 : 1);
+#pragma unroll
+        for (int u0 = 0; u0 < R; u0 += V) {
+            uint32_t c2[V];  // c1^2, canonical, for the key switch's own-digit term
+#pragma unroll
+            for (int z = 0; z < V; z++) {
+                const int u = u0 + z;
+                const uint32_t a = x[0][u], b = x[1][u];  // [0, 4q)
+                c2[z] = mont_mul(shoup_mul(b, P.r_mod, P.r_shoup, P.q), b, P.q, P.qneg_inv);
+                const uint32_t aRN = shoup_mul(a, P.rn, P.rn_shoup, P.q);
+                const uint32_t bRN = shoup_mul(b, P.rn, P.rn_shoup, P.q);
+                const uint32_t ab = mont_mul(aRN, b, P.q, P.qneg_inv);
+                x[0][u] = mont_mul(aRN, a, P.q, P.qneg_inv);  // c0^2 / N
+                x[1][u] = add_mod(ab, ab, P.q);                // 2 c0 c1 / N
+                s2[u * T + tid] = mont_mul(bRN, b, P.q, P.qneg_inv);  // c1^2 / N
+            }
+            if (d2n != nullptr) {
+                const int e = C::ntt_elem(u0, tid);
+                if constexpr (V == 4)
+                    *reinterpret_cast<uint4 *>(d2n + e) = make_uint4(c2[0], c2[1], c2[2], c2[3]);
+                else if constexpr (V == 2)
+                    *reinterpret_cast<uint2 *>(d2n + e) = make_uint2(c2[0], c2[1]);
+                else
+                    d2n[e] = c2[0];
+            }
+        }
+        C::inverse_unscaled_n(x, sm, tid, mq, ti);
+        C::store_natural(x[0], D + (((size_t)ct * 3 + 0) * n + i) * N, tid);
+        C::store_natural(x[1], D + (((size_t)ct * 3 + 1) * n + i) * N, tid);
+#pragma unroll
+        for (int u = 0; u < R; u++) x[0][u] = s2[u * T + tid];
+        C::inverse_unscaled(x[0], sm, tid, mq, ti);
+        C::store_natural(x[0], D + (((size_t)ct * 3 + 2) * n + i) * N, tid);
+        return;
+    }
+    // exchange buffer, then two thread-private parking areas (slot u*T + tid)
+    uint32_t *s1 = sm + C::SMEM_WORDS, *s2 = s1 + N;
     uint32_t x[R];
     // c0 -> NTT, parked in s1
     C::load_natural(x, Y + (((size_t)ct * 2 + 0) * n + i) * N, tid);
@@ -150,8 +201,9 @@ __device__ __forceinline__ void ks_core_body(const uint32_t *__restrict__ D, con
         }
     };
     extern __shared__ __align__(16) uint32_t sm[];
-    // exchange buffer, then the two running sums in thread-private slots u*T + tid
-    uint32_t *s0 = sm + C::SMEM_WORDS, *s1 = s0 + N;
+    // exchange buffer(s) -- two where the final inverse transforms run together --
+    // then the two running sums in thread-private slots u*T + tid
+    uint32_t *s0 = sm + (kDual<LOGN> ? 2 : 1) * C::SMEM_WORDS, *s1 = s0 + N;
     const int t = blockIdx.x, ct = blockIdx.y, tid = threadIdx.x;
     const int A = ks.alpha, dnum = (n + A - 1) / A, nb = n + ks.K;
     const int pt = t < n ? t : ks.L + (t - n);
@@ -243,6 +295,18 @@ __device__ __forceinline__ void ks_core_body(const uint32_t *__restrict__ D, con
             }
         }
     }
+    if constexpr (kDual<LOGN>) {
+        uint32_t y[2][R];
+#pragma unroll
+        for (int u = 0; u < R; u++) {
+            y[0][u] = s0[u * T + tid];
+            y[1][u] = s1[u * T + tid];
+        }
+        C::inverse_unscaled_n(y, sm, tid, ModQ(P.q, kFmaOne<LOGN> ? P.one : 1u), ti);
+        C::store_natural(y[0], acc_out + (((size_t)ct * 2 + 0) * nb + t) * N, tid);
+        C::store_natural(y[1], acc_out + (((size_t)ct * 2 + 1) * nb + t) * N, tid);
+        return;
+    }
 #pragma unroll
     for (int u = 0; u < R; u++) x[u] = s0[u * T + tid];
     C::inverse_unscaled(x, sm, tid, ModQ(P.q, kFmaOne<LOGN> ? P.one : 1u), ti);
@@ -272,7 +336,11 @@ template <int LOGN, int R>
 struct CoreImpl {
     using Core = NttCore<LOGN, R>;
     static constexpr size_t SMEM = (size_t)Core::SMEM_WORDS * 4;            // NTT alone
-    static constexpr size_t SMEM3 = ((size_t)Core::SMEM_WORDS + 2 * Core::N) * 4;  // + two parking areas
+    // NTT alone; + two parking areas (or a second exchange buffer and one)
+    static constexpr size_t SMEM3 =
+        ((size_t)(kDual<LOGN> ? 2 * Core::SMEM_WORDS + Core::N : Core::SMEM_WORDS + 2 * Core::N)) * 4;
+    // key switch: exchange buffer(s) and the two running sums
+    static constexpr size_t SMEM_KS = ((size_t)(kDual<LOGN> ? 2 : 1) * Core::SMEM_WORDS + 2 * Core::N) * 4;
 
     static bcn_status ntt(const bcn_ctx *c, uint32_t *data, size_t n_limbs, PrimeMap pm, bool inverse,
                           cudaStream_t st) {
@@ -290,19 +358,19 @@ struct CoreImpl {
     }
     static bcn_status keyswitch(const bcn_ctx *c, int n, const uint32_t *D, const uint32_t *D2N,
                                 const uint32_t *evk, uint32_t *acc, int C, cudaStream_t st) {
-        k_ks_core<LOGN, R><<<dim3(n + c->K, C), Core::T, SMEM3, st>>>(D, D2N, evk, acc, n, ks_dev(c), c->d_pc,
+        k_ks_core<LOGN, R><<<dim3(n + c->K, C), Core::T, SMEM_KS, st>>>(D, D2N, evk, acc, n, ks_dev(c), c->d_pc,
                                                                      c->d_tw_fwd, c->d_tw_inv);
         return check_launch("k_ks_core");
     }
     static bcn_status setup() {
-        const int smem = (int)SMEM, smem3 = (int)SMEM3;
+        const int smem = (int)SMEM, smem3 = (int)SMEM3, smem_ks = (int)SMEM_KS;
         if (cudaFuncSetAttribute(k_ntt_fwd<LOGN, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
                 cudaSuccess ||
             cudaFuncSetAttribute(k_ntt_inv<LOGN, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
                 cudaSuccess ||
             cudaFuncSetAttribute(k_square_core<LOGN, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem3) !=
                 cudaSuccess ||
-            cudaFuncSetAttribute(k_ks_core<LOGN, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem3) !=
+            cudaFuncSetAttribute(k_ks_core<LOGN, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_ks) !=
                 cudaSuccess ||
             cudaFuncSetAttribute(k_square_core<LOGN, R>, cudaFuncAttributePreferredSharedMemoryCarveout, 100) !=
                 cudaSuccess ||

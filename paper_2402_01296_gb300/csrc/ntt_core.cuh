@@ -131,21 +131,32 @@ struct NttCore {
         }
     }
 
+    // The transforms below run NP polynomials in lockstep (x[p], p < NP): they
+    // share every twiddle load and every barrier, and their butterflies give the
+    // scheduler NP independent streams.  Polynomial p exchanges through
+    // sm + p * SMEM_WORDS.
+
     // FIRST: the first exchange of a transform (what ran before is unknown)
-    template <int PF, int PT, bool FIRST>
-    __device__ __forceinline__ static void exchange(uint32_t (&x)[R], uint32_t *sm, int tid) {
+    template <int PF, int PT, bool FIRST, int NP>
+    __device__ __forceinline__ static void exchange(uint32_t (&x)[NP][R], uint32_t *sm, int tid) {
         constexpr bool WF = warp_local<PF>(), WT = warp_local<PT>();
         if constexpr (FIRST && !WF) __syncthreads();
-        uint32_t *wf = sm + pad_base<PF>(tid);
 #pragma unroll
-        for (int u = 0; u < R; u++) wf[pad_off<PF>(u)] = x[u];
+        for (int p = 0; p < NP; p++) {
+            uint32_t *wf = sm + p * SMEM_WORDS + pad_base<PF>(tid);
+#pragma unroll
+            for (int u = 0; u < R; u++) wf[pad_off<PF>(u)] = x[p][u];
+        }
         if constexpr (WF && WT)
             __syncwarp();
         else
             __syncthreads();
-        const uint32_t *rt = sm + pad_base<PT>(tid);
 #pragma unroll
-        for (int u = 0; u < R; u++) x[u] = rt[pad_off<PT>(u)];
+        for (int p = 0; p < NP; p++) {
+            const uint32_t *rt = sm + p * SMEM_WORDS + pad_base<PT>(tid);
+#pragma unroll
+            for (int u = 0; u < R; u++) x[p][u] = rt[pad_off<PT>(u)];
+        }
         if constexpr (WT)
             __syncwarp();
         else
@@ -153,8 +164,8 @@ struct NttCore {
     }
 
     // stage s0 + KS of pass P (forward) for group g
-    template <int P, int KS>
-    __device__ __forceinline__ static void stage_fwd(uint32_t (&x)[R], int g, int hi, ModQ m,
+    template <int P, int KS, int NP>
+    __device__ __forceinline__ static void stage_fwd(uint32_t (&x)[NP][R], int g, int hi, ModQ m,
                                                      const uint2 *__restrict__ tw) {
         constexpr int rp = rp_of(P), s = s0_of(P) + KS, d = 1 << (rp - 1 - KS);
         const uint32_t q = m.q;
@@ -166,25 +177,28 @@ struct NttCore {
 #pragma unroll
             for (int w = 0; w < d; w++) {
                 const int u = (g << rp) + b * 2 * d + w;
-                if constexpr (LAZY) {
-                    const uint32_t q2 = 2 * q, nq2 = 0u - q2, xu = x[u];
-                    const uint32_t U = min(xu, xu * m.one + nq2);  // [0, 2q)
-                    const uint32_t V = shoup_mul_lazy(x[u + d], W.x, W.y, q);
-                    x[u] = V * m.one + U;   // [0, 4q)
-                    x[u + d] = U - V + q2;  // [0, 4q)
-                } else {
-                    const uint32_t U = x[u], V = shoup_mul(x[u + d], W.x, W.y, q);
-                    x[u] = add_mod(U, V, q);
-                    x[u + d] = sub_mod(U, V, q);
+#pragma unroll
+                for (int p = 0; p < NP; p++) {
+                    if constexpr (LAZY) {
+                        const uint32_t q2 = 2 * q, nq2 = 0u - q2, xu = x[p][u];
+                        const uint32_t U = min(xu, xu * m.one + nq2);  // [0, 2q)
+                        const uint32_t V = shoup_mul_lazy(x[p][u + d], W.x, W.y, q);
+                        x[p][u] = V * m.one + U;   // [0, 4q)
+                        x[p][u + d] = U - V + q2;  // [0, 4q)
+                    } else {
+                        const uint32_t U = x[p][u], V = shoup_mul(x[p][u + d], W.x, W.y, q);
+                        x[p][u] = add_mod(U, V, q);
+                        x[p][u + d] = sub_mod(U, V, q);
+                    }
                 }
             }
         }
-        if constexpr (KS + 1 < rp) stage_fwd<P, KS + 1>(x, g, hi, m, tw);
+        if constexpr (KS + 1 < rp) stage_fwd<P, KS + 1, NP>(x, g, hi, m, tw);
     }
 
     // stage s0 + KS of pass P (inverse), then the stages below it
-    template <int P, int KS>
-    __device__ __forceinline__ static void stage_inv(uint32_t (&x)[R], int g, int hi, ModQ m,
+    template <int P, int KS, int NP>
+    __device__ __forceinline__ static void stage_inv(uint32_t (&x)[NP][R], int g, int hi, ModQ m,
                                                      const uint2 *__restrict__ tw) {
         constexpr int rp = rp_of(P), s = s0_of(P) + KS, d = 1 << (rp - 1 - KS);
         const uint32_t q = m.q;
@@ -196,68 +210,95 @@ struct NttCore {
 #pragma unroll
             for (int w = 0; w < d; w++) {
                 const int u = (g << rp) + b * 2 * d + w;
-                const uint32_t U = x[u], V = x[u + d];
-                if constexpr (LAZY) {
-                    const uint32_t q2 = 2 * q, nq2 = 0u - q2, sum = V * m.one + U;
-                    x[u] = min(sum, sum * m.one + nq2);                        // [0, 2q)
-                    x[u + d] = shoup_mul_lazy(U - V + q2, W.x, W.y, q);        // [0, 2q)
-                } else {
-                    x[u] = add_mod(U, V, q);
-                    x[u + d] = shoup_mul(sub_mod(U, V, q), W.x, W.y, q);
+#pragma unroll
+                for (int p = 0; p < NP; p++) {
+                    const uint32_t U = x[p][u], V = x[p][u + d];
+                    if constexpr (LAZY) {
+                        const uint32_t q2 = 2 * q, nq2 = 0u - q2, sum = V * m.one + U;
+                        x[p][u] = min(sum, sum * m.one + nq2);                   // [0, 2q)
+                        x[p][u + d] = shoup_mul_lazy(U - V + q2, W.x, W.y, q);   // [0, 2q)
+                    } else {
+                        x[p][u] = add_mod(U, V, q);
+                        x[p][u + d] = shoup_mul(sub_mod(U, V, q), W.x, W.y, q);
+                    }
                 }
             }
         }
-        if constexpr (KS > 0) stage_inv<P, KS - 1>(x, g, hi, m, tw);
+        if constexpr (KS > 0) stage_inv<P, KS - 1, NP>(x, g, hi, m, tw);
     }
 
-    template <int P>
-    __device__ __forceinline__ static void pass_fwd(uint32_t (&x)[R], int tid, ModQ m,
+    template <int P, int NP>
+    __device__ __forceinline__ static void pass_fwd(uint32_t (&x)[NP][R], int tid, ModQ m,
                                                     const uint2 *__restrict__ tw) {
         constexpr int rp = rp_of(P);
 #pragma unroll
         for (int g = 0; g < (R >> rp); g++) {
             const int hi = gidx_of<P>(g, tid) >> (LOGN - s1_of(P));
-            stage_fwd<P, 0>(x, g, hi, m, tw);
+            stage_fwd<P, 0, NP>(x, g, hi, m, tw);
         }
     }
-    template <int P>
-    __device__ __forceinline__ static void pass_inv(uint32_t (&x)[R], int tid, ModQ m,
+    template <int P, int NP>
+    __device__ __forceinline__ static void pass_inv(uint32_t (&x)[NP][R], int tid, ModQ m,
                                                     const uint2 *__restrict__ tw) {
         constexpr int rp = rp_of(P);
 #pragma unroll
         for (int g = 0; g < (R >> rp); g++) {
             const int hi = gidx_of<P>(g, tid) >> (LOGN - s1_of(P));
-            stage_inv<P, rp - 1>(x, g, hi, m, tw);
+            stage_inv<P, rp - 1, NP>(x, g, hi, m, tw);
         }
     }
 
-    template <int P>
-    __device__ __forceinline__ static void forward_from(uint32_t (&x)[R], uint32_t *sm, int tid, ModQ m,
+    template <int P, int NP>
+    __device__ __forceinline__ static void forward_from(uint32_t (&x)[NP][R], uint32_t *sm, int tid, ModQ m,
                                                         const uint2 *__restrict__ tw) {
-        if constexpr (P > 0) exchange<P - 1, P, P == 1>(x, sm, tid);
-        pass_fwd<P>(x, tid, m, tw);
-        if constexpr (P + 1 < PASSES) forward_from<P + 1>(x, sm, tid, m, tw);
+        if constexpr (P > 0) exchange<P - 1, P, P == 1, NP>(x, sm, tid);
+        pass_fwd<P, NP>(x, tid, m, tw);
+        if constexpr (P + 1 < PASSES) forward_from<P + 1, NP>(x, sm, tid, m, tw);
     }
-    template <int P>
-    __device__ __forceinline__ static void inverse_from(uint32_t (&x)[R], uint32_t *sm, int tid, ModQ m,
+    template <int P, int NP>
+    __device__ __forceinline__ static void inverse_from(uint32_t (&x)[NP][R], uint32_t *sm, int tid, ModQ m,
                                                         const uint2 *__restrict__ tw) {
-        pass_inv<P>(x, tid, m, tw);
+        pass_inv<P, NP>(x, tid, m, tw);
         if constexpr (P > 0) {
-            exchange<P, P - 1, P == PASSES - 1>(x, sm, tid);
-            inverse_from<P - 1>(x, sm, tid, m, tw);
+            exchange<P, P - 1, P == PASSES - 1, NP>(x, sm, tid);
+            inverse_from<P - 1, NP>(x, sm, tid, m, tw);
         }
     }
 
+    // NP polynomials: pass-0 distribution (natural order) -> last-pass
+    // distribution (NTT domain); sm holds NP exchange buffers
+    template <int NP>
+    __device__ __forceinline__ static void forward_n(uint32_t (&x)[NP][R], uint32_t *sm, int tid, ModQ m,
+                                                     const uint2 *__restrict__ tw) {
+        forward_from<0, NP>(x, sm, tid, m, tw);
+    }
+    // NP polynomials: NTT domain -> pass-0 distribution, without the N^{-1}
+    // factor; the result is canonical
+    template <int NP>
+    __device__ __forceinline__ static void inverse_unscaled_n(uint32_t (&x)[NP][R], uint32_t *sm, int tid, ModQ m,
+                                                              const uint2 *__restrict__ tw) {
+        inverse_from<PASSES - 1, NP>(x, sm, tid, m, tw);
+        if constexpr (LAZY) {
+#pragma unroll
+            for (int p = 0; p < NP; p++)
+#pragma unroll
+                for (int u = 0; u < R; u++) x[p][u] = reduce_once(x[p][u], m.q);
+        }
+    }
+
+    // one polynomial
+    __device__ __forceinline__ static uint32_t (&as_one(uint32_t (&x)[R]))[1][R] {
+        return *reinterpret_cast<uint32_t(*)[1][R]>(&x);
+    }
     // x: pass-0 distribution (natural order) -> last-pass distribution (NTT domain)
     __device__ __forceinline__ static void forward(uint32_t (&x)[R], uint32_t *sm, int tid, ModQ m,
                                                    const uint2 *__restrict__ tw) {
-        forward_from<0>(x, sm, tid, m, tw);
+        forward_from<0, 1>(as_one(x), sm, tid, m, tw);
     }
-
     // x: last-pass distribution (NTT domain) -> pass-0 distribution, times N^{-1}
     __device__ __forceinline__ static void inverse(uint32_t (&x)[R], uint32_t *sm, int tid, ModQ m,
                                                    const uint2 *__restrict__ tw, uint32_t ninv, uint32_t ninv_shoup) {
-        inverse_from<PASSES - 1>(x, sm, tid, m, tw);
+        inverse_from<PASSES - 1, 1>(as_one(x), sm, tid, m, tw);
 #pragma unroll
         for (int u = 0; u < R; u++) x[u] = shoup_mul(x[u], ninv, ninv_shoup, m.q);
     }
@@ -265,11 +306,7 @@ struct NttCore {
     // inputs); the result is canonical
     __device__ __forceinline__ static void inverse_unscaled(uint32_t (&x)[R], uint32_t *sm, int tid, ModQ m,
                                                             const uint2 *__restrict__ tw) {
-        inverse_from<PASSES - 1>(x, sm, tid, m, tw);
-        if constexpr (LAZY) {
-#pragma unroll
-            for (int u = 0; u < R; u++) x[u] = reduce_once(x[u], m.q);
-        }
+        inverse_unscaled_n<1>(as_one(x), sm, tid, m, tw);
     }
 
     // natural-order limb <-> pass-0 distribution (coalesced)
