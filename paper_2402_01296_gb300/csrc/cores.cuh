@@ -230,13 +230,13 @@ __device__ __forceinline__ void ks_core_body(const uint32_t *__restrict__ D, con
                     const uint32_t tmq = P.q - dp;
 #pragma unroll
                     for (int u = 0; u < R; u++) {
-                        const uint32_t d = __ldg(xj + tid + u * T);
+                        const uint32_t d = __ldg(xj + C::nat_elem(u, tid));
                         x[u] = d * one + (d > half ? tmq : 0u);
                     }
                 } else {
 #pragma unroll
                     for (int u = 0; u < R; u++) {
-                        const uint32_t d = __ldg(xj + tid + u * T);
+                        const uint32_t d = __ldg(xj + C::nat_elem(u, tid));
                         uint32_t y = reduce_once(d, P.q);  // d < q_j < 2t
                         if (d > half) y = sub_mod(y, dp, P.q);
                         x[u] = y;
@@ -254,7 +254,7 @@ __device__ __forceinline__ void ks_core_body(const uint32_t *__restrict__ D, con
                     const uint32_t *xi = x2 + (size_t)i * N;
 #pragma unroll
                     for (int u = 0; u < R; u++) {
-                        const uint32_t r = shoup_mul(__ldg(xi + tid + u * T), di.x, di.y, qi);
+                        const uint32_t r = shoup_mul(__ldg(xi + C::nat_elem(u, tid)), di.x, di.y, qi);
                         uint32_t y = add_mod(x[u], shoup_mul(r, dh.x, dh.y, P.q), P.q);
                         if (r > half) y = sub_mod(y, dp, P.q);
                         x[u] = y;
@@ -332,15 +332,17 @@ __global__ void __launch_bounds__((1 << LOGN) / R, CoreOcc<(1 << LOGN) / R>::MIN
         ks_core_body<LOGN, R, false>(D, D2N, evk, acc_out, n, ks, pc, twf, twi);
 }
 
-template <int LOGN, int R>
+// R residues per thread for the NTT and square kernels, RKS for the key switch
+template <int LOGN, int R, int RKS = R>
 struct CoreImpl {
     using Core = NttCore<LOGN, R>;
+    using CoreKs = NttCore<LOGN, RKS>;
     static constexpr size_t SMEM = (size_t)Core::SMEM_WORDS * 4;            // NTT alone
     // NTT alone; + two parking areas (or a second exchange buffer and one)
     static constexpr size_t SMEM3 =
         ((size_t)(kDual<LOGN> ? 2 * Core::SMEM_WORDS + Core::N : Core::SMEM_WORDS + 2 * Core::N)) * 4;
     // key switch: exchange buffer(s) and the two running sums
-    static constexpr size_t SMEM_KS = ((size_t)(kDual<LOGN> ? 2 : 1) * Core::SMEM_WORDS + 2 * Core::N) * 4;
+    static constexpr size_t SMEM_KS = ((size_t)(kDual<LOGN> ? 2 : 1) * CoreKs::SMEM_WORDS + 2 * CoreKs::N) * 4;
 
     static bcn_status ntt(const bcn_ctx *c, uint32_t *data, size_t n_limbs, PrimeMap pm, bool inverse,
                           cudaStream_t st) {
@@ -358,7 +360,7 @@ struct CoreImpl {
     }
     static bcn_status keyswitch(const bcn_ctx *c, int n, const uint32_t *D, const uint32_t *D2N,
                                 const uint32_t *evk, uint32_t *acc, int C, cudaStream_t st) {
-        k_ks_core<LOGN, R><<<dim3(n + c->K, C), Core::T, SMEM_KS, st>>>(D, D2N, evk, acc, n, ks_dev(c), c->d_pc,
+        k_ks_core<LOGN, RKS><<<dim3(n + c->K, C), CoreKs::T, SMEM_KS, st>>>(D, D2N, evk, acc, n, ks_dev(c), c->d_pc,
                                                                      c->d_tw_fwd, c->d_tw_inv);
         return check_launch("k_ks_core");
     }
@@ -370,11 +372,11 @@ struct CoreImpl {
                 cudaSuccess ||
             cudaFuncSetAttribute(k_square_core<LOGN, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem3) !=
                 cudaSuccess ||
-            cudaFuncSetAttribute(k_ks_core<LOGN, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_ks) !=
+            cudaFuncSetAttribute(k_ks_core<LOGN, RKS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_ks) !=
                 cudaSuccess ||
             cudaFuncSetAttribute(k_square_core<LOGN, R>, cudaFuncAttributePreferredSharedMemoryCarveout, 100) !=
                 cudaSuccess ||
-            cudaFuncSetAttribute(k_ks_core<LOGN, R>, cudaFuncAttributePreferredSharedMemoryCarveout, 100) !=
+            cudaFuncSetAttribute(k_ks_core<LOGN, RKS>, cudaFuncAttributePreferredSharedMemoryCarveout, 100) !=
                 cudaSuccess)
             return fail(BCN_E_CUDA, "cudaFuncSetAttribute failed for the NTT-based kernels");
         return BCN_OK;

@@ -4,7 +4,10 @@
 #ifndef BCN_R12
 #define BCN_R12 16  // residues per thread
 #endif
+#ifndef BCN_R12_KS
+#define BCN_R12_KS BCN_R12  // key switch
+#endif
 
 namespace bcn {
-const CoreFns *core_fns_12() { return CoreImpl<12, BCN_R12>::fns(); }
+const CoreFns *core_fns_12() { return CoreImpl<12, BCN_R12, BCN_R12_KS>::fns(); }
 }  // namespace bcn

@@ -2,9 +2,12 @@
 #include "cores.cuh"
 
 #ifndef BCN_R14
-#define BCN_R14 16  // residues per thread
+#define BCN_R14 16  // residues per thread: NTT and square kernels (1024 threads)
+#endif
+#ifndef BCN_R14_KS
+#define BCN_R14_KS 32  // key switch: two groups of 16 per pass (512 threads, 128 registers)
 #endif
 
 namespace bcn {
-const CoreFns *core_fns_14() { return CoreImpl<14, BCN_R14>::fns(); }
+const CoreFns *core_fns_14() { return CoreImpl<14, BCN_R14, BCN_R14_KS>::fns(); }
 }  // namespace bcn

@@ -1,10 +1,11 @@
 // Register-resident negacyclic NTT for one limb per thread block.
 //
 // N = 2^LOGN residues, T = N / R threads, R residues per thread.  The log N
-// butterfly stages are grouped into passes of r = log2(R) stages (the last
-// pass may be shorter); inside a pass every butterfly of a thread pairs two of
-// its own registers, and between passes the limb is re-distributed through
-// shared memory (one padded word per 32 avoids most bank conflicts).
+// butterfly stages are grouped into passes of up to 4 stages (log2 R for
+// R <= 16; the last pass may be shorter); inside a pass every butterfly of a
+// thread pairs two of its own registers, and between passes the limb is
+// re-distributed through shared memory (one padded word per 32 avoids most
+// bank conflicts).
 //
 // Forward: Cooley-Tukey with psi merged into the twiddles (table
 // psi^{brv(k)}); natural-order input, bit-reversed output.  Inverse:
@@ -19,8 +20,8 @@
 //     lo = gidx mod tmin,  hi = gidx / tmin.
 // Only the last pass can have G > 1; there the groups of a warp interleave by
 // lane, so one register across a warp is a contiguous run (coalesced NTT-domain
-// loads and stores).  Pass 0 is e = tid + u * T (coalesced loads of natural
-// order).  Everything that selects a register is a template parameter, so the
+// loads and stores); so is one register in pass 0 (natural order: coalesced
+// loads and stores of coefficient-form limbs).  Everything that selects a register is a template parameter, so the
 // limb stays in registers.
 //
 // A pass is warp-local when every warp holds the contiguous block of 32 R
@@ -57,14 +58,17 @@ struct NttCore {
     static constexpr int N = 1 << LOGN;
     static constexpr int T = N / R;
     static constexpr int LOGR = (R == 2) ? 1 : (R == 4) ? 2 : (R == 8) ? 3 : (R == 16) ? 4 : (R == 32) ? 5 : 6;
-    static constexpr int PASSES = (LOGN + LOGR - 1) / LOGR;
+    // stages per pass: log2 R up to 4; a thread with more residues holds
+    // R / 16 independent groups of 16 in every pass
+    static constexpr int SP = LOGR > 4 ? 4 : LOGR;
+    static constexpr int PASSES = (LOGN + SP - 1) / SP;
     static constexpr int SMEM_WORDS = N + N / 32;  // padded exchange buffer
     static constexpr int WS = T < 32 ? T : 32;     // threads of one warp
     static_assert((1 << LOGR) == R, "R must be a power of two");
     static_assert(LOGN >= LOGR, "R must not exceed N");
 
-    __host__ __device__ static constexpr int s0_of(int p) { return p * LOGR; }
-    __host__ __device__ static constexpr int s1_of(int p) { return (p + 1) * LOGR < LOGN ? (p + 1) * LOGR : LOGN; }
+    __host__ __device__ static constexpr int s0_of(int p) { return p * SP; }
+    __host__ __device__ static constexpr int s1_of(int p) { return (p + 1) * SP < LOGN ? (p + 1) * SP : LOGN; }
     __host__ __device__ static constexpr int rp_of(int p) { return s1_of(p) - s0_of(p); }
     static constexpr int LAST_RP = rp_of(PASSES - 1);
 
@@ -84,7 +88,8 @@ struct NttCore {
     }
     template <int P>
     __host__ __device__ static constexpr bool warp_local() {
-        return T >= 32 && (T == 32 || P == PASSES - 1 || (N >> s1_of(P)) <= 32);  // full warps only
+        // full warps only; a warp covers 32 G consecutive butterfly groups
+        return T >= 32 && (T == 32 || P == PASSES - 1 || (N >> s1_of(P)) <= 32 * (R >> rp_of(P)));
     }
     __host__ __device__ static constexpr int padded(int e) { return e + (e >> 5); }
     // For every supported (LOGN, R, pass) both maps are linear in the thread:
@@ -309,14 +314,17 @@ struct NttCore {
         inverse_unscaled_n<1>(as_one(x), sm, tid, m, tw);
     }
 
+    // element of register u in the pass-0 distribution (natural order; one
+    // register across a warp is 32 consecutive elements)
+    __device__ __forceinline__ static int nat_elem(int u, int tid) { return elem<0>(u, tid); }
     // natural-order limb <-> pass-0 distribution (coalesced)
     __device__ __forceinline__ static void load_natural(uint32_t (&x)[R], const uint32_t *__restrict__ g, int tid) {
 #pragma unroll
-        for (int u = 0; u < R; u++) x[u] = __ldg(g + tid + u * T);
+        for (int u = 0; u < R; u++) x[u] = __ldg(g + nat_elem(u, tid));
     }
     __device__ __forceinline__ static void store_natural(const uint32_t (&x)[R], uint32_t *__restrict__ g, int tid) {
 #pragma unroll
-        for (int u = 0; u < R; u++) g[tid + u * T] = x[u];
+        for (int u = 0; u < R; u++) g[nat_elem(u, tid)] = x[u];
     }
     // element index of register u in the NTT-domain (last-pass) distribution;
     // registers 4k..4k+3 hold 4 consecutive elements when the last pass has
