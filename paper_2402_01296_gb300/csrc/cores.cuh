@@ -40,16 +40,17 @@ __global__ void __launch_bounds__((1 << LOGN) / R) k_ntt_inv(uint32_t *__restric
 }
 
 // The lazy butterflies' additions go through the FMA pipe (ModQ::one read at
-// run time) where registers are plentiful; at N = 16384 (1024-thread blocks,
-// 64 registers) the compile-time 1 folds them back into plain additions.
-template <int LOGN>
-constexpr bool kFmaOne = LOGN <= 13;
+// run time) up to N = 8192 (blocks of at most 512 threads, 128 registers); at
+// N = 16384 the compile-time 1 folds them back into plain additions (measured:
+// slower there with either block shape).
+template <int LOGN, int R>
+constexpr bool kFmaOne = (1 << LOGN) / R <= 512 && LOGN <= 13;
 
 // Pairs of independent transforms run in lockstep (shared twiddle loads and
 // barriers, twice the independent work per thread) where the registers allow
 // it: up to N = 8192.
-template <int LOGN>
-constexpr bool kDual = LOGN <= 13;
+template <int LOGN, int R>
+constexpr bool kDual = (1 << LOGN) / R <= 512 && R <= 16;
 
 // Register budget per thread of the fused kernels (sets their blocks per SM).
 #ifndef BCN_CORE_REGS
@@ -78,11 +79,11 @@ __global__ void __launch_bounds__((1 << LOGN) / R, CoreOcc<(1 << LOGN) / R>::MIN
     const int i = blockIdx.x, ct = blockIdx.y, tid = threadIdx.x;
     const PrimeConst P = pc[i];
     const uint2 *tf = twf + (size_t)i * N, *ti = twi + (size_t)i * N;
-    if constexpr (kDual<LOGN>) {
+    if constexpr (kDual<LOGN, R>) {
         // c0 and c1 transformed together (two exchange buffers), then d0 and d1
         // back together; d2 waits in a thread-private parking area (u*T + tid)
         uint32_t *s2 = sm + 2 * C::SMEM_WORDS;
-        const ModQ mq(P.q, kFmaOne<LOGN> ? P.one : 1u);
+        const ModQ mq(P.q, kFmaOne<LOGN, R> ? P.one : 1u);
         uint32_t x[2][R];
         C::load_natural(x[0], Y + (((size_t)ct * 2 + 0) * n + i) * N, tid);
         C::load_natural(x[1], Y + (((size_t)ct * 2 + 1) * n + i) * N, tid);
@@ -128,12 +129,12 @@ __global__ void __launch_bounds__((1 << LOGN) / R, CoreOcc<(1 << LOGN) / R>::MIN
     uint32_t x[R];
     // c0 -> NTT, parked in s1
     C::load_natural(x, Y + (((size_t)ct * 2 + 0) * n + i) * N, tid);
-    C::forward(x, sm, tid, ModQ(P.q, kFmaOne<LOGN> ? P.one : 1u), tf);
+    C::forward(x, sm, tid, ModQ(P.q, kFmaOne<LOGN, R> ? P.one : 1u), tf);
 #pragma unroll
     for (int u = 0; u < R; u++) s1[u * T + tid] = x[u];
     // c1 -> NTT; c0^2/N in registers, 2 c0 c1/N in s1, c1^2/N in s2 (inputs in [0, 4q))
     C::load_natural(x, Y + (((size_t)ct * 2 + 1) * n + i) * N, tid);
-    C::forward(x, sm, tid, ModQ(P.q, kFmaOne<LOGN> ? P.one : 1u), tf);
+    C::forward(x, sm, tid, ModQ(P.q, kFmaOne<LOGN, R> ? P.one : 1u), tf);
     if (D2N != nullptr) {
         uint32_t y[R];
 #pragma unroll
@@ -153,15 +154,15 @@ __global__ void __launch_bounds__((1 << LOGN) / R, CoreOcc<(1 << LOGN) / R>::MIN
         s2[u * T + tid] = mont_mul(bRN, b, P.q, P.qneg_inv);
         x[u] = mont_mul(aRN, a, P.q, P.qneg_inv);
     }
-    C::inverse_unscaled(x, sm, tid, ModQ(P.q, kFmaOne<LOGN> ? P.one : 1u), ti);
+    C::inverse_unscaled(x, sm, tid, ModQ(P.q, kFmaOne<LOGN, R> ? P.one : 1u), ti);
     C::store_natural(x, D + (((size_t)ct * 3 + 0) * n + i) * N, tid);
 #pragma unroll
     for (int u = 0; u < R; u++) x[u] = s1[u * T + tid];
-    C::inverse_unscaled(x, sm, tid, ModQ(P.q, kFmaOne<LOGN> ? P.one : 1u), ti);
+    C::inverse_unscaled(x, sm, tid, ModQ(P.q, kFmaOne<LOGN, R> ? P.one : 1u), ti);
     C::store_natural(x, D + (((size_t)ct * 3 + 1) * n + i) * N, tid);
 #pragma unroll
     for (int u = 0; u < R; u++) x[u] = s2[u * T + tid];
-    C::inverse_unscaled(x, sm, tid, ModQ(P.q, kFmaOne<LOGN> ? P.one : 1u), ti);
+    C::inverse_unscaled(x, sm, tid, ModQ(P.q, kFmaOne<LOGN, R> ? P.one : 1u), ti);
     C::store_natural(x, D + (((size_t)ct * 3 + 2) * n + i) * N, tid);
 }
 
@@ -186,7 +187,7 @@ __device__ __forceinline__ void ks_core_body(const uint32_t *__restrict__ D, con
     // Montgomery products on the data primes (the lazy inverse NTT takes
     // [0, 2q)), canonical on the special primes
     // (additions through the FMA pipe as in the lazy butterflies)
-    const uint32_t one = kFmaOne<LOGN> ? pc[0].one : 1u;
+    const uint32_t one = kFmaOne<LOGN, R> ? pc[0].one : 1u;
     auto ks_accumulate = [one](uint32_t &r0, uint32_t &r1, uint32_t xv, uint32_t w0, uint32_t w1,
                                const PrimeConst &P) {
         if constexpr (LAZY) {
@@ -203,7 +204,7 @@ __device__ __forceinline__ void ks_core_body(const uint32_t *__restrict__ D, con
     extern __shared__ __align__(16) uint32_t sm[];
     // exchange buffer(s) -- two where the final inverse transforms run together --
     // then the two running sums in thread-private slots u*T + tid
-    uint32_t *s0 = sm + (kDual<LOGN> ? 2 : 1) * C::SMEM_WORDS, *s1 = s0 + N;
+    uint32_t *s0 = sm + (kDual<LOGN, R> ? 2 : 1) * C::SMEM_WORDS, *s1 = s0 + N;
     const int t = blockIdx.x, ct = blockIdx.y, tid = threadIdx.x;
     const int A = ks.alpha, dnum = (n + A - 1) / A, nb = n + ks.K;
     const int pt = t < n ? t : ks.L + (t - n);
@@ -261,7 +262,7 @@ __device__ __forceinline__ void ks_core_body(const uint32_t *__restrict__ D, con
                     }
                 }
             }
-            C::forward(x, sm, tid, ModQ(P.q, kFmaOne<LOGN> ? P.one : 1u), tf);
+            C::forward(x, sm, tid, ModQ(P.q, kFmaOne<LOGN, R> ? P.one : 1u), tf);
         }
         const uint32_t *k0 = evk + ((size_t)(j * 2 + 0) * ks.P + pt) * N;
         const uint32_t *k1 = evk + ((size_t)(j * 2 + 1) * ks.P + pt) * N;
@@ -295,25 +296,25 @@ __device__ __forceinline__ void ks_core_body(const uint32_t *__restrict__ D, con
             }
         }
     }
-    if constexpr (kDual<LOGN>) {
+    if constexpr (kDual<LOGN, R>) {
         uint32_t y[2][R];
 #pragma unroll
         for (int u = 0; u < R; u++) {
             y[0][u] = s0[u * T + tid];
             y[1][u] = s1[u * T + tid];
         }
-        C::inverse_unscaled_n(y, sm, tid, ModQ(P.q, kFmaOne<LOGN> ? P.one : 1u), ti);
+        C::inverse_unscaled_n(y, sm, tid, ModQ(P.q, kFmaOne<LOGN, R> ? P.one : 1u), ti);
         C::store_natural(y[0], acc_out + (((size_t)ct * 2 + 0) * nb + t) * N, tid);
         C::store_natural(y[1], acc_out + (((size_t)ct * 2 + 1) * nb + t) * N, tid);
         return;
     }
 #pragma unroll
     for (int u = 0; u < R; u++) x[u] = s0[u * T + tid];
-    C::inverse_unscaled(x, sm, tid, ModQ(P.q, kFmaOne<LOGN> ? P.one : 1u), ti);
+    C::inverse_unscaled(x, sm, tid, ModQ(P.q, kFmaOne<LOGN, R> ? P.one : 1u), ti);
     C::store_natural(x, acc_out + (((size_t)ct * 2 + 0) * nb + t) * N, tid);
 #pragma unroll
     for (int u = 0; u < R; u++) x[u] = s1[u * T + tid];
-    C::inverse_unscaled(x, sm, tid, ModQ(P.q, kFmaOne<LOGN> ? P.one : 1u), ti);
+    C::inverse_unscaled(x, sm, tid, ModQ(P.q, kFmaOne<LOGN, R> ? P.one : 1u), ti);
     C::store_natural(x, acc_out + (((size_t)ct * 2 + 1) * nb + t) * N, tid);
 }
 
@@ -340,9 +341,9 @@ struct CoreImpl {
     static constexpr size_t SMEM = (size_t)Core::SMEM_WORDS * 4;            // NTT alone
     // NTT alone; + two parking areas (or a second exchange buffer and one)
     static constexpr size_t SMEM3 =
-        ((size_t)(kDual<LOGN> ? 2 * Core::SMEM_WORDS + Core::N : Core::SMEM_WORDS + 2 * Core::N)) * 4;
+        ((size_t)(kDual<LOGN, R> ? 2 * Core::SMEM_WORDS + Core::N : Core::SMEM_WORDS + 2 * Core::N)) * 4;
     // key switch: exchange buffer(s) and the two running sums
-    static constexpr size_t SMEM_KS = ((size_t)(kDual<LOGN> ? 2 : 1) * CoreKs::SMEM_WORDS + 2 * CoreKs::N) * 4;
+    static constexpr size_t SMEM_KS = ((size_t)(kDual<LOGN, RKS> ? 2 : 1) * CoreKs::SMEM_WORDS + 2 * CoreKs::N) * 4;
 
     static bcn_status ntt(const bcn_ctx *c, uint32_t *data, size_t n_limbs, PrimeMap pm, bool inverse,
                           cudaStream_t st) {
