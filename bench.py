@@ -202,17 +202,26 @@ def csrc_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str, workload: str):
-    """DRAM bytes per launch of `kernel` from a committed ncu summary, if it was
-    taken on the current sources; else None."""
+def ncu_traffic(kernel: str, workload: str, units_per_launch: float):
+    """DRAM bytes per launch of `kernel` from a committed ncu capture taken on
+    the current sources (else None): its bytes per unit of work (one block of
+    the kernel) times the units of this run's average launch."""
     p = ROOT / "profiles" / "ncu_traffic.json"
     if not p.exists():
         return None
     d = json.loads(p.read_text())
     e = d.get(workload, {}).get(kernel)
-    if not e or e.get("csrc_hash") != csrc_hash():
+    if not e or e.get("csrc_hash") != csrc_hash() or "dram_bytes_per_unit" not in e:
         return None
-    return e.get("dram_bytes_per_launch")
+    return e["dram_bytes_per_unit"] * units_per_launch
+
+
+def ks_units(cfg):
+    """(target prime, ciphertext) blocks of the key-switching kernel per evaluation."""
+    import workloads
+    levels, _ = workloads.level_schedule(cfg)
+    return sum(workloads.cipher_layer_io(l)[1] * (n + cfg["n_special"])
+               for l, n in zip(cfg["cipher"], levels) if l["square"])
 
 
 # ---------------------------------------------------------------------------
@@ -401,12 +410,14 @@ def run_ours(args, cfg, rank, world, local_rank):
     dom = max(prof, key=lambda k: prof[k][0])
     dms, dn, dbytes = prof[dom]
     ops = alu_ops(cfg)
-    traffic = ncu_traffic(dom, cfg["name"])
+    traffic = ncu_traffic(dom, cfg["name"], ks_units(cfg) * K / dn) if dom == "keyswitch" and dn else None
     if dom in ops:
         ipeak, mhz = int_peak_ops()
         achieved = ops[dom] * K / (dms / 1e3) / 1e12
         roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": ipeak / 1e12, "unit": "Tintop/s",
                 "frac": achieved * 1e12 / ipeak, "traffic": traffic,
+                "traffic_source": "ncu dram bytes per block of this kernel (profiles/ncu_traffic.json) x blocks per "
+                                  "launch of this run" if traffic else None,
                 "peak_source": f"derived: {GB300_SMS} SMs x {INT_LANES_PER_SM} int32 lanes x {mhz:.0f} MHz",
                 "ops_per_launch": ops[dom] * K / dn,
                 "hbm_achieved_GBps": (dbytes / (dms / 1e3)) / 1e9, "hbm_peak_GBps": measured_peaks()[0]}
