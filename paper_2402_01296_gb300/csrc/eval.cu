@@ -19,6 +19,22 @@ namespace bcn {
 
 // taps whose weights and indices a MAC block holds in shared memory at a time
 constexpr int kMacTapChunk = 2048;
+// input staging of the grouped MAC: every thread streams its taps' words
+// through a private ring of kMacS stages x kMacU taps in shared memory
+// (cp.async), so the loads of kMacS - 1 stages are in flight while it
+// multiplies the current one
+constexpr int kMacU = 4, kMacS = 3, kMacThreads = 256;
+constexpr size_t kMacRingBytes = (size_t)kMacS * kMacU * kMacThreads * 16;
+
+__device__ __forceinline__ void mac_cp_async16(uint32_t dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+
+// shared memory of a grouped-MAC block with OT outputs per thread and taps
+// chunks of kca: input ring, then weights [kca][OTP], then tap inputs [kca]
+__host__ __device__ constexpr size_t mac_grouped_smem(int OT, int kca) {
+    return kMacRingBytes + (size_t)kca * 4 * (1 + (OT + 3) / 4 * 4);
+}
 
 // ------------------------------------------------------------------- kernels
 // Integer-weight MAC + feature add over output groups.  A group is a set of
@@ -29,19 +45,20 @@ constexpr int kMacTapChunk = 2048;
 // store(g, o) is the output's natural (channel, row, column) index gout[g][o]
 // when store_natural, else its group-major position (g - g_base) * n_go + o
 // (the order kept between layers, so a chunk of outputs is a run of groups).
-// Columns run over the (poly, limb, coefficient) words of a ciphertext.
+// Columns run over the (poly, limb, coefficient) words of a ciphertext.  Taps
+// are taken in chunks of kca (weights and input indices in shared memory).
 // grid (ceil(2*level*N/4/256), groups in this launch * ceil(n_go/OT)), 256 threads.
 template <int OT>
-__global__ void __launch_bounds__(256) k_mac_grouped(const uint32_t *__restrict__ in, uint32_t *__restrict__ out,
+__global__ void __launch_bounds__(kMacThreads, OT <= 5 ? 3 : 2) k_mac_grouped(const uint32_t *__restrict__ in, uint32_t *__restrict__ out,
                                                      const int32_t *__restrict__ gidx, const int8_t *__restrict__ gw,
                                                      const int32_t *__restrict__ gout, const uint32_t *__restrict__ pt,
-                                                     int K, int n_go, int level, int N, int g_base,
+                                                     int K, int kca, int n_go, int level, int N, int g_base,
                                                      int store_natural, int t_lo, int n_tl,
                                                      const PrimeConst *__restrict__ pc) {
     constexpr int OTP = (OT + 3) / 4 * 4;  // weight row padded to whole int4 loads
     extern __shared__ __align__(16) unsigned char smraw[];
-    int32_t *sw = reinterpret_cast<int32_t *>(smraw);                        // [KC][OTP] weights (0: padding tap)
-    int32_t *sidx = reinterpret_cast<int32_t *>(smraw) + (size_t)kMacTapChunk * OTP;  // [KC] input (0: padding)
+    int32_t *sw = reinterpret_cast<int32_t *>(smraw + kMacRingBytes);  // [kca][OTP] weights (0: padding tap)
+    int32_t *sidx = sw + (size_t)kca * OTP;                            // [kca] input (0: padding)
     // output tiles [t_lo, t_lo + n_tl) of every group
     const int g = g_base + blockIdx.y / n_tl, o0 = (t_lo + (int)blockIdx.y % n_tl) * OT;
     const int no = min(OT, n_go - o0);
@@ -53,8 +70,8 @@ __global__ void __launch_bounds__(256) k_mac_grouped(const uint32_t *__restrict_
 #pragma unroll
     for (int o = 0; o < OT; o++) acc[o][0] = acc[o][1] = acc[o][2] = acc[o][3] = 0;
     const uint32_t *base = in + (active ? col : 0);
-    for (int t0 = 0; t0 < K; t0 += kMacTapChunk) {  // taps in chunks that fit shared memory
-        const int KC = min(kMacTapChunk, K - t0);
+    for (int t0 = 0; t0 < K; t0 += kca) {  // taps in chunks that fit shared memory
+        const int KC = min(kca, K - t0);
         __syncthreads();  // the previous chunk's taps are no longer read
         for (int t = threadIdx.x; t < KC; t += blockDim.x) {
             const int src = gidx[(size_t)g * K + t0 + t];
@@ -67,36 +84,46 @@ __global__ void __launch_bounds__(256) k_mac_grouped(const uint32_t *__restrict_
         }
         __syncthreads();
         if (!active) continue;
-        constexpr int U = 4;  // taps in flight per thread
-        int t = 0;
-        for (; t + U <= KC; t += U) {
-            uint4 x[U];
+        // thread-private ring: slot (stage % kMacS, k) of this thread at
+        // ((slot * kMacU + k) * kMacThreads + tid) * 16 bytes; only the thread
+        // that copies a word reads it, so cp.async.wait_group is the only sync
+        const uint32_t ring = (uint32_t)__cvta_generic_to_shared(smraw) + threadIdx.x * 16;
+        const uint4 *rr = reinterpret_cast<const uint4 *>(smraw) + threadIdx.x;
+        const int nst = (KC + kMacU - 1) / kMacU;
+        auto issue = [&](int s) {  // taps of stage s, one commit group (empty past the last stage)
+            if (s < nst) {
+                const int slot = s % kMacS;
 #pragma unroll
-            for (int k = 0; k < U; k++)
-                x[k] = __ldg(reinterpret_cast<const uint4 *>(base + (size_t)sidx[t + k] * cols));
-#pragma unroll
-            for (int k = 0; k < U; k++) {
-                const int32_t *wr = sw + (t + k) * OTP;
-#pragma unroll
-                for (int o = 0; o < OT; o++) {
-                    const long long w = wr[o];
-                    acc[o][0] += w * (int)x[k].x;
-                    acc[o][1] += w * (int)x[k].y;
-                    acc[o][2] += w * (int)x[k].z;
-                    acc[o][3] += w * (int)x[k].w;
+                for (int k = 0; k < kMacU; k++) {
+                    const int t = s * kMacU + k;
+                    if (t < KC)
+                        mac_cp_async16(ring + (uint32_t)((slot * kMacU + k) * kMacThreads * 16),
+                                       base + (size_t)sidx[t] * cols);
                 }
             }
-        }
-        for (; t < KC; t++) {
-            const uint4 x = __ldg(reinterpret_cast<const uint4 *>(base + (size_t)sidx[t] * cols));
-            const int32_t *wr = sw + t * OTP;
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
 #pragma unroll
-            for (int o = 0; o < OT; o++) {
-                const long long w = wr[o];
-                acc[o][0] += w * (int)x.x;
-                acc[o][1] += w * (int)x.y;
-                acc[o][2] += w * (int)x.z;
-                acc[o][3] += w * (int)x.w;
+        for (int s = 0; s < kMacS - 1; s++) issue(s);
+        for (int s = 0; s < nst; s++) {
+            issue(s + kMacS - 1);
+            asm volatile("cp.async.wait_group %0;" ::"n"(kMacS - 1) : "memory");
+            const int slot = s % kMacS;
+#pragma unroll
+            for (int k = 0; k < kMacU; k++) {
+                const int t = s * kMacU + k;
+                if (t < KC) {
+                    const uint4 x = rr[(slot * kMacU + k) * kMacThreads];
+                    const int32_t *wr = sw + t * OTP;
+#pragma unroll
+                    for (int o = 0; o < OT; o++) {
+                        const long long w = wr[o];
+                        acc[o][0] += w * (int)x.x;
+                        acc[o][1] += w * (int)x.y;
+                        acc[o][2] += w * (int)x.z;
+                        acc[o][3] += w * (int)x.w;
+                    }
+                }
             }
         }
     }
@@ -105,24 +132,39 @@ __global__ void __launch_bounds__(256) k_mac_grouped(const uint32_t *__restrict_
     const uint32_t q = pc[i].q;
     const uint64_t mu = pc[i].barrett;
     const long long off = (long long)pc[i].mac_offset;
+    // every output's index and feature word are requested before any is used
+    // (independent loads, one round trip)
+    int og[OT];
+    uint4 r[OT];
 #pragma unroll
     for (int o = 0; o < OT; o++) {
-        if (o >= no) break;
-        const int og = gout != nullptr ? gout[(size_t)g * n_go + o0 + o] : g * n_go + o0 + o;
-        const int os = store_natural ? og : (g - g_base) * n_go + o0 + o;
-        uint4 r;
-        r.x = barrett_reduce64((uint64_t)(acc[o][0] + off), q, mu);
-        r.y = barrett_reduce64((uint64_t)(acc[o][1] + off), q, mu);
-        r.z = barrett_reduce64((uint64_t)(acc[o][2] + off), q, mu);
-        r.w = barrett_reduce64((uint64_t)(acc[o][3] + off), q, mu);
-        if (pt != nullptr && poly == 0) {
-            const uint4 p = __ldg(reinterpret_cast<const uint4 *>(pt + (size_t)og * level * N + col));
-            r.x = add_mod(r.x, p.x, q);
-            r.y = add_mod(r.y, p.y, q);
-            r.z = add_mod(r.z, p.z, q);
-            r.w = add_mod(r.w, p.w, q);
+        og[o] = o < no ? (gout != nullptr ? gout[(size_t)g * n_go + o0 + o] : g * n_go + o0 + o) : 0;
+        r[o].x = barrett_reduce64((uint64_t)(acc[o][0] + off), q, mu);
+        r[o].y = barrett_reduce64((uint64_t)(acc[o][1] + off), q, mu);
+        r[o].z = barrett_reduce64((uint64_t)(acc[o][2] + off), q, mu);
+        r[o].w = barrett_reduce64((uint64_t)(acc[o][3] + off), q, mu);
+    }
+    if (pt != nullptr && poly == 0) {
+        uint4 p[OT];
+#pragma unroll
+        for (int o = 0; o < OT; o++)
+            if (o < no) p[o] = __ldg(reinterpret_cast<const uint4 *>(pt + (size_t)og[o] * level * N + col));
+#pragma unroll
+        for (int o = 0; o < OT; o++) {
+            if (o < no) {
+                r[o].x = add_mod(r[o].x, p[o].x, q);
+                r[o].y = add_mod(r[o].y, p[o].y, q);
+                r[o].z = add_mod(r[o].z, p[o].z, q);
+                r[o].w = add_mod(r[o].w, p[o].w, q);
+            }
         }
-        *reinterpret_cast<uint4 *>(out + (size_t)os * cols + col) = r;
+    }
+#pragma unroll
+    for (int o = 0; o < OT; o++) {
+        if (o < no) {
+            const int os = store_natural ? og[o] : (g - g_base) * n_go + o0 + o;
+            *reinterpret_cast<uint4 *>(out + (size_t)os * cols + col) = r[o];
+        }
     }
 }
 
@@ -338,13 +380,14 @@ static bcn_status launch_mac(const bcn_ctx *c, int level, int K, int n_groups, i
     const int OT = std::min(8, n_go);
     const int t_lo = o_lo / OT, n_tl = (o_hi + OT - 1) / OT - t_lo;
     const size_t cols = (size_t)2 * level * N;
-    const size_t smem = (size_t)kMacTapChunk * 4 * (1 + (OT + 3) / 4 * 4);
+    const int kca = std::min(K, kMacTapChunk);
+    const size_t smem = mac_grouped_smem(OT, kca);
     if ((long long)n_groups * n_tl > 65535) return fail(BCN_E_INVAL, "MAC layer with more than 65535 output tiles");
     Timed tm(prof, st, BCN_KERNEL_MAC, alg_bytes);
     dim3 grid((unsigned)((cols / 4 + 255) / 256), (unsigned)(n_groups * n_tl));
 #define BCN_MAC(OTV)                                                                                          \
     case OTV:                                                                                                 \
-        k_mac_grouped<OTV><<<grid, 256, smem, st>>>(in, out, gidx, gw, gout, pt, K, n_go, level, N, g_base, \
+        k_mac_grouped<OTV><<<grid, kMacThreads, smem, st>>>(in, out, gidx, gw, gout, pt, K, kca, n_go, level, N, g_base, \
                                                     store_natural ? 1 : 0, t_lo, n_tl, c->d_pc);              \
         break;
     switch (OT) { BCN_MAC(1) BCN_MAC(2) BCN_MAC(3) BCN_MAC(4) BCN_MAC(5) BCN_MAC(6) BCN_MAC(7) BCN_MAC(8) }
@@ -415,7 +458,7 @@ bcn_status device_ctx_init(bcn_ctx *c) {
     if (!ok) return fail(BCN_E_CUDA, "upload of the context tables failed");
     BCN_TRY(cores_setup_all());
     BCN_TRY(mac_tc_setup());
-    const int mac_smem = kMacTapChunk * 4 * (1 + 8);
+    const int mac_smem = (int)mac_grouped_smem(8, kMacTapChunk);
 #define BCN_MSETUP(OTV)                                                                                           \
     if (cudaFuncSetAttribute(k_mac_grouped<OTV>, cudaFuncAttributeMaxDynamicSharedMemorySize, mac_smem) !=      \
         cudaSuccess)                                                                                            \

@@ -120,7 +120,7 @@ __device__ __forceinline__ void stage_slab(uint32_t stage, const uint32_t *__res
 // Shared memory: kStages raw stages (cp.async, kStages - 1 slabs in flight
 // ahead of the one being converted), the fp16 planes of one slab (A), the
 // tile's weights (B), the tap indices, the mbarrier.
-__global__ void __launch_bounds__(kThreads) k_mac_tc(const uint32_t *__restrict__ in, uint32_t *__restrict__ out,
+__global__ void __launch_bounds__(kThreads, 2) k_mac_tc(const uint32_t *__restrict__ in, uint32_t *__restrict__ out,
                                                      const int32_t *__restrict__ gidx, const uint4 *__restrict__ w16,
                                                      const int32_t *__restrict__ gout,
                                                      const uint32_t *__restrict__ pt, int K, int Kpad, int n_go,
@@ -135,6 +135,7 @@ __global__ void __launch_bounds__(kThreads) k_mac_tc(const uint32_t *__restrict_
     uint64_t *mbar = reinterpret_cast<uint64_t *>(sidx + Kpad);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
     volatile int *flag = reinterpret_cast<volatile int *>(tslot + 1);
+    int32_t *sgo = reinterpret_cast<int32_t *>(tslot + 2);  // [NT] the tile's output indices
 
     const int tid = threadIdx.x, warp = tid >> 5, r = tid & (kRows - 1), half = tid >> 7;
     const int g = g_base + (int)blockIdx.y / n_tl, tile = t_lo + (int)blockIdx.y % n_tl;
@@ -154,6 +155,7 @@ __global__ void __launch_bounds__(kThreads) k_mac_tc(const uint32_t *__restrict_
         *flag = 0;
     }
     for (int t = tid; t < Kpad; t += kThreads) sidx[t] = t < K ? gidx[(size_t)g * K + t] : -1;
+    for (int o = tid; o < no; o += kThreads) sgo[o] = gout != nullptr ? gout[(size_t)g * n_go + o0 + o] : g * n_go + o0 + o;
     __syncthreads();  // sidx
     const uint32_t s_base = smem_addr(S);
 #pragma unroll
@@ -246,19 +248,24 @@ __global__ void __launch_bounds__(kThreads) k_mac_tc(const uint32_t *__restrict_
             uint32_t f[kPlanes][16];
 #pragma unroll
             for (int b = 0; b < kPlanes; b++) tmem_ld16(lanes + (uint32_t)(b * NT + ob), f[b]);
+            const int nv = min(16, no - ob);  // live outputs of this block of 16 (may be <= 0)
+            // the feature words of all 16 outputs are requested before any is used
+            uint32_t pv[16];
+#pragma unroll
+            for (int o = 0; o < 16; o++)
+                pv[o] = pt != nullptr && poly == 0 && o < nv ? __ldg(pt + (size_t)sgo[ob + o] * level * N + col) : 0u;
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
             for (int o = 0; o < 16; o++) {
-                if (ob + o >= no) break;
-                long long v = offs;
+                if (o < nv) {
+                    long long v = offs;
 #pragma unroll
-                for (int b = 0; b < kPlanes; b++)
-                    v += (long long)__float2int_rn(__uint_as_float(f[b][o])) << (8 * b);
-                uint32_t res = barrett_reduce64((uint64_t)v, q, mu);
-                const int og = gout != nullptr ? gout[(size_t)g * n_go + o0 + ob + o] : g * n_go + o0 + ob + o;
-                const int os = store_natural ? og : (g - g_base) * n_go + o0 + ob + o;
-                if (pt != nullptr && poly == 0) res = add_mod(res, __ldg(pt + (size_t)og * level * N + col), q);
-                out[(size_t)os * cols + col] = res;
+                    for (int b = 0; b < kPlanes; b++)
+                        v += (long long)__float2int_rn(__uint_as_float(f[b][o])) << (8 * b);
+                    const uint32_t res = add_mod(barrett_reduce64((uint64_t)v, q, mu), pv[o], q);
+                    const int os = store_natural ? sgo[ob + o] : (g - g_base) * n_go + o0 + ob + o;
+                    out[(size_t)os * cols + col] = res;
+                }
             }
         }
     } else if (tid == 0) {
@@ -287,7 +294,8 @@ bool mac_tc_eligible(const bcn_ctx *c, int K, int n_go) {
 }
 
 size_t mac_tc_smem(int NT, int Kpad) {
-    return (size_t)kStages * kStageBytes + kABytes + (size_t)NT * Kpad * 2 + (size_t)Kpad * 4 + 16 + 1024;
+    return (size_t)kStages * kStageBytes + kABytes + (size_t)NT * Kpad * 2 + (size_t)Kpad * 4 + 16 + (size_t)NT * 4 +
+           1024;
 }
 
 bcn_status mac_tc_plan(const bcn_ctx *c, int K, int n_go, const int8_t *w, MacTcPlan *p) {
