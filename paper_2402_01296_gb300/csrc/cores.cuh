@@ -211,10 +211,90 @@ __device__ __forceinline__ void ks_core_body(const uint32_t *__restrict__ D, con
     const PrimeConst P = pc[pt];
     const uint2 *tf = twf + (size_t)pt * N, *ti = twi + (size_t)pt * N;
     const uint32_t *x2 = D + ((size_t)ct * 3 + 2) * n * N;
+    // product of a digit's NTT-domain ModUp limb with both halves of its key,
+    // added to the running sums
+    auto key_product = [&](const uint32_t(&xr)[R], int j) {
+        const uint32_t *k0 = evk + ((size_t)(j * 2 + 0) * ks.P + pt) * N;
+        const uint32_t *k1 = evk + ((size_t)(j * 2 + 1) * ks.P + pt) * N;
+        if constexpr (C::NTT_QUADS) {
+#pragma unroll
+            for (int u = 0; u < R; u += 4) {
+                const int e = C::ntt_elem(u, tid);
+                const uint4 v0 = __ldg(reinterpret_cast<const uint4 *>(k0 + e));
+                const uint4 v1 = __ldg(reinterpret_cast<const uint4 *>(k1 + e));
+                const uint32_t w0[4] = {v0.x, v0.y, v0.z, v0.w}, w1[4] = {v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+                for (int z = 0; z < 4; z++) ks_accumulate(s0[(u + z) * T + tid], s1[(u + z) * T + tid], xr[u + z],
+                                                          w0[z], w1[z], P);
+            }
+        } else if constexpr (C::NTT_PAIRS) {
+#pragma unroll
+            for (int u = 0; u < R; u += 2) {
+                const int e = C::ntt_elem(u, tid);
+                const uint2 v0 = __ldg(reinterpret_cast<const uint2 *>(k0 + e));
+                const uint2 v1 = __ldg(reinterpret_cast<const uint2 *>(k1 + e));
+                const uint32_t w0[2] = {v0.x, v0.y}, w1[2] = {v1.x, v1.y};
+#pragma unroll
+                for (int z = 0; z < 2; z++) ks_accumulate(s0[(u + z) * T + tid], s1[(u + z) * T + tid], xr[u + z],
+                                                          w0[z], w1[z], P);
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < R; u++) {
+                const int e = C::ntt_elem(u, tid);
+                ks_accumulate(s0[u * T + tid], s1[u * T + tid], xr[u], __ldg(k0 + e), __ldg(k1 + e), P);
+            }
+        }
+    };
     uint32_t x[R];
 #pragma unroll
     for (int u = 0; u < R; u++) s0[u * T + tid] = s1[u * T + tid] = 0;
-    for (int j = 0; j < dnum; j++) {
+    bool summed = false;
+    if constexpr (LAZY && kDual<LOGN, R>) {
+        if (A == 1) {
+            // one-prime digits: the digit's own limb from D2N when given; the
+            // others lifted (d, less q_j mod t when d > (q_j-1)/2; the own
+            // limb unchanged) and transformed two at a time in lockstep
+            const bool own_ntt = t < n && D2N != nullptr;
+            if (own_ntt) {
+                C::load_ntt(x, D2N + ((size_t)ct * n + t) * N, tid);
+                key_product(x, t);
+            }
+            auto lift = [&](uint32_t(&xr)[R], int j) {
+                uint32_t half = 0xFFFFFFFFu, tmq = 0u;
+                if (j != t) {
+                    half = pc[j].half;
+                    tmq = P.q - ks.dprod[(size_t)(n * ks.dnum_max + j) * ks.P + pt];  // t - (q_j mod t)
+                }
+                const uint32_t *xj = x2 + (size_t)j * N;
+#pragma unroll
+                for (int u = 0; u < R; u++) {
+                    const uint32_t d = __ldg(xj + C::nat_elem(u, tid));
+                    xr[u] = d * one + (d > half ? tmq : 0u);
+                }
+            };
+            auto skip_own = [&](int j) { return own_ntt && j == t ? j + 1 : j; };
+            uint32_t y[2][R];
+            for (int j = skip_own(0); j < n;) {
+                const int j1 = skip_own(j + 1);
+                if (j1 < n) {
+                    lift(y[0], j);
+                    lift(y[1], j1);
+                    C::template forward_n<2>(y, sm, tid, ModQ(P.q, kFmaOne<LOGN, R> ? P.one : 1u), tf);
+                    key_product(y[0], j);
+                    key_product(y[1], j1);
+                    j = skip_own(j1 + 1);
+                } else {
+                    lift(x, j);
+                    C::forward(x, sm, tid, ModQ(P.q, kFmaOne<LOGN, R> ? P.one : 1u), tf);
+                    key_product(x, j);
+                    j = n;
+                }
+            }
+            summed = true;
+        }
+    }
+    for (int j = 0; j < dnum && !summed; j++) {
         const int lo = j * A, hi = min(lo + A, n);
         if (t >= lo && t < hi && D2N != nullptr) {
             C::load_ntt(x, D2N + ((size_t)ct * n + t) * N, tid);
@@ -264,37 +344,7 @@ __device__ __forceinline__ void ks_core_body(const uint32_t *__restrict__ D, con
             }
             C::forward(x, sm, tid, ModQ(P.q, kFmaOne<LOGN, R> ? P.one : 1u), tf);
         }
-        const uint32_t *k0 = evk + ((size_t)(j * 2 + 0) * ks.P + pt) * N;
-        const uint32_t *k1 = evk + ((size_t)(j * 2 + 1) * ks.P + pt) * N;
-        if constexpr (C::NTT_QUADS) {
-#pragma unroll
-            for (int u = 0; u < R; u += 4) {
-                const int e = C::ntt_elem(u, tid);
-                const uint4 v0 = __ldg(reinterpret_cast<const uint4 *>(k0 + e));
-                const uint4 v1 = __ldg(reinterpret_cast<const uint4 *>(k1 + e));
-                const uint32_t w0[4] = {v0.x, v0.y, v0.z, v0.w}, w1[4] = {v1.x, v1.y, v1.z, v1.w};
-#pragma unroll
-                for (int z = 0; z < 4; z++) ks_accumulate(s0[(u + z) * T + tid], s1[(u + z) * T + tid], x[u + z],
-                                                          w0[z], w1[z], P);
-            }
-        } else if constexpr (C::NTT_PAIRS) {
-#pragma unroll
-            for (int u = 0; u < R; u += 2) {
-                const int e = C::ntt_elem(u, tid);
-                const uint2 v0 = __ldg(reinterpret_cast<const uint2 *>(k0 + e));
-                const uint2 v1 = __ldg(reinterpret_cast<const uint2 *>(k1 + e));
-                const uint32_t w0[2] = {v0.x, v0.y}, w1[2] = {v1.x, v1.y};
-#pragma unroll
-                for (int z = 0; z < 2; z++) ks_accumulate(s0[(u + z) * T + tid], s1[(u + z) * T + tid], x[u + z],
-                                                          w0[z], w1[z], P);
-            }
-        } else {
-#pragma unroll
-            for (int u = 0; u < R; u++) {
-                const int e = C::ntt_elem(u, tid);
-                ks_accumulate(s0[u * T + tid], s1[u * T + tid], x[u], __ldg(k0 + e), __ldg(k1 + e), P);
-            }
-        }
+        key_product(x, j);
     }
     if constexpr (kDual<LOGN, R>) {
         uint32_t y[2][R];
