@@ -39,12 +39,24 @@ __global__ void __launch_bounds__((1 << LOGN) / R) k_ntt_inv(uint32_t *__restric
     C::store_natural(x, a, tid);
 }
 
-// The lazy butterflies' additions go through the FMA pipe (ModQ::one read at
-// run time) up to N = 8192 (blocks of at most 512 threads, 128 registers); at
-// N = 16384 the compile-time 1 folds them back into plain additions (measured:
-// slower there with either block shape).
+// The lazy butterflies' additions selected by each kernel's FMA bits go
+// through the FMA pipe (ModQ::one read at run time) in blocks of at most 512
+// threads (128 registers); in the 1024-thread blocks of the N = 16384 square
+// kernel the compile-time 1 folds them back into plain additions.
 template <int LOGN, int R>
-constexpr bool kFmaOne = (1 << LOGN) / R <= 512 && LOGN <= 13;
+constexpr bool kFmaOne = (1 << LOGN) / R <= 512;
+
+// Lazy-butterfly additions on the FMA pipe, per kernel (measured at N = 8192:
+// the square kernel's transforms are best with only the forward min's
+// subtraction there, the key switch's with the inverse min's as well; its
+// running sums add on the ALU pipe)
+#ifndef BCN_FMA_SQ
+#define BCN_FMA_SQ kFmaFwdMin
+#endif
+#ifndef BCN_FMA_KS
+#define BCN_FMA_KS (kFmaFwdMin | kFmaInvMin)
+#endif
+constexpr int kFmaSquare = BCN_FMA_SQ, kFmaKs = BCN_FMA_KS;
 
 // Pairs of independent transforms run in lockstep (shared twiddle loads and
 // barriers, twice the independent work per thread) where the registers allow
@@ -73,7 +85,7 @@ template <int LOGN, int R>
 __global__ void __launch_bounds__((1 << LOGN) / R, CoreOcc<(1 << LOGN) / R>::MIN_BLOCKS)
     k_square_core(const uint32_t *__restrict__ Y, uint32_t *__restrict__ D, uint32_t *__restrict__ D2N, int n,
                   const PrimeConst *__restrict__ pc, const uint2 *__restrict__ twf, const uint2 *__restrict__ twi) {
-    using C = NttCore<LOGN, R, true>;  // data primes only (q < 2^30): lazy butterflies
+    using C = NttCore<LOGN, R, true, kFmaSquare>;  // data primes only (q < 2^30): lazy butterflies
     constexpr int N = C::N, T = C::T;
     extern __shared__ __align__(16) uint32_t sm[];
     const int i = blockIdx.x, ct = blockIdx.y, tid = threadIdx.x;
@@ -181,21 +193,20 @@ __device__ __forceinline__ void ks_core_body(const uint32_t *__restrict__ D, con
                                              const uint32_t *__restrict__ evk, uint32_t *__restrict__ acc_out,
                                              int n, const KsDev &ks, const PrimeConst *__restrict__ pc,
                                              const uint2 *__restrict__ twf, const uint2 *__restrict__ twi) {
-    using C = NttCore<LOGN, R, LAZY>;
+    using C = NttCore<LOGN, R, LAZY, kFmaKs>;
     constexpr int N = C::N, T = C::T;
     // running sums r0 += x k0 / R, r1 += x k1 / R: kept in [0, 2q) with lazy
     // Montgomery products on the data primes (the lazy inverse NTT takes
     // [0, 2q)), canonical on the special primes
     // (additions through the FMA pipe as in the lazy butterflies)
-    const uint32_t one = kFmaOne<LOGN, R> ? pc[0].one : 1u;
-    auto ks_accumulate = [one](uint32_t &r0, uint32_t &r1, uint32_t xv, uint32_t w0, uint32_t w1,
-                               const PrimeConst &P) {
+    auto ks_accumulate = [](uint32_t &r0, uint32_t &r1, uint32_t xv, uint32_t w0, uint32_t w1,
+                            const PrimeConst &P) {
         if constexpr (LAZY) {
             const uint32_t nq2 = 0u - 2 * P.q;
-            const uint32_t a0 = mont_mul_lazy(xv, w0, P.q, P.qneg_inv) * one + r0;
-            const uint32_t a1 = mont_mul_lazy(xv, w1, P.q, P.qneg_inv) * one + r1;
-            r0 = min(a0, a0 * one + nq2);
-            r1 = min(a1, a1 * one + nq2);
+            const uint32_t a0 = mont_mul_lazy(xv, w0, P.q, P.qneg_inv) + r0;
+            const uint32_t a1 = mont_mul_lazy(xv, w1, P.q, P.qneg_inv) + r1;
+            r0 = min(a0, a0 + nq2);
+            r1 = min(a1, a1 + nq2);
         } else {
             r0 = add_mod(r0, mont_mul(xv, w0, P.q, P.qneg_inv), P.q);
             r1 = add_mod(r1, mont_mul(xv, w1, P.q, P.qneg_inv), P.q);
@@ -246,6 +257,39 @@ __device__ __forceinline__ void ks_core_body(const uint32_t *__restrict__ D, con
             }
         }
     };
+    // the same for two digits' limbs, one pass over the sums
+    auto key_product2 = [&](const uint32_t(&xr)[2][R], int ja, int jb) {
+        const uint32_t *ka0 = evk + ((size_t)(ja * 2 + 0) * ks.P + pt) * N;
+        const uint32_t *ka1 = evk + ((size_t)(ja * 2 + 1) * ks.P + pt) * N;
+        const uint32_t *kb0 = evk + ((size_t)(jb * 2 + 0) * ks.P + pt) * N;
+        const uint32_t *kb1 = evk + ((size_t)(jb * 2 + 1) * ks.P + pt) * N;
+        static_assert(C::NTT_QUADS || C::NTT_PAIRS, "paired key products read whole pairs");
+        constexpr int V = C::NTT_QUADS ? 4 : 2;
+#pragma unroll
+        for (int u = 0; u < R; u += V) {
+            const int e = C::ntt_elem(u, tid);
+            uint32_t wa0[V], wa1[V], wb0[V], wb1[V];
+            if constexpr (V == 4) {
+                *reinterpret_cast<uint4 *>(wa0) = __ldg(reinterpret_cast<const uint4 *>(ka0 + e));
+                *reinterpret_cast<uint4 *>(wa1) = __ldg(reinterpret_cast<const uint4 *>(ka1 + e));
+                *reinterpret_cast<uint4 *>(wb0) = __ldg(reinterpret_cast<const uint4 *>(kb0 + e));
+                *reinterpret_cast<uint4 *>(wb1) = __ldg(reinterpret_cast<const uint4 *>(kb1 + e));
+            } else {
+                *reinterpret_cast<uint2 *>(wa0) = __ldg(reinterpret_cast<const uint2 *>(ka0 + e));
+                *reinterpret_cast<uint2 *>(wa1) = __ldg(reinterpret_cast<const uint2 *>(ka1 + e));
+                *reinterpret_cast<uint2 *>(wb0) = __ldg(reinterpret_cast<const uint2 *>(kb0 + e));
+                *reinterpret_cast<uint2 *>(wb1) = __ldg(reinterpret_cast<const uint2 *>(kb1 + e));
+            }
+#pragma unroll
+            for (int z = 0; z < V; z++) {
+                uint32_t r0 = s0[(u + z) * T + tid], r1 = s1[(u + z) * T + tid];
+                ks_accumulate(r0, r1, xr[0][u + z], wa0[z], wa1[z], P);
+                ks_accumulate(r0, r1, xr[1][u + z], wb0[z], wb1[z], P);
+                s0[(u + z) * T + tid] = r0;
+                s1[(u + z) * T + tid] = r1;
+            }
+        }
+    };
     uint32_t x[R];
 #pragma unroll
     for (int u = 0; u < R; u++) s0[u * T + tid] = s1[u * T + tid] = 0;
@@ -270,7 +314,7 @@ __device__ __forceinline__ void ks_core_body(const uint32_t *__restrict__ D, con
 #pragma unroll
                 for (int u = 0; u < R; u++) {
                     const uint32_t d = __ldg(xj + C::nat_elem(u, tid));
-                    xr[u] = d * one + (d > half ? tmq : 0u);
+                    xr[u] = d + (d > half ? tmq : 0u);
                 }
             };
             auto skip_own = [&](int j) { return own_ntt && j == t ? j + 1 : j; };
@@ -281,8 +325,7 @@ __device__ __forceinline__ void ks_core_body(const uint32_t *__restrict__ D, con
                     lift(y[0], j);
                     lift(y[1], j1);
                     C::template forward_n<2>(y, sm, tid, ModQ(P.q, kFmaOne<LOGN, R> ? P.one : 1u), tf);
-                    key_product(y[0], j);
-                    key_product(y[1], j1);
+                    key_product2(y, j, j1);
                     j = skip_own(j1 + 1);
                 } else {
                     lift(x, j);
@@ -312,7 +355,7 @@ __device__ __forceinline__ void ks_core_body(const uint32_t *__restrict__ D, con
 #pragma unroll
                     for (int u = 0; u < R; u++) {
                         const uint32_t d = __ldg(xj + C::nat_elem(u, tid));
-                        x[u] = d * one + (d > half ? tmq : 0u);
+                        x[u] = d + (d > half ? tmq : 0u);
                     }
                 } else {
 #pragma unroll

@@ -44,16 +44,27 @@
 
 namespace bcn {
 
-// A prime and the value 1 read at run time.  The lazy butterflies add through
-// multiply-adds by `one`, which the compiler cannot fold into plain additions:
-// they issue on the FMA pipe and leave the half-rate ALU pipe to the min and
-// three-input add that remain.  Constructed from q alone, one is the constant 1.
+// A prime and the value 1 read at run time.  A lazy butterfly's addition
+// written as a multiply-add by `one`, which the compiler cannot fold into a
+// plain addition, issues on the FMA pipe instead of the ALU pipe; which of them
+// do is the FMA bit set of NttCore (both pipes run 32-bit integer work at half
+// rate, and the Shoup products already load the FMA pipe, so the best split
+// is measured per kernel).  Constructed from q alone, one is the constant 1 and
+// every addition stays on the ALU pipe.
 struct ModQ {
     uint32_t q, one;
     __device__ __forceinline__ ModQ(uint32_t q_, uint32_t one_ = 1u) : q(q_), one(one_) {}
 };
 
-template <int LOGN, int R, bool LAZY = false>
+// FMA bits: which lazy-butterfly additions multiply by ModQ::one
+enum : int {
+    kFmaFwdMin = 1,  // forward: the subtraction of 2q under the min
+    kFmaFwdSum = 2,  // forward: U + V
+    kFmaInvSum = 4,  // inverse: U + V
+    kFmaInvMin = 8,  // inverse: the subtraction of 2q under the min
+};
+
+template <int LOGN, int R, bool LAZY = false, int FMA = kFmaFwdMin>
 struct NttCore {
     static constexpr int N = 1 << LOGN;
     static constexpr int T = N / R;
@@ -186,9 +197,9 @@ struct NttCore {
                 for (int p = 0; p < NP; p++) {
                     if constexpr (LAZY) {
                         const uint32_t q2 = 2 * q, nq2 = 0u - q2, xu = x[p][u];
-                        const uint32_t U = min(xu, xu * m.one + nq2);  // [0, 2q)
+                        const uint32_t U = min(xu, xu * ((FMA & kFmaFwdMin) ? m.one : 1u) + nq2);  // [0, 2q)
                         const uint32_t V = shoup_mul_lazy(x[p][u + d], W.x, W.y, q);
-                        x[p][u] = V * m.one + U;   // [0, 4q)
+                        x[p][u] = V * ((FMA & kFmaFwdSum) ? m.one : 1u) + U;   // [0, 4q)
                         x[p][u + d] = U - V + q2;  // [0, 4q)
                     } else {
                         const uint32_t U = x[p][u], V = shoup_mul(x[p][u + d], W.x, W.y, q);
@@ -219,8 +230,8 @@ struct NttCore {
                 for (int p = 0; p < NP; p++) {
                     const uint32_t U = x[p][u], V = x[p][u + d];
                     if constexpr (LAZY) {
-                        const uint32_t q2 = 2 * q, nq2 = 0u - q2, sum = V * m.one + U;
-                        x[p][u] = min(sum, sum * m.one + nq2);                   // [0, 2q)
+                        const uint32_t q2 = 2 * q, nq2 = 0u - q2, sum = V * ((FMA & kFmaInvSum) ? m.one : 1u) + U;
+                        x[p][u] = min(sum, sum * ((FMA & kFmaInvMin) ? m.one : 1u) + nq2);                   // [0, 2q)
                         x[p][u + d] = shoup_mul_lazy(U - V + q2, W.x, W.y, q);   // [0, 2q)
                     } else {
                         x[p][u] = add_mod(U, V, q);
