@@ -164,34 +164,52 @@ def int_peak_ops():
 
 
 def alu_ops(cfg):
-    """Algorithmic integer operations per evaluation of the two NTT-based
-    kernel classes: {"square": ops, "keyswitch": ops}.
+    """Algorithmic integer operations per evaluation of the NTT-based kernel
+    classes: {"square": ops, "keyswitch": ops, "moddown_rescale": ops}.
 
-    Tensor square of a ciphertext at n limbs: 2 forward and 3 inverse NTTs per
-    limb, 3 products per coefficient.  Key switch of its d2 part (hybrid, digits
-    of at most alpha primes, n + K target primes): ModUp (one product per digit
-    residue, then alpha products per coefficient and prime outside the digit),
-    a forward NTT of every digit in every target prime outside it (inside it,
-    the tensor square's NTT form is reused), two products per digit and target
-    prime with the key, two inverse NTTs per target prime."""
+    From the first square layer on, ciphertexts stay in the NTT domain.  Tensor
+    square of a ciphertext at n limbs: per limb 2 forward NTTs (only on
+    coefficient-form input, the first square layer) and 1 inverse NTT (d2 for
+    ModUp), 4 products per coefficient; the square class also holds the domain
+    changes: a forward NTT of every feature-plaintext limb that meets NTT-domain
+    ciphertexts and the inverse NTT of the outputs.  Key switch of d2 (hybrid,
+    digits of at most alpha primes, n + K target primes): ModUp (one product per
+    digit residue, then alpha products per coefficient and prime outside the
+    digit), a forward NTT of every digit in every target prime outside it
+    (inside it, the tensor square's NTT form is reused), two products per digit
+    and target prime with the key, then two inverse NTTs on each special prime
+    and on the top data prime (with its 4 products folding in the rescale's
+    first step) and a product by N on the other data primes.  ModDown and
+    rescale: per poly and data limb below the top, 3K + 4 products per
+    coefficient and one forward NTT."""
     import math
 
     import workloads
     N, logN, K, a = 1 << cfg["log_n"], cfg["log_n"], cfg["n_special"], cfg["alpha"]
     bf = (N // 2) * logN
     levels, _ = workloads.level_schedule(cfg)
-    sq = ks = 0.0
+    sq = ks = md = 0.0
+    in_ntt = False
     for layer, n in zip(cfg["cipher"], levels):
+        n_out = workloads.cipher_layer_io(layer)[1]
+        if layer["add"] and in_ntt:
+            sq += n_out * n * bf * OPS_BUTTERFLY
         if not layer["square"]:
             continue
-        C = workloads.cipher_layer_io(layer)[1]
-        sq += C * (5 * n * bf * OPS_BUTTERFLY + 3 * n * N * OPS_MULADD)
+        C = n_out
+        sq += C * (n * (1 if in_ntt else 3) * bf * OPS_BUTTERFLY + 4 * n * N * OPS_MULADD)
         digits = [min(a, n - j * a) for j in range(math.ceil(n / a))]
         nb = n + K
         fwd = sum(nb - d for d in digits)
-        mads = sum(digits) + sum(d * (nb - d) for d in digits) + 2 * nb * len(digits)
-        ks += C * ((fwd + 2 * nb) * bf * OPS_BUTTERFLY + mads * N * OPS_MULADD)
-    return {"square": sq, "keyswitch": ks}
+        mads = sum(digits) + sum(d * (nb - d) for d in digits) + 2 * nb * len(digits) + 2 * (n - 1) + 4
+        ks += C * ((fwd + 2 * (K + 1)) * bf * OPS_BUTTERFLY + mads * N * OPS_MULADD)
+        md += C * 2 * (n - 1) * (bf * OPS_BUTTERFLY + (3 * K + 4) * N * OPS_MULADD)
+        in_ntt = True
+    last = cfg["cipher"][-1]
+    if in_ntt:
+        lout = levels[-1] - (1 if last["square"] else 0)
+        sq += workloads.cipher_layer_io(last)[1] * 2 * lout * bf * OPS_BUTTERFLY
+    return {"square": sq, "keyswitch": ks, "moddown_rescale": md}
 
 
 def csrc_hash():

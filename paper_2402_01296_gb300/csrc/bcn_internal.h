@@ -43,6 +43,8 @@ struct PrimeConst {
     uint32_t rn;         // R * N^{-1} mod q: Montgomery form of N^{-1}
     uint32_t rn_shoup;   // Shoup companion of rn
     uint32_t one;        // 1, read at run time: multiply-adds by it stay on the FMA pipe
+    uint32_t nmod;       // N mod q (= N)
+    uint32_t nmod_shoup; // Shoup companion of nmod
     uint64_t barrett;    // floor(2^64 / q)
     uint64_t mac_offset; // a multiple of q >= 2^58 (makes a signed MAC sum non-negative)
 };
@@ -113,6 +115,7 @@ struct bcn_ctx {
 // (one conv position with all its output channels; a whole dense layer).
 struct bcn_layer_plan {
     int type, n_in, n_out, K, level, add, square;
+    int in_ntt;                // the layer's inputs are in the NTT domain (a square layer came before)
     double s_w;
     int n_groups, n_go;        // groups, outputs per group
     int n_distinct_in;         // inputs the layer reads
@@ -160,6 +163,7 @@ struct bcn_model {
     size_t ws_x_bytes;  // one ping-pong activation buffer
     size_t ws_y_bytes;  // MAC output of a square layer
     size_t ws_chunk_bytes;
+    size_t ws_pt_bytes;  // NTT-domain copy of one layer's feature plaintexts
     int out_level;
 };
 

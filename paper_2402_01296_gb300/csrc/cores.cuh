@@ -7,16 +7,18 @@
 
 namespace bcn {
 
+// In-place NTT of limb blockIdx.x of group blockIdx.y (groups `stride` words
+// apart): natural order <-> last-pass layout.
 template <int LOGN, int R>
 __global__ void __launch_bounds__((1 << LOGN) / R) k_ntt_fwd(uint32_t *__restrict__ data, PrimeMap pm,
-                                                            const PrimeConst *__restrict__ pc,
+                                                            size_t stride, const PrimeConst *__restrict__ pc,
                                                             const uint2 *__restrict__ tw) {
     using C = NttCore<LOGN, R>;
     extern __shared__ __align__(16) uint32_t sm[];
     const int limb = blockIdx.x, tid = threadIdx.x;
     const int p = prime_of(pm, limb);
     const uint32_t q = pc[p].q;
-    uint32_t *a = data + (size_t)limb * C::N;
+    uint32_t *a = data + blockIdx.y * stride + (size_t)limb * C::N;
     uint32_t x[R];
     C::load_natural(x, a, tid);
     C::forward(x, sm, tid, q, tw + (size_t)p * C::N);
@@ -25,14 +27,14 @@ __global__ void __launch_bounds__((1 << LOGN) / R) k_ntt_fwd(uint32_t *__restric
 
 template <int LOGN, int R>
 __global__ void __launch_bounds__((1 << LOGN) / R) k_ntt_inv(uint32_t *__restrict__ data, PrimeMap pm,
-                                                            const PrimeConst *__restrict__ pc,
+                                                            size_t stride, const PrimeConst *__restrict__ pc,
                                                             const uint2 *__restrict__ tw) {
     using C = NttCore<LOGN, R>;
     extern __shared__ __align__(16) uint32_t sm[];
     const int limb = blockIdx.x, tid = threadIdx.x;
     const int p = prime_of(pm, limb);
     const PrimeConst P = pc[p];
-    uint32_t *a = data + (size_t)limb * C::N;
+    uint32_t *a = data + blockIdx.y * stride + (size_t)limb * C::N;
     uint32_t x[R];
     C::load_ntt(x, a, tid);
     C::inverse(x, sm, tid, P.q, tw + (size_t)p * C::N, P.ninv, P.ninv_shoup);
@@ -74,108 +76,117 @@ struct CoreOcc {
     static constexpr int MIN_BLOCKS = B > 32 ? 32 : (B < 1 ? 1 : B);
 };
 
-// Square activation, first half: forward NTT of c0 and c1 of one limb,
-// tensor square (c0^2, 2 c0 c1, c1^2) in the NTT domain, inverse NTT of the
-// three products.  Y [C][2][n][N] -> D [C][3][n][N], coefficient form; with
-// D2N != nullptr also c1^2 in the NTT domain (last-pass layout of the NTT) to
-// D2N [C][n][N], which the key-switching kernel reuses on the digit's own prime.
-// The products are formed with R*N^{-1} in place of R, so they carry the
-// inverse transform's N^{-1} already.  grid (n, C): one block per (limb, ct).
-template <int LOGN, int R>
+// Square activation, first half, one block per (limb, ct): the tensor square
+// (c0^2, 2 c0 c1, c1^2) in the NTT domain of the limb's prime.  Y [C][2][n][N]
+// is in coefficient form (natural order; transformed here) or, with IN_NTT, in
+// the NTT domain (the last-pass layout of the transform).  Out: d0 and d1 in
+// the NTT domain (D [C][3][n][N] slots 0 and 1, last-pass layout), d2 in
+// coefficient form (slot 2, the key switch's ModUp input: one inverse NTT)
+// and, with D2N != nullptr, d2 in the NTT domain too (D2N [C][n][N], which the
+// key switch reuses on the digit's own prime).  All outputs canonical.
+// grid (n, C).
+template <int LOGN, int R, bool IN_NTT>
 __global__ void __launch_bounds__((1 << LOGN) / R, CoreOcc<(1 << LOGN) / R>::MIN_BLOCKS)
     k_square_core(const uint32_t *__restrict__ Y, uint32_t *__restrict__ D, uint32_t *__restrict__ D2N, int n,
                   const PrimeConst *__restrict__ pc, const uint2 *__restrict__ twf, const uint2 *__restrict__ twi) {
     using C = NttCore<LOGN, R, true, kFmaSquare>;  // data primes only (q < 2^30): lazy butterflies
     constexpr int N = C::N, T = C::T;
+    constexpr int V = C::NTT_QUADS ? 4 : (C::NTT_PAIRS ? 2 : 1);  // consecutive NTT-domain elements per register run
     extern __shared__ __align__(16) uint32_t sm[];
     const int i = blockIdx.x, ct = blockIdx.y, tid = threadIdx.x;
     const PrimeConst P = pc[i];
     const uint2 *tf = twf + (size_t)i * N, *ti = twi + (size_t)i * N;
-    if constexpr (kDual<LOGN, R>) {
-        // c0 and c1 transformed together (two exchange buffers), then d0 and d1
-        // back together; d2 waits in a thread-private parking area (u*T + tid)
-        uint32_t *s2 = sm + 2 * C::SMEM_WORDS;
-        const ModQ mq(P.q, kFmaOne<LOGN, R> ? P.one : 1u);
-        uint32_t x[2][R];
-        C::load_natural(x[0], Y + (((size_t)ct * 2 + 0) * n + i) * N, tid);
-        C::load_natural(x[1], Y + (((size_t)ct * 2 + 1) * n + i) * N, tid);
-        C::forward_n(x, sm, tid, mq, tf);
-        uint32_t *d2n = D2N != nullptr ? D2N + ((size_t)ct * n + i) * N : nullptr;
-        constexpr int V = C::NTT_QUADS ? 4 : (C::NTT_PAIRS ? 2 : 1);
+    const ModQ mq(P.q, kFmaOne<LOGN, R> ? P.one : 1u);
+    const uint32_t *y0 = Y + (((size_t)ct * 2 + 0) * n + i) * N, *y1 = Y + (((size_t)ct * 2 + 1) * n + i) * N;
+    uint32_t *d0 = D + (((size_t)ct * 3 + 0) * n + i) * N, *d1 = D + (((size_t)ct * 3 + 1) * n + i) * N;
+    uint32_t *d2 = D + (((size_t)ct * 3 + 2) * n + i) * N;
+    uint32_t *d2n = D2N != nullptr ? D2N + ((size_t)ct * n + i) * N : nullptr;
+    uint32_t x[R];  // c1^2 / N in the NTT domain, then d2 in coefficient form
+    // V consecutive NTT-domain elements (registers u0 .. u0+V-1, any residues
+    // below 4q): d0, d1 and d2 stored, c1^2 / N (the inverse NTT's input,
+    // whose N^{-1} this folds in) left in x
+    auto square_run = [&](const uint32_t(&a)[V], const uint32_t(&b)[V], int u0) {
+        uint32_t o0[V], o1[V], o2[V];
+#pragma unroll
+        for (int z = 0; z < V; z++) {
+            const uint32_t aR = shoup_mul(a[z], P.r_mod, P.r_shoup, P.q);
+            const uint32_t bR = shoup_mul(b[z], P.r_mod, P.r_shoup, P.q);
+            const uint32_t ab = mont_mul(aR, b[z], P.q, P.qneg_inv);
+            o0[z] = mont_mul(aR, a[z], P.q, P.qneg_inv);  // c0^2
+            o1[z] = add_mod(ab, ab, P.q);                  // 2 c0 c1
+            o2[z] = mont_mul(bR, b[z], P.q, P.qneg_inv);  // c1^2
+            x[u0 + z] = shoup_mul(o2[z], P.ninv, P.ninv_shoup, P.q);
+        }
+        const int e = C::ntt_elem(u0, tid);
+        if constexpr (V == 4) {
+            *reinterpret_cast<uint4 *>(d0 + e) = make_uint4(o0[0], o0[1], o0[2], o0[3]);
+            *reinterpret_cast<uint4 *>(d1 + e) = make_uint4(o1[0], o1[1], o1[2], o1[3]);
+            if (d2n != nullptr) *reinterpret_cast<uint4 *>(d2n + e) = make_uint4(o2[0], o2[1], o2[2], o2[3]);
+        } else if constexpr (V == 2) {
+            *reinterpret_cast<uint2 *>(d0 + e) = make_uint2(o0[0], o0[1]);
+            *reinterpret_cast<uint2 *>(d1 + e) = make_uint2(o1[0], o1[1]);
+            if (d2n != nullptr) *reinterpret_cast<uint2 *>(d2n + e) = make_uint2(o2[0], o2[1]);
+        } else {
+            d0[e] = o0[0];
+            d1[e] = o1[0];
+            if (d2n != nullptr) d2n[e] = o2[0];
+        }
+    };
+    if constexpr (IN_NTT) {
 #pragma unroll
         for (int u0 = 0; u0 < R; u0 += V) {
-            uint32_t c2[V];  // c1^2, canonical, for the key switch's own-digit term
+            uint32_t a[V], b[V];
+            const int e = C::ntt_elem(u0, tid);
+            if constexpr (V == 4) {
+                *reinterpret_cast<uint4 *>(a) = __ldg(reinterpret_cast<const uint4 *>(y0 + e));
+                *reinterpret_cast<uint4 *>(b) = __ldg(reinterpret_cast<const uint4 *>(y1 + e));
+            } else if constexpr (V == 2) {
+                *reinterpret_cast<uint2 *>(a) = __ldg(reinterpret_cast<const uint2 *>(y0 + e));
+                *reinterpret_cast<uint2 *>(b) = __ldg(reinterpret_cast<const uint2 *>(y1 + e));
+            } else {
+                a[0] = __ldg(y0 + e);
+                b[0] = __ldg(y1 + e);
+            }
+            square_run(a, b, u0);
+        }
+    } else if constexpr (kDual<LOGN, R>) {
+        // c0 and c1 transformed together (two exchange buffers)
+        uint32_t y[2][R];
+        C::load_natural(y[0], y0, tid);
+        C::load_natural(y[1], y1, tid);
+        C::forward_n(y, sm, tid, mq, tf);
+#pragma unroll
+        for (int u0 = 0; u0 < R; u0 += V) {
+            uint32_t a[V], b[V];
 #pragma unroll
             for (int z = 0; z < V; z++) {
-                const int u = u0 + z;
-                const uint32_t a = x[0][u], b = x[1][u];  // [0, 4q)
-                c2[z] = mont_mul(shoup_mul(b, P.r_mod, P.r_shoup, P.q), b, P.q, P.qneg_inv);
-                const uint32_t aRN = shoup_mul(a, P.rn, P.rn_shoup, P.q);
-                const uint32_t bRN = shoup_mul(b, P.rn, P.rn_shoup, P.q);
-                const uint32_t ab = mont_mul(aRN, b, P.q, P.qneg_inv);
-                x[0][u] = mont_mul(aRN, a, P.q, P.qneg_inv);  // c0^2 / N
-                x[1][u] = add_mod(ab, ab, P.q);                // 2 c0 c1 / N
-                s2[u * T + tid] = mont_mul(bRN, b, P.q, P.qneg_inv);  // c1^2 / N
+                a[z] = y[0][u0 + z];
+                b[z] = y[1][u0 + z];
             }
-            if (d2n != nullptr) {
-                const int e = C::ntt_elem(u0, tid);
-                if constexpr (V == 4)
-                    *reinterpret_cast<uint4 *>(d2n + e) = make_uint4(c2[0], c2[1], c2[2], c2[3]);
-                else if constexpr (V == 2)
-                    *reinterpret_cast<uint2 *>(d2n + e) = make_uint2(c2[0], c2[1]);
-                else
-                    d2n[e] = c2[0];
+            square_run(a, b, u0);
+        }
+    } else {
+        // c0 transformed and parked in a thread-private area (u*T + tid), then c1
+        uint32_t *s1 = sm + C::SMEM_WORDS;
+        C::load_natural(x, y0, tid);
+        C::forward(x, sm, tid, mq, tf);
+#pragma unroll
+        for (int u = 0; u < R; u++) s1[u * T + tid] = x[u];
+        C::load_natural(x, y1, tid);
+        C::forward(x, sm, tid, mq, tf);
+#pragma unroll
+        for (int u0 = 0; u0 < R; u0 += V) {
+            uint32_t a[V], b[V];
+#pragma unroll
+            for (int z = 0; z < V; z++) {
+                a[z] = s1[(u0 + z) * T + tid];
+                b[z] = x[u0 + z];
             }
+            square_run(a, b, u0);
         }
-        C::inverse_unscaled_n(x, sm, tid, mq, ti);
-        C::store_natural(x[0], D + (((size_t)ct * 3 + 0) * n + i) * N, tid);
-        C::store_natural(x[1], D + (((size_t)ct * 3 + 1) * n + i) * N, tid);
-#pragma unroll
-        for (int u = 0; u < R; u++) x[0][u] = s2[u * T + tid];
-        C::inverse_unscaled(x[0], sm, tid, mq, ti);
-        C::store_natural(x[0], D + (((size_t)ct * 3 + 2) * n + i) * N, tid);
-        return;
     }
-    // exchange buffer, then two thread-private parking areas (slot u*T + tid)
-    uint32_t *s1 = sm + C::SMEM_WORDS, *s2 = s1 + N;
-    uint32_t x[R];
-    // c0 -> NTT, parked in s1
-    C::load_natural(x, Y + (((size_t)ct * 2 + 0) * n + i) * N, tid);
-    C::forward(x, sm, tid, ModQ(P.q, kFmaOne<LOGN, R> ? P.one : 1u), tf);
-#pragma unroll
-    for (int u = 0; u < R; u++) s1[u * T + tid] = x[u];
-    // c1 -> NTT; c0^2/N in registers, 2 c0 c1/N in s1, c1^2/N in s2 (inputs in [0, 4q))
-    C::load_natural(x, Y + (((size_t)ct * 2 + 1) * n + i) * N, tid);
-    C::forward(x, sm, tid, ModQ(P.q, kFmaOne<LOGN, R> ? P.one : 1u), tf);
-    if (D2N != nullptr) {
-        uint32_t y[R];
-#pragma unroll
-        for (int u = 0; u < R; u++) {
-            const uint32_t bR = shoup_mul(x[u], P.r_mod, P.r_shoup, P.q);
-            y[u] = mont_mul(bR, x[u], P.q, P.qneg_inv);  // c1^2, canonical
-        }
-        C::store_ntt(y, D2N + ((size_t)ct * n + i) * N, tid);
-    }
-#pragma unroll
-    for (int u = 0; u < R; u++) {
-        const uint32_t a = s1[u * T + tid], b = x[u];
-        const uint32_t aRN = shoup_mul(a, P.rn, P.rn_shoup, P.q);
-        const uint32_t bRN = shoup_mul(b, P.rn, P.rn_shoup, P.q);
-        const uint32_t ab = mont_mul(aRN, b, P.q, P.qneg_inv);
-        s1[u * T + tid] = add_mod(ab, ab, P.q);
-        s2[u * T + tid] = mont_mul(bRN, b, P.q, P.qneg_inv);
-        x[u] = mont_mul(aRN, a, P.q, P.qneg_inv);
-    }
-    C::inverse_unscaled(x, sm, tid, ModQ(P.q, kFmaOne<LOGN, R> ? P.one : 1u), ti);
-    C::store_natural(x, D + (((size_t)ct * 3 + 0) * n + i) * N, tid);
-#pragma unroll
-    for (int u = 0; u < R; u++) x[u] = s1[u * T + tid];
-    C::inverse_unscaled(x, sm, tid, ModQ(P.q, kFmaOne<LOGN, R> ? P.one : 1u), ti);
-    C::store_natural(x, D + (((size_t)ct * 3 + 1) * n + i) * N, tid);
-#pragma unroll
-    for (int u = 0; u < R; u++) x[u] = s2[u * T + tid];
-    C::inverse_unscaled(x, sm, tid, ModQ(P.q, kFmaOne<LOGN, R> ? P.one : 1u), ti);
-    C::store_natural(x, D + (((size_t)ct * 3 + 2) * n + i) * N, tid);
+    C::inverse_unscaled(x, sm, tid, mq, ti);
+    C::store_natural(x, d2, tid);
 }
 
 // Key switching of d2, fused per (target prime t, ciphertext): for every
@@ -186,12 +197,16 @@ __global__ void __launch_bounds__((1 << LOGN) / R, CoreOcc<(1 << LOGN) / R>::MIN
 // which for one-prime digits is d mod t, less q_j mod t when d > (q_j-1)/2),
 // forward NTT, and the product with evk_j (prepared as k*R*N^{-1}, so one
 // Montgomery product gives k*x/N) accumulated for both key halves; then the
-// inverse NTT of the two sums.  No extended-basis limb is stored.
-// D [C][3][n][N] (d2 in coefficient form) -> ACC [C][2][n+K][N] (coefficient form).
+// inverse NTT of the two sums -- or, with ntt_out, on the data primes below
+// the top one the sums times N left in the NTT domain (last-pass layout), and
+// on the top prime the rescale's INTT(A_top P^{-1} + D_top).  No extended-basis
+// limb is stored.  D [C][3][n][N] (d2 in coefficient form; with ntt_out, d0
+// and d1 in the NTT domain) -> ACC [C][2][n+K][N] (coefficient form; with
+// ntt_out the first n-1 limbs of each poly in the NTT domain).
 template <int LOGN, int R, bool LAZY>
 __device__ __forceinline__ void ks_core_body(const uint32_t *__restrict__ D, const uint32_t *__restrict__ D2N,
                                              const uint32_t *__restrict__ evk, uint32_t *__restrict__ acc_out,
-                                             int n, const KsDev &ks, const PrimeConst *__restrict__ pc,
+                                             int n, int ntt_out, const KsDev &ks, const PrimeConst *__restrict__ pc,
                                              const uint2 *__restrict__ twf, const uint2 *__restrict__ twi) {
     using C = NttCore<LOGN, R, LAZY, kFmaKs>;
     constexpr int N = C::N, T = C::T;
@@ -389,6 +404,34 @@ __device__ __forceinline__ void ks_core_body(const uint32_t *__restrict__ D, con
         }
         key_product(x, j);
     }
+    // with ntt_out, the data primes' sums below the top prime stay in the NTT
+    // domain: times N (the key carries N^{-1} for the inverse transform),
+    // canonical, last-pass layout.  On the top prime q_{n-1} the block folds in
+    // the rescale's first step: INTT(A_top P^{-1} + D_top) in coefficient form,
+    // i.e. the unscaled inverse of s P^{-1} + D_top N^{-1} (D_top: d0 or d1 of
+    // the square, NTT domain), stored in place of the sums.
+    const bool to_ntt = ntt_out && t < n - 1, top_fold = ntt_out && t == n - 1;
+    // s P^{-1} + D_top N^{-1} for poly b, registers u .. u+V-1 (NTT domain)
+    auto fold = [&](uint32_t(&y)[R], int b) {
+        const uint2 pi = ks.pinv[t];
+        const uint32_t *dt = D + (((size_t)ct * 3 + b) * n + t) * N;
+        constexpr int V = C::NTT_QUADS ? 4 : (C::NTT_PAIRS ? 2 : 1);
+#pragma unroll
+        for (int u0 = 0; u0 < R; u0 += V) {
+            uint32_t dv[V];
+            const int e = C::ntt_elem(u0, tid);
+            if constexpr (V == 4)
+                *reinterpret_cast<uint4 *>(dv) = __ldg(reinterpret_cast<const uint4 *>(dt + e));
+            else if constexpr (V == 2)
+                *reinterpret_cast<uint2 *>(dv) = __ldg(reinterpret_cast<const uint2 *>(dt + e));
+            else
+                dv[0] = __ldg(dt + e);
+#pragma unroll
+            for (int z = 0; z < V; z++)
+                y[u0 + z] = add_mod(shoup_mul(y[u0 + z], pi.x, pi.y, P.q),
+                                    shoup_mul(dv[z], P.ninv, P.ninv_shoup, P.q), P.q);
+        }
+    };
     if constexpr (kDual<LOGN, R>) {
         uint32_t y[2][R];
 #pragma unroll
@@ -396,19 +439,41 @@ __device__ __forceinline__ void ks_core_body(const uint32_t *__restrict__ D, con
             y[0][u] = s0[u * T + tid];
             y[1][u] = s1[u * T + tid];
         }
+        if (top_fold) {
+            fold(y[0], 0);
+            fold(y[1], 1);
+        }
+        if (to_ntt) {
+#pragma unroll
+            for (int u = 0; u < R; u++) {
+                y[0][u] = shoup_mul(y[0][u], P.nmod, P.nmod_shoup, P.q);
+                y[1][u] = shoup_mul(y[1][u], P.nmod, P.nmod_shoup, P.q);
+            }
+            C::store_ntt(y[0], acc_out + (((size_t)ct * 2 + 0) * nb + t) * N, tid);
+            C::store_ntt(y[1], acc_out + (((size_t)ct * 2 + 1) * nb + t) * N, tid);
+            return;
+        }
         C::inverse_unscaled_n(y, sm, tid, ModQ(P.q, kFmaOne<LOGN, R> ? P.one : 1u), ti);
         C::store_natural(y[0], acc_out + (((size_t)ct * 2 + 0) * nb + t) * N, tid);
         C::store_natural(y[1], acc_out + (((size_t)ct * 2 + 1) * nb + t) * N, tid);
         return;
     }
 #pragma unroll
-    for (int u = 0; u < R; u++) x[u] = s0[u * T + tid];
-    C::inverse_unscaled(x, sm, tid, ModQ(P.q, kFmaOne<LOGN, R> ? P.one : 1u), ti);
-    C::store_natural(x, acc_out + (((size_t)ct * 2 + 0) * nb + t) * N, tid);
+    for (int b = 0; b < 2; b++) {
+        const uint32_t *sb = b == 0 ? s0 : s1;
+        uint32_t *dst = acc_out + (((size_t)ct * 2 + b) * nb + t) * N;
 #pragma unroll
-    for (int u = 0; u < R; u++) x[u] = s1[u * T + tid];
-    C::inverse_unscaled(x, sm, tid, ModQ(P.q, kFmaOne<LOGN, R> ? P.one : 1u), ti);
-    C::store_natural(x, acc_out + (((size_t)ct * 2 + 1) * nb + t) * N, tid);
+        for (int u = 0; u < R; u++) x[u] = sb[u * T + tid];
+        if (top_fold) fold(x, b);
+        if (to_ntt) {
+#pragma unroll
+            for (int u = 0; u < R; u++) x[u] = shoup_mul(x[u], P.nmod, P.nmod_shoup, P.q);
+            C::store_ntt(x, dst, tid);
+        } else {
+            C::inverse_unscaled(x, sm, tid, ModQ(P.q, kFmaOne<LOGN, R> ? P.one : 1u), ti);
+            C::store_natural(x, dst, tid);
+        }
+    }
 }
 
 // grid (n+K, C); lazy butterflies for the data primes (< 2^30), strict ones for
@@ -416,14 +481,139 @@ __device__ __forceinline__ void ks_core_body(const uint32_t *__restrict__ D, con
 template <int LOGN, int R>
 __global__ void __launch_bounds__((1 << LOGN) / R, CoreOcc<(1 << LOGN) / R>::MIN_BLOCKS)
     k_ks_core(const uint32_t *__restrict__ D, const uint32_t *__restrict__ D2N, const uint32_t *__restrict__ evk,
-              uint32_t *__restrict__ acc_out, int n, KsDev ks, const PrimeConst *__restrict__ pc,
+              uint32_t *__restrict__ acc_out, int n, int ntt_out, KsDev ks, const PrimeConst *__restrict__ pc,
               const uint2 *__restrict__ twf, const uint2 *__restrict__ twi) {
     const int t = blockIdx.x;
     const int pt = t < n ? t : ks.L + (t - n);
     if (pc[pt].q < (1u << 30))
-        ks_core_body<LOGN, R, true>(D, D2N, evk, acc_out, n, ks, pc, twf, twi);
+        ks_core_body<LOGN, R, true>(D, D2N, evk, acc_out, n, ntt_out, ks, pc, twf, twi);
     else
-        ks_core_body<LOGN, R, false>(D, D2N, evk, acc_out, n, ks, pc, twf, twi);
+        ks_core_body<LOGN, R, false>(D, D2N, evk, acc_out, n, ntt_out, ks, pc, twf, twi);
+}
+
+// ModDown by P and rescale by the top prime q_top = q_{n-1} in the NTT domain
+// (App. A of the paper: relinearisation ends with the division by P, the
+// square activation with the rescale; the two roundings in sequence, as the
+// coefficient-form definition states them):
+//   c_i   = (a_i - conv_i(a_P)) P^{-1} + d_i        ModDown, every limb i < n
+//   out_i = (c_i - [c_top]) q_top^{-1}                rescale, i < n - 1
+// where conv_i(a_P) = sum_m r_m Phat_m - #{m : r_m > (p_m - 1)/2} P (mod q_i),
+// r_m = [a_{P,m} Phat_m^{-1}]_{p_m}, is the centred fast basis conversion of the
+// special-prime limbs (coefficient form) and [c_top] the centred lift of the
+// top limb.  The NTT is linear, so with A_i, D_i the NTT-domain a_i, d_i:
+//   c_top = INTT(A_top P^{-1} + D_top) - conv_top(a_P) P^{-1}
+//   out_i = (A_i P^{-1} + D_i - NTT(conv_i(a_P) P^{-1} + [c_top])) q_top^{-1}
+// The inverse NTT of c_top is the key switch's (its block on the top prime
+// forms INTT(A_top P^{-1} + D_top)); what is left is one forward NTT per limb
+// and poly.  The results equal the NTT of the coefficient-form ModDown and
+// rescale, residue for residue.
+
+// out_i of polys b0 .. b0+NP-1 of ciphertext ct, i < n - 1 (NP = 2: both
+// polys transformed in lockstep).  D [C][3][n][N] (slots 0, 1: d0, d1 in the
+// NTT domain), ACC [C][2][n+K][N] (limbs i < n-1: A_i in the NTT domain; limb
+// n-1: INTT(A_top P^{-1} + D_top), coefficient form, from the key switch;
+// limbs n..n+K-1: a_P, coefficient form) -> OUT [C][2][n-1][N] (NTT domain,
+// last-pass layout, canonical).  grid (n - 1, 2 / NP, C)
+#ifndef BCN_MD_REGS
+#define BCN_MD_REGS 64
+#endif
+#ifndef BCN_MD_R14
+#define BCN_MD_R14 0
+#endif
+template <int T>
+struct MdOcc {  // one-poly blocks: 64 registers a thread
+    static constexpr int B = 65536 / (T * BCN_MD_REGS);
+    static constexpr int MIN_BLOCKS = B > 32 ? 32 : (B < 1 ? 1 : B);
+};
+template <int LOGN, int R, int NP, int K>
+__global__ void __launch_bounds__((1 << LOGN) / R, NP == 1 ? MdOcc<(1 << LOGN) / R>::MIN_BLOCKS
+                                                           : CoreOcc<(1 << LOGN) / R>::MIN_BLOCKS)
+    k_md_limb(const uint32_t *__restrict__ D, const uint32_t *__restrict__ acc, uint32_t *__restrict__ out, int n,
+              KsDev ks, const PrimeConst *__restrict__ pc, const uint2 *__restrict__ twf) {
+    using C = NttCore<LOGN, R, true, kFmaSquare>;  // data primes: lazy butterflies
+    constexpr int N = C::N;
+    constexpr int V = C::NTT_QUADS ? 4 : (C::NTT_PAIRS ? 2 : 1);
+    extern __shared__ __align__(16) uint32_t sm[];
+    const int i = blockIdx.x, b0 = blockIdx.y * NP, ct = blockIdx.z, tid = threadIdx.x;
+    const int nb = n + ks.K, top = n - 1;
+    const PrimeConst P = pc[i];
+    const uint32_t qtop = pc[top].q, htop = pc[top].half, tmq = P.q - qtop;  // q_i > q_top
+    const uint2 pi = ks.pinv[i], pit = ks.pinv[top], qti = ks.qtop_inv[(size_t)top * ks.L + i];
+    const uint32_t pmod_i = ks.pmod[i], pmod_t = ks.pmod[top];
+    const uint32_t *row[NP];
+#pragma unroll
+    for (int p = 0; p < NP; p++) row[p] = acc + ((size_t)ct * 2 + b0 + p) * nb * N;
+    // coefficient form: conv_i(a_P) P^{-1} + [c_top] (mod q_i), with
+    // c_top = acc_top - conv_top(a_P) P^{-1} (mod q_top)
+    uint32_t x[NP][R];
+#pragma unroll
+    for (int u = 0; u < R; u++) {
+        const int e = C::nat_elem(u, tid);
+#pragma unroll
+        for (int p = 0; p < NP; p++) {
+            // K (the number of special primes) is a template parameter and the
+            // correction below a chain of selects: no branch, so the loads of
+            // all R elements can be issued together
+            uint32_t conv_i = 0, conv_t = 0;
+            int cnt = 0;
+#pragma unroll
+            for (int m = 0; m < K; m++) {
+                const uint32_t pq = pc[ks.L + m].q, ph2 = pc[ks.L + m].half;
+                const uint2 hi = ks.phat_inv[m], phi = ks.phat[(size_t)m * ks.L + i],
+                            pht = ks.phat[(size_t)m * ks.L + top];
+                const uint32_t r = shoup_mul(__ldg(row[p] + (size_t)(n + m) * N + e), hi.x, hi.y, pq);
+                cnt += r > ph2;
+                conv_i = add_mod(conv_i, shoup_mul(r, phi.x, phi.y, P.q), P.q);
+                conv_t = add_mod(conv_t, shoup_mul(r, pht.x, pht.y, qtop), qtop);
+            }
+#pragma unroll
+            for (int c = 0; c < K; c++) {
+                const uint32_t si = sub_mod(conv_i, pmod_i, P.q), st = sub_mod(conv_t, pmod_t, qtop);
+                conv_i = c < cnt ? si : conv_i;
+                conv_t = c < cnt ? st : conv_t;
+            }
+            const uint32_t y =
+                sub_mod(__ldg(row[p] + (size_t)top * N + e), shoup_mul(conv_t, pit.x, pit.y, qtop), qtop);
+            const uint32_t lift = y > htop ? y + tmq : y;
+            x[p][u] = add_mod(shoup_mul(conv_i, pi.x, pi.y, P.q), lift, P.q);
+        }
+    }
+    C::template forward_n<NP>(x, sm, tid, ModQ(P.q, kFmaOne<LOGN, R> ? P.one : 1u), twf + (size_t)i * N);  // [0, 4q)
+    const uint32_t q2 = 2 * P.q;
+#pragma unroll
+    for (int p = 0; p < NP; p++) {
+        const uint32_t *A = row[p] + (size_t)i * N;
+        const uint32_t *Di = D + (((size_t)ct * 3 + b0 + p) * n + i) * N;
+        uint32_t *o = out + (((size_t)ct * 2 + b0 + p) * (n - 1) + i) * N;
+#pragma unroll
+        for (int u0 = 0; u0 < R; u0 += V) {
+            const int e = C::ntt_elem(u0, tid);
+            uint32_t av[V], dv[V], r[V];
+            if constexpr (V == 4) {
+                *reinterpret_cast<uint4 *>(av) = __ldg(reinterpret_cast<const uint4 *>(A + e));
+                *reinterpret_cast<uint4 *>(dv) = __ldg(reinterpret_cast<const uint4 *>(Di + e));
+            } else if constexpr (V == 2) {
+                *reinterpret_cast<uint2 *>(av) = __ldg(reinterpret_cast<const uint2 *>(A + e));
+                *reinterpret_cast<uint2 *>(dv) = __ldg(reinterpret_cast<const uint2 *>(Di + e));
+            } else {
+                av[0] = __ldg(A + e);
+                dv[0] = __ldg(Di + e);
+            }
+#pragma unroll
+            for (int z = 0; z < V; z++) {
+                uint32_t f = x[p][u0 + z] >= q2 ? x[p][u0 + z] - q2 : x[p][u0 + z];
+                f = f >= P.q ? f - P.q : f;
+                const uint32_t c = add_mod(shoup_mul(av[z], pi.x, pi.y, P.q), dv[z], P.q);
+                r[z] = shoup_mul(sub_mod(c, f, P.q), qti.x, qti.y, P.q);
+            }
+            if constexpr (V == 4)
+                *reinterpret_cast<uint4 *>(o + e) = make_uint4(r[0], r[1], r[2], r[3]);
+            else if constexpr (V == 2)
+                *reinterpret_cast<uint2 *>(o + e) = make_uint2(r[0], r[1]);
+            else
+                o[e] = r[0];
+        }
+    }
 }
 
 // R residues per thread for the NTT and square kernels, RKS for the key switch
@@ -433,50 +623,84 @@ struct CoreImpl {
     using CoreKs = NttCore<LOGN, RKS>;
     static constexpr size_t SMEM = (size_t)Core::SMEM_WORDS * 4;            // NTT alone
     // NTT alone; + two parking areas (or a second exchange buffer and one)
-    static constexpr size_t SMEM3 =
-        ((size_t)(kDual<LOGN, R> ? 2 * Core::SMEM_WORDS + Core::N : Core::SMEM_WORDS + 2 * Core::N)) * 4;
+    // square kernel, coefficient input: two exchange buffers, or one and a parking area
+    static constexpr size_t SMEM3 = ((size_t)(kDual<LOGN, R> ? 2 : 1) * Core::SMEM_WORDS + (kDual<LOGN, R> ? 0 : Core::N)) * 4;
+    // square kernel, NTT-domain input: the inverse transform of d2 alone
+    static constexpr size_t SMEM_SQ_NTT = SMEM;
+    // ModDown/rescale: the square kernel's block shape up to N = 8192, else
+    // the key switch's
+    // (one poly per block measured faster than two in lockstep: the kernel's
+    // element-wise prologue wants the occupancy of 64-register blocks)
+    static constexpr int RMD = kDual<LOGN, R> ? R : (BCN_MD_R14 > 0 ? BCN_MD_R14 : RKS);
+    static constexpr int MD_NP = 1;
+    using CoreMd = NttCore<LOGN, RMD>;
+    static constexpr size_t SMEM_MD = (size_t)MD_NP * CoreMd::SMEM_WORDS * 4;
     // key switch: exchange buffer(s) and the two running sums
     static constexpr size_t SMEM_KS = ((size_t)(kDual<LOGN, RKS> ? 2 : 1) * CoreKs::SMEM_WORDS + 2 * CoreKs::N) * 4;
 
-    static bcn_status ntt(const bcn_ctx *c, uint32_t *data, size_t n_limbs, PrimeMap pm, bool inverse,
-                          cudaStream_t st) {
+    static bcn_status ntt(const bcn_ctx *c, uint32_t *data, size_t n_limbs, size_t n_groups, size_t stride,
+                          PrimeMap pm, bool inverse, cudaStream_t st) {
+        if (n_limbs == 0 || n_groups == 0) return BCN_OK;
+        if (n_limbs > 0x7FFFFFFFull || n_groups > 65535) return fail(BCN_E_INVAL, "NTT launch too large");
+        const dim3 grid((unsigned)n_limbs, (unsigned)n_groups);
         if (inverse)
-            k_ntt_inv<LOGN, R><<<(unsigned)n_limbs, Core::T, SMEM, st>>>(data, pm, c->d_pc, c->d_tw_inv);
+            k_ntt_inv<LOGN, R><<<grid, Core::T, SMEM, st>>>(data, pm, stride, c->d_pc, c->d_tw_inv);
         else
-            k_ntt_fwd<LOGN, R><<<(unsigned)n_limbs, Core::T, SMEM, st>>>(data, pm, c->d_pc, c->d_tw_fwd);
+            k_ntt_fwd<LOGN, R><<<grid, Core::T, SMEM, st>>>(data, pm, stride, c->d_pc, c->d_tw_fwd);
         return check_launch("NTT");
     }
     static bcn_status square(const bcn_ctx *c, int n, const uint32_t *Y, uint32_t *D, uint32_t *D2N, int C,
-                             cudaStream_t st) {
-        k_square_core<LOGN, R><<<dim3(n, C), Core::T, SMEM3, st>>>(Y, D, D2N, n, c->d_pc, c->d_tw_fwd,
-                                                                   c->d_tw_inv);
+                             bool in_ntt, cudaStream_t st) {
+        if (in_ntt)
+            k_square_core<LOGN, R, true><<<dim3(n, C), Core::T, SMEM_SQ_NTT, st>>>(Y, D, D2N, n, c->d_pc, c->d_tw_fwd,
+                                                                                c->d_tw_inv);
+        else
+            k_square_core<LOGN, R, false><<<dim3(n, C), Core::T, SMEM3, st>>>(Y, D, D2N, n, c->d_pc, c->d_tw_fwd,
+                                                                           c->d_tw_inv);
         return check_launch("k_square_core");
     }
     static bcn_status keyswitch(const bcn_ctx *c, int n, const uint32_t *D, const uint32_t *D2N,
-                                const uint32_t *evk, uint32_t *acc, int C, cudaStream_t st) {
-        k_ks_core<LOGN, RKS><<<dim3(n + c->K, C), CoreKs::T, SMEM_KS, st>>>(D, D2N, evk, acc, n, ks_dev(c), c->d_pc,
-                                                                     c->d_tw_fwd, c->d_tw_inv);
+                                const uint32_t *evk, uint32_t *acc, int C, bool ntt_out, cudaStream_t st) {
+        k_ks_core<LOGN, RKS><<<dim3(n + c->K, C), CoreKs::T, SMEM_KS, st>>>(
+            D, D2N, evk, acc, n, ntt_out ? 1 : 0, ks_dev(c), c->d_pc, c->d_tw_fwd, c->d_tw_inv);
         return check_launch("k_ks_core");
     }
+    static bcn_status moddown_rescale(const bcn_ctx *c, int n, const uint32_t *D, const uint32_t *acc,
+                                      uint32_t *out, int C, cudaStream_t st) {
+        const dim3 grid(n - 1, 2 / MD_NP, C);
+        const KsDev ks = ks_dev(c);
+        switch (c->K) {
+        case 1: k_md_limb<LOGN, RMD, MD_NP, 1><<<grid, CoreMd::T, SMEM_MD, st>>>(D, acc, out, n, ks, c->d_pc, c->d_tw_fwd); break;
+        case 2: k_md_limb<LOGN, RMD, MD_NP, 2><<<grid, CoreMd::T, SMEM_MD, st>>>(D, acc, out, n, ks, c->d_pc, c->d_tw_fwd); break;
+        case 3: k_md_limb<LOGN, RMD, MD_NP, 3><<<grid, CoreMd::T, SMEM_MD, st>>>(D, acc, out, n, ks, c->d_pc, c->d_tw_fwd); break;
+        case 4: k_md_limb<LOGN, RMD, MD_NP, 4><<<grid, CoreMd::T, SMEM_MD, st>>>(D, acc, out, n, ks, c->d_pc, c->d_tw_fwd); break;
+        default: return fail(BCN_E_INVAL, "ModDown: 1 to 4 special primes");
+        }
+        return check_launch("k_md_limb");
+    }
     static bcn_status setup() {
-        const int smem = (int)SMEM, smem3 = (int)SMEM3, smem_ks = (int)SMEM_KS;
-        if (cudaFuncSetAttribute(k_ntt_fwd<LOGN, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
-                cudaSuccess ||
-            cudaFuncSetAttribute(k_ntt_inv<LOGN, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
-                cudaSuccess ||
-            cudaFuncSetAttribute(k_square_core<LOGN, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem3) !=
-                cudaSuccess ||
-            cudaFuncSetAttribute(k_ks_core<LOGN, RKS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_ks) !=
-                cudaSuccess ||
-            cudaFuncSetAttribute(k_square_core<LOGN, R>, cudaFuncAttributePreferredSharedMemoryCarveout, 100) !=
-                cudaSuccess ||
-            cudaFuncSetAttribute(k_ks_core<LOGN, RKS>, cudaFuncAttributePreferredSharedMemoryCarveout, 100) !=
-                cudaSuccess)
+        const int smem = (int)SMEM, smem3 = (int)SMEM3, smem_sq = (int)SMEM_SQ_NTT, smem_ks = (int)SMEM_KS;
+        auto big = [](const void *k, int bytes) {
+            return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess;
+        };
+        auto carve = [](const void *k) {
+            return cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100) == cudaSuccess;
+        };
+        if (!big((const void *)k_ntt_fwd<LOGN, R>, smem) || !big((const void *)k_ntt_inv<LOGN, R>, smem) ||
+            !big((const void *)k_square_core<LOGN, R, false>, smem3) ||
+            !big((const void *)k_square_core<LOGN, R, true>, smem_sq) ||
+            !big((const void *)k_ks_core<LOGN, RKS>, smem_ks) || !big((const void *)k_md_limb<LOGN, RMD, MD_NP, 1>, (int)SMEM_MD) ||
+            !big((const void *)k_md_limb<LOGN, RMD, MD_NP, 2>, (int)SMEM_MD) ||
+            !big((const void *)k_md_limb<LOGN, RMD, MD_NP, 3>, (int)SMEM_MD) ||
+            !big((const void *)k_md_limb<LOGN, RMD, MD_NP, 4>, (int)SMEM_MD) ||
+            !carve((const void *)k_square_core<LOGN, R, false>) || !carve((const void *)k_square_core<LOGN, R, true>) ||
+            !carve((const void *)k_ks_core<LOGN, RKS>) || !carve((const void *)k_md_limb<LOGN, RMD, MD_NP, 1>) ||
+            !carve((const void *)k_md_limb<LOGN, RMD, MD_NP, 2>))
             return fail(BCN_E_CUDA, "cudaFuncSetAttribute failed for the NTT-based kernels");
         return BCN_OK;
     }
     static const CoreFns *fns() {
-        static const CoreFns f = {&ntt, &square, &keyswitch, &setup};
+        static const CoreFns f = {&ntt, &square, &keyswitch, &moddown_rescale, &setup};
         return &f;
     }
 };

@@ -214,6 +214,8 @@ bcn_status bcn_ctx_create(const bcn_params *p, int device, bcn_ctx **out) {
         pc.rn = (uint32_t)mulmod64(pc.r_mod, pc.ninv, q);
         pc.rn_shoup = shoup_companion(pc.rn, pc.q);
         pc.one = 1;
+        pc.nmod = (uint32_t)((uint64_t)N % q);
+        pc.nmod_shoup = shoup_companion(pc.nmod, pc.q);
         pc.barrett = (uint64_t)(((unsigned __int128)1 << 64) / q);
         pc.mac_offset = ((1ull << 58) / q + 1) * q;
     }

@@ -55,15 +55,24 @@ inline KsDev ks_dev(const bcn_ctx *c) {
 // The NTT-based kernels of one ring degree (template instances live in
 // cores_*.cu so they compile in parallel).
 struct CoreFns {
-    // in-place NTT of n_limbs limbs; limb l uses prime prime_of(pm, l)
-    bcn_status (*ntt)(const bcn_ctx *, uint32_t *data, size_t n_limbs, PrimeMap pm, bool inverse, cudaStream_t);
-    // Y [C][2][n][N] -> D [C][3][n][N] (tensor square, coefficient form) and, if
-    // D2N is not null, d2 in the NTT domain [C][n][N]
-    bcn_status (*square)(const bcn_ctx *, int n, const uint32_t *Y, uint32_t *D, uint32_t *D2N, int C,
+    // in-place NTT of n_limbs limbs in each of n_groups groups `stride` words
+    // apart; limb l uses prime prime_of(pm, l).  Forward: natural order ->
+    // last-pass layout; inverse: back.
+    bcn_status (*ntt)(const bcn_ctx *, uint32_t *data, size_t n_limbs, size_t n_groups, size_t stride, PrimeMap pm,
+                      bool inverse, cudaStream_t);
+    // Y [C][2][n][N] (coefficient form, or NTT domain when in_ntt) -> D [C][3][n][N]:
+    // d0, d1 in the NTT domain, d2 in coefficient form; if D2N is not null, d2
+    // in the NTT domain [C][n][N] too
+    bcn_status (*square)(const bcn_ctx *, int n, const uint32_t *Y, uint32_t *D, uint32_t *D2N, int C, bool in_ntt,
                          cudaStream_t);
-    // D (d2; D2N optional) -> ACC [C][2][n+K][N] (key-switching sums, coefficient form)
+    // D (d2; D2N optional) -> ACC [C][2][n+K][N] (key-switching sums, coefficient
+    // form; with ntt_out the data limbs in the NTT domain)
     bcn_status (*keyswitch)(const bcn_ctx *, int n, const uint32_t *D, const uint32_t *D2N, const uint32_t *evk,
-                            uint32_t *acc, int C, cudaStream_t);
+                            uint32_t *acc, int C, bool ntt_out, cudaStream_t);
+    // D (NTT-domain d0, d1) and ACC (the key switch's output with ntt_out) ->
+    // OUT [C][2][n-1][N] (ModDown by P, add, rescale by q_{n-1}; NTT domain)
+    bcn_status (*moddown_rescale)(const bcn_ctx *, int n, const uint32_t *D, const uint32_t *acc, uint32_t *out,
+                                  int C, cudaStream_t);
     bcn_status (*setup)();
 };
 const CoreFns *core_fns(int logN);  // nullptr if unsupported
@@ -73,16 +82,17 @@ const CoreFns *core_fns_13();
 const CoreFns *core_fns_14();
 
 // square + relinearise + rescale of C ciphertexts Y [C][2][n][N] -> out [C][2][n-1][N],
-// intermediates in d [C][3][n][N] and acc [C][2][n+K][N]
+// both in coefficient form, intermediates in d [C][3][n][N] and acc [C][2][n+K][N]
 bcn_status square_relin_rescale_chunk(const bcn_ctx *c, int n, const uint32_t *evk, const uint32_t *Y, uint32_t *d,
                                       uint32_t *acc, int C, uint32_t *out, cudaStream_t st);
-// the same with d2 also kept in the NTT domain in d2n [C][n][N] (saves one
-// forward NTT per key-switching target)
-bcn_status square_relin_rescale_chunk2(const bcn_ctx *c, int n, const uint32_t *evk, const uint32_t *Y, uint32_t *d,
-                                       uint32_t *d2n, uint32_t *acc, int C, uint32_t *out, cudaStream_t st);
 
+// in-place NTT of n_limbs limbs (limb l with prime prime_of(pm, l)); forward:
+// natural order -> last-pass layout, inverse: back.  The strided form does it
+// for n_groups groups `stride` words apart.
 bcn_status launch_ntt(const bcn_ctx *c, uint32_t *data, size_t n_limbs, const PrimeMap &pm, bool inverse,
                       cudaStream_t st);
+bcn_status launch_ntt_strided(const bcn_ctx *c, uint32_t *data, size_t n_limbs, size_t n_groups, size_t stride,
+                              const PrimeMap &pm, bool inverse, cudaStream_t st);
 
 // key-switching chunk of the op entry points (eval.cu): ciphertexts per chunk
 // at level n for n_ct ciphertexts, and the chunk's buffers in a workspace of

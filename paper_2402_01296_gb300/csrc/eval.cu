@@ -9,6 +9,9 @@
 //               ModDown by P
 //   5. rescale  divide by the last live prime
 // Steps 3-5 run over chunks of output ciphertexts whose intermediates fit in L2.
+// From the first square layer on the ciphertexts stay in the NTT domain: the
+// square kernel takes them there, ModDown and rescale return them there, the
+// MAC and the feature add are linear; the outputs return to coefficient form.
 #include <algorithm>
 #include <cuda_runtime.h>
 
@@ -168,76 +171,6 @@ __global__ void __launch_bounds__(kMacThreads, OT <= 5 ? 3 : 2) k_mac_grouped(co
     }
 }
 
-// ModDown by P, add to (d0, d1), then rescale by q_top -- the two roundings in
-// sequence.  D [C][3][n][N] and ACC [C][2][n+K][N] in coefficient form ->
-// out [C][2][n-1][N].  Four coefficients per thread.   grid (N/4/256, 2, C)
-__global__ void __launch_bounds__(256) k_moddown_rescale(const uint32_t *__restrict__ D,
-                                                         const uint32_t *__restrict__ acc, uint32_t *__restrict__ out,
-                                                         int n, int N, KsDev ks, const PrimeConst *__restrict__ pc) {
-    const int k4 = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k4 * 4 >= N) return;
-    const int b = blockIdx.y, ct = blockIdx.z;
-    const int nb = n + ks.K, L = ks.L;
-    const uint4 *db = reinterpret_cast<const uint4 *>(D + ((size_t)ct * 3 + b) * n * N) + k4;
-    const uint4 *ab = reinterpret_cast<const uint4 *>(acc + ((size_t)ct * 2 + b) * nb * N) + k4;
-    uint4 *ob = reinterpret_cast<uint4 *>(out + ((size_t)ct * 2 + b) * (n - 1) * N) + k4;
-    const size_t stride = (size_t)N / 4;  // one limb, in uint4
-    uint32_t r[4][4];                      // [special prime][coefficient]
-    int cnt[4] = {0, 0, 0, 0};
-#pragma unroll
-    for (int m = 0; m < 4; m++) {  // K <= 4; constant indices keep r in registers
-        if (m >= ks.K) break;
-        const PrimeConst &pm = pc[L + m];
-        const uint2 hi = ks.phat_inv[m];
-        const uint4 v = __ldg(ab + (size_t)(n + m) * stride);
-        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-        for (int z = 0; z < 4; z++) {
-            r[m][z] = shoup_mul(w[z], hi.x, hi.y, pm.q);
-            cnt[z] += r[m][z] > pm.half;
-        }
-    }
-    auto limb = [&](int i, uint32_t (&res)[4]) {
-        const uint32_t q = pc[i].q;
-        uint32_t conv[4] = {0, 0, 0, 0};
-#pragma unroll
-        for (int m = 0; m < 4; m++) {
-            if (m >= ks.K) break;
-            const uint2 ph = ks.phat[(size_t)m * L + i];
-#pragma unroll
-            for (int z = 0; z < 4; z++) conv[z] = add_mod(conv[z], shoup_mul(r[m][z], ph.x, ph.y, q), q);
-        }
-        const uint32_t pmod = ks.pmod[i];
-        const uint2 pi = ks.pinv[i];
-        const uint4 av = __ldg(ab + (size_t)i * stride), dv = __ldg(db + (size_t)i * stride);
-        const uint32_t a[4] = {av.x, av.y, av.z, av.w}, d[4] = {dv.x, dv.y, dv.z, dv.w};
-#pragma unroll
-        for (int z = 0; z < 4; z++) {
-            for (int c = 0; c < cnt[z]; c++) conv[z] = sub_mod(conv[z], pmod, q);
-            const uint32_t kv = shoup_mul(sub_mod(a[z], conv[z], q), pi.x, pi.y, q);
-            res[z] = add_mod(d[z], kv, q);
-        }
-    };
-    const int top = n - 1;
-    uint32_t ctop[4];
-    limb(top, ctop);
-    const uint32_t qtop = pc[top].q, htop = pc[top].half;
-    for (int i = 0; i < top; i++) {
-        const uint32_t q = pc[i].q;
-        const uint2 qi = ks.qtop_inv[(size_t)top * L + i];
-        uint32_t ci[4];
-        limb(i, ci);
-        uint32_t o[4];
-#pragma unroll
-        for (int z = 0; z < 4; z++) {
-            uint32_t v = sub_mod(ci[z], ctop[z], q);
-            if (ctop[z] > htop) v = add_mod(v, qtop, q);
-            o[z] = shoup_mul(v, qi.x, qi.y, q);
-        }
-        ob[(size_t)i * stride] = make_uint4(o[0], o[1], o[2], o[3]);
-    }
-}
-
 // Pointwise product in the NTT domain (both operands canonical):
 // data[r][k] <- data[r][k] * u[r mod level][k] mod q_{r mod level}.  grid (N/256, rows)
 __global__ void __launch_bounds__(256) k_mul_ntt(uint32_t *__restrict__ data, const uint32_t *__restrict__ u,
@@ -344,6 +277,7 @@ static int default_chunk(const bcn_ctx *c, int n, int n_ct) {
 struct ChunkBufs {
     uint32_t *d, *acc, *d2n;
 };
+// d [chunk][3][n][N], d2n [chunk][n][N], acc [chunk][2][n+K][N]
 static ChunkBufs carve_chunk(const bcn_ctx *c, int n, int chunk, char *ws) {
     ChunkBufs b;
     const size_t d_b = align_up(3 * (size_t)n * c->N * 4 * chunk), d2n_b = align_up((size_t)n * c->N * 4 * chunk);
@@ -351,6 +285,12 @@ static ChunkBufs carve_chunk(const bcn_ctx *c, int n, int chunk, char *ws) {
     b.d2n = reinterpret_cast<uint32_t *>(ws + d_b);
     b.acc = reinterpret_cast<uint32_t *>(ws + d_b + d2n_b);
     return b;
+}
+// the part of a chunk's buffers from ciphertext o on
+static ChunkBufs chunk_from(const bcn_ctx *c, int n, const ChunkBufs &b, int o) {
+    const size_t N = c->N;
+    return ChunkBufs{b.d + (size_t)o * 3 * n * N, b.acc + (size_t)o * 2 * (n + c->K) * N,
+                     b.d2n + (size_t)o * n * N};
 }
 
 int ks_default_chunk(const bcn_ctx *c, int n, int n_ct) { return default_chunk(c, n, n_ct); }
@@ -402,36 +342,32 @@ static int mac_out_tile(const bcn_layer_plan &p, bool use_tc) {
 
 // Square activation on a chunk of C ciphertexts: Y [C][2][n][N] (coefficient
 // form) -> out [C][2][n-1][N].
-static bcn_status square_chunk(const bcn_ctx *c, int n, const uint32_t *evk, const uint32_t *Y, const ChunkBufs &b,
-                               int C, uint32_t *out, cudaStream_t st, Profiler *prof = nullptr) {
+static bcn_status square_chunk(const bcn_ctx *c, int n, const uint32_t *evk, const uint32_t *Y, bool in_ntt,
+                               const ChunkBufs &b, int C, uint32_t *out, cudaStream_t st, Profiler *prof = nullptr) {
     const int N = c->N, K = c->K, nb = n + K, dnum = (n + c->alpha - 1) / c->alpha;
     const double limb = (double)N * 4;
     const CoreFns *f = core_fns(c->logN);
     if (!f) return fail(BCN_E_INVAL, "unsupported ring degree");
     {
-        Timed tm(prof, st, BCN_KERNEL_SQUARE, limb * C * 5 * n);
-        BCN_TRY(f->square(c, n, Y, b.d, b.d2n, C, st));
+        Timed tm(prof, st, BCN_KERNEL_SQUARE, limb * C * 6.0 * n);
+        BCN_TRY(f->square(c, n, Y, b.d, b.d2n, C, in_ntt, st));
     }
     {
         Timed tm(prof, st, BCN_KERNEL_KEYSWITCH, limb * ((double)C * (n + 2 * nb) + 2.0 * dnum * nb));
-        BCN_TRY(f->keyswitch(c, n, b.d, b.d2n, evk, b.acc, C, st));
+        BCN_TRY(f->keyswitch(c, n, b.d, b.d2n, evk, b.acc, C, true, st));
     }
     Timed tm(prof, st, BCN_KERNEL_MODDOWN_RESCALE, limb * C * (2.0 * n + 2.0 * nb + 2.0 * (n - 1)));
-    k_moddown_rescale<<<dim3((N / 4 + 255) / 256, 2, C), 256, 0, st>>>(b.d, b.acc, out, n, N, ks_dev(c), c->d_pc);
-    return check_launch("k_moddown_rescale");
+    return f->moddown_rescale(c, n, b.d, b.acc, out, C, st);
 }
 
-// Square activation of C ciphertexts with the intermediates in caller-chosen
-// memory: d [C][3][n][N], acc [C][2][n+K][N].
+// Square activation of C coefficient-form ciphertexts with the intermediates in
+// caller-chosen memory (d [C][3][n][N], acc [C][2][n+K][N]); out [C][2][n-1][N]
+// in coefficient form.
 bcn_status square_relin_rescale_chunk(const bcn_ctx *c, int n, const uint32_t *evk, const uint32_t *Y, uint32_t *d,
                                       uint32_t *acc, int C, uint32_t *out, cudaStream_t st) {
     ChunkBufs b{d, acc, nullptr};
-    return square_chunk(c, n, evk, Y, b, C, out, st);
-}
-bcn_status square_relin_rescale_chunk2(const bcn_ctx *c, int n, const uint32_t *evk, const uint32_t *Y, uint32_t *d,
-                                       uint32_t *d2n, uint32_t *acc, int C, uint32_t *out, cudaStream_t st) {
-    ChunkBufs b{d, acc, d2n};
-    return square_chunk(c, n, evk, Y, b, C, out, st);
+    BCN_TRY(square_chunk(c, n, evk, Y, false, b, C, out, st));
+    return launch_ntt(c, out, (size_t)C * 2 * (n - 1), PrimeMap{n - 1, n - 1, 0}, true, st);
 }
 
 // ----------------------------------------------------------- device context
@@ -490,10 +426,14 @@ extern "C" {
 // ------------------------------------------------------------------ model
 static void model_layout(bcn_model *m) {
     const bcn_ctx *c = m->ctx;
-    size_t x_bytes = 0;
+    size_t x_bytes = 0, pt_bytes = 0;
     int max_sq_level = 0, max_sq_out = 0, max_go = 1;
+    bool ntt = false;  // ciphertexts stay in the NTT domain from the first square layer on
     for (size_t l = 0; l < m->layers.size(); l++) {
-        const bcn_layer_plan &p = m->layers[l];
+        bcn_layer_plan &p = m->layers[l];
+        p.in_ntt = ntt ? 1 : 0;
+        if (p.add && ntt) pt_bytes = std::max(pt_bytes, (size_t)p.n_out * p.level * c->N * 4);
+        ntt = ntt || p.square;
         const int lout = p.square ? p.level - 1 : p.level;
         if (p.square) {
             max_sq_level = std::max(max_sq_level, p.level);
@@ -508,6 +448,7 @@ static void model_layout(bcn_model *m) {
     m->chunk = std::max(1, std::min(ch, std::max(max_go, max_sq_out)));
     m->ws_y_bytes = max_sq_level ? y_chunk_bytes(c, max_sq_level, m->chunk) : 0;
     m->ws_chunk_bytes = max_sq_level ? chunk_bytes(c, max_sq_level, m->chunk) : 0;
+    m->ws_pt_bytes = align_up(pt_bytes);
 }
 
 bcn_status bcn_model_create(bcn_ctx *c, const bcn_layer *layers, int n_layers, bcn_model **out) {
@@ -712,7 +653,7 @@ bcn_status bcn_evk_prepare(const bcn_ctx *c, const uint32_t *evk, uint32_t *evk_
 
 bcn_status bcn_eval_workspace_bytes(const bcn_model *m, size_t *bytes) {
     if (!m || !bytes) return fail(BCN_E_INVAL, "bcn_eval_workspace_bytes: null argument");
-    *bytes = 2 * m->ws_x_bytes + m->ws_y_bytes + m->ws_chunk_bytes;
+    *bytes = 2 * m->ws_x_bytes + m->ws_y_bytes + m->ws_chunk_bytes + m->ws_pt_bytes;
     return BCN_OK;
 }
 
@@ -767,6 +708,10 @@ static bcn_status eval_impl(const bcn_model *m, const uint32_t *evk, const uint3
     uint32_t *X[2] = {reinterpret_cast<uint32_t *>(w), reinterpret_cast<uint32_t *>(w + m->ws_x_bytes)};
     uint32_t *Ychunk = reinterpret_cast<uint32_t *>(w + 2 * m->ws_x_bytes);
     char *chunk_ws = w + 2 * m->ws_x_bytes + m->ws_y_bytes;
+    uint32_t *PT = reinterpret_cast<uint32_t *>(chunk_ws + m->ws_chunk_bytes);
+    // the input ciphertexts are in coefficient form; from the first square layer
+    // on they stay in the NTT domain (the MAC is linear, so it runs in either),
+    // and the last layer's outputs return to coefficient form at the end
     const uint32_t *x = cts;
     int a = 0;
     const size_t N = c->N;
@@ -779,12 +724,20 @@ static bcn_status eval_impl(const bcn_model *m, const uint32_t *evk, const uint3
             for (cudaEvent_t e : (*layer_ready)[l])
                 if (cudaStreamWaitEvent(st, e, 0) != cudaSuccess) return fail(BCN_E_CUDA, "bcn_eval: event wait");
         const uint32_t *pt = nullptr;
+        const double limb = (double)N * 4;
         if (p.add) {
             if (!pts || !pts[a] || !aligned16(pts[a]))
                 return fail(BCN_E_INVAL, "bcn_eval: missing feature plaintexts");
             pt = pts[a++];
+            if (p.in_ntt) {  // the features join NTT-domain ciphertexts: transform a copy
+                const size_t bytes = (size_t)p.n_out * p.level * N * 4;
+                Timed tm(prof, st, BCN_KERNEL_SQUARE, 2.0 * bytes);
+                if (cudaMemcpyAsync(PT, pt, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                    return fail(BCN_E_CUDA, "bcn_eval: feature copy failed");
+                BCN_TRY(launch_ntt(c, PT, (size_t)p.n_out * p.level, data_map(p.level), false, st));
+                pt = PT;
+            }
         }
-        const double limb = (double)N * 4;
         if (!p.square) {
             const double mac_bytes = limb * ((double)p.n_distinct_in * 2 * p.level + (double)p.n_out * 2 * p.level +
                                              (pt ? (double)p.n_out * p.level : 0.0));
@@ -812,12 +765,11 @@ static bcn_status eval_impl(const bcn_model *m, const uint32_t *evk, const uint3
                 if (split == nullptr || oA >= C) {
                     BCN_TRY(launch_mac(c, n, p.K, ng, p.n_go, p.d_gidx, p.d_gw, p.d_gout, x, pt, Ychunk, st, prof,
                                        mac_bytes, g0, false, tc));
-                    BCN_TRY(square_chunk(c, n, evk, Ychunk, b, C, yo, st, prof));
+                    BCN_TRY(square_chunk(c, n, evk, Ychunk, p.in_ntt != 0, b, C, yo, st, prof));
                     continue;
                 }
                 const int C1 = C - oA;
-                ChunkBufs b1{b.d + (size_t)oA * 3 * n * N, b.acc + (size_t)oA * 2 * (n + c->K) * N,
-                             b.d2n + (size_t)oA * n * N};
+                const ChunkBufs b1 = chunk_from(c, n, b, oA);
                 if (cudaEventRecord(split_ev[0], st) != cudaSuccess ||
                     cudaStreamWaitEvent(split, split_ev[0], 0) != cudaSuccess)
                     return fail(BCN_E_CUDA, "bcn_eval: fork failed");
@@ -832,8 +784,8 @@ static bcn_status eval_impl(const bcn_model *m, const uint32_t *evk, const uint3
                     BCN_TRY(launch_mac(c, n, p.K, 1, p.n_go, p.d_gidx, p.d_gw, p.d_gout, x, pt, Ychunk, split, nullptr,
                                        0, g0, false, tc, oA, p.n_go));
                 }
-                BCN_TRY(square_chunk(c, n, evk, Ychunk, b, oA, yo, st, nullptr));
-                BCN_TRY(square_chunk(c, n, evk, Ychunk + (size_t)oA * 2 * n * N, b1, C1,
+                BCN_TRY(square_chunk(c, n, evk, Ychunk, p.in_ntt != 0, b, oA, yo, st, nullptr));
+                BCN_TRY(square_chunk(c, n, evk, Ychunk + (size_t)oA * 2 * n * N, p.in_ntt != 0, b1, C1,
                                      yo + (size_t)oA * 2 * (n - 1) * N, split, nullptr));
                 if (cudaEventRecord(split_ev[1], split) != cudaSuccess ||
                     cudaStreamWaitEvent(st, split_ev[1], 0) != cudaSuccess)
@@ -841,6 +793,12 @@ static bcn_status eval_impl(const bcn_model *m, const uint32_t *evk, const uint3
             }
         }
         x = y;
+    }
+    const bcn_layer_plan &pl = m->layers.back();
+    if (pl.in_ntt || pl.square) {  // back to coefficient form
+        const int lout = pl.square ? pl.level - 1 : pl.level;
+        Timed tm(prof, st, BCN_KERNEL_SQUARE, 2.0 * pl.n_out * 2 * lout * (double)N * 4);
+        BCN_TRY(launch_ntt(c, out, (size_t)pl.n_out * 2 * lout, data_map(lout), true, st));
     }
     return BCN_OK;
 }
@@ -1056,8 +1014,10 @@ bcn_status bcn_op_tensor_square(const bcn_ctx *c, int level, const uint32_t *in,
     if (!f) return fail(BCN_E_INVAL, "unsupported ring degree");
     for (int o0 = 0; o0 < n_ct; o0 += 32768) {
         const int C = std::min(32768, n_ct - o0);
-        BCN_TRY(f->square(c, level, in + (size_t)o0 * 2 * level * N, out + (size_t)o0 * 3 * level * N, nullptr, C,
-                          st));
+        uint32_t *o = out + (size_t)o0 * 3 * level * N;
+        BCN_TRY(f->square(c, level, in + (size_t)o0 * 2 * level * N, o, nullptr, C, false, st));
+        // d0 and d1 leave the kernel in the NTT domain
+        BCN_TRY(launch_ntt_strided(c, o, 2 * (size_t)level, C, 3 * (size_t)level * N, data_map(level), true, st));
     }
     return BCN_OK;
 }
@@ -1077,7 +1037,9 @@ bcn_status bcn_op_square_relin_rescale(const bcn_ctx *c, int level, const uint32
     ChunkBufs b = carve_chunk(c, n, chunk, reinterpret_cast<char *>(ws));
     for (int o0 = 0; o0 < n_ct; o0 += chunk) {
         const int C = std::min(chunk, n_ct - o0);
-        BCN_TRY(square_chunk(c, n, evk, in + (size_t)o0 * 2 * n * N, b, C, out + (size_t)o0 * 2 * (n - 1) * N, st));
+        uint32_t *o = out + (size_t)o0 * 2 * (n - 1) * N;
+        BCN_TRY(square_chunk(c, n, evk, in + (size_t)o0 * 2 * n * N, false, b, C, o, st));
+        BCN_TRY(launch_ntt(c, o, (size_t)C * 2 * (n - 1), data_map(n - 1), true, st));
     }
     return BCN_OK;
 }

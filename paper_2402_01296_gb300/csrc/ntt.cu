@@ -1,4 +1,5 @@
 // Dispatch of the NTT-based kernels by ring degree.
+#include <algorithm>
 #include <cuda_runtime.h>
 
 #include "device_api.h"
@@ -23,13 +24,23 @@ bcn_status cores_setup_all() {
     return BCN_OK;
 }
 
+bcn_status launch_ntt_strided(const bcn_ctx *c, uint32_t *data, size_t n_limbs, size_t n_groups, size_t stride,
+                              const PrimeMap &pm, bool inverse, cudaStream_t st) {
+    const CoreFns *f = core_fns(c->logN);
+    if (!f) return fail(BCN_E_INVAL, "unsupported ring degree");
+    for (size_t g0 = 0; g0 < n_groups; g0 += 65535) {  // grid.y limit
+        const size_t G = std::min<size_t>(65535, n_groups - g0);
+        bcn_status s = f->ntt(c, data + g0 * stride, n_limbs, G, stride, pm, inverse, st);
+        if (s != BCN_OK) return s;
+    }
+    return BCN_OK;
+}
+
 bcn_status launch_ntt(const bcn_ctx *c, uint32_t *data, size_t n_limbs, const PrimeMap &pm, bool inverse,
                       cudaStream_t st) {
     if (n_limbs == 0) return BCN_OK;
     if (n_limbs > 0x7FFFFFFFull) return fail(BCN_E_INVAL, "too many limbs for one NTT launch");
-    const CoreFns *f = core_fns(c->logN);
-    if (!f) return fail(BCN_E_INVAL, "unsupported ring degree");
-    return f->ntt(c, data, n_limbs, pm, inverse, st);
+    return launch_ntt_strided(c, data, n_limbs, 1, 0, pm, inverse, st);
 }
 
 }  // namespace bcn

@@ -135,7 +135,7 @@ extern "C" bcn_status bcn_op_rotate(const bcn_ctx *c, int level, const uint32_t 
         k_automorph_c1<<<dim3((unsigned)((N + 255) / 256), n, C), 256, 0, st>>>(x, d, n, (int)N, (uint32_t)ginv,
                                                                              c->d_pc);
         BCN_TRY(check_launch("k_automorph_c1"));
-        BCN_TRY(f->keyswitch(c, n, d, nullptr, gk, acc, C, st));
+        BCN_TRY(f->keyswitch(c, n, d, nullptr, gk, acc, C, false, st));
         k_moddown_rotate<<<dim3((unsigned)((N / 4 + 255) / 256), 2, C), 256, 0, st>>>(
             x, acc, out + (size_t)o0 * ct_words, n, (int)N, (uint32_t)ginv, ks_dev(c), c->d_pc);
         BCN_TRY(check_launch("k_moddown_rotate"));
