@@ -85,8 +85,14 @@ struct CoreOcc {
 // and, with D2N != nullptr, d2 in the NTT domain too (D2N [C][n][N], which the
 // key switch reuses on the digit's own prime).  All outputs canonical.
 // grid (n, C).
+template <int T>
+struct SqnOcc {  // square kernel on NTT-domain input (one transform a block): 64 registers
+    static constexpr int B = 65536 / (T * 64);
+    static constexpr int MIN_BLOCKS = B > 32 ? 32 : (B < 1 ? 1 : B);
+};
 template <int LOGN, int R, bool IN_NTT>
-__global__ void __launch_bounds__((1 << LOGN) / R, CoreOcc<(1 << LOGN) / R>::MIN_BLOCKS)
+__global__ void __launch_bounds__((1 << LOGN) / R, IN_NTT ? SqnOcc<(1 << LOGN) / R>::MIN_BLOCKS
+                                                          : CoreOcc<(1 << LOGN) / R>::MIN_BLOCKS)
     k_square_core(const uint32_t *__restrict__ Y, uint32_t *__restrict__ D, uint32_t *__restrict__ D2N, int n,
                   const PrimeConst *__restrict__ pc, const uint2 *__restrict__ twf, const uint2 *__restrict__ twi) {
     using C = NttCore<LOGN, R, true, kFmaSquare>;  // data primes only (q < 2^30): lazy butterflies
@@ -514,19 +520,18 @@ __global__ void __launch_bounds__((1 << LOGN) / R, CoreOcc<(1 << LOGN) / R>::MIN
 // n-1: INTT(A_top P^{-1} + D_top), coefficient form, from the key switch;
 // limbs n..n+K-1: a_P, coefficient form) -> OUT [C][2][n-1][N] (NTT domain,
 // last-pass layout, canonical).  grid (n - 1, 2 / NP, C)
-#ifndef BCN_MD_REGS
-#define BCN_MD_REGS 64
-#endif
-#ifndef BCN_MD_R14
-#define BCN_MD_R14 0
-#endif
-template <int T>
-struct MdOcc {  // one-poly blocks: 64 registers a thread
-    static constexpr int B = 65536 / (T * BCN_MD_REGS);
+// Register budget of the ModDown/rescale blocks: its element-wise prologue
+// (loads of the special-prime limbs and the top limb) wants occupancy --
+// measured at N = 8192: 40 registers (3 blocks per SM) 0.140 ms, 64 registers
+// 0.155 ms, 128 registers 0.193 ms; 32 residues a thread need 64
+template <int T, int R>
+struct MdOcc {
+    static constexpr int REGS = R >= 32 ? 64 : 40;
+    static constexpr int B = 65536 / (T * REGS);
     static constexpr int MIN_BLOCKS = B > 32 ? 32 : (B < 1 ? 1 : B);
 };
 template <int LOGN, int R, int NP, int K>
-__global__ void __launch_bounds__((1 << LOGN) / R, NP == 1 ? MdOcc<(1 << LOGN) / R>::MIN_BLOCKS
+__global__ void __launch_bounds__((1 << LOGN) / R, NP == 1 ? MdOcc<(1 << LOGN) / R, R>::MIN_BLOCKS
                                                            : CoreOcc<(1 << LOGN) / R>::MIN_BLOCKS)
     k_md_limb(const uint32_t *__restrict__ D, const uint32_t *__restrict__ acc, uint32_t *__restrict__ out, int n,
               KsDev ks, const PrimeConst *__restrict__ pc, const uint2 *__restrict__ twf) {
@@ -631,7 +636,7 @@ struct CoreImpl {
     // the key switch's
     // (one poly per block measured faster than two in lockstep: the kernel's
     // element-wise prologue wants the occupancy of 64-register blocks)
-    static constexpr int RMD = kDual<LOGN, R> ? R : (BCN_MD_R14 > 0 ? BCN_MD_R14 : RKS);
+    static constexpr int RMD = kDual<LOGN, R> ? R : RKS;
     static constexpr int MD_NP = 1;
     using CoreMd = NttCore<LOGN, RMD>;
     static constexpr size_t SMEM_MD = (size_t)MD_NP * CoreMd::SMEM_WORDS * 4;
