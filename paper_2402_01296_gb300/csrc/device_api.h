@@ -100,12 +100,16 @@ bcn_status launch_ntt_strided(const bcn_ctx *c, uint32_t *data, size_t n_limbs, 
 int ks_default_chunk(const bcn_ctx *c, int n, int n_ct);
 void ks_carve(const bcn_ctx *c, int n, int chunk, char *ws, uint32_t **d, uint32_t **d2n, uint32_t **acc);
 
-// Tensor-core MAC (mac_tc.cu): used for groups of at least kMacTcMinOutputs
-// outputs and at most kMacTcMaxTaps taps (the fp32 sums stay exact).
+// Tensor-core MAC (mac_tc.cu): used for groups of at most kMacTcMaxTaps taps
+// (the fp32 sums stay exact) and at least kMacTcMinOutputs outputs, or at least
+// kMacTcMinOutputsLong outputs when they have kMacTcLongTaps taps or more
+// (measured: dense layers of 10 outputs and 80-100 taps are faster there, a
+// 27-tap convolution with 16 outputs is not).
 #ifndef BCN_TC_MIN_OUTPUTS
 #define BCN_TC_MIN_OUTPUTS 32
 #endif
 constexpr int kMacTcMaxTaps = 512, kMacTcMinOutputs = BCN_TC_MIN_OUTPUTS;
+constexpr int kMacTcMinOutputsLong = 10, kMacTcLongTaps = 64;
 bool mac_tc_eligible(const bcn_ctx *c, int K, int n_go);
 // w: [n_go][K] int8 weights shared by every group
 bcn_status mac_tc_plan(const bcn_ctx *c, int K, int n_go, const int8_t *w, MacTcPlan *p);

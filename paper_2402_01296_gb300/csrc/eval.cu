@@ -301,6 +301,13 @@ void ks_carve(const bcn_ctx *c, int n, int chunk, char *ws, uint32_t **d, uint32
     *acc = b.acc;
 }
 
+// outputs per thread of the grouped MAC: at most 8, the tiles of a group as
+// even as possible (every tile reads all of the group's taps)
+static int mac_grouped_tile(int n_go) {
+    const int tiles = (n_go + 7) / 8;
+    return (n_go + tiles - 1) / tiles;
+}
+
 // MAC over groups [g_base, g_base + n_groups) of a layer
 static bcn_status launch_mac(const bcn_ctx *c, int level, int K, int n_groups, int n_go, const int32_t *gidx,
                              const int8_t *gw, const int32_t *gout, const uint32_t *in, const uint32_t *pt,
@@ -317,7 +324,7 @@ static bcn_status launch_mac(const bcn_ctx *c, int level, int K, int n_groups, i
                              t_lo, t_hi - t_lo);
     }
     const int N = c->N;
-    const int OT = std::min(8, n_go);
+    const int OT = mac_grouped_tile(n_go);
     const int t_lo = o_lo / OT, n_tl = (o_hi + OT - 1) / OT - t_lo;
     const size_t cols = (size_t)2 * level * N;
     const int kca = std::min(K, kMacTapChunk);
@@ -337,7 +344,7 @@ static bcn_status launch_mac(const bcn_ctx *c, int level, int K, int n_groups, i
 
 // outputs per tile of the MAC kernel a layer runs (splits fall on tile boundaries)
 static int mac_out_tile(const bcn_layer_plan &p, bool use_tc) {
-    return use_tc && p.tc.w16 != nullptr ? p.tc.tile_out : std::min(8, p.n_go);
+    return use_tc && p.tc.w16 != nullptr ? p.tc.tile_out : mac_grouped_tile(p.n_go);
 }
 
 // Square activation on a chunk of C ciphertexts: Y [C][2][n][N] (coefficient

@@ -290,7 +290,8 @@ static uint16_t half_of_int(int v) {  // exact for |v| < 2048
 }
 
 bool mac_tc_eligible(const bcn_ctx *c, int K, int n_go) {
-    return K >= 1 && K <= kMacTcMaxTaps && n_go >= kMacTcMinOutputs && c->N >= kRows && c->N % kRows == 0;
+    const bool wide = n_go >= kMacTcMinOutputs || (n_go >= kMacTcMinOutputsLong && K >= kMacTcLongTaps);
+    return K >= 1 && K <= kMacTcMaxTaps && wide && c->N >= kRows && c->N % kRows == 0;
 }
 
 size_t mac_tc_smem(int NT, int Kpad) {

@@ -43,7 +43,8 @@ def run_model(ctx, layer, w, x, pt, impl):
 
 
 @pytest.mark.parametrize("n_in,n_out,extreme", [(180, 100, False), (512, 64, True), (37, 33, False),
-                                                (100, 130, False), (16, 32, True)])
+                                                (100, 130, False), (16, 32, True), (100, 10, True),
+                                                (64, 12, False)])
 def test_dense_matches_oracle(n_in, n_out, extreme):
     c, P = pair((13, 3, 1, 1))
     rng = np.random.default_rng(n_in * 7 + n_out)
