@@ -35,15 +35,26 @@ namespace bcn {
 
 namespace {
 
+#ifndef BCN_TC_SLAB
+#define BCN_TC_SLAB 32
+#endif
+#ifndef BCN_TC_ABUF
+#define BCN_TC_ABUF 1
+#endif
 constexpr int kRows = 128;                       // columns per CTA (MMA M)
 constexpr int kThreads = 256;                    // two threads per column
-constexpr int kSlab = 32;                        // taps per slab
+constexpr int kSlab = BCN_TC_SLAB;               // taps per slab (16 or 32)
+constexpr int kABuf = BCN_TC_ABUF;               // A buffers: with 2, one slab converts while the last multiplies
+// (measured on the CryptoNets-scale dense layer: 32-tap slabs and one A buffer
+// 0.234 ms of MAC per evaluation; 16-tap slabs 0.247, with two A buffers
+// 0.249; 32-tap slabs with two A buffers, one CTA per SM, 0.300)
 constexpr int kPlanes = 4;                       // bytes of a residue
 constexpr int kStages = 3;                       // raw slabs in shared memory
-constexpr int kStageBytes = kSlab * kRows * 4;   // raw residues of one slab (16 KiB)
-constexpr int kPlaneBytes = kRows * kSlab * 2;   // one fp16 plane of a slab (8 KiB)
-constexpr int kABytes = kPlanes * kPlaneBytes;   // 32 KiB
+constexpr int kStageBytes = kSlab * kRows * 4;   // raw residues of one slab
+constexpr int kPlaneBytes = kRows * kSlab * 2;   // one fp16 plane of a slab
+constexpr int kABytes = kPlanes * kPlaneBytes;   // one A buffer
 constexpr uint32_t kSboA = (kSlab / 8) * 128;    // bytes between row groups of a plane
+static_assert(kSlab == 16 || kSlab == 32, "slabs of 16 or 32 taps");
 constexpr int kWaitLimit = 1 << 20;              // mbarrier polls before giving up
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -129,11 +140,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_mac_tc(const uint32_t *__restri
                                                      uint32_t tmem_cols, uint32_t *__restrict__ status) {
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char *S = sm;                          // [kStages][kSlab][kRows] u32
-    unsigned char *A = sm + kStages * kStageBytes;  // [kPlanes] planes
-    unsigned char *B = A + kABytes;                 // [NT][Kpad] fp16
+    unsigned char *A = sm + kStages * kStageBytes;  // [kABuf][kPlanes] planes
+    unsigned char *B = A + kABuf * kABytes;         // [NT][Kpad] fp16
     int32_t *sidx = reinterpret_cast<int32_t *>(B + (size_t)NT * Kpad * 2);
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(sidx + Kpad);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(sidx + Kpad);  // [kABuf]: MMAs of the slabs in A buffer b
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + kABuf);
     volatile int *flag = reinterpret_cast<volatile int *>(tslot + 1);
     int32_t *sgo = reinterpret_cast<int32_t *>(tslot + 2);  // [NT] the tile's output indices
 
@@ -150,7 +161,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_mac_tc(const uint32_t *__restri
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar)));
+#pragma unroll
+        for (int b = 0; b < kABuf; b++) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar + b)));
         asm volatile("fence.mbarrier_init.release.cluster;");
         *flag = 0;
     }
@@ -172,7 +184,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_mac_tc(const uint32_t *__restri
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *tslot;
-    const uint32_t a_base = smem_addr(A), b_base = smem_addr(B), mb = smem_addr(mbar);
+    const uint32_t a_base0 = smem_addr(A), b_base = smem_addr(B), mb0 = smem_addr(mbar);
     const uint32_t idesc = instr_desc(kRows, NT);
     const uint32_t sbo_b = (uint32_t)(Kpad / 8) * 128;
 
@@ -187,15 +199,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_mac_tc(const uint32_t *__restri
             asm volatile("cp.async.commit_group;" ::: "memory");
             asm volatile("cp.async.wait_group %0;" ::"n"(kStages - 1) : "memory");
         }
-        __syncthreads();  // slab sl is in its stage for every thread; A is free
+        // A buffer ab held slab sl - kABuf: its MMAs (the (sl/kABuf - 1)-th
+        // commit to mbar[ab]) must be done before it is overwritten
+        const int ab = sl % kABuf;
+        const uint32_t a_base = a_base0 + (uint32_t)(ab * kABytes), mb = mb0 + (uint32_t)(ab * 8);
+        if (tid == 0 && sl >= kABuf && !mbar_wait(mb, (uint32_t)((sl / kABuf - 1) & 1))) *flag = 1;
+        __syncthreads();  // slab sl is in its stage for every thread; A buffer ab is free
+        if (*flag) break;
         {
+            constexpr int TT = kSlab / 2;  // taps a thread converts
             const uint32_t *st = reinterpret_cast<const uint32_t *>(S + (sl % kStages) * kStageBytes);
-            uint32_t x[16];
+            uint32_t x[TT];
 #pragma unroll
-            for (int j = 0; j < 16; j++) x[j] = st[(16 * half + j) * kRows + r];
+            for (int j = 0; j < TT; j++) x[j] = st[(TT * half + j) * kRows + r];
 #pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const int t8 = 16 * half + 8 * h;
+            for (int h = 0; h < TT / 8; h++) {
+                const int t8 = TT * half + 8 * h;
                 const uint32_t off = (uint32_t)(r >> 3) * kSboA + (uint32_t)(t8 >> 3) * 128 + (r & 7) * 16;
 #pragma unroll
                 for (int b = 0; b < kPlanes; b++) {
@@ -204,7 +223,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_mac_tc(const uint32_t *__restri
                     v.y = byte_pair(x[8 * h + 2], x[8 * h + 3], b);
                     v.z = byte_pair(x[8 * h + 4], x[8 * h + 5], b);
                     v.w = byte_pair(x[8 * h + 6], x[8 * h + 7], b);
-                    *reinterpret_cast<uint4 *>(A + b * kPlaneBytes + off) = v;
+                    *reinterpret_cast<uint4 *>(A + ab * kABytes + b * kPlaneBytes + off) = v;
                 }
             }
         }
@@ -228,11 +247,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_mac_tc(const uint32_t *__restri
                 }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb));
-            if (!mbar_wait(mb, (uint32_t)(sl & 1))) *flag = 1;
         }
-        __syncthreads();  // the MMAs of this slab are done (or the wait gave up)
-        if (*flag) break;
     }
+    // the last commit tracks every MMA before it
+    if (tid == 0 && *flag == 0 && n_slabs > 0) {
+        const int last = n_slabs - 1;
+        if (!mbar_wait(mb0 + (uint32_t)((last % kABuf) * 8), (uint32_t)((last / kABuf) & 1))) *flag = 1;
+    }
+    __syncthreads();
     asm volatile("cp.async.wait_group 0;" ::: "memory");
 
     if (*flag == 0) {
@@ -295,8 +317,8 @@ bool mac_tc_eligible(const bcn_ctx *c, int K, int n_go) {
 }
 
 size_t mac_tc_smem(int NT, int Kpad) {
-    return (size_t)kStages * kStageBytes + kABytes + (size_t)NT * Kpad * 2 + (size_t)Kpad * 4 + 16 + (size_t)NT * 4 +
-           1024;
+    return (size_t)kStages * kStageBytes + (size_t)kABuf * kABytes + (size_t)NT * Kpad * 2 + (size_t)Kpad * 4 +
+           8 * kABuf + 8 + (size_t)NT * 4 + 1024;
 }
 
 bcn_status mac_tc_plan(const bcn_ctx *c, int K, int n_go, const int8_t *w, MacTcPlan *p) {
