@@ -66,13 +66,24 @@ constexpr int kFmaSquare = BCN_FMA_SQ, kFmaKs = BCN_FMA_KS;
 template <int LOGN, int R>
 constexpr bool kDual = (1 << LOGN) / R <= 512 && R <= 16;
 
+// The key switch's block shape: at N = 8192 (512 threads) two blocks per SM of
+// 64 registers and one exchange buffer (digits transformed one at a time)
+// measured faster than one block of 128 registers with digit pairs (0.486
+// against 0.501 ms per CryptoNets-scale evaluation; the pairs' second buffer
+// and the running sums do not fit twice in shared memory); at N = 4096 and
+// 16384 the pairs / 128 registers are faster.
+template <int LOGN, int R>
+constexpr bool kKsWide = LOGN == 13 && R == 16;
+template <int LOGN, int R>
+constexpr bool kKsDual = kDual<LOGN, R> && !kKsWide<LOGN, R>;
+
 // Register budget per thread of the fused kernels (sets their blocks per SM).
 #ifndef BCN_CORE_REGS
 #define BCN_CORE_REGS 128
 #endif
-template <int T>
+template <int T, int REGS = BCN_CORE_REGS>
 struct CoreOcc {
-    static constexpr int B = 65536 / (T * BCN_CORE_REGS);
+    static constexpr int B = 65536 / (T * REGS);
     static constexpr int MIN_BLOCKS = B > 32 ? 32 : (B < 1 ? 1 : B);
 };
 
@@ -85,14 +96,17 @@ struct CoreOcc {
 // and, with D2N != nullptr, d2 in the NTT domain too (D2N [C][n][N], which the
 // key switch reuses on the digit's own prime).  All outputs canonical.
 // grid (n, C).
-template <int T>
-struct SqnOcc {  // square kernel on NTT-domain input (one transform a block): 64 registers
-    static constexpr int B = 65536 / (T * 64);
+// Register budget of the square kernel: 64 (two 512-thread blocks per SM at
+// N = 8192) measured faster than 128 with either input domain (coefficient
+// input: 0.173 against 0.194 ms per CryptoNets-scale evaluation)
+template <int T, int REGS>
+struct SqnOcc {
+    static constexpr int B = 65536 / (T * REGS);
     static constexpr int MIN_BLOCKS = B > 32 ? 32 : (B < 1 ? 1 : B);
 };
 template <int LOGN, int R, bool IN_NTT>
-__global__ void __launch_bounds__((1 << LOGN) / R, IN_NTT ? SqnOcc<(1 << LOGN) / R>::MIN_BLOCKS
-                                                          : CoreOcc<(1 << LOGN) / R>::MIN_BLOCKS)
+__global__ void __launch_bounds__((1 << LOGN) / R, IN_NTT ? SqnOcc<(1 << LOGN) / R, 64>::MIN_BLOCKS
+                                                          : SqnOcc<(1 << LOGN) / R, 64>::MIN_BLOCKS)
     k_square_core(const uint32_t *__restrict__ Y, uint32_t *__restrict__ D, uint32_t *__restrict__ D2N, int n,
                   const PrimeConst *__restrict__ pc, const uint2 *__restrict__ twf, const uint2 *__restrict__ twi) {
     using C = NttCore<LOGN, R, true, kFmaSquare>;  // data primes only (q < 2^30): lazy butterflies
@@ -236,7 +250,7 @@ __device__ __forceinline__ void ks_core_body(const uint32_t *__restrict__ D, con
     extern __shared__ __align__(16) uint32_t sm[];
     // exchange buffer(s) -- two where the final inverse transforms run together --
     // then the two running sums in thread-private slots u*T + tid
-    uint32_t *s0 = sm + (kDual<LOGN, R> ? 2 : 1) * C::SMEM_WORDS, *s1 = s0 + N;
+    uint32_t *s0 = sm + (kKsDual<LOGN, R> ? 2 : 1) * C::SMEM_WORDS, *s1 = s0 + N;
     const int t = blockIdx.x, ct = blockIdx.y, tid = threadIdx.x;
     const int A = ks.alpha, dnum = (n + A - 1) / A, nb = n + ks.K;
     const int pt = t < n ? t : ks.L + (t - n);
@@ -315,7 +329,7 @@ __device__ __forceinline__ void ks_core_body(const uint32_t *__restrict__ D, con
 #pragma unroll
     for (int u = 0; u < R; u++) s0[u * T + tid] = s1[u * T + tid] = 0;
     bool summed = false;
-    if constexpr (LAZY && kDual<LOGN, R>) {
+    if constexpr (LAZY && kKsDual<LOGN, R>) {
         if (A == 1) {
             // one-prime digits: the digit's own limb from D2N when given; the
             // others lifted (d, less q_j mod t when d > (q_j-1)/2; the own
@@ -438,7 +452,7 @@ __device__ __forceinline__ void ks_core_body(const uint32_t *__restrict__ D, con
                                     shoup_mul(dv[z], P.ninv, P.ninv_shoup, P.q), P.q);
         }
     };
-    if constexpr (kDual<LOGN, R>) {
+    if constexpr (kKsDual<LOGN, R>) {
         uint32_t y[2][R];
 #pragma unroll
         for (int u = 0; u < R; u++) {
@@ -485,7 +499,7 @@ __device__ __forceinline__ void ks_core_body(const uint32_t *__restrict__ D, con
 // grid (n+K, C); lazy butterflies for the data primes (< 2^30), strict ones for
 // the special primes (< 2^31)
 template <int LOGN, int R>
-__global__ void __launch_bounds__((1 << LOGN) / R, CoreOcc<(1 << LOGN) / R>::MIN_BLOCKS)
+__global__ void __launch_bounds__((1 << LOGN) / R, CoreOcc<(1 << LOGN) / R, kKsWide<LOGN, R> ? 64 : BCN_CORE_REGS>::MIN_BLOCKS)
     k_ks_core(const uint32_t *__restrict__ D, const uint32_t *__restrict__ D2N, const uint32_t *__restrict__ evk,
               uint32_t *__restrict__ acc_out, int n, int ntt_out, KsDev ks, const PrimeConst *__restrict__ pc,
               const uint2 *__restrict__ twf, const uint2 *__restrict__ twi) {
@@ -641,7 +655,7 @@ struct CoreImpl {
     using CoreMd = NttCore<LOGN, RMD>;
     static constexpr size_t SMEM_MD = (size_t)MD_NP * CoreMd::SMEM_WORDS * 4;
     // key switch: exchange buffer(s) and the two running sums
-    static constexpr size_t SMEM_KS = ((size_t)(kDual<LOGN, RKS> ? 2 : 1) * CoreKs::SMEM_WORDS + 2 * CoreKs::N) * 4;
+    static constexpr size_t SMEM_KS = ((size_t)(kKsDual<LOGN, RKS> ? 2 : 1) * CoreKs::SMEM_WORDS + 2 * CoreKs::N) * 4;
 
     static bcn_status ntt(const bcn_ctx *c, uint32_t *data, size_t n_limbs, size_t n_groups, size_t stride,
                           PrimeMap pm, bool inverse, cudaStream_t st) {
