@@ -160,6 +160,7 @@ struct bcn_model {
     // by split_mu): a chunk's two halves run side by side
     std::mutex split_mu;
     cudaStream_t split_stream = nullptr;
+    cudaStream_t aux_stream = nullptr;  // feature-plaintext transforms (also under split_mu)
     size_t ws_x_bytes;  // one ping-pong activation buffer
     size_t ws_y_bytes;  // MAC output of a square layer
     size_t ws_chunk_bytes;

@@ -439,7 +439,7 @@ static void model_layout(bcn_model *m) {
     for (size_t l = 0; l < m->layers.size(); l++) {
         bcn_layer_plan &p = m->layers[l];
         p.in_ntt = ntt ? 1 : 0;
-        if (p.add && ntt) pt_bytes = std::max(pt_bytes, (size_t)p.n_out * p.level * c->N * 4);
+        if (p.add && ntt) pt_bytes += align_up((size_t)p.n_out * p.level * c->N * 4);
         ntt = ntt || p.square;
         const int lout = p.square ? p.level - 1 : p.level;
         if (p.square) {
@@ -603,6 +603,7 @@ bcn_status bcn_model_destroy(bcn_model *m) {
     for (auto s2 : m->copy_streams) cudaStreamDestroy(s2);
     for (auto &kv : m->staging_free) cudaEventDestroy(kv.second);
     if (m->split_stream) cudaStreamDestroy(m->split_stream);
+    if (m->aux_stream) cudaStreamDestroy(m->aux_stream);
     delete m;
     return BCN_OK;
 }
@@ -715,13 +716,73 @@ static bcn_status eval_impl(const bcn_model *m, const uint32_t *evk, const uint3
     uint32_t *X[2] = {reinterpret_cast<uint32_t *>(w), reinterpret_cast<uint32_t *>(w + m->ws_x_bytes)};
     uint32_t *Ychunk = reinterpret_cast<uint32_t *>(w + 2 * m->ws_x_bytes);
     char *chunk_ws = w + 2 * m->ws_x_bytes + m->ws_y_bytes;
-    uint32_t *PT = reinterpret_cast<uint32_t *>(chunk_ws + m->ws_chunk_bytes);
     // the input ciphertexts are in coefficient form; from the first square layer
     // on they stay in the NTT domain (the MAC is linear, so it runs in either),
-    // and the last layer's outputs return to coefficient form at the end
+    // and the last layer's outputs return to coefficient form at the end.  The
+    // feature plaintexts that join NTT-domain ciphertexts are transformed (into
+    // their own slices of the workspace) on the model's aux stream, forked from
+    // `st` at the start, while the layers before them run; each such layer's MAC
+    // waits for its event.  With kernel timing on they run on `st` in place.
+    const size_t N = c->N;
+    std::vector<uint32_t *> pt_ntt(m->layers.size(), nullptr);
+    std::vector<cudaEvent_t> pt_ev(m->layers.size(), nullptr);
+    struct EventList {
+        std::vector<cudaEvent_t> &e;
+        ~EventList() {
+            for (cudaEvent_t v : e)
+                if (v) cudaEventDestroy(v);
+        }
+    } pt_guard{pt_ev};
+    {
+        char *PT = chunk_ws + m->ws_chunk_bytes;
+        int a = 0;
+        for (size_t l = 0; l < m->layers.size(); l++) {
+            const bcn_layer_plan &p = m->layers[l];
+            if (!p.add) continue;
+            if (!pts || !pts[a] || !aligned16(pts[a])) return fail(BCN_E_INVAL, "bcn_eval: missing feature plaintexts");
+            a++;
+            if (!p.in_ntt) continue;
+            pt_ntt[l] = reinterpret_cast<uint32_t *>(PT);
+            PT += align_up((size_t)p.n_out * p.level * N * 4);
+        }
+    }
+    cudaStream_t aux = nullptr;
+    bool any_pt_ntt = false;
+    for (uint32_t *q : pt_ntt) any_pt_ntt |= q != nullptr;
+    if (!m->prof.on && any_pt_ntt) {
+        bcn_model *mm = const_cast<bcn_model *>(m);
+        {
+            std::lock_guard<std::mutex> lock(mm->split_mu);
+            if (!mm->aux_stream && cudaStreamCreateWithFlags(&mm->aux_stream, cudaStreamNonBlocking) != cudaSuccess)
+                return fail(BCN_E_CUDA, "bcn_eval: stream creation failed");
+            aux = mm->aux_stream;
+        }
+        cudaEvent_t fork = nullptr;
+        if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess)
+            return fail(BCN_E_CUDA, "bcn_eval: event creation failed");
+        const bool forked = cudaEventRecord(fork, st) == cudaSuccess && cudaStreamWaitEvent(aux, fork, 0) == cudaSuccess;
+        cudaEventDestroy(fork);
+        if (!forked) return fail(BCN_E_CUDA, "bcn_eval: fork failed");
+        int a = 0;
+        for (size_t l = 0; l < m->layers.size(); l++) {
+            const bcn_layer_plan &p = m->layers[l];
+            if (!p.add) continue;
+            const uint32_t *pt = pts[a++];
+            if (!pt_ntt[l]) continue;
+            if (layer_ready != nullptr)
+                for (cudaEvent_t e : (*layer_ready)[l])
+                    if (cudaStreamWaitEvent(aux, e, 0) != cudaSuccess) return fail(BCN_E_CUDA, "bcn_eval: event wait");
+            const size_t bytes = (size_t)p.n_out * p.level * N * 4;
+            if (cudaMemcpyAsync(pt_ntt[l], pt, bytes, cudaMemcpyDeviceToDevice, aux) != cudaSuccess)
+                return fail(BCN_E_CUDA, "bcn_eval: feature copy failed");
+            BCN_TRY(launch_ntt(c, pt_ntt[l], (size_t)p.n_out * p.level, data_map(p.level), false, aux));
+            if (cudaEventCreateWithFlags(&pt_ev[l], cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventRecord(pt_ev[l], aux) != cudaSuccess)
+                return fail(BCN_E_CUDA, "bcn_eval: event record failed");
+        }
+    }
     const uint32_t *x = cts;
     int a = 0;
-    const size_t N = c->N;
     Profiler *prof = &m->prof;
     for (size_t l = 0; l < m->layers.size(); l++) {
         const bcn_layer_plan &p = m->layers[l];
@@ -736,13 +797,17 @@ static bcn_status eval_impl(const bcn_model *m, const uint32_t *evk, const uint3
             if (!pts || !pts[a] || !aligned16(pts[a]))
                 return fail(BCN_E_INVAL, "bcn_eval: missing feature plaintexts");
             pt = pts[a++];
-            if (p.in_ntt) {  // the features join NTT-domain ciphertexts: transform a copy
+            if (pt_ev[l] != nullptr) {  // transformed on the aux stream
+                if (cudaStreamWaitEvent(st, pt_ev[l], 0) != cudaSuccess)
+                    return fail(BCN_E_CUDA, "bcn_eval: event wait");
+                pt = pt_ntt[l];
+            } else if (pt_ntt[l] != nullptr) {  // kernel timing: on `st`
                 const size_t bytes = (size_t)p.n_out * p.level * N * 4;
                 Timed tm(prof, st, BCN_KERNEL_SQUARE, 2.0 * bytes);
-                if (cudaMemcpyAsync(PT, pt, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                if (cudaMemcpyAsync(pt_ntt[l], pt, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
                     return fail(BCN_E_CUDA, "bcn_eval: feature copy failed");
-                BCN_TRY(launch_ntt(c, PT, (size_t)p.n_out * p.level, data_map(p.level), false, st));
-                pt = PT;
+                BCN_TRY(launch_ntt(c, pt_ntt[l], (size_t)p.n_out * p.level, data_map(p.level), false, st));
+                pt = pt_ntt[l];
             }
         }
         if (!p.square) {
