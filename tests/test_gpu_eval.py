@@ -91,6 +91,25 @@ def test_eval_chunk_size_does_not_change_results(case):
     assert np.array_equal(host(out), ref)
 
 
+def test_eval_with_kernel_timing_matches(case):
+    """With kernel timing on, an evaluation runs on one stream (no split chunk
+    halves; the feature plaintexts that join NTT-domain ciphertexts are
+    transformed in place on it): the same residues, and every kernel class of
+    the square layers timed."""
+    cfg, prob, ref = case
+    ctx = bcn.Context.from_config(cfg)
+    model = bcn.Model(ctx, cfg["cipher"], prob.w_int, prob.s_w)
+    model.profile_enable(True)
+    evk_eval = ctx.evk_prepare(dev(prob.evk))
+    out = torch.empty(model.out_shape(), dtype=torch.int32, device="cuda")
+    model.eval(evk_eval, dev(prob.cts), [dev(p) for p in prob.pts], out, model.alloc_workspace())
+    assert np.array_equal(host(out), ref)
+    prof = model.profile_read()
+    model.profile_enable(False)
+    for k in ("mac", "square", "keyswitch", "moddown_rescale"):
+        assert prof[k][1] > 0 and prof[k][0] > 0, k
+
+
 def test_eval_host_path_matches_device_path(case):
     cfg, prob, ref = case
     ctx = bcn.Context.from_config(cfg)
