@@ -106,7 +106,7 @@ struct SqnOcc {
 };
 template <int LOGN, int R, bool IN_NTT>
 __global__ void __launch_bounds__((1 << LOGN) / R, IN_NTT ? SqnOcc<(1 << LOGN) / R, 64>::MIN_BLOCKS
-                                                          : SqnOcc<(1 << LOGN) / R, 64>::MIN_BLOCKS)
+                                                          : SqnOcc<(1 << LOGN) / R, R >= 32 ? 128 : 64>::MIN_BLOCKS)
     k_square_core(const uint32_t *__restrict__ Y, uint32_t *__restrict__ D, uint32_t *__restrict__ D2N, int n,
                   const PrimeConst *__restrict__ pc, const uint2 *__restrict__ twf, const uint2 *__restrict__ twi) {
     using C = NttCore<LOGN, R, true, kFmaSquare>;  // data primes only (q < 2^30): lazy butterflies
