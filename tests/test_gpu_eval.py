@@ -153,6 +153,32 @@ def test_eval_host_async_two_in_flight(case):
         assert np.array_equal(u32(o), ref)
 
 
+def mixed_depth_config():
+    """A square layer, a dense layer without add or square (its MAC runs on
+    NTT-domain ciphertexts with no feature), a dense layer with add and square
+    (NTT-domain features, square on NTT-domain input), a dense output layer:
+    N = 4096, 3 + 1 primes."""
+    cfg = workloads.with_batch(workloads.get_config("cnn3_small"), 512)
+    cfg["name"] = "mixed_depth"
+    cfg["cipher"] = [
+        dict(type="conv", cin=1, h=12, w=12, cout=5, k=5, stride=2, pad=0, add=True, square=True),
+        dict(type="dense", n_in=80, n_out=20, add=False, square=False),
+        dict(type="dense", n_in=20, n_out=12, add=True, square=True),
+        dict(type="dense", n_in=12, n_out=10, add=False, square=False),
+    ]
+    cfg["plain"] = cfg["plain"] + [dict(op="tap_fc", n_out=12)]
+    return cfg
+
+
+def test_eval_mixed_depth_bit_exact():
+    cfg = mixed_depth_config()
+    prob = O.Problem(cfg)
+    ref = prob.evaluate([])
+    ctx, model, _, got = run_gpu(cfg, prob.w_int, prob.s_w, prob.evk, prob.cts, prob.pts)
+    assert model.levels == prob.levels and model.out_level == prob.out_level
+    assert np.array_equal(got, ref), f"{np.mean(got != ref):.3%} of residues differ"
+
+
 def test_eval_is_deterministic_and_stream_ordered():
     cfg = workloads.with_batch(workloads.get_config("cnn3_small"), 128)
     prob = O.Problem(cfg)
