@@ -83,6 +83,9 @@ class ClockSampler:
         self.lines = []
 
     def start(self):
+        """Starts sampling and returns once the first sample is in: the
+        sampler's start-up (NVML initialisation) stays out of the timed region,
+        where it has been seen to stall the launching thread for tens of ms."""
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "100"],
@@ -91,6 +94,10 @@ class ClockSampler:
             self.t.start()
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        t0 = time.time()
+        while not self.lines and time.time() - t0 < 5.0 and self.proc.poll() is None:
+            time.sleep(0.01)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -734,6 +741,17 @@ def run_rotate(args, rank, world, local_rank):
 
 
 def main():
+    # no garbage-collector pause inside a timed step (the steps are timed on the
+    # device, and a host pause while a step is being enqueued idles the GPU)
+    import gc
+    gc.disable()
+    try:
+        _main()
+    finally:
+        gc.enable()
+
+
+def _main():
     args = parse()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
