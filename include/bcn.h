@@ -225,10 +225,11 @@ bcn_status bcn_model_destroy(bcn_model *m);
  * chunk's intermediates bounded by 1 GiB).  Changes bcn_eval_workspace_bytes;
  * results do not depend on it. */
 bcn_status bcn_model_set_chunk(bcn_model *m, int chunk);
-/* MAC implementation: 0 (default) runs the layer groups with at least 32
- * outputs and at most 512 taps on the tensor cores (the residues split into
- * byte planes, fp16 operands, exact fp32 sums), the rest on the CUDA cores;
- * 1 runs every MAC on the CUDA cores.  Results are identical either way. */
+/* MAC implementation: 0 (default) runs the layer groups with at most 512 taps
+ * and at least 32 outputs (or at least 10 outputs and 64 taps) on the tensor
+ * cores (the residues split into byte planes, fp16 operands, exact fp32 sums),
+ * the rest on the CUDA cores; 1 runs every MAC on the CUDA cores.  Results are
+ * identical either way. */
 bcn_status bcn_model_set_mac_impl(bcn_model *m, int impl);
 bcn_status bcn_model_get_info(const bcn_model *m, bcn_model_info *out);
 /* per layer: live level at its input and its output count (arrays of n_layers) */
@@ -251,8 +252,12 @@ bcn_status bcn_eval_workspace_bytes(const bcn_model *m, size_t *bytes);
  * square + relinearise + rescale.  cts_dev [n_in][2][L][N];
  * pts_dev[a] [n_out of the a-th add layer][its level][N] encoded at the scale
  * bcn_model_scales gives; out_dev [n_out][2][out_level][N].  All device
- * memory; evk_eval_dev from bcn_evk_prepare; workspace of at least
- * bcn_eval_workspace_bytes.  Asynchronous on `cuda_stream`. */
+ * memory in the interchange layout (coefficient form; between square layers
+ * the evaluation keeps ciphertexts in the NTT domain and transforms a copy of
+ * the features that join them, in the workspace); evk_eval_dev from
+ * bcn_evk_prepare; workspace of at least bcn_eval_workspace_bytes.
+ * Asynchronous on `cuda_stream` (it may also use the model's internal streams,
+ * forked from and joined back to `cuda_stream`). */
 bcn_status bcn_eval(const bcn_model *m, const uint32_t *evk_eval_dev, const uint32_t *cts_dev,
                     const uint32_t *const *pts_dev, uint32_t *out_dev, void *workspace_dev, size_t workspace_bytes,
                     void *cuda_stream);
