@@ -43,8 +43,8 @@ __global__ void __launch_bounds__((1 << LOGN) / R) k_ntt_inv(uint32_t *__restric
 
 // The lazy butterflies' additions selected by each kernel's FMA bits go
 // through the FMA pipe (ModQ::one read at run time) in blocks of at most 512
-// threads (128 registers); in the 1024-thread blocks of the N = 16384 square
-// kernel the compile-time 1 folds them back into plain additions.
+// threads (every block shape in use); in larger blocks the compile-time 1
+// folds them back into plain additions (measured slower there).
 template <int LOGN, int R>
 constexpr bool kFmaOne = (1 << LOGN) / R <= 512;
 
@@ -62,7 +62,7 @@ constexpr int kFmaSquare = BCN_FMA_SQ, kFmaKs = BCN_FMA_KS;
 
 // Pairs of independent transforms run in lockstep (shared twiddle loads and
 // barriers, twice the independent work per thread) where the registers allow
-// it: up to N = 8192.
+// it: 16 residues a thread, at most 512 threads.
 template <int LOGN, int R>
 constexpr bool kDual = (1 << LOGN) / R <= 512 && R <= 16;
 

@@ -650,3 +650,50 @@ def test_bhw_conv_by_rotations_is_the_convolution():
     assert np.abs(dm[:, :, :h - k + 1, :w - k + 1] - ref).max() < 1e-3
     dm[:, :, :h - k + 1, :w - k + 1] = 0
     assert np.abs(dm).max() < 1e-3
+
+
+@pytest.mark.parametrize("K", [1, 2])
+def test_ntt_domain_moddown_rescale_identity(K):
+    """ModDown by P followed by the rescale by the top prime, written in the NTT
+    domain the way the evaluator computes it -- the top limb
+    c_top = INTT(A_top P^-1 + D_top) - conv_top(a_P) P^-1 in coefficient form,
+    then out_i = (A_i P^-1 + D_i - NTT(conv_i(a_P) P^-1 + [c_top])) q_top^-1 --
+    equals the coefficient-form definition (centred fast basis conversion of the
+    P limbs, c_i = (a_i - conv_i) P^-1 + d_i, out_i = (c_i - [c_top]) q_top^-1)
+    residue for residue, on random limbs."""
+    P = O.Params(5, 4, K, 1)  # N = 32
+    N, n = P.N, 4
+    rng = np.random.default_rng(17 + K)
+    q, p = P.q[:n], P.p
+    a = [rng.integers(0, m, N, dtype=np.int64) for m in q + p]  # extended-basis limbs, coefficient form
+    d = [rng.integers(0, m, N, dtype=np.int64) for m in q]
+    Pprod = int(np.prod([int(v) for v in p], dtype=object))
+
+    def conv(i_mod):  # centred fast basis conversion of the P limbs into modulus i_mod
+        out = np.zeros(N, dtype=object)
+        cnt = np.zeros(N, dtype=np.int64)
+        for m, pm in enumerate(p):
+            phat = Pprod // pm
+            r = (a[n + m].astype(object) * pow(phat % pm, -1, pm)) % pm
+            cnt += (r > (pm - 1) // 2).astype(np.int64)
+            out = out + r * (phat % i_mod)
+        return np.array([(int(v) - int(c) * Pprod) % i_mod for v, c in zip(out, cnt)], dtype=np.int64)
+
+    top = n - 1
+    qt = q[top]
+    # coefficient-form definition
+    c = [((a[i] - conv(q[i])) % q[i] * pow(Pprod % q[i], -1, q[i]) + d[i]) % q[i] for i in range(n)]
+    lift = np.where(c[top] > (qt - 1) // 2, c[top] - qt, c[top])
+    ref = [((c[i] - lift) % q[i] * pow(qt, -1, q[i])) % q[i] for i in range(top)]
+    # NTT-domain form (the oracle's transform; any NTT of the same ring works)
+    A = [P.ntt_fwd(i, a[i].astype(np.uint32)).astype(np.int64) for i in range(n)]
+    D = [P.ntt_fwd(i, d[i].astype(np.uint32)).astype(np.int64) for i in range(n)]
+    pinv = [pow(Pprod % m, -1, m) for m in q]
+    ctop = (P.ntt_inv(top, ((A[top] * pinv[top] + D[top]) % qt).astype(np.uint32)).astype(np.int64)
+            - conv(qt) * pinv[top]) % qt
+    lt = np.where(ctop > (qt - 1) // 2, ctop - qt, ctop)
+    for i in range(top):
+        f = P.ntt_fwd(i, ((conv(q[i]) * pinv[i] + lt) % q[i]).astype(np.uint32)).astype(np.int64)
+        o = ((A[i] * pinv[i] + D[i] - f) % q[i] * pow(qt, -1, q[i])) % q[i]
+        got = P.ntt_inv(i, o.astype(np.uint32)).astype(np.int64)
+        assert np.array_equal(got, ref[i])
