@@ -329,6 +329,115 @@ def test_keyswitch_noise_bound(cfg):
         assert np.abs(noise).max() < 2.0**40
 
 
+def _ks_by_definition(q_data, p_special, alpha, level, x, evk):
+    """Hybrid key switching written out with Python integers (App. A Mult(c1, c2)
+    relinearisation; the variant read for this build): for each digit j (primes
+    q_{j alpha} .. q_{min((j+1) alpha, level) - 1}) the digit value is the
+    integer v_j = sum_i [x_i Dhat_i^-1]_{q_i} Dhat_i with centred residues
+    [.]_q in (-q/2, q/2] and Dhat_i the product of the digit's other primes;
+    its residue on a target prime t outside the digit is v_j mod t, on the
+    digit's own primes x_t itself.  acc_b = sum_j ext_j * evk_j,b (negacyclic
+    products by schoolbook, per prime of Q_level u P).  ModDown: the integer
+    u_b = sum_m [acc_b,m Phat_m^-1]_{p_m} Phat_m and
+    out_b,i = (acc_b,i - u_b) P^-1 mod q_i.  No NTT anywhere."""
+    N = x.shape[-1]
+    L, K = len(q_data), len(p_special)
+    targets = list(q_data[:level]) + list(p_special)
+    limb_of = list(range(level)) + [L + m for m in range(K)]  # target -> key limb
+    Pbig = 1
+    for p in p_special:
+        Pbig *= p
+
+    def cen(v, m):
+        v %= m
+        return v - m if v > (m - 1) // 2 else v
+
+    dnum = -(-level // alpha)
+    acc = [[[0] * N for _ in targets] for _ in range(2)]
+    for j in range(dnum):
+        lo, hi = j * alpha, min((j + 1) * alpha, level)
+        D = q_data[lo:hi]
+        Dbig = 1
+        for d in D:
+            Dbig *= d
+        v = [0] * N  # integer digit values
+        for i, qi in zip(range(lo, hi), D):
+            dhat = Dbig // qi
+            inv = pow(dhat % qi, -1, qi)
+            for k in range(N):
+                v[k] += cen(int(x[i, k]) * inv, qi) * dhat
+        for ti, t in enumerate(targets):
+            ext = [int(x[ti, k]) for k in range(N)] if lo <= ti < hi else [vk % t for vk in v]
+            for b in range(2):
+                key = [int(evk[j, b, limb_of[ti], k]) for k in range(N)]
+                prod = schoolbook(np.array(ext, dtype=object), np.array(key, dtype=object), t)
+                acc[b][ti] = [(a + int(pv)) % t for a, pv in zip(acc[b][ti], prod)]
+    out = np.zeros((2, level, N), dtype=np.int64)
+    for b in range(2):
+        u = [0] * N
+        for m, pm in enumerate(p_special):
+            phat = Pbig // pm
+            inv = pow(phat % pm, -1, pm)
+            for k in range(N):
+                u[k] += cen(acc[b][level + m][k] * inv, pm) * phat
+        for i in range(level):
+            qi = q_data[i]
+            pinv = pow(Pbig % qi, -1, qi)
+            out[b, i] = [((acc[b][i][k] - u[k]) * pinv) % qi for k in range(N)]
+    return out
+
+
+@pytest.mark.parametrize("cfg", [(4, 3, 1, 1), (4, 3, 2, 1), (4, 3, 2, 2), (4, 4, 2, 2)])
+def test_keyswitch_exact_by_definition(cfg):
+    """oc_keyswitch equals hybrid key switching computed from its definition with
+    Python big integers and schoolbook products (N = 16), residue for residue,
+    at the top level and below it (truncated last digits with alpha = 2), on
+    random inputs and a random key: pins the centred ModUp lift, the fast basis
+    conversion into every target prime, the key inner product and the centred
+    ModDown, which a noise bound alone cannot tell from their uncentred forms."""
+    P = O.Params(*cfg)
+    rng = np.random.default_rng(sum(cfg))
+    evk = np.zeros(P.evk_shape(), dtype=np.uint32)
+    for t, m in enumerate(P.primes):
+        evk[:, :, t] = rng.integers(0, m, size=evk[:, :, t].shape, dtype=np.uint64).astype(np.uint32)
+    for level in sorted({P.L, P.L - 1, 1}, reverse=True):
+        x = np.stack([rng.integers(0, q, P.N, dtype=np.uint64) for q in P.q[:level]]).astype(np.uint32)
+        # edge residues in the first coefficients: 0, 1, (q-1)/2, (q+1)/2, q-1
+        for i, q in enumerate(P.q[:level]):
+            x[i, :5] = [0, 1, (q - 1) // 2, (q + 1) // 2, q - 1]
+        got = P.keyswitch(level, evk, x[None])[0]
+        want = _ks_by_definition(P.q, P.p, P.alpha, level, x, evk)
+        assert np.array_equal(got.astype(np.int64), want), f"level {level}"
+
+
+@pytest.mark.parametrize("level", [4, 3, 2])
+def test_rescale_exact_by_definition(level):
+    """oc_rescale equals the rescale of the CRT integer: with X the centred
+    integer of a polynomial's limbs mod Q_level and r = [X]_{q_top} centred,
+    (X - r) / q_top is an exact integer whose residues are the output limbs
+    (at the top level and below it, with edge residues around q_top / 2)."""
+    P = O.Params(4, 4, 1, 1)
+    rng = np.random.default_rng(40 + level)
+    q = P.q[:level]
+    ct = np.stack([np.stack([rng.integers(0, m, P.N, dtype=np.uint64) for m in q]) for _ in range(2)])
+    qt = q[-1]
+    ct[:, -1, :4] = [(qt - 1) // 2, (qt + 1) // 2, 0, qt - 1]
+    ct = ct.astype(np.uint32)
+    got = P.rescale(level, ct[None])[0]
+    Q = 1
+    for m in q:
+        Q *= m
+    for b in range(2):
+        X = O.crt_centered(ct[b][None], q)[0]
+        for k in range(P.N):
+            xk = int(X[k])
+            r = xk % qt
+            r = r - qt if r > (qt - 1) // 2 else r
+            assert (xk - r) % qt == 0
+            y = (xk - r) // qt
+            assert [int(got[b, i, k]) for i in range(level - 1)] == [y % m for m in q[:-1]], (b, k)
+
+
 def test_relin_keeps_the_message(small):
     P = small
     sk, evk = P.keygen(3)
