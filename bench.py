@@ -2,16 +2,18 @@
 
 A step is one ciphertext-branch evaluation (every layer: integer-weight MAC,
 unidirectional feature add, square = tensor square + relinearisation +
-rescale) over one slot batch of the CryptoNets-scale workload: 4096 MNIST-
-shaped images, a 16x16 sensitive segment (256 ciphertexts), N = 8192, 7 data
-primes + 1 special prime, conv 5x5/2 -> add -> square -> dense 100 -> add ->
-square -> dense 10.  Inputs are seeded synthetic data made by the library's own
-client calls.  Replicas only across GPUs: every rank evaluates its own batch.
+rescale) over one slot batch of the CIFAR-shaped workload: 8192 CIFAR-shaped
+images, a 16x16x3 sensitive segment (768 ciphertexts), N = 16384, 11 data
+primes + 2 special primes (alpha 2), conv 3x3 x16 -> add -> square -> conv
+3x3/2 x32 -> add -> square -> dense 10.  Inputs are seeded synthetic data made
+by the library's own client calls.  Replicas only across GPUs: every rank
+evaluates its own batch.  --workload selects the smaller configurations and the
+batched, serving and rotation workloads.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle on the
-host cores instead (a bounded number of whole evaluations).
+host cores instead (bounded samples of one evaluation, projected to the whole).
 """
 from __future__ import annotations
 
@@ -35,7 +37,7 @@ import workloads  # noqa: E402
 
 METRIC = "encrypted inferences/s + p50/p99 latency; NTT/keyswitch HBM GB/s vs peak"
 UNIT = "encrypted inferences/s"
-WORKLOAD = "cryptonets"
+WORKLOAD = "cifar_cnn"
 
 
 E2E_LANES = 2  # workspaces used in turn by the end-to-end measurement
@@ -48,7 +50,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD,
-                    choices=list(workloads.CONFIGS) + ["uneven64", "serve", "rotate"])
+                    choices=list(workloads.CONFIGS) + ["uneven64", "serve", "rotate", "op_square", "op_mac"])
+    ap.add_argument("--cts", type=int, default=384, help="op_square: ciphertexts")
+    ap.add_argument("--map", type=int, default=8, help="op_mac: input map height and width")
     ap.add_argument("--rates", default="50,100,200,500,1000,2000", help="serve: request rates (req/s)")
     ap.add_argument("--serve-seconds", type=float, default=5.0, help="serve: seconds of arrivals per rate")
     ap.add_argument("--lanes", type=int, default=8, help="serve: lanes (concurrent requests)")
@@ -170,9 +174,10 @@ def int_peak_ops():
     return GB300_SMS * INT_LANES_PER_SM * mhz * 1e6, mhz
 
 
-def alu_ops(cfg):
-    """Algorithmic integer operations per evaluation of the NTT-based kernel
-    classes: {"square": ops, "keyswitch": ops, "moddown_rescale": ops}.
+def alu_work(cfg):
+    """Integer work per evaluation of the NTT-based kernel classes:
+    {"square" | "keyswitch" | "moddown_rescale": {"fwd": forward NTTs, "inv":
+    inverse NTTs, "mad": N-element multiply-add passes}}.
 
     From the first square layer on, ciphertexts stay in the NTT domain.  Tensor
     square of a ciphertext at n limbs: per limb 2 forward NTTs (only on
@@ -192,31 +197,52 @@ def alu_ops(cfg):
     import math
 
     import workloads
-    N, logN, K, a = 1 << cfg["log_n"], cfg["log_n"], cfg["n_special"], cfg["alpha"]
-    bf = (N // 2) * logN
+    K, a = cfg["n_special"], cfg["alpha"]
     levels, _ = workloads.level_schedule(cfg)
-    sq = ks = md = 0.0
+    w = {k: {"fwd": 0, "inv": 0, "mad": 0} for k in ("square", "keyswitch", "moddown_rescale")}
     in_ntt = False
     for layer, n in zip(cfg["cipher"], levels):
         n_out = workloads.cipher_layer_io(layer)[1]
         if layer["add"] and in_ntt:
-            sq += n_out * n * bf * OPS_BUTTERFLY
+            w["square"]["fwd"] += n_out * n
         if not layer["square"]:
             continue
         C = n_out
-        sq += C * (n * (1 if in_ntt else 3) * bf * OPS_BUTTERFLY + 4 * n * N * OPS_MULADD)
+        w["square"]["fwd"] += C * n * (0 if in_ntt else 2)
+        w["square"]["inv"] += C * n
+        w["square"]["mad"] += C * 4 * n
         digits = [min(a, n - j * a) for j in range(math.ceil(n / a))]
         nb = n + K
-        fwd = sum(nb - d for d in digits)
-        mads = sum(digits) + sum(d * (nb - d) for d in digits) + 2 * nb * len(digits) + 2 * (n - 1) + 4
-        ks += C * ((fwd + 2 * (K + 1)) * bf * OPS_BUTTERFLY + mads * N * OPS_MULADD)
-        md += C * 2 * (n - 1) * (bf * OPS_BUTTERFLY + (3 * K + 4) * N * OPS_MULADD)
+        w["keyswitch"]["fwd"] += C * sum(nb - d for d in digits)
+        w["keyswitch"]["inv"] += C * 2 * (K + 1)
+        w["keyswitch"]["mad"] += C * (sum(digits) + sum(d * (nb - d) for d in digits) + 2 * nb * len(digits)
+                                      + 2 * (n - 1) + 4)
+        w["moddown_rescale"]["fwd"] += C * 2 * (n - 1)
+        w["moddown_rescale"]["mad"] += C * 2 * (n - 1) * (3 * K + 4)
         in_ntt = True
     last = cfg["cipher"][-1]
     if in_ntt:
         lout = levels[-1] - (1 if last["square"] else 0)
-        sq += workloads.cipher_layer_io(last)[1] * 2 * lout * bf * OPS_BUTTERFLY
-    return {"square": sq, "keyswitch": ks, "moddown_rescale": md}
+        w["square"]["inv"] += workloads.cipher_layer_io(last)[1] * 2 * lout
+    return w
+
+
+def alu_ops(cfg):
+    """Algorithmic integer operations per evaluation of the NTT-based kernel
+    classes (alu_work: 10 per butterfly, (N/2) log N butterflies per NTT, 5 per
+    multiply-add, N per pass)."""
+    N, logN = 1 << cfg["log_n"], cfg["log_n"]
+    bf = (N // 2) * logN
+    return {k: (v["fwd"] + v["inv"]) * bf * OPS_BUTTERFLY + v["mad"] * N * OPS_MULADD
+            for k, v in alu_work(cfg).items()}
+
+
+def alu_units(cfg):
+    """The same work in the microbenchmark's units: {class: (forward
+    butterflies, inverse butterflies, multiply-adds)} per evaluation."""
+    N, logN = 1 << cfg["log_n"], cfg["log_n"]
+    bf = (N // 2) * logN
+    return {k: (v["fwd"] * bf, v["inv"] * bf, v["mad"] * N) for k, v in alu_work(cfg).items()}
 
 
 def csrc_hash():
@@ -258,46 +284,115 @@ def oracle_problem(cfg):
     return O, O.Problem(cfg)
 
 
-def oracle_time(cfg, max_evals: int, budget_s: float, single_thread: bool = False):
-    """Whole evaluations by the oracle with OpenMP on every core (bounded by
-    max_evals and budget_s); with single_thread, one more on one thread.
-    Returns (times, cores, single-thread time or None)."""
-    O, prob = oracle_problem(cfg)
+class OracleSample:
+    """A bounded sample of one evaluation by the oracle, projected to the whole
+    evaluation: per cipher layer the MAC of a subset of its outputs (with only
+    the input ciphertexts they read) and the square activation of a subset of
+    its ciphertexts, each timed and scaled by the layer's output count.  The
+    oracle's time does not depend on the residues' values, so the inputs are
+    uniform residues of the right shapes.  `scale` shrinks every subset (the
+    single-thread run)."""
+
+    MAC_OUTPUTS, SQUARE_CTS, DENSE_OUTPUTS = 64, 64, 2
+
+    def __init__(self, cfg, scale: float = 1.0, seed: int = 77):
+        from oracle import oracle as O
+
+        self.O, self.cfg = O, cfg
+        self.P = O.Params.from_config(cfg)
+        _, self.evk = self.P.keygen(workloads.SEED_KEYS)
+        w_int = [O.quantize(w)[0] for w in workloads.cipher_weights(cfg)]
+        self.levels, _ = workloads.level_schedule(cfg)
+        self.parts = []  # (kind, level, n_total, args)
+        rng_seed = seed
+        for layer, wi, n in zip(cfg["cipher"], w_int, self.levels):
+            idx, wt = O.layer_table(layer, wi)
+            n_out = idx.shape[0]
+            cap = self.MAC_OUTPUTS if layer["type"] == "conv" else self.DENSE_OUTPUTS
+            s_mac = max(1, min(n_out, int(round(cap * scale))))
+            # whole groups of outputs that read the same taps (a conv position's
+            # channels, a dense layer), so that the sample reads few inputs
+            _, first, inv = np.unique(idx, axis=0, return_index=True, return_inverse=True)
+            inv = np.asarray(inv).reshape(-1)
+            chosen = []
+            for gr in np.argsort(first):
+                chosen.extend(np.nonzero(inv == gr)[0].tolist())
+                if len(chosen) >= s_mac:
+                    break
+            chosen = np.array(chosen[:s_mac])
+            sel = idx[chosen]
+            used = np.unique(sel[sel >= 0])
+            remap = np.full(int(idx.max()) + 1 if idx.size else 1, -1, dtype=np.int32)
+            remap[used] = np.arange(used.size, dtype=np.int32)
+            sidx = np.where(sel >= 0, remap[np.maximum(sel, 0)], -1).astype(np.int32)
+            x = workloads.random_residues(self.P.q[:n], (max(1, used.size), 2), self.P.N, rng_seed)
+            rng_seed += 1
+            pt = workloads.random_residues(self.P.q[:n], (s_mac,), self.P.N, rng_seed) if layer["add"] else None
+            rng_seed += 1
+            self.parts.append(("mac", n, n_out, (sidx, wt[chosen], x, pt)))
+            if layer["square"]:
+                s_sq = max(1, min(n_out, int(round(self.SQUARE_CTS * scale))))
+                y = workloads.random_residues(self.P.q[:n], (s_sq, 2), self.P.N, rng_seed)
+                rng_seed += 1
+                self.parts.append(("square", n, n_out, (y,)))
+
+    def describe(self):
+        return "; ".join(
+            f"{k} at {n} limbs: {a[0].shape[0]} of {tot}" for k, n, tot, a in self.parts)
+
+    def run(self) -> float:
+        """Seconds one whole evaluation would take (sum of the scaled parts)."""
+        total = 0.0
+        for kind, n, n_total, a in self.parts:
+            t0 = time.perf_counter()
+            if kind == "mac":
+                self.P.mac(n, a[0], a[1], a[2], a[3])
+            else:
+                self.P.square_relin_rescale(n, self.evk, a[0])
+            total += (time.perf_counter() - t0) * n_total / a[0].shape[0]
+        return total
+
+
+def oracle_time(cfg, max_samples: int, budget_s: float, single_thread: bool = False):
+    """Projected seconds per whole evaluation by the oracle with OpenMP on every
+    core (OracleSample, up to max_samples samples within budget_s); with
+    single_thread, one more sample, 16x smaller, on one thread.  Returns
+    (projected times, cores, single-thread projection or None, sample text)."""
+    from oracle import oracle as O
+
+    samp = OracleSample(cfg)
     times = []
     t_start = time.perf_counter()
-    for _ in range(max_evals):
-        t0 = time.perf_counter()
-        prob.evaluate()
-        times.append(time.perf_counter() - t0)
+    for _ in range(max_samples):
+        times.append(samp.run())
         if time.perf_counter() - t_start > budget_s:
             break
     cores = O.max_threads()
     t1 = None
     if single_thread:
+        small = OracleSample(cfg, scale=1.0 / 16)
         O.set_threads(1)
         try:
-            t0 = time.perf_counter()
-            prob.evaluate()
-            t1 = time.perf_counter() - t0
+            t1 = small.run()
         finally:
             O.set_threads(cores)
-    return times, cores, t1
+    return times, cores, t1, samp.describe()
 
 
 def run_reference(args, cfg, rank, world):
     if rank != 0:
         return
+    from oracle import oracle as O
+
     W = min(args.warmup, 1)
     K = max(1, args.steps)
-    O, prob = oracle_problem(cfg)
+    samp = OracleSample(cfg)
     for _ in range(W):
-        prob.evaluate()
+        samp.run()
     times = []
     t_start = time.perf_counter()
     for _ in range(K):
-        t0 = time.perf_counter()
-        prob.evaluate()
-        times.append(time.perf_counter() - t0)
+        times.append(samp.run())
         if time.perf_counter() - t_start > args.ref_budget_s:
             break
     mean = statistics.mean(times)
@@ -308,8 +403,9 @@ def run_reference(args, cfg, rank, world):
         "dtype": "u32", "data": "synthetic", "config": config_desc(cfg),
         "p50_ms": statistics.median(times) * 1e3, "p99_ms": float(np.percentile(times, 99)) * 1e3,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
-                         "sample": f"{len(times)} whole evaluations of the workload (of {K} requested; wall budget "
-                                   f"{args.ref_budget_s:.0f} s), inputs prepared outside the timed region"},
+                         "sample": f"{len(times)} steps (of {K} requested; wall budget {args.ref_budget_s:.0f} s), "
+                                   f"each a timed sample of one evaluation projected to the whole by the layers' "
+                                   f"output counts: {samp.describe()}; inputs prepared outside the timing"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -372,6 +468,14 @@ def run_ours(args, cfg, rank, world, local_rank):
     for _ in range(max(3, args.warmup)):
         model.eval(evk_eval, cts_d, pts_d, out, ws)
     torch.cuda.synchronize()
+
+    # integer-issue rates of this GPU (register-resident butterflies and
+    # multiply-adds): the roofline of the NTT-based kernels, measured here
+    from paper_2402_01296_gb300 import peak as peak_mod
+    pclk = ClockSampler(device)
+    pclk.start()
+    rates = peak_mod.measure(device)
+    peak_clocks = pclk.stop()
 
     K = args.steps
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
@@ -448,15 +552,21 @@ def run_ours(args, cfg, rank, world, local_rank):
     dom = max(prof, key=lambda k: prof[k][0])
     dms, dn, dbytes = prof[dom]
     ops = alu_ops(cfg)
+    units = alu_units(cfg)
+    mix = {k: peak_mod.mix_peak(rates, *units[k]) for k in ops}
     traffic = ncu_traffic(dom, cfg["name"], ks_units(cfg) * K / dn) if dom == "keyswitch" and dn else None
+    dpeak, mhz = int_peak_ops()
     if dom in ops:
-        ipeak, mhz = int_peak_ops()
         achieved = ops[dom] * K / (dms / 1e3) / 1e12
-        roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": ipeak / 1e12, "unit": "Tintop/s",
-                "frac": achieved * 1e12 / ipeak, "traffic": traffic,
+        roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": mix[dom] / 1e12, "unit": "Tintop/s",
+                "frac": achieved * 1e12 / mix[dom], "traffic": traffic,
                 "traffic_source": "ncu dram bytes per block of this kernel (profiles/ncu_traffic.json) x blocks per "
                                   "launch of this run" if traffic else None,
-                "peak_source": f"derived: {GB300_SMS} SMs x {INT_LANES_PER_SM} int32 lanes x {mhz:.0f} MHz",
+                "peak_source": "measured in this run: register-resident rates of the evaluator's own lazy forward "
+                               "and inverse butterflies and Montgomery multiply-adds (bcn_int_peak_launch, full "
+                               "occupancy), weighted by this kernel's mix of the three",
+                "derived_peak": dpeak / 1e12,
+                "derived_peak_source": f"{GB300_SMS} SMs x {INT_LANES_PER_SM} int32 lanes x {mhz:.0f} MHz",
                 "ops_per_launch": ops[dom] * K / dn,
                 "hbm_achieved_GBps": (dbytes / (dms / 1e3)) / 1e9, "hbm_peak_GBps": measured_peaks()[0]}
     else:
@@ -478,12 +588,13 @@ def run_ours(args, cfg, rank, world, local_rank):
         return
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        times, cores, t1 = oracle_time(cfg, max_evals=3, budget_s=30.0, single_thread=True)
+        times, cores, t1, desc = oracle_time(cfg, max_samples=3, budget_s=30.0, single_thread=True)
         cpu = {"value": B / statistics.mean(times), "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{len(times)} whole evaluation(s) of the same workload ({B} images each) by the C oracle "
-                         f"with OpenMP over ciphertexts; inputs prepared outside the timing",
+               "sample": f"{len(times)} timed sample(s) of one evaluation of the same workload ({B} images) by the "
+                         f"C oracle with OpenMP over outputs, each projected to the whole evaluation by the layers' "
+                         f"output counts ({desc}); inputs prepared outside the timing",
                "single_thread": {"value": B / t1, "unit": UNIT, "cores": 1,
-                                 "sample": "one whole evaluation of the same workload on one thread"}}
+                                 "sample": "the same projection from a 16x smaller sample on one thread"}}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": max(3, args.warmup),
         "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
@@ -496,7 +607,15 @@ def run_ours(args, cfg, rank, world, local_rank):
                               "inputs copy while the step before it computes"},
         "gpu_launches": int(launches),
         "roofline": roof,
-        "alu_frac": {k: ops[k] * K / (prof[k][0] / 1e3) / int_peak_ops()[0] for k in ops if prof[k][0]},
+        "alu_frac": {k: ops[k] * K / (prof[k][0] / 1e3) / mix[k] for k in ops if prof[k][0]},
+        "alu_frac_of_derived_peak": {k: ops[k] * K / (prof[k][0] / 1e3) / dpeak for k in ops if prof[k][0]},
+        "int_peak": {"rates_per_s": {k: v["units_per_s"] for k, v in rates.items()},
+                     "per_sm_per_clk": {k: v["units_per_s"] / GB300_SMS / (peak_clocks["sm_mhz"] * 1e6)
+                                        for k, v in rates.items()} if peak_clocks.get("sm_mhz") else None,
+                     "mix_peak_Tops": {k: v / 1e12 for k, v in mix.items()},
+                     "clocks": peak_clocks,
+                     "units": "instructions (imad_lo, imad_hi), modular additions (modadd), butterflies "
+                              "(butterfly_fwd, butterfly_inv), multiply-adds (mont_muladd)"},
         "ntt_GBps": ntt_b / (ntt_ms / 1e3) / 1e9 if ntt_ms else None,
         "keyswitch_GBps": ks_b / (ks_ms / 1e3) / 1e9 if ks_ms else None,
         "kernels": kernels,
@@ -755,6 +874,73 @@ def run_rotate(args, rank, world, local_rank):
                           "rotations": res}), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# op-level workloads (small cases for kernel profiles)
+# ---------------------------------------------------------------------------
+def run_op(args, rank, world, local_rank):
+    """One operation of the CIFAR-shaped network on a bounded number of
+    ciphertexts, L2 flushed between timed steps: `op_square` is the square
+    activation (tensor square, key switch, ModDown, rescale) of --cts
+    ciphertexts at the top level (N = 16384, 11 + 2 primes, alpha 2); `op_mac`
+    is one layer shaped like the network's second convolution (16 -> 32 maps,
+    3x3, stride 2, padding 1) on a --map x --map input at 11 limbs, on the
+    tensor cores."""
+    import torch
+
+    from paper_2402_01296_gb300 import bcn
+
+    device = local_rank
+    torch.cuda.set_device(device)
+    dev = f"cuda:{device}"
+    cfg = workloads.get_config("cifar_cnn")
+    ctx = bcn.Context.from_config(cfg, device)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(workloads.SEED_ENC)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    if args.workload == "op_square":
+        n = args.cts
+        _, ek = ctx.keygen(workloads.SEED_KEYS)
+        evk = ctx.evk_prepare(bcn.to_device(ek, dev))
+        x = _dev_residues(torch, ctx.q, (n, 2), ctx.N, gen, dev)
+        out = torch.empty((n, 2, ctx.L - 1, ctx.N), dtype=torch.int32, device=dev)
+        run = lambda: ctx.op_square_relin_rescale(ctx.L, evk, x, n, out)  # noqa: E731
+        what, unit = f"op_square: {n} ciphertexts at 11 limbs, N=16384, 11+2 primes, alpha 2", "squares/s"
+    else:
+        hw = args.map
+        layer = dict(type="conv", cin=16, h=hw, w=hw, cout=32, k=3, stride=2, pad=1, add=True, square=False)
+        n_in, n = workloads.cipher_layer_io(layer)
+        w = np.random.default_rng(workloads.SEED_WEIGHTS).integers(-127, 128, (32, 16, 3, 3)).astype(np.int8)
+        m = bcn.Model(ctx, [layer], [w], [1.0])
+        x = _dev_residues(torch, ctx.q, (n_in, 2), ctx.N, gen, dev)
+        pt = [_dev_residues(torch, ctx.q, (n,), ctx.N, gen, dev)]
+        out = torch.empty(m.out_shape(), dtype=torch.int32, device=dev)
+        ws = m.alloc_workspace()
+        key = torch.zeros(ctx.evk_words(), dtype=torch.int32, device=dev)  # no square: the key is not read
+        run = lambda: m.eval(key, x, pt, out, ws)  # noqa: E731
+        what, unit = f"op_mac: conv 16->32 3x3/2 pad 1 on {hw}x{hw} ({n_in} -> {n} ciphertexts, 11 limbs)", "outputs/s"
+    for _ in range(max(3, args.warmup)):
+        run()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s_.record(stream)
+        run()
+        e_.record(stream)
+        torch.cuda.synchronize()
+        ms.append(s_.elapsed_time(e_))
+    t = statistics.mean(ms)
+    if rank == 0:
+        print(json.dumps({"metric": unit, "value": n / (t / 1e3), "unit": unit, "n_gpus": world,
+                          "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": t,
+                          "higher_is_better": True, "dtype": "u32", "data": "synthetic (uniform residues)",
+                          "config": {"workload": what,
+                                     "l2": "flushed (512 MiB write) between timed steps, outside the events"}}),
+              flush=True)
+
+
 def main():
     # no garbage-collector pause inside a timed step (the steps are timed on the
     # device, and a host pause while a step is being enqueued idles the GPU)
@@ -777,6 +963,8 @@ def _main():
         return run_serve(args, rank, world, local_rank)
     if args.workload == "rotate":
         return run_rotate(args, rank, world, local_rank)
+    if args.workload in ("op_square", "op_mac"):
+        return run_op(args, rank, world, local_rank)
     cfg = workloads.get_config(args.workload)
     if args.impl == "reference":
         run_reference(args, cfg, rank, world)

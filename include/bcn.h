@@ -143,9 +143,13 @@ bcn_status bcn_encrypt(const bcn_ctx *ctx, const int8_t *sk, const uint32_t *pts
 bcn_status bcn_encrypt_segment(const bcn_ctx *ctx, const int8_t *sk, const uint8_t *images, int B, int H, int W,
                                int C, const int seg[4], double scale, uint64_t seed, uint32_t *cts_out);
 
-/* Decrypt m = c0 + c1 s (mod q_i), recombine the residues into the centred
- * integer (balanced-digit Garner CRT, exact), decode the first B slots and
- * divide by `scale`.  cts [n_ct][2][level][N] -> out [n_ct][B].  Host. */
+/* The client's last step (Sec. 2 threat model: only the client can decrypt
+ * the inference result; App. A: the decryption function D, and the N/2 slots
+ * that carry one value each): decrypt m = c0 + c1 s (mod q_i), recombine the
+ * residues into the centred integer (balanced-digit Garner CRT, exact), decode
+ * the first B slots and divide by `scale`.  cts [n_ct][2][level][N] -> out
+ * [n_ct][B], host memory; BCN_E_INVAL on a null buffer, a level outside
+ * 1..L or B outside 0..N/2. */
 bcn_status bcn_decrypt_decode(const bcn_ctx *ctx, const int8_t *sk, const uint32_t *cts, int n_ct, int level,
                               double scale, int B, double *out);
 
@@ -247,7 +251,11 @@ bcn_status bcn_evk_prepare(const bcn_ctx *ctx, const uint32_t *evk_dev, uint32_t
 
 bcn_status bcn_eval_workspace_bytes(const bcn_model *m, size_t *bytes);
 
-/* Ciphertext-branch evaluation (the hot path): for each layer the integer
+/* Ciphertext-branch evaluation (the hot path; Sec. 3.2: the ciphertext
+ * branch with its unidirectional connections x_{c,l} + CRot(Resize(x_{p,l})),
+ * built from the CKKS operations of App. A -- Mult(c, u) with the integer
+ * weights, Add(c1, c2) for the sums, Add(c, u) for the features, Mult(c1, c2)
+ * for the square activation of App. B): for each layer the integer
  * weight multiply-accumulate, the optional feature add, the optional
  * square + relinearise + rescale.  cts_dev [n_in][2][L][N];
  * pts_dev[a] [n_out of the a-th add layer][its level][N] encoded at the scale
@@ -257,7 +265,10 @@ bcn_status bcn_eval_workspace_bytes(const bcn_model *m, size_t *bytes);
  * the features that join them, in the workspace); evk_eval_dev from
  * bcn_evk_prepare; workspace of at least bcn_eval_workspace_bytes.
  * Asynchronous on `cuda_stream` (it may also use the model's internal streams,
- * forked from and joined back to `cuda_stream`). */
+ * forked from and joined back to `cuda_stream`).  Errors: BCN_E_BUDGET if the
+ * workspace is smaller than bcn_eval_workspace_bytes, BCN_E_INVAL on a null or
+ * unaligned (16-byte) buffer or a missing feature plaintext, BCN_E_CUDA if a
+ * launch fails; nothing is written to out_dev before the first launch. */
 bcn_status bcn_eval(const bcn_model *m, const uint32_t *evk_eval_dev, const uint32_t *cts_dev,
                     const uint32_t *const *pts_dev, uint32_t *out_dev, void *workspace_dev, size_t workspace_bytes,
                     void *cuda_stream);
@@ -368,7 +379,9 @@ bcn_status bcn_op_square_relin_rescale(const bcn_ctx *ctx, int level, const uint
  * chunks that fit it; BCN_E_BUDGET if a single ciphertext at `level` does not.
  * The first call on a device looks the array's device address up (once per
  * device, with that device current); make that first call before any stream
- * capture.  Every call shares the array, so calls that overlap on the GPU (other
+ * capture.  The address is kept for the life of the process: a device reset
+ * (cudaDeviceReset, or a reset of the primary context) unloads the module and
+ * leaves it stale, so do not call this entry point after one.  Every call shares the array, so calls that overlap on the GPU (other
  * streams, other threads) race; nothing in it has to start at zero (each word is
  * written before it is read within a call).  Same layouts, results and errors
  * as bcn_op_square_relin_rescale; allocates nothing (no cudaMalloc/cudaFree, no
@@ -405,6 +418,29 @@ bcn_status bcn_op_mul_plain_rescale(const bcn_ctx *ctx, int level, const uint32_
                                     size_t workspace_bytes, void *cuda_stream);
 bcn_status bcn_op_rescale(const bcn_ctx *ctx, int level, const uint32_t *in_dev, int n_ct, uint32_t *out_dev,
                           void *cuda_stream);
+
+/* ------------------------------------------- measurement (device) */
+/* Integer-issue microbenchmark: the ceiling the NTT-based kernels' arithmetic
+ * is reported against (the paper has no counterpart; it measures nothing on a
+ * GPU).  One launch on the current device and `cuda_stream` (asynchronous):
+ * every thread of a full-occupancy grid of 256-thread blocks runs `iters`
+ * rounds of one sequence on 16 register-resident words.  kind:
+ *   0  32-bit multiply-add, low half (16 a round)
+ *   1  32-bit multiply-add, high half with an addend (16 a round)
+ *   2  modular addition: add, then min(y, y - q) (16 a round)
+ *   3  lazy forward NTT butterflies of the evaluator's NTT core (32 a round)
+ *   4  lazy inverse NTT butterflies of the evaluator's NTT core (32 a round)
+ *   5  lazy Montgomery multiply-add of the key switch's running sums (16 a round)
+ * units_out: the operations the launch performs (instructions for kinds 0-1,
+ * modular additions, butterflies or multiply-adds for 2-5), to divide by the
+ * launch's time.  sink_dev: device memory of at least bcn_int_peak_grid's
+ * block count in uint32 words (written only if a result equals an improbable
+ * value; it keeps the work from being optimised away).  BCN_E_INVAL for a kind
+ * outside 0..5, iters < 1 or a null pointer; BCN_E_BUDGET if the sink is too
+ * small. */
+bcn_status bcn_int_peak_grid(int kind, int *blocks);
+bcn_status bcn_int_peak_launch(int kind, int iters, uint32_t *sink_dev, size_t sink_words, void *cuda_stream,
+                               double *units_out);
 
 #ifdef __cplusplus
 }

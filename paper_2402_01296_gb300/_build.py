@@ -59,7 +59,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
         objs = list(ex.map(compile_one, sources()))
     tmp = OUT / f"libbcn.{os.getpid()}.so"
-    cmd = [nv, "-shared", *ARCH, "-o", str(tmp), *map(str, objs), "-lpthread"]
+    cmd = [nv, "-shared", *ARCH, "-o", str(tmp), *map(str, objs), "-lpthread", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")

@@ -109,6 +109,8 @@ _SIGS = {
     "bcn_galois_keygen": (_I, [_P, _P, _I, _U64, _P]),
     "bcn_op_rotate": (_I, [_P, _I, _P, _I, _P, _I, _P, _P, _SZ, _P]),
     "bcn_op_square_relin_rescale_noalloc": (_I, [_P, _I, _P, _P, _I, _P, _P]),
+    "bcn_int_peak_grid": (_I, [_I, ctypes.POINTER(_I)]),
+    "bcn_int_peak_launch": (_I, [_I, _I, _P, _SZ, _P, ctypes.POINTER(_D)]),
 }
 
 _lock = threading.Lock()

@@ -2,10 +2,21 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "bcn_internal.h"
 
 namespace bcn {
+
+// Host-side NVTX range: names the library's phases (an evaluation, its layers,
+// each kernel class's launches) on a profiler's timeline.  Header-only NVTX:
+// with no tool attached a push or pop is a check of one function pointer.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // prime map of a buffer whose limbs cycle through the data primes q_0..q_{level-1}
 inline PrimeMap data_map(int level) { return PrimeMap{level, level, 0}; }

@@ -13,6 +13,7 @@
 // square kernel takes them there, ModDown and rescale return them there, the
 // MAC and the feature add are linear; the outputs return to coefficient form.
 #include <algorithm>
+#include <cstdio>
 #include <cuda_runtime.h>
 
 #include "device_api.h"
@@ -230,15 +231,20 @@ static bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 
 static size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 
-// CUDA-event pair around one launch when the model's profiler is on
+// names of the kernel classes (NVTX ranges)
+static const char *const kClassName[BCN_KERNEL_COUNT] = {"mac", "square", "keyswitch", "moddown_rescale"};
+
+// CUDA-event pair around one launch when the model's profiler is on; an NVTX
+// range named by the kernel class always
 struct Timed {
+    NvtxRange range;
     Profiler *p;
     cudaStream_t st;
     int cls;
     double bytes;
     size_t e0 = 0;
     Timed(Profiler *p_, cudaStream_t st_, int cls_, double bytes_)
-        : p(p_ && p_->on ? p_ : nullptr), st(st_), cls(cls_), bytes(bytes_) {
+        : range(kClassName[cls_]), p(p_ && p_->on ? p_ : nullptr), st(st_), cls(cls_), bytes(bytes_) {
         if (p) e0 = mark();
     }
     size_t mark() {
@@ -684,6 +690,7 @@ static bcn_status eval_impl(const bcn_model *m, const uint32_t *evk, const uint3
                             uint32_t *out, void *ws, size_t ws_bytes, void *stream,
                             const std::vector<std::vector<cudaEvent_t>> *layer_ready) {
     if (!m) return fail(BCN_E_INVAL, "bcn_eval: null model");
+    NvtxRange r_eval("bcn_eval");
     const bcn_ctx *c = m->ctx;
     BCN_TRY(check_device(c));
     size_t need = 0;
@@ -790,6 +797,9 @@ static bcn_status eval_impl(const bcn_model *m, const uint32_t *evk, const uint3
     Profiler *prof = &m->prof;
     for (size_t l = 0; l < m->layers.size(); l++) {
         const bcn_layer_plan &p = m->layers[l];
+        char lname[32];
+        snprintf(lname, sizeof lname, "layer %d", (int)l);
+        NvtxRange r_layer(lname);
         const bool last = l + 1 == m->layers.size();
         uint32_t *y = last ? out : X[l % 2];
         if (layer_ready != nullptr)

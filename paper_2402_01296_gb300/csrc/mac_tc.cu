@@ -188,7 +188,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_mac_tc(const uint32_t *__restri
     const uint32_t idesc = instr_desc(kRows, NT);
     const uint32_t sbo_b = (uint32_t)(Kpad / 8) * 128;
 
-    for (int sl = 0; sl < n_slabs; sl++) {
+    int sl = 0;  // after the loop: the slabs whose MMAs were issued and committed
+    for (; sl < n_slabs; sl++) {
         // keep kStages - 1 slabs in flight: issue slab sl + kStages - 1 (its
         // stage was converted at iteration sl - 1), then wait for slab sl
         {
@@ -249,9 +250,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_mac_tc(const uint32_t *__restri
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb));
         }
     }
-    // the last commit tracks every MMA before it
-    if (tid == 0 && *flag == 0 && n_slabs > 0) {
-        const int last = n_slabs - 1;
+    // The last commit tracks every MMA issued before it.  On the normal path
+    // this is the wait for the whole contraction.  After a timed-out wait (the
+    // loop stopped before committing slab sl) it drains the MMAs still in
+    // flight, again bounded, so that neither shared memory nor tensor memory
+    // is released while they may read or write it; only if that wait gives up
+    // too does the CTA go on to free its tensor memory regardless (there is no
+    // unbounded way left that keeps the GPU answering).
+    if (tid == 0 && sl > 0) {
+        const int last = sl - 1;
         if (!mbar_wait(mb0 + (uint32_t)((last % kABuf) * 8), (uint32_t)((last / kABuf) & 1))) *flag = 1;
     }
     __syncthreads();

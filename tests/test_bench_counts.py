@@ -15,10 +15,10 @@ import workloads
 
 
 def enumerate_work(cfg):
-    """{class: (NTTs, N-element multiply-add passes)} per evaluation."""
+    """{class: [forward NTTs, N-element multiply-add passes, inverse NTTs]} per evaluation."""
     N, logN, K, a = 1 << cfg["log_n"], cfg["log_n"], cfg["n_special"], cfg["alpha"]
     levels, _ = workloads.level_schedule(cfg)
-    work = {"square": [0, 0], "keyswitch": [0, 0], "moddown_rescale": [0, 0]}
+    work = {"square": [0, 0, 0], "keyswitch": [0, 0, 0], "moddown_rescale": [0, 0, 0]}
     in_ntt = False
     for layer, n in zip(cfg["cipher"], levels):
         C = workloads.cipher_layer_io(layer)[1]
@@ -28,7 +28,8 @@ def enumerate_work(cfg):
             continue
         for _ in range(C):
             for _limb in range(n):
-                work["square"][0] += 1 if in_ntt else 3
+                work["square"][0] += 0 if in_ntt else 2  # c0, c1 to the NTT domain
+                work["square"][2] += 1  # d2 back to coefficient form
                 work["square"][1] += 4  # c0^2, 2 c0 c1, c1^2 and c1^2 / N
             targets = list(range(n)) + [("p", m) for m in range(K)]
             digits = [list(range(j * a, min(n, j * a + a))) for j in range(math.ceil(n / a))]
@@ -41,7 +42,7 @@ def enumerate_work(cfg):
                     work["keyswitch"][1] += 2  # both key halves
             for t in targets:
                 if isinstance(t, tuple) or t == n - 1:
-                    work["keyswitch"][0] += 2  # inverse NTT of both sums
+                    work["keyswitch"][2] += 2  # inverse NTT of both sums
                     if t == n - 1:
                         work["keyswitch"][1] += 4  # the rescale's first step, both polys
                 else:
@@ -54,7 +55,7 @@ def enumerate_work(cfg):
     if in_ntt:
         last = cfg["cipher"][-1]
         lout = levels[-1] - (1 if last["square"] else 0)
-        work["square"][0] += workloads.cipher_layer_io(last)[1] * 2 * lout
+        work["square"][2] += workloads.cipher_layer_io(last)[1] * 2 * lout
     return work, N, logN
 
 
@@ -64,8 +65,10 @@ def test_alu_ops_match_enumeration(name):
     work, N, logN = enumerate_work(cfg)
     ops = bench.alu_ops(cfg)
     bf = (N // 2) * logN * bench.OPS_BUTTERFLY
-    for k, (n_ntt, passes) in work.items():
-        assert ops[k] == n_ntt * bf + passes * N * bench.OPS_MULADD, k
+    split = bench.alu_work(cfg)
+    for k, (n_fwd, passes, n_inv) in work.items():
+        assert ops[k] == (n_fwd + n_inv) * bf + passes * N * bench.OPS_MULADD, k
+        assert (split[k]["fwd"], split[k]["inv"], split[k]["mad"]) == (n_fwd, n_inv, passes), k
 
 
 def test_cryptonets_ntt_counts_by_hand():
@@ -73,7 +76,10 @@ def test_cryptonets_ntt_counts_by_hand():
     180 ciphertexts, layer 2 at n = 6 with 100."""
     work, _, _ = enumerate_work(workloads.get_config("cryptonets"))
     # key switch: 7 digits x 7 foreign targets of 8, plus 4 inverses, per ciphertext
-    assert work["keyswitch"][0] == 180 * (7 * 7 + 4) + 100 * (6 * 6 + 4)
+    assert work["keyswitch"][0] == 180 * 7 * 7 + 100 * 6 * 6
+    assert work["keyswitch"][2] == 180 * 4 + 100 * 4
     assert work["moddown_rescale"][0] == 180 * 12 + 100 * 10
-    # square: 3 per limb on layer 1, 1 per limb on layer 2, the layer-2 features, the outputs (10 x 2 x 5)
-    assert work["square"][0] == 180 * 7 * 3 + 100 * 6 * 1 + 100 * 6 + 10 * 2 * 5
+    # square: forward 2 per limb on layer 1 and the layer-2 features; inverse 1 per limb of both layers
+    # and the outputs (10 x 2 x 5)
+    assert work["square"][0] == 180 * 7 * 2 + 100 * 6
+    assert work["square"][2] == 180 * 7 + 100 * 6 + 10 * 2 * 5

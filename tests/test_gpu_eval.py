@@ -47,15 +47,35 @@ def run_gpu(cfg, w_int, s_w, evk, cts, pts):
 CASES = {
     "cnn3_small": lambda: workloads.get_config("cnn3_small"),
     "cryptonets": lambda: workloads.get_config("cryptonets"),
+    "cryptonets_planted": lambda: workloads.get_config("cryptonets"),
     "cryptonets_fi": lambda: workloads.get_config("cryptonets_fi"),
     "cifar_reduced": lambda: workloads.reduced_cifar(cout1=2, cout2=3, seg=8, batch=512),
 }
+# cases whose plaintext-branch features are replaced by seeded nonzero values
+PLANTED = {"cryptonets_planted"}
+
+
+def plant_features(prob, seed=91):
+    """Replace every tap's features by seeded values in [-0.5, 0.5) and
+    re-encode them with the oracle at the same scales and levels.  The
+    CryptoNets-scale branch's conv tap is a centre crop that falls inside the
+    zero-filled segment, so its real features are exactly zero; planted ones
+    make the first feature add (and everything after it) see nonzero data."""
+    rng = np.random.default_rng(seed)
+    P = prob.params
+    adds = [lv for layer, lv in zip(prob.cfg["cipher"], prob.levels) if layer["add"]]
+    for fi, lv in enumerate(adds):
+        prob.feats[fi] = rng.uniform(-0.5, 0.5, size=prob.feats[fi].shape)
+        prob.pts[fi] = O.encode(prob.feats[fi], P.N, prob.add_scales[fi], P.q[:lv])
+    assert all(np.abs(f).max() > 0.1 for f in prob.feats)
 
 
 @pytest.fixture(scope="module", params=list(CASES))
 def case(request):
     cfg = CASES[request.param]()
     prob = O.Problem(cfg)
+    if request.param in PLANTED:
+        plant_features(prob)
     trace = []
     ref = prob.evaluate(trace)
     return cfg, prob, ref
@@ -66,6 +86,7 @@ def test_eval_bit_exact(case):
     ctx, model, _, got = run_gpu(cfg, prob.w_int, prob.s_w, prob.evk, prob.cts, prob.pts)
     assert got.shape == ref.shape
     assert np.array_equal(got, ref), f"{np.mean(got != ref):.3%} of residues differ"
+    assert ctx.device_status() == 0
     # scale schedule and levels agree with the oracle's bookkeeping
     adds, out_scale = model.scales(2.0 ** cfg["log_scale"])
     assert adds == prob.add_scales and out_scale == prob.out_scale

@@ -95,3 +95,54 @@ def test_conv_with_padding_matches_cuda_cores():
                                 idx[o, t] = (ci * 9 + iy) * 7 + ix
                                 wt[o, t] = w[co, ci, ky, kx]
     assert np.array_equal(got, P.mac(P.L, idx, wt, x, pt))
+
+
+def test_cifar_conv2_shape_at_full_ring():
+    """The CIFAR-shaped second convolution's groups (16 -> 32 channels, 3x3,
+    stride 2, padding 1: 144 taps x 32 outputs, on the tensor cores) at
+    N = 16384 with its 10 live limbs of the 11 + 2 prime chain and the feature
+    add, on a 4 x 4 map (border positions with zero taps, inner ones with all
+    144): bit-exact against the oracle and the CUDA-core MAC."""
+    c, P = pair((14, 11, 2, 2))
+    level = 10
+    layer = dict(type="conv", cin=16, h=4, w=4, cout=32, k=3, stride=2, pad=1, add=True, square=False)
+    rng = np.random.default_rng(23)
+    w = rng.integers(-127, 128, size=(32, 16, 3, 3)).astype(np.int8)
+    w[0] = 127
+    w[1] = -127
+    n_in, n_out = workloads.cipher_layer_io(layer)
+    x = workloads.random_residues(P.q[:level], (n_in, 2), P.N, 24)
+    x[:3] = np.array(P.q[:level], dtype=np.uint32)[None, None, :, None] - 1  # residues at q - 1
+    pt = workloads.random_residues(P.q[:level], (n_out,), P.N, 25)
+    # the model runs at the chain's top level: evaluate at level 10 through the op entry point
+    idx, wt = O.layer_table(layer, w)  # [n_out][144] input index (-1: padding) and weight
+    want = P.mac(level, idx, wt, x, pt)
+    got = torch.full((n_out, 2, level, P.N), -1, dtype=torch.int32, device="cuda")
+    c.op_mac(level, n_in, torch.from_numpy(idx).cuda(), torch.from_numpy(wt).cuda(), bcn.to_device(x),
+             bcn.to_device(pt), got)
+    assert np.array_equal(host(got), want)
+    # the model path (tensor cores, groups of 32 outputs) on the same layer at the top level
+    xl = workloads.random_residues(P.q, (n_in, 2), P.N, 26)
+    ptl = workloads.random_residues(P.q, (n_out,), P.N, 27)
+    tc = run_model(c, layer, w, xl, ptl, 0)
+    assert np.array_equal(tc, P.mac(P.L, idx, wt, xl, ptl))
+    assert np.array_equal(tc, run_model(c, layer, w, xl, ptl, 1))
+
+
+def test_cifar_dense_2048_to_10_at_full_ring():
+    """The CIFAR-shaped output layer: 2048 -> 10 at N = 16384, 9 limbs of the
+    11 + 2 chain (more taps than the tensor cores' exact 512, so the CUDA-core
+    MAC), extreme weights and residues near q, against the oracle."""
+    c, P = pair((14, 11, 2, 2))
+    level, n_in, n_out = 9, 2048, 10
+    rng = np.random.default_rng(31)
+    x = workloads.random_residues(P.q[:level], (n_in, 2), P.N, 32)
+    x[: n_in // 4] = np.array(P.q[:level], dtype=np.uint32)[None, None, :, None] - 1
+    w = rng.integers(-127, 128, size=(n_out, n_in)).astype(np.int8)
+    w[0] = 127
+    w[1] = -127
+    idx = np.tile(np.arange(n_in, dtype=np.int32), (n_out, 1))
+    got = torch.full((n_out, 2, level, P.N), -1, dtype=torch.int32, device="cuda")
+    c.op_mac(level, n_in, torch.from_numpy(idx).cuda(), torch.from_numpy(w).cuda(), bcn.to_device(x), None, got)
+    assert np.array_equal(host(got), P.mac(level, idx, w, x, None))
+    assert c.device_status() == 0
