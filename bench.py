@@ -177,29 +177,32 @@ def int_peak_ops():
 def alu_work(cfg):
     """Integer work per evaluation of the NTT-based kernel classes:
     {"square" | "keyswitch" | "moddown_rescale": {"fwd": forward NTTs, "inv":
-    inverse NTTs, "mad": N-element multiply-add passes}}.
+    inverse NTTs, "mont": N-element passes of products of two variables,
+    "shoup": N-element passes of products by constants}} (every product a
+    multiply-add).
 
     From the first square layer on, ciphertexts stay in the NTT domain.  Tensor
     square of a ciphertext at n limbs: per limb 2 forward NTTs (only on
     coefficient-form input, the first square layer) and 1 inverse NTT (d2 for
-    ModUp), 4 products per coefficient; the square class also holds the domain
-    changes: a forward NTT of every feature-plaintext limb that meets NTT-domain
-    ciphertexts and the inverse NTT of the outputs.  Key switch of d2 (hybrid,
-    digits of at most alpha primes, n + K target primes): ModUp (one product per
-    digit residue, then alpha products per coefficient and prime outside the
-    digit), a forward NTT of every digit in every target prime outside it
-    (inside it, the tensor square's NTT form is reused), two products per digit
-    and target prime with the key, then two inverse NTTs on each special prime
-    and on the top data prime (with its 4 products folding in the rescale's
-    first step) and a product by N on the other data primes.  ModDown and
-    rescale: per poly and data limb below the top, 3K + 4 products per
-    coefficient and one forward NTT."""
+    ModUp); per coefficient the 3 products c0^2, c0 c1, c1^2 and the N^{-1}
+    scaling of the inverse transform's input.  The square class also holds the
+    domain changes: a forward NTT of every feature-plaintext limb that meets
+    NTT-domain ciphertexts and the inverse NTT of the outputs.  Key switch of d2
+    (hybrid, digits of at most alpha primes, n + K target primes): ModUp (one
+    constant product per digit residue, then alpha per coefficient and prime
+    outside the digit), a forward NTT of every digit in every target prime
+    outside it (inside it, the tensor square's NTT form is reused), two products
+    per digit and target prime with the key, then two inverse NTTs on each
+    special prime and on the top data prime (with its 4 constant products
+    folding in the rescale's first step) and a constant product by N on the
+    other data primes.  ModDown and rescale: per poly and data limb below the
+    top, 3K + 4 constant products per coefficient and one forward NTT."""
     import math
 
     import workloads
     K, a = cfg["n_special"], cfg["alpha"]
     levels, _ = workloads.level_schedule(cfg)
-    w = {k: {"fwd": 0, "inv": 0, "mad": 0} for k in ("square", "keyswitch", "moddown_rescale")}
+    w = {k: {"fwd": 0, "inv": 0, "mont": 0, "shoup": 0} for k in ("square", "keyswitch", "moddown_rescale")}
     in_ntt = False
     for layer, n in zip(cfg["cipher"], levels):
         n_out = workloads.cipher_layer_io(layer)[1]
@@ -210,15 +213,16 @@ def alu_work(cfg):
         C = n_out
         w["square"]["fwd"] += C * n * (0 if in_ntt else 2)
         w["square"]["inv"] += C * n
-        w["square"]["mad"] += C * 4 * n
+        w["square"]["mont"] += C * 3 * n
+        w["square"]["shoup"] += C * n
         digits = [min(a, n - j * a) for j in range(math.ceil(n / a))]
         nb = n + K
         w["keyswitch"]["fwd"] += C * sum(nb - d for d in digits)
         w["keyswitch"]["inv"] += C * 2 * (K + 1)
-        w["keyswitch"]["mad"] += C * (sum(digits) + sum(d * (nb - d) for d in digits) + 2 * nb * len(digits)
-                                      + 2 * (n - 1) + 4)
+        w["keyswitch"]["mont"] += C * 2 * nb * len(digits)
+        w["keyswitch"]["shoup"] += C * (sum(digits) + sum(d * (nb - d) for d in digits) + 2 * (n - 1) + 4)
         w["moddown_rescale"]["fwd"] += C * 2 * (n - 1)
-        w["moddown_rescale"]["mad"] += C * 2 * (n - 1) * (3 * K + 4)
+        w["moddown_rescale"]["shoup"] += C * 2 * (n - 1) * (3 * K + 4)
         in_ntt = True
     last = cfg["cipher"][-1]
     if in_ntt:
@@ -233,16 +237,17 @@ def alu_ops(cfg):
     multiply-add, N per pass)."""
     N, logN = 1 << cfg["log_n"], cfg["log_n"]
     bf = (N // 2) * logN
-    return {k: (v["fwd"] + v["inv"]) * bf * OPS_BUTTERFLY + v["mad"] * N * OPS_MULADD
+    return {k: (v["fwd"] + v["inv"]) * bf * OPS_BUTTERFLY + (v["mont"] + v["shoup"]) * N * OPS_MULADD
             for k, v in alu_work(cfg).items()}
 
 
 def alu_units(cfg):
     """The same work in the microbenchmark's units: {class: (forward
-    butterflies, inverse butterflies, multiply-adds)} per evaluation."""
+    butterflies, inverse butterflies, Montgomery multiply-adds, Shoup
+    multiply-adds)} per evaluation."""
     N, logN = 1 << cfg["log_n"], cfg["log_n"]
     bf = (N // 2) * logN
-    return {k: (v["fwd"] * bf, v["inv"] * bf, v["mad"] * N) for k, v in alu_work(cfg).items()}
+    return {k: (v["fwd"] * bf, v["inv"] * bf, v["mont"] * N, v["shoup"] * N) for k, v in alu_work(cfg).items()}
 
 
 def csrc_hash():
@@ -563,8 +568,8 @@ def run_ours(args, cfg, rank, world, local_rank):
                 "traffic_source": "ncu dram bytes per block of this kernel (profiles/ncu_traffic.json) x blocks per "
                                   "launch of this run" if traffic else None,
                 "peak_source": "measured in this run: register-resident rates of the evaluator's own lazy forward "
-                               "and inverse butterflies and Montgomery multiply-adds (bcn_int_peak_launch, full "
-                               "occupancy), weighted by this kernel's mix of the three",
+                               "and inverse butterflies, Montgomery and Shoup multiply-adds (bcn_int_peak_launch, "
+                               "full occupancy), weighted by this kernel's mix of the four",
                 "derived_peak": dpeak / 1e12,
                 "derived_peak_source": f"{GB300_SMS} SMs x {INT_LANES_PER_SM} int32 lanes x {mhz:.0f} MHz",
                 "ops_per_launch": ops[dom] * K / dn,
@@ -615,7 +620,7 @@ def run_ours(args, cfg, rank, world, local_rank):
                      "mix_peak_Tops": {k: v / 1e12 for k, v in mix.items()},
                      "clocks": peak_clocks,
                      "units": "instructions (imad_lo, imad_hi), modular additions (modadd), butterflies "
-                              "(butterfly_fwd, butterfly_inv), multiply-adds (mont_muladd)"},
+                              "(butterfly_fwd, butterfly_inv), multiply-adds (mont_muladd, shoup_muladd)"},
         "ntt_GBps": ntt_b / (ntt_ms / 1e3) / 1e9 if ntt_ms else None,
         "keyswitch_GBps": ks_b / (ks_ms / 1e3) / 1e9 if ks_ms else None,
         "kernels": kernels,
@@ -864,6 +869,46 @@ def run_rotate(args, rank, world, local_rank):
             ms.append(s_.elapsed_time(e_))
         t = statistics.mean(ms)
         res[name] = {"ciphertexts": n_ct, "level": ctx.L, "ms_per_step": t, "rotations_per_s": n_ct / (t / 1e3)}
+        # the nine offsets of a 3x3 packed convolution over rows of 16 slots:
+        # one at a time (nine bcn_op_rotate calls) against one hoisted call
+        steps = [i * 16 + j for i in range(3) for j in range(3) if i * 16 + j]
+        gks = {r: ctx.evk_prepare(bcn.to_device(ctx.galois_keygen(sk, r, workloads.SEED_KEYS + r), dev))
+               for r in steps}
+        n_h = min(n_ct, 64)
+        xh = x[:n_h].contiguous()
+        many = torch.empty((n_h, len(steps), 2, ctx.L, ctx.N), dtype=torch.int32, device=dev)
+        one = torch.empty((n_h, 2, ctx.L, ctx.N), dtype=torch.int32, device=dev)
+        ws_h, nb_h = ctx._ws(ctx.L, n_h)
+
+        def seq():
+            for r in steps:
+                assert bcn.lib().bcn_op_rotate(ctx.handle, ctx.L, gks[r].data_ptr(), r, xh.data_ptr(), n_h,
+                                               one.data_ptr(), ws_h.data_ptr(), nb_h,
+                                               torch.cuda.current_stream().cuda_stream) == 0
+
+        def hoisted():
+            ctx.op_rotate_many(ctx.L, gks, steps, xh, n_h, many)
+
+        tm = {}
+        for label, fn in (("one_at_a_time", seq), ("hoisted", hoisted)):
+            for _ in range(2):
+                fn()
+            torch.cuda.synchronize()
+            mm = []
+            for _ in range(max(1, args.steps // 2)):
+                flush.zero_()
+                s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s_.record()
+                fn()
+                e_.record()
+                torch.cuda.synchronize()
+                mm.append(s_.elapsed_time(e_))
+            tm[label] = statistics.mean(mm)
+        res[name]["conv3x3_rotations"] = {
+            "ciphertexts": n_h, "rotations_each": len(steps),
+            "ms_one_at_a_time": tm["one_at_a_time"], "ms_hoisted": tm["hoisted"],
+            "rotations_per_s_hoisted": n_h * len(steps) / (tm["hoisted"] / 1e3),
+            "speedup": tm["one_at_a_time"] / tm["hoisted"]}
         del ctx
     if rank == 0:
         print(json.dumps({"metric": "rotations/s", "value": res["cryptonets"]["rotations_per_s"],

@@ -407,6 +407,24 @@ uint32_t bcn_galois_elt(const bcn_ctx *ctx, int steps);
 bcn_status bcn_galois_keygen(const bcn_ctx *ctx, const int8_t *sk, int steps, uint64_t seed, uint32_t *gk_out);
 bcn_status bcn_op_rotate(const bcn_ctx *ctx, int level, const uint32_t *gk_eval_dev, int steps, const uint32_t *in_dev,
                          int n_ct, uint32_t *out_dev, void *workspace_dev, size_t workspace_bytes, void *cuda_stream);
+/* Many rotations of each ciphertext with one shared ModUp (App. D builds its
+ * packed convolutions and dense layers from many rotations of the same
+ * ciphertext).  The automorphism commutes with ModUp (it permutes and negates
+ * coefficients; the centred lift is odd and the basis conversion linear), so
+ * the digit decomposition of c1, in the NTT domain, is computed once per
+ * ciphertext and each rotation only permutes it, multiplies by its Galois key,
+ * transforms back and runs ModDown: results equal bcn_op_rotate's, bit for bit.
+ * steps[n_rot] (any sign, taken mod N/2; 0 copies the input), gk_evals[n_rot]
+ * a host array of device pointers to prepared Galois keys (bcn_evk_prepare of
+ * bcn_galois_keygen; ignored for steps = 0 mod N/2).  in [n_ct][2][level][N],
+ * out [n_ct][n_rot][2][level][N], device, coefficient form; workspace of
+ * bcn_op_rotate_many_workspace_bytes(level, n_ct).  BCN_E_INVAL on a bad
+ * level, a missing key, unaligned or overlapping buffers; BCN_E_BUDGET if the
+ * workspace is too small. */
+bcn_status bcn_op_rotate_many_workspace_bytes(const bcn_ctx *ctx, int level, int n_ct, size_t *bytes);
+bcn_status bcn_op_rotate_many(const bcn_ctx *ctx, int level, const uint32_t *const *gk_evals, const int *steps,
+                              int n_rot, const uint32_t *in_dev, int n_ct, uint32_t *out_dev, void *workspace_dev,
+                              size_t workspace_bytes, void *cuda_stream);
 /* Ciphertext-plaintext product then rescale (App. A Mult(c, u) with an encoded
  * u -- the masks of App. D's packed layers): (c0 u, c1 u) in R_{Q_level}, then
  * the rescale by q_{level-1}.  Encode u at scale q_{level-1} to keep the
@@ -431,12 +449,13 @@ bcn_status bcn_op_rescale(const bcn_ctx *ctx, int level, const uint32_t *in_dev,
  *   3  lazy forward NTT butterflies of the evaluator's NTT core (32 a round)
  *   4  lazy inverse NTT butterflies of the evaluator's NTT core (32 a round)
  *   5  lazy Montgomery multiply-add of the key switch's running sums (16 a round)
+ *   6  Shoup multiply-add by a constant, as in the basis conversions (16 a round)
  * units_out: the operations the launch performs (instructions for kinds 0-1,
- * modular additions, butterflies or multiply-adds for 2-5), to divide by the
+ * modular additions, butterflies or multiply-adds for 2-6), to divide by the
  * launch's time.  sink_dev: device memory of at least bcn_int_peak_grid's
  * block count in uint32 words (written only if a result equals an improbable
  * value; it keeps the work from being optimised away).  BCN_E_INVAL for a kind
- * outside 0..5, iters < 1 or a null pointer; BCN_E_BUDGET if the sink is too
+ * outside 0..6, iters < 1 or a null pointer; BCN_E_BUDGET if the sink is too
  * small. */
 bcn_status bcn_int_peak_grid(int kind, int *blocks);
 bcn_status bcn_int_peak_launch(int kind, int iters, uint32_t *sink_dev, size_t sink_words, void *cuda_stream,

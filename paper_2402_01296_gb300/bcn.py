@@ -109,6 +109,8 @@ _SIGS = {
     "bcn_galois_keygen": (_I, [_P, _P, _I, _U64, _P]),
     "bcn_op_rotate": (_I, [_P, _I, _P, _I, _P, _I, _P, _P, _SZ, _P]),
     "bcn_op_square_relin_rescale_noalloc": (_I, [_P, _I, _P, _P, _I, _P, _P]),
+    "bcn_op_rotate_many_workspace_bytes": (_I, [_P, _I, _I, ctypes.POINTER(_SZ)]),
+    "bcn_op_rotate_many": (_I, [_P, _I, _P, _P, _I, _P, _I, _P, _P, _SZ, _P]),
     "bcn_int_peak_grid": (_I, [_I, ctypes.POINTER(_I)]),
     "bcn_int_peak_launch": (_I, [_I, _I, _P, _SZ, _P, ctypes.POINTER(_D)]),
 }
@@ -357,6 +359,31 @@ class Context:
                                    _dev_ptr(in_dev, n_ct * 2 * level * self.N), n_ct,
                                    _dev_ptr(out_dev, n_ct * 2 * level * self.N), ws.data_ptr(), nb, _stream(stream)),
                "bcn_op_rotate")
+
+    def op_rotate_many(self, level, gk_evals: dict, steps: list, in_dev, n_ct, out_dev, workspace=None,
+                       stream=None):
+        """bcn_op_rotate_many: every ciphertext of in_dev [n_ct][2][level][N] rotated
+        by every entry of `steps`, one hoisted ModUp per ciphertext; out_dev
+        [n_ct][len(steps)][2][level][N].  gk_evals: {steps: prepared Galois key}
+        (steps taken mod N/2; 0 needs no key)."""
+        n_rot = len(steps)
+        half = self.N // 2
+        ptrs = (ctypes.c_void_p * max(1, n_rot))()
+        st = (ctypes.c_int * max(1, n_rot))()
+        for i, r in enumerate(steps):
+            st[i] = int(r)
+            key = gk_evals.get(r, gk_evals.get(r % half)) if r % half else None
+            ptrs[i] = _dev_ptr(key, self.evk_words()) if key is not None else None
+        nb = _SZ(0)
+        _check(lib().bcn_op_rotate_many_workspace_bytes(self._h, level, n_ct, ctypes.byref(nb)),
+               "bcn_op_rotate_many_workspace_bytes")
+        if workspace is None:
+            import torch
+            workspace = torch.empty(max(1, (nb.value + 3) // 4), dtype=torch.int32, device=f"cuda:{self.device}")
+        _check(lib().bcn_op_rotate_many(self._h, level, ptrs, st, n_rot, _dev_ptr(in_dev, n_ct * 2 * level * self.N),
+                                        n_ct, _dev_ptr(out_dev, n_ct * n_rot * 2 * level * self.N),
+                                        workspace.data_ptr(), workspace.numel() * workspace.element_size(),
+                                        _stream(stream)), "bcn_op_rotate_many")
 
     def op_mul_plain_rescale(self, level, in_dev, n_ct, pt_dev, out_dev, stream=None):
         """(c0 u, c1 u), then rescale: in [n_ct][2][level][N], pt [level][N] -> out at level - 1."""

@@ -216,6 +216,67 @@ __global__ void __launch_bounds__((1 << LOGN) / R, IN_NTT ? SqnOcc<(1 << LOGN) /
     C::store_natural(x, d2, tid);
 }
 
+// ModUp residue of digit j (primes q_lo .. q_{hi-1}, lo = j alpha) of the
+// polynomial x2 ([n][N] coefficient form, canonical) in target prime t (prime
+// index pt, constants P), in the pass-0 distribution of NttCore<LOGN, R>, ready
+// for the forward NTT: on the digit's own primes the residue itself; else the
+// centred fast basis conversion
+//     sum_u r_u * Dhat_u - #{u : r_u > (q_u-1)/2} * D_j,  r_u = [x_u Dhat_u^{-1}]_{q_u},
+// which for one-prime digits is d mod t, less q_j mod t when d > (q_j-1)/2.
+// With LAZY (t a data prime) one-prime digits leave d + (t - q_j mod t) < 3t,
+// a valid lazy NTT input; otherwise the residue is canonical.
+template <int LOGN, int R, bool LAZY>
+__device__ __forceinline__ void modup_residue(uint32_t (&x)[R], const uint32_t *__restrict__ x2, int t, int pt,
+                                              int j, int n, const KsDev &ks, const PrimeConst *__restrict__ pc,
+                                              const PrimeConst &P, int tid) {
+    using C = NttCore<LOGN, R>;
+    constexpr int N = C::N;
+    const int A = ks.alpha, lo = j * A, hi = min(lo + A, n);
+    if (t >= lo && t < hi) {
+        C::load_natural(x, x2 + (size_t)t * N, tid);
+    } else if (A == 1) {
+        const uint32_t half = pc[j].half;
+        const uint32_t dp = ks.dprod[(size_t)(n * ks.dnum_max + j) * ks.P + pt];  // q_j mod t
+        const uint32_t *xj = x2 + (size_t)j * N;
+        if constexpr (LAZY) {
+            // d - [d > (q_j-1)/2] q_j as d + (t - q_j mod t): below q_j + t < 3t (the
+            // data primes are within a factor 2), a valid lazy NTT input
+            const uint32_t tmq = P.q - dp;
+#pragma unroll
+            for (int u = 0; u < R; u++) {
+                const uint32_t d = __ldg(xj + C::nat_elem(u, tid));
+                x[u] = d + (d > half ? tmq : 0u);
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < R; u++) {
+                const uint32_t d = __ldg(xj + C::nat_elem(u, tid));
+                uint32_t y = reduce_once(d, P.q);  // d < q_j < 2t
+                if (d > half) y = sub_mod(y, dp, P.q);
+                x[u] = y;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int u = 0; u < R; u++) x[u] = 0;
+        const uint32_t dp = ks.dprod[(size_t)(n * ks.dnum_max + j) * ks.P + pt];
+        for (int v = 0; v < hi - lo; v++) {
+            const int i = lo + v;
+            const uint32_t qi = pc[i].q, half = pc[i].half;
+            const uint2 di = ks.dhat_inv[(size_t)(n * ks.dnum_max + j) * A + v];
+            const uint2 dh = ks.dhat[((size_t)(n * ks.dnum_max + j) * A + v) * ks.P + pt];
+            const uint32_t *xi = x2 + (size_t)i * N;
+#pragma unroll
+            for (int u = 0; u < R; u++) {
+                const uint32_t r = shoup_mul(__ldg(xi + C::nat_elem(u, tid)), di.x, di.y, qi);
+                uint32_t y = add_mod(x[u], shoup_mul(r, dh.x, dh.y, P.q), P.q);
+                if (r > half) y = sub_mod(y, dp, P.q);
+                x[u] = y;
+            }
+        }
+    }
+}
+
 // Key switching of d2, fused per (target prime t, ciphertext): for every
 // digit j, ModUp of d2 into prime t (the residue itself on the digit's own
 // primes -- taken from D2N in the NTT domain when given -- else the centred
@@ -391,49 +452,7 @@ __device__ __forceinline__ void ks_core_body(const uint32_t *__restrict__ D, con
         if (t >= lo && t < hi && D2N != nullptr) {
             C::load_ntt(x, D2N + ((size_t)ct * n + t) * N, tid);
         } else {
-            if (t >= lo && t < hi) {
-                C::load_natural(x, x2 + (size_t)t * N, tid);
-            } else if (A == 1) {
-                const uint32_t half = pc[j].half;
-                const uint32_t dp = ks.dprod[(size_t)(n * ks.dnum_max + j) * ks.P + pt];  // q_j mod t
-                const uint32_t *xj = x2 + (size_t)j * N;
-                if constexpr (LAZY) {
-                    // d - [d > (q_j-1)/2] q_j as d + (t - q_j mod t): below q_j + t < 3t (the
-                    // data primes are within a factor 2), a valid lazy NTT input
-                    const uint32_t tmq = P.q - dp;
-#pragma unroll
-                    for (int u = 0; u < R; u++) {
-                        const uint32_t d = __ldg(xj + C::nat_elem(u, tid));
-                        x[u] = d + (d > half ? tmq : 0u);
-                    }
-                } else {
-#pragma unroll
-                    for (int u = 0; u < R; u++) {
-                        const uint32_t d = __ldg(xj + C::nat_elem(u, tid));
-                        uint32_t y = reduce_once(d, P.q);  // d < q_j < 2t
-                        if (d > half) y = sub_mod(y, dp, P.q);
-                        x[u] = y;
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int u = 0; u < R; u++) x[u] = 0;
-                const uint32_t dp = ks.dprod[(size_t)(n * ks.dnum_max + j) * ks.P + pt];
-                for (int v = 0; v < hi - lo; v++) {
-                    const int i = lo + v;
-                    const uint32_t qi = pc[i].q, half = pc[i].half;
-                    const uint2 di = ks.dhat_inv[(size_t)(n * ks.dnum_max + j) * A + v];
-                    const uint2 dh = ks.dhat[((size_t)(n * ks.dnum_max + j) * A + v) * ks.P + pt];
-                    const uint32_t *xi = x2 + (size_t)i * N;
-#pragma unroll
-                    for (int u = 0; u < R; u++) {
-                        const uint32_t r = shoup_mul(__ldg(xi + C::nat_elem(u, tid)), di.x, di.y, qi);
-                        uint32_t y = add_mod(x[u], shoup_mul(r, dh.x, dh.y, P.q), P.q);
-                        if (r > half) y = sub_mod(y, dp, P.q);
-                        x[u] = y;
-                    }
-                }
-            }
+            modup_residue<LOGN, R, LAZY>(x, x2, t, pt, j, n, ks, pc, P, tid);
             C::forward(x, sm, tid, ModQ(P.q, kFmaOne<LOGN, R> ? P.one : 1u), tf);
         }
         key_product(x, j);
@@ -648,6 +667,141 @@ __global__ void __launch_bounds__((1 << LOGN) / R, NP == 1 ? MdOcc<(1 << LOGN) /
     }
 }
 
+// ------------------------------------------------------------ hoisted rotations
+// Rotations of one ciphertext by many steps share their ModUp (App. D builds
+// packed convolutions and dense layers from many rotations of the same
+// ciphertext).  The automorphism sigma_g acts on a limb's coefficients as a
+// signed permutation, the centred lift is odd (q odd) and the fast basis
+// conversion linear, so ModUp(sigma_g(c1)) = sigma_g(ModUp(c1)) residue for
+// residue: one ModUp of c1, kept in the NTT domain, serves every rotation, and
+// in the NTT domain sigma_g is a plain permutation of the evaluation points.
+// The results equal those of rotating one step at a time, bit for bit.
+
+// U [C][dnum][n+K][N] <- ModUp of digit j of the ciphertexts' c1 (in
+// [C][2][n][N], coefficient form) into target prime t, forward NTT (last-pass
+// layout; lazy values below 4q on the data primes, canonical on the special
+// primes).  grid (n+K, dnum, C)
+template <int LOGN, int R, bool LAZY>
+__device__ __forceinline__ void modup_hoist_body(const uint32_t *__restrict__ in, uint32_t *__restrict__ U, int n,
+                                                 const KsDev &ks, const PrimeConst *__restrict__ pc,
+                                                 const uint2 *__restrict__ twf) {
+    using C = NttCore<LOGN, R, LAZY, kFmaKs>;
+    constexpr int N = C::N;
+    extern __shared__ __align__(16) uint32_t sm[];
+    const int t = blockIdx.x, j = blockIdx.y, ct = blockIdx.z, tid = threadIdx.x;
+    const int nb = n + ks.K, dnum = (n + ks.alpha - 1) / ks.alpha;
+    const int pt = t < n ? t : ks.L + (t - n);
+    const PrimeConst P = pc[pt];
+    const uint32_t *x2 = in + ((size_t)ct * 2 + 1) * n * N;
+    uint32_t x[R];
+    modup_residue<LOGN, R, LAZY>(x, x2, t, pt, j, n, ks, pc, P, tid);
+    C::forward(x, sm, tid, ModQ(P.q, kFmaOne<LOGN, R> ? P.one : 1u), twf + (size_t)pt * N);
+    C::store_ntt(x, U + (((size_t)ct * dnum + j) * nb + t) * N, tid);
+}
+
+template <int LOGN, int R>
+__global__ void __launch_bounds__((1 << LOGN) / R) k_modup_hoist(const uint32_t *__restrict__ in,
+                                                                 uint32_t *__restrict__ U, int n, KsDev ks,
+                                                                 const PrimeConst *__restrict__ pc,
+                                                                 const uint2 *__restrict__ twf) {
+    const int t = blockIdx.x;
+    const int pt = t < n ? t : ks.L + (t - n);
+    if (pc[pt].q < (1u << 30))
+        modup_hoist_body<LOGN, R, true>(in, U, n, ks, pc, twf);
+    else
+        modup_hoist_body<LOGN, R, false>(in, U, n, ks, pc, twf);
+}
+
+// NTT-domain element whose value sigma_g moves to element e: with the
+// evaluation point psi^(2 brv(e) + 1) at element e, sigma_g(a) there is a at
+// psi^((2 brv(e) + 1) g) = psi^(2 k + 1), held by element brv(k).
+template <int LOGN>
+__device__ __forceinline__ int auto_ntt_src(int e, uint32_t g) {
+    const uint32_t k = __brev((uint32_t)e) >> (32 - LOGN);
+    const uint32_t m = ((2 * k + 1) * g) & ((2u << LOGN) - 1);
+    return (int)(__brev((m - 1) >> 1) >> (32 - LOGN));
+}
+
+// Key switching of sigma_g(c1) for a batch of rotations, from the hoisted U:
+// for every digit j the limb U[ct][j][t] is staged in shared memory, gathered
+// through the permutation of sigma_g, multiplied by both halves of the
+// rotation's Galois key (prepared form: k R N^{-1}, NTT domain) and added to
+// two running sums, whose inverse NTT (the key's N^{-1} folded in) gives
+// ACC [C][count][2][n+K][N] in coefficient form, as the key-switching core
+// leaves it for ModDown.  grid (n+K, count, C)
+template <int LOGN, int R, bool LAZY>
+__device__ __forceinline__ void ks_rot_body(const uint32_t *__restrict__ U, RotBatch rb,
+                                            uint32_t *__restrict__ acc_out, int n, const KsDev &ks,
+                                            const PrimeConst *__restrict__ pc, const uint2 *__restrict__ twi) {
+    using C = NttCore<LOGN, R, LAZY, kFmaKs>;
+    constexpr int N = C::N, T = C::T;
+    extern __shared__ __align__(16) uint32_t sm[];
+    uint32_t *s0 = sm + C::SMEM_WORDS, *s1 = s0 + N;  // running sums, thread-private slots u*T + tid
+    const int t = blockIdx.x, r = blockIdx.y, ct = blockIdx.z, tid = threadIdx.x;
+    const int nb = n + ks.K, dnum = (n + ks.alpha - 1) / ks.alpha;
+    const int pt = t < n ? t : ks.L + (t - n);
+    const PrimeConst P = pc[pt];
+    const uint32_t g = rb.g[r];
+    const uint32_t *key = rb.gk[r];
+#pragma unroll
+    for (int u = 0; u < R; u++) s0[u * T + tid] = s1[u * T + tid] = 0;
+    for (int j = 0; j < dnum; j++) {
+        const uint32_t *src = U + (((size_t)ct * dnum + j) * nb + t) * N;
+        __syncthreads();  // the previous digit's gathers are done
+        for (int e = 4 * tid; e < N; e += 4 * T) {
+            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(src + e));
+            const int pe = C::padded(e);  // e..e+3 lie in one run of 32
+            sm[pe] = v.x;
+            sm[pe + 1] = v.y;
+            sm[pe + 2] = v.z;
+            sm[pe + 3] = v.w;
+        }
+        __syncthreads();
+        const uint32_t *k0 = key + ((size_t)(j * 2 + 0) * ks.P + pt) * N;
+        const uint32_t *k1 = key + ((size_t)(j * 2 + 1) * ks.P + pt) * N;
+        // one element at a time: gathered through sigma_g, multiplied, added
+#pragma unroll 4
+        for (int u = 0; u < R; u++) {
+            const int e = C::ntt_elem(u, tid);
+            const uint32_t xv = sm[C::padded(auto_ntt_src<LOGN>(e, g))];
+            const uint32_t w0 = __ldg(k0 + e), w1 = __ldg(k1 + e);
+            uint32_t &a0 = s0[u * T + tid], &a1 = s1[u * T + tid];
+            if constexpr (LAZY) {  // sums in [0, 2q) (the lazy inverse NTT's input range)
+                const uint32_t nq2 = 0u - 2 * P.q;
+                const uint32_t v0 = mont_mul_lazy(xv, w0, P.q, P.qneg_inv) + a0;
+                const uint32_t v1 = mont_mul_lazy(xv, w1, P.q, P.qneg_inv) + a1;
+                a0 = min(v0, v0 + nq2);
+                a1 = min(v1, v1 + nq2);
+            } else {
+                a0 = add_mod(a0, mont_mul(xv, w0, P.q, P.qneg_inv), P.q);
+                a1 = add_mod(a1, mont_mul(xv, w1, P.q, P.qneg_inv), P.q);
+            }
+        }
+    }
+    uint32_t x[R];
+#pragma unroll 1
+    for (int b = 0; b < 2; b++) {
+        const uint32_t *sb = b == 0 ? s0 : s1;
+#pragma unroll
+        for (int u = 0; u < R; u++) x[u] = sb[u * T + tid];
+        C::inverse_unscaled(x, sm, tid, ModQ(P.q, kFmaOne<LOGN, R> ? P.one : 1u), twi + (size_t)pt * N);
+        C::store_natural(x, acc_out + ((((size_t)ct * rb.count + r) * 2 + b) * nb + t) * N, tid);
+    }
+}
+
+template <int LOGN, int R>
+__global__ void __launch_bounds__((1 << LOGN) / R) k_ks_rot(const uint32_t *__restrict__ U, RotBatch rb,
+                                                            uint32_t *__restrict__ acc_out, int n, KsDev ks,
+                                                            const PrimeConst *__restrict__ pc,
+                                                            const uint2 *__restrict__ twi) {
+    const int t = blockIdx.x;
+    const int pt = t < n ? t : ks.L + (t - n);
+    if (pc[pt].q < (1u << 30))
+        ks_rot_body<LOGN, R, true>(U, rb, acc_out, n, ks, pc, twi);
+    else
+        ks_rot_body<LOGN, R, false>(U, rb, acc_out, n, ks, pc, twi);
+}
+
 // R residues per thread for the NTT and square kernels, RKS for the key switch
 template <int LOGN, int R, int RKS = R>
 struct CoreImpl {
@@ -669,6 +823,10 @@ struct CoreImpl {
     static constexpr size_t SMEM_MD = (size_t)MD_NP * CoreMd::SMEM_WORDS * 4;
     // key switch: exchange buffer(s) and the two running sums
     static constexpr size_t SMEM_KS = ((size_t)(kKsDual<LOGN, RKS> ? 2 : 1) * CoreKs::SMEM_WORDS + 2 * CoreKs::N) * 4;
+    // hoisted rotations (key switch's block shape): ModUp, one exchange buffer;
+    // rotation key products, the staging / exchange buffer and the two sums
+    static constexpr size_t SMEM_HOIST = (size_t)CoreKs::SMEM_WORDS * 4;
+    static constexpr size_t SMEM_KSROT = ((size_t)CoreKs::SMEM_WORDS + 2 * CoreKs::N) * 4;
 
     static bcn_status ntt(const bcn_ctx *c, uint32_t *data, size_t n_limbs, size_t n_groups, size_t stride,
                           PrimeMap pm, bool inverse, cudaStream_t st) {
@@ -710,6 +868,18 @@ struct CoreImpl {
         }
         return check_launch("k_md_limb");
     }
+    static bcn_status modup_hoist(const bcn_ctx *c, int n, const uint32_t *in, uint32_t *U, int C, cudaStream_t st) {
+        const int dnum = (n + c->alpha - 1) / c->alpha;
+        k_modup_hoist<LOGN, RKS><<<dim3(n + c->K, dnum, C), CoreKs::T, SMEM_HOIST, st>>>(in, U, n, ks_dev(c), c->d_pc,
+                                                                                       c->d_tw_fwd);
+        return check_launch("k_modup_hoist");
+    }
+    static bcn_status ks_rot(const bcn_ctx *c, int n, const uint32_t *U, const RotBatch &rb, uint32_t *acc, int C,
+                             cudaStream_t st) {
+        k_ks_rot<LOGN, RKS><<<dim3(n + c->K, rb.count, C), CoreKs::T, SMEM_KSROT, st>>>(U, rb, acc, n, ks_dev(c),
+                                                                                     c->d_pc, c->d_tw_inv);
+        return check_launch("k_ks_rot");
+    }
     static bcn_status setup() {
         const int smem = (int)SMEM, smem3 = (int)SMEM3, smem_sq = (int)SMEM_SQ_NTT, smem_ks = (int)SMEM_KS;
         auto big = [](const void *k, int bytes) {
@@ -727,12 +897,14 @@ struct CoreImpl {
             !big((const void *)k_md_limb<LOGN, RMD, MD_NP, 4>, (int)SMEM_MD) ||
             !carve((const void *)k_square_core<LOGN, R, false>) || !carve((const void *)k_square_core<LOGN, R, true>) ||
             !carve((const void *)k_ks_core<LOGN, RKS>) || !carve((const void *)k_md_limb<LOGN, RMD, MD_NP, 1>) ||
-            !carve((const void *)k_md_limb<LOGN, RMD, MD_NP, 2>))
+            !carve((const void *)k_md_limb<LOGN, RMD, MD_NP, 2>) ||
+            !big((const void *)k_modup_hoist<LOGN, RKS>, (int)SMEM_HOIST) ||
+            !big((const void *)k_ks_rot<LOGN, RKS>, (int)SMEM_KSROT))
             return fail(BCN_E_CUDA, "cudaFuncSetAttribute failed for the NTT-based kernels");
         return BCN_OK;
     }
     static const CoreFns *fns() {
-        static const CoreFns f = {&ntt, &square, &keyswitch, &moddown_rescale, &setup};
+        static const CoreFns f = {&ntt, &square, &keyswitch, &moddown_rescale, &setup, &modup_hoist, &ks_rot};
         return &f;
     }
 };

@@ -63,6 +63,16 @@ inline KsDev ks_dev(const bcn_ctx *c) {
     return k;
 }
 
+// A batch of rotations for the hoisted key switch, passed by value: the
+// prepared Galois key and the Galois element g of each (kRotBatch at most).
+constexpr int kRotBatch = 32;
+struct RotBatch {
+    const uint32_t *gk[kRotBatch];
+    uint32_t g[kRotBatch];
+    uint32_t ginv[kRotBatch];
+    int count;
+};
+
 // The NTT-based kernels of one ring degree (template instances live in
 // cores_*.cu so they compile in parallel).
 struct CoreFns {
@@ -85,6 +95,13 @@ struct CoreFns {
     bcn_status (*moddown_rescale)(const bcn_ctx *, int n, const uint32_t *D, const uint32_t *acc, uint32_t *out,
                                   int C, cudaStream_t);
     bcn_status (*setup)();
+    // hoisted rotations: U [C][dnum][n+K][N] <- NTT-domain ModUp of every digit
+    // of the ciphertexts' c1 (in [C][2][n][N], coefficient form)
+    bcn_status (*modup_hoist)(const bcn_ctx *, int n, const uint32_t *in, uint32_t *U, int C, cudaStream_t);
+    // ACC [C][rb.count][2][n+K][N] <- key switching of sigma_g(c1) for every
+    // rotation of the batch (coefficient form, ready for ModDown)
+    bcn_status (*ks_rot)(const bcn_ctx *, int n, const uint32_t *U, const RotBatch &rb, uint32_t *acc, int C,
+                         cudaStream_t);
 };
 const CoreFns *core_fns(int logN);  // nullptr if unsupported
 const CoreFns *core_fns_small(int logN);

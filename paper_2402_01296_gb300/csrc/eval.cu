@@ -51,7 +51,7 @@ __host__ __device__ constexpr size_t mac_grouped_smem(int OT, int kca) {
 // (the order kept between layers, so a chunk of outputs is a run of groups).
 // Columns run over the (poly, limb, coefficient) words of a ciphertext.  Taps
 // are taken in chunks of kca (weights and input indices in shared memory).
-// grid (ceil(2*level*N/4/256), groups in this launch * ceil(n_go/OT)), 256 threads.
+// grid (groups in this launch * ceil(n_go/OT), ceil(2*level*N/4/256)), 256 threads.
 template <int OT>
 __global__ void __launch_bounds__(kMacThreads, OT <= 5 ? 3 : 2) k_mac_grouped(const uint32_t *__restrict__ in, uint32_t *__restrict__ out,
                                                      const int32_t *__restrict__ gidx, const int8_t *__restrict__ gw,
@@ -64,10 +64,12 @@ __global__ void __launch_bounds__(kMacThreads, OT <= 5 ? 3 : 2) k_mac_grouped(co
     int32_t *sw = reinterpret_cast<int32_t *>(smraw + kMacRingBytes);  // [kca][OTP] weights (0: padding tap)
     int32_t *sidx = sw + (size_t)kca * OTP;                            // [kca] input (0: padding)
     // output tiles [t_lo, t_lo + n_tl) of every group
-    const int g = g_base + blockIdx.y / n_tl, o0 = (t_lo + (int)blockIdx.y % n_tl) * OT;
+    // output tiles vary fastest over the grid: the blocks that run together read
+    // the same columns of every input, which stay in L2 between them
+    const int g = g_base + blockIdx.x / n_tl, o0 = (t_lo + (int)blockIdx.x % n_tl) * OT;
     const int no = min(OT, n_go - o0);
     const size_t cols = (size_t)2 * level * N;
-    const size_t col = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    const size_t col = ((size_t)blockIdx.y * blockDim.x + threadIdx.x) * 4;
     const bool active = col < cols;
     // residues are below 2^31, so signed 32 x 32 -> 64 products are exact
     long long acc[OT][4];
@@ -339,9 +341,9 @@ static bcn_status launch_mac(const bcn_ctx *c, int level, int K, int n_groups, i
     const size_t cols = (size_t)2 * level * N;
     const int kca = std::min(K, kMacTapChunk);
     const size_t smem = mac_grouped_smem(OT, kca);
-    if ((long long)n_groups * n_tl > 65535) return fail(BCN_E_INVAL, "MAC layer with more than 65535 output tiles");
+    if ((cols / 4 + 255) / 256 > 65535) return fail(BCN_E_INVAL, "MAC: more than 65535 column blocks");
     Timed tm(prof, st, BCN_KERNEL_MAC, alg_bytes);
-    dim3 grid((unsigned)((cols / 4 + 255) / 256), (unsigned)(n_groups * n_tl));
+    dim3 grid((unsigned)(n_groups * n_tl), (unsigned)((cols / 4 + 255) / 256));
 #define BCN_MAC(OTV)                                                                                          \
     case OTV:                                                                                                 \
         k_mac_grouped<OTV><<<grid, kMacThreads, smem, st>>>(in, out, gidx, gw, gout, pt, K, kca, n_go, level, N, g_base, \

@@ -125,7 +125,7 @@ __device__ __forceinline__ void stage_slab(uint32_t stage, const uint32_t *__res
 
 }  // namespace
 
-// grid (2 level N / 128, n_groups * tiles), 256 threads.  w16: per output tile
+// grid (n_groups * tiles, 2 level N / 128), 256 threads.  w16: per output tile
 // the fp16 weights [NT][Kpad] in the canonical K-major layout (zero rows past
 // the tile's outputs, zero columns past K).  Kpad is a multiple of kSlab.
 // Shared memory: kStages raw stages (cp.async, kStages - 1 slabs in flight
@@ -149,10 +149,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_mac_tc(const uint32_t *__restri
     int32_t *sgo = reinterpret_cast<int32_t *>(tslot + 2);  // [NT] the tile's output indices
 
     const int tid = threadIdx.x, warp = tid >> 5, r = tid & (kRows - 1), half = tid >> 7;
-    const int g = g_base + (int)blockIdx.y / n_tl, tile = t_lo + (int)blockIdx.y % n_tl;
+    // output tiles vary fastest over the grid: the CTAs that run together read
+    // the same columns of every input, which stay in L2 between them
+    const int g = g_base + (int)blockIdx.x / n_tl, tile = t_lo + (int)blockIdx.x % n_tl;
     const int o0 = tile * tile_out, no = min(tile_out, n_go - o0);
     const size_t cols = (size_t)2 * level * N;
-    const size_t col0 = (size_t)blockIdx.x * kRows, col = col0 + r;
+    const size_t col0 = (size_t)blockIdx.y * kRows, col = col0 + r;
     const int n_slabs = Kpad / kSlab;
 
     if (warp == 0) {
@@ -378,8 +380,8 @@ bcn_status launch_mac_tc(const bcn_ctx *c, const MacTcPlan &p, int level, int K,
                          uint32_t *out, cudaStream_t st, int g_base, bool store_natural, int t_lo, int n_tl) {
     const size_t cols = (size_t)2 * level * c->N;
     if (t_lo < 0 || n_tl < 1 || t_lo + n_tl > p.tiles) return fail(BCN_E_INVAL, "MAC tile range");
-    if ((long long)n_groups * n_tl > 65535) return fail(BCN_E_INVAL, "MAC layer with more than 65535 output tiles");
-    dim3 grid((unsigned)(cols / kRows), (unsigned)(n_groups * n_tl));
+    if (cols / kRows > 65535) return fail(BCN_E_INVAL, "MAC: more than 65535 column blocks");
+    dim3 grid((unsigned)(n_groups * n_tl), (unsigned)(cols / kRows));
     k_mac_tc<<<grid, kThreads, p.smem, st>>>(in, out, gidx, reinterpret_cast<const uint4 *>(p.w16), gout, pt, K, p.Kpad,
                                           n_go, p.tile_out, p.NT, t_lo, n_tl, level, c->N, g_base,
                                           store_natural ? 1 : 0, c->d_pc, p.tmem_cols, c->d_status);

@@ -14,8 +14,10 @@
 //   4  lazy inverse butterflies             the same for the inverse transform
 //   5  lazy Montgomery multiply-add         the key switch's running-sum step
 //                                            (product, addition, min), 16 a round
-// Kinds 3-5 use the exact device functions of the evaluator (NttCore's passes
-// with the key switch's FMA-pipe choice, mont_mul_lazy), so their rates are
+//   6  Shoup multiply-add by a constant     the basis conversions' step (shoup_mul,
+//                                            add_mod), 16 a round
+// Kinds 3-6 use the exact device functions of the evaluator (NttCore's passes
+// with the key switch's FMA-pipe choice, mont_mul_lazy, shoup_mul), so their rates are
 // what the NTT-based kernels could reach with their data in registers and no
 // exchange, load or barrier: the roofline their algorithmic operations are
 // measured against.  Values are not meaningful; a final word per thread is
@@ -48,9 +50,12 @@ __global__ void __launch_bounds__(kPeakThreads) k_int_peak(uint32_t *__restrict_
     const uint32_t seed = (blockIdx.x * kPeakThreads + threadIdx.x) * 0x9E3779B9u;
 #pragma unroll
     for (int u = 0; u < kPeakRegs; u++) x[u] = (seed + (uint32_t)u * 0x85EBCA6Bu) % q;
-    uint32_t k[kPeakRegs];  // key words of kind 5
+    uint32_t k[kPeakRegs], kp[kPeakRegs];  // key words (kind 5), constants and their Shoup companions (kind 6)
 #pragma unroll
-    for (int u = 0; u < kPeakRegs; u++) k[u] = (seed ^ ((uint32_t)u * 0xC2B2AE35u)) % q;
+    for (int u = 0; u < kPeakRegs; u++) {
+        k[u] = (seed ^ ((uint32_t)u * 0xC2B2AE35u)) % q;
+        kp[u] = (uint32_t)(((uint64_t)k[u] << 32) / q);
+    }
     uint32_t xs = seed % q;
     const ModQ m(q, one);
 #pragma unroll 1
@@ -71,7 +76,7 @@ __global__ void __launch_bounds__(kPeakThreads) k_int_peak(uint32_t *__restrict_
         } else if constexpr (KIND == 4) {
             uint32_t(&xx)[1][kPeakRegs] = *reinterpret_cast<uint32_t(*)[1][kPeakRegs]>(&x);
             C::template pass_inv<0, 1>(xx, 0, m, g_peak_tw);
-        } else {
+        } else if constexpr (KIND == 5) {
             const uint32_t nq2 = 0u - 2 * q;
 #pragma unroll
             for (int u = 0; u < kPeakRegs; u++) {
@@ -79,6 +84,10 @@ __global__ void __launch_bounds__(kPeakThreads) k_int_peak(uint32_t *__restrict_
                 x[u] = min(s, s + nq2);
             }
             xs = x[kPeakRegs - 1];  // the next round multiplies the last sum (no dynamic register index)
+        } else {
+#pragma unroll
+            for (int u = 0; u < kPeakRegs; u++) x[u] = add_mod(x[u], shoup_mul(xs, k[u], kp[u], q), q);
+            xs = x[kPeakRegs - 1];
         }
     }
     uint32_t v = xs;
@@ -99,7 +108,7 @@ bcn_status peak_grid(int *grid) {
 }
 
 // operations one thread performs per round
-constexpr double kUnitsPerRound[6] = {kPeakRegs, kPeakRegs, kPeakRegs, 32, 32, kPeakRegs};
+constexpr double kUnitsPerRound[7] = {kPeakRegs, kPeakRegs, kPeakRegs, 32, 32, kPeakRegs, kPeakRegs};
 
 }  // namespace
 }  // namespace bcn
@@ -117,7 +126,8 @@ bcn_status bcn_int_peak_grid(int kind, int *blocks) {
     case 3: return peak_grid<3>(blocks);
     case 4: return peak_grid<4>(blocks);
     case 5: return peak_grid<5>(blocks);
-    default: return fail(BCN_E_INVAL, "bcn_int_peak_grid: kind must be 0..5");
+    case 6: return peak_grid<6>(blocks);
+    default: return fail(BCN_E_INVAL, "bcn_int_peak_grid: kind must be 0..6");
     }
 }
 
@@ -142,7 +152,8 @@ bcn_status bcn_int_peak_launch(int kind, int iters, uint32_t *sink_dev, size_t s
     case 2: k_int_peak<2><<<grid, kPeakThreads, 0, st>>>(sink_dev, iters, q, 1u, a, b, qneg_inv, magic); break;
     case 3: k_int_peak<3><<<grid, kPeakThreads, 0, st>>>(sink_dev, iters, q, 1u, a, b, qneg_inv, magic); break;
     case 4: k_int_peak<4><<<grid, kPeakThreads, 0, st>>>(sink_dev, iters, q, 1u, a, b, qneg_inv, magic); break;
-    default: k_int_peak<5><<<grid, kPeakThreads, 0, st>>>(sink_dev, iters, q, 1u, a, b, qneg_inv, magic); break;
+    case 5: k_int_peak<5><<<grid, kPeakThreads, 0, st>>>(sink_dev, iters, q, 1u, a, b, qneg_inv, magic); break;
+    default: k_int_peak<6><<<grid, kPeakThreads, 0, st>>>(sink_dev, iters, q, 1u, a, b, qneg_inv, magic); break;
     }
     s = check_launch("k_int_peak");
     if (s != BCN_OK) return s;

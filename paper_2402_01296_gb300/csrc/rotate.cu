@@ -38,19 +38,17 @@ __global__ void __launch_bounds__(256) k_automorph_c1(const uint32_t *__restrict
     D[(((size_t)ct * 3 + 2) * n + i) * N + j] = auto_coeff(a, j, ginv, N, pc[i].q);
 }
 
-// ModDown by P of the key-switching sums ACC [C][2][n+K][N] (centred fast
-// basis conversion of the P part), plus sigma_g(c0) on the first polynomial:
-// out [C][2][n][N].  Four coefficients per thread.  grid (N/4/256, 2, C)
-__global__ void __launch_bounds__(256) k_moddown_rotate(const uint32_t *__restrict__ in,
-                                                        const uint32_t *__restrict__ acc,
-                                                        uint32_t *__restrict__ out, int n, int N, uint32_t ginv,
-                                                        KsDev ks, const PrimeConst *__restrict__ pc) {
-    const int k4 = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k4 * 4 >= N) return;
-    const int b = blockIdx.y, ct = blockIdx.z;
-    const int nb = n + ks.K, L = ks.L;
-    const uint4 *ab = reinterpret_cast<const uint4 *>(acc + ((size_t)ct * 2 + b) * nb * N) + k4;
-    uint4 *ob = reinterpret_cast<uint4 *>(out + ((size_t)ct * 2 + b) * n * N) + k4;
+// ModDown by P of the key-switching sums of one poly b (acc [n+K][N], centred
+// fast basis conversion of the P part), plus sigma_g(c0) (c0 [n][N], the
+// rotated ciphertext's first poly) when b == 0: out [n][N].  Coefficients
+// 4 k4 .. 4 k4 + 3.
+__device__ __forceinline__ void moddown_rotate_body(const uint32_t *__restrict__ c0_base,
+                                                    const uint32_t *__restrict__ acc_b, uint32_t *__restrict__ out_b,
+                                                    int b, int n, int N, uint32_t ginv, const KsDev &ks,
+                                                    const PrimeConst *__restrict__ pc, int k4) {
+    const int L = ks.L;
+    const uint4 *ab = reinterpret_cast<const uint4 *>(acc_b) + k4;
+    uint4 *ob = reinterpret_cast<uint4 *>(out_b) + k4;
     const size_t stride = (size_t)N / 4;
     uint32_t r[4][4];  // [special prime][coefficient]
     int cnt[4] = {0, 0, 0, 0};
@@ -81,7 +79,7 @@ __global__ void __launch_bounds__(256) k_moddown_rotate(const uint32_t *__restri
         const uint2 pi = ks.pinv[i];
         const uint4 av = __ldg(ab + (size_t)i * stride);
         const uint32_t a[4] = {av.x, av.y, av.z, av.w};
-        const uint32_t *c0 = in + (((size_t)ct * 2 + 0) * n + i) * N;
+        const uint32_t *c0 = c0_base + (size_t)i * N;
         uint32_t o[4];
 #pragma unroll
         for (int z = 0; z < 4; z++) {
@@ -93,10 +91,147 @@ __global__ void __launch_bounds__(256) k_moddown_rotate(const uint32_t *__restri
     }
 }
 
+// ModDown + sigma_g(c0) of one rotation of C ciphertexts: ACC [C][2][n+K][N]
+// -> out [C][2][n][N].  grid (N/4/256, 2, C)
+__global__ void __launch_bounds__(256) k_moddown_rotate(const uint32_t *__restrict__ in,
+                                                        const uint32_t *__restrict__ acc,
+                                                        uint32_t *__restrict__ out, int n, int N, uint32_t ginv,
+                                                        KsDev ks, const PrimeConst *__restrict__ pc) {
+    const int k4 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k4 * 4 >= N) return;
+    const int b = blockIdx.y, ct = blockIdx.z, nb = n + ks.K;
+    moddown_rotate_body(in + (size_t)ct * 2 * n * N, acc + ((size_t)ct * 2 + b) * nb * N,
+                        out + ((size_t)ct * 2 + b) * n * N, b, n, N, ginv, ks, pc, k4);
+}
+
+// The same for a batch of rotations of C ciphertexts: ACC [C][count][2][n+K][N]
+// (k_ks_rot) -> out [n_ct_total][n_rot_total][2][n][N] at ciphertext ct0 + ct,
+// rotation r0 + r.  grid (N/4/256, 2 * count, C)
+__global__ void __launch_bounds__(256) k_moddown_rot_many(const uint32_t *__restrict__ in,
+                                                          const uint32_t *__restrict__ acc,
+                                                          uint32_t *__restrict__ out, int n, int N, RotBatch rb,
+                                                          int n_rot_total, int r0, KsDev ks,
+                                                          const PrimeConst *__restrict__ pc) {
+    const int k4 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k4 * 4 >= N) return;
+    const int b = blockIdx.y & 1, r = blockIdx.y >> 1, ct = blockIdx.z, nb = n + ks.K;
+    const size_t ct_words = (size_t)2 * n * N;
+    moddown_rotate_body(in + (size_t)ct * ct_words, acc + (((size_t)ct * rb.count + r) * 2 + b) * nb * N,
+                        out + ((size_t)ct * n_rot_total + r0 + r) * ct_words + (size_t)b * n * N, b, n, N,
+                        rb.ginv[r], ks, pc, k4);
+}
+
+// g^{-1} mod 2N: the odd residues mod 2N form a group of order N, so g^{N-1}
+static uint64_t galois_inverse(uint64_t g, uint64_t N) {
+    const uint64_t two_n = 2 * N;
+    uint64_t ginv = 1, base = g % two_n;
+    for (uint64_t e = N - 1; e; e >>= 1) {
+        if (e & 1) ginv = ginv * base % two_n;
+        base = base * base % two_n;
+    }
+    return ginv;
+}
+
+// ciphertexts per hoisted-rotation chunk: U and one rotation batch's sums per
+// ciphertext (words)
+static size_t hoist_words_per_ct(const bcn_ctx *c, int n) {
+    const size_t nb = (size_t)n + c->K, dnum = ((size_t)n + c->alpha - 1) / c->alpha;
+    return (dnum * nb + (size_t)kRotBatch * 2 * nb) * c->N;
+}
+constexpr int kHoistChunk = 8;
+
 }  // namespace
 }  // namespace bcn
 
 using namespace bcn;
+
+extern "C" bcn_status bcn_op_rotate_many_workspace_bytes(const bcn_ctx *c, int level, int n_ct, size_t *bytes) {
+    if (!c || !bytes || level < 1 || level > c->L || n_ct < 0) return fail(BCN_E_INVAL, "bad argument");
+    const size_t chunk = (size_t)std::min(std::max(n_ct, 1), kHoistChunk);
+    *bytes = chunk * hoist_words_per_ct(c, level) * 4;
+    return BCN_OK;
+}
+
+extern "C" bcn_status bcn_op_rotate_many(const bcn_ctx *c, int level, const uint32_t *const *gk_evals,
+                                         const int *steps, int n_rot, const uint32_t *in, int n_ct, uint32_t *out,
+                                         void *ws, size_t ws_bytes, void *stream) {
+    if (!c) return fail(BCN_E_INVAL, "bcn_op_rotate_many: null context");
+    if (c->device < 0) return fail(BCN_E_INVAL, "bcn_op_rotate_many: host-only ctx");
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess || cur != c->device)
+        return fail(BCN_E_INVAL, "bcn_op_rotate_many: the ctx's device must be current");
+    if (level < 1 || level > c->L || n_ct < 0 || n_rot < 0 || c->K < 1)
+        return fail(BCN_E_INVAL, "bcn_op_rotate_many: bad level or count");
+    if (n_ct == 0 || n_rot == 0) return BCN_OK;
+    if (!gk_evals || !steps) return fail(BCN_E_INVAL, "bcn_op_rotate_many: null key or step array");
+    size_t need = 0;
+    BCN_TRY(bcn_op_rotate_many_workspace_bytes(c, level, n_ct, &need));
+    if (!ws || ws_bytes < need) return fail(BCN_E_BUDGET, "bcn_op_rotate_many: workspace too small");
+    auto a16 = [](const void *p) { return ((uintptr_t)p & 15) == 0; };
+    if (!in || !out || !a16(in) || !a16(out) || !a16(ws))
+        return fail(BCN_E_INVAL, "bcn_op_rotate_many: null or unaligned buffer");
+    const size_t N = c->N, n = (size_t)level, ct_words = 2 * n * N;
+    const uint32_t *in_end = in + (size_t)n_ct * ct_words, *out_end = out + (size_t)n_ct * n_rot * ct_words;
+    if (in < out_end && out < in_end) return fail(BCN_E_INVAL, "bcn_op_rotate_many: in and out overlap");
+    const uint32_t half = (uint32_t)(N / 2);
+    for (int r = 0; r < n_rot; r++) {
+        const uint32_t s = (uint32_t)(((long long)steps[r] % (long long)half + half) % half);
+        if (s != 0 && (!gk_evals[r] || !a16(gk_evals[r])))
+            return fail(BCN_E_INVAL, "bcn_op_rotate_many: missing or unaligned Galois key");
+    }
+    const CoreFns *f = core_fns(c->logN);
+    if (!f) return fail(BCN_E_INVAL, "unsupported ring degree");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t nb = n + c->K, dnum = (n + c->alpha - 1) / c->alpha;
+    const int chunk = std::min(n_ct, kHoistChunk);
+    uint32_t *U = reinterpret_cast<uint32_t *>(ws);
+    uint32_t *acc = U + (size_t)chunk * dnum * nb * N;
+    for (int o0 = 0; o0 < n_ct; o0 += chunk) {
+        const int C = std::min(chunk, n_ct - o0);
+        const uint32_t *x = in + (size_t)o0 * ct_words;
+        bool any = false;
+        for (int r = 0; r < n_rot; r++) {  // identity rotations are copies
+            const uint32_t s = (uint32_t)(((long long)steps[r] % (long long)half + half) % half);
+            if (s != 0) {
+                any = true;
+                continue;
+            }
+            for (int k = 0; k < C; k++)
+                if (cudaMemcpyAsync(out + ((size_t)(o0 + k) * n_rot + r) * ct_words, x + (size_t)k * ct_words,
+                                    ct_words * 4, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                    return fail(BCN_E_CUDA, "bcn_op_rotate_many: copy failed");
+        }
+        if (!any) continue;
+        BCN_TRY(f->modup_hoist(c, level, x, U, C, st));
+        RotBatch rb;
+        rb.count = 0;
+        int r0 = -1;
+        // gather the non-identity rotations into batches of consecutive indices
+        auto flush = [&]() -> bcn_status {
+            if (rb.count == 0) return BCN_OK;
+            BCN_TRY(f->ks_rot(c, level, U, rb, acc, C, st));
+            k_moddown_rot_many<<<dim3((unsigned)((N / 4 + 255) / 256), 2 * rb.count, C), 256, 0, st>>>(
+                x, acc, out + (size_t)o0 * n_rot * ct_words, level, (int)N, rb, n_rot, r0, ks_dev(c), c->d_pc);
+            BCN_TRY(check_launch("k_moddown_rot_many"));
+            rb.count = 0;
+            r0 = -1;
+            return BCN_OK;
+        };
+        for (int r = 0; r < n_rot; r++) {
+            const uint32_t s = (uint32_t)(((long long)steps[r] % (long long)half + half) % half);
+            if (s == 0 || (r0 >= 0 && r != r0 + rb.count) || rb.count == kRotBatch) BCN_TRY(flush());
+            if (s == 0) continue;
+            if (r0 < 0) r0 = r;
+            const uint64_t g = bcn_galois_elt(c, (int)s);
+            rb.gk[rb.count] = gk_evals[r];
+            rb.g[rb.count] = (uint32_t)g;
+            rb.ginv[rb.count] = (uint32_t)galois_inverse(g, N);
+            rb.count++;
+        }
+        BCN_TRY(flush());
+    }
+    return BCN_OK;
+}
 
 extern "C" bcn_status bcn_op_rotate(const bcn_ctx *c, int level, const uint32_t *gk, int steps, const uint32_t *in,
                                     int n_ct, uint32_t *out, void *ws, size_t ws_bytes, void *stream) {
@@ -118,13 +253,7 @@ extern "C" bcn_status bcn_op_rotate(const bcn_ctx *c, int level, const uint32_t 
     if (in < out_end && out < in_end) return fail(BCN_E_INVAL, "bcn_op_rotate: in and out overlap");
     const CoreFns *f = core_fns(c->logN);
     if (!f) return fail(BCN_E_INVAL, "unsupported ring degree");
-    // g^{-1} mod 2N: the odd residues mod 2N form a group of order N, so g^{N-1}
-    const uint64_t g = bcn_galois_elt(c, steps), two_n = 2 * N;
-    uint64_t ginv = 1, base = g;
-    for (uint64_t e = N - 1; e; e >>= 1) {
-        if (e & 1) ginv = ginv * base % two_n;
-        base = base * base % two_n;
-    }
+    const uint64_t g = bcn_galois_elt(c, steps), ginv = galois_inverse(g, N);
     cudaStream_t st = (cudaStream_t)stream;
     const int n = level, chunk = ks_default_chunk(c, level, n_ct);
     uint32_t *d, *d2n, *acc;

@@ -5,14 +5,15 @@ in registers and shared memory; what bounds them is integer instruction issue,
 not HBM.  Their roofline is therefore the rate of their own arithmetic with the
 data in registers: the NTT core's lazy forward and inverse butterflies and the
 key switch's Montgomery multiply-add, each timed here with CUDA events over a
-full-occupancy launch of the library's microbenchmark kernel.  The raw
-multiply-add (low and high half) and modular-addition rates are measured beside
-them for context.
+full-occupancy launch of the library's microbenchmark kernel, beside the Shoup
+multiply-add by a constant of the basis conversions.  The raw multiply-add (low
+and high half) and modular-addition rates are measured for context.
 
-A kernel class whose work is f forward butterflies, i inverse butterflies and m
-multiply-adds would take at least f / r_fwd + i / r_inv + m / r_mad seconds;
-its algorithmic operations (10 per butterfly, 5 per multiply-add) over that
-time are its peak (`mix_peak`).
+A kernel class whose work is f forward butterflies, i inverse butterflies, m
+Montgomery and s Shoup multiply-adds would take at least
+f / r_fwd + i / r_inv + m / r_mont + s / r_shoup seconds; its algorithmic
+operations (10 per butterfly, 5 per multiply-add) over that time are its peak
+(`mix_peak`).
 """
 from __future__ import annotations
 
@@ -25,6 +26,7 @@ KINDS = {
     3: "butterfly_fwd",
     4: "butterfly_inv",
     5: "mont_muladd",
+    6: "shoup_muladd",
 }
 OPS_BUTTERFLY, OPS_MULADD = 10, 5
 
@@ -75,11 +77,12 @@ def measure(device: int = 0, target_ms: float = 30.0, reps: int = 5) -> dict:
     return out
 
 
-def mix_peak(rates: dict, fwd: float, inv: float, mad: float) -> float:
+def mix_peak(rates: dict, fwd: float, inv: float, mont: float, shoup: float) -> float:
     """Algorithmic integer operations per second of a kernel whose work is
-    `fwd` forward and `inv` inverse butterflies and `mad` multiply-adds, at
-    the measured register-resident rates."""
+    `fwd` forward and `inv` inverse butterflies, `mont` products of two
+    variables (Montgomery) and `shoup` products by constants (Shoup), each a
+    multiply-add, at the measured register-resident rates."""
     t = (fwd / rates["butterfly_fwd"]["units_per_s"] + inv / rates["butterfly_inv"]["units_per_s"]
-         + mad / rates["mont_muladd"]["units_per_s"])
-    ops = OPS_BUTTERFLY * (fwd + inv) + OPS_MULADD * mad
+         + mont / rates["mont_muladd"]["units_per_s"] + shoup / rates["shoup_muladd"]["units_per_s"])
+    ops = OPS_BUTTERFLY * (fwd + inv) + OPS_MULADD * (mont + shoup)
     return ops / t if t > 0 else 0.0

@@ -68,7 +68,11 @@ def test_alu_ops_match_enumeration(name):
     split = bench.alu_work(cfg)
     for k, (n_fwd, passes, n_inv) in work.items():
         assert ops[k] == (n_fwd + n_inv) * bf + passes * N * bench.OPS_MULADD, k
-        assert (split[k]["fwd"], split[k]["inv"], split[k]["mad"]) == (n_fwd, n_inv, passes), k
+        assert (split[k]["fwd"], split[k]["inv"], split[k]["mont"] + split[k]["shoup"]) == (n_fwd, n_inv, passes), k
+    # products of two variables: the square's three, the key switch's two per digit and target
+    sq_mont = sum(workloads.cipher_layer_io(l)[1] * 3 * n
+                  for l, n in zip(cfg["cipher"], workloads.level_schedule(cfg)[0]) if l["square"])
+    assert split["square"]["mont"] == sq_mont and split["moddown_rescale"]["mont"] == 0
 
 
 def test_cryptonets_ntt_counts_by_hand():
