@@ -425,6 +425,23 @@ bcn_status bcn_op_rotate_many_workspace_bytes(const bcn_ctx *ctx, int level, int
 bcn_status bcn_op_rotate_many(const bcn_ctx *ctx, int level, const uint32_t *const *gk_evals, const int *steps,
                               int n_rot, const uint32_t *in_dev, int n_ct, uint32_t *out_dev, void *workspace_dev,
                               size_t workspace_bytes, void *cuda_stream);
+/* Homomorphic fully connected layer by the diagonal method (App. D): y = W x
+ * for every image block of the slots, computed as
+ *     Rescale_{q_{level-1}}( sum_r u_r * Rot(x, r) )
+ * over the rotations r = i - j that W needs, u_r the r-th diagonal of W laid
+ * out in the slots (u_r[b B + j] = W[j][j + r]) and encoded at the scale
+ * q_{level-1}, so that the rescale keeps the ciphertext's scale.  The rotations
+ * share one ModUp (bcn_op_rotate_many); each rotated copy is transformed, the
+ * products are summed in the NTT domain and transformed back once.
+ * steps[n_rot], gk_evals[n_rot] as for bcn_op_rotate_many; diag_ntt
+ * [n_rot][level][N] the encoded diagonals of the same order in the NTT domain
+ * (bcn_op_ntt forward of the coefficient-form encodings); in [n_ct][2][level][N]
+ * -> out [n_ct][2][level-1][N], coefficient form, device; workspace of
+ * bcn_op_fc_diag_workspace_bytes(level, n_rot).  level >= 2. */
+bcn_status bcn_op_fc_diag_workspace_bytes(const bcn_ctx *ctx, int level, int n_rot, size_t *bytes);
+bcn_status bcn_op_fc_diag(const bcn_ctx *ctx, int level, const uint32_t *const *gk_evals, const int *steps, int n_rot,
+                          const uint32_t *diag_ntt_dev, const uint32_t *in_dev, int n_ct, uint32_t *out_dev,
+                          void *workspace_dev, size_t workspace_bytes, void *cuda_stream);
 /* Ciphertext-plaintext product then rescale (App. A Mult(c, u) with an encoded
  * u -- the masks of App. D's packed layers): (c0 u, c1 u) in R_{Q_level}, then
  * the rescale by q_{level-1}.  Encode u at scale q_{level-1} to keep the

@@ -641,19 +641,80 @@ def unpack_bhw(z: np.ndarray, n: int, h: int, w: int) -> np.ndarray:
     return z[:, :n * h * w].reshape(C, n, h, w).transpose(1, 0, 2, 3)
 
 
-def conv_bhw(P: "Params", level: int, gks: dict, w_int: np.ndarray, cts: np.ndarray, w_img: int) -> np.ndarray:
+def conv_bhw(P: "Params", level: int, gks: dict, w_int: np.ndarray, cts: np.ndarray, w_img: int,
+             gap: int = 1) -> np.ndarray:
     """Convolution of BHW-packed ciphertexts by rotations (App. D, homomorphic
-    convolutional layer): out[co] = sum_{ci,i,j} w[co][ci][i][j] Rot(ct[ci], i w_img + j),
-    k x k kernel, stride 1.  Output (y, x) of each image sits in the input's slot
-    of (y, x); slots with y > h-k or x > w_img-k hold neighbours' values (mask them).
+    convolutional layer): out[co] = sum_{ci,i,j} w[co][ci][i][j] Rot(ct[ci], gap (i w_img + j)),
+    k x k kernel.  The input map's logical pixel (y, x) sits in slot
+    gap (y w_img + x) of its image's block (gap 1: every pixel of the segment;
+    gap s after a stride-s layer), so the rotation by gap (i w_img + j) brings
+    pixel (y + i, x + j) to the slot of (y, x): output (y, x) of each image sits
+    in the input's slot of (y, x).  A stride-s layer is this sum with the
+    outputs at logical positions (s y', s x') kept by a mask (mask_bhw); slots
+    past the valid outputs hold neighbours' values.
     gks: {steps: Galois key}; cts [cin][2][level][N] -> [cout][2][level][N]."""
     cout, cin, k, _ = w_int.shape
     rots = []
     for ci in range(cin):
         for i in range(k):
             for j in range(k):
-                r = i * w_img + j
+                r = gap * (i * w_img + j)
                 rots.append(cts[ci] if r == 0 else P.rotate(level, gks[r], r, cts[ci:ci + 1])[0])
     x = np.stack(rots)
     idx = np.tile(np.arange(cin * k * k, dtype=np.int32), (cout, 1))
     return P.mac(level, idx, w_int.reshape(cout, -1).astype(np.int8), x)
+
+
+def mask_bhw(n: int, h: int, w: int, k: int, stride: int, gap: int, N: int) -> np.ndarray:
+    """0/1 slot vector [N/2] of the outputs a valid k x k, stride-s convolution
+    keeps, for n images' h x w segments (slot b h w + y w + x) whose input
+    pixels sit at gap `gap`: output (y', x') of the logical (h/gap) x (w/gap)
+    map is at logical input position (s y', s x'), i.e. at slot
+    b h w + gap s (y' w + x'), for s y' + k <= h/gap and s x' + k <= w/gap."""
+    hl, wl = h // gap, w // gap
+    m = np.zeros((n, h, w))
+    ys = [gap * stride * yy for yy in range((hl - k) // stride + 1)]
+    xs = [gap * stride * xx for xx in range((wl - k) // stride + 1)]
+    for y in ys:
+        m[:, y, xs] = 1.0
+    return m.reshape(-1) if n * h * w == N // 2 else np.concatenate([m.reshape(-1), np.zeros(N // 2 - n * h * w)])
+
+
+def fc_diagonals(W: np.ndarray, n_img: int, block: int, N: int) -> dict:
+    """Slot vectors of the diagonal method (App. D, homomorphic fully connected
+    layer) for y = W x, W [n2][n1], with image b's input x in slots
+    [b block, b block + n1) and its output y in slots [b block, b block + n2):
+    {r: u_r} over the rotations r = i - j (-(n2-1) <= r <= n1-1) with
+    u_r[b block + j] = W[j][j + r] wherever 0 <= j < n2 and 0 <= j + r < n1,
+    zero elsewhere, so that y = sum_r u_r * Rot(x, r) slot by slot."""
+    n2, n1 = W.shape
+    assert block >= max(n1, n2) and n_img * block <= N // 2
+    out = {}
+    for r in range(-(n2 - 1), n1):
+        u = np.zeros(N // 2)
+        for j in range(n2):
+            if 0 <= j + r < n1:
+                for b in range(n_img):
+                    u[b * block + j] = W[j][j + r]
+        if np.any(u):
+            out[r] = u
+    return out
+
+
+def fc_diag(P: "Params", level: int, gks: dict, W: np.ndarray, ct: np.ndarray, n_img: int, block: int) -> np.ndarray:
+    """Homomorphic fully connected layer by the diagonal method (App. D): the
+    input ciphertext rotated by every r of fc_diagonals, each rotation multiplied
+    by its diagonal u_r (Mult(c, u), u encoded at the scale q_{level-1} so that
+    the rescale by q_{level-1} keeps the ciphertext's scale), the products summed,
+    then one rescale.  Integer weights W [n2][n1].  ct [2][level][N] ->
+    [2][level-1][N].  gks: {r mod N/2: Galois key}."""
+    half = P.N // 2
+    diags = fc_diagonals(W, n_img, block, P.N)
+    acc = None
+    for r, u in diags.items():
+        rc = ct[None] if r % half == 0 else P.rotate(level, gks[r % half], r % half, ct[None])
+        pt = encode(u[None], P.N, float(P.q[level - 1]), P.q[:level])[0]
+        prod = P.mul_plain(level, rc, pt)[0].astype(np.uint64)
+        acc = prod if acc is None else acc + prod
+        acc %= np.array(P.q[:level], dtype=np.uint64)[None, :, None]
+    return P.rescale(level, acc.astype(np.uint32)[None])[0]

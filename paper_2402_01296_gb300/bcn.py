@@ -111,6 +111,8 @@ _SIGS = {
     "bcn_op_square_relin_rescale_noalloc": (_I, [_P, _I, _P, _P, _I, _P, _P]),
     "bcn_op_rotate_many_workspace_bytes": (_I, [_P, _I, _I, ctypes.POINTER(_SZ)]),
     "bcn_op_rotate_many": (_I, [_P, _I, _P, _P, _I, _P, _I, _P, _P, _SZ, _P]),
+    "bcn_op_fc_diag_workspace_bytes": (_I, [_P, _I, _I, ctypes.POINTER(_SZ)]),
+    "bcn_op_fc_diag": (_I, [_P, _I, _P, _P, _I, _P, _P, _I, _P, _P, _SZ, _P]),
     "bcn_int_peak_grid": (_I, [_I, ctypes.POINTER(_I)]),
     "bcn_int_peak_launch": (_I, [_I, _I, _P, _SZ, _P, ctypes.POINTER(_D)]),
 }
@@ -367,13 +369,7 @@ class Context:
         [n_ct][len(steps)][2][level][N].  gk_evals: {steps: prepared Galois key}
         (steps taken mod N/2; 0 needs no key)."""
         n_rot = len(steps)
-        half = self.N // 2
-        ptrs = (ctypes.c_void_p * max(1, n_rot))()
-        st = (ctypes.c_int * max(1, n_rot))()
-        for i, r in enumerate(steps):
-            st[i] = int(r)
-            key = gk_evals.get(r, gk_evals.get(r % half)) if r % half else None
-            ptrs[i] = _dev_ptr(key, self.evk_words()) if key is not None else None
+        ptrs, st = self._key_table(gk_evals, steps)
         nb = _SZ(0)
         _check(lib().bcn_op_rotate_many_workspace_bytes(self._h, level, n_ct, ctypes.byref(nb)),
                "bcn_op_rotate_many_workspace_bytes")
@@ -384,6 +380,32 @@ class Context:
                                         n_ct, _dev_ptr(out_dev, n_ct * n_rot * 2 * level * self.N),
                                         workspace.data_ptr(), workspace.numel() * workspace.element_size(),
                                         _stream(stream)), "bcn_op_rotate_many")
+
+    def _key_table(self, gk_evals: dict, steps: list):
+        half = self.N // 2
+        ptrs = (ctypes.c_void_p * max(1, len(steps)))()
+        st = (ctypes.c_int * max(1, len(steps)))()
+        for i, r in enumerate(steps):
+            st[i] = int(r)
+            key = gk_evals.get(r, gk_evals.get(r % half)) if r % half else None
+            ptrs[i] = _dev_ptr(key, self.evk_words()) if key is not None else None
+        return ptrs, st
+
+    def op_fc_diag(self, level, gk_evals: dict, steps: list, diag_ntt, in_dev, n_ct, out_dev, stream=None):
+        """bcn_op_fc_diag: the diagonal-method dense layer; diag_ntt [len(steps)][level][N]
+        (NTT domain), in [n_ct][2][level][N] -> out [n_ct][2][level-1][N]."""
+        import torch
+
+        n_rot = len(steps)
+        ptrs, st = self._key_table(gk_evals, steps)
+        nb = _SZ(0)
+        _check(lib().bcn_op_fc_diag_workspace_bytes(self._h, level, n_rot, ctypes.byref(nb)),
+               "bcn_op_fc_diag_workspace_bytes")
+        ws = torch.empty(max(1, (nb.value + 3) // 4), dtype=torch.int32, device=f"cuda:{self.device}")
+        _check(lib().bcn_op_fc_diag(self._h, level, ptrs, st, n_rot, _dev_ptr(diag_ntt, n_rot * level * self.N),
+                                    _dev_ptr(in_dev, n_ct * 2 * level * self.N), n_ct,
+                                    _dev_ptr(out_dev, n_ct * 2 * (level - 1) * self.N), ws.data_ptr(), nb.value,
+                                    _stream(stream)), "bcn_op_fc_diag")
 
     def op_mul_plain_rescale(self, level, in_dev, n_ct, pt_dev, out_dev, stream=None):
         """(c0 u, c1 u), then rescale: in [n_ct][2][level][N], pt [level][N] -> out at level - 1."""

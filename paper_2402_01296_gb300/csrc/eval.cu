@@ -204,6 +204,14 @@ __global__ void __launch_bounds__(256) k_rescale(const uint32_t *__restrict__ in
     }
 }
 
+// rescale of C ciphertexts (coefficient form): in [C][2][n][N] -> out [C][2][n-1][N]
+bcn_status launch_rescale(const bcn_ctx *c, int n, const uint32_t *in, uint32_t *out, int C, cudaStream_t st) {
+    if (C <= 0) return BCN_OK;
+    k_rescale<<<dim3((unsigned)((c->N + 255) / 256), 2, (unsigned)C), 256, 0, st>>>(in, out, n, c->N, ks_dev(c),
+                                                                                    c->d_pc);
+    return check_launch("k_rescale");
+}
+
 // x -> x * R * N^{-1} mod q over rows of N words; row r uses prime prime_of(pm, r).
 // The evaluation key in this form makes one Montgomery product per digit give
 // the key product already divided by N, which the key-switching kernel's

@@ -121,6 +121,42 @@ __global__ void __launch_bounds__(256) k_moddown_rot_many(const uint32_t *__rest
                         rb.ginv[r], ks, pc, k4);
 }
 
+// Sum of products in the NTT domain: out[b][i][k] = sum_r R[r][b][i][k] U[r][i][k]
+// mod q_i (R [n_terms][2][n][N] the rotated ciphertexts, U [n_terms][n][N] the
+// diagonal plaintexts, both canonical).  Products below 2^60 summed in 64 bits,
+// reduced every 15 terms.  Four coefficients a thread.  grid (N/4/256, n, 2)
+__global__ void __launch_bounds__(256) k_mul_acc(const uint32_t *__restrict__ R, const uint32_t *__restrict__ U,
+                                                 uint32_t *__restrict__ out, int n_terms, int n, int N,
+                                                 const PrimeConst *__restrict__ pc) {
+    const int k4 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k4 * 4 >= N) return;
+    const int i = blockIdx.y, b = blockIdx.z;
+    const uint32_t q = pc[i].q;
+    const uint64_t mu = pc[i].barrett;
+    const size_t ct_words = (size_t)2 * n * N;
+    uint64_t acc[4] = {0, 0, 0, 0};
+    int cnt = 0;
+    for (int r = 0; r < n_terms; r++) {
+        const uint4 x = __ldg(reinterpret_cast<const uint4 *>(R + r * ct_words + ((size_t)b * n + i) * N) + k4);
+        const uint4 u = __ldg(reinterpret_cast<const uint4 *>(U + ((size_t)r * n + i) * N) + k4);
+        acc[0] += (uint64_t)x.x * u.x;
+        acc[1] += (uint64_t)x.y * u.y;
+        acc[2] += (uint64_t)x.z * u.z;
+        acc[3] += (uint64_t)x.w * u.w;
+        if (++cnt == 15) {
+#pragma unroll
+            for (int z = 0; z < 4; z++) acc[z] = barrett_reduce64(acc[z], q, mu);
+            cnt = 0;
+        }
+    }
+    uint4 o;
+    o.x = barrett_reduce64(acc[0], q, mu);
+    o.y = barrett_reduce64(acc[1], q, mu);
+    o.z = barrett_reduce64(acc[2], q, mu);
+    o.w = barrett_reduce64(acc[3], q, mu);
+    reinterpret_cast<uint4 *>(out + ((size_t)b * n + i) * N)[k4] = o;
+}
+
 // g^{-1} mod 2N: the odd residues mod 2N form a group of order N, so g^{N-1}
 static uint64_t galois_inverse(uint64_t g, uint64_t N) {
     const uint64_t two_n = 2 * N;
@@ -229,6 +265,47 @@ extern "C" bcn_status bcn_op_rotate_many(const bcn_ctx *c, int level, const uint
             rb.count++;
         }
         BCN_TRY(flush());
+    }
+    return BCN_OK;
+}
+
+extern "C" bcn_status bcn_op_fc_diag_workspace_bytes(const bcn_ctx *c, int level, int n_rot, size_t *bytes) {
+    if (!c || !bytes || level < 2 || level > c->L || n_rot < 1) return fail(BCN_E_INVAL, "bad argument");
+    size_t rot = 0;
+    BCN_TRY(bcn_op_rotate_many_workspace_bytes(c, level, 1, &rot));
+    const size_t ct_bytes = (size_t)2 * level * c->N * 4;
+    *bytes = rot + (size_t)n_rot * ct_bytes + ct_bytes;
+    return BCN_OK;
+}
+
+extern "C" bcn_status bcn_op_fc_diag(const bcn_ctx *c, int level, const uint32_t *const *gk_evals, const int *steps,
+                                     int n_rot, const uint32_t *diag_ntt, const uint32_t *in, int n_ct,
+                                     uint32_t *out, void *ws, size_t ws_bytes, void *stream) {
+    if (!c) return fail(BCN_E_INVAL, "bcn_op_fc_diag: null context");
+    if (level < 2 || level > c->L || n_ct < 0 || n_rot < 1) return fail(BCN_E_INVAL, "bcn_op_fc_diag: bad level");
+    if (n_ct == 0) return BCN_OK;
+    size_t need = 0;
+    BCN_TRY(bcn_op_fc_diag_workspace_bytes(c, level, n_rot, &need));
+    if (!ws || ws_bytes < need) return fail(BCN_E_BUDGET, "bcn_op_fc_diag: workspace too small");
+    auto a16 = [](const void *p) { return ((uintptr_t)p & 15) == 0; };
+    if (!diag_ntt || !in || !out || !a16(diag_ntt) || !a16(in) || !a16(out) || !a16(ws))
+        return fail(BCN_E_INVAL, "bcn_op_fc_diag: null or unaligned buffer");
+    const size_t N = c->N, n = (size_t)level, ct_words = 2 * n * N;
+    size_t rot_bytes = 0;
+    BCN_TRY(bcn_op_rotate_many_workspace_bytes(c, level, 1, &rot_bytes));
+    char *w = reinterpret_cast<char *>(ws);
+    uint32_t *R = reinterpret_cast<uint32_t *>(w + rot_bytes);
+    uint32_t *acc = R + (size_t)n_rot * ct_words;
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int k = 0; k < n_ct; k++) {
+        const uint32_t *x = in + (size_t)k * ct_words;
+        BCN_TRY(bcn_op_rotate_many(c, level, gk_evals, steps, n_rot, x, 1, R, ws, rot_bytes, stream));
+        BCN_TRY(launch_ntt(c, R, (size_t)n_rot * 2 * n, data_map(level), false, st));
+        k_mul_acc<<<dim3((unsigned)((N / 4 + 255) / 256), (unsigned)n, 2), 256, 0, st>>>(R, diag_ntt, acc, n_rot,
+                                                                                       level, (int)N, c->d_pc);
+        BCN_TRY(check_launch("k_mul_acc"));
+        BCN_TRY(launch_ntt(c, acc, 2 * n, data_map(level), true, st));
+        BCN_TRY(launch_rescale(c, level, acc, out + (size_t)k * 2 * (n - 1) * N, 1, st));
     }
     return BCN_OK;
 }

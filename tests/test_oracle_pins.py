@@ -806,3 +806,86 @@ def test_ntt_domain_moddown_rescale_identity(K):
         o = ((A[i] * pinv[i] + D[i] - f) % q[i] * pow(qt, -1, q[i])) % q[i]
         got = P.ntt_inv(i, o.astype(np.uint32)).astype(np.int64)
         assert np.array_equal(got, ref[i])
+
+
+# --------------------------------------------------------------------------
+# App. D: fully connected layer by the diagonal method, strided packed convolution
+# --------------------------------------------------------------------------
+def test_fc_diagonals_reproduce_the_matrix_product():
+    """Slot arithmetic alone (no encryption): sum_r u_r * (x rotated left by r)
+    equals W x in every image's block, exactly (integers), for tall, wide and
+    square W and blocks wider than both sides."""
+    N = 256
+    rng = np.random.default_rng(80)
+    for n2, n1, n_img, block in ((10, 20, 4, 32), (30, 7, 3, 40), (16, 16, 8, 16)):
+        W = rng.integers(-127, 128, (n2, n1))
+        x = np.zeros(N // 2, dtype=np.int64)
+        xs = rng.integers(-1000, 1000, (n_img, n1))
+        for b in range(n_img):
+            x[b * block:b * block + n1] = xs[b]
+        diags = O.fc_diagonals(W, n_img, block, N)
+        assert set(diags) <= set(range(-(n2 - 1), n1))
+        y = sum(u * np.roll(x, -r) for r, u in diags.items())
+        for b in range(n_img):
+            assert np.array_equal(y[b * block:b * block + n2], W @ xs[b])
+            assert not np.any(y[b * block + n2:(b + 1) * block])
+
+
+def test_fc_diag_decrypts_to_the_matrix_product():
+    P = O.Params(10, 4, 1, 1)
+    n2, n1, n_img, block = 10, 20, 4, 32
+    rng = np.random.default_rng(81)
+    W = rng.integers(-127, 128, (n2, n1))
+    xs = rng.uniform(-1, 1, (n_img, n1))
+    z = np.zeros((1, P.N // 2))
+    for b in range(n_img):
+        z[0, b * block:b * block + n1] = xs[b]
+    sk, _ = P.keygen(3)
+    S = 2.0**30
+    ct = P.encrypt(sk, O.encode(z, P.N, S, P.q), P.L, 4)[0]
+    half = P.N // 2
+    gks = {r % half: P.galois_keygen(sk, r % half, 90 + r % half)
+           for r in O.fc_diagonals(W, n_img, block, P.N) if r % half}
+    out = O.fc_diag(P, P.L, gks, W, ct, n_img, block)
+    dec = O.decode(O.crt_centered(P.decrypt(sk, out[None], P.L - 1), P.q[:P.L - 1]), P.N, half, S)[0]
+    for b in range(n_img):
+        assert np.abs(dec[b * block:b * block + n2] - W @ xs[b]).max() < 1e-3
+        assert np.abs(dec[b * block + n2:(b + 1) * block]).max() < 1e-3
+
+
+def test_strided_conv_then_gapped_conv_is_the_convolution_chain():
+    """A stride-2 3x3 convolution of BHW-packed maps (rotations, integer
+    weights, a mask keeping the strided outputs) leaves its outputs at gap 2;
+    a 2x2 convolution on that gap-2 map (rotations scaled by the gap) puts its
+    outputs in the same gap-2 slots.  Against torch conv2d: the stride-2 conv,
+    then a stride-1 conv of its output (absolute error 1e-3 on the first, whose
+    values are O(10^2); relative 1e-5 on the second, O(10^4) after two layers of
+    weights up to 127)."""
+    P = O.Params(10, 5, 1, 1)
+    n, cin, c1, c2, h, w = 3, 2, 2, 2, 12, 12
+    rng = np.random.default_rng(82)
+    x = rng.uniform(-1, 1, (n, cin, h, w))
+    w1 = rng.integers(-127, 128, (c1, cin, 3, 3)).astype(np.int8)
+    w2 = rng.integers(-127, 128, (c2, c1, 2, 2)).astype(np.int8)
+    sk, _ = P.keygen(3)
+    S = 2.0**30
+    cts = P.encrypt(sk, O.encode(O.pack_bhw(x, P.N), P.N, S, P.q), P.L, 4)
+    steps1 = {(i * w + j) for i in range(3) for j in range(3)} - {0}
+    steps2 = {2 * (i * w + j) for i in range(2) for j in range(2)} - {0}
+    gks = {r: P.galois_keygen(sk, r, 100 + r) for r in steps1 | steps2}
+    y1 = O.conv_bhw(P, P.L, gks, w1, cts, w)                       # stride 1 everywhere
+    m1 = O.mask_bhw(n, h, w, 3, 2, 1, P.N)                         # keep (2y', 2x')
+    mpt = O.encode(m1[None], P.N, float(P.q[P.L - 1]), P.q)[0]
+    y1 = P.rescale(P.L, P.mul_plain(P.L, y1, mpt))
+    lv = P.L - 1
+    y2 = O.conv_bhw(P, lv, gks, w2, y1, w, gap=2)
+    ref1 = F.conv2d(torch.from_numpy(x), torch.from_numpy(w1.astype(np.float64)), stride=2).numpy()
+    ref2 = F.conv2d(torch.from_numpy(ref1), torch.from_numpy(w2.astype(np.float64))).numpy()
+    S1 = S  # the mask at scale q_top and its rescale keep the scale
+    d1 = O.unpack_bhw(O.decode(O.crt_centered(P.decrypt(sk, y1, lv), P.q[:lv]), P.N, P.N // 2, S1), n, h, w)
+    d2 = O.unpack_bhw(O.decode(O.crt_centered(P.decrypt(sk, y2, lv), P.q[:lv]), P.N, P.N // 2, S1), n, h, w)
+    assert np.abs(d1[:, :, 0:10:2, 0:10:2] - ref1).max() < 1e-3           # 5 x 5 strided outputs at gap 2
+    keep = np.zeros((h, w), bool)
+    keep[0:10:2, 0:10:2] = True
+    assert np.abs(d1[:, :, ~keep]).max() < 1e-3                            # the mask zeroed the rest
+    assert np.abs(d2[:, :, 0:8:2, 0:8:2] - ref2).max() < 1e-5 * np.abs(ref2).max()  # its 4 x 4 outputs
