@@ -619,7 +619,7 @@ def run_ours(args, cfg, rank, world, local_rank):
                                         for k, v in rates.items()} if peak_clocks.get("sm_mhz") else None,
                      "mix_peak_Tops": {k: v / 1e12 for k, v in mix.items()},
                      "clocks": peak_clocks,
-                     "units": "instructions (imad_lo, imad_hi), modular additions (modadd), butterflies "
+                     "units": "instructions (imad_lo, imad_hi, imad_wide, dp4a), modular additions (modadd), butterflies "
                               "(butterfly_fwd, butterfly_inv), multiply-adds (mont_muladd, shoup_muladd)"},
         "ntt_GBps": ntt_b / (ntt_ms / 1e3) / 1e9 if ntt_ms else None,
         "keyswitch_GBps": ks_b / (ks_ms / 1e3) / 1e9 if ks_ms else None,

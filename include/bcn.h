@@ -467,12 +467,14 @@ bcn_status bcn_op_rescale(const bcn_ctx *ctx, int level, const uint32_t *in_dev,
  *   4  lazy inverse NTT butterflies of the evaluator's NTT core (32 a round)
  *   5  lazy Montgomery multiply-add of the key switch's running sums (16 a round)
  *   6  Shoup multiply-add by a constant, as in the basis conversions (16 a round)
- * units_out: the operations the launch performs (instructions for kinds 0-1,
- * modular additions, butterflies or multiply-adds for 2-6), to divide by the
+ *   7  signed 32 x 32 -> 64-bit multiply-add, the CUDA-core MAC's step (16 a round)
+ *   8  4-way int8 x uint8 dot product with 32-bit accumulation, dp4a (16 a round)
+ * units_out: the operations the launch performs (instructions for kinds 0-1 and
+ * 7-8, modular additions, butterflies or multiply-adds for 2-6), to divide by the
  * launch's time.  sink_dev: device memory of at least bcn_int_peak_grid's
  * block count in uint32 words (written only if a result equals an improbable
  * value; it keeps the work from being optimised away).  BCN_E_INVAL for a kind
- * outside 0..6, iters < 1 or a null pointer; BCN_E_BUDGET if the sink is too
+ * outside 0..8, iters < 1 or a null pointer; BCN_E_BUDGET if the sink is too
  * small. */
 bcn_status bcn_int_peak_grid(int kind, int *blocks);
 bcn_status bcn_int_peak_launch(int kind, int iters, uint32_t *sink_dev, size_t sink_words, void *cuda_stream,

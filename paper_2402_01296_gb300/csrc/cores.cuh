@@ -778,6 +778,9 @@ __device__ __forceinline__ void ks_rot_body(const uint32_t *__restrict__ U, RotB
             }
         }
     }
+    // the gathers read the staged limb at any position; the inverse NTT's first
+    // exchange is warp-local and writes without a block barrier of its own
+    __syncthreads();
     uint32_t x[R];
 #pragma unroll 1
     for (int b = 0; b < 2; b++) {

@@ -16,6 +16,9 @@
 //                                            (product, addition, min), 16 a round
 //   6  Shoup multiply-add by a constant     the basis conversions' step (shoup_mul,
 //                                            add_mod), 16 a round
+//   7  signed 32 x 32 -> 64 multiply-add    16 independent chains (IMAD.WIDE: the
+//                                            CUDA-core MAC's inner step)
+//   8  4-way int8 x uint8 dot product       16 independent chains (dp4a)
 // Kinds 3-6 use the exact device functions of the evaluator (NttCore's passes
 // with the key switch's FMA-pipe choice, mont_mul_lazy, shoup_mul), so their rates are
 // what the NTT-based kernels could reach with their data in registers and no
@@ -57,6 +60,9 @@ __global__ void __launch_bounds__(kPeakThreads) k_int_peak(uint32_t *__restrict_
         kp[u] = (uint32_t)(((uint64_t)k[u] << 32) / q);
     }
     uint32_t xs = seed % q;
+    long long acc64[KIND == 7 ? kPeakRegs : 1];
+#pragma unroll
+    for (int u = 0; u < (KIND == 7 ? kPeakRegs : 1); u++) acc64[u] = (long long)seed * (u + 1);
     const ModQ m(q, one);
 #pragma unroll 1
     for (int it = 0; it < iters; it++) {
@@ -84,11 +90,22 @@ __global__ void __launch_bounds__(kPeakThreads) k_int_peak(uint32_t *__restrict_
                 x[u] = min(s, s + nq2);
             }
             xs = x[kPeakRegs - 1];  // the next round multiplies the last sum (no dynamic register index)
-        } else {
+        } else if constexpr (KIND == 6) {
 #pragma unroll
             for (int u = 0; u < kPeakRegs; u++) x[u] = add_mod(x[u], shoup_mul(xs, k[u], kp[u], q), q);
             xs = x[kPeakRegs - 1];
+        } else if constexpr (KIND == 7) {
+#pragma unroll
+            for (int u = 0; u < kPeakRegs; u++) acc64[u] += (long long)(int)a * (int)(x[u] + (uint32_t)u);
+        } else {
+#pragma unroll
+            for (int u = 0; u < kPeakRegs; u++)  // signed weights x unsigned bytes, as a byte-plane MAC would use it
+                asm volatile("dp4a.s32.u32 %0, %1, %2, %0;" : "+r"(x[u]) : "r"(a), "r"(k[u] ^ (uint32_t)it));
         }
+    }
+    if constexpr (KIND == 7) {
+#pragma unroll
+        for (int u = 0; u < kPeakRegs; u++) x[u] ^= (uint32_t)acc64[u] ^ (uint32_t)(acc64[u] >> 32);
     }
     uint32_t v = xs;
 #pragma unroll
@@ -108,7 +125,8 @@ bcn_status peak_grid(int *grid) {
 }
 
 // operations one thread performs per round
-constexpr double kUnitsPerRound[7] = {kPeakRegs, kPeakRegs, kPeakRegs, 32, 32, kPeakRegs, kPeakRegs};
+constexpr double kUnitsPerRound[9] = {kPeakRegs, kPeakRegs, kPeakRegs, 32, 32, kPeakRegs, kPeakRegs,
+                                      kPeakRegs, kPeakRegs};
 
 }  // namespace
 }  // namespace bcn
@@ -127,7 +145,9 @@ bcn_status bcn_int_peak_grid(int kind, int *blocks) {
     case 4: return peak_grid<4>(blocks);
     case 5: return peak_grid<5>(blocks);
     case 6: return peak_grid<6>(blocks);
-    default: return fail(BCN_E_INVAL, "bcn_int_peak_grid: kind must be 0..6");
+    case 7: return peak_grid<7>(blocks);
+    case 8: return peak_grid<8>(blocks);
+    default: return fail(BCN_E_INVAL, "bcn_int_peak_grid: kind must be 0..8");
     }
 }
 
@@ -153,7 +173,9 @@ bcn_status bcn_int_peak_launch(int kind, int iters, uint32_t *sink_dev, size_t s
     case 3: k_int_peak<3><<<grid, kPeakThreads, 0, st>>>(sink_dev, iters, q, 1u, a, b, qneg_inv, magic); break;
     case 4: k_int_peak<4><<<grid, kPeakThreads, 0, st>>>(sink_dev, iters, q, 1u, a, b, qneg_inv, magic); break;
     case 5: k_int_peak<5><<<grid, kPeakThreads, 0, st>>>(sink_dev, iters, q, 1u, a, b, qneg_inv, magic); break;
-    default: k_int_peak<6><<<grid, kPeakThreads, 0, st>>>(sink_dev, iters, q, 1u, a, b, qneg_inv, magic); break;
+    case 6: k_int_peak<6><<<grid, kPeakThreads, 0, st>>>(sink_dev, iters, q, 1u, a, b, qneg_inv, magic); break;
+    case 7: k_int_peak<7><<<grid, kPeakThreads, 0, st>>>(sink_dev, iters, q, 1u, a, b, qneg_inv, magic); break;
+    default: k_int_peak<8><<<grid, kPeakThreads, 0, st>>>(sink_dev, iters, q, 1u, a, b, qneg_inv, magic); break;
     }
     s = check_launch("k_int_peak");
     if (s != BCN_OK) return s;

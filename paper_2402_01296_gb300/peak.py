@@ -27,6 +27,8 @@ KINDS = {
     4: "butterfly_inv",
     5: "mont_muladd",
     6: "shoup_muladd",
+    7: "imad_wide",
+    8: "dp4a",
 }
 OPS_BUTTERFLY, OPS_MULADD = 10, 5
 

@@ -1,7 +1,9 @@
-"""Continuous-batching server: requests of two models from several clients,
-arriving while others run, admitted under a device-memory budget.  Every
-result must equal the stand-alone evaluation of the same request (bit-exact),
-in the mix and on the per-request path."""
+"""Continuous-batching server on the GPU: requests of two models from several
+clients, arriving while others run, admitted by their own working sets under a
+device-memory budget.  Every result must equal the stand-alone evaluation of
+the same request (bit-exact), in the mix, under a budget that holds only a few
+working sets, with malformed and cancelled requests among them, and on the
+per-request path."""
 import numpy as np
 import pytest
 import torch
@@ -49,34 +51,58 @@ def _fresh(reqs):
             for r in reqs]
 
 
-def test_budget_limits_lanes_and_results_equal_standalone(world):
+def _keys(models):
+    return sum(e.numel() * 4 for _, evks in models.values() for e in evks)
+
+
+def test_tight_budget_admits_by_working_set_and_results_equal_standalone(world):
     models, images, reqs, refs = world
-    keys = sum(e.numel() * 4 for _, evks in models.values() for e in evks)
-    lane = max(m.workspace_bytes() for m, _ in models.values()) + sum(
-        serve.request_bytes(m) for m, _ in models.values())
-    # asked for 3 lanes, the budget holds 2: requests queue for a free lane
-    srv = serve.Server(models, lanes=3, budget_bytes=keys + 2 * lane + lane // 2)
-    assert len(srv.lanes) == 2 and srv.budget.used == keys + 2 * lane
+    specs = {n: serve.model_spec(m, len(e)) for n, (m, e) in models.items()}
+    big, small = specs["cryptonets"].working_set(), specs["cnn3_small"].working_set()
+    arena = big + 2 * small  # one CryptoNets-scale request and two small ones at a time
+    srv = serve.Server(models, lanes=8, budget_bytes=_keys(models) + arena)
     done = srv.run(_fresh(reqs), keep_outputs=True)
     for r in done:
-        assert r.done >= r.arrival
+        assert r.status == "ok" and r.done >= r.arrival
         assert np.array_equal(r.out, refs[r.rid])
+    assert srv.scheduler.peak_used <= arena and srv.scheduler.arena.used == 0
     stats = serve.latency_stats(done, images)
     assert stats["requests"] == 12 and stats["p99_ms"] >= stats["p50_ms"] > 0
     with pytest.raises(MemoryError):
-        serve.Server(models, lanes=1, budget_bytes=keys + lane // 2)
+        serve.Server(models, lanes=1, budget_bytes=_keys(models) + small // 2)
 
 
 def test_mixed_in_flight_equals_alone(world):
-    """Many requests in flight on several lanes: the same residues as alone."""
+    """Many requests in flight on several streams: the same residues as alone."""
     models, images, reqs, refs = world
-    srv = serve.Server(models, lanes=4, budget_bytes=1 << 40)
+    srv = serve.Server(models, lanes=6, budget_bytes=1 << 40)
     burst = _fresh(reqs)
     for r in burst:
         r.arrival = 0.0  # all at once
     done = srv.run(burst, keep_outputs=True)
     for r in done:
-        assert np.array_equal(r.out, refs[r.rid])
+        assert r.status == "ok" and np.array_equal(r.out, refs[r.rid])
+
+
+def test_failures_in_the_mix_leave_the_others_exact(world):
+    """A malformed request (a limb short), one for a client without a key, one
+    cancelled before it starts and one whose producer stalls: each ends with
+    its status, and every other request still equals its stand-alone result."""
+    models, images, reqs, refs = world
+    srv = serve.Server(models, lanes=4, budget_bytes=1 << 40, payload_timeout=0.05)
+    mix = _fresh(reqs)
+    short = mix[0]
+    short.cts = np.ascontiguousarray(short.cts[:, :, :-1])
+    mix[1].client = 7
+    mix[2].cancel()
+    mix[3].ready = lambda: False
+    done = srv.run(mix, keep_outputs=True)
+    want = {0: "rejected", 1: "rejected", 2: "cancelled", 3: "timeout"}
+    for r in done:
+        assert r.status == want.get(r.rid, "ok"), (r.rid, r.status, r.detail)
+        if r.status == "ok":
+            assert np.array_equal(r.out, refs[r.rid])
+    assert srv.scheduler.arena.used == 0
 
 
 def test_plain_path_equals_standalone(world):

@@ -1,5 +1,8 @@
-"""Host logic of the server that needs no GPU: memory-budget admission and
-Poisson arrivals."""
+"""Host logic of the server that needs no GPU: the arena allocator, admission
+by each request's working set, and the statuses of injected failures (a
+malformed request, one too large for the arena, a cancelled request before and
+during its run, a producer that stalls and one that is late but finishes),
+over a fake executor that completes a request after a set number of polls."""
 import numpy as np
 import pytest
 
@@ -19,3 +22,151 @@ def test_poisson_arrivals_rate():
     t = serve.poisson_arrivals(500.0, 20.0, seed=3)
     assert np.all(np.diff(t) > 0) and t[-1] <= 20.0
     assert abs(len(t) / 20.0 - 500.0) < 5 * np.sqrt(500.0 / 20.0)  # within 5 sigma of the rate
+
+
+def test_arena_first_fit_alignment_and_coalescing():
+    a = serve.Arena(4096, align=256)
+    x = a.alloc(1)
+    y = a.alloc(300)        # rounds up to 512
+    z = a.alloc(256)
+    assert (x, y, z) == (0, 256, 768) and a.used == 1024
+    assert a.alloc(4096) is None
+    a.free(y)
+    assert a.alloc(256) == 256   # first fit reuses the hole
+    a.free(256)
+    a.free(x)
+    a.free(z)
+    assert a.free_list == [(0, 4096)] and a.used == 0  # everything coalesced back
+    rng = np.random.default_rng(0)
+    live = []
+    for _ in range(2000):  # random traffic never overlaps and never leaks
+        if live and rng.random() < 0.5:
+            a.free(live.pop(rng.integers(len(live))))
+        else:
+            off = a.alloc(int(rng.integers(1, 900)))
+            if off is not None:
+                live.append(off)
+        spans = sorted((o, a.live[o]) for o in a.live)
+        assert all(o1 + s1 <= o2 for (o1, s1), (o2, _) in zip(spans, spans[1:]))
+        assert all(o % 256 == 0 for o in a.live)
+        assert a.used + sum(s for _, s in a.free_list) == 4096
+    for off in live:
+        a.free(off)
+    assert a.free_list == [(0, 4096)]
+
+
+class FakeExecutor:
+    """Completes a request after `polls[model]` polls; records starts."""
+
+    def __init__(self, polls):
+        self.polls, self.started, self.live = polls, [], 0
+        self.max_live = 0
+
+    def start(self, req, offs):
+        self.started.append(req.rid)
+        self.live += 1
+        self.max_live = max(self.max_live, self.live)
+        return [req, self.polls[req.model], offs]
+
+    def poll(self, h):
+        h[1] -= 1
+        if h[1] <= 0:
+            if h[1] == 0:
+                self.live -= 1
+            return True
+        return False
+
+    def finish(self, h, req):
+        req.out = np.full(1, req.rid, dtype=np.uint32)
+
+
+def specs():
+    small = serve.ModelSpec(cts_shape=(4, 2, 3, 16), pt_shapes=[(2, 3, 16)], out_shape=(2, 2, 2, 16),
+                            workspace=3000, n_clients=4)
+    big = serve.ModelSpec(cts_shape=(16, 2, 5, 32), pt_shapes=[(8, 5, 32), (4, 4, 32)], out_shape=(2, 2, 3, 32),
+                          workspace=30000, n_clients=4)
+    return {"small": small, "big": big}
+
+
+def make(rid, model, client=0, arrival=0.0, **kw):
+    s = specs()[model]
+    return serve.Request(rid=rid, client=client, model=model, arrival=arrival,
+                         cts=np.zeros(s.cts_shape, np.uint32), pts=[np.zeros(p, np.uint32) for p in s.pt_shapes], **kw)
+
+
+def test_admission_by_working_set_lets_small_requests_pass():
+    sp = specs()
+    cap = sp["big"].working_set() + sp["small"].working_set()  # one big and one small fit together
+    ex = FakeExecutor({"small": 3, "big": 50})
+    sch = serve.Scheduler(sp, cap, slots=8, executor=ex)
+    reqs = [make(0, "big"), make(1, "big"), make(2, "small"), make(3, "small"), make(4, "small")]
+    done = sch.run(reqs, t0=None, keep_outputs=True, sleep=False)
+    assert [r.status for r in done] == ["ok"] * 5
+    assert all(int(r.out[0]) == r.rid for r in done)
+    # the second big request waits for the first; the small ones overtake it
+    assert ex.started.index(1) > ex.started.index(2) and ex.started.index(1) > ex.started.index(4)
+    assert sch.peak_used <= cap and sch.arena.used == 0 and sch.arena.free_list == [(0, cap)]
+
+
+def test_slots_bound_requests_in_flight():
+    sp = specs()
+    ex = FakeExecutor({"small": 4, "big": 4})
+    sch = serve.Scheduler(sp, 1 << 30, slots=2, executor=ex)
+    done = sch.run([make(i, "small") for i in range(9)], t0=None, sleep=False)
+    assert all(r.status == "ok" for r in done) and ex.max_live == 2
+
+
+def test_injected_failures_surface_as_statuses():
+    sp = specs()
+    ex = FakeExecutor({"small": 3, "big": 5})
+    sch = serve.Scheduler(sp, sp["big"].working_set() * 2, slots=4, executor=ex, payload_timeout=0.05)
+    bad_level = make(0, "small")
+    bad_level.cts = np.zeros((4, 2, 2, 16), np.uint32)            # one limb short
+    bad_pts = make(1, "big")
+    bad_pts.pts = bad_pts.pts[:1]                                  # a feature plaintext missing
+    bad_client = make(2, "small", client=9)                        # no key for this client
+    cancelled = make(3, "small")
+    cancelled.cancel()
+    stalled = make(4, "small", ready=lambda: False)                # the producer never finishes
+    flag = {"n": 0}
+
+    def late():  # the producer finishes after a few polls, well within the timeout
+        flag["n"] += 1
+        return flag["n"] > 5
+
+    late_ok = make(5, "small", ready=late)
+    good = make(6, "big")
+    unknown = make(7, "small")
+    unknown.model = "nope"
+    done = sch.run([bad_level, bad_pts, bad_client, cancelled, stalled, late_ok, good, unknown], t0=None,
+                   keep_outputs=True, sleep=False)
+    st = {r.rid: r.status for r in done}
+    assert st == {0: "rejected", 1: "rejected", 2: "rejected", 3: "cancelled", 4: "timeout", 5: "ok", 6: "ok",
+                  7: "rejected"}
+    assert "limb" in done[0].detail or "expected" in done[0].detail
+    assert 3 not in ex.started and 4 not in ex.started  # never reserved, never started
+    assert sch.arena.used == 0
+
+
+def test_cancel_in_flight_discards_the_result_and_frees_its_memory():
+    sp = specs()
+
+    class CancelOnStart(FakeExecutor):
+        def start(self, req, offs):
+            h = super().start(req, offs)
+            if req.rid == 1:
+                req.cancel()  # the client gives up while its request runs
+            return h
+
+    ex = CancelOnStart({"small": 3, "big": 3})
+    sch = serve.Scheduler(sp, 1 << 20, slots=4, executor=ex)
+    done = sch.run([make(0, "small"), make(1, "small"), make(2, "small")], t0=None, keep_outputs=True, sleep=False)
+    assert [r.status for r in done] == ["ok", "cancelled", "ok"]
+    assert done[1].out is None and sch.arena.used == 0
+
+
+def test_too_large_for_the_arena():
+    sp = specs()
+    sch = serve.Scheduler(sp, sp["small"].working_set(), slots=4, executor=FakeExecutor({"small": 1, "big": 1}))
+    done = sch.run([make(0, "big"), make(1, "small")], t0=None, sleep=False)
+    assert [r.status for r in done] == ["too_large", "ok"]
