@@ -720,19 +720,44 @@ def run_uneven(args, rank, world, local_rank):
     batch.close()
     del batch
     torch.cuda.empty_cache()
-    # the plain per-request path: the same 64 evaluations one after another, no graph
+    # the same tuned models one after another, no graph (what the graph and lanes add)
     big = max((it[0] for it in items), key=lambda m: m.workspace_bytes())
     ws = big.alloc_workspace()
-    plain_ms = []
-    for rep in range(2):
-        s0, e0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        s0.record()
-        for (m, evk, cts, pts, out) in items:
-            m.eval(evk, cts, pts, out, ws)
-        e0.record()
-        torch.cuda.synchronize()
-        plain_ms.append(s0.elapsed_time(e0))
+
+    def time_seq(seq_items, reps=2):
+        best = None
+        for _ in range(reps):
+            s0, e0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            s0.record()
+            for (m, evk, cts, pts, out) in seq_items:
+                m.eval(evk, cts, pts, out, ws)
+            e0.record()
+            torch.cuda.synchronize()
+            t = s0.elapsed_time(e0)
+            best = t if best is None else min(best, t)
+        return best
+
+    seq_tuned_ms = time_seq(items)
+    # the plain per-request path: each evaluation alone, every kernel in order
+    # on one stream (no chunk halves side by side, no feature transforms ahead),
+    # the configuration's own digit size and the default chunk, no graph
+    plain_ctx, plain_evk = {}, {}
+    plain_items = []
+    for cfg, (m_t, _, cts, pts, out) in zip(cfgs, items):
+        if cfg["log_n"] not in plain_ctx:
+            cx = bcn.Context.from_config(cfg, device)
+            _, ek = cx.keygen(workloads.SEED_KEYS)
+            plain_ctx[cfg["log_n"]], plain_evk[cfg["log_n"]] = cx, cx.evk_prepare(bcn.to_device(ek, dev))
+        wq = [bcn.quantize(w) for w in workloads.cipher_weights(cfg)]
+        m = bcn.Model(plain_ctx[cfg["log_n"]], cfg["cipher"], [x for x, _ in wq], [y for _, y in wq])
+        m.set_overlap(False)
+        plain_items.append((m, plain_evk[cfg["log_n"]], cts, pts, out))
+    del ws
+    torch.cuda.empty_cache()
+    big = max((it[0] for it in plain_items), key=lambda m: m.workspace_bytes())
+    ws = big.alloc_workspace()
+    plain_ms = [time_seq(plain_items)]
     value, mean_ms = replica_summary(statistics.mean(ms), images, None)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": max(1, args.warmup),
@@ -744,7 +769,12 @@ def run_uneven(args, rank, world, local_rank):
                    "counts": {str(k): sum(1 for c in cfgs if c["log_n"] == k) for k in (12, 13, 14)}},
         "p50_ms": statistics.median(ms), "p99_ms": float(np.percentile(ms, 99)),
         "tuning": {"lanes_ms": {str(k): round(v, 3) for k, v in lane_res.items()}, "alpha_ms": alpha_note},
-        "plain_sequential": {"value": images / (min(plain_ms) / 1e3), "ms_per_step": min(plain_ms)},
+        "plain_sequential": {"value": images / (min(plain_ms) / 1e3), "ms_per_step": min(plain_ms),
+                             "path": "each evaluation alone, every kernel in order on one stream, the "
+                                     "configuration's digit size and the default chunk, no graph"},
+        "speedup_vs_plain": min(plain_ms) / statistics.mean(ms),
+        "sequential_tuned_models": {"value": images / (seq_tuned_ms / 1e3), "ms_per_step": seq_tuned_ms,
+                                    "path": "the batch's own (tuned) models one after another, no graph"},
         "clocks": clk,
     }
     if rank == 0:

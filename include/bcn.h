@@ -235,6 +235,13 @@ bcn_status bcn_model_set_chunk(bcn_model *m, int chunk);
  * the rest on the CUDA cores; 1 runs every MAC on the CUDA cores.  Results are
  * identical either way. */
 bcn_status bcn_model_set_mac_impl(bcn_model *m, int impl);
+/* Streams of one evaluation: 1 (default) runs each square layer's chunk in two
+ * halves side by side (the second on an internal stream forked from and joined
+ * back to the caller's) and transforms the feature plaintexts that join
+ * NTT-domain ciphertexts on another internal stream while earlier layers run;
+ * 0 runs every kernel in order on the caller's stream (the plain per-request
+ * path: one kernel at a time).  Results are identical either way. */
+bcn_status bcn_model_set_overlap(bcn_model *m, int on);
 bcn_status bcn_model_get_info(const bcn_model *m, bcn_model_info *out);
 /* per layer: live level at its input and its output count (arrays of n_layers) */
 bcn_status bcn_model_layers(const bcn_model *m, int *level_out, int *n_out_out);

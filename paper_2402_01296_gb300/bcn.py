@@ -81,6 +81,7 @@ _SIGS = {
     "bcn_model_destroy": (_I, [_P]),
     "bcn_model_set_chunk": (_I, [_P, _I]),
     "bcn_model_set_mac_impl": (_I, [_P, _I]),
+    "bcn_model_set_overlap": (_I, [_P, _I]),
     "bcn_model_get_info": (_I, [_P, ctypes.POINTER(_ModelInfo)]),
     "bcn_model_layers": (_I, [_P, _P, _P]),
     "bcn_model_scales": (_I, [_P, _D, _P, ctypes.POINTER(_D)]),
@@ -497,6 +498,10 @@ class Model:
 
     def set_chunk(self, chunk: int):
         _check(lib().bcn_model_set_chunk(self._h, int(chunk)), "bcn_model_set_chunk")
+
+    def set_overlap(self, on: bool):
+        """bcn_model_set_overlap: False gives the plain path (every kernel in order on one stream)."""
+        _check(lib().bcn_model_set_overlap(self._h, 1 if on else 0), "bcn_model_set_overlap")
 
     def set_mac_impl(self, impl: int):
         """0: tensor cores where eligible (default); 1: CUDA cores only."""

@@ -150,6 +150,7 @@ struct bcn_model {
     int chunk;          // ciphertexts per key-switching chunk
     int chunk_request;  // 0: automatic
     int mac_impl = 0;   // 0: tensor cores where eligible, 1: CUDA cores only
+    int overlap = 1;    // 1: a square layer's chunk halves and the feature transforms on extra streams
     // copy streams of bcn_eval_host (created on first use) and, per workspace,
     // the event after the last evaluation that read its staged inputs; guarded
     // by copy_mu

@@ -596,6 +596,12 @@ bcn_status bcn_model_set_chunk(bcn_model *m, int chunk) {
     return BCN_OK;
 }
 
+bcn_status bcn_model_set_overlap(bcn_model *m, int on) {
+    if (!m || on < 0 || on > 1) return fail(BCN_E_INVAL, "bcn_model_set_overlap: bad argument");
+    m->overlap = on;
+    return BCN_OK;
+}
+
 bcn_status bcn_model_set_mac_impl(bcn_model *m, int impl) {
     if (!m || impl < 0 || impl > 1) return fail(BCN_E_INVAL, "bcn_model_set_mac_impl: bad argument");
     m->mac_impl = impl;
@@ -723,7 +729,7 @@ static bcn_status eval_impl(const bcn_model *m, const uint32_t *evk, const uint3
     } split_guard{split_ev};
     bool has_square = false;
     for (auto &l : m->layers) has_square |= l.square != 0;
-    if (!m->prof.on && has_square) {
+    if (!m->prof.on && m->overlap && has_square) {
         bcn_model *mm = const_cast<bcn_model *>(m);
         std::lock_guard<std::mutex> lock(mm->split_mu);
         if (!mm->split_stream && cudaStreamCreateWithFlags(&mm->split_stream, cudaStreamNonBlocking) != cudaSuccess)
@@ -770,7 +776,7 @@ static bcn_status eval_impl(const bcn_model *m, const uint32_t *evk, const uint3
     cudaStream_t aux = nullptr;
     bool any_pt_ntt = false;
     for (uint32_t *q : pt_ntt) any_pt_ntt |= q != nullptr;
-    if (!m->prof.on && any_pt_ntt) {
+    if (!m->prof.on && m->overlap && any_pt_ntt) {
         bcn_model *mm = const_cast<bcn_model *>(m);
         {
             std::lock_guard<std::mutex> lock(mm->split_mu);
