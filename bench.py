@@ -817,6 +817,7 @@ def run_serve(args, rank, world, local_rank):
             payload[(name, c)] = (res(ctx.q, (model.n_in, 2)),
                                   [res(ctx.q[:sh[1]], (sh[0],)) for sh in model.pt_shapes()])
     srv = serve.Server(models, lanes=args.lanes, budget_bytes=budget, device=device)
+    srv.warm(args.lanes)  # idle slots with their evaluations captured for every client key
     rates = [float(r) for r in args.rates.split(",")]
     results = []
     for rate in rates:
@@ -848,7 +849,12 @@ def run_serve(args, rank, world, local_rank):
         "data": "synthetic (uniform residues as request ciphertexts and encoded features)",
         "config": {"workload": "serve: Poisson arrivals, 70% cnn3_small (N=4096, 2048 images) / 30% cryptonets "
                                "(N=8192, 4096 images), 16 clients with resident keys, 120 GiB budget",
-                   "lanes": len(srv.lanes), "seconds_per_rate": args.serve_seconds},
+                   "lanes": len(srv.lanes), "seconds_per_rate": args.serve_seconds,
+                   "admission": "per request working set (inputs, features, output, workspace) from the arena "
+                                "left after the keys; idle working sets kept as slots with captured graphs, "
+                                "reclaimed for other models on demand",
+                   "slots_created": srv.scheduler.n_slots, "slot_evictions": srv.scheduler.evictions,
+                   "arena_peak_bytes": srv.scheduler.peak_used},
         "rates": results,
     }
     if rank == 0:

@@ -12,7 +12,13 @@ working set fits in what the requests in flight leave of the arena, so small
 requests pass large ones that do not fit yet (first fit over the arrival-order
 queue, with a bounded number of requests allowed to overtake a waiting one);
 requests that arrive while others are on the GPU start at once on their own
-streams, and their copies and kernels overlap on the device.
+streams, and their copies and kernels overlap on the device.  A completed
+request's working set stays reserved as an idle slot of its model (its device
+buffers keep their addresses, so the executor can replay the evaluation it
+captured for them); idle slots are handed to the next requests of that model
+and are returned to the arena, least recently used first, as soon as a
+request of another model needs the memory (with cache_slots=False a working
+set goes back to the arena at completion).
 
 Every request ends with a status: "ok"; "rejected" (malformed: an unknown
 model or client, or ciphertexts / plaintexts whose level, limb count or shape
@@ -22,11 +28,12 @@ completes but the result is discarded); "timeout" (its producer did not
 finish the payload -- Request.ready() stayed false -- within `payload_timeout`
 seconds of its arrival).  Nothing of a request that does not end "ok" is kept.
 
-The scheduling (admission, arena, statuses) is host logic over an executor
-that starts a request's copies and evaluation and reports completion; the GPU
-executor runs bcn_eval on device views into the arena, one stream per request
-in flight.  The per-request baseline ("plain") serves the same arrivals one at
-a time on one stream.
+The scheduling (admission, arena, slots, statuses) is host logic over an
+executor that starts a request's copies and evaluation and reports completion;
+the GPU executor copies the payload into the slot's device buffers and replays
+a CUDA graph of bcn_eval captured once per (slot, client key), one stream per
+request in flight.  The per-request baseline ("plain") serves the same
+arrivals one at a time on one stream.
 """
 from __future__ import annotations
 
@@ -160,35 +167,82 @@ def validate(req: Request, spec: ModelSpec) -> str:
     return ""
 
 
+@dataclasses.dataclass
+class Slot:
+    """One request's working set in the arena: offsets of its parts."""
+    sid: int
+    model: str
+    offs: list
+
+
 class Scheduler:
     """Admission and completion over an executor (host logic only).
 
-    executor: start(req, offsets) -> handle (copies + evaluation queued),
-    poll(handle) -> bool, finish(handle, req) (fetch the result into req.out).
-    specs: {model name: ModelSpec}; capacity: arena bytes (the budget left
-    after the keys); slots: requests in flight at most; overtake: how many later
-    requests may start ahead of a waiting one before admission stops at it."""
+    executor: start(req, slot) -> handle (copies + evaluation queued),
+    poll(handle) -> bool, finish(handle, req) (fetch the result into req.out),
+    drop(slot) (the slot's memory goes back to the arena).  specs: {model name:
+    ModelSpec}; capacity: arena bytes (the budget left after the keys); slots:
+    requests in flight at most; overtake: how many later requests may start
+    ahead of a waiting one before admission stops at it; cache_slots: keep a
+    completed request's working set as an idle slot of its model."""
 
     def __init__(self, specs: dict, capacity: int, slots: int, executor, payload_timeout: float = 1.0,
-                 overtake: int = 64):
+                 overtake: int = 64, cache_slots: bool = True):
         self.specs, self.executor = specs, executor
         self.arena = Arena(capacity)
         self.slots, self.payload_timeout, self.overtake = int(slots), float(payload_timeout), int(overtake)
+        self.cache_slots = cache_slots
+        self.idle = []  # idle slots, least recently used first
+        self.n_slots = 0
         self.peak_used = 0
+        self.evictions = 0
 
-    def _admit(self, req: Request, now: float, in_flight: list):
-        spec = self.specs[req.model]
+    def _carve(self, spec):
         offs = []
         for nbytes in spec.parts(self.arena.align):
             off = self.arena.alloc(nbytes)
             if off is None:
                 for o in offs:
                     self.arena.free(o)
-                return False
+                return None
             offs.append(off)
+        return offs
+
+    def _drop(self, slot: Slot):
+        for o in slot.offs:
+            self.arena.free(o)
+        self.executor.drop(slot)
+
+    def _acquire(self, model: str):
+        """An idle slot of `model`, else a new one carved from the arena, after
+        returning idle slots of other models (least recently used first) while
+        it does not fit."""
+        for i, sl in enumerate(self.idle):
+            if sl.model == model:
+                return self.idle.pop(i)
+        spec = self.specs[model]
+        offs = self._carve(spec)
+        while offs is None:
+            victim = next((i for i, sl in enumerate(self.idle) if sl.model != model), None)
+            if victim is None:
+                return None
+            self._drop(self.idle.pop(victim))
+            self.evictions += 1
+            offs = self._carve(spec)
+        self.n_slots += 1
         self.peak_used = max(self.peak_used, self.arena.used)
-        in_flight.append((req, offs, self.executor.start(req, offs)))
-        return True
+        return Slot(self.n_slots - 1, model, offs)
+
+    def _release(self, slot: Slot):
+        if self.cache_slots:
+            self.idle.append(slot)
+        else:
+            self._drop(slot)
+
+    def close(self):
+        """Return every idle slot to the arena."""
+        while self.idle:
+            self._drop(self.idle.pop())
 
     def run(self, requests: list, t0: float | None = None, keep_outputs: bool = False, sleep: bool = True):
         """Serve `requests`; returns them (arrival order) with status and completion times."""
@@ -218,7 +272,7 @@ class Scheduler:
                     queue.append(r)
             progressed = False
             for item in list(in_flight):  # completions
-                r, offs, h = item
+                r, slot, h = item
                 if self.executor.poll(h):
                     if r.cancelled:
                         end(r, "cancelled", "cancelled while in flight; result discarded")
@@ -226,8 +280,7 @@ class Scheduler:
                         if keep_outputs:
                             self.executor.finish(h, r)
                         end(r, "ok")
-                    for o in offs:
-                        self.arena.free(o)
+                    self._release(slot)
                     in_flight.remove(item)
                     progressed = True
             # admission: first fit over the queue, in arrival order
@@ -244,8 +297,10 @@ class Scheduler:
                     continue
                 if len(in_flight) >= self.slots:
                     break
-                if self._admit(r, now, in_flight):
+                slot = self._acquire(r.model)
+                if slot is not None:
                     queue.remove(r)
+                    in_flight.append((r, slot, self.executor.start(r, slot)))
                     progressed = True
                 else:
                     skipped += 1
@@ -259,59 +314,87 @@ class Scheduler:
 
 
 class GpuExecutor:
-    """Runs a request on the device: copies its payload into its arena views on
-    a stream of its own, evaluates with bcn_eval on those views and copies the
-    output back to a page-locked host buffer."""
+    """Runs a request on the device: copies its payload into its slot's device
+    buffers on a stream of its own, replays the evaluation captured for that
+    slot and the request's client key (bcn_batch of one item, captured on first
+    use), and copies the output back to a page-locked host buffer."""
 
     def __init__(self, models: dict, arena_bytes: int, streams: int, device: int = 0):
         import torch
 
-        self.torch = torch
+        from . import bcn
+
+        self.torch, self.bcn = torch, bcn
         self.models = models
         self.dev = f"cuda:{device}"
         self.buf = torch.empty(max(1, arena_bytes // 4), dtype=torch.int32, device=self.dev)
         self.streams = [torch.cuda.Stream(device=device) for _ in range(max(1, streams))]
         self.free_streams = list(range(len(self.streams)))
-        self.out_pool = {name: [] for name in models}
+        self.views, self.graphs, self.out_host = {}, {}, {}
 
     def _view(self, off, shape):
         n = int(np.prod(shape))
         return self.buf[off // 4: off // 4 + n].view(*shape)
 
-    def start(self, req: Request, offs):
+    def _slot_views(self, slot):
+        v = self.views.get(slot.sid)
+        if v is None:
+            model, _ = self.models[slot.model]
+            N, L = model.ctx.N, model.ctx.L
+            offs = slot.offs
+            cts = self._view(offs[0], (model.n_in, 2, L, N))
+            pts = [self._view(o, tuple(sh)) for o, sh in zip(offs[1:-2], model.pt_shapes())]
+            out = self._view(offs[-2], tuple(model.out_shape()))
+            ws = self.buf[offs[-1] // 4: offs[-1] // 4 + (model.workspace_bytes() + 3) // 4]
+            v = (cts, pts, out, ws)
+            self.views[slot.sid] = v
+            self.out_host[slot.sid] = self.torch.empty(model.out_shape(), dtype=self.torch.int32).pin_memory()
+        return v
+
+    def graph(self, slot, client: int):
+        key = (slot.sid, client)
+        g = self.graphs.get(key)
+        if g is None:
+            model, evks = self.models[slot.model]
+            cts, pts, out, ws = self._slot_views(slot)
+            g = self.bcn.Batch([(model, evks[client], cts, pts, out)], 1, workspace=ws)
+            self.graphs[key] = g
+        return g
+
+    def start(self, req: Request, slot: Slot):
         torch = self.torch
-        model, evks = self.models[req.model]
-        parts = [tuple(req.cts.shape)] + [tuple(np.asarray(p).shape) for p in req.pts] + [model.out_shape()]
-        cts = self._view(offs[0], parts[0])
-        pts = [self._view(o, s) for o, s in zip(offs[1:-2], parts[1:-1])]
-        out = self._view(offs[-2], parts[-1])
-        ws = self.buf[offs[-1] // 4: offs[-1] // 4 + (model.workspace_bytes() + 3) // 4]
+        cts, pts, out, ws = self._slot_views(slot)
+        g = self.graph(slot, req.client)
         si = self.free_streams.pop()
         st = self.streams[si]
-        pool = self.out_pool[req.model]
-        oh = pool.pop() if pool else torch.empty(model.out_shape(), dtype=torch.int32).pin_memory()
+        oh = self.out_host[slot.sid]
         with torch.cuda.stream(st):
             cts.copy_(torch.from_numpy(np.asarray(req.cts).view(np.int32)), non_blocking=True)
             for d, h in zip(pts, req.pts):
                 d.copy_(torch.from_numpy(np.asarray(h).view(np.int32)), non_blocking=True)
-            model.eval(evks[req.client], cts, pts, out, ws, stream=st)
+            g.launch(st)
             oh.copy_(out, non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(st)
-        return [si, ev, oh, req.model, False]
+        return [si, ev, oh, False]
 
     def poll(self, h) -> bool:
-        if h[4]:
+        if h[3]:
             return True
         if h[1].query():
-            h[4] = True
+            h[3] = True
             self.free_streams.append(h[0])
             return True
         return False
 
     def finish(self, h, req: Request):
         req.out = h[2].numpy().view(np.uint32).copy()
-        self.out_pool[h[3]].append(h[2])
+
+    def drop(self, slot):
+        for key in [k for k in self.graphs if k[0] == slot.sid]:
+            self.graphs.pop(key).close()
+        self.views.pop(slot.sid, None)
+        self.out_host.pop(slot.sid, None)
 
 
 def model_spec(model, n_clients: int) -> ModelSpec:
@@ -337,6 +420,7 @@ class Server:
 
         # the arena: what the budget leaves after the keys, at most what the
         # device has free (less 1 GiB for the library's own tables and streams)
+        torch.cuda.empty_cache()  # what torch's allocator holds but does not use counts as free
         free = torch.cuda.mem_get_info(device)[0]
         arena = min(self.budget.budget - self.budget.used, max(0, free - (1 << 30)))
         self.specs = {name: model_spec(m, len(evks)) for name, (m, evks) in models.items()}
@@ -346,6 +430,22 @@ class Server:
         self.executor = GpuExecutor(models, arena, lanes, device)
         self.scheduler = Scheduler(self.specs, arena, lanes, self.executor, payload_timeout=payload_timeout)
         self.lanes = list(range(lanes))
+
+    def warm(self, slots_per_model: int):
+        """Carve up to `slots_per_model` idle slots per model (as the budget
+        allows) and capture their evaluations for every client key, so that the
+        first requests replay instead of capturing."""
+        sch = self.scheduler
+        for name, (model, evks) in self.models.items():
+            got = []
+            for _ in range(slots_per_model):
+                sl = sch._acquire(name)
+                if sl is None:
+                    break
+                got.append(sl)
+                for c in range(len(evks)):
+                    self.executor.graph(sl, c)
+            sch.idle.extend(got)
 
     def run(self, requests: list, t0: float | None = None, keep_outputs: bool = False, sleep: bool = True):
         return self.scheduler.run(requests, t0=t0, keep_outputs=keep_outputs, sleep=sleep)

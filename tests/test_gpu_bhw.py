@@ -80,8 +80,10 @@ def test_fc_diag_bit_exact(params, n2, n1, n_img, block):
     assert np.array_equal(got[0], want)
     assert c.device_status() == 0
     dec = c.decrypt_decode(sk, got, level - 1, S, half)[0]
-    for b in range(n_img):
-        assert np.abs(dec[b * block:b * block + n2] - W @ xs[b]).max() < 1e-3
+    ref = np.stack([W @ xs[b] for b in range(n_img)])
+    got_y = np.stack([dec[b * block:b * block + n2] for b in range(n_img)])
+    # rotation noise times weights up to 127 over n1 inputs: relative to the outputs' size
+    assert np.abs(got_y - ref).max() < 1e-5 * np.abs(ref).max()
 
 
 def test_strided_then_gapped_conv_bit_exact():

@@ -65,7 +65,9 @@ def test_tight_budget_admits_by_working_set_and_results_equal_standalone(world):
     for r in done:
         assert r.status == "ok" and r.done >= r.arrival
         assert np.array_equal(r.out, refs[r.rid])
-    assert srv.scheduler.peak_used <= arena and srv.scheduler.arena.used == 0
+    assert srv.scheduler.peak_used <= arena
+    srv.scheduler.close()
+    assert srv.scheduler.arena.used == 0
     stats = serve.latency_stats(done, images)
     assert stats["requests"] == 12 and stats["p99_ms"] >= stats["p50_ms"] > 0
     with pytest.raises(MemoryError):
@@ -75,7 +77,7 @@ def test_tight_budget_admits_by_working_set_and_results_equal_standalone(world):
 def test_mixed_in_flight_equals_alone(world):
     """Many requests in flight on several streams: the same residues as alone."""
     models, images, reqs, refs = world
-    srv = serve.Server(models, lanes=6, budget_bytes=1 << 40)
+    srv = serve.Server(models, lanes=6, budget_bytes=_keys(models) + (4 << 30))
     burst = _fresh(reqs)
     for r in burst:
         r.arrival = 0.0  # all at once
@@ -89,7 +91,7 @@ def test_failures_in_the_mix_leave_the_others_exact(world):
     cancelled before it starts and one whose producer stalls: each ends with
     its status, and every other request still equals its stand-alone result."""
     models, images, reqs, refs = world
-    srv = serve.Server(models, lanes=4, budget_bytes=1 << 40, payload_timeout=0.05)
+    srv = serve.Server(models, lanes=4, budget_bytes=_keys(models) + (4 << 30), payload_timeout=0.05)
     mix = _fresh(reqs)
     short = mix[0]
     short.cts = np.ascontiguousarray(short.cts[:, :, :-1])
@@ -102,6 +104,7 @@ def test_failures_in_the_mix_leave_the_others_exact(world):
         assert r.status == want.get(r.rid, "ok"), (r.rid, r.status, r.detail)
         if r.status == "ok":
             assert np.array_equal(r.out, refs[r.rid])
+    srv.scheduler.close()
     assert srv.scheduler.arena.used == 0
 
 

@@ -61,12 +61,17 @@ class FakeExecutor:
     def __init__(self, polls):
         self.polls, self.started, self.live = polls, [], 0
         self.max_live = 0
+        self.slots_used, self.dropped = [], []
 
-    def start(self, req, offs):
+    def start(self, req, slot):
         self.started.append(req.rid)
+        self.slots_used.append(slot.sid)
         self.live += 1
         self.max_live = max(self.max_live, self.live)
-        return [req, self.polls[req.model], offs]
+        return [req, self.polls[req.model], slot]
+
+    def drop(self, slot):
+        self.dropped.append(slot.sid)
 
     def poll(self, h):
         h[1] -= 1
@@ -105,7 +110,36 @@ def test_admission_by_working_set_lets_small_requests_pass():
     assert all(int(r.out[0]) == r.rid for r in done)
     # the second big request waits for the first; the small ones overtake it
     assert ex.started.index(1) > ex.started.index(2) and ex.started.index(1) > ex.started.index(4)
-    assert sch.peak_used <= cap and sch.arena.used == 0 and sch.arena.free_list == [(0, cap)]
+    assert sch.peak_used <= cap
+    sch.close()
+    assert sch.arena.used == 0 and sch.arena.free_list == [(0, cap)]
+
+
+def test_idle_slots_are_reused_and_reclaimed_for_other_models():
+    sp = specs()
+    cap = sp["big"].working_set() + sp["small"].working_set()
+    ex = FakeExecutor({"small": 2, "big": 2})
+    sch = serve.Scheduler(sp, cap, slots=1, executor=ex)
+    done = sch.run([make(i, "small", arrival=0.0) for i in range(4)], sleep=False)
+    assert all(r.status == "ok" for r in done)
+    assert len(set(ex.slots_used)) == 1  # one request at a time: the same slot every time
+    # a big request needs the memory the idle small slot holds... it fits beside it here
+    done = sch.run([make(10, "big")], sleep=False)
+    assert done[0].status == "ok" and ex.dropped == []
+    # two big ones in flight need the small slot's memory: it goes back to the arena
+    sch2 = serve.Scheduler(sp, 2 * sp["big"].working_set(), slots=2, executor=ex)
+    sch2.run([make(20, "small")], sleep=False)
+    assert len(sch2.idle) == 1
+    done = sch2.run([make(21, "big"), make(22, "big")], sleep=False)
+    assert [r.status for r in done] == ["ok", "ok"] and sch2.evictions == 1
+    assert sch2.peak_used <= 2 * sp["big"].working_set()
+
+
+def test_without_slot_cache_memory_returns_at_completion():
+    sp = specs()
+    sch = serve.Scheduler(sp, 1 << 20, slots=4, executor=FakeExecutor({"small": 2, "big": 2}), cache_slots=False)
+    sch.run([make(i, "small") for i in range(5)], sleep=False)
+    assert sch.arena.used == 0 and not sch.idle
 
 
 def test_slots_bound_requests_in_flight():
@@ -145,6 +179,7 @@ def test_injected_failures_surface_as_statuses():
                   7: "rejected"}
     assert "limb" in done[0].detail or "expected" in done[0].detail
     assert 3 not in ex.started and 4 not in ex.started  # never reserved, never started
+    sch.close()
     assert sch.arena.used == 0
 
 
@@ -152,8 +187,8 @@ def test_cancel_in_flight_discards_the_result_and_frees_its_memory():
     sp = specs()
 
     class CancelOnStart(FakeExecutor):
-        def start(self, req, offs):
-            h = super().start(req, offs)
+        def start(self, req, slot):
+            h = super().start(req, slot)
             if req.rid == 1:
                 req.cancel()  # the client gives up while its request runs
             return h
@@ -162,6 +197,7 @@ def test_cancel_in_flight_discards_the_result_and_frees_its_memory():
     sch = serve.Scheduler(sp, 1 << 20, slots=4, executor=ex)
     done = sch.run([make(0, "small"), make(1, "small"), make(2, "small")], t0=None, keep_outputs=True, sleep=False)
     assert [r.status for r in done] == ["ok", "cancelled", "ok"]
+    sch.close()
     assert done[1].out is None and sch.arena.used == 0
 
 
