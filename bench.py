@@ -50,7 +50,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD,
-                    choices=list(workloads.CONFIGS) + ["uneven64", "serve", "rotate", "op_square", "op_mac"])
+                    choices=list(workloads.CONFIGS) + ["cifar_profile", "uneven64", "serve", "rotate", "op_square",
+                                                       "op_mac"])
     ap.add_argument("--cts", type=int, default=384, help="op_square: ciphertexts")
     ap.add_argument("--map", type=int, default=8, help="op_mac: input map height and width")
     ap.add_argument("--rates", default="50,100,200,500,1000,2000", help="serve: request rates (req/s)")
@@ -1046,7 +1047,13 @@ def _main():
         return run_rotate(args, rank, world, local_rank)
     if args.workload in ("op_square", "op_mac"):
         return run_op(args, rank, world, local_rank)
-    cfg = workloads.get_config(args.workload)
+    if args.workload == "cifar_profile":
+        # the CIFAR-shaped network on the full ring and chain (N = 16384, 11 + 2
+        # primes, 16x16x3 segment) with 4 and 8 maps: the same kernels and launch
+        # sizes as the full network with a few GB on the device (profiling captures)
+        cfg = workloads.reduced_cifar(cout1=4, cout2=8, seg=16, batch=8192)
+    else:
+        cfg = workloads.get_config(args.workload)
     if args.impl == "reference":
         run_reference(args, cfg, rank, world)
     else:

@@ -232,10 +232,11 @@ bcn_status bcn_model_set_chunk(bcn_model *m, int chunk);
 /* MAC implementation: 0 (default) runs the layer groups with at most 512 taps
  * and at least 32 outputs (or at least 10 outputs and 64 taps) on the tensor
  * cores (the residues split into byte planes, fp16 operands, exact fp32 sums),
- * the rest on the CUDA cores with dp4a on byte planes (int8 weights against
- * uint8 bytes, exact 32-bit sums; 64-bit multiply-adds past 32768 taps); 1 runs
- * every MAC on the CUDA cores that way; 2 runs every MAC on the CUDA cores with
- * 64-bit multiply-adds.  Results are identical in every case. */
+ * the rest on the CUDA cores with 64-bit multiply-adds; 1 runs every MAC on the
+ * CUDA cores that way; 2 runs every MAC on the CUDA cores with dp4a on byte
+ * planes (int8 weights against uint8 bytes, exact 32-bit sums; 64-bit
+ * multiply-adds past 32768 taps), measured slower.  Results are identical in
+ * every case. */
 bcn_status bcn_model_set_mac_impl(bcn_model *m, int impl);
 /* Streams of one evaluation: 1 (default) runs each square layer's chunk in two
  * halves side by side (the second on an internal stream forked from and joined

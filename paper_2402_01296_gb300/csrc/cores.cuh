@@ -80,9 +80,13 @@ template <int LOGN, int R>
 constexpr bool kKsDual = kDual<LOGN, R> && !kKsWide<LOGN, R>;
 // the one-digit-at-a-time key switch keeps its first running sum in registers
 // (the second in shared memory): half the shared-memory traffic of the key
-// products (measured 0.483 against 0.486-0.490 ms)
+// products (measured 0.483 against 0.486-0.490 ms); at N = 16384 (32 residues a
+// thread, 128 registers) it fits as well
+#ifndef BCN_KS_REGSUM14
+#define BCN_KS_REGSUM14 0
+#endif
 template <int LOGN, int R>
-constexpr bool kKsRegSum = kKsWide<LOGN, R>;
+constexpr bool kKsRegSum = kKsWide<LOGN, R> || (BCN_KS_REGSUM14 && LOGN == 14 && R == 32);
 
 // Register budget per thread of the fused kernels (sets their blocks per SM).
 #ifndef BCN_CORE_REGS

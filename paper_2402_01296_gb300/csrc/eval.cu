@@ -182,8 +182,12 @@ __global__ void __launch_bounds__(kMacThreads, OT <= 5 ? 3 : 2) k_mac_grouped(co
 // permutations, shared by the OT outputs.  A thread keeps 2 columns x OT
 // outputs x 4 planes of 32-bit sums; the epilogue recombines the planes in 64
 // bits, adds the offset that makes the sum non-negative, reduces and adds the
-// feature.  Measured rates on this GPU: dp4a 52.6 and IMAD.WIDE 29.7 per SM and
-// clock.  Taps in chunks of kca (a multiple of 4), 4 taps a ring stage.
+// feature.  The instruction is faster (dp4a 52.6 against IMAD.WIDE 29.7 per SM
+// and clock, measured) but the kernel is slower than k_mac_grouped (CIFAR-shaped
+// network: MAC 19.6 against 14.2 ms per evaluation; the byte transposes, twice
+// the load instructions and the smaller output tiles cost more than the faster
+// multiply-adds save), so it runs only when asked for (mac impl 2).  Taps in
+// chunks of kca (a multiple of 4), 4 taps a ring stage.
 // grid (groups in this launch * ceil(n_go/OT), ceil(2*level*N/2/256)), 256 threads.
 constexpr int kMacDp4aMaxTaps = 32768;
 constexpr size_t kMacDp4aRingBytes = (size_t)kMacS * 4 * kMacThreads * 8;
@@ -476,7 +480,7 @@ static bcn_status launch_mac(const bcn_ctx *c, int level, int K, int n_groups, i
                              const int8_t *gw, const int32_t *gout, const uint32_t *in, const uint32_t *pt,
                              uint32_t *out, cudaStream_t st, Profiler *prof = nullptr, double alg_bytes = 0,
                              int g_base = 0, bool store_natural = true, const MacTcPlan *tc = nullptr,
-                             int o_lo = 0, int o_hi = -1, bool dp4a = true) {
+                             int o_lo = 0, int o_hi = -1, bool dp4a = false) {
     if (n_groups <= 0 || n_go <= 0) return BCN_OK;
     if (K > kMaxMacTaps) return fail(BCN_E_INVAL, "MAC fan-in above 2^20");
     if (o_hi < 0) o_hi = n_go;  // outputs [o_lo, o_hi) of every group, o_lo on a tile boundary
@@ -978,7 +982,7 @@ static bcn_status eval_impl(const bcn_model *m, const uint32_t *evk, const uint3
     const uint32_t *x = cts;
     int a = 0;
     Profiler *prof = &m->prof;
-    const bool dp4a = m->mac_impl != 2;  // byte-plane dp4a MAC on the CUDA cores (2: 64-bit multiply-adds)
+    const bool dp4a = m->mac_impl == 2;  // byte-plane dp4a MAC on the CUDA cores (measured slower: opt-in)
     for (size_t l = 0; l < m->layers.size(); l++) {
         const bcn_layer_plan &p = m->layers[l];
         char lname[32];

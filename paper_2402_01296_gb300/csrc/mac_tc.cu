@@ -41,6 +41,12 @@ namespace {
 #ifndef BCN_TC_ABUF
 #define BCN_TC_ABUF 1
 #endif
+#ifndef BCN_TC_MINB
+#define BCN_TC_MINB 2  // CTAs per SM the register budget is sized for
+#endif
+#ifndef BCN_TC_EPI
+#define BCN_TC_EPI 16  // outputs per epilogue step (tensor-memory loads of 16 or 8 columns)
+#endif
 constexpr int kRows = 128;                       // columns per CTA (MMA M)
 constexpr int kThreads = 256;                    // two threads per column
 constexpr int kSlab = BCN_TC_SLAB;               // taps per slab (16 or 32)
@@ -80,6 +86,12 @@ __device__ __forceinline__ uint32_t byte_pair(uint32_t x0, uint32_t x1, int b) {
     return *reinterpret_cast<uint32_t *>(&h);
 }
 
+__device__ __forceinline__ void tmem_ld8(uint32_t addr, uint32_t (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(addr));
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t addr, uint32_t (&r)[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
@@ -87,6 +99,14 @@ __device__ __forceinline__ void tmem_ld16(uint32_t addr, uint32_t (&r)[16]) {
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(addr));
+}
+
+template <int E>
+__device__ __forceinline__ void tmem_ld(uint32_t addr, uint32_t (&r)[E]) {
+    if constexpr (E == 16)
+        tmem_ld16(addr, r);
+    else
+        tmem_ld8(addr, r);
 }
 
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
@@ -131,7 +151,7 @@ __device__ __forceinline__ void stage_slab(uint32_t stage, const uint32_t *__res
 // Shared memory: kStages raw stages (cp.async, kStages - 1 slabs in flight
 // ahead of the one being converted), the fp16 planes of one slab (A), the
 // tile's weights (B), the tap indices, the mbarrier.
-__global__ void __launch_bounds__(kThreads, 2) k_mac_tc(const uint32_t *__restrict__ in, uint32_t *__restrict__ out,
+__global__ void __launch_bounds__(kThreads, BCN_TC_MINB) k_mac_tc(const uint32_t *__restrict__ in, uint32_t *__restrict__ out,
                                                      const int32_t *__restrict__ gidx, const uint4 *__restrict__ w16,
                                                      const int32_t *__restrict__ gout,
                                                      const uint32_t *__restrict__ pt, int K, int Kpad, int n_go,
@@ -269,25 +289,26 @@ __global__ void __launch_bounds__(kThreads, 2) k_mac_tc(const uint32_t *__restri
     if (*flag == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;");
         // warp w reads tensor-memory lanes 32 (w mod 4) ..; the two warp halves
-        // take alternate blocks of 16 outputs
+        // take alternate blocks of E outputs
         const uint32_t lanes = tmem + ((uint32_t)((warp & 3) * 32) << 16);
         const int i = (int)((col / N) % level), poly = (int)(col / ((size_t)level * N));
         const uint32_t q = pc[i].q;
         const uint64_t mu = pc[i].barrett;
         const long long offs = (long long)pc[i].mac_offset;
-        for (int ob = 16 * half; ob < NT; ob += 32) {
-            uint32_t f[kPlanes][16];
+        constexpr int E = BCN_TC_EPI;
+        for (int ob = E * half; ob < NT; ob += 2 * E) {
+            uint32_t f[kPlanes][E];
 #pragma unroll
-            for (int b = 0; b < kPlanes; b++) tmem_ld16(lanes + (uint32_t)(b * NT + ob), f[b]);
-            const int nv = min(16, no - ob);  // live outputs of this block of 16 (may be <= 0)
-            // the feature words of all 16 outputs are requested before any is used
-            uint32_t pv[16];
+            for (int b = 0; b < kPlanes; b++) tmem_ld<E>(lanes + (uint32_t)(b * NT + ob), f[b]);
+            const int nv = min(E, no - ob);  // live outputs of this block of E (may be <= 0)
+            // the feature words of all E outputs are requested before any is used
+            uint32_t pv[E];
 #pragma unroll
-            for (int o = 0; o < 16; o++)
+            for (int o = 0; o < E; o++)
                 pv[o] = pt != nullptr && poly == 0 && o < nv ? __ldg(pt + (size_t)sgo[ob + o] * level * N + col) : 0u;
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-            for (int o = 0; o < 16; o++) {
+            for (int o = 0; o < E; o++) {
                 if (o < nv) {
                     long long v = offs;
 #pragma unroll

@@ -146,3 +146,21 @@ def test_cifar_dense_2048_to_10_at_full_ring():
     c.op_mac(level, n_in, torch.from_numpy(idx).cuda(), torch.from_numpy(w).cuda(), bcn.to_device(x), None, got)
     assert np.array_equal(host(got), P.mac(level, idx, w, x, None))
     assert c.device_status() == 0
+
+
+@pytest.mark.parametrize("n_in,n_out", [(27, 16), (2048, 10), (37, 33)])
+def test_dp4a_mac_matches_oracle(n_in, n_out):
+    """The byte-plane dp4a MAC (mac impl 2): fan-in not a multiple of 4, extreme
+    weights, residues near q, the feature add; against the oracle."""
+    c, P = pair((13, 3, 1, 1))
+    rng = np.random.default_rng(n_in + 3 * n_out)
+    level = P.L
+    x = workloads.random_residues(P.q[:level], (n_in, 2), P.N, 41)
+    x[: n_in // 3] = np.array(P.q[:level], dtype=np.uint32)[None, None, :, None] - 1
+    w = rng.integers(-127, 128, size=(n_out, n_in)).astype(np.int8)
+    w[0] = -127
+    pt = workloads.random_residues(P.q[:level], (n_out,), P.N, 42)
+    layer = dict(type="dense", n_in=n_in, n_out=n_out, add=True, square=False)
+    got = run_model(c, layer, w, x, pt, 2)
+    idx = np.tile(np.arange(n_in, dtype=np.int32), (n_out, 1))
+    assert np.array_equal(got, P.mac(level, idx, w, x, pt))
