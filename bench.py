@@ -842,7 +842,8 @@ def run_serve(args, rank, world, local_rank):
         st = serve.latency_stats(done, images)
         gg = np.random.default_rng(int(rate) + 1)
         plain = serve.latency_stats(serve.run_plain(models, make(), device), images)
-        results.append({"rate_req_per_s": rate, "served": st, "plain": plain, "clocks": clk})
+        results.append({"rate_req_per_s": rate, "served": st, "plain": plain, "clocks": clk,
+                        "host": dict(srv.scheduler.stats)})
     best = max(r["served"]["throughput_inferences_per_s"] for r in results)
     line = {
         "metric": METRIC, "value": best, "unit": UNIT, "n_gpus": world, "steps": len(rates), "warmup": 1,

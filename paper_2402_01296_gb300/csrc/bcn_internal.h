@@ -89,6 +89,7 @@ struct MacTcPlan {
     int tiles = 0, tile_out = 0, NT = 0, Kpad = 0;
     uint32_t tmem_cols = 0;
     size_t smem = 0;
+    int slab = 32;  // taps per slab: 16 (tiles of at most 32 outputs) or 32
 };
 }  // namespace bcn
 

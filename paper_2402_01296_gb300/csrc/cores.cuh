@@ -83,7 +83,7 @@ constexpr bool kKsDual = kDual<LOGN, R> && !kKsWide<LOGN, R>;
 // products (measured 0.483 against 0.486-0.490 ms); at N = 16384 (32 residues a
 // thread, 128 registers) it fits as well
 #ifndef BCN_KS_REGSUM14
-#define BCN_KS_REGSUM14 0
+#define BCN_KS_REGSUM14 1  // measured 34.34 against 34.78 ms of key switch per CIFAR-shaped evaluation
 #endif
 template <int LOGN, int R>
 constexpr bool kKsRegSum = kKsWide<LOGN, R> || (BCN_KS_REGSUM14 && LOGN == 14 && R == 32);

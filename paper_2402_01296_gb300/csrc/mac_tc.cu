@@ -16,9 +16,11 @@
 // One CTA: 128 coefficient columns (the MMA's M, one tensor-memory lane
 // each) x one tile of at most 64 outputs (N, padded to a multiple of 16) of
 // one group, all taps.  The weights of the tile are staged once in shared
-// memory (B, K-major); the residues of 32 taps at a time arrive by cp.async in
-// a ring of 3 stages (two slabs load while one converts) and are split into
-// the 4 fp16 planes of A (K-major) by the two threads that own the column.
+// memory (B, K-major); the residues of a slab of 16 or 32 taps at a time (16
+// for tiles of at most 32 outputs, whose CTAs fit 4 to an SM) arrive by
+// cp.async in a ring of 3 stages (two slabs load while one converts) and are
+// split into the 4 fp16 planes of A (K-major) by the two threads that own the
+// column.
 // One elected thread issues the MMAs and commits them to an mbarrier; the
 // wait on it is bounded and records a status word on timeout.  Operand layout
 // is the no-swizzle canonical K-major form: 8 rows x 16 bytes per core matrix,
@@ -35,32 +37,27 @@ namespace bcn {
 
 namespace {
 
-#ifndef BCN_TC_SLAB
-#define BCN_TC_SLAB 32
-#endif
-#ifndef BCN_TC_ABUF
-#define BCN_TC_ABUF 1
-#endif
-#ifndef BCN_TC_MINB
-#define BCN_TC_MINB 2  // CTAs per SM the register budget is sized for
-#endif
-#ifndef BCN_TC_EPI
-#define BCN_TC_EPI 16  // outputs per epilogue step (tensor-memory loads of 16 or 8 columns)
-#endif
 constexpr int kRows = 128;                       // columns per CTA (MMA M)
 constexpr int kThreads = 256;                    // two threads per column
-constexpr int kSlab = BCN_TC_SLAB;               // taps per slab (16 or 32)
-constexpr int kABuf = BCN_TC_ABUF;               // A buffers: with 2, one slab converts while the last multiplies
-// (measured on the CryptoNets-scale dense layer: 32-tap slabs and one A buffer
-// 0.234 ms of MAC per evaluation; 16-tap slabs 0.247, with two A buffers
-// 0.249; 32-tap slabs with two A buffers, one CTA per SM, 0.300)
+constexpr int kABuf = 1;                         // A buffers (two measured slower: they halve the CTAs per SM)
 constexpr int kPlanes = 4;                       // bytes of a residue
 constexpr int kStages = 3;                       // raw slabs in shared memory
-constexpr int kStageBytes = kSlab * kRows * 4;   // raw residues of one slab
-constexpr int kPlaneBytes = kRows * kSlab * 2;   // one fp16 plane of a slab
-constexpr int kABytes = kPlanes * kPlaneBytes;   // one A buffer
-constexpr uint32_t kSboA = (kSlab / 8) * 128;    // bytes between row groups of a plane
-static_assert(kSlab == 16 || kSlab == 32, "slabs of 16 or 32 taps");
+
+// Two shapes, chosen per layer by its output tile (mac_tc_plan):
+//   tiles of at most 32 outputs: 16-tap slabs, registers for 4 CTAs per SM,
+//     epilogue steps of 8 outputs (4 CTAs x 4 planes x 32 columns fill the
+//     512 tensor-memory columns): the CIFAR-shaped conv2 layer 1.34 ms against
+//     1.69 ms with the other shape;
+//   wider tiles: 32-tap slabs, 2 CTAs per SM, epilogue steps of 16 outputs
+//     (the CryptoNets-scale dense layer: 0.227 ms against 0.240 ms).
+template <int SLAB>
+struct TcSlab {
+    static_assert(SLAB == 16 || SLAB == 32, "slabs of 16 or 32 taps");
+    static constexpr int kStageBytes = SLAB * kRows * 4;   // raw residues of one slab
+    static constexpr int kPlaneBytes = kRows * SLAB * 2;   // one fp16 plane of a slab
+    static constexpr int kABytes = kPlanes * kPlaneBytes;  // one A buffer
+    static constexpr uint32_t kSboA = (SLAB / 8) * 128;    // bytes between row groups of a plane
+};
 constexpr int kWaitLimit = 1 << 20;              // mbarrier polls before giving up
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -130,12 +127,13 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool v
                  : "memory");
 }
 
-// residues of slab taps [t0, t0 + kSlab) of columns [col0, col0 + 128) into a
+// residues of slab taps [t0, t0 + SLAB) of columns [col0, col0 + 128) into a
 // stage ([tap][column] words), as one cp.async group
+template <int SLAB>
 __device__ __forceinline__ void stage_slab(uint32_t stage, const uint32_t *__restrict__ in, const int32_t *sidx,
                                            int t0, size_t cols, size_t col0, int tid) {
 #pragma unroll
-    for (int i = 0; i < kStageBytes / 16 / kThreads; i++) {
+    for (int i = 0; i < TcSlab<SLAB>::kStageBytes / 16 / kThreads; i++) {
         const int c = tid + i * kThreads, tap = c >> 5, q4 = c & 31;
         const int s = sidx[t0 + tap];
         const uint32_t *src = s >= 0 ? in + (size_t)s * cols + col0 + 4 * q4 : in;
@@ -151,13 +149,17 @@ __device__ __forceinline__ void stage_slab(uint32_t stage, const uint32_t *__res
 // Shared memory: kStages raw stages (cp.async, kStages - 1 slabs in flight
 // ahead of the one being converted), the fp16 planes of one slab (A), the
 // tile's weights (B), the tap indices, the mbarrier.
-__global__ void __launch_bounds__(kThreads, BCN_TC_MINB) k_mac_tc(const uint32_t *__restrict__ in, uint32_t *__restrict__ out,
+template <int SLAB, int MINB, int EPI>
+__global__ void __launch_bounds__(kThreads, MINB) k_mac_tc(const uint32_t *__restrict__ in, uint32_t *__restrict__ out,
                                                      const int32_t *__restrict__ gidx, const uint4 *__restrict__ w16,
                                                      const int32_t *__restrict__ gout,
                                                      const uint32_t *__restrict__ pt, int K, int Kpad, int n_go,
                                                      int tile_out, int NT, int t_lo, int n_tl, int level, int N,
                                                      int g_base, int store_natural, const PrimeConst *__restrict__ pc,
                                                      uint32_t tmem_cols, uint32_t *__restrict__ status) {
+    constexpr int kSlab = SLAB, kStageBytes = TcSlab<SLAB>::kStageBytes, kPlaneBytes = TcSlab<SLAB>::kPlaneBytes;
+    constexpr int kABytes = TcSlab<SLAB>::kABytes;
+    constexpr uint32_t kSboA = TcSlab<SLAB>::kSboA;
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char *S = sm;                          // [kStages][kSlab][kRows] u32
     unsigned char *A = sm + kStages * kStageBytes;  // [kABuf][kPlanes] planes
@@ -194,7 +196,7 @@ __global__ void __launch_bounds__(kThreads, BCN_TC_MINB) k_mac_tc(const uint32_t
     const uint32_t s_base = smem_addr(S);
 #pragma unroll
     for (int k = 0; k < kStages - 1; k++) {  // the first slabs, one cp.async group each
-        if (k < n_slabs) stage_slab(s_base + (uint32_t)(k * kStageBytes), in, sidx, k * kSlab, cols, col0, tid);
+        if (k < n_slabs) stage_slab<SLAB>(s_base + (uint32_t)(k * kStageBytes), in, sidx, k * kSlab, cols, col0, tid);
         asm volatile("cp.async.commit_group;" ::: "memory");
     }
     {
@@ -217,7 +219,7 @@ __global__ void __launch_bounds__(kThreads, BCN_TC_MINB) k_mac_tc(const uint32_t
         {
             const int nx = sl + kStages - 1;
             if (nx < n_slabs)
-                stage_slab(s_base + (uint32_t)((nx % kStages) * kStageBytes), in, sidx, nx * kSlab, cols, col0,
+                stage_slab<SLAB>(s_base + (uint32_t)((nx % kStages) * kStageBytes), in, sidx, nx * kSlab, cols, col0,
                            tid);
             asm volatile("cp.async.commit_group;" ::: "memory");
             asm volatile("cp.async.wait_group %0;" ::"n"(kStages - 1) : "memory");
@@ -295,7 +297,7 @@ __global__ void __launch_bounds__(kThreads, BCN_TC_MINB) k_mac_tc(const uint32_t
         const uint32_t q = pc[i].q;
         const uint64_t mu = pc[i].barrett;
         const long long offs = (long long)pc[i].mac_offset;
-        constexpr int E = BCN_TC_EPI;
+        constexpr int E = EPI;
         for (int ob = E * half; ob < NT; ob += 2 * E) {
             uint32_t f[kPlanes][E];
 #pragma unroll
@@ -346,15 +348,26 @@ bool mac_tc_eligible(const bcn_ctx *c, int K, int n_go) {
     return K >= 1 && K <= kMacTcMaxTaps && wide && c->N >= kRows && c->N % kRows == 0;
 }
 
-size_t mac_tc_smem(int NT, int Kpad) {
-    return (size_t)kStages * kStageBytes + (size_t)kABuf * kABytes + (size_t)NT * Kpad * 2 + (size_t)Kpad * 4 +
-           8 * kABuf + 8 + (size_t)NT * 4 + 1024;
+template <int SLAB>
+size_t mac_tc_smem_t(int NT, int Kpad) {
+    using TS = TcSlab<SLAB>;
+    return (size_t)kStages * TS::kStageBytes + (size_t)kABuf * TS::kABytes + (size_t)NT * Kpad * 2 +
+           (size_t)Kpad * 4 + 8 * kABuf + 8 + (size_t)NT * 4 + 1024;
 }
+size_t mac_tc_smem(int NT, int Kpad, int slab) {
+    return slab == 16 ? mac_tc_smem_t<16>(NT, Kpad) : mac_tc_smem_t<32>(NT, Kpad);
+}
+
+// the two kernel shapes (see TcSlab)
+#define BCN_TC_NARROW k_mac_tc<16, 4, 8>
+#define BCN_TC_WIDE k_mac_tc<32, 2, 16>
 
 bcn_status mac_tc_plan(const bcn_ctx *c, int K, int n_go, const int8_t *w, MacTcPlan *p) {
     const int tiles = (n_go + 63) / 64;
     const int tile_out = (n_go + tiles - 1) / tiles;
-    const int NT = (tile_out + 15) / 16 * 16, Kpad = (K + kSlab - 1) / kSlab * kSlab;
+    const int NT0 = (tile_out + 15) / 16 * 16;
+    const int slab = NT0 <= 32 ? 16 : 32;
+    const int NT = NT0, Kpad = (K + slab - 1) / slab * slab;
     uint32_t cols = 32;
     while (cols < (uint32_t)(kPlanes * NT)) cols *= 2;
     // weights per tile in the canonical K-major layout
@@ -372,10 +385,11 @@ bcn_status mac_tc_plan(const bcn_ctx *c, int K, int n_go, const int8_t *w, MacTc
         return fail(BCN_E_CUDA, "upload of the MAC weight tables failed");
     // co-resident CTAs must fit the 512 tensor-memory columns of an SM: grow
     // the shared-memory request until they do
-    size_t smem = mac_tc_smem(NT, Kpad);
+    size_t smem = mac_tc_smem(NT, Kpad, slab);
     for (;;) {
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_mac_tc, kThreads, smem) != cudaSuccess)
+        const void *kern = slab == 16 ? (const void *)BCN_TC_NARROW : (const void *)BCN_TC_WIDE;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kThreads, smem) != cudaSuccess)
             return fail(BCN_E_CUDA, "occupancy query for the tensor-core MAC failed");
         if (nb < 1) return fail(BCN_E_INVAL, "tensor-core MAC: shared memory does not fit");
         if ((uint32_t)nb * cols <= 512) break;
@@ -387,11 +401,13 @@ bcn_status mac_tc_plan(const bcn_ctx *c, int K, int n_go, const int8_t *w, MacTc
     p->Kpad = Kpad;
     p->tmem_cols = cols;
     p->smem = smem;
+    p->slab = slab;
     return BCN_OK;
 }
 
 bcn_status mac_tc_setup() {
-    if (cudaFuncSetAttribute(k_mac_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) != cudaSuccess)
+    if (cudaFuncSetAttribute(BCN_TC_NARROW, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) != cudaSuccess ||
+        cudaFuncSetAttribute(BCN_TC_WIDE, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) != cudaSuccess)
         return fail(BCN_E_CUDA, "cudaFuncSetAttribute failed for the tensor-core MAC");
     return BCN_OK;
 }
@@ -403,9 +419,16 @@ bcn_status launch_mac_tc(const bcn_ctx *c, const MacTcPlan &p, int level, int K,
     if (t_lo < 0 || n_tl < 1 || t_lo + n_tl > p.tiles) return fail(BCN_E_INVAL, "MAC tile range");
     if (cols / kRows > 65535) return fail(BCN_E_INVAL, "MAC: more than 65535 column blocks");
     dim3 grid((unsigned)(n_groups * n_tl), (unsigned)(cols / kRows));
-    k_mac_tc<<<grid, kThreads, p.smem, st>>>(in, out, gidx, reinterpret_cast<const uint4 *>(p.w16), gout, pt, K, p.Kpad,
-                                          n_go, p.tile_out, p.NT, t_lo, n_tl, level, c->N, g_base,
-                                          store_natural ? 1 : 0, c->d_pc, p.tmem_cols, c->d_status);
+    if (p.slab == 16)
+        BCN_TC_NARROW<<<grid, kThreads, p.smem, st>>>(in, out, gidx, reinterpret_cast<const uint4 *>(p.w16), gout, pt,
+                                                       K, p.Kpad, n_go, p.tile_out, p.NT, t_lo, n_tl, level, c->N,
+                                                       g_base, store_natural ? 1 : 0, c->d_pc, p.tmem_cols,
+                                                       c->d_status);
+    else
+        BCN_TC_WIDE<<<grid, kThreads, p.smem, st>>>(in, out, gidx, reinterpret_cast<const uint4 *>(p.w16), gout, pt,
+                                                     K, p.Kpad, n_go, p.tile_out, p.NT, t_lo, n_tl, level, c->N,
+                                                     g_base, store_natural ? 1 : 0, c->d_pc, p.tmem_cols,
+                                                     c->d_status);
     return check_launch("k_mac_tc");
 }
 

@@ -192,6 +192,7 @@ class Scheduler:
         self.arena = Arena(capacity)
         self.slots, self.payload_timeout, self.overtake = int(slots), float(payload_timeout), int(overtake)
         self.cache_slots = cache_slots
+        self.stats = {"loops": 0, "start_s": 0.0, "poll_s": 0.0, "max_in_flight": 0}  # host time of the last run
         self.idle = []  # idle slots, least recently used first
         self.n_slots = 0
         self.peak_used = 0
@@ -250,6 +251,8 @@ class Scheduler:
         queue, in_flight = [], []
         t0 = time.perf_counter() if t0 is None else t0
         nxt, finished = 0, 0
+        st = self.stats = {"loops": 0, "start_s": 0.0, "poll_s": 0.0, "max_in_flight": 0}
+        clock = time.perf_counter
 
         def end(r, status, detail="", now=None):
             nonlocal finished
@@ -271,6 +274,8 @@ class Scheduler:
                 else:
                     queue.append(r)
             progressed = False
+            st["loops"] += 1
+            tp = clock()
             for item in list(in_flight):  # completions
                 r, slot, h = item
                 if self.executor.poll(h):
@@ -283,6 +288,7 @@ class Scheduler:
                     self._release(slot)
                     in_flight.remove(item)
                     progressed = True
+            st["poll_s"] += clock() - tp
             # admission: first fit over the queue, in arrival order
             skipped = 0
             for r in list(queue):
@@ -300,7 +306,10 @@ class Scheduler:
                 slot = self._acquire(r.model)
                 if slot is not None:
                     queue.remove(r)
+                    ts = clock()
                     in_flight.append((r, slot, self.executor.start(r, slot)))
+                    st["start_s"] += clock() - ts
+                    st["max_in_flight"] = max(st["max_in_flight"], len(in_flight))
                     progressed = True
                 else:
                     skipped += 1
