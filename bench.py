@@ -56,7 +56,9 @@ def parse():
     ap.add_argument("--map", type=int, default=8, help="op_mac: input map height and width")
     ap.add_argument("--rates", default="50,100,200,500,1000,2000", help="serve: request rates (req/s)")
     ap.add_argument("--serve-seconds", type=float, default=5.0, help="serve: seconds of arrivals per rate")
-    ap.add_argument("--lanes", type=int, default=8, help="serve: lanes (concurrent requests)")
+    ap.add_argument("--lanes", type=int, default=32, help="serve: batches in flight")
+    ap.add_argument("--stacks", default="cnn3_small:2,4,8;cryptonets:2",
+                    help="serve: stack sizes per model (requests of one model sharing launches)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-budget-s", type=float, default=150.0, help="wall budget of the reference arm")
     return ap.parse_args()
@@ -817,7 +819,11 @@ def run_serve(args, rank, world, local_rank):
                 return t.numpy().view(np.uint32)
             payload[(name, c)] = (res(ctx.q, (model.n_in, 2)),
                                   [res(ctx.q[:sh[1]], (sh[0],)) for sh in model.pt_shapes()])
-    srv = serve.Server(models, lanes=args.lanes, budget_bytes=budget, device=device)
+    stacks = {}
+    for part in filter(None, args.stacks.split(";")):
+        name, sizes = part.split(":")
+        stacks[name] = [int(v) for v in sizes.split(",")]
+    srv = serve.Server(models, lanes=args.lanes, budget_bytes=budget, device=device, stacks=stacks)
     srv.warm(args.lanes)  # idle slots with their evaluations captured for every client key
     rates = [float(r) for r in args.rates.split(",")]
     results = []
@@ -855,6 +861,7 @@ def run_serve(args, rank, world, local_rank):
                    "admission": "per request working set (inputs, features, output, workspace) from the arena "
                                 "left after the keys; idle working sets kept as slots with captured graphs, "
                                 "reclaimed for other models on demand",
+                   "stacks": stacks,
                    "slots_created": srv.scheduler.n_slots, "slot_evictions": srv.scheduler.evictions,
                    "arena_peak_bytes": srv.scheduler.peak_used},
         "rates": results,

@@ -217,13 +217,24 @@ typedef struct {
 
 typedef struct {
     int n_layers;
-    int n_in;         /* input ciphertexts of layer 0 */
-    int n_out;        /* output ciphertexts of the last layer */
+    int n_in;         /* input ciphertexts of layer 0 (all requests of a stacked model) */
+    int n_out;        /* output ciphertexts of the last layer (all requests of a stacked model) */
     int out_level;    /* level of the output ciphertexts */
     int n_add;        /* layers with add != 0 */
+    int stack;        /* requests evaluated side by side (1 unless bcn_model_create_stacked) */
 } bcn_model_info;
 
 bcn_status bcn_model_create(bcn_ctx *ctx, const bcn_layer *layers, int n_layers, bcn_model **out);
+/* The same network for `requests` (1..16) slot batches side by side, so that
+ * one launch of every kernel serves all of them: request r's input
+ * ciphertexts, feature plaintexts and outputs are the r-th block of each
+ * buffer of bcn_eval ([requests * n][...] in place of [n][...]); every layer's
+ * output groups are replicated with the inputs and outputs offset accordingly.
+ * Each request may come from a different client: bcn_eval_stacked takes one
+ * evaluation key per request, and the key switch of a ciphertext uses its
+ * request's key.  Results equal `requests` separate evaluations bit for bit. */
+bcn_status bcn_model_create_stacked(bcn_ctx *ctx, const bcn_layer *layers, int n_layers, int requests,
+                                    bcn_model **out);
 bcn_status bcn_model_destroy(bcn_model *m);
 /* Ciphertexts per key-switching chunk of the square layers (0: automatic, a
  * chunk's intermediates bounded by 1 GiB).  Changes bcn_eval_workspace_bytes;
@@ -282,6 +293,15 @@ bcn_status bcn_eval_workspace_bytes(const bcn_model *m, size_t *bytes);
 bcn_status bcn_eval(const bcn_model *m, const uint32_t *evk_eval_dev, const uint32_t *cts_dev,
                     const uint32_t *const *pts_dev, uint32_t *out_dev, void *workspace_dev, size_t workspace_bytes,
                     void *cuda_stream);
+
+/* Evaluation of a stacked model (bcn_model_create_stacked) with one prepared
+ * evaluation key per request: evk_evals, a host array of n_keys device
+ * pointers, n_keys equal to the model's request count; the other arguments as
+ * for bcn_eval (bcn_eval on a stacked model uses its one key for every
+ * request).  BCN_E_INVAL if n_keys differs or a key is null or unaligned. */
+bcn_status bcn_eval_stacked(const bcn_model *m, const uint32_t *const *evk_evals, int n_keys, const uint32_t *cts_dev,
+                            const uint32_t *const *pts_dev, uint32_t *out_dev, void *workspace_dev,
+                            size_t workspace_bytes, void *cuda_stream);
 
 /* Same evaluation with host inputs and outputs: copies cts_host and pts_host
  * to device staging buffers carved from the workspace (size:

@@ -44,7 +44,7 @@ class _Layer(ctypes.Structure):
 
 
 class _ModelInfo(ctypes.Structure):
-    _fields_ = [("n_layers", _I), ("n_in", _I), ("n_out", _I), ("out_level", _I), ("n_add", _I)]
+    _fields_ = [("n_layers", _I), ("n_in", _I), ("n_out", _I), ("out_level", _I), ("n_add", _I), ("stack", _I)]
 
 
 class _BatchItem(ctypes.Structure):
@@ -78,6 +78,8 @@ _SIGS = {
     "bcn_plain_workspace_bytes": (_I, [_P, _I, ctypes.POINTER(_SZ)]),
     "bcn_plain_branch_forward": (_I, [_P, _P, _P, _I, _P, _P, _SZ, _P]),
     "bcn_model_create": (_I, [_P, _P, _I, ctypes.POINTER(_P)]),
+    "bcn_model_create_stacked": (_I, [_P, _P, _I, _I, ctypes.POINTER(_P)]),
+    "bcn_eval_stacked": (_I, [_P, _P, _I, _P, _P, _P, _P, _SZ, _P]),
     "bcn_model_destroy": (_I, [_P]),
     "bcn_model_set_chunk": (_I, [_P, _I]),
     "bcn_model_set_mac_impl": (_I, [_P, _I]),
@@ -428,8 +430,10 @@ LAYER_TYPES = {"conv": 0, "dense": 1}
 class Model:
     """bcn_model: the ciphertext branch (integer weights, feature adds, squares)."""
 
-    def __init__(self, ctx: Context, layers: list, w_int: list, s_w: list):
+    def __init__(self, ctx: Context, layers: list, w_int: list, s_w: list, stack: int = 1):
+        """stack > 1: bcn_model_create_stacked (that many requests side by side)."""
         self.ctx = ctx
+        self._spec = (list(layers), list(w_int), list(s_w))
         self._keep = [np.ascontiguousarray(w, dtype=np.int8) for w in w_int]
         arr = (_Layer * len(layers))()
         for i, (l, w, s) in enumerate(zip(layers, self._keep, s_w)):
@@ -441,13 +445,18 @@ class Model:
             a.w_int = w.ctypes.data
             a.s_w = float(s)
         h = _P()
-        _check(lib().bcn_model_create(ctx.handle, ctypes.cast(arr, _P), len(layers), ctypes.byref(h)),
-               "bcn_model_create")
+        if stack == 1:
+            _check(lib().bcn_model_create(ctx.handle, ctypes.cast(arr, _P), len(layers), ctypes.byref(h)),
+                   "bcn_model_create")
+        else:
+            _check(lib().bcn_model_create_stacked(ctx.handle, ctypes.cast(arr, _P), len(layers), int(stack),
+                                                  ctypes.byref(h)), "bcn_model_create_stacked")
         self._h = h
         info = _ModelInfo()
         _check(lib().bcn_model_get_info(self._h, ctypes.byref(info)), "bcn_model_get_info")
         self.n_layers, self.n_in, self.n_out, self.out_level, self.n_add = (info.n_layers, info.n_in, info.n_out,
                                                                             info.out_level, info.n_add)
+        self.stack = info.stack
         lv = np.zeros(self.n_layers, dtype=np.int32)
         no = np.zeros(self.n_layers, dtype=np.int32)
         _check(lib().bcn_model_layers(self._h, _np_ptr(lv, np.int32), _np_ptr(no, np.int32)), "bcn_model_layers")
@@ -527,6 +536,22 @@ class Model:
                               _dev_ptr(cts_dev, self.n_in * 2 * self.ctx.L * N), ctypes.cast(arr, _P),
                               _dev_ptr(out_dev, int(np.prod(self.out_shape()))), workspace.data_ptr(),
                               workspace.numel() * workspace.element_size(), _stream(stream)), "bcn_eval")
+
+    def stacked(self, requests: int) -> "Model":
+        """The same network for `requests` slot batches side by side."""
+        layers, w_int, s_w = self._spec
+        return Model(self.ctx, layers, w_int, s_w, stack=requests)
+
+    def eval_stacked(self, evk_evals: list, cts_dev, pts_dev: list, out_dev, workspace, stream=None):
+        """bcn_eval_stacked: one prepared key per request of a stacked model."""
+        N = self.ctx.N
+        keys = (_P * len(evk_evals))(*[_dev_ptr(k, self.ctx.evk_words()) for k in evk_evals])
+        arr = (_P * max(1, len(pts_dev)))(*[_dev_ptr(p, int(np.prod(s))) for p, s in zip(pts_dev, self.pt_shapes())])
+        _check(lib().bcn_eval_stacked(self._h, ctypes.cast(keys, _P), len(evk_evals),
+                                      _dev_ptr(cts_dev, self.n_in * 2 * self.ctx.L * N), ctypes.cast(arr, _P),
+                                      _dev_ptr(out_dev, int(np.prod(self.out_shape()))), workspace.data_ptr(),
+                                      workspace.numel() * workspace.element_size(), _stream(stream)),
+               "bcn_eval_stacked")
 
     def eval_host(self, evk_eval, cts_host: np.ndarray, pts_host: list, out_host: np.ndarray, workspace,
                   stream=None):

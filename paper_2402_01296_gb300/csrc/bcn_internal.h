@@ -152,6 +152,7 @@ struct bcn_model {
     int chunk_request;  // 0: automatic
     int mac_impl = 0;   // 0: tensor cores where eligible, 1: CUDA cores only
     int overlap = 1;    // 1: a square layer's chunk halves and the feature transforms on extra streams
+    int stack = 1;      // requests evaluated side by side (bcn_model_create_stacked)
     // copy streams of bcn_eval_host (created on first use) and, per workspace,
     // the event after the last evaluation that read its staged inputs; guarded
     // by copy_mu

@@ -63,6 +63,17 @@ inline KsDev ks_dev(const bcn_ctx *c) {
     return k;
 }
 
+// Keys of a stacked evaluation (several requests of one model, each with its
+// client's evaluation key): the ciphertexts of a square-layer chunk that starts
+// at position ct_base of the layer's group-major order belong to request
+// (ct_base + ct) / cts_per_key, and the chunk's key switch is launched once per
+// request it covers, with that request's key.  n == 0: one key for the chunk.
+constexpr int kMaxStack = 16;
+struct KeyTable {
+    const uint32_t *key[kMaxStack];
+    int n, ct_base, cts_per_key;
+};
+
 // A batch of rotations for the hoisted key switch, passed by value: the
 // prepared Galois key and the Galois element g of each (kRotBatch at most).
 constexpr int kRotBatch = 32;

@@ -534,7 +534,8 @@ static int mac_out_tile(const bcn_layer_plan &p, bool use_tc, bool dp4a) {
 // Square activation on a chunk of C ciphertexts: Y [C][2][n][N] (coefficient
 // form) -> out [C][2][n-1][N].
 static bcn_status square_chunk(const bcn_ctx *c, int n, const uint32_t *evk, const uint32_t *Y, bool in_ntt,
-                               const ChunkBufs &b, int C, uint32_t *out, cudaStream_t st, Profiler *prof = nullptr) {
+                               const ChunkBufs &b, int C, uint32_t *out, cudaStream_t st, Profiler *prof = nullptr,
+                               const KeyTable &kt = KeyTable{}) {
     const int N = c->N, K = c->K, nb = n + K, dnum = (n + c->alpha - 1) / c->alpha;
     const double limb = (double)N * 4;
     const CoreFns *f = core_fns(c->logN);
@@ -545,7 +546,17 @@ static bcn_status square_chunk(const bcn_ctx *c, int n, const uint32_t *evk, con
     }
     {
         Timed tm(prof, st, BCN_KERNEL_KEYSWITCH, limb * ((double)C * (n + 2 * nb) + 2.0 * dnum * nb));
-        BCN_TRY(f->keyswitch(c, n, b.d, b.d2n, evk, b.acc, C, true, st));
+        if (kt.n == 0) {
+            BCN_TRY(f->keyswitch(c, n, b.d, b.d2n, evk, b.acc, C, true, st));
+        } else {  // one launch per request the chunk covers, with its key
+            for (int r = kt.ct_base / kt.cts_per_key; r < kt.n && r * kt.cts_per_key < kt.ct_base + C; r++) {
+                const int lo = std::max(r * kt.cts_per_key, kt.ct_base) - kt.ct_base;
+                const int hi = std::min((r + 1) * kt.cts_per_key, kt.ct_base + C) - kt.ct_base;
+                if (hi <= lo) continue;
+                const ChunkBufs sb = chunk_from(c, n, b, lo);
+                BCN_TRY(f->keyswitch(c, n, sb.d, sb.d2n, kt.key[r], sb.acc, hi - lo, true, st));
+            }
+        }
     }
     Timed tm(prof, st, BCN_KERNEL_MODDOWN_RESCALE, limb * C * (2.0 * n + 2.0 * nb + 2.0 * (n - 1)));
     return f->moddown_rescale(c, n, b.d, b.acc, out, C, st);
@@ -649,12 +660,14 @@ static void model_layout(bcn_model *m) {
     m->ws_pt_bytes = align_up(pt_bytes);
 }
 
-bcn_status bcn_model_create(bcn_ctx *c, const bcn_layer *layers, int n_layers, bcn_model **out) {
+static bcn_status model_create(bcn_ctx *c, const bcn_layer *layers, int n_layers, int stack, bcn_model **out) {
     if (!c || !layers || !out || n_layers < 1) return fail(BCN_E_INVAL, "bcn_model_create: bad argument");
+    if (stack < 1 || stack > kMaxStack) return fail(BCN_E_INVAL, "bcn_model_create_stacked: 1 to 16 requests");
     *out = nullptr;
     BCN_TRY(check_device(c));
     bcn_model *m = new bcn_model();
     m->ctx = c;
+    m->stack = stack;
     int level = c->L, prev_out = -1;
     std::vector<int32_t> prev_perm;
     auto cleanup = [&](bcn_status s, const std::string &msg) {
@@ -717,8 +730,26 @@ bcn_status bcn_model_create(bcn_ctx *c, const bcn_layer *layers, int n_layers, b
         } else {
             return cleanup(BCN_E_INVAL, "layer " + std::to_string(l) + ": unknown type");
         }
+        if (stack > 1) {  // the same layer for `stack` requests side by side: groups replicated, inputs and
+                          // outputs of request r offset by r times the layer's counts
+            const int n_in1 = p.n_in, n_out1 = p.n_out, G1 = p.n_groups;
+            std::vector<int32_t> gi((size_t)stack * gidx.size()), go((size_t)stack * gout.size());
+            std::vector<int8_t> gwr((size_t)stack * gw.size());
+            for (int r = 0; r < stack; r++) {
+                for (size_t k = 0; k < gidx.size(); k++)
+                    gi[r * gidx.size() + k] = gidx[k] >= 0 ? gidx[k] + r * n_in1 : -1;
+                for (size_t k = 0; k < gout.size(); k++) go[r * gout.size() + k] = gout[k] + r * n_out1;
+                std::copy(gw.begin(), gw.end(), gwr.begin() + r * gw.size());
+            }
+            gidx.swap(gi);
+            gout.swap(go);
+            gw.swap(gwr);
+            p.n_in *= stack;
+            p.n_out *= stack;
+            p.n_groups = G1 * stack;
+        }
         if (p.K > kMaxMacTaps) return cleanup(BCN_E_INVAL, "layer fan-in above 2^20");
-        if ((long long)p.n_groups * ((p.n_go + 7) / 8) > 65535)
+        if ((long long)p.n_groups * ((p.n_go + 7) / 8) > (1ll << 30))
             return cleanup(BCN_E_INVAL, "layer " + std::to_string(l) + ": too many output tiles");
         if (prev_out >= 0 && p.n_in != prev_out)
             return cleanup(BCN_E_INVAL, "layer " + std::to_string(l) + ": input count does not match");
@@ -758,6 +789,15 @@ bcn_status bcn_model_create(bcn_ctx *c, const bcn_layer *layers, int n_layers, b
     model_layout(m);
     *out = m;
     return BCN_OK;
+}
+
+bcn_status bcn_model_create(bcn_ctx *c, const bcn_layer *layers, int n_layers, bcn_model **out) {
+    return model_create(c, layers, n_layers, 1, out);
+}
+
+bcn_status bcn_model_create_stacked(bcn_ctx *c, const bcn_layer *layers, int n_layers, int requests,
+                                    bcn_model **out) {
+    return model_create(c, layers, n_layers, requests, out);
 }
 
 bcn_status bcn_model_set_chunk(bcn_model *m, int chunk) {
@@ -812,6 +852,7 @@ bcn_status bcn_model_get_info(const bcn_model *m, bcn_model_info *o) {
     o->n_out = m->layers.back().n_out;
     o->out_level = m->out_level;
     o->n_add = 0;
+    o->stack = m->stack;
     for (auto &p : m->layers) o->n_add += p.add;
     return BCN_OK;
 }
@@ -866,7 +907,17 @@ bcn_status bcn_eval_workspace_bytes(const bcn_model *m, size_t *bytes) {
 // not null) before layer l's first launch (bcn_eval_host: feature copies).
 static bcn_status eval_impl(const bcn_model *m, const uint32_t *evk, const uint32_t *cts, const uint32_t *const *pts,
                             uint32_t *out, void *ws, size_t ws_bytes, void *stream,
-                            const std::vector<std::vector<cudaEvent_t>> *layer_ready);
+                            const std::vector<std::vector<cudaEvent_t>> *layer_ready,
+                            const uint32_t *const *keys = nullptr);
+
+bcn_status bcn_eval_stacked(const bcn_model *m, const uint32_t *const *evk_evals, int n_keys, const uint32_t *cts,
+                            const uint32_t *const *pts, uint32_t *out, void *ws, size_t ws_bytes, void *stream) {
+    if (!m || !evk_evals || n_keys != m->stack) return fail(BCN_E_INVAL, "bcn_eval_stacked: one key per request");
+    for (int r = 0; r < n_keys; r++)
+        if (!evk_evals[r] || ((uintptr_t)evk_evals[r] & 15))
+            return fail(BCN_E_INVAL, "bcn_eval_stacked: null or unaligned key");
+    return eval_impl(m, evk_evals[0], cts, pts, out, ws, ws_bytes, stream, nullptr, evk_evals);
+}
 
 bcn_status bcn_eval(const bcn_model *m, const uint32_t *evk, const uint32_t *cts, const uint32_t *const *pts,
                     uint32_t *out, void *ws, size_t ws_bytes, void *stream) {
@@ -875,7 +926,8 @@ bcn_status bcn_eval(const bcn_model *m, const uint32_t *evk, const uint32_t *cts
 
 static bcn_status eval_impl(const bcn_model *m, const uint32_t *evk, const uint32_t *cts, const uint32_t *const *pts,
                             uint32_t *out, void *ws, size_t ws_bytes, void *stream,
-                            const std::vector<std::vector<cudaEvent_t>> *layer_ready) {
+                            const std::vector<std::vector<cudaEvent_t>> *layer_ready,
+                            const uint32_t *const *keys) {
     if (!m) return fail(BCN_E_INVAL, "bcn_eval: null model");
     NvtxRange r_eval("bcn_eval");
     const bcn_ctx *c = m->ctx;
@@ -1036,10 +1088,20 @@ static bcn_status eval_impl(const bcn_model *m, const uint32_t *evk, const uint3
                 // groups split by groups, of one group by output tiles.
                 const int ngA = (ng + 1) / 2;
                 const int oA = ng >= 2 ? ngA * p.n_go : std::min(p.n_go, (((p.n_go + ts - 1) / ts + 1) / 2) * ts);
+                // a stacked model's ciphertext at group-major position o belongs to request
+                // o / (n_out / stack) and uses that request's key
+                KeyTable ktA{}, ktB{};
+                if (keys != nullptr) {
+                    for (int r = 0; r < m->stack; r++) ktA.key[r] = ktB.key[r] = keys[r];
+                    ktA.n = ktB.n = m->stack;
+                    ktA.cts_per_key = ktB.cts_per_key = p.n_out / m->stack;
+                    ktA.ct_base = o0;
+                    ktB.ct_base = o0 + oA;
+                }
                 if (split == nullptr || oA >= C) {
                     BCN_TRY(launch_mac(c, n, p.K, ng, p.n_go, p.d_gidx, p.d_gw, p.d_gout, x, pt, Ychunk, st, prof,
                                        mac_bytes, g0, false, tc, 0, -1, dp4a));
-                    BCN_TRY(square_chunk(c, n, evk, Ychunk, p.in_ntt != 0, b, C, yo, st, prof));
+                    BCN_TRY(square_chunk(c, n, evk, Ychunk, p.in_ntt != 0, b, C, yo, st, prof, ktA));
                     continue;
                 }
                 const int C1 = C - oA;
@@ -1059,9 +1121,9 @@ static bcn_status eval_impl(const bcn_model *m, const uint32_t *evk, const uint3
                     BCN_TRY(launch_mac(c, n, p.K, 1, p.n_go, p.d_gidx, p.d_gw, p.d_gout, x, pt, Ychunk, split, nullptr,
                                        0, g0, false, tc, oA, p.n_go, dp4a));
                 }
-                BCN_TRY(square_chunk(c, n, evk, Ychunk, p.in_ntt != 0, b, oA, yo, st, nullptr));
+                BCN_TRY(square_chunk(c, n, evk, Ychunk, p.in_ntt != 0, b, oA, yo, st, nullptr, ktA));
                 BCN_TRY(square_chunk(c, n, evk, Ychunk + (size_t)oA * 2 * n * N, p.in_ntt != 0, b1, C1,
-                                     yo + (size_t)oA * 2 * (n - 1) * N, split, nullptr));
+                                     yo + (size_t)oA * 2 * (n - 1) * N, split, nullptr, ktB));
                 if (cudaEventRecord(split_ev[1], split) != cudaSuccess ||
                     cudaStreamWaitEvent(st, split_ev[1], 0) != cudaSuccess)
                     return fail(BCN_E_CUDA, "bcn_eval: join failed");

@@ -28,11 +28,19 @@ completes but the result is discarded); "timeout" (its producer did not
 finish the payload -- Request.ready() stayed false -- within `payload_timeout`
 seconds of its arrival).  Nothing of a request that does not end "ok" is kept.
 
-The scheduling (admission, arena, slots, statuses) is host logic over an
-executor that starts a request's copies and evaluation and reports completion;
-the GPU executor copies the payload into the slot's device buffers and replays
-a CUDA graph of bcn_eval captured once per (slot, client key), one stream per
-request in flight.  The per-request baseline ("plain") serves the same
+Requests of one model that wait together share their launches: the first
+ready request in the queue is started together with the next ready requests of
+its model, up to the largest stack size configured for that model, as one
+stacked evaluation (bcn_model_create_stacked: every kernel launch serves all of
+them, each ciphertext's key switch with its own client's key) in a slot sized
+for the stack.
+
+The scheduling (admission, arena, slots, batches, statuses) is host logic over
+an executor that starts a batch's copies and evaluation and reports
+completion; the GPU executor copies the payloads into the slot's device
+buffers and replays a CUDA graph of bcn_eval captured once per (slot, client
+key) for a single request, or runs bcn_eval_stacked with the batch's keys, one
+stream per batch in flight.  The per-request baseline ("plain") serves the same
 arrivals one at a time on one stream.
 """
 from __future__ import annotations
@@ -169,30 +177,36 @@ def validate(req: Request, spec: ModelSpec) -> str:
 
 @dataclasses.dataclass
 class Slot:
-    """One request's working set in the arena: offsets of its parts."""
+    """One batch's working set in the arena: offsets of its parts."""
     sid: int
     model: str
+    stack: int
     offs: list
 
 
 class Scheduler:
     """Admission and completion over an executor (host logic only).
 
-    executor: start(req, slot) -> handle (copies + evaluation queued),
-    poll(handle) -> bool, finish(handle, req) (fetch the result into req.out),
-    drop(slot) (the slot's memory goes back to the arena).  specs: {model name:
-    ModelSpec}; capacity: arena bytes (the budget left after the keys); slots:
-    requests in flight at most; overtake: how many later requests may start
-    ahead of a waiting one before admission stops at it; cache_slots: keep a
-    completed request's working set as an idle slot of its model."""
+    executor: start(reqs, slot) -> handle (copies + evaluation of the batch
+    queued), poll(handle) -> bool, finish(handle, reqs) (fetch the results into
+    each req.out), drop(slot) (the slot's memory goes back to the arena).
+    specs: {model name: ModelSpec} (one request); stacks: {model name: {size:
+    ModelSpec of that many requests side by side}} (size 1 may be left out);
+    capacity: arena bytes (the budget left after the keys); slots: batches in
+    flight at most; overtake: how many later requests may start ahead of a
+    waiting one before admission stops at it; cache_slots: keep a completed
+    batch's working set as an idle slot of its model and stack size."""
 
     def __init__(self, specs: dict, capacity: int, slots: int, executor, payload_timeout: float = 1.0,
-                 overtake: int = 64, cache_slots: bool = True):
+                 overtake: int = 64, cache_slots: bool = True, stacks: dict | None = None):
         self.specs, self.executor = specs, executor
+        self.stacks = {m: {1: sp} for m, sp in specs.items()}
+        for m, by_size in (stacks or {}).items():
+            self.stacks[m].update(by_size)
         self.arena = Arena(capacity)
         self.slots, self.payload_timeout, self.overtake = int(slots), float(payload_timeout), int(overtake)
         self.cache_slots = cache_slots
-        self.stats = {"loops": 0, "start_s": 0.0, "poll_s": 0.0, "max_in_flight": 0}  # host time of the last run
+        self.stats = {"loops": 0, "start_s": 0.0, "poll_s": 0.0, "max_in_flight": 0, "batches": 0, "requests": 0}
         self.idle = []  # idle slots, least recently used first
         self.n_slots = 0
         self.peak_used = 0
@@ -214,17 +228,17 @@ class Scheduler:
             self.arena.free(o)
         self.executor.drop(slot)
 
-    def _acquire(self, model: str):
-        """An idle slot of `model`, else a new one carved from the arena, after
-        returning idle slots of other models (least recently used first) while
-        it does not fit."""
+    def _acquire(self, model: str, stack: int = 1):
+        """An idle slot of (model, stack), else a new one carved from the arena,
+        after returning other idle slots (least recently used first) while it
+        does not fit."""
         for i, sl in enumerate(self.idle):
-            if sl.model == model:
+            if sl.model == model and sl.stack == stack:
                 return self.idle.pop(i)
-        spec = self.specs[model]
+        spec = self.stacks[model][stack]
         offs = self._carve(spec)
         while offs is None:
-            victim = next((i for i, sl in enumerate(self.idle) if sl.model != model), None)
+            victim = next((i for i, sl in enumerate(self.idle) if (sl.model, sl.stack) != (model, stack)), None)
             if victim is None:
                 return None
             self._drop(self.idle.pop(victim))
@@ -232,7 +246,7 @@ class Scheduler:
             offs = self._carve(spec)
         self.n_slots += 1
         self.peak_used = max(self.peak_used, self.arena.used)
-        return Slot(self.n_slots - 1, model, offs)
+        return Slot(self.n_slots - 1, model, stack, offs)
 
     def _release(self, slot: Slot):
         if self.cache_slots:
@@ -251,7 +265,8 @@ class Scheduler:
         queue, in_flight = [], []
         t0 = time.perf_counter() if t0 is None else t0
         nxt, finished = 0, 0
-        st = self.stats = {"loops": 0, "start_s": 0.0, "poll_s": 0.0, "max_in_flight": 0}
+        st = self.stats = {"loops": 0, "start_s": 0.0, "poll_s": 0.0, "max_in_flight": 0, "batches": 0,
+                           "requests": 0}
         clock = time.perf_counter
 
         def end(r, status, detail="", now=None):
@@ -259,6 +274,9 @@ class Scheduler:
             r.status, r.detail = status, detail
             r.done = (time.perf_counter() - t0) if now is None else now
             finished += 1
+
+        def ready(r):
+            return r.ready is None or r.ready()
 
         while finished < len(pending):
             now = time.perf_counter() - t0
@@ -277,38 +295,60 @@ class Scheduler:
             st["loops"] += 1
             tp = clock()
             for item in list(in_flight):  # completions
-                r, slot, h = item
+                batch, slot, h = item
                 if self.executor.poll(h):
-                    if r.cancelled:
-                        end(r, "cancelled", "cancelled while in flight; result discarded")
-                    else:
-                        if keep_outputs:
-                            self.executor.finish(h, r)
-                        end(r, "ok")
+                    live = [r for r in batch if not r.cancelled]
+                    if keep_outputs and live:
+                        self.executor.finish(h, batch)
+                    for r in batch:
+                        if r.cancelled:
+                            r.out = None
+                            end(r, "cancelled", "cancelled while in flight; result discarded")
+                        else:
+                            end(r, "ok")
                     self._release(slot)
                     in_flight.remove(item)
                     progressed = True
             st["poll_s"] += clock() - tp
-            # admission: first fit over the queue, in arrival order
+            # admission: first fit over the queue, in arrival order; a request
+            # starts together with the next ready requests of its model
             skipped = 0
             for r in list(queue):
+                if r not in queue:  # started in an earlier batch of this pass
+                    continue
                 if r.cancelled:
                     queue.remove(r)
                     end(r, "cancelled", "cancelled before it started")
                     continue
-                if r.ready is not None and not r.ready():
+                if not ready(r):
                     if now - r.arrival > self.payload_timeout:
                         queue.remove(r)
                         end(r, "timeout", f"payload not ready {now - r.arrival:.3f} s after arrival")
                     continue
                 if len(in_flight) >= self.slots:
                     break
-                slot = self._acquire(r.model)
+                sizes = sorted(self.stacks[r.model], reverse=True)
+                mates = [r]
+                for x in queue:
+                    if len(mates) >= sizes[0]:
+                        break
+                    if x is not r and x.model == r.model and not x.cancelled and ready(x):
+                        mates.append(x)
+                slot = None
+                for size in sizes:  # the largest stack the waiting requests fill, else smaller ones
+                    if size <= len(mates):
+                        slot = self._acquire(r.model, size)
+                        if slot is not None:
+                            mates = mates[:size]
+                            break
                 if slot is not None:
-                    queue.remove(r)
+                    for x in mates:
+                        queue.remove(x)
                     ts = clock()
-                    in_flight.append((r, slot, self.executor.start(r, slot)))
+                    in_flight.append((mates, slot, self.executor.start(mates, slot)))
                     st["start_s"] += clock() - ts
+                    st["batches"] += 1
+                    st["requests"] += len(mates)
                     st["max_in_flight"] = max(st["max_in_flight"], len(in_flight))
                     progressed = True
                 else:
@@ -323,23 +363,29 @@ class Scheduler:
 
 
 class GpuExecutor:
-    """Runs a request on the device: copies its payload into its slot's device
-    buffers on a stream of its own, replays the evaluation captured for that
-    slot and the request's client key (bcn_batch of one item, captured on first
-    use), and copies the output back to a page-locked host buffer."""
+    """Runs a batch on the device on a stream of its own: copies the payloads
+    into the slot's device buffers (request i in the i-th block of each), then
+    for a single request replays the evaluation captured for that slot and the
+    request's client key (bcn_batch of one item, captured on first use), for a
+    stack runs bcn_eval_stacked with the requests' keys; copies the outputs back
+    to a page-locked host buffer."""
 
-    def __init__(self, models: dict, arena_bytes: int, streams: int, device: int = 0):
+    def __init__(self, models: dict, arena_bytes: int, streams: int, device: int = 0, stacked: dict | None = None):
         import torch
 
         from . import bcn
 
         self.torch, self.bcn = torch, bcn
         self.models = models
+        self.stacked = stacked or {}  # {name: {size: bcn.Model}}
         self.dev = f"cuda:{device}"
         self.buf = torch.empty(max(1, arena_bytes // 4), dtype=torch.int32, device=self.dev)
         self.streams = [torch.cuda.Stream(device=device) for _ in range(max(1, streams))]
         self.free_streams = list(range(len(self.streams)))
         self.views, self.graphs, self.out_host = {}, {}, {}
+
+    def _model(self, slot):
+        return self.models[slot.model][0] if slot.stack == 1 else self.stacked[slot.model][slot.stack]
 
     def _view(self, off, shape):
         n = int(np.prod(shape))
@@ -348,7 +394,7 @@ class GpuExecutor:
     def _slot_views(self, slot):
         v = self.views.get(slot.sid)
         if v is None:
-            model, _ = self.models[slot.model]
+            model = self._model(slot)
             N, L = model.ctx.N, model.ctx.L
             offs = slot.offs
             cts = self._view(offs[0], (model.n_in, 2, L, N))
@@ -370,18 +416,26 @@ class GpuExecutor:
             self.graphs[key] = g
         return g
 
-    def start(self, req: Request, slot: Slot):
+    def start(self, reqs: list, slot: Slot):
         torch = self.torch
         cts, pts, out, ws = self._slot_views(slot)
-        g = self.graph(slot, req.client)
+        _, evks = self.models[slot.model]
         si = self.free_streams.pop()
         st = self.streams[si]
         oh = self.out_host[slot.sid]
         with torch.cuda.stream(st):
-            cts.copy_(torch.from_numpy(np.asarray(req.cts).view(np.int32)), non_blocking=True)
-            for d, h in zip(pts, req.pts):
-                d.copy_(torch.from_numpy(np.asarray(h).view(np.int32)), non_blocking=True)
-            g.launch(st)
+            n_in = cts.shape[0] // slot.stack
+            for i, r in enumerate(reqs):
+                cts[i * n_in:(i + 1) * n_in].copy_(torch.from_numpy(np.asarray(r.cts).view(np.int32)),
+                                                   non_blocking=True)
+                for d, h in zip(pts, r.pts):
+                    n_pt = d.shape[0] // slot.stack
+                    d[i * n_pt:(i + 1) * n_pt].copy_(torch.from_numpy(np.asarray(h).view(np.int32)),
+                                                     non_blocking=True)
+            if slot.stack == 1:
+                self.graph(slot, reqs[0].client).launch(st)
+            else:
+                self._model(slot).eval_stacked([evks[r.client] for r in reqs], cts, pts, out, ws, stream=st)
             oh.copy_(out, non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(st)
@@ -396,8 +450,11 @@ class GpuExecutor:
             return True
         return False
 
-    def finish(self, h, req: Request):
-        req.out = h[2].numpy().view(np.uint32).copy()
+    def finish(self, h, reqs: list):
+        full = h[2].numpy().view(np.uint32)
+        n_out = full.shape[0] // len(reqs)
+        for i, r in enumerate(reqs):
+            r.out = full[i * n_out:(i + 1) * n_out].copy()
 
     def drop(self, slot):
         for key in [k for k in self.graphs if k[0] == slot.sid]:
@@ -415,10 +472,12 @@ def model_spec(model, n_clients: int) -> ModelSpec:
 class Server:
     """models: {name: (bcn.Model, [evk_eval per client])}.  The keys are
     reserved from the budget first; the rest (at most the device's free memory
-    less 1 GiB) is the requests' arena.  `lanes`: requests in flight at most
-    (one stream each)."""
+    less 1 GiB) is the requests' arena.  `lanes`: batches in flight at most
+    (one stream each).  stacks: {name: [sizes > 1]}: requests of that model
+    that wait together run as one stacked evaluation of up to the largest size."""
 
-    def __init__(self, models: dict, lanes: int, budget_bytes: int, device: int = 0, payload_timeout: float = 1.0):
+    def __init__(self, models: dict, lanes: int, budget_bytes: int, device: int = 0, payload_timeout: float = 1.0,
+                 stacks: dict | None = None):
         self.models = models
         self.device = device
         self.budget = MemoryBudget(budget_bytes)
@@ -436,8 +495,13 @@ class Server:
         if min(s.working_set() for s in self.specs.values()) > arena:
             raise MemoryError("no request fits the device-memory budget left after the keys")
         self.budget.reserve(arena)
-        self.executor = GpuExecutor(models, arena, lanes, device)
-        self.scheduler = Scheduler(self.specs, arena, lanes, self.executor, payload_timeout=payload_timeout)
+        stacked = {name: {int(k): models[name][0].stacked(int(k)) for k in sizes if int(k) > 1}
+                   for name, sizes in (stacks or {}).items()}
+        stack_specs = {name: {k: model_spec(m, len(models[name][1])) for k, m in by.items()}
+                       for name, by in stacked.items()}
+        self.executor = GpuExecutor(models, arena, lanes, device, stacked=stacked)
+        self.scheduler = Scheduler(self.specs, arena, lanes, self.executor, payload_timeout=payload_timeout,
+                                   stacks=stack_specs)
         self.lanes = list(range(lanes))
 
     def warm(self, slots_per_model: int):
@@ -454,6 +518,15 @@ class Server:
                 got.append(sl)
                 for c in range(len(evks)):
                     self.executor.graph(sl, c)
+            for size in sch.stacks[name]:  # and a few slots of every stack size
+                for _ in range(min(4, slots_per_model)):
+                    if size == 1:
+                        break
+                    sl = sch._acquire(name, size)
+                    if sl is None:
+                        break
+                    self.executor._slot_views(sl)
+                    got.append(sl)
             sch.idle.extend(got)
 
     def run(self, requests: list, t0: float | None = None, keep_outputs: bool = False, sleep: bool = True):

@@ -113,3 +113,19 @@ def test_plain_path_equals_standalone(world):
     done = serve.run_plain(models, _fresh(reqs), keep_outputs=True)
     for r in done:
         assert np.array_equal(r.out, refs[r.rid])
+
+
+def test_small_requests_share_launches_and_equal_standalone(world):
+    """With stacks of the small model, requests that wait together run as one
+    stacked evaluation (each with its client's key); every result still equals
+    its stand-alone evaluation."""
+    models, images, reqs, refs = world
+    srv = serve.Server(models, lanes=4, budget_bytes=_keys(models) + (4 << 30),
+                       stacks={"cnn3_small": [2, 4], "cryptonets": [2]})
+    burst = _fresh(reqs)
+    for r in burst:
+        r.arrival = 0.0
+    done = srv.run(burst, keep_outputs=True)
+    for r in done:
+        assert r.status == "ok" and np.array_equal(r.out, refs[r.rid]), r.rid
+    assert srv.scheduler.stats["batches"] < len(reqs)  # some launches were shared

@@ -61,14 +61,16 @@ class FakeExecutor:
     def __init__(self, polls):
         self.polls, self.started, self.live = polls, [], 0
         self.max_live = 0
-        self.slots_used, self.dropped = [], []
+        self.slots_used, self.dropped, self.batches = [], [], []
 
-    def start(self, req, slot):
-        self.started.append(req.rid)
+    def start(self, reqs, slot):
+        assert len(reqs) == slot.stack and all(r.model == slot.model for r in reqs)
+        self.started.extend(r.rid for r in reqs)
+        self.batches.append([r.rid for r in reqs])
         self.slots_used.append(slot.sid)
         self.live += 1
         self.max_live = max(self.max_live, self.live)
-        return [req, self.polls[req.model], slot]
+        return [reqs, self.polls[slot.model], slot]
 
     def drop(self, slot):
         self.dropped.append(slot.sid)
@@ -81,8 +83,9 @@ class FakeExecutor:
             return True
         return False
 
-    def finish(self, h, req):
-        req.out = np.full(1, req.rid, dtype=np.uint32)
+    def finish(self, h, reqs):
+        for r in reqs:
+            r.out = np.full(1, r.rid, dtype=np.uint32)
 
 
 def specs():
@@ -187,10 +190,11 @@ def test_cancel_in_flight_discards_the_result_and_frees_its_memory():
     sp = specs()
 
     class CancelOnStart(FakeExecutor):
-        def start(self, req, slot):
-            h = super().start(req, slot)
-            if req.rid == 1:
-                req.cancel()  # the client gives up while its request runs
+        def start(self, reqs, slot):
+            h = super().start(reqs, slot)
+            for r in reqs:
+                if r.rid == 1:
+                    r.cancel()  # the client gives up while its request runs
             return h
 
     ex = CancelOnStart({"small": 3, "big": 3})
@@ -206,3 +210,57 @@ def test_too_large_for_the_arena():
     sch = serve.Scheduler(sp, sp["small"].working_set(), slots=4, executor=FakeExecutor({"small": 1, "big": 1}))
     done = sch.run([make(0, "big"), make(1, "small")], t0=None, sleep=False)
     assert [r.status for r in done] == ["too_large", "ok"]
+
+
+def stacked_specs(sizes=(2, 4)):
+    sp = specs()
+    small = sp["small"]
+    by = {k: serve.ModelSpec(cts_shape=(k * small.cts_shape[0],) + small.cts_shape[1:],
+                             pt_shapes=[(k * p[0],) + tuple(p[1:]) for p in small.pt_shapes],
+                             out_shape=(k * small.out_shape[0],) + small.out_shape[1:],
+                             workspace=small.workspace * k, n_clients=4) for k in sizes}
+    return sp, {"small": by}
+
+
+def test_small_requests_share_launches():
+    """Seven small requests waiting together run as stacks of 4 and 2 and a
+    single one (the largest stack the waiting requests fill, first); the big
+    request among them runs alone; a stack is one batch of the executor."""
+    sp, st = stacked_specs()
+    ex = FakeExecutor({"small": 3, "big": 3})
+    sch = serve.Scheduler(sp, 1 << 24, slots=8, executor=ex, stacks=st)
+    reqs = [make(i, "small") for i in range(5)] + [make(5, "big")] + [make(6 + i, "small", client=i % 4)
+                                                                      for i in range(2)]
+    done = sch.run(reqs, keep_outputs=True, sleep=False)
+    assert all(r.status == "ok" and int(r.out[0]) == r.rid for r in done)
+    assert ex.batches[0] == [0, 1, 2, 3] and [5] in ex.batches
+    # the other three small ones: a stack of 2 (the largest they fill), then one alone; the big one alone
+    assert sorted(len(b) for b in ex.batches) == [1, 1, 2, 4]
+    assert sch.stats["requests"] == 8 and sch.stats["batches"] == len(ex.batches)
+
+
+def test_cancel_inside_a_stack_discards_only_that_result():
+    sp, st = stacked_specs((2,))
+
+    class CancelOnStart(FakeExecutor):
+        def start(self, reqs, slot):
+            h = super().start(reqs, slot)
+            reqs[1].cancel()
+            return h
+
+    ex = CancelOnStart({"small": 2, "big": 2})
+    sch = serve.Scheduler(sp, 1 << 24, slots=4, executor=ex, stacks=st)
+    done = sch.run([make(0, "small"), make(1, "small")], keep_outputs=True, sleep=False)
+    assert [r.status for r in done] == ["ok", "cancelled"] and done[1].out is None and int(done[0].out[0]) == 0
+
+
+def test_stack_that_does_not_fit_falls_back_to_smaller():
+    """An arena that holds a stack of 2 but not of 4: four waiting requests run as
+    two stacks of 2."""
+    sp, st = stacked_specs((2, 4))
+    cap = st["small"][2].working_set()
+    ex = FakeExecutor({"small": 2, "big": 2})
+    sch = serve.Scheduler(sp, cap, slots=4, executor=ex, stacks=st)
+    done = sch.run([make(i, "small") for i in range(4)], sleep=False)
+    assert all(r.status == "ok" for r in done) and [len(b) for b in ex.batches] == [2, 2]
+    assert sch.peak_used <= cap
