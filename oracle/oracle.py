@@ -718,3 +718,107 @@ def fc_diag(P: "Params", level: int, gks: dict, W: np.ndarray, ct: np.ndarray, n
         acc = prod if acc is None else acc + prod
         acc %= np.array(P.q[:level], dtype=np.uint64)[None, :, None]
     return P.rescale(level, acc.astype(np.uint32)[None])[0]
+
+
+def fc_diagonals_at(W: np.ndarray, n_img: int, block: int, s_in, o_out, N: int) -> dict:
+    """The diagonal method (App. D, homomorphic fully connected layer) for
+    inputs and outputs at any slots of each image's block: input p of image b
+    in slot b block + s_in[p], output j in slot b block + o_out[j] (a strided
+    packed convolution leaves its outputs at every s-th position).  A rotation
+    by r moves slot k + r to slot k, so the term W[j][p] x_p needs the rotation
+    r = s_in[p] - o_out[j] and sits in slot b block + o_out[j] of u_r:
+    {r: u_r [N/2]} with y = sum_r u_r * Rot(x, r) holding y_j in slot
+    b block + o_out[j].  Slots that are no s_in[p] never meet a nonzero entry,
+    so the product also drops what a strided convolution's mask would."""
+    n2, n1 = W.shape
+    assert len(s_in) == n1 and len(o_out) == n2 and n_img * block <= N // 2
+    assert 0 <= min(s_in) and max(s_in) < block and 0 <= min(o_out) and max(o_out) < block
+    out = {}
+    for j in range(n2):
+        for p in range(n1):
+            r = int(s_in[p]) - int(o_out[j])
+            u = out.setdefault(r, np.zeros(N // 2))
+            for b in range(n_img):
+                u[b * block + o_out[j]] = W[j][p]
+    return out
+
+
+def add_plain(P: "Params", level: int, ct: np.ndarray, pt: np.ndarray) -> np.ndarray:
+    """Add(c, u) of App. A: (c0 + u, c1) mod Q_level; ct [2][level][N], pt [level][N]."""
+    out = np.array(ct, dtype=np.uint32)
+    q = np.array(P.q[:level], dtype=np.uint64)[:, None]
+    out[0] = ((out[0].astype(np.uint64) + np.asarray(pt, dtype=np.uint64)) % q).astype(np.uint32)
+    return out
+
+
+def fc_diag_sum(P: "Params", level: int, gks: dict, diags: list, cts: np.ndarray, pt=None) -> np.ndarray:
+    """The dense layer of App. D over several input ciphertexts (BHW packing: one
+    channel each): sum over inputs k and rotations r of Mult(Rot(x_k, r), u_{k,r}),
+    each u encoded at the scale q_{level-1}; one rescale; then Add(c, pt) when
+    pt [level-1][N] is given.  diags[k] = {r: u_r [N/2]} (fc_diagonals_at);
+    cts [n_in][2][level][N] -> [2][level-1][N].  gks: {r mod N/2: Galois key}."""
+    half = P.N // 2
+    q = np.array(P.q[:level], dtype=np.uint64)[None, :, None]
+    acc = np.zeros((2, level, P.N), dtype=np.uint64)
+    for k, dk in enumerate(diags):
+        for r in sorted(dk):
+            x = cts[k][None]
+            rc = x if r % half == 0 else P.rotate(level, gks[r % half], r % half, x)
+            u = encode(dk[r][None], P.N, float(P.q[level - 1]), P.q[:level])[0]
+            acc = (acc + P.mul_plain(level, rc, u)[0].astype(np.uint64)) % q
+    y = P.rescale(level, acc.astype(np.uint32)[None])[0]
+    return y if pt is None else add_plain(P, level - 1, y, pt)
+
+
+def bhw_branch(P: "Params", evk: np.ndarray, gks: dict, layers: list, weights: list, feats: list,
+               cts: np.ndarray, n_img: int) -> np.ndarray:
+    """A ciphertext branch of one valid convolution then dense layers evaluated
+    in BHW packing (App. D): n_img images' h x w segments of each input channel
+    in one ciphertext (cts [cin][2][L][N], slot b h w + y w + x), in the
+    layers' order:
+      * conv (k x k, stride s): the packed convolution by rotations (conv_bhw);
+        output (y', x') of image b stays at slot b h w + s (y' w + x');
+      * dense: the diagonal method over the previous layer's ciphertexts
+        (fc_diag_sum), input p = (channel, y', x') in torch's flattening order,
+        output j at slot b h w + j;
+    each followed, as the layer says, by Add(c, feature) (the unidirectional
+    connection, Sec. 3.2) and the square (Mult(c, c), relinearise, rescale).
+    weights: integer weights per layer (conv [cout][cin][k][k], dense
+    [n_out][n_in]); feats: the encoded features of the layers with add=True in
+    order (conv [cout][level][N] at the layer's level, dense [level-1][N] at the
+    level after its rescale).  Returns [2][level][N] at the final level (outputs
+    of image b at slots b h w + j)."""
+    level = P.L
+    h, w = layers[0]["h"], layers[0]["w"]
+    block = h * w
+    fi = 0
+    x = cts
+    pos = None
+    for li, (lay, wt) in enumerate(zip(layers, weights)):
+        if lay["type"] == "conv":
+            assert li == 0 and lay["pad"] == 0
+            x = conv_bhw(P, level, gks, np.asarray(wt, dtype=np.int8), x, w)
+            if lay["add"]:
+                x = np.stack([add_plain(P, level, x[c], feats[fi][c]) for c in range(x.shape[0])])
+                fi += 1
+            ho = (h - lay["k"]) // lay["stride"] + 1
+            wo = (w - lay["k"]) // lay["stride"] + 1
+            pos = [lay["stride"] * (yy * w + xx) for yy in range(ho) for xx in range(wo)]
+        else:
+            C = x.shape[0]
+            n_pos = len(pos)
+            assert wt.shape == (lay["n_out"], C * n_pos)
+            diags = [fc_diagonals_at(wt[:, c * n_pos:(c + 1) * n_pos], n_img, block, pos,
+                                     list(range(lay["n_out"])), P.N) for c in range(C)]
+            pt = None
+            if lay["add"]:
+                pt = feats[fi]
+                fi += 1
+            x = fc_diag_sum(P, level, gks, diags, x, pt)[None]
+            level -= 1
+            pos = list(range(lay["n_out"]))
+        if lay["square"]:
+            x = P.square_relin_rescale(level, evk, x)
+            level -= 1
+    assert x.shape[0] == 1
+    return x[0]

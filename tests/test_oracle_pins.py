@@ -889,3 +889,76 @@ def test_strided_conv_then_gapped_conv_is_the_convolution_chain():
     keep[0:10:2, 0:10:2] = True
     assert np.abs(d1[:, :, ~keep]).max() < 1e-3                            # the mask zeroed the rest
     assert np.abs(d2[:, :, 0:8:2, 0:8:2] - ref2).max() < 1e-5 * np.abs(ref2).max()  # its 4 x 4 outputs
+
+
+def test_fc_diagonals_at_reproduce_the_gathered_product():
+    """The diagonal method with inputs at arbitrary slots (App. D, after a
+    strided packed convolution): sum_r u_r * (x rotated by r) on plain slot
+    vectors holds sum_p W[j][p] x[s_in[p]] in slot o_out[j] of every image
+    block and zero in every other slot, whatever the other slots hold."""
+    rng = np.random.default_rng(83)
+    N, n_img, block = 128, 3, 20
+    s_in, o_out = [0, 2, 4, 10, 12, 14, 19], [0, 1, 2, 5]
+    W = rng.integers(-9, 10, (len(o_out), len(s_in))).astype(float)
+    x = rng.integers(-50, 51, N // 2).astype(float)  # every slot nonzero, the unused ones too
+    diags = O.fc_diagonals_at(W, n_img, block, s_in, o_out, N)
+    y = sum(u * np.roll(x, -r) for r, u in diags.items())  # rotation by r: slot k takes slot k + r
+    want = np.zeros(N // 2)
+    for b in range(n_img):
+        for j, o in enumerate(o_out):
+            want[b * block + o] = sum(W[j][p] * x[b * block + s] for p, s in enumerate(s_in))
+    assert np.array_equal(y, want)
+
+
+def _bhw_net(x, w1, f1, W2, f2, W3, stride):
+    """The branch in plain fp64 per image: conv, +f1, square, flatten, dense,
+    +f2, square, dense."""
+    y = F.conv2d(torch.from_numpy(x), torch.from_numpy(w1.astype(np.float64)), stride=stride).numpy() + f1
+    y = (y * y).reshape(x.shape[0], -1)
+    z = y @ W2.T + f2
+    return (z * z) @ W3.T
+
+
+def test_bhw_branch_decrypts_to_the_network():
+    """A conv-square-dense-square-dense branch evaluated in BHW packing (two
+    images' 16 x 16 segments per ciphertext, a 5 x 5 stride-2 convolution, the
+    dense layers by diagonals over the strided outputs) decrypts to the same
+    network in plain fp64 within 1e-5 of its largest output; the scales follow
+    the rescales (q_{L-1} after the first square, q_{L-3} after the second)."""
+    P = O.Params(10, 7, 1, 1)
+    n, h, w, k, s, c1, n2, n3 = 2, 16, 16, 5, 2, 2, 12, 4
+    ho = (h - k) // s + 1
+    layers = [dict(type="conv", cin=1, h=h, w=w, cout=c1, k=k, stride=s, pad=0, add=True, square=True),
+              dict(type="dense", n_in=c1 * ho * ho, n_out=n2, add=True, square=True),
+              dict(type="dense", n_in=n2, n_out=n3, add=False, square=False)]
+    rng = np.random.default_rng(84)
+    x = rng.uniform(0, 1, (n, 1, h, w))
+    w1 = rng.integers(-3, 4, (c1, 1, k, k))
+    W2 = rng.integers(-3, 4, (n2, c1 * ho * ho))
+    W3 = rng.integers(-3, 4, (n3, n2))
+    f1 = rng.uniform(-1, 1, (n, c1, ho, ho))
+    f2 = rng.uniform(-1, 1, (n, n2))
+    sk, evk = P.keygen(3)
+    L, half, S = P.L, P.N // 2, 2.0**30
+    s1 = S * S / P.q[L - 1]
+    s2 = s1 * s1 / P.q[L - 3]
+    cts = P.encrypt(sk, O.encode(O.pack_bhw(x, P.N), P.N, S, P.q), L, 4)
+    v1 = np.zeros((c1, half))
+    for b in range(n):
+        for yy in range(ho):
+            for xx in range(ho):
+                v1[:, b * h * w + s * (yy * w + xx)] = f1[b, :, yy, xx]
+    v2 = np.zeros((1, half))
+    for b in range(n):
+        v2[0, b * h * w:b * h * w + n2] = f2[b]
+    feats = [O.encode(v1, P.N, S, P.q[:L]), O.encode(v2, P.N, s1, P.q[:L - 2])[0]]
+    pos = [s * (yy * w + xx) for yy in range(ho) for xx in range(ho)]
+    steps = {i * w + j for i in range(k) for j in range(k)}
+    steps |= {p - j for p in pos for j in range(n2)} | {p - j for p in range(n2) for j in range(n3)}
+    gks = {r % half: P.galois_keygen(sk, r % half, 400 + r % half) for r in steps if r % half}
+    out = O.bhw_branch(P, evk, gks, layers, [w1, W2, W3], feats, cts, n)
+    assert out.shape == (2, L - 4, P.N)
+    dec = O.decode(O.crt_centered(P.decrypt(sk, out[None], L - 4), P.q[:L - 4]), P.N, half, s2)[0]
+    ref = _bhw_net(x, w1, f1, W2, f2, W3, s)
+    got = np.stack([dec[b * h * w:b * h * w + n3] for b in range(n)])
+    assert np.abs(got - ref).max() < 1e-5 * np.abs(ref).max()
