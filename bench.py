@@ -51,14 +51,17 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=list(workloads.CONFIGS) + ["cifar_profile", "uneven64", "serve", "rotate", "op_square",
-                                                       "op_mac"])
+                                                       "op_mac", "bhw"])
     ap.add_argument("--cts", type=int, default=384, help="op_square: ciphertexts")
     ap.add_argument("--map", type=int, default=8, help="op_mac: input map height and width")
+    ap.add_argument("--groups", type=int, default=16, help="bhw: ciphertext groups of 16 images per step")
     ap.add_argument("--rates", default="50,100,200,500,1000,2000", help="serve: request rates (req/s)")
     ap.add_argument("--serve-seconds", type=float, default=5.0, help="serve: seconds of arrivals per rate")
     ap.add_argument("--lanes", type=int, default=32, help="serve: batches in flight")
-    ap.add_argument("--stacks", default="cnn3_small:2,4,8;cryptonets:2",
-                    help="serve: stack sizes per model (requests of one model sharing launches)")
+    ap.add_argument("--stacks", default="",
+                    help="serve: stack sizes per model, e.g. 'cnn3_small:2,4,8;cryptonets:2' (requests of one "
+                         "model sharing launches; measured no faster than captured per-request graphs here, so "
+                         "off by default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-budget-s", type=float, default=150.0, help="wall budget of the reference arm")
     return ap.parse_args()
@@ -964,6 +967,76 @@ def run_rotate(args, rank, world, local_rank):
                           "rotations": res}), flush=True)
 
 
+def run_bhw(args, rank, world, local_rank):
+    """The CryptoNets-scale ciphertext branch in BHW packing (App. D): 16
+    images' 16 x 16 segments per ciphertext (N = 8192, 7 + 1 primes), 5 x 5
+    stride-2 conv to 5 maps by hoisted rotations and the MAC, square, 180 -> 100
+    and 100 -> 10 by the diagonal method over the strided outputs, the feature
+    adds and the second square.  --groups ciphertext groups per step, and one
+    group alone (the latency of 16 images); L2 flushed between timed steps."""
+    import torch
+
+    from paper_2402_01296_gb300 import bcn, bhw
+
+    device = local_rank
+    torch.cuda.set_device(device)
+    dev = f"cuda:{device}"
+    cfg = workloads.get_config("cryptonets")
+    ctx = bcn.Context.from_config(cfg, device)
+    n_img, G = 16, args.groups
+    layers = [dict(cfg["cipher"][0])] + [dict(l) for l in cfg["cipher"][1:]]
+    rng = np.random.default_rng(workloads.SEED_WEIGHTS)
+    ho = (16 - 5) // 2 + 1
+    wts = [rng.integers(-3, 4, (5, 1, 5, 5)).astype(np.int8), rng.integers(-3, 4, (100, 5 * ho * ho)),
+           rng.integers(-3, 4, (10, 100))]
+    sk, ek = ctx.keygen(workloads.SEED_KEYS)
+    steps = bhw.BranchBHW.steps_for(layers, n_img, ctx.N)
+    gks = {r: ctx.evk_prepare(bcn.to_device(ctx.galois_keygen(sk, r, workloads.SEED_KEYS + r), dev)) for r in steps}
+    br = bhw.BranchBHW(ctx, layers, wts, n_img, gks, ctx.evk_prepare(bcn.to_device(ek, dev)))
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(workloads.SEED_ENC)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    n_rot = len(br.conv_steps) - 1 + sum(d["n_in"] * len(d["steps"]) for d in br.dense)
+
+    def timed(g, steps_):
+        x = _dev_residues(torch, ctx.q, (g, 1, 2), ctx.N, gen, dev)
+        feats = []
+        for shp in br.feature_shapes(g):
+            feats.append(_dev_residues(torch, ctx.q[:shp[-2]], shp[:-2], ctx.N, gen, dev))
+        out = torch.empty((g, 2, br.out_level, ctx.N), dtype=torch.int32, device=dev)
+        for _ in range(max(3, args.warmup)):
+            br(x, g, feats, out)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(steps_):
+            flush.zero_()
+            s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s_.record()
+            br(x, g, feats, out)
+            e_.record()
+            torch.cuda.synchronize()
+            ms.append(s_.elapsed_time(e_))
+        assert ctx.device_status() == 0
+        return statistics.mean(ms)
+
+    clocks = ClockSampler(device)
+    clocks.start()
+    t = timed(G, args.steps)
+    clk = clocks.stop()
+    t1 = timed(1, args.steps)
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": G * n_img * world / (t / 1e3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": t, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic (uniform residues as ciphertexts and features; integer weights in [-3, 3])",
+            "config": {"workload": f"bhw: CryptoNets-scale branch in BHW packing, {G} groups of {n_img} images "
+                                   "(N=8192, 7+1 primes)",
+                       "l2": "flushed (512 MiB write) between timed steps, outside the events"},
+            "rotations_per_group": n_rot, "rotations_per_s": G * n_rot * world / (t / 1e3),
+            "latency_ms_one_group": t1, "clocks": clk}), flush=True)
+
+
 # ---------------------------------------------------------------------------
 # op-level workloads (small cases for kernel profiles)
 # ---------------------------------------------------------------------------
@@ -1053,6 +1126,8 @@ def _main():
         return run_serve(args, rank, world, local_rank)
     if args.workload == "rotate":
         return run_rotate(args, rank, world, local_rank)
+    if args.workload == "bhw":
+        return run_bhw(args, rank, world, local_rank)
     if args.workload in ("op_square", "op_mac"):
         return run_op(args, rank, world, local_rank)
     if args.workload == "cifar_profile":

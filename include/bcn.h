@@ -472,6 +472,29 @@ bcn_status bcn_op_fc_diag_workspace_bytes(const bcn_ctx *ctx, int level, int n_r
 bcn_status bcn_op_fc_diag(const bcn_ctx *ctx, int level, const uint32_t *const *gk_evals, const int *steps, int n_rot,
                           const uint32_t *diag_ntt_dev, const uint32_t *in_dev, int n_ct, uint32_t *out_dev,
                           void *workspace_dev, size_t workspace_bytes, void *cuda_stream);
+/* The dense layer of App. D over c input ciphertexts per group (BHW packing
+ * holds one channel per ciphertext, so a dense layer after a convolution reads
+ * c of them), with the layer's plaintext feature added (Sec. 3.2's
+ * unidirectional add, App. A Add(c, u)):
+ *     y = Rescale_{q_{level-1}}( sum_k sum_r u_{k,r} * Rot(x_k, r) ) + f.
+ * The inputs' slots may sit anywhere in each image block (a strided
+ * convolution leaves its outputs at every s-th position): u_{k,r} carries
+ * W[j][p] in output j's slot for every input position p of channel k at slot
+ * distance r from it, which also drops the slots a strided convolution does
+ * not keep.  Every input ciphertext's rotations share one ModUp; all products
+ * are summed in the NTT domain, transformed back and rescaled once.
+ * steps[n_rot], gk_evals[n_rot] as for bcn_op_rotate_many (the same rotations
+ * for every input); diag_ntt [n_in][n_rot][level][N] (NTT domain, encoded at
+ * scale q_{level-1}); in [n_groups][n_in][2][level][N] -> out
+ * [n_groups][2][level-1][N], coefficient form, device; pt NULL or
+ * [n_groups][level-1][N] (coefficient form) added to each output's first
+ * polynomial.  Workspace bcn_op_fc_diag_workspace_bytes(level, n_rot).
+ * BCN_E_INVAL on a bad level or count, an unaligned buffer or in/out overlap;
+ * BCN_E_BUDGET if the workspace is too small. */
+bcn_status bcn_op_fc_diag_sum(const bcn_ctx *ctx, int level, const uint32_t *const *gk_evals, const int *steps,
+                              int n_rot, const uint32_t *diag_ntt_dev, const uint32_t *in_dev, int n_in, int n_groups,
+                              const uint32_t *pt_dev, uint32_t *out_dev, void *workspace_dev, size_t workspace_bytes,
+                              void *cuda_stream);
 /* Ciphertext-plaintext product then rescale (App. A Mult(c, u) with an encoded
  * u -- the masks of App. D's packed layers): (c0 u, c1 u) in R_{Q_level}, then
  * the rescale by q_{level-1}.  Encode u at scale q_{level-1} to keep the

@@ -116,6 +116,7 @@ _SIGS = {
     "bcn_op_rotate_many": (_I, [_P, _I, _P, _P, _I, _P, _I, _P, _P, _SZ, _P]),
     "bcn_op_fc_diag_workspace_bytes": (_I, [_P, _I, _I, ctypes.POINTER(_SZ)]),
     "bcn_op_fc_diag": (_I, [_P, _I, _P, _P, _I, _P, _P, _I, _P, _P, _SZ, _P]),
+    "bcn_op_fc_diag_sum": (_I, [_P, _I, _P, _P, _I, _P, _P, _I, _I, _P, _P, _P, _SZ, _P]),
     "bcn_int_peak_grid": (_I, [_I, ctypes.POINTER(_I)]),
     "bcn_int_peak_launch": (_I, [_I, _I, _P, _SZ, _P, ctypes.POINTER(_D)]),
 }
@@ -409,6 +410,34 @@ class Context:
                                     _dev_ptr(in_dev, n_ct * 2 * level * self.N), n_ct,
                                     _dev_ptr(out_dev, n_ct * 2 * (level - 1) * self.N), ws.data_ptr(), nb.value,
                                     _stream(stream)), "bcn_op_fc_diag")
+
+    def op_fc_diag_sum(self, level, gk_evals: dict, steps: list, diag_ntt, in_dev, n_in, n_groups, out_dev,
+                       pt_dev=None, workspace=None, stream=None):
+        """bcn_op_fc_diag_sum: the diagonal-method dense layer over n_in inputs per
+        group; diag_ntt [n_in][len(steps)][level][N] (NTT domain), in
+        [n_groups][n_in][2][level][N] -> out [n_groups][2][level-1][N], plus
+        pt_dev [n_groups][level-1][N] when given."""
+        n_rot = len(steps)
+        ptrs, st = self._key_table(gk_evals, steps)
+        if workspace is None:
+            workspace = self.fc_diag_workspace(level, n_rot)
+        _check(lib().bcn_op_fc_diag_sum(self._h, level, ptrs, st, n_rot,
+                                        _dev_ptr(diag_ntt, n_in * n_rot * level * self.N),
+                                        _dev_ptr(in_dev, n_groups * n_in * 2 * level * self.N), n_in, n_groups,
+                                        _dev_ptr(pt_dev, n_groups * (level - 1) * self.N) if pt_dev is not None
+                                        else None,
+                                        _dev_ptr(out_dev, n_groups * 2 * (level - 1) * self.N), workspace.data_ptr(),
+                                        workspace.numel() * workspace.element_size(), _stream(stream)),
+               "bcn_op_fc_diag_sum")
+
+    def fc_diag_workspace(self, level: int, n_rot: int):
+        """A device workspace for bcn_op_fc_diag / bcn_op_fc_diag_sum."""
+        import torch
+
+        nb = _SZ(0)
+        _check(lib().bcn_op_fc_diag_workspace_bytes(self._h, level, n_rot, ctypes.byref(nb)),
+               "bcn_op_fc_diag_workspace_bytes")
+        return torch.empty(max(1, (nb.value + 3) // 4), dtype=torch.int32, device=f"cuda:{self.device}")
 
     def op_mul_plain_rescale(self, level, in_dev, n_ct, pt_dev, out_dev, stream=None):
         """(c0 u, c1 u), then rescale: in [n_ct][2][level][N], pt [level][N] -> out at level - 1."""

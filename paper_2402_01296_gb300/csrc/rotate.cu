@@ -9,6 +9,7 @@
 // key-switching core (ModUp, NTT, key product, iNTT -- the same kernel as the
 // relinearisation), then ModDown with sigma_g(c0) added (no rescale).
 #include <algorithm>
+#include <string>
 #include <cuda_runtime.h>
 
 #include "device_api.h"
@@ -123,11 +124,12 @@ __global__ void __launch_bounds__(256) k_moddown_rot_many(const uint32_t *__rest
 
 // Sum of products in the NTT domain: out[b][i][k] = sum_r R[r][b][i][k] U[r][i][k]
 // mod q_i (R [n_terms][2][n][N] the rotated ciphertexts, U [n_terms][n][N] the
-// diagonal plaintexts, both canonical).  Products below 2^60 summed in 64 bits,
-// reduced every 15 terms.  Four coefficients a thread.  grid (N/4/256, n, 2)
+// diagonal plaintexts, both canonical), added to out's own values when
+// `accumulate` is set.  Products below 2^60 summed in 64 bits, reduced every 15
+// terms (the first group of 15 also holds out's value, below 2^32).  Four coefficients a thread.  grid (N/4/256, n, 2)
 __global__ void __launch_bounds__(256) k_mul_acc(const uint32_t *__restrict__ R, const uint32_t *__restrict__ U,
                                                  uint32_t *__restrict__ out, int n_terms, int n, int N,
-                                                 const PrimeConst *__restrict__ pc) {
+                                                 int accumulate, const PrimeConst *__restrict__ pc) {
     const int k4 = blockIdx.x * blockDim.x + threadIdx.x;
     if (k4 * 4 >= N) return;
     const int i = blockIdx.y, b = blockIdx.z;
@@ -135,6 +137,10 @@ __global__ void __launch_bounds__(256) k_mul_acc(const uint32_t *__restrict__ R,
     const uint64_t mu = pc[i].barrett;
     const size_t ct_words = (size_t)2 * n * N;
     uint64_t acc[4] = {0, 0, 0, 0};
+    if (accumulate) {  // add to the running sum of earlier inputs (canonical, < 2^32)
+        const uint4 o = reinterpret_cast<const uint4 *>(out + ((size_t)b * n + i) * N)[k4];
+        acc[0] = o.x, acc[1] = o.y, acc[2] = o.z, acc[3] = o.w;
+    }
     int cnt = 0;
     for (int r = 0; r < n_terms; r++) {
         const uint4 x = __ldg(reinterpret_cast<const uint4 *>(R + r * ct_words + ((size_t)b * n + i) * N) + k4);
@@ -155,6 +161,25 @@ __global__ void __launch_bounds__(256) k_mul_acc(const uint32_t *__restrict__ R,
     o.z = barrett_reduce64(acc[2], q, mu);
     o.w = barrett_reduce64(acc[3], q, mu);
     reinterpret_cast<uint4 *>(out + ((size_t)b * n + i) * N)[k4] = o;
+}
+
+// Add(c, u) of App. A for a plaintext per ciphertext: c0 += u mod q_i, in place
+// (ct [C][2][n][N], pt [C][n][N], coefficient form, canonical).  Four
+// coefficients a thread.  grid (N/4/256, n, C)
+__global__ void __launch_bounds__(256) k_add_plain(uint32_t *__restrict__ ct, const uint32_t *__restrict__ pt, int n,
+                                                   int N, const PrimeConst *__restrict__ pc) {
+    const int k4 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k4 * 4 >= N) return;
+    const int i = blockIdx.y, g = blockIdx.z;
+    const uint32_t q = pc[i].q;
+    uint4 *c = reinterpret_cast<uint4 *>(ct + ((size_t)g * 2 * n + i) * N) + k4;
+    const uint4 u = __ldg(reinterpret_cast<const uint4 *>(pt + ((size_t)g * n + i) * N) + k4);
+    uint4 v = *c;
+    v.x = add_mod(v.x, u.x, q);
+    v.y = add_mod(v.y, u.y, q);
+    v.z = add_mod(v.z, u.z, q);
+    v.w = add_mod(v.w, u.w, q);
+    *c = v;
 }
 
 // g^{-1} mod 2N: the odd residues mod 2N form a group of order N, so g^{N-1}
@@ -278,36 +303,67 @@ extern "C" bcn_status bcn_op_fc_diag_workspace_bytes(const bcn_ctx *c, int level
     return BCN_OK;
 }
 
-extern "C" bcn_status bcn_op_fc_diag(const bcn_ctx *c, int level, const uint32_t *const *gk_evals, const int *steps,
-                                     int n_rot, const uint32_t *diag_ntt, const uint32_t *in, int n_ct,
-                                     uint32_t *out, void *ws, size_t ws_bytes, void *stream) {
-    if (!c) return fail(BCN_E_INVAL, "bcn_op_fc_diag: null context");
-    if (level < 2 || level > c->L || n_ct < 0 || n_rot < 1) return fail(BCN_E_INVAL, "bcn_op_fc_diag: bad level");
-    if (n_ct == 0) return BCN_OK;
+// Diagonal-method dense layer over n_in input ciphertexts per group, summed
+// before the one inverse transform and rescale, then the optional plaintext
+// added (bcn_op_fc_diag is n_in = 1, no plaintext).
+static bcn_status fc_diag_impl(const bcn_ctx *c, const char *who, int level, const uint32_t *const *gk_evals,
+                               const int *steps, int n_rot, const uint32_t *diag_ntt, const uint32_t *in, int n_in,
+                               int n_groups, const uint32_t *pt, uint32_t *out, void *ws, size_t ws_bytes,
+                               void *stream) {
+    if (!c) return fail(BCN_E_INVAL, std::string(who) + ": null context");
+    if (level < 2 || level > c->L || n_groups < 0 || n_rot < 1 || n_in < 1)
+        return fail(BCN_E_INVAL, std::string(who) + ": bad level or count");
+    if (n_groups == 0) return BCN_OK;
     size_t need = 0;
     BCN_TRY(bcn_op_fc_diag_workspace_bytes(c, level, n_rot, &need));
-    if (!ws || ws_bytes < need) return fail(BCN_E_BUDGET, "bcn_op_fc_diag: workspace too small");
+    if (!ws || ws_bytes < need) return fail(BCN_E_BUDGET, std::string(who) + ": workspace too small");
     auto a16 = [](const void *p) { return ((uintptr_t)p & 15) == 0; };
-    if (!diag_ntt || !in || !out || !a16(diag_ntt) || !a16(in) || !a16(out) || !a16(ws))
-        return fail(BCN_E_INVAL, "bcn_op_fc_diag: null or unaligned buffer");
-    const size_t N = c->N, n = (size_t)level, ct_words = 2 * n * N;
+    if (!diag_ntt || !in || !out || !a16(diag_ntt) || !a16(in) || !a16(out) || !a16(ws) || (pt && !a16(pt)))
+        return fail(BCN_E_INVAL, std::string(who) + ": null or unaligned buffer");
+    const size_t N = c->N, n = (size_t)level, ct_words = 2 * n * N, out_words = 2 * (n - 1) * N;
+    const uint32_t *in_end = in + (size_t)n_groups * n_in * ct_words, *out_end = out + (size_t)n_groups * out_words;
+    if (in < out_end && out < in_end) return fail(BCN_E_INVAL, std::string(who) + ": in and out overlap");
     size_t rot_bytes = 0;
     BCN_TRY(bcn_op_rotate_many_workspace_bytes(c, level, 1, &rot_bytes));
     char *w = reinterpret_cast<char *>(ws);
     uint32_t *R = reinterpret_cast<uint32_t *>(w + rot_bytes);
     uint32_t *acc = R + (size_t)n_rot * ct_words;
     cudaStream_t st = (cudaStream_t)stream;
-    for (int k = 0; k < n_ct; k++) {
-        const uint32_t *x = in + (size_t)k * ct_words;
-        BCN_TRY(bcn_op_rotate_many(c, level, gk_evals, steps, n_rot, x, 1, R, ws, rot_bytes, stream));
-        BCN_TRY(launch_ntt(c, R, (size_t)n_rot * 2 * n, data_map(level), false, st));
-        k_mul_acc<<<dim3((unsigned)((N / 4 + 255) / 256), (unsigned)n, 2), 256, 0, st>>>(R, diag_ntt, acc, n_rot,
-                                                                                       level, (int)N, c->d_pc);
-        BCN_TRY(check_launch("k_mul_acc"));
+    const dim3 grid((unsigned)((N / 4 + 255) / 256), (unsigned)n, 2);
+    for (int g = 0; g < n_groups; g++) {
+        for (int k = 0; k < n_in; k++) {
+            const uint32_t *x = in + ((size_t)g * n_in + k) * ct_words;
+            BCN_TRY(bcn_op_rotate_many(c, level, gk_evals, steps, n_rot, x, 1, R, ws, rot_bytes, stream));
+            BCN_TRY(launch_ntt(c, R, (size_t)n_rot * 2 * n, data_map(level), false, st));
+            k_mul_acc<<<grid, 256, 0, st>>>(R, diag_ntt + (size_t)k * n_rot * n * N, acc, n_rot, level, (int)N,
+                                            k > 0, c->d_pc);
+            BCN_TRY(check_launch("k_mul_acc"));
+        }
+        uint32_t *o = out + (size_t)g * out_words;
         BCN_TRY(launch_ntt(c, acc, 2 * n, data_map(level), true, st));
-        BCN_TRY(launch_rescale(c, level, acc, out + (size_t)k * 2 * (n - 1) * N, 1, st));
+        BCN_TRY(launch_rescale(c, level, acc, o, 1, st));
+        if (pt) {
+            k_add_plain<<<dim3((unsigned)((N / 4 + 255) / 256), (unsigned)(n - 1), 1), 256, 0, st>>>(
+                o, pt + (size_t)g * (n - 1) * N, (int)(n - 1), (int)N, c->d_pc);
+            BCN_TRY(check_launch("k_add_plain"));
+        }
     }
     return BCN_OK;
+}
+
+extern "C" bcn_status bcn_op_fc_diag(const bcn_ctx *c, int level, const uint32_t *const *gk_evals, const int *steps,
+                                     int n_rot, const uint32_t *diag_ntt, const uint32_t *in, int n_ct,
+                                     uint32_t *out, void *ws, size_t ws_bytes, void *stream) {
+    return fc_diag_impl(c, "bcn_op_fc_diag", level, gk_evals, steps, n_rot, diag_ntt, in, 1, n_ct, nullptr, out, ws,
+                        ws_bytes, stream);
+}
+
+extern "C" bcn_status bcn_op_fc_diag_sum(const bcn_ctx *c, int level, const uint32_t *const *gk_evals,
+                                         const int *steps, int n_rot, const uint32_t *diag_ntt, const uint32_t *in,
+                                         int n_in, int n_groups, const uint32_t *pt, uint32_t *out, void *ws,
+                                         size_t ws_bytes, void *stream) {
+    return fc_diag_impl(c, "bcn_op_fc_diag_sum", level, gk_evals, steps, n_rot, diag_ntt, in, n_in, n_groups, pt, out,
+                        ws, ws_bytes, stream);
 }
 
 extern "C" bcn_status bcn_op_rotate(const bcn_ctx *c, int level, const uint32_t *gk, int steps, const uint32_t *in,

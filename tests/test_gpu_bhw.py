@@ -125,3 +125,122 @@ def test_strided_then_gapped_conv_bit_exact():
     ref2 = torch.nn.functional.conv2d(ref1, torch.from_numpy(w2.astype(np.float64))).numpy()
     dec = bhw.unpack(c.decrypt_decode(sk, got, P.L - 1, S, P.N // 2), n, h, w)
     assert np.abs(dec[:, :, 0:8:2, 0:8:2] - ref2).max() < 1e-5 * np.abs(ref2).max()
+
+
+def _branch_case(P, n, h, w, k, s, c1, n2, n3, rng):
+    ho = (h - k) // s + 1
+    layers = [dict(type="conv", cin=1, h=h, w=w, cout=c1, k=k, stride=s, pad=0, add=True, square=True),
+              dict(type="dense", n_in=c1 * ho * ho, n_out=n2, add=True, square=True),
+              dict(type="dense", n_in=n2, n_out=n3, add=False, square=False)]
+    x = rng.uniform(0, 1, (n, 1, h, w))
+    wts = [rng.integers(-3, 4, (c1, 1, k, k)).astype(np.int8), rng.integers(-3, 4, (n2, c1 * ho * ho)),
+           rng.integers(-3, 4, (n3, n2))]
+    f1 = rng.uniform(-1, 1, (n, c1, ho, ho))
+    f2 = rng.uniform(-1, 1, (n, n2))
+    half = P.N // 2
+    v1 = np.zeros((c1, half))
+    for b in range(n):
+        for yy in range(ho):
+            for xx in range(ho):
+                v1[:, b * h * w + s * (yy * w + xx)] = f1[b, :, yy, xx]
+    v2 = np.zeros((1, half))
+    for b in range(n):
+        v2[0, b * h * w:b * h * w + n2] = f2[b]
+    return layers, x, wts, f1, f2, v1, v2
+
+
+def _net(x, wts, f1, f2, s):
+    y = torch.nn.functional.conv2d(torch.from_numpy(x), torch.from_numpy(wts[0].astype(np.float64)),
+                                   stride=s).numpy() + f1
+    y = (y * y).reshape(x.shape[0], -1)
+    z = y @ wts[1].T + f2
+    return (z * z) @ wts[2].T
+
+
+def test_bhw_branch_bit_exact():
+    """A whole conv-square-dense-square-dense branch in BHW packing (App. D) on
+    the device -- hoisted rotations + MAC with the feature add, square,
+    bcn_op_fc_diag_sum over the strided outputs of two channels with the
+    feature add, square, the output dense layer -- for two groups of two
+    images, bit-exact against the oracle's branch on the same encodings; the
+    library's diagonal layout equals the oracle's."""
+    c, P = bcn.Context(10, 7, 1, 1, device=0), O.Params(10, 7, 1, 1)
+    n, h, w, k, s, c1, n2, n3 = 2, 16, 16, 5, 2, 2, 12, 4
+    rng = np.random.default_rng(85)
+    L, half, S = P.L, P.N // 2, 2.0**30
+    s1 = S * S / P.q[L - 1]
+    sk, evk = P.keygen(3)
+    layers, _, wts, _, _, _, _ = _branch_case(P, n, h, w, k, s, c1, n2, n3, rng)
+    steps = bhw.BranchBHW.steps_for(layers, n, P.N)
+    keys = {r: P.galois_keygen(sk, r, 500 + r) for r in steps}
+    groups, want, feats = [], [], [[], []]
+    for g in range(2):
+        _, x, _, _, _, v1, v2 = _branch_case(P, n, h, w, k, s, c1, n2, n3, rng)
+        cts = P.encrypt(sk, O.encode(O.pack_bhw(x, P.N), P.N, S, P.q), L, 4 + g)
+        ft = [O.encode(v1, P.N, S, P.q[:L]), O.encode(v2, P.N, s1, P.q[:L - 2])[0]]
+        want.append(O.bhw_branch(P, evk, keys, layers, wts, ft, cts, n))
+        groups.append(cts)
+        feats[0].append(ft[0])
+        feats[1].append(ft[1])
+    # the device's diagonals: its own layout, the oracle's encodings of it
+    ho = (h - k) // s + 1
+    pos = [s * (yy * w + xx) for yy in range(ho) for xx in range(ho)]
+    diag_pts, lv = [], L - 1
+    for W, s_in, C in ((wts[1], pos, c1), (wts[2], list(range(n2)), 1)):
+        per = []
+        for ch in range(C):
+            part = W[:, ch * len(s_in):(ch + 1) * len(s_in)]
+            st, lay = bhw.fc_layout_at(part, n, h * w, s_in, list(range(W.shape[0])), P.N)
+            od = O.fc_diagonals_at(part, n, h * w, s_in, list(range(W.shape[0])), P.N)
+            assert st == sorted(od) and np.array_equal(lay, np.array([od[r] for r in st]))
+            per.append(O.encode(lay, P.N, float(P.q[lv - 1]), P.q[:lv]))
+        diag_pts.append(np.stack(per))
+        lv -= 2
+    gks = {r: c.evk_prepare(bcn.to_device(kk)) for r, kk in keys.items()}
+    ev = c.evk_prepare(bcn.to_device(evk))
+    br = bhw.BranchBHW(c, layers, wts, n, gks, ev, diag_pts=diag_pts)
+    assert br.rotation_steps_needed() == steps and br.out_level == L - 4
+    out = torch.empty((2, 2, L - 4, P.N), dtype=torch.int32, device="cuda")
+    br(bcn.to_device(np.stack(groups)), 2, [bcn.to_device(np.stack(feats[0])), bcn.to_device(np.stack(feats[1]))],
+       out)
+    got = bcn.to_host_u32(out)
+    assert c.device_status() == 0
+    for g in range(2):
+        assert np.array_equal(got[g], want[g]), g
+
+
+def test_bhw_cryptonets_branch_full_size_decrypts():
+    """The CryptoNets-scale branch (5 x 5 stride-2 conv to 5 maps, 180 -> 100,
+    100 -> 10, two feature adds and two squares) in BHW packing at its full
+    ring, N = 8192 with 16 images' 16 x 16 segments per ciphertext, three
+    groups, with the library's own encoder and keys: every image's outputs
+    decrypt to the same network in fp64 within 1e-4 of the largest output."""
+    cfg = workloads.get_config("cryptonets")
+    c = bcn.Context.from_config(cfg)
+    n, h, w, k, s, c1, n2, n3 = 16, 16, 16, 5, 2, 5, 100, 10
+    rng = np.random.default_rng(86)
+    L, half, S = c.L, c.N // 2, 2.0**30
+    s1 = S * S / c.q[L - 1]
+    s2 = s1 * s1 / c.q[L - 3]
+    sk, evk = c.keygen(3)
+    layers, _, wts, _, _, _, _ = _branch_case(c, n, h, w, k, s, c1, n2, n3, rng)
+    assert [l["n_in"] for l in layers[1:]] == [l["n_in"] for l in cfg["cipher"][1:]]
+    steps = bhw.BranchBHW.steps_for(layers, n, c.N)
+    gks = {r: c.evk_prepare(bcn.to_device(c.galois_keygen(sk, r, 600 + r))) for r in steps}
+    br = bhw.BranchBHW(c, layers, wts, n, gks, c.evk_prepare(bcn.to_device(evk)))
+    G = 3
+    xs, cts, f1s, f2s, ft0, ft1 = [], [], [], [], [], []
+    for g in range(G):
+        _, x, _, f1, f2, v1, v2 = _branch_case(c, n, h, w, k, s, c1, n2, n3, rng)
+        xs.append(x), f1s.append(f1), f2s.append(f2)
+        cts.append(c.encrypt(sk, c.encode(bhw.pack(x, c.N), L, S), L, 10 + g))
+        ft0.append(c.encode(v1, L, S))
+        ft1.append(c.encode(v2, L - 2, s1)[0])
+    out = torch.empty((G, 2, br.out_level, c.N), dtype=torch.int32, device="cuda")
+    br(bcn.to_device(np.stack(cts)), G, [bcn.to_device(np.stack(ft0)), bcn.to_device(np.stack(ft1))], out)
+    assert c.device_status() == 0
+    dec = c.decrypt_decode(sk, bcn.to_host_u32(out), br.out_level, s2, half)
+    for g in range(G):
+        ref = _net(xs[g], wts, f1s[g], f2s[g], s)
+        got = np.stack([dec[g, b * h * w:b * h * w + n3] for b in range(n)])
+        assert np.abs(got - ref).max() < 1e-4 * np.abs(ref).max()
