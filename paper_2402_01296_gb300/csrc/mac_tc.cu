@@ -5,11 +5,13 @@
 // int8 weights times residues below 2^30 (Sec. 3.2: the ciphertext branch's
 // linear layers use integer weights, so a MAC is plain integer arithmetic on
 // the residues).  The tensor cores have no exact wide-integer path here, so a
-// residue is split into its 4 bytes and each byte plane is one fp16 GEMM:
-// bytes (0..255) and weights (-127..127) are exact in fp16, their products are
-// exact, and every partial sum of at most 512 taps stays below
-// 512 * 255 * 127 < 2^24 in magnitude, so the fp32 accumulation in tensor
-// memory is exact.  The epilogue recombines the planes in int64
+// residue is split into its 4 bytes and each byte plane is one fp16 GEMM: a
+// byte v sits in a half as the subnormal v * 2^-24 (the half's bit pattern is
+// the byte itself, so a byte permute and a mask make two taps' halves),
+// weights (-127..127) are exact, their products are exact multiples of 2^-24,
+// and every partial sum of at most 512 taps stays below 512 * 255 * 127 < 2^24
+// of those units, so the fp32 accumulation in tensor memory is exact.  The
+// epilogue scales by 2^24, recombines the planes in int64
 // (sum_b plane_b * 2^{8b}), adds a multiple of q that makes the sum
 // non-negative and reduces mod q (Barrett), then adds the feature plaintext.
 //
@@ -74,13 +76,11 @@ __host__ __device__ constexpr uint32_t instr_desc(int M, int N) {
     return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-// two residues' byte b as fp16 pair (tap k in the low half, tap k+1 in the high)
+// two residues' byte b as a pair of subnormal halves (byte v is the half
+// v * 2^-24): tap k in the low half, tap k + 1 in the high
 __device__ __forceinline__ uint32_t byte_pair(uint32_t x0, uint32_t x1, int b) {
     const uint32_t sel = (uint32_t)b | ((uint32_t)b << 4) | ((uint32_t)(4 + b) << 8) | ((uint32_t)(4 + b) << 12);
-    uint32_t v = (__byte_perm(x0, x1, sel) & 0x00FF00FFu) | 0x64006400u;  // 1024 + byte
-    __half2 h = *reinterpret_cast<__half2 *>(&v);
-    h = __hsub2(h, __half2(__ushort_as_half(0x6400), __ushort_as_half(0x6400)));  // exact byte
-    return *reinterpret_cast<uint32_t *>(&h);
+    return __byte_perm(x0, x1, sel) & 0x00FF00FFu;
 }
 
 __device__ __forceinline__ void tmem_ld8(uint32_t addr, uint32_t (&r)[8]) {
@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_mac_tc(const uint32_t *__res
                     long long v = offs;
 #pragma unroll
                     for (int b = 0; b < kPlanes; b++)
-                        v += (long long)__float2int_rn(__uint_as_float(f[b][o])) << (8 * b);
+                        v += (long long)__float2int_rn(__uint_as_float(f[b][o]) * 16777216.0f) << (8 * b);
                     const uint32_t res = add_mod(barrett_reduce64((uint64_t)v, q, mu), pv[o], q);
                     const int os = store_natural ? sgo[ob + o] : (g - g_base) * n_go + o0 + ob + o;
                     out[(size_t)os * cols + col] = res;
