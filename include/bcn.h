@@ -153,6 +153,39 @@ bcn_status bcn_encrypt_segment(const bcn_ctx *ctx, const int8_t *sk, const uint8
 bcn_status bcn_decrypt_decode(const bcn_ctx *ctx, const int8_t *sk, const uint32_t *cts, int n_ct, int level,
                               double scale, int B, double *out);
 
+/* Messages (Sec. 2: the client sends its encrypted segments, plaintexts and
+ * evaluation keys to the server and receives the output ciphertexts).  A
+ * message is a 64-byte header followed by the payload words; every field and
+ * word is little-endian:
+ *   bytes  0..3   magic "BCN1"
+ *          4..7   kind (bcn_message_kind)
+ *          8..23  log_n, n_data, n_special, alpha of the context (uint32 each)
+ *         24..27  level (ciphertexts, plaintexts; 0 for keys)
+ *         28..31  count (ciphertexts or plaintexts; 1 for a key)
+ *         32..35  Galois element g (Galois keys; 0 otherwise)
+ *         36..43  payload words (uint64)
+ *         44..47  FNV-1a (32-bit) checksum of the payload bytes
+ *         48..63  zero
+ * Payload: ciphertexts [count][2][level][N], plaintexts [count][level][N]
+ * (coefficient form), keys [dnum][2][L+K][N] in the raw form bcn_keygen and
+ * bcn_galois_keygen write (the server prepares them with bcn_evk_prepare);
+ * every residue below its prime.  bcn_message_bytes: the message size (0 for a
+ * bad shape).  bcn_serialize writes header and payload to `out`.
+ * bcn_deserialize_header checks the magic, the kind, the reserved bytes, the
+ * context's parameters, the payload size against the shape and the buffer,
+ * and reports kind, level, count and g; bcn_deserialize also verifies the
+ * checksum and that every residue is below its prime, then copies the words.
+ * BCN_E_INVAL on any mismatch, BCN_E_BUDGET if an output buffer is too small.
+ * Host memory. */
+typedef enum { BCN_MSG_CIPHERTEXTS = 1, BCN_MSG_RELIN_KEY = 2, BCN_MSG_GALOIS_KEY = 3, BCN_MSG_PLAINTEXTS = 4 } bcn_message_kind;
+size_t bcn_message_bytes(const bcn_ctx *ctx, int kind, int level, int count);
+bcn_status bcn_serialize(const bcn_ctx *ctx, int kind, int level, int count, uint32_t galois, const uint32_t *words,
+                         uint8_t *out, size_t out_bytes);
+bcn_status bcn_deserialize_header(const bcn_ctx *ctx, const uint8_t *in, size_t in_bytes, int *kind, int *level,
+                                  int *count, uint32_t *galois);
+bcn_status bcn_deserialize(const bcn_ctx *ctx, const uint8_t *in, size_t in_bytes, uint32_t *words_out,
+                           size_t out_words);
+
 /* ------------------------------------------------ plaintext branch (fp32) */
 /* The plaintext branch (Sec. 3.1) runs on the whole image with the sensitive
  * segment set to zero and the insensitive segment perturbed by additive

@@ -72,6 +72,11 @@ _SIGS = {
     "bcn_encrypt": (_I, [_P, _P, _P, _I, _I, _U64, _P]),
     "bcn_encrypt_segment": (_I, [_P, _P, _P, _I, _I, _I, _I, _P, _D, _U64, _P]),
     "bcn_decrypt_decode": (_I, [_P, _P, _P, _I, _I, _D, _I, _P]),
+    "bcn_message_bytes": (_SZ, [_P, _I, _I, _I]),
+    "bcn_serialize": (_I, [_P, _I, _I, _I, ctypes.c_uint32, _P, _P, _SZ]),
+    "bcn_deserialize_header": (_I, [_P, _P, _SZ, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                                    ctypes.POINTER(ctypes.c_uint32)]),
+    "bcn_deserialize": (_I, [_P, _P, _SZ, _P, _SZ]),
     "bcn_plain_model_create": (_I, [_P, _P, _I, _I, _I, _I, _P, ctypes.POINTER(_P)]),
     "bcn_plain_model_destroy": (_I, [_P]),
     "bcn_plain_feature_count": (_I, [_P, ctypes.POINTER(_I)]),
@@ -303,6 +308,42 @@ class Context:
                                         _np_ptr(cts, np.uint32), n, level, scale, B, _np_ptr(out, np.float64)),
                "bcn_decrypt_decode")
         return out
+
+    # -- messages (client <-> server) -------------------------------------
+    MSG_CIPHERTEXTS, MSG_RELIN_KEY, MSG_GALOIS_KEY, MSG_PLAINTEXTS = 1, 2, 3, 4
+
+    def serialize(self, kind: int, words: np.ndarray, level: int = 0, galois: int = 0) -> bytes:
+        """bcn_serialize: ciphertexts [n][2][level][N] or plaintexts [n][level][N]
+        (count = n), or a raw key (level 0, count 1; galois = its element for a
+        Galois key) -> the message bytes."""
+        w = np.ascontiguousarray(words, dtype=np.uint32)
+        count = 1 if kind in (self.MSG_RELIN_KEY, self.MSG_GALOIS_KEY) else int(w.shape[0])
+        nb = int(lib().bcn_message_bytes(self._h, kind, level, count))
+        if nb == 0:
+            raise BcnError(-1, "bcn_message_bytes", "bad message shape")
+        out = np.zeros(nb, dtype=np.uint8)
+        _check(lib().bcn_serialize(self._h, kind, level, count, int(galois), _np_ptr(w, np.uint32),
+                                   _np_ptr(out, np.uint8), nb), "bcn_serialize")
+        return out.tobytes()
+
+    def deserialize(self, msg: bytes) -> dict:
+        """bcn_deserialize: the message -> {kind, level, count, galois, words}
+        (words shaped as serialize took them)."""
+        buf = np.frombuffer(msg, dtype=np.uint8)
+        k, lv, ct, g = _I(), _I(), _I(), ctypes.c_uint32()
+        _check(lib().bcn_deserialize_header(self._h, _np_ptr(buf, np.uint8), buf.size, ctypes.byref(k),
+                                            ctypes.byref(lv), ctypes.byref(ct), ctypes.byref(g)),
+               "bcn_deserialize_header")
+        if k.value == self.MSG_CIPHERTEXTS:
+            shape = (ct.value, 2, lv.value, self.N)
+        elif k.value == self.MSG_PLAINTEXTS:
+            shape = (ct.value, lv.value, self.N)
+        else:
+            shape = self.evk_shape()
+        out = np.zeros(shape, dtype=np.uint32)
+        _check(lib().bcn_deserialize(self._h, _np_ptr(buf, np.uint8), buf.size, _np_ptr(out, np.uint32), out.size),
+               "bcn_deserialize")
+        return {"kind": k.value, "level": lv.value, "count": ct.value, "galois": g.value, "words": out}
 
     # -- device ----------------------------------------------------------
     def evk_prepare(self, evk_dev, out=None, stream=None):

@@ -440,3 +440,124 @@ bcn_status bcn_decrypt_decode(const bcn_ctx *c, const int8_t *sk, const uint32_t
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- messages
+// Serialised ciphertexts, plaintexts and keys (the client -> server messages
+// of Sec. 2): a 64-byte little-endian header, then the payload words.
+namespace {
+constexpr uint32_t kMagic = 0x314E4342u;  // "BCN1" read as a little-endian word
+constexpr size_t kHeader = 64;
+
+void put32(uint8_t *p, uint32_t v) {
+    for (int b = 0; b < 4; b++) p[b] = (uint8_t)(v >> (8 * b));
+}
+uint32_t get32(const uint8_t *p) {
+    uint32_t v = 0;
+    for (int b = 0; b < 4; b++) v |= (uint32_t)p[b] << (8 * b);
+    return v;
+}
+
+// FNV-1a, 32 bits (Fowler, Noll, Vo): offset basis 2166136261, prime 16777619
+uint32_t fnv1a(const uint8_t *p, size_t n) {
+    uint32_t h = 2166136261u;
+    for (size_t i = 0; i < n; i++) h = (h ^ p[i]) * 16777619u;
+    return h;
+}
+
+// payload words and the prime index of word w (limb-major within each poly)
+bool message_shape(const bcn_ctx *c, int kind, int level, int count, size_t *words, int *limbs) {
+    if (kind == BCN_MSG_CIPHERTEXTS || kind == BCN_MSG_PLAINTEXTS) {
+        if (level < 1 || level > c->L || count < 0) return false;
+        *limbs = level;
+        *words = (size_t)count * (kind == BCN_MSG_CIPHERTEXTS ? 2 : 1) * level * c->N;
+        return true;
+    }
+    if (kind == BCN_MSG_RELIN_KEY || kind == BCN_MSG_GALOIS_KEY) {
+        if (level != 0 || count != 1) return false;
+        *limbs = c->L + c->K;
+        *words = bcn_evk_words(c);
+        return true;
+    }
+    return false;
+}
+}  // namespace
+
+extern "C" size_t bcn_message_bytes(const bcn_ctx *c, int kind, int level, int count) {
+    size_t words = 0;
+    int limbs = 0;
+    if (!c || !message_shape(c, kind, level, count, &words, &limbs)) return 0;
+    return kHeader + 4 * words;
+}
+
+extern "C" bcn_status bcn_serialize(const bcn_ctx *c, int kind, int level, int count, uint32_t galois,
+                                    const uint32_t *words, uint8_t *out, size_t out_bytes) {
+    if (!c || !out) return fail(BCN_E_INVAL, "bcn_serialize: null argument");
+    size_t n = 0;
+    int limbs = 0;
+    if (!message_shape(c, kind, level, count, &n, &limbs)) return fail(BCN_E_INVAL, "bcn_serialize: bad kind, level or count");
+    if ((kind == BCN_MSG_GALOIS_KEY) != (galois != 0)) return fail(BCN_E_INVAL, "bcn_serialize: a Galois element belongs to Galois keys only");
+    if (out_bytes < kHeader + 4 * n) return fail(BCN_E_BUDGET, "bcn_serialize: output buffer too small");
+    if (n && !words) return fail(BCN_E_INVAL, "bcn_serialize: null payload");
+    std::fill(out, out + kHeader, (uint8_t)0);
+    put32(out + 0, kMagic);
+    put32(out + 4, (uint32_t)kind);
+    put32(out + 8, c->params.log_n);
+    put32(out + 12, c->params.n_data);
+    put32(out + 16, c->params.n_special);
+    put32(out + 20, c->params.alpha);
+    put32(out + 24, (uint32_t)level);
+    put32(out + 28, (uint32_t)count);
+    put32(out + 32, galois);
+    put32(out + 36, (uint32_t)(n & 0xFFFFFFFFu));
+    put32(out + 40, (uint32_t)((uint64_t)n >> 32));
+    for (size_t w = 0; w < n; w++) put32(out + kHeader + 4 * w, words[w]);
+    put32(out + 44, fnv1a(out + kHeader, 4 * n));
+    return BCN_OK;
+}
+
+extern "C" bcn_status bcn_deserialize_header(const bcn_ctx *c, const uint8_t *in, size_t in_bytes, int *kind,
+                                             int *level, int *count, uint32_t *galois) {
+    if (!c || !in || !kind || !level || !count || !galois) return fail(BCN_E_INVAL, "bcn_deserialize_header: null argument");
+    if (in_bytes < kHeader || get32(in) != kMagic) return fail(BCN_E_INVAL, "bcn_deserialize_header: not a message");
+    for (size_t b = 48; b < kHeader; b++)
+        if (in[b]) return fail(BCN_E_INVAL, "bcn_deserialize_header: reserved bytes are not zero");
+    if (get32(in + 8) != c->params.log_n || get32(in + 12) != c->params.n_data ||
+        get32(in + 16) != c->params.n_special || get32(in + 20) != c->params.alpha)
+        return fail(BCN_E_INVAL, "bcn_deserialize_header: the message belongs to other parameters");
+    const int k = (int)get32(in + 4), lv = (int)get32(in + 24), ct = (int)get32(in + 28);
+    const uint32_t g = get32(in + 32);
+    size_t n = 0;
+    int limbs = 0;
+    if (!message_shape(c, k, lv, ct, &n, &limbs)) return fail(BCN_E_INVAL, "bcn_deserialize_header: bad kind, level or count");
+    if ((k == BCN_MSG_GALOIS_KEY) != (g != 0) || (g != 0 && (g % 2 == 0 || g >= 2 * (uint32_t)c->N)))
+        return fail(BCN_E_INVAL, "bcn_deserialize_header: bad Galois element");
+    const uint64_t nw = (uint64_t)get32(in + 36) | ((uint64_t)get32(in + 40) << 32);
+    if (nw != n) return fail(BCN_E_INVAL, "bcn_deserialize_header: payload size does not match the shape");
+    if (in_bytes < kHeader + 4 * n) return fail(BCN_E_INVAL, "bcn_deserialize_header: truncated payload");
+    *kind = k;
+    *level = lv;
+    *count = ct;
+    *galois = g;
+    return BCN_OK;
+}
+
+extern "C" bcn_status bcn_deserialize(const bcn_ctx *c, const uint8_t *in, size_t in_bytes, uint32_t *words,
+                                      size_t out_words) {
+    int kind = 0, level = 0, count = 0;
+    uint32_t g = 0;
+    const bcn_status st = bcn_deserialize_header(c, in, in_bytes, &kind, &level, &count, &g);
+    if (st != BCN_OK) return st;
+    size_t n = 0;
+    int limbs = 0;
+    message_shape(c, kind, level, count, &n, &limbs);
+    if (out_words < n || (n && !words)) return fail(BCN_E_BUDGET, "bcn_deserialize: output buffer too small");
+    if (fnv1a(in + kHeader, 4 * n) != get32(in + 44)) return fail(BCN_E_INVAL, "bcn_deserialize: checksum mismatch");
+    const size_t N = (size_t)c->N;
+    for (size_t w = 0; w < n; w++) {
+        const uint32_t v = get32(in + kHeader + 4 * w);
+        const size_t limb = (w / N) % (size_t)limbs;
+        if (v >= c->primes[limb]) return fail(BCN_E_INVAL, "bcn_deserialize: a residue is not below its prime");
+        words[w] = v;
+    }
+    return BCN_OK;
+}
