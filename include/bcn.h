@@ -94,8 +94,23 @@ size_t bcn_evk_words(const bcn_ctx *ctx);
 /* Reads and clears the context's device status word (synchronous): 0 when no
  * kernel gave up a bounded wait since the last call; otherwise a bit set by
  * the kernel that gave up (1: the tensor-core MAC's wait for its MMAs), whose
- * outputs are then unspecified. */
+ * outputs are then unspecified (bits 2 and 4: see the debug checks). */
 bcn_status bcn_device_status(const bcn_ctx *ctx, uint32_t *status);
+/* Debug checks (no compute-sanitizer here; the checks take its place for the
+ * inputs): with them on -- bcn_ctx_set_debug(ctx, 1), or every context of a
+ * library built with -DBCN_DEBUG -- bcn_eval, bcn_eval_stacked, bcn_op_mac,
+ * bcn_op_square_relin_rescale, bcn_op_rotate, bcn_op_rotate_many and the
+ * diagonal-method layers first run device-side checks on their inputs: every
+ * residue of the input ciphertexts and feature plaintexts below its prime, and
+ * (bcn_eval) every MAC tap index inside [-1, n_in) and output index inside
+ * [0, n_out).  A failed check sets a bit of the status word (2: a residue not
+ * below its prime; 4: an index out of range) instead of trapping; the host
+ * waits for the checks, clears those bits and returns BCN_E_INVAL without
+ * launching the operation.  The checks read every input once more and
+ * synchronise the stream, and they are skipped on a stream being captured
+ * into a graph.  Off by default. */
+bcn_status bcn_ctx_set_debug(bcn_ctx *ctx, int on);
+bcn_status bcn_ctx_get_debug(const bcn_ctx *ctx, int *on);
 
 /* ------------------------------------------------------------ client side */
 /* Secret key (uniform ternary) and relinearisation key for hybrid key

@@ -66,6 +66,8 @@ _SIGS = {
     "bcn_ctx_primes": (_I, [_P, _P]),
     "bcn_evk_words": (_SZ, [_P]),
     "bcn_device_status": (_I, [_P, _P]),
+    "bcn_ctx_set_debug": (_I, [_P, _I]),
+    "bcn_ctx_get_debug": (_I, [_P, ctypes.POINTER(_I)]),
     "bcn_keygen": (_I, [_P, _U64, _P, _P]),
     "bcn_quantize": (_I, [_P, _SZ, _P, ctypes.POINTER(_D)]),
     "bcn_encode": (_I, [_P, _P, _I, _I, _I, _D, _P]),
@@ -248,6 +250,16 @@ class Context:
 
     def evk_shape(self):
         return (self.dnum, 2, self.L + self.K, self.N)
+
+    def set_debug(self, on: bool = True):
+        """bcn_ctx_set_debug: device-side checks of every call's inputs (residues
+        below their primes, table indices in range) before it launches."""
+        _check(lib().bcn_ctx_set_debug(self._h, int(on)), "bcn_ctx_set_debug")
+
+    def debug(self) -> bool:
+        v = _I()
+        _check(lib().bcn_ctx_get_debug(self._h, ctypes.byref(v)), "bcn_ctx_get_debug")
+        return bool(v.value)
 
     def device_status(self) -> int:
         """Reads and clears the device status word (0: no bounded wait gave up)."""

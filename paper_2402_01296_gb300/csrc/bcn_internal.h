@@ -97,6 +97,11 @@ struct bcn_ctx {
     bcn_params params;
     int N, logN, L, K, alpha, dnum;
     int device;  // -1: host only
+#ifdef BCN_DEBUG
+    bool debug = true;                 // device-side input checks before each call (bcn_ctx_set_debug)
+#else
+    bool debug = false;
+#endif
     std::vector<uint64_t> primes;      // L data then K special
     // NTT twiddles per prime, [2N] interleaved (value, Shoup companion):
     // fwd[k] = psi^{brv(k)}, inv[k] = psi^{-brv(k)}; used by the host (client)

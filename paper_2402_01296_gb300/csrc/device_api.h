@@ -157,6 +157,11 @@ bcn_status launch_mac_tc(const bcn_ctx *c, const MacTcPlan &p, int level, int K,
                          const int32_t *gidx, const int32_t *gout, const uint32_t *in, const uint32_t *pt,
                          uint32_t *out, cudaStream_t st, int g_base, bool store_natural, int t_lo, int n_tl);
 bcn_status cores_setup_all();
+// with the context's debug checks on (and the stream not capturing): every
+// residue of polys [n_poly][level][N] below its prime, checked on the device,
+// else BCN_E_INVAL naming `who`; a no-op otherwise
+bcn_status debug_check_input(const bcn_ctx *c, const uint32_t *a, size_t n_poly, int level, cudaStream_t st,
+                             const char *who);
 // rescale of C coefficient-form ciphertexts: in [C][2][n][N] -> out [C][2][n-1][N]
 bcn_status launch_rescale(const bcn_ctx *c, int n, const uint32_t *in, uint32_t *out, int C, cudaStream_t st);
 

@@ -819,6 +819,95 @@ bcn_status bcn_model_set_mac_impl(bcn_model *m, int impl) {
     return BCN_OK;
 }
 
+// ------------------------------------------------------------ debug checks
+// With a context's debug checks on (bcn_ctx_set_debug, or every context of a
+// library built with -DBCN_DEBUG) the entry points check their inputs on the
+// device before launching anything: a failed check sets a bit of the status
+// word (never a trap), the host waits for the checks and refuses the call.
+namespace {
+constexpr uint32_t kStatusResidue = 2u, kStatusIndex = 4u;
+
+// every word of polys [..][level][N] (limb i mod q_i) below its prime
+__global__ void __launch_bounds__(256) k_check_residues(const uint32_t *__restrict__ a, size_t n_words, int level,
+                                                        int N, const PrimeConst *__restrict__ pc,
+                                                        uint32_t *__restrict__ status) {
+    for (size_t w = (size_t)blockIdx.x * blockDim.x + threadIdx.x; w < n_words; w += (size_t)gridDim.x * blockDim.x)
+        if (__ldg(a + w) >= pc[(w / N) % level].q) {
+            atomicOr(status, kStatusResidue);
+            return;
+        }
+}
+
+// every entry of a table inside [lo, hi)
+__global__ void __launch_bounds__(256) k_check_index(const int32_t *__restrict__ v, size_t n, int lo, int hi,
+                                                     uint32_t *__restrict__ status) {
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+        if (__ldg(v + k) < lo || __ldg(v + k) >= hi) {
+            atomicOr(status, kStatusIndex);
+            return;
+        }
+}
+
+unsigned check_grid(size_t n) { return (unsigned)std::min<size_t>((n + 255) / 256, 4096); }
+
+// checks run only outside stream capture (a captured graph replays without them)
+bool debug_on(const bcn_ctx *c, cudaStream_t st) {
+    if (!c->debug) return false;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone;
+}
+
+bcn_status debug_residues(const bcn_ctx *c, const uint32_t *a, size_t n_poly, int level, cudaStream_t st) {
+    const size_t n = n_poly * (size_t)level * c->N;
+    if (n == 0 || !a) return BCN_OK;
+    k_check_residues<<<check_grid(n), 256, 0, st>>>(a, n, level, c->N, c->d_pc, c->d_status);
+    return check_launch("k_check_residues");
+}
+
+bcn_status debug_index(const bcn_ctx *c, const int32_t *v, size_t n, int lo, int hi, cudaStream_t st) {
+    if (n == 0 || !v) return BCN_OK;
+    k_check_index<<<check_grid(n), 256, 0, st>>>(v, n, lo, hi, c->d_status);
+    return check_launch("k_check_index");
+}
+
+// wait for the checks; a set bit refuses the call (and is cleared)
+bcn_status debug_verdict(const bcn_ctx *c, cudaStream_t st, const char *who) {
+    uint32_t s = 0;
+    if (cudaStreamSynchronize(st) != cudaSuccess || cudaMemcpy(&s, c->d_status, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(BCN_E_CUDA, std::string(who) + ": reading the debug checks failed");
+    const uint32_t bad = s & (kStatusResidue | kStatusIndex);
+    if (!bad) return BCN_OK;
+    const uint32_t keep = s & ~bad;
+    if (cudaMemcpy(c->d_status, &keep, 4, cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(BCN_E_CUDA, std::string(who) + ": clearing the debug bits failed");
+    return fail(BCN_E_INVAL, std::string(who) + (bad & kStatusResidue ? ": an input residue is not below its prime"
+                                                                       : ": a table index is out of range"));
+}
+}  // namespace
+
+extern "C++" {
+namespace bcn {
+bcn_status debug_check_input(const bcn_ctx *c, const uint32_t *a, size_t n_poly, int level, cudaStream_t st,
+                             const char *who) {
+    if (!debug_on(c, st)) return BCN_OK;
+    BCN_TRY(debug_residues(c, a, n_poly, level, st));
+    return debug_verdict(c, st, who);
+}
+}  // namespace bcn
+}
+
+bcn_status bcn_ctx_set_debug(bcn_ctx *c, int on) {
+    if (!c) return fail(BCN_E_INVAL, "bcn_ctx_set_debug: null context");
+    c->debug = on != 0;
+    return BCN_OK;
+}
+
+bcn_status bcn_ctx_get_debug(const bcn_ctx *c, int *on) {
+    if (!c || !on) return fail(BCN_E_INVAL, "bcn_ctx_get_debug: null argument");
+    *on = c->debug ? 1 : 0;
+    return BCN_OK;
+}
+
 bcn_status bcn_device_status(const bcn_ctx *c, uint32_t *status) {
     if (!c || !status) return fail(BCN_E_INVAL, "bcn_device_status: null argument");
     BCN_TRY(check_device(c));
@@ -995,6 +1084,17 @@ static bcn_status eval_impl(const bcn_model *m, const uint32_t *evk, const uint3
             pt_ntt[l] = reinterpret_cast<uint32_t *>(PT);
             PT += align_up((size_t)p.n_out * p.level * N * 4);
         }
+    }
+    if (layer_ready == nullptr && debug_on(c, st)) {
+        const bcn_layer_plan &p0 = m->layers.front();
+        BCN_TRY(debug_residues(c, cts, 2 * (size_t)p0.n_in, p0.level, st));
+        int a = 0;
+        for (const bcn_layer_plan &p : m->layers) {
+            if (p.add) BCN_TRY(debug_residues(c, pts[a++], (size_t)p.n_out, p.level, st));
+            BCN_TRY(debug_index(c, p.d_gidx, (size_t)p.n_groups * p.K, -1, p.n_in, st));
+            BCN_TRY(debug_index(c, p.d_gout, (size_t)p.n_groups * p.n_go, 0, p.n_out, st));
+        }
+        BCN_TRY(debug_verdict(c, st, "bcn_eval"));
     }
     cudaStream_t aux = nullptr;
     bool any_pt_ntt = false;
@@ -1328,6 +1428,11 @@ bcn_status bcn_op_mac(const bcn_ctx *c, int level, int n_in, int n_out, int K, c
         for (int32_t v : h)
             if (v < -1 || v >= n_in) return fail(BCN_E_INVAL, "bcn_op_mac: idx entry outside [-1, n_in)");
     }
+    if (debug_on(c, (cudaStream_t)stream)) {
+        BCN_TRY(debug_residues(c, in, 2 * (size_t)n_in, level, (cudaStream_t)stream));
+        BCN_TRY(debug_residues(c, pt, (size_t)n_out, level, (cudaStream_t)stream));
+        BCN_TRY(debug_verdict(c, (cudaStream_t)stream, "bcn_op_mac"));
+    }
     // every output is a group of one with its own taps
     return launch_mac(c, level, K, n_out, 1, idx, w, nullptr, in, pt, out, (cudaStream_t)stream);
 }
@@ -1369,6 +1474,7 @@ bcn_status bcn_op_square_relin_rescale(const bcn_ctx *c, int level, const uint32
     if (!in || !out || !evk || !aligned16(in) || !aligned16(out) || !aligned16(evk))
         return fail(BCN_E_INVAL, "bcn_op_square_relin_rescale: buffers");
     cudaStream_t st = (cudaStream_t)stream;
+    BCN_TRY(debug_check_input(c, in, 2 * (size_t)n_ct, level, st, "bcn_op_square_relin_rescale"));
     const int n = level, chunk = default_chunk(c, level, n_ct);
     const size_t N = c->N;
     ChunkBufs b = carve_chunk(c, n, chunk, reinterpret_cast<char *>(ws));

@@ -243,6 +243,7 @@ extern "C" bcn_status bcn_op_rotate_many(const bcn_ctx *c, int level, const uint
     const CoreFns *f = core_fns(c->logN);
     if (!f) return fail(BCN_E_INVAL, "unsupported ring degree");
     cudaStream_t st = (cudaStream_t)stream;
+    BCN_TRY(debug_check_input(c, in, 2 * (size_t)n_ct, level, st, "bcn_op_rotate_many"));
     const size_t nb = n + c->K, dnum = (n + c->alpha - 1) / c->alpha;
     const int chunk = std::min(n_ct, kHoistChunk);
     uint32_t *U = reinterpret_cast<uint32_t *>(ws);
@@ -329,6 +330,8 @@ static bcn_status fc_diag_impl(const bcn_ctx *c, const char *who, int level, con
     uint32_t *R = reinterpret_cast<uint32_t *>(w + rot_bytes);
     uint32_t *acc = R + (size_t)n_rot * ct_words;
     cudaStream_t st = (cudaStream_t)stream;
+    BCN_TRY(debug_check_input(c, in, 2 * (size_t)n_groups * n_in, level, st, who));
+    if (pt) BCN_TRY(debug_check_input(c, pt, (size_t)n_groups, level - 1, st, who));
     const dim3 grid((unsigned)((N / 4 + 255) / 256), (unsigned)n, 2);
     for (int g = 0; g < n_groups; g++) {
         for (int k = 0; k < n_in; k++) {
@@ -388,6 +391,7 @@ extern "C" bcn_status bcn_op_rotate(const bcn_ctx *c, int level, const uint32_t 
     if (!f) return fail(BCN_E_INVAL, "unsupported ring degree");
     const uint64_t g = bcn_galois_elt(c, steps), ginv = galois_inverse(g, N);
     cudaStream_t st = (cudaStream_t)stream;
+    BCN_TRY(debug_check_input(c, in, 2 * (size_t)n_ct, level, st, "bcn_op_rotate"));
     const int n = level, chunk = ks_default_chunk(c, level, n_ct);
     uint32_t *d, *d2n, *acc;
     ks_carve(c, n, chunk, reinterpret_cast<char *>(ws), &d, &d2n, &acc);
