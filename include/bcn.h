@@ -94,7 +94,8 @@ size_t bcn_evk_words(const bcn_ctx *ctx);
 /* Reads and clears the context's device status word (synchronous): 0 when no
  * kernel gave up a bounded wait since the last call; otherwise a bit set by
  * the kernel that gave up (1: the tensor-core MAC's wait for its MMAs), whose
- * outputs are then unspecified (bits 2 and 4: see the debug checks). */
+ * outputs are then unspecified (bits 2 and 4: see the debug checks; bit 8: see
+ * the seeded ciphertexts). */
 bcn_status bcn_device_status(const bcn_ctx *ctx, uint32_t *status);
 /* Debug checks (no compute-sanitizer here; the checks take its place for the
  * inputs): with them on -- bcn_ctx_set_debug(ctx, 1), or every context of a
@@ -157,6 +158,24 @@ bcn_status bcn_encrypt(const bcn_ctx *ctx, const int8_t *sk, const uint32_t *pts
  * cts_out: [C*h*w][2][L][N], host memory. */
 bcn_status bcn_encrypt_segment(const bcn_ctx *ctx, const int8_t *sk, const uint8_t *images, int B, int H, int W,
                                int C, const int seg[4], double scale, uint64_t seed, uint32_t *cts_out);
+
+/* Seeded ciphertexts (Sec. 2: the client uploads every encrypted segment; c1 = a
+ * is uniform noise drawn from the seed, so c0 and the seed carry the whole
+ * ciphertext in half the bytes).  bcn_encrypt_seeded / bcn_encrypt_segment_seeded
+ * write c0 alone, [n_ct][level][N] (host), identical to the c0 of bcn_encrypt /
+ * bcn_encrypt_segment with the same arguments.  bcn_expand_seeded (device):
+ * c0_dev [n_ct][level][N] -> cts_dev [n_ct][2][level][N], c1 of ciphertext k
+ * drawn from the stream of `seed` with index (ct_base + k) * 256 + limb exactly
+ * as bcn_encrypt draws it (SplitMix64, rejection below floor(2^32/q) q); the
+ * buffers must not overlap.  Asynchronous on `cuda_stream`; a limb that would
+ * need more than N + 16384 draws (never seen: about one draw in 30000 is
+ * rejected) sets bit 8 of the status word. */
+bcn_status bcn_encrypt_seeded(const bcn_ctx *ctx, const int8_t *sk, const uint32_t *pts, int n_ct, int level,
+                              uint64_t seed, uint32_t *c0_out);
+bcn_status bcn_encrypt_segment_seeded(const bcn_ctx *ctx, const int8_t *sk, const uint8_t *images, int B, int H,
+                                      int W, int C, const int seg[4], double scale, uint64_t seed, uint32_t *c0_out);
+bcn_status bcn_expand_seeded(const bcn_ctx *ctx, const uint32_t *c0_dev, int n_ct, int level, uint64_t seed,
+                             int ct_base, uint32_t *cts_dev, void *cuda_stream);
 
 /* The client's last step (Sec. 2 threat model: only the client can decrypt
  * the inference result; App. A: the decryption function D, and the N/2 slots
@@ -371,6 +390,15 @@ bcn_status bcn_eval_host(const bcn_model *m, const uint32_t *evk_eval_dev, const
 bcn_status bcn_eval_host_async(const bcn_model *m, const uint32_t *evk_eval_dev, const uint32_t *cts_host,
                                const uint32_t *const *pts_host, uint32_t *out_host, void *workspace_dev,
                                size_t workspace_bytes, void *cuda_stream);
+/* bcn_eval_host_async from seeded ciphertexts: c0_host [n_in][L][N] (from
+ * bcn_encrypt_segment_seeded with `seed`) is copied into the staging area's
+ * first halves and c1 drawn there on the device, so half the ciphertext bytes
+ * cross to the device.  Results equal bcn_eval_host_async's on the full
+ * ciphertexts.  Single-request models only (a stacked model's requests have
+ * seeds of their own): BCN_E_INVAL otherwise. */
+bcn_status bcn_eval_host_seeded_async(const bcn_model *m, const uint32_t *evk_eval_dev, const uint32_t *c0_host,
+                                      uint64_t seed, const uint32_t *const *pts_host, uint32_t *out_host,
+                                      void *workspace_dev, size_t workspace_bytes, void *cuda_stream);
 
 /* ------------------------------------------------ batched evaluation (device) */
 /* Many evaluations of different models (ring degrees, segment sizes) replayed

@@ -73,6 +73,9 @@ _SIGS = {
     "bcn_encode": (_I, [_P, _P, _I, _I, _I, _D, _P]),
     "bcn_encrypt": (_I, [_P, _P, _P, _I, _I, _U64, _P]),
     "bcn_encrypt_segment": (_I, [_P, _P, _P, _I, _I, _I, _I, _P, _D, _U64, _P]),
+    "bcn_encrypt_seeded": (_I, [_P, _P, _P, _I, _I, _U64, _P]),
+    "bcn_encrypt_segment_seeded": (_I, [_P, _P, _P, _I, _I, _I, _I, _P, _D, _U64, _P]),
+    "bcn_expand_seeded": (_I, [_P, _P, _I, _I, _U64, _I, _P, _P]),
     "bcn_decrypt_decode": (_I, [_P, _P, _P, _I, _I, _D, _I, _P]),
     "bcn_message_bytes": (_SZ, [_P, _I, _I, _I]),
     "bcn_serialize": (_I, [_P, _I, _I, _I, ctypes.c_uint32, _P, _P, _SZ]),
@@ -100,6 +103,7 @@ _SIGS = {
     "bcn_eval_host_workspace_bytes": (_I, [_P, ctypes.POINTER(_SZ)]),
     "bcn_eval_host": (_I, [_P, _P, _P, _P, _P, _P, _SZ, _P]),
     "bcn_eval_host_async": (_I, [_P, _P, _P, _P, _P, _P, _SZ, _P]),
+    "bcn_eval_host_seeded_async": (_I, [_P, _P, _P, _U64, _P, _P, _P, _SZ, _P]),
     "bcn_batch_plan": (_I, [_P, _I, _I, ctypes.POINTER(_SZ)]),
     "bcn_batch_create": (_I, [_P, _I, _I, _P, _SZ, ctypes.POINTER(_P)]),
     "bcn_batch_launch": (_I, [_P, _P]),
@@ -310,6 +314,34 @@ class Context:
                                          _np_ptr(images, np.uint8), B, H, W, C, _np_ptr(seg_a, np.int32), scale,
                                          seed, _np_ptr(out, np.uint32)), "bcn_encrypt_segment")
         return out
+
+    def encrypt_seeded(self, sk: np.ndarray, pts: np.ndarray, level: int, seed: int) -> np.ndarray:
+        """bcn_encrypt_seeded: c0 alone [n][level][N] (c1 follows from the seed)."""
+        pts = np.ascontiguousarray(pts, dtype=np.uint32)
+        n = pts.shape[0]
+        assert pts.shape == (n, level, self.N)
+        out = np.zeros((n, level, self.N), dtype=np.uint32)
+        _check(lib().bcn_encrypt_seeded(self._h, _np_ptr(np.ascontiguousarray(sk), np.int8), _np_ptr(pts, np.uint32),
+                                        n, level, seed, _np_ptr(out, np.uint32)), "bcn_encrypt_seeded")
+        return out
+
+    def encrypt_segment_seeded(self, sk, images: np.ndarray, seg, scale: float, seed: int) -> np.ndarray:
+        """bcn_encrypt_segment_seeded: c0 alone [C*h*w][L][N]."""
+        images = np.ascontiguousarray(images, dtype=np.uint8)
+        B, H, W, C = images.shape
+        seg_a = np.ascontiguousarray(seg, dtype=np.int32)
+        n = C * int(seg[2]) * int(seg[3])
+        out = np.zeros((n, self.L, self.N), dtype=np.uint32)
+        _check(lib().bcn_encrypt_segment_seeded(self._h, _np_ptr(np.ascontiguousarray(sk), np.int8),
+                                                _np_ptr(images, np.uint8), B, H, W, C, _np_ptr(seg_a, np.int32), scale,
+                                                seed, _np_ptr(out, np.uint32)), "bcn_encrypt_segment_seeded")
+        return out
+
+    def expand_seeded(self, c0_dev, n_ct: int, level: int, seed: int, out_dev, ct_base: int = 0, stream=None):
+        """bcn_expand_seeded: c0 [n][level][N] (device) -> full ciphertexts [n][2][level][N]."""
+        _check(lib().bcn_expand_seeded(self._h, _dev_ptr(c0_dev, n_ct * level * self.N), n_ct, level, seed, ct_base,
+                                       _dev_ptr(out_dev, 2 * n_ct * level * self.N), _stream(stream)),
+               "bcn_expand_seeded")
 
     def decrypt_decode(self, sk, cts: np.ndarray, level: int, scale: float, B: int) -> np.ndarray:
         cts = np.ascontiguousarray(cts, dtype=np.uint32)
@@ -658,6 +690,19 @@ class Model:
                                          ctypes.cast(arr, _P), out_host.ctypes.data, workspace.data_ptr(),
                                          workspace.numel() * workspace.element_size(), _stream(stream)),
                "bcn_eval_host_async")
+
+    def eval_host_seeded_async(self, evk_eval, c0_host: np.ndarray, seed: int, pts_host: list, out_host: np.ndarray,
+                               workspace, stream=None):
+        """bcn_eval_host_seeded_async: eval_host_async from c0 alone [n_in][L][N]
+        and the encryption seed (c1 drawn on the device)."""
+        for a in [c0_host, out_host, *pts_host]:
+            assert a.dtype == np.uint32 and a.flags["C_CONTIGUOUS"]
+        assert out_host.shape == self.out_shape()
+        arr = (_P * max(1, len(pts_host)))(*[p.ctypes.data for p in pts_host])
+        _check(lib().bcn_eval_host_seeded_async(self._h, _dev_ptr(evk_eval, self.ctx.evk_words()), c0_host.ctypes.data,
+                                                seed, ctypes.cast(arr, _P), out_host.ctypes.data, workspace.data_ptr(),
+                                                workspace.numel() * workspace.element_size(), _stream(stream)),
+               "bcn_eval_host_seeded_async")
 
 
 class Batch:

@@ -325,8 +325,10 @@ bcn_status bcn_encode(const bcn_ctx *c, const double *values, int n_vec, int B, 
     return BCN_OK;
 }
 
-bcn_status bcn_encrypt(const bcn_ctx *c, const int8_t *sk, const uint32_t *pts, int n_ct, int level,
-                       uint64_t seed, uint32_t *cts) {
+// secret-key encryption; with c0_only the output is [n_ct][level][N] (c0 alone,
+// c1 being the uniform stream the seed defines)
+static bcn_status encrypt_impl(const bcn_ctx *c, const int8_t *sk, const uint32_t *pts, int n_ct, int level,
+                               uint64_t seed, uint32_t *cts, bool c0_only) {
     if (!c || !sk || ((!pts || !cts) && n_ct)) return fail(BCN_E_INVAL, "bcn_encrypt: null argument");
     if (level < 1 || level > c->L || n_ct < 0) return fail(BCN_E_INVAL, "bcn_encrypt: bad level or count");
     const int N = c->N;
@@ -344,10 +346,10 @@ bcn_status bcn_encrypt(const bcn_ctx *c, const int8_t *sk, const uint32_t *pts, 
         for (int i = 0; i < level; i++) {
             uint32_t q = (uint32_t)c->primes[i];
             Stream ra(seed, kTagEncA, (uint64_t)ci * 256 + (uint64_t)i);
-            uint32_t *c0 = cts + (((size_t)ci * 2 + 0) * level + i) * N;
-            uint32_t *c1 = cts + (((size_t)ci * 2 + 1) * level + i) * N;
+            uint32_t *c0 = c0_only ? cts + ((size_t)ci * level + i) * N : cts + (((size_t)ci * 2 + 0) * level + i) * N;
+            uint32_t *c1 = c0_only ? as.data() : cts + (((size_t)ci * 2 + 1) * level + i) * N;
             for (int k = 0; k < N; k++) c1[k] = ra.uniform(q);
-            std::copy(c1, c1 + N, as.begin());
+            if (!c0_only) std::copy(c1, c1 + N, as.begin());
             ntt_fwd(c, i, as.data());
             for (int k = 0; k < N; k++) as[k] = mulq(as[k], S[i][k], q);
             ntt_inv(c, i, as.data());
@@ -358,8 +360,33 @@ bcn_status bcn_encrypt(const bcn_ctx *c, const int8_t *sk, const uint32_t *pts, 
     return BCN_OK;
 }
 
+bcn_status bcn_encrypt(const bcn_ctx *c, const int8_t *sk, const uint32_t *pts, int n_ct, int level,
+                       uint64_t seed, uint32_t *cts) {
+    return encrypt_impl(c, sk, pts, n_ct, level, seed, cts, false);
+}
+
+bcn_status bcn_encrypt_seeded(const bcn_ctx *c, const int8_t *sk, const uint32_t *pts, int n_ct, int level,
+                              uint64_t seed, uint32_t *c0) {
+    return encrypt_impl(c, sk, pts, n_ct, level, seed, c0, true);
+}
+
+static bcn_status encrypt_segment_impl(const bcn_ctx *c, const int8_t *sk, const uint8_t *images, int B, int H,
+                                       int W, int C, const int seg[4], double scale, uint64_t seed, uint32_t *cts,
+                                       bool c0_only);
+
 bcn_status bcn_encrypt_segment(const bcn_ctx *c, const int8_t *sk, const uint8_t *images, int B, int H, int W,
                                int C, const int seg[4], double scale, uint64_t seed, uint32_t *cts) {
+    return encrypt_segment_impl(c, sk, images, B, H, W, C, seg, scale, seed, cts, false);
+}
+
+bcn_status bcn_encrypt_segment_seeded(const bcn_ctx *c, const int8_t *sk, const uint8_t *images, int B, int H,
+                                      int W, int C, const int seg[4], double scale, uint64_t seed, uint32_t *c0) {
+    return encrypt_segment_impl(c, sk, images, B, H, W, C, seg, scale, seed, c0, true);
+}
+
+static bcn_status encrypt_segment_impl(const bcn_ctx *c, const int8_t *sk, const uint8_t *images, int B, int H,
+                                       int W, int C, const int seg[4], double scale, uint64_t seed, uint32_t *cts,
+                                       bool c0_only) {
     if (!c || !sk || !images || !seg || !cts) return fail(BCN_E_INVAL, "bcn_encrypt_segment: null argument");
     int y0 = seg[0], x0 = seg[1], h = seg[2], w = seg[3];
     if (B < 1 || B > c->N / 2 || y0 < 0 || x0 < 0 || h < 1 || w < 1 || y0 + h > H || x0 + w > W || C < 1)
@@ -376,7 +403,7 @@ bcn_status bcn_encrypt_segment(const bcn_ctx *c, const int8_t *sk, const uint8_t
     std::vector<uint32_t> pts((size_t)n_ct * c->L * c->N);
     bcn_status st = bcn_encode(c, vals.data(), n_ct, B, c->L, scale, pts.data());
     if (st != BCN_OK) return st;
-    return bcn_encrypt(c, sk, pts.data(), n_ct, c->L, seed, cts);
+    return encrypt_impl(c, sk, pts.data(), n_ct, c->L, seed, cts, c0_only);
 }
 
 bcn_status bcn_decrypt_decode(const bcn_ctx *c, const int8_t *sk, const uint32_t *cts, int n_ct, int level,

@@ -157,6 +157,10 @@ bcn_status launch_mac_tc(const bcn_ctx *c, const MacTcPlan &p, int level, int K,
                          const int32_t *gidx, const int32_t *gout, const uint32_t *in, const uint32_t *pt,
                          uint32_t *out, cudaStream_t st, int g_base, bool store_natural, int t_lo, int n_tl);
 bcn_status cores_setup_all();
+// seeded ciphertexts: c1 of cts [n_ct][2][level][N] drawn from the seed (ciphertext
+// ct takes the stream of index ct_base + ct); c0 untouched
+bcn_status launch_expand_c1(const bcn_ctx *c, uint32_t *cts, int n_ct, int level, uint64_t seed, int ct_base,
+                            cudaStream_t st);
 // with the context's debug checks on (and the stream not capturing): every
 // residue of polys [n_poly][level][N] below its prime, checked on the device,
 // else BCN_E_INVAL naming `who`; a no-op otherwise

@@ -1273,10 +1273,29 @@ bcn_status bcn_eval_host(const bcn_model *m, const uint32_t *evk, const uint32_t
     return BCN_OK;
 }
 
+// with `seeded`, cts_h holds c0 alone ([n_in][L][N]) and c1 is drawn on the
+// device from the seed
+static bcn_status eval_host_async_impl(const bcn_model *m, const uint32_t *evk, const uint32_t *cts_h,
+                                       const uint32_t *const *pts_h, uint32_t *out_h, void *ws, size_t ws_bytes,
+                                       void *stream, bool seeded, uint64_t seed);
+
 bcn_status bcn_eval_host_async(const bcn_model *m, const uint32_t *evk, const uint32_t *cts_h,
                                const uint32_t *const *pts_h, uint32_t *out_h, void *ws, size_t ws_bytes,
                                void *stream) {
+    return eval_host_async_impl(m, evk, cts_h, pts_h, out_h, ws, ws_bytes, stream, false, 0);
+}
+
+bcn_status bcn_eval_host_seeded_async(const bcn_model *m, const uint32_t *evk, const uint32_t *c0_h, uint64_t seed,
+                                      const uint32_t *const *pts_h, uint32_t *out_h, void *ws, size_t ws_bytes,
+                                      void *stream) {
+    return eval_host_async_impl(m, evk, c0_h, pts_h, out_h, ws, ws_bytes, stream, true, seed);
+}
+
+static bcn_status eval_host_async_impl(const bcn_model *m, const uint32_t *evk, const uint32_t *cts_h,
+                                       const uint32_t *const *pts_h, uint32_t *out_h, void *ws, size_t ws_bytes,
+                                       void *stream, bool seeded, uint64_t seed) {
     if (!m || !cts_h || !out_h) return fail(BCN_E_INVAL, "bcn_eval_host: null argument");
+    if (seeded && m->stack != 1) return fail(BCN_E_INVAL, "bcn_eval_host_seeded_async: single-request models only");
     const bcn_ctx *c = m->ctx;
     BCN_TRY(check_device(c));
     size_t need = 0, eval_need = 0;
@@ -1346,7 +1365,29 @@ bcn_status bcn_eval_host_async(const bcn_model *m, const uint32_t *evk, const ui
     uint32_t *cts_d = reinterpret_cast<uint32_t *>(p);
     p += align_up(cts_b);
     std::vector<std::vector<cudaEvent_t>> ready(m->layers.size());
-    if (!copy_in(cts_d, cts_h, cts_b, ready[0])) return cleanup(BCN_E_CUDA, "bcn_eval_host: input copy failed");
+    if (!seeded) {
+        if (!copy_in(cts_d, cts_h, cts_b, ready[0])) return cleanup(BCN_E_CUDA, "bcn_eval_host: input copy failed");
+    } else {
+        // c0 rows into their ciphertexts' first halves, then c1 drawn in place,
+        // kCopyLanes ranges of ciphertexts side by side
+        const int n_in = m->layers.front().n_in;
+        const size_t poly = (size_t)c->L * c->N;
+        const int per = (n_in + kCopyLanes - 1) / kCopyLanes;
+        for (int k = 0; k < kCopyLanes; k++) {
+            const int lo = k * per, hi = std::min(n_in, lo + per);
+            if (lo >= hi) break;
+            cudaStream_t cs = mm->copy_streams[k];
+            if (cudaMemcpy2DAsync(cts_d + (size_t)lo * 2 * poly, 2 * poly * 4, cts_h + (size_t)lo * poly, poly * 4,
+                                  poly * 4, (size_t)(hi - lo), cudaMemcpyHostToDevice, cs) != cudaSuccess)
+                return cleanup(BCN_E_CUDA, "bcn_eval_host: input copy failed");
+            const bcn_status es = launch_expand_c1(c, cts_d + (size_t)lo * 2 * poly, hi - lo, c->L, seed, lo, cs);
+            if (es != BCN_OK) return cleanup(es, bcn_last_error());
+            cudaEvent_t e;
+            if (!new_event(&e) || cudaEventRecord(e, cs) != cudaSuccess)
+                return cleanup(BCN_E_CUDA, "bcn_eval_host: event failed");
+            ready[0].push_back(e);
+        }
+    }
     std::vector<const uint32_t *> pts_d;
     for (size_t l = 0, a = 0; l < m->layers.size(); l++) {
         if (!m->layers[l].add) continue;

@@ -87,3 +87,15 @@ def test_rejections(ctx):
     sk, evk = ctx.keygen(3)
     with pytest.raises(bcn.BcnError):
         ctx.serialize(ctx.MSG_RELIN_KEY, evk, 0, galois=5)  # a Galois element on a relinearisation key
+
+
+def test_seeded_encryption_c0_equals_full(ctx):
+    """c0 of a seeded encryption is the c0 of the full encryption with the same
+    key, plaintexts and seed (the seed then stands for c1)."""
+    sk, _ = ctx.keygen(3)
+    pts = _cts(ctx, n=4, level=ctx.L)[:, 0].copy()
+    assert np.array_equal(ctx.encrypt_seeded(sk, pts, ctx.L, 11), ctx.encrypt(sk, pts, ctx.L, 11)[:, 0])
+    imgs = np.random.default_rng(2).integers(0, 256, (3, 8, 8, 2), dtype=np.uint8)
+    seg = (1, 2, 4, 5)
+    assert np.array_equal(ctx.encrypt_segment_seeded(sk, imgs, seg, 2.0**20, 12),
+                          ctx.encrypt_segment(sk, imgs, seg, 2.0**20, 12)[:, 0])
