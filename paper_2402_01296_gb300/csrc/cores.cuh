@@ -110,6 +110,20 @@ struct CoreOcc {
 // Register budget of the square kernel: 64 (two 512-thread blocks per SM at
 // N = 8192) measured faster than 128 with either input domain (coefficient
 // input: 0.173 against 0.194 ms per CryptoNets-scale evaluation)
+// the square kernel's first forward transform (c0), parked in the
+// thread-private shared area s1[u T + tid]: a call of its own, so that the
+// two transforms' register allocations do not overlap
+template <int LOGN, int R>
+__device__ __noinline__ void square_park_c0(const uint32_t *__restrict__ y0, uint32_t *sm, uint32_t *s1, int tid,
+                                            ModQ mq, const uint2 *__restrict__ tf) {
+    using C = NttCore<LOGN, R, true, kFmaSquare>;
+    uint32_t x[R];
+    C::load_natural(x, y0, tid);
+    C::forward(x, sm, tid, mq, tf);
+#pragma unroll
+    for (int u = 0; u < R; u++) s1[u * C::T + tid] = x[u];
+}
+
 template <int T, int REGS>
 struct SqnOcc {
     static constexpr int B = 65536 / (T * REGS);
@@ -199,10 +213,7 @@ __global__ void __launch_bounds__((1 << LOGN) / R, IN_NTT ? SqnOcc<(1 << LOGN) /
     } else {
         // c0 transformed and parked in a thread-private area (u*T + tid), then c1
         uint32_t *s1 = sm + C::SMEM_WORDS;
-        C::load_natural(x, y0, tid);
-        C::forward(x, sm, tid, mq, tf);
-#pragma unroll
-        for (int u = 0; u < R; u++) s1[u * T + tid] = x[u];
+        square_park_c0<LOGN, R>(y0, sm, s1, tid, mq, tf);
         C::load_natural(x, y1, tid);
         C::forward(x, sm, tid, mq, tf);
 #pragma unroll
