@@ -191,12 +191,14 @@ def alu_work(cfg):
     square of a ciphertext at n limbs: per limb 2 forward NTTs (only on
     coefficient-form input, the first square layer) and 1 inverse NTT (d2 for
     ModUp); per coefficient the 3 products c0^2, c0 c1, c1^2 and the N^{-1}
-    scaling of the inverse transform's input.  The square class also holds the
+    scaling of the inverse transform's input, and with digits of more than one
+    prime the ModUp's constant product of d2 (done there once for the key
+    switch's every target prime).  The square class also holds the
     domain changes: a forward NTT of every feature-plaintext limb that meets
     NTT-domain ciphertexts and the inverse NTT of the outputs.  Key switch of d2
     (hybrid, digits of at most alpha primes, n + K target primes): ModUp (one
-    constant product per digit residue, then alpha per coefficient and prime
-    outside the digit), a forward NTT of every digit in every target prime
+    constant product per digit residue -- in the square kernel when alpha > 1 --
+    then alpha per coefficient and prime outside the digit), a forward NTT of every digit in every target prime
     outside it (inside it, the tensor square's NTT form is reused), two products
     per digit and target prime with the key, then two inverse NTTs on each
     special prime and on the top data prime (with its 4 constant products
@@ -220,13 +222,16 @@ def alu_work(cfg):
         w["square"]["fwd"] += C * n * (0 if in_ntt else 2)
         w["square"]["inv"] += C * n
         w["square"]["mont"] += C * 3 * n
-        w["square"]["shoup"] += C * n
+        # with multi-prime digits the square kernel also multiplies d2 by each
+        # limb's ModUp factor Dhat^-1 (once, for every target prime of the key switch)
+        pre = a >= 2
+        w["square"]["shoup"] += C * n * (2 if pre else 1)
         digits = [min(a, n - j * a) for j in range(math.ceil(n / a))]
         nb = n + K
         w["keyswitch"]["fwd"] += C * sum(nb - d for d in digits)
         w["keyswitch"]["inv"] += C * 2 * (K + 1)
         w["keyswitch"]["mont"] += C * 2 * nb * len(digits)
-        w["keyswitch"]["shoup"] += C * (sum(digits) + sum(d * (nb - d) for d in digits) + 2 * (n - 1) + 4)
+        w["keyswitch"]["shoup"] += C * ((0 if pre else sum(digits)) + sum(d * (nb - d) for d in digits) + 2 * (n - 1) + 4)
         w["moddown_rescale"]["fwd"] += C * 2 * (n - 1)
         w["moddown_rescale"]["shoup"] += C * 2 * (n - 1) * (3 * K + 4)
         in_ntt = True

@@ -105,7 +105,9 @@ struct CoreOcc {
 // the NTT domain (D [C][3][n][N] slots 0 and 1, last-pass layout), d2 in
 // coefficient form (slot 2, the key switch's ModUp input: one inverse NTT)
 // and, with D2N != nullptr, d2 in the NTT domain too (D2N [C][n][N], which the
-// key switch reuses on the digit's own prime).  All outputs canonical.
+// key switch reuses on the digit's own prime).  With `pre` (per limb i, the
+// Shoup pair of Dhat_i^{-1} mod q_i of its digit) slot 2 holds d2 Dhat_i^{-1}
+// instead.  All outputs canonical.
 // grid (n, C).
 // Register budget of the square kernel: 64 (two 512-thread blocks per SM at
 // N = 8192) measured faster than 128 with either input domain (coefficient
@@ -133,7 +135,8 @@ template <int LOGN, int R, bool IN_NTT>
 __global__ void __launch_bounds__((1 << LOGN) / R, IN_NTT ? SqnOcc<(1 << LOGN) / R, 64>::MIN_BLOCKS
                                                           : SqnOcc<(1 << LOGN) / R, R >= 32 ? 128 : 64>::MIN_BLOCKS)
     k_square_core(const uint32_t *__restrict__ Y, uint32_t *__restrict__ D, uint32_t *__restrict__ D2N, int n,
-                  const PrimeConst *__restrict__ pc, const uint2 *__restrict__ twf, const uint2 *__restrict__ twi) {
+                  const PrimeConst *__restrict__ pc, const uint2 *__restrict__ twf, const uint2 *__restrict__ twi,
+                  const uint2 *__restrict__ pre) {
     using C = NttCore<LOGN, R, true, kFmaSquare>;  // data primes only (q < 2^30): lazy butterflies
     constexpr int N = C::N, T = C::T;
     constexpr int V = C::NTT_QUADS ? 4 : (C::NTT_PAIRS ? 2 : 1);  // consecutive NTT-domain elements per register run
@@ -228,6 +231,11 @@ __global__ void __launch_bounds__((1 << LOGN) / R, IN_NTT ? SqnOcc<(1 << LOGN) /
         }
     }
     C::inverse_unscaled(x, sm, tid, mq, ti);
+    if (pre != nullptr) {  // d2 Dhat_i^{-1} mod q_i, the key switch's ModUp factor of this limb
+        const uint2 f = pre[i];
+#pragma unroll
+        for (int u = 0; u < R; u++) x[u] = shoup_mul(x[u], f.x, f.y, P.q);
+    }
     C::store_natural(x, d2, tid);
 }
 
@@ -239,8 +247,11 @@ __global__ void __launch_bounds__((1 << LOGN) / R, IN_NTT ? SqnOcc<(1 << LOGN) /
 //     sum_u r_u * Dhat_u - #{u : r_u > (q_u-1)/2} * D_j,  r_u = [x_u Dhat_u^{-1}]_{q_u},
 // which for one-prime digits is d mod t, less q_j mod t when d > (q_j-1)/2.
 // With LAZY (t a data prime) one-prime digits leave d + (t - q_j mod t) < 3t,
-// a valid lazy NTT input; otherwise the residue is canonical.
-template <int LOGN, int R, bool LAZY>
+// a valid lazy NTT input; otherwise the residue is canonical.  With PRE the
+// limbs of multi-prime digits already hold r_u = [x_u Dhat_u^{-1}]_{q_u} (the
+// square kernel's output for the key switch: computed there once instead of
+// once per target prime); the digit's own primes are then never read here.
+template <int LOGN, int R, bool LAZY, bool PRE = false>
 __device__ __forceinline__ void modup_residue(uint32_t (&x)[R], const uint32_t *__restrict__ x2, int t, int pt,
                                               int j, int n, const KsDev &ks, const PrimeConst *__restrict__ pc,
                                               const PrimeConst &P, int tid) {
@@ -283,7 +294,8 @@ __device__ __forceinline__ void modup_residue(uint32_t (&x)[R], const uint32_t *
             const uint32_t *xi = x2 + (size_t)i * N;
 #pragma unroll
             for (int u = 0; u < R; u++) {
-                const uint32_t r = shoup_mul(__ldg(xi + C::nat_elem(u, tid)), di.x, di.y, qi);
+                const uint32_t raw = __ldg(xi + C::nat_elem(u, tid));
+                const uint32_t r = PRE ? raw : shoup_mul(raw, di.x, di.y, qi);
                 uint32_t y = add_mod(x[u], shoup_mul(r, dh.x, dh.y, P.q), P.q);
                 if (r > half) y = sub_mod(y, dp, P.q);
                 x[u] = y;
@@ -309,8 +321,9 @@ __device__ __forceinline__ void modup_residue(uint32_t (&x)[R], const uint32_t *
 template <int LOGN, int R, bool LAZY>
 __device__ __forceinline__ void ks_core_body(const uint32_t *__restrict__ D, const uint32_t *__restrict__ D2N,
                                              const uint32_t *__restrict__ evk, uint32_t *__restrict__ acc_out,
-                                             int n, int ntt_out, const KsDev &ks, const PrimeConst *__restrict__ pc,
-                                             const uint2 *__restrict__ twf, const uint2 *__restrict__ twi) {
+                                             int n, int ntt_out, int pre, const KsDev &ks,
+                                             const PrimeConst *__restrict__ pc, const uint2 *__restrict__ twf,
+                                             const uint2 *__restrict__ twi) {
     using C = NttCore<LOGN, R, LAZY, kFmaKs>;
     constexpr int N = C::N, T = C::T;
     // running sums r0 += x k0 / R, r1 += x k1 / R: kept in [0, 2q) with lazy
@@ -467,7 +480,10 @@ __device__ __forceinline__ void ks_core_body(const uint32_t *__restrict__ D, con
         if (t >= lo && t < hi && D2N != nullptr) {
             C::load_ntt(x, D2N + ((size_t)ct * n + t) * N, tid);
         } else {
-            modup_residue<LOGN, R, LAZY>(x, x2, t, pt, j, n, ks, pc, P, tid);
+            if (pre)
+                modup_residue<LOGN, R, LAZY, true>(x, x2, t, pt, j, n, ks, pc, P, tid);
+            else
+                modup_residue<LOGN, R, LAZY>(x, x2, t, pt, j, n, ks, pc, P, tid);
             C::forward(x, sm, tid, ModQ(P.q, kFmaOne<LOGN, R> ? P.one : 1u), tf);
         }
         key_product(x, j);
@@ -548,14 +564,14 @@ __device__ __forceinline__ void ks_core_body(const uint32_t *__restrict__ D, con
 template <int LOGN, int R>
 __global__ void __launch_bounds__((1 << LOGN) / R, CoreOcc<(1 << LOGN) / R, kKsWide<LOGN, R> ? 64 : BCN_CORE_REGS>::MIN_BLOCKS)
     k_ks_core(const uint32_t *__restrict__ D, const uint32_t *__restrict__ D2N, const uint32_t *__restrict__ evk,
-              uint32_t *__restrict__ acc_out, int n, int ntt_out, KsDev ks, const PrimeConst *__restrict__ pc,
-              const uint2 *__restrict__ twf, const uint2 *__restrict__ twi) {
+              uint32_t *__restrict__ acc_out, int n, int ntt_out, int pre, KsDev ks,
+              const PrimeConst *__restrict__ pc, const uint2 *__restrict__ twf, const uint2 *__restrict__ twi) {
     const int t = blockIdx.x;
     const int pt = t < n ? t : ks.L + (t - n);
     if (pc[pt].q < (1u << 30))
-        ks_core_body<LOGN, R, true>(D, D2N, evk, acc_out, n, ntt_out, ks, pc, twf, twi);
+        ks_core_body<LOGN, R, true>(D, D2N, evk, acc_out, n, ntt_out, pre, ks, pc, twf, twi);
     else
-        ks_core_body<LOGN, R, false>(D, D2N, evk, acc_out, n, ntt_out, ks, pc, twf, twi);
+        ks_core_body<LOGN, R, false>(D, D2N, evk, acc_out, n, ntt_out, pre, ks, pc, twf, twi);
 }
 
 // ModDown by P and rescale by the top prime q_top = q_{n-1} in the NTT domain
@@ -857,20 +873,31 @@ struct CoreImpl {
             k_ntt_fwd<LOGN, R><<<grid, Core::T, SMEM, st>>>(data, pm, stride, c->d_pc, c->d_tw_fwd);
         return check_launch("NTT");
     }
+    // Digits of more than one prime, with the NTT-domain d2 kept for the key
+    // switch's own primes: the square kernel stores d2 times each limb's ModUp
+    // factor Dhat_i^{-1} and the key switch reads it as is (both sides decide
+    // alike from alpha and D2N)
+    static const uint2 *modup_pre(const bcn_ctx *c, int n, const uint32_t *D2N) {
+        if (c->alpha < 2 || D2N == nullptr) return nullptr;
+        const KsDev ks = ks_dev(c);
+        return ks.dhat_inv + (size_t)n * ks.dnum_max * ks.alpha;  // [(n dnum_max + j) alpha + v] at limb j alpha + v
+    }
     static bcn_status square(const bcn_ctx *c, int n, const uint32_t *Y, uint32_t *D, uint32_t *D2N, int C,
                              bool in_ntt, cudaStream_t st) {
+        const uint2 *pre = modup_pre(c, n, D2N);
         if (in_ntt)
             k_square_core<LOGN, R, true><<<dim3(n, C), Core::T, SMEM_SQ_NTT, st>>>(Y, D, D2N, n, c->d_pc, c->d_tw_fwd,
-                                                                                c->d_tw_inv);
+                                                                                c->d_tw_inv, pre);
         else
             k_square_core<LOGN, R, false><<<dim3(n, C), Core::T, SMEM3, st>>>(Y, D, D2N, n, c->d_pc, c->d_tw_fwd,
-                                                                           c->d_tw_inv);
+                                                                           c->d_tw_inv, pre);
         return check_launch("k_square_core");
     }
     static bcn_status keyswitch(const bcn_ctx *c, int n, const uint32_t *D, const uint32_t *D2N,
                                 const uint32_t *evk, uint32_t *acc, int C, bool ntt_out, cudaStream_t st) {
         k_ks_core<LOGN, RKS><<<dim3(n + c->K, C), CoreKs::T, SMEM_KS, st>>>(
-            D, D2N, evk, acc, n, ntt_out ? 1 : 0, ks_dev(c), c->d_pc, c->d_tw_fwd, c->d_tw_inv);
+            D, D2N, evk, acc, n, ntt_out ? 1 : 0, modup_pre(c, n, D2N) != nullptr ? 1 : 0, ks_dev(c), c->d_pc,
+            c->d_tw_fwd, c->d_tw_inv);
         return check_launch("k_ks_core");
     }
     static bcn_status moddown_rescale(const bcn_ctx *c, int n, const uint32_t *D, const uint32_t *acc,

@@ -31,10 +31,13 @@ def enumerate_work(cfg):
                 work["square"][0] += 0 if in_ntt else 2  # c0, c1 to the NTT domain
                 work["square"][2] += 1  # d2 back to coefficient form
                 work["square"][1] += 4  # c0^2, 2 c0 c1, c1^2 and c1^2 / N
+                if a > 1:
+                    work["square"][1] += 1  # d2 * Dhat^-1 for the key switch's ModUp
             targets = list(range(n)) + [("p", m) for m in range(K)]
             digits = [list(range(j * a, min(n, j * a + a))) for j in range(math.ceil(n / a))]
             for d in digits:
-                work["keyswitch"][1] += len(d)  # x * Dhat^-1 on the digit's primes
+                if a == 1:
+                    work["keyswitch"][1] += len(d)  # x * Dhat^-1 on the digit's primes (else in the square)
                 for t in targets:
                     if t not in d:
                         work["keyswitch"][0] += 1  # ModUp residue -> forward NTT
