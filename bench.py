@@ -204,7 +204,8 @@ def alu_work(cfg):
     special prime and on the top data prime (with its 4 constant products
     folding in the rescale's first step) and a constant product by N on the
     other data primes.  ModDown and rescale: per poly and data limb below the
-    top, 3K + 4 constant products per coefficient and one forward NTT."""
+    top, 2K + 4 constant products per coefficient and one forward NTT (the
+    conversion's first factor Phat_m^-1 rides in the prepared key)."""
     import math
 
     import workloads
@@ -233,7 +234,7 @@ def alu_work(cfg):
         w["keyswitch"]["mont"] += C * 2 * nb * len(digits)
         w["keyswitch"]["shoup"] += C * ((0 if pre else sum(digits)) + sum(d * (nb - d) for d in digits) + 2 * (n - 1) + 4)
         w["moddown_rescale"]["fwd"] += C * 2 * (n - 1)
-        w["moddown_rescale"]["shoup"] += C * 2 * (n - 1) * (3 * K + 4)
+        w["moddown_rescale"]["shoup"] += C * 2 * (n - 1) * (2 * K + 4)
         in_ntt = True
     last = cfg["cipher"][-1]
     if in_ntt:

@@ -595,7 +595,8 @@ __global__ void __launch_bounds__((1 << LOGN) / R, CoreOcc<(1 << LOGN) / R, kKsW
 // polys transformed in lockstep).  D [C][3][n][N] (slots 0, 1: d0, d1 in the
 // NTT domain), ACC [C][2][n+K][N] (limbs i < n-1: A_i in the NTT domain; limb
 // n-1: INTT(A_top P^{-1} + D_top), coefficient form, from the key switch;
-// limbs n..n+K-1: a_P, coefficient form) -> OUT [C][2][n-1][N] (NTT domain,
+// limbs n..n+K-1: a_P times Phat_m^{-1} -- the key carries that factor --,
+// coefficient form) -> OUT [C][2][n-1][N] (NTT domain,
 // last-pass layout, canonical).  grid (n - 1, 2 / NP, C)
 // Register budget of the ModDown/rescale blocks: its element-wise prologue
 // (loads of the special-prime limbs and the top limb) wants occupancy --
@@ -640,10 +641,10 @@ __global__ void __launch_bounds__((1 << LOGN) / R, NP == 1 ? MdOcc<(1 << LOGN) /
             int cnt = 0;
 #pragma unroll
             for (int m = 0; m < K; m++) {
-                const uint32_t pq = pc[ks.L + m].q, ph2 = pc[ks.L + m].half;
-                const uint2 hi = ks.phat_inv[m], phi = ks.phat[(size_t)m * ks.L + i],
-                            pht = ks.phat[(size_t)m * ks.L + top];
-                const uint32_t r = shoup_mul(__ldg(row[p] + (size_t)(n + m) * N + e), hi.x, hi.y, pq);
+                const uint32_t ph2 = pc[ks.L + m].half;
+                const uint2 phi = ks.phat[(size_t)m * ks.L + i], pht = ks.phat[(size_t)m * ks.L + top];
+                // a_m Phat_m^{-1}: the prepared key's special-prime limbs carry Phat_m^{-1}
+                const uint32_t r = __ldg(row[p] + (size_t)(n + m) * N + e);
                 cnt += r > ph2;
                 conv_i = add_mod(conv_i, shoup_mul(r, phi.x, phi.y, P.q), P.q);
                 conv_t = add_mod(conv_t, shoup_mul(r, pht.x, pht.y, qtop), qtop);

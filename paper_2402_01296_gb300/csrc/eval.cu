@@ -360,13 +360,20 @@ bcn_status launch_rescale(const bcn_ctx *c, int n, const uint32_t *in, uint32_t 
 // The evaluation key in this form makes one Montgomery product per digit give
 // the key product already divided by N, which the key-switching kernel's
 // inverse NTT then needs no longer apply.
-__global__ void k_key_form(uint32_t *__restrict__ data, int N, PrimeMap pm, const PrimeConst *__restrict__ pc) {
+// rows on a special prime p_m also take Phat_m^{-1} mod p_m: the key switch's
+// sums there then come out as a_m Phat_m^{-1}, the factor every ModDown
+// conversion applies first (once here instead of once per ciphertext, limb and
+// poly)
+__global__ void k_key_form(uint32_t *__restrict__ data, int N, PrimeMap pm, int L, const uint2 *__restrict__ phat_inv,
+                           const PrimeConst *__restrict__ pc) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= N) return;
-    const int row = blockIdx.y;
-    const PrimeConst &P = pc[prime_of(pm, row)];
+    const int row = blockIdx.y, prime = prime_of(pm, row);
+    const PrimeConst &P = pc[prime];
     uint32_t *x = data + (size_t)row * N + k;
-    *x = shoup_mul(*x, P.rn, P.rn_shoup, P.q);
+    uint32_t v = shoup_mul(*x, P.rn, P.rn_shoup, P.q);
+    if (prime >= L) v = shoup_mul(v, phat_inv[prime - L].x, phat_inv[prime - L].y, P.q);
+    *x = v;
 }
 
 // ------------------------------------------------------------- host helpers
@@ -982,7 +989,8 @@ bcn_status bcn_evk_prepare(const bcn_ctx *c, const uint32_t *evk, uint32_t *evk_
     const PrimeMap all = data_map(c->L + c->K);
     const size_t rows = (size_t)c->dnum * 2 * (c->L + c->K);
     BCN_TRY(launch_ntt(c, evk_eval, rows, all, false, st));
-    k_key_form<<<dim3((c->N + 255) / 256, (unsigned)rows), 256, 0, st>>>(evk_eval, c->N, all, c->d_pc);
+    k_key_form<<<dim3((c->N + 255) / 256, (unsigned)rows), 256, 0, st>>>(evk_eval, c->N, all, c->L,
+                                                                         ks_dev(c).phat_inv, c->d_pc);
     return check_launch("k_key_form");
 }
 

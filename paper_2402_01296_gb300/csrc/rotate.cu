@@ -57,12 +57,12 @@ __device__ __forceinline__ void moddown_rotate_body(const uint32_t *__restrict__
     for (int m = 0; m < 4; m++) {  // K <= 4
         if (m >= ks.K) break;
         const PrimeConst &pm = pc[L + m];
-        const uint2 hi = ks.phat_inv[m];
+        // a_m Phat_m^{-1}: the prepared key's special-prime limbs carry Phat_m^{-1}
         const uint4 v = __ldg(ab + (size_t)(n + m) * stride);
         const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
         for (int z = 0; z < 4; z++) {
-            r[m][z] = shoup_mul(w[z], hi.x, hi.y, pm.q);
+            r[m][z] = w[z];
             cnt[z] += r[m][z] > pm.half;
         }
     }

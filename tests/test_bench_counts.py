@@ -53,7 +53,7 @@ def enumerate_work(cfg):
             for _limb in range(n - 1):
                 for _poly in range(2):
                     work["moddown_rescale"][0] += 1
-                    work["moddown_rescale"][1] += 3 * K + 4
+                    work["moddown_rescale"][1] += 2 * K + 4  # Phat_m^-1 rides in the prepared key
         in_ntt = True
     if in_ntt:
         last = cfg["cipher"][-1]
