@@ -333,8 +333,11 @@ bcn_status bcn_model_layers(const bcn_model *m, int *level_out, int *n_out_out);
 bcn_status bcn_model_scales(const bcn_model *m, double input_scale, double *add_scales_out, double *out_scale);
 
 /* Convert a boundary-layout evaluation key (coefficient form, device memory)
- * into the evaluator's form (NTT domain, Montgomery representation) in
- * evk_eval_dev (same size; may equal evk_dev for in-place). */
+ * into the evaluator's form (NTT domain, Montgomery representation; the limbs
+ * on special prime p_m also times Phat_m^{-1} = (P / p_m)^{-1} mod p_m, the
+ * first factor of every ModDown conversion, applied here once) in
+ * evk_eval_dev (same size; may equal evk_dev for in-place).  Relinearisation
+ * and Galois keys alike. */
 bcn_status bcn_evk_prepare(const bcn_ctx *ctx, const uint32_t *evk_dev, uint32_t *evk_eval_dev, void *cuda_stream);
 
 bcn_status bcn_eval_workspace_bytes(const bcn_model *m, size_t *bytes);
