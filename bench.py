@@ -203,9 +203,10 @@ def alu_work(cfg):
     per digit and target prime with the key, then two inverse NTTs on each
     special prime and on the top data prime (with its 4 constant products
     folding in the rescale's first step) and a constant product by N on the
-    other data primes.  ModDown and rescale: per poly and data limb below the
-    top, 2K + 4 constant products per coefficient and one forward NTT (the
-    conversion's first factor Phat_m^-1 rides in the prepared key)."""
+    other data primes.  ModDown and rescale: per poly, K + 1 constant products
+    per coefficient for the top limb's correction (shared by every limb), then
+    per data limb below the top K + 3 and one forward NTT (the conversion's
+    first factor Phat_m^-1 rides in the prepared key)."""
     import math
 
     import workloads
@@ -234,7 +235,7 @@ def alu_work(cfg):
         w["keyswitch"]["mont"] += C * 2 * nb * len(digits)
         w["keyswitch"]["shoup"] += C * ((0 if pre else sum(digits)) + sum(d * (nb - d) for d in digits) + 2 * (n - 1) + 4)
         w["moddown_rescale"]["fwd"] += C * 2 * (n - 1)
-        w["moddown_rescale"]["shoup"] += C * 2 * (n - 1) * (2 * K + 4)
+        w["moddown_rescale"]["shoup"] += C * 2 * ((n - 1) * (K + 3) + K + 1)
         in_ntt = True
     last = cfg["cipher"][-1]
     if in_ntt:

@@ -141,6 +141,7 @@ struct Profiler {
         int cls;
         size_t e0, e1;
         double bytes;
+        int kernels;  // launches inside the timed scope
     };
     std::vector<Rec> recs;
     double ms[BCN_KERNEL_COUNT] = {};

@@ -594,7 +594,8 @@ __global__ void __launch_bounds__((1 << LOGN) / R, CoreOcc<(1 << LOGN) / R, kKsW
 // out_i of polys b0 .. b0+NP-1 of ciphertext ct, i < n - 1 (NP = 2: both
 // polys transformed in lockstep).  D [C][3][n][N] (slots 0, 1: d0, d1 in the
 // NTT domain), ACC [C][2][n+K][N] (limbs i < n-1: A_i in the NTT domain; limb
-// n-1: INTT(A_top P^{-1} + D_top), coefficient form, from the key switch;
+// n-1: c_top = INTT(A_top P^{-1} + D_top) - conv_top(a_P) P^{-1}, coefficient
+// form, from the key switch and k_md_top;
 // limbs n..n+K-1: a_P times Phat_m^{-1} -- the key carries that factor --,
 // coefficient form) -> OUT [C][2][n-1][N] (NTT domain,
 // last-pass layout, canonical).  grid (n - 1, 2 / NP, C)
@@ -602,6 +603,47 @@ __global__ void __launch_bounds__((1 << LOGN) / R, CoreOcc<(1 << LOGN) / R, kKsW
 // (loads of the special-prime limbs and the top limb) wants occupancy --
 // measured at N = 8192: 40 registers (3 blocks per SM) 0.140 ms, 64 registers
 // 0.155 ms, 128 registers 0.193 ms; 32 residues a thread need 64
+// The top limb's part of ModDown and rescale, the same for every limb i:
+// c_top = acc_top - conv_top(a_P) P^{-1} (mod q_top), stored over acc_top
+// (limb n-1 of ACC) for k_md_limb to lift; once per (coefficient, poly,
+// ciphertext) instead of once per limb.  Four coefficients a thread.
+// grid (N/4/256, 2, C)
+template <int K>
+__global__ void __launch_bounds__(256) k_md_top(uint32_t *__restrict__ acc, int n, int N, KsDev ks,
+                                                const PrimeConst *__restrict__ pc) {
+    const int k4 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k4 * 4 >= N) return;
+    const int b = blockIdx.y, ct = blockIdx.z, nb = n + K, top = n - 1;
+    const uint32_t qtop = pc[top].q, pmod_t = ks.pmod[top];
+    const uint2 pit = ks.pinv[top];
+    uint32_t *row = acc + ((size_t)ct * 2 + b) * nb * N;
+    uint32_t conv[4] = {0, 0, 0, 0};
+    int cnt[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int m = 0; m < K; m++) {
+        const uint32_t ph2 = pc[ks.L + m].half;
+        const uint2 pht = ks.phat[(size_t)m * ks.L + top];
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(row + (size_t)(n + m) * N) + k4);  // a_m Phat_m^{-1}
+        const uint32_t r[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int z = 0; z < 4; z++) {
+            cnt[z] += r[z] > ph2;
+            conv[z] = add_mod(conv[z], shoup_mul(r[z], pht.x, pht.y, qtop), qtop);
+        }
+    }
+    uint4 *tp = reinterpret_cast<uint4 *>(row + (size_t)top * N) + k4;
+    const uint4 a = *tp;
+    const uint32_t av[4] = {a.x, a.y, a.z, a.w};
+    uint32_t y[4];
+#pragma unroll
+    for (int z = 0; z < 4; z++) {
+#pragma unroll
+        for (int c = 0; c < K; c++) conv[z] = c < cnt[z] ? sub_mod(conv[z], pmod_t, qtop) : conv[z];
+        y[z] = sub_mod(av[z], shoup_mul(conv[z], pit.x, pit.y, qtop), qtop);
+    }
+    *tp = make_uint4(y[0], y[1], y[2], y[3]);
+}
+
 template <int T, int R>
 struct MdOcc {
     static constexpr int REGS = R >= 32 ? 64 : 40;
@@ -621,13 +663,13 @@ __global__ void __launch_bounds__((1 << LOGN) / R, NP == 1 ? MdOcc<(1 << LOGN) /
     const int nb = n + ks.K, top = n - 1;
     const PrimeConst P = pc[i];
     const uint32_t qtop = pc[top].q, htop = pc[top].half, tmq = P.q - qtop;  // q_i > q_top
-    const uint2 pi = ks.pinv[i], pit = ks.pinv[top], qti = ks.qtop_inv[(size_t)top * ks.L + i];
-    const uint32_t pmod_i = ks.pmod[i], pmod_t = ks.pmod[top];
+    const uint2 pi = ks.pinv[i], qti = ks.qtop_inv[(size_t)top * ks.L + i];
+    const uint32_t pmod_i = ks.pmod[i];
     const uint32_t *row[NP];
 #pragma unroll
     for (int p = 0; p < NP; p++) row[p] = acc + ((size_t)ct * 2 + b0 + p) * nb * N;
     // coefficient form: conv_i(a_P) P^{-1} + [c_top] (mod q_i), with
-    // c_top = acc_top - conv_top(a_P) P^{-1} (mod q_top)
+    // c_top = acc_top - conv_top(a_P) P^{-1} (mod q_top) formed by k_md_top
     uint32_t x[NP][R];
 #pragma unroll
     for (int u = 0; u < R; u++) {
@@ -637,26 +679,20 @@ __global__ void __launch_bounds__((1 << LOGN) / R, NP == 1 ? MdOcc<(1 << LOGN) /
             // K (the number of special primes) is a template parameter and the
             // correction below a chain of selects: no branch, so the loads of
             // all R elements can be issued together
-            uint32_t conv_i = 0, conv_t = 0;
+            uint32_t conv_i = 0;
             int cnt = 0;
 #pragma unroll
             for (int m = 0; m < K; m++) {
                 const uint32_t ph2 = pc[ks.L + m].half;
-                const uint2 phi = ks.phat[(size_t)m * ks.L + i], pht = ks.phat[(size_t)m * ks.L + top];
+                const uint2 phi = ks.phat[(size_t)m * ks.L + i];
                 // a_m Phat_m^{-1}: the prepared key's special-prime limbs carry Phat_m^{-1}
                 const uint32_t r = __ldg(row[p] + (size_t)(n + m) * N + e);
                 cnt += r > ph2;
                 conv_i = add_mod(conv_i, shoup_mul(r, phi.x, phi.y, P.q), P.q);
-                conv_t = add_mod(conv_t, shoup_mul(r, pht.x, pht.y, qtop), qtop);
             }
 #pragma unroll
-            for (int c = 0; c < K; c++) {
-                const uint32_t si = sub_mod(conv_i, pmod_i, P.q), st = sub_mod(conv_t, pmod_t, qtop);
-                conv_i = c < cnt ? si : conv_i;
-                conv_t = c < cnt ? st : conv_t;
-            }
-            const uint32_t y =
-                sub_mod(__ldg(row[p] + (size_t)top * N + e), shoup_mul(conv_t, pit.x, pit.y, qtop), qtop);
+            for (int c = 0; c < K; c++) conv_i = c < cnt ? sub_mod(conv_i, pmod_i, P.q) : conv_i;
+            const uint32_t y = __ldg(row[p] + (size_t)top * N + e);  // c_top (k_md_top)
             const uint32_t lift = y > htop ? y + tmq : y;
             x[p][u] = add_mod(shoup_mul(conv_i, pi.x, pi.y, P.q), lift, P.q);
         }
@@ -905,6 +941,17 @@ struct CoreImpl {
                                       uint32_t *out, int C, cudaStream_t st) {
         const dim3 grid(n - 1, 2 / MD_NP, C);
         const KsDev ks = ks_dev(c);
+        // the top limb's correction, shared by every limb (in place on acc's limb n-1)
+        uint32_t *acc_w = const_cast<uint32_t *>(acc);
+        const dim3 gtop((unsigned)((c->N / 4 + 255) / 256), 2, (unsigned)C);
+        switch (c->K) {
+        case 1: k_md_top<1><<<gtop, 256, 0, st>>>(acc_w, n, c->N, ks, c->d_pc); break;
+        case 2: k_md_top<2><<<gtop, 256, 0, st>>>(acc_w, n, c->N, ks, c->d_pc); break;
+        case 3: k_md_top<3><<<gtop, 256, 0, st>>>(acc_w, n, c->N, ks, c->d_pc); break;
+        case 4: k_md_top<4><<<gtop, 256, 0, st>>>(acc_w, n, c->N, ks, c->d_pc); break;
+        default: return fail(BCN_E_INVAL, "ModDown: 1 to 4 special primes");
+        }
+        BCN_TRY(check_launch("k_md_top"));
         switch (c->K) {
         case 1: k_md_limb<LOGN, RMD, MD_NP, 1><<<grid, CoreMd::T, SMEM_MD, st>>>(D, acc, out, n, ks, c->d_pc, c->d_tw_fwd); break;
         case 2: k_md_limb<LOGN, RMD, MD_NP, 2><<<grid, CoreMd::T, SMEM_MD, st>>>(D, acc, out, n, ks, c->d_pc, c->d_tw_fwd); break;

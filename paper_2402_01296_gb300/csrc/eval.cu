@@ -403,6 +403,7 @@ struct Timed {
     cudaStream_t st;
     int cls;
     double bytes;
+    int kernels = 1;  // launches the scope covers (the reported launch count)
     size_t e0 = 0;
     Timed(Profiler *p_, cudaStream_t st_, int cls_, double bytes_)
         : range(kClassName[cls_]), p(p_ && p_->on ? p_ : nullptr), st(st_), cls(cls_), bytes(bytes_) {
@@ -420,7 +421,7 @@ struct Timed {
     ~Timed() {
         if (p) {
             size_t e1 = mark();
-            p->recs.push_back({cls, e0, e1, bytes});
+            p->recs.push_back({cls, e0, e1, bytes, kernels});
         }
     }
 };
@@ -556,16 +557,19 @@ static bcn_status square_chunk(const bcn_ctx *c, int n, const uint32_t *evk, con
         if (kt.n == 0) {
             BCN_TRY(f->keyswitch(c, n, b.d, b.d2n, evk, b.acc, C, true, st));
         } else {  // one launch per request the chunk covers, with its key
+            tm.kernels = 0;
             for (int r = kt.ct_base / kt.cts_per_key; r < kt.n && r * kt.cts_per_key < kt.ct_base + C; r++) {
                 const int lo = std::max(r * kt.cts_per_key, kt.ct_base) - kt.ct_base;
                 const int hi = std::min((r + 1) * kt.cts_per_key, kt.ct_base + C) - kt.ct_base;
                 if (hi <= lo) continue;
                 const ChunkBufs sb = chunk_from(c, n, b, lo);
                 BCN_TRY(f->keyswitch(c, n, sb.d, sb.d2n, kt.key[r], sb.acc, hi - lo, true, st));
+                tm.kernels++;
             }
         }
     }
     Timed tm(prof, st, BCN_KERNEL_MODDOWN_RESCALE, limb * C * (2.0 * n + 2.0 * nb + 2.0 * (n - 1)));
+    tm.kernels = 2;  // the top limb's correction, then the per-limb kernel
     return f->moddown_rescale(c, n, b.d, b.acc, out, C, st);
 }
 
@@ -1443,7 +1447,7 @@ bcn_status bcn_profile_read(bcn_model *m, int cls, double *ms, long long *launch
         float t = 0;
         cudaEventElapsedTime(&t, p.ev[r.e0], p.ev[r.e1]);
         p.ms[r.cls] += t;
-        p.launches[r.cls] += 1;
+        p.launches[r.cls] += r.kernels;
         p.bytes[r.cls] += r.bytes;
     }
     p.recs.clear();

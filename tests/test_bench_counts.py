@@ -50,10 +50,11 @@ def enumerate_work(cfg):
                         work["keyswitch"][1] += 4  # the rescale's first step, both polys
                 else:
                     work["keyswitch"][1] += 2  # sums times N, both polys
-            for _limb in range(n - 1):
-                for _poly in range(2):
+            for _poly in range(2):
+                work["moddown_rescale"][1] += K + 1  # the top limb's correction, shared by every limb
+                for _limb in range(n - 1):
                     work["moddown_rescale"][0] += 1
-                    work["moddown_rescale"][1] += 2 * K + 4  # Phat_m^-1 rides in the prepared key
+                    work["moddown_rescale"][1] += K + 3  # Phat_m^-1 rides in the prepared key
         in_ntt = True
     if in_ntt:
         last = cfg["cipher"][-1]
