@@ -738,6 +738,17 @@ def run_uneven(args, rank, world, local_rank):
         items.append((m, evks[cfg["log_n"]], cts, pts, out))
         images += cfg["batch"]
     torch.cuda.synchronize()
+    # the NTT-based kernels' block shape per ring degree, timed on each
+    # context's first evaluation (the context keeps the faster)
+    shape_note = {}
+    for log_n, cx in ctxs.items():
+        m0, ev0, c0, p0, o0 = next(it for it, cf in zip(items, cfgs) if cf["log_n"] == log_n)
+        ws0 = m0.alloc_workspace()
+        best, _, res = tuner.tune_ntt_shape(cx, lambda: m0.eval(ev0, c0, p0, o0, ws0))
+        shape_note[str(log_n)] = {"chosen": best, "residues_per_thread": cx.ntt_shape()[1],
+                                  "ms": {str(k): round(v, 3) for k, v in res.items()}}
+        del ws0
+    torch.cuda.empty_cache()
     free, total = torch.cuda.mem_get_info()
     budget = max(0, free - (8 << 30))
     lanes, _, lane_res = tuner.tune_lanes(items, candidates=(1, 2, 4, 8), budget_bytes=budget)
@@ -808,7 +819,8 @@ def run_uneven(args, rank, world, local_rank):
                    "images_per_step": images, "lanes": lanes,
                    "counts": {str(k): sum(1 for c in cfgs if c["log_n"] == k) for k in (12, 13, 14)}},
         "p50_ms": statistics.median(ms), "p99_ms": float(np.percentile(ms, 99)),
-        "tuning": {"lanes_ms": {str(k): round(v, 3) for k, v in lane_res.items()}, "alpha_ms": alpha_note},
+        "tuning": {"lanes_ms": {str(k): round(v, 3) for k, v in lane_res.items()}, "alpha_ms": alpha_note,
+                   "ntt_shape": shape_note},
         "plain_sequential": {"value": images / (min(plain_ms) / 1e3), "ms_per_step": min(plain_ms),
                              "path": "each evaluation alone, every kernel in order on one stream, the "
                                      "configuration's digit size and the default chunk, no graph"},

@@ -110,6 +110,17 @@ bcn_status bcn_device_status(const bcn_ctx *ctx, uint32_t *status);
  * launching the operation.  The checks read every input once more and
  * synchronise the stream, and they are skipped on a stream being captured
  * into a graph.  Off by default. */
+/* Block shape of the NTT-based kernels (the square activation's, the key
+ * switch's, ModDown's, the transforms'): 0 the default, 1 an alternative, for
+ * N = 4096 (16 residues per thread; alternative 8), 8192 (16; alternative 32)
+ * and 16384 (32; alternative 16); smaller rings have one shape.  Every later
+ * call on the context uses the selected shape; results are identical (the
+ * element order of the NTT domain does not depend on the shape), only the
+ * speed differs -- the autotuner measures both.  Not to be changed while work
+ * on the context is in flight.  bcn_ctx_get_ntt_shape: the selection and its
+ * residues per thread (-1 below N = 4096). */
+bcn_status bcn_ctx_set_ntt_shape(bcn_ctx *ctx, int shape);
+bcn_status bcn_ctx_get_ntt_shape(const bcn_ctx *ctx, int *shape, int *residues_per_thread);
 bcn_status bcn_ctx_set_debug(bcn_ctx *ctx, int on);
 bcn_status bcn_ctx_get_debug(const bcn_ctx *ctx, int *on);
 

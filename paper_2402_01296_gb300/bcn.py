@@ -67,6 +67,8 @@ _SIGS = {
     "bcn_evk_words": (_SZ, [_P]),
     "bcn_device_status": (_I, [_P, _P]),
     "bcn_ctx_set_debug": (_I, [_P, _I]),
+    "bcn_ctx_set_ntt_shape": (_I, [_P, _I]),
+    "bcn_ctx_get_ntt_shape": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "bcn_ctx_get_debug": (_I, [_P, ctypes.POINTER(_I)]),
     "bcn_keygen": (_I, [_P, _U64, _P, _P]),
     "bcn_quantize": (_I, [_P, _SZ, _P, ctypes.POINTER(_D)]),
@@ -254,6 +256,16 @@ class Context:
 
     def evk_shape(self):
         return (self.dnum, 2, self.L + self.K, self.N)
+
+    def set_ntt_shape(self, shape: int):
+        """bcn_ctx_set_ntt_shape: 0 the default block shape of the NTT-based kernels, 1 the alternative."""
+        _check(lib().bcn_ctx_set_ntt_shape(self._h, int(shape)), "bcn_ctx_set_ntt_shape")
+
+    def ntt_shape(self):
+        """(selected shape, residues per thread of the NTT kernels)."""
+        a, r = _I(), _I()
+        _check(lib().bcn_ctx_get_ntt_shape(self._h, ctypes.byref(a), ctypes.byref(r)), "bcn_ctx_get_ntt_shape")
+        return a.value, r.value
 
     def set_debug(self, on: bool = True):
         """bcn_ctx_set_debug: device-side checks of every call's inputs (residues

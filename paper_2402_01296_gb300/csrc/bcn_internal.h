@@ -97,6 +97,7 @@ struct bcn_ctx {
     bcn_params params;
     int N, logN, L, K, alpha, dnum;
     int device;  // -1: host only
+    int ntt_alt = 0;  // block shape of the NTT-based kernels: 0 default, 1 the alternative (N >= 4096)
 #ifdef BCN_DEBUG
     bool debug = true;                 // device-side input checks before each call (bcn_ctx_set_debug)
 #else

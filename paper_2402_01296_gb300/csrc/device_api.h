@@ -114,7 +114,12 @@ struct CoreFns {
     bcn_status (*ks_rot)(const bcn_ctx *, int n, const uint32_t *U, const RotBatch &rb, uint32_t *acc, int C,
                          cudaStream_t);
 };
-const CoreFns *core_fns(int logN);  // nullptr if unsupported
+const CoreFns *core_fns(int logN, int alt = 0);  // nullptr if unsupported; alt: the alternative block shape
+// the context's selected block shape (bcn_ctx_set_ntt_shape)
+const CoreFns *core_fns(const bcn_ctx *c);
+const CoreFns *core_fns_12_alt();
+const CoreFns *core_fns_13_alt();
+const CoreFns *core_fns_14_alt();
 const CoreFns *core_fns_small(int logN);
 const CoreFns *core_fns_12();
 const CoreFns *core_fns_13();

@@ -546,7 +546,7 @@ static bcn_status square_chunk(const bcn_ctx *c, int n, const uint32_t *evk, con
                                const KeyTable &kt = KeyTable{}) {
     const int N = c->N, K = c->K, nb = n + K, dnum = (n + c->alpha - 1) / c->alpha;
     const double limb = (double)N * 4;
-    const CoreFns *f = core_fns(c->logN);
+    const CoreFns *f = core_fns(c);
     if (!f) return fail(BCN_E_INVAL, "unsupported ring degree");
     {
         Timed tm(prof, st, BCN_KERNEL_SQUARE, limb * C * 6.0 * n);
@@ -1505,7 +1505,7 @@ bcn_status bcn_op_tensor_square(const bcn_ctx *c, int level, const uint32_t *in,
     (void)ws_bytes;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t N = c->N;
-    const CoreFns *f = core_fns(c->logN);
+    const CoreFns *f = core_fns(c);
     if (!f) return fail(BCN_E_INVAL, "unsupported ring degree");
     for (int o0 = 0; o0 < n_ct; o0 += 32768) {
         const int C = std::min(32768, n_ct - o0);

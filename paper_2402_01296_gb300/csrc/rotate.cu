@@ -240,7 +240,7 @@ extern "C" bcn_status bcn_op_rotate_many(const bcn_ctx *c, int level, const uint
         if (s != 0 && (!gk_evals[r] || !a16(gk_evals[r])))
             return fail(BCN_E_INVAL, "bcn_op_rotate_many: missing or unaligned Galois key");
     }
-    const CoreFns *f = core_fns(c->logN);
+    const CoreFns *f = core_fns(c);
     if (!f) return fail(BCN_E_INVAL, "unsupported ring degree");
     cudaStream_t st = (cudaStream_t)stream;
     BCN_TRY(debug_check_input(c, in, 2 * (size_t)n_ct, level, st, "bcn_op_rotate_many"));
@@ -387,7 +387,7 @@ extern "C" bcn_status bcn_op_rotate(const bcn_ctx *c, int level, const uint32_t 
     const size_t N = c->N, ct_words = 2 * (size_t)level * N;
     const uint32_t *in_end = in + (size_t)n_ct * ct_words, *out_end = out + (size_t)n_ct * ct_words;
     if (in < out_end && out < in_end) return fail(BCN_E_INVAL, "bcn_op_rotate: in and out overlap");
-    const CoreFns *f = core_fns(c->logN);
+    const CoreFns *f = core_fns(c);
     if (!f) return fail(BCN_E_INVAL, "unsupported ring degree");
     const uint64_t g = bcn_galois_elt(c, steps), ginv = galois_inverse(g, N);
     cudaStream_t st = (cudaStream_t)stream;

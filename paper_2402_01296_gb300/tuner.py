@@ -6,7 +6,10 @@ Knobs:
   * chunk      -- ciphertexts per key-switching chunk of a model
                   (bcn_model_set_chunk; the workspace follows);
   * alpha      -- primes per key-switching digit (a parameter of the context and
-                  of its evaluation key), where K > 1 allows a choice.
+                  of its evaluation key), where K > 1 allows a choice;
+  * NTT shape  -- residues per thread of the NTT-based kernels of a context
+                  (bcn_ctx_set_ntt_shape: the default or the alternative block
+                  shape, N >= 4096).
 Every candidate computes the same residues; only the time differs.  Timing is
 CUDA events on the launching stream, after a warm-up launch.
 """
@@ -68,4 +71,19 @@ def tune_alpha(make_eval, alphas):
     Returns (alpha, ms, {alpha: ms})."""
     results = {a: _time(make_eval(a)) for a in alphas}
     best = min(results, key=results.get)
+    return best, results[best], results
+
+
+def tune_ntt_shape(ctx, run, shapes=(0, 1)):
+    """Fastest block shape of the context's NTT-based kernels: run() is a
+    zero-argument callable evaluating a representative model on the context.
+    Leaves the context set to the winner.  Returns (shape, ms, {shape: ms})."""
+    if ctx.N < 4096:
+        return 0, _time(run), {0: _time(run)}
+    results = {}
+    for sh in shapes:
+        ctx.set_ntt_shape(sh)
+        results[sh] = _time(run)
+    best = min(results, key=results.get)
+    ctx.set_ntt_shape(best)
     return best, results[best], results
