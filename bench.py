@@ -452,7 +452,13 @@ def build_inputs(bcn, torch, cfg, device):
     pts = [ctx.encode(fv, model.levels[i], sc) for fv, i, sc in zip(f_split, model.add_layers, adds)]
     sk, evk = ctx.keygen(workloads.SEED_KEYS)
     cts = ctx.encrypt_segment(sk, imgs, cfg["segment"], scale0, workloads.SEED_ENC)
-    return ctx, model, sk, evk, cts, pts, out_scale
+    # the same features as integer coefficients, for the compact upload (None
+    # where a coefficient reaches 2^63)
+    try:
+        feats_i64 = [ctx.encode_i64(fv, sc) for fv, sc in zip(f_split, adds)]
+    except bcn.BcnError:
+        feats_i64 = None
+    return ctx, model, sk, evk, cts, pts, out_scale, feats_i64
 
 
 def run_ours(args, cfg, rank, world, local_rank):
@@ -469,7 +475,7 @@ def run_ours(args, cfg, rank, world, local_rank):
         dist = dist_mod
         dist.init_process_group("nccl", device_id=torch.device("cuda", device))
 
-    ctx, model, sk, evk, cts, pts, out_scale = build_inputs(bcn, torch, cfg, device)
+    ctx, model, sk, evk, cts, pts, out_scale, feats_i64 = build_inputs(bcn, torch, cfg, device)
     dev = f"cuda:{device}"
     evk_eval = ctx.evk_prepare(bcn.to_device(evk, dev))
     cts_d = bcn.to_device(cts, dev)
@@ -574,11 +580,24 @@ def run_ours(args, cfg, rank, world, local_rank):
     full_total, full_steps = e2e_run(lambda i: model.eval_host_async(
         evk_eval, as_u32(cts_h), pts_u, as_u32(outs_h[i % E2E_LANES]), ws_h2[i % E2E_LANES]))
     full_value, full_ms = replica_summary(full_total / K * 1e3, cfg["batch"], dist, dev)
-    e2e_total, e2e_steps = e2e_run(lambda i: model.eval_host_seeded_async(
+    seed_total, seed_steps = e2e_run(lambda i: model.eval_host_seeded_async(
         evk_eval, as_u32(c0_h), workloads.SEED_ENC, pts_u, as_u32(outs_h[i % E2E_LANES]), ws_h2[i % E2E_LANES]))
-    e2e_value, e2e_ms = replica_summary(e2e_total / K * 1e3, cfg["batch"], dist, dev)
-    h2d = c0_h.numel() * 4 + sum(p.nbytes for p in pts)
+    seed_value, seed_ms = replica_summary(seed_total / K * 1e3, cfg["batch"], dist, dev)
+    h2d_seed = c0_h.numel() * 4 + sum(p.nbytes for p in pts)
     h2d_full = cts.nbytes + sum(p.nbytes for p in pts)
+    if feats_i64 is not None:  # the headline upload: c0, the seed and the features' integer coefficients
+        f64_h = [torch.from_numpy(np.ascontiguousarray(f)).pin_memory().numpy() for f in feats_i64]
+        e2e_total, e2e_steps = e2e_run(lambda i: model.eval_host_compact_async(
+            evk_eval, as_u32(c0_h), workloads.SEED_ENC, f64_h, as_u32(outs_h[i % E2E_LANES]), ws_h2[i % E2E_LANES]))
+        e2e_value, e2e_ms = replica_summary(e2e_total / K * 1e3, cfg["batch"], dist, dev)
+        h2d = c0_h.numel() * 4 + sum(f.nbytes for f in feats_i64)
+        upload = ("seeded ciphertexts (c0 and the encryption seed, c1 drawn on the device) and the features' "
+                  "integer coefficients (reduced mod each prime on the device)")
+        e2e_path = "bcn_eval_host_compact_async"
+    else:
+        e2e_total, e2e_steps, e2e_value, e2e_ms, h2d = seed_total, seed_steps, seed_value, seed_ms, h2d_seed
+        upload = "seeded ciphertexts (c0 and the encryption seed, c1 drawn on the device) and the encoded features"
+        e2e_path = "bcn_eval_host_seeded_async"
     d2h = out_h.numel() * 4
 
     B = cfg["batch"]
@@ -642,10 +661,13 @@ def run_ours(args, cfg, rank, world, local_rank):
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms,
                 "first_step_ms": e2e_steps[0],
                 "later_steps_ms": statistics.mean(e2e_steps[1:]) if K > 1 else None,
-                "upload": "seeded ciphertexts (c0 and the encryption seed, c1 drawn on the device) and the encoded "
-                          "features",
-                "pipelining": f"bcn_eval_host_seeded_async with {E2E_LANES} workspaces in turn on one stream: a "
-                              "step's inputs copy while the step before it computes",
+                "upload": upload,
+                "pipelining": f"{e2e_path} with {E2E_LANES} workspaces in turn on one stream: a step's inputs "
+                              "copy while the step before it computes",
+                "seeded_ciphertexts": {"value": seed_value, "ms_per_step": seed_ms,
+                                       "h2d_bytes_per_step": int(h2d_seed), "first_step_ms": seed_steps[0],
+                                       "later_steps_ms": statistics.mean(seed_steps[1:]) if K > 1 else None,
+                                       "path": "bcn_eval_host_seeded_async (features as residues)"},
                 "full_ciphertexts": {"value": full_value, "ms_per_step": full_ms, "h2d_bytes_per_step": int(h2d_full),
                                      "first_step_ms": full_steps[0],
                                      "later_steps_ms": statistics.mean(full_steps[1:]) if K > 1 else None,

@@ -154,6 +154,17 @@ bcn_status bcn_quantize(const float *w, size_t n, int8_t *w_int_out, double *s_w
  * each prime.  BCN_E_SCALE if a product is not finite. Host memory. */
 bcn_status bcn_encode(const bcn_ctx *ctx, const double *values, int n_vec, int B, int level, double scale,
                       uint32_t *pts_out);
+/* The same encoding as integer coefficients, coeffs_out [n_vec][N] int64 (the
+ * m_j whose residues bcn_encode writes), for uploads that let the device reduce
+ * them (bcn_expand_i64, bcn_eval_host_compact_async): 8 bytes a coefficient
+ * whatever the level.  BCN_E_SCALE if a coefficient is not below 2^63 in
+ * magnitude (use bcn_encode there).  Host. */
+bcn_status bcn_encode_i64(const bcn_ctx *ctx, const double *values, int n_vec, int B, double scale,
+                          int64_t *coeffs_out);
+/* coeffs_dev [n][N] int64 -> pts_dev [n][level][N], m_j mod q_i (device,
+ * asynchronous on `cuda_stream`; the buffers must not overlap). */
+bcn_status bcn_expand_i64(const bcn_ctx *ctx, const int64_t *coeffs_dev, int n, int level, uint32_t *pts_dev,
+                          void *cuda_stream);
 
 /* Symmetric encryption (the client holds the key, Sec. 2):
  * ct = (-a s + e + m, a) with a uniform per limb and e centred binomial, drawn
@@ -413,6 +424,17 @@ bcn_status bcn_eval_host_async(const bcn_model *m, const uint32_t *evk_eval_dev,
 bcn_status bcn_eval_host_seeded_async(const bcn_model *m, const uint32_t *evk_eval_dev, const uint32_t *c0_host,
                                       uint64_t seed, const uint32_t *const *pts_host, uint32_t *out_host,
                                       void *workspace_dev, size_t workspace_bytes, void *cuda_stream);
+/* The same with the feature plaintexts as their integer coefficients
+ * (bcn_encode_i64): feats_host[a] [n_out][N] int64 for the a-th layer with a
+ * feature, 8 bytes a coefficient instead of 4 per prime; the device reduces
+ * them mod each prime into the staging area (through the workspace's first
+ * ciphertext buffer, so the evaluation's first layer waits for all of them).
+ * Results equal bcn_eval_host_seeded_async's with the residues bcn_encode
+ * gives.  BCN_E_BUDGET if the integer features exceed that buffer (the largest
+ * layer output of the model). */
+bcn_status bcn_eval_host_compact_async(const bcn_model *m, const uint32_t *evk_eval_dev, const uint32_t *c0_host,
+                                       uint64_t seed, const int64_t *const *feats_host, uint32_t *out_host,
+                                       void *workspace_dev, size_t workspace_bytes, void *cuda_stream);
 
 /* ------------------------------------------------ batched evaluation (device) */
 /* Many evaluations of different models (ring degrees, segment sizes) replayed

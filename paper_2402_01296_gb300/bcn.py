@@ -78,6 +78,8 @@ _SIGS = {
     "bcn_encrypt_seeded": (_I, [_P, _P, _P, _I, _I, _U64, _P]),
     "bcn_encrypt_segment_seeded": (_I, [_P, _P, _P, _I, _I, _I, _I, _P, _D, _U64, _P]),
     "bcn_expand_seeded": (_I, [_P, _P, _I, _I, _U64, _I, _P, _P]),
+    "bcn_encode_i64": (_I, [_P, _P, _I, _I, _D, _P]),
+    "bcn_expand_i64": (_I, [_P, _P, _I, _I, _P, _P]),
     "bcn_decrypt_decode": (_I, [_P, _P, _P, _I, _I, _D, _I, _P]),
     "bcn_message_bytes": (_SZ, [_P, _I, _I, _I]),
     "bcn_serialize": (_I, [_P, _I, _I, _I, ctypes.c_uint32, _P, _P, _SZ]),
@@ -106,6 +108,7 @@ _SIGS = {
     "bcn_eval_host": (_I, [_P, _P, _P, _P, _P, _P, _SZ, _P]),
     "bcn_eval_host_async": (_I, [_P, _P, _P, _P, _P, _P, _SZ, _P]),
     "bcn_eval_host_seeded_async": (_I, [_P, _P, _P, _U64, _P, _P, _P, _SZ, _P]),
+    "bcn_eval_host_compact_async": (_I, [_P, _P, _P, _U64, _P, _P, _P, _SZ, _P]),
     "bcn_batch_plan": (_I, [_P, _I, _I, ctypes.POINTER(_SZ)]),
     "bcn_batch_create": (_I, [_P, _I, _I, _P, _SZ, ctypes.POINTER(_P)]),
     "bcn_batch_launch": (_I, [_P, _P]),
@@ -306,6 +309,24 @@ class Context:
         _check(lib().bcn_encode(self._h, _np_ptr(v, np.float64), n_vec, B, level, scale, _np_ptr(out, np.uint32)),
                "bcn_encode")
         return out
+
+    def encode_i64(self, values: np.ndarray, scale: float) -> np.ndarray:
+        """bcn_encode_i64: the encoding's integer coefficients [n_vec][N] (int64)."""
+        v = np.ascontiguousarray(np.atleast_2d(values), dtype=np.float64)
+        n_vec, B = v.shape
+        out = np.zeros((n_vec, self.N), dtype=np.int64)
+        _check(lib().bcn_encode_i64(self._h, _np_ptr(v, np.float64), n_vec, B, scale, _np_ptr(out, np.int64)),
+               "bcn_encode_i64")
+        return out
+
+    def expand_i64(self, coeffs_dev, n: int, level: int, out_dev, stream=None):
+        """bcn_expand_i64: integer coefficients [n][N] (device int64) -> residues [n][level][N]."""
+        import torch
+
+        assert coeffs_dev.dtype == torch.int64 and coeffs_dev.is_cuda and coeffs_dev.is_contiguous()
+        assert coeffs_dev.numel() >= n * self.N
+        _check(lib().bcn_expand_i64(self._h, coeffs_dev.data_ptr(), n, level, _dev_ptr(out_dev, n * level * self.N),
+                                    _stream(stream)), "bcn_expand_i64")
 
     def encrypt(self, sk: np.ndarray, pts: np.ndarray, level: int, seed: int) -> np.ndarray:
         pts = np.ascontiguousarray(pts, dtype=np.uint32)
@@ -715,6 +736,21 @@ class Model:
                                                 seed, ctypes.cast(arr, _P), out_host.ctypes.data, workspace.data_ptr(),
                                                 workspace.numel() * workspace.element_size(), _stream(stream)),
                "bcn_eval_host_seeded_async")
+
+    def eval_host_compact_async(self, evk_eval, c0_host: np.ndarray, seed: int, feats_i64: list, out_host: np.ndarray,
+                                workspace, stream=None):
+        """bcn_eval_host_compact_async: from c0, the encryption seed and the
+        features' integer coefficients (bcn_encode_i64, [n_out][N] int64 each)."""
+        for a in [c0_host, out_host]:
+            assert a.dtype == np.uint32 and a.flags["C_CONTIGUOUS"]
+        for f in feats_i64:
+            assert f.dtype == np.int64 and f.flags["C_CONTIGUOUS"]
+        assert out_host.shape == self.out_shape()
+        arr = (_P * max(1, len(feats_i64)))(*[f.ctypes.data for f in feats_i64])
+        _check(lib().bcn_eval_host_compact_async(self._h, _dev_ptr(evk_eval, self.ctx.evk_words()), c0_host.ctypes.data,
+                                                 seed, ctypes.cast(arr, _P), out_host.ctypes.data, workspace.data_ptr(),
+                                                 workspace.numel() * workspace.element_size(), _stream(stream)),
+               "bcn_eval_host_compact_async")
 
 
 class Batch:

@@ -288,9 +288,11 @@ bcn_status bcn_quantize(const float *w, size_t n, int8_t *w_int, double *s_w) {
     return BCN_OK;
 }
 
-bcn_status bcn_encode(const bcn_ctx *c, const double *values, int n_vec, int B, int level, double scale,
-                      uint32_t *pts) {
-    if (!c || (!values && n_vec) || (!pts && n_vec)) return fail(BCN_E_INVAL, "bcn_encode: null argument");
+// the encoder: residues of `level` primes (pts), or the integer coefficients
+// themselves (coeffs, when every |m_j| < 2^63)
+static bcn_status encode_impl(const bcn_ctx *c, const double *values, int n_vec, int B, int level, double scale,
+                              uint32_t *pts, int64_t *coeffs) {
+    if (!c || (!values && n_vec) || (!pts && !coeffs && n_vec)) return fail(BCN_E_INVAL, "bcn_encode: null argument");
     const int N = c->N;
     if (B < 0 || B > N / 2 || level < 1 || level > c->L || n_vec < 0)
         return fail(BCN_E_INVAL, "bcn_encode: bad batch or level");
@@ -308,6 +310,16 @@ bcn_status bcn_encode(const bcn_ctx *c, const double *values, int n_vec, int B, 
             y[(2 * N - e[k] - 1) / 2] += z[k];
         }
         fft.run(y.data());
+        if (coeffs != nullptr) {
+            int64_t *co = coeffs + (size_t)v * N;
+            for (int j = 0; j < N; j++) {
+                double x = (twist[j] * y[j]).real() * (scale / N);
+                if (!std::isfinite(x) || std::fabs(x) >= 9223372036854775808.0) { bad[v] = 2; return; }  // 2^63
+                // below 2^52: round half away from zero; above, already an integer
+                co[j] = std::fabs(x) < 4503599627370496.0 ? (int64_t)std::llround(x) : (int64_t)x;
+            }
+            return;
+        }
         uint32_t *out = pts + (size_t)v * level * N;
         for (int j = 0; j < N; j++) {
             double x = (twist[j] * y[j]).real() * (scale / N);
@@ -321,8 +333,18 @@ bcn_status bcn_encode(const bcn_ctx *c, const double *values, int n_vec, int B, 
         }
     });
     for (int v = 0; v < n_vec; v++)
-        if (bad[v]) return fail(BCN_E_SCALE, "bcn_encode: a coefficient is not finite");
+        if (bad[v]) return fail(BCN_E_SCALE, bad[v] == 2 ? "bcn_encode_i64: a coefficient is not below 2^63"
+                                                         : "bcn_encode: a coefficient is not finite");
     return BCN_OK;
+}
+
+bcn_status bcn_encode(const bcn_ctx *c, const double *values, int n_vec, int B, int level, double scale,
+                      uint32_t *pts) {
+    return encode_impl(c, values, n_vec, B, level, scale, pts, nullptr);
+}
+
+bcn_status bcn_encode_i64(const bcn_ctx *c, const double *values, int n_vec, int B, double scale, int64_t *coeffs) {
+    return encode_impl(c, values, n_vec, B, 1, scale, nullptr, coeffs);
 }
 
 // secret-key encryption; with c0_only the output is [n_ct][level][N] (c0 alone,

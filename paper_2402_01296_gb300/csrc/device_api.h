@@ -166,6 +166,9 @@ bcn_status cores_setup_all();
 // ct takes the stream of index ct_base + ct); c0 untouched
 bcn_status launch_expand_c1(const bcn_ctx *c, uint32_t *cts, int n_ct, int level, uint64_t seed, int ct_base,
                             cudaStream_t st);
+// integer plaintexts: coeffs [n][N] (|m| < 2^63) -> pts [n][level][N], m mod q_i
+bcn_status launch_expand_i64(const bcn_ctx *c, const int64_t *coeffs, int n, int level, uint32_t *pts,
+                             cudaStream_t st);
 // with the context's debug checks on (and the stream not capturing): every
 // residue of polys [n_poly][level][N] below its prime, checked on the device,
 // else BCN_E_INVAL naming `who`; a no-op otherwise

@@ -1289,7 +1289,8 @@ bcn_status bcn_eval_host(const bcn_model *m, const uint32_t *evk, const uint32_t
 // device from the seed
 static bcn_status eval_host_async_impl(const bcn_model *m, const uint32_t *evk, const uint32_t *cts_h,
                                        const uint32_t *const *pts_h, uint32_t *out_h, void *ws, size_t ws_bytes,
-                                       void *stream, bool seeded, uint64_t seed);
+                                       void *stream, bool seeded, uint64_t seed,
+                                       const int64_t *const *feats_i64 = nullptr);
 
 bcn_status bcn_eval_host_async(const bcn_model *m, const uint32_t *evk, const uint32_t *cts_h,
                                const uint32_t *const *pts_h, uint32_t *out_h, void *ws, size_t ws_bytes,
@@ -1303,9 +1304,16 @@ bcn_status bcn_eval_host_seeded_async(const bcn_model *m, const uint32_t *evk, c
     return eval_host_async_impl(m, evk, c0_h, pts_h, out_h, ws, ws_bytes, stream, true, seed);
 }
 
+bcn_status bcn_eval_host_compact_async(const bcn_model *m, const uint32_t *evk, const uint32_t *c0_h, uint64_t seed,
+                                       const int64_t *const *feats_h, uint32_t *out_h, void *ws, size_t ws_bytes,
+                                       void *stream) {
+    if (!feats_h) return fail(BCN_E_INVAL, "bcn_eval_host_compact_async: null feature list");
+    return eval_host_async_impl(m, evk, c0_h, nullptr, out_h, ws, ws_bytes, stream, true, seed, feats_h);
+}
+
 static bcn_status eval_host_async_impl(const bcn_model *m, const uint32_t *evk, const uint32_t *cts_h,
                                        const uint32_t *const *pts_h, uint32_t *out_h, void *ws, size_t ws_bytes,
-                                       void *stream, bool seeded, uint64_t seed) {
+                                       void *stream, bool seeded, uint64_t seed, const int64_t *const *feats_i64) {
     if (!m || !cts_h || !out_h) return fail(BCN_E_INVAL, "bcn_eval_host: null argument");
     if (seeded && m->stack != 1) return fail(BCN_E_INVAL, "bcn_eval_host_seeded_async: single-request models only");
     const bcn_ctx *c = m->ctx;
@@ -1317,7 +1325,8 @@ static bcn_status eval_host_async_impl(const bcn_model *m, const uint32_t *evk, 
     int n_add = 0;
     for (auto &l : m->layers) n_add += l.add;
     for (int a = 0; a < n_add; a++)
-        if (!pts_h || !pts_h[a]) return fail(BCN_E_INVAL, "bcn_eval_host: missing feature plaintexts");
+        if (feats_i64 ? !feats_i64[a] : (!pts_h || !pts_h[a]))
+            return fail(BCN_E_INVAL, "bcn_eval_host: missing feature plaintexts");
     cudaStream_t st = (cudaStream_t)stream;
     // Host-to-device copies go out in kCopyLanes parts on as many streams (the
     // copies run side by side), each after the caller's earlier work on `st`
@@ -1401,10 +1410,47 @@ static bcn_status eval_host_async_impl(const bcn_model *m, const uint32_t *evk, 
         }
     }
     std::vector<const uint32_t *> pts_d;
+    // integer features: copied into the evaluation scratch's first ciphertext
+    // buffer (idle until this evaluation's first layer writes it), reduced mod
+    // each prime into the staging area on the copy streams; the first layer
+    // waits for all of them, the layer of each (and its feature transform) for
+    // its own
+    char *i64 = reinterpret_cast<char *>(ws);
+    size_t i64_used = 0;
     for (size_t l = 0, a = 0; l < m->layers.size(); l++) {
         if (!m->layers[l].add) continue;
         const size_t b = pts_words(m, (int)a) * 4;
-        if (!copy_in(p, pts_h[a], b, ready[l])) return cleanup(BCN_E_CUDA, "bcn_eval_host: feature copy failed");
+        if (!feats_i64) {
+            if (!copy_in(p, pts_h[a], b, ready[l])) return cleanup(BCN_E_CUDA, "bcn_eval_host: feature copy failed");
+        } else {
+            const bcn_layer_plan &lp = m->layers[l];
+            const size_t row = (size_t)c->N * 8, rows_b = (size_t)lp.n_out * row;
+            if (i64_used + rows_b > m->ws_x_bytes)
+                return cleanup(BCN_E_BUDGET, "bcn_eval_host_compact_async: the integer features exceed the scratch");
+            int64_t *src_d = reinterpret_cast<int64_t *>(i64 + i64_used);
+            i64_used += align_up(rows_b);
+            const int per = (lp.n_out + kCopyLanes - 1) / kCopyLanes;
+            for (int k = 0; k < kCopyLanes; k++) {
+                const int lo = k * per, hi = std::min(lp.n_out, lo + per);
+                if (lo >= hi) break;
+                cudaStream_t cs = mm->copy_streams[k];
+                if (cudaMemcpyAsync(src_d + (size_t)lo * c->N, feats_i64[a] + (size_t)lo * c->N,
+                                    (size_t)(hi - lo) * row, cudaMemcpyHostToDevice, cs) != cudaSuccess)
+                    return cleanup(BCN_E_CUDA, "bcn_eval_host: feature copy failed");
+                for (int v0 = lo; v0 < hi; v0 += 65535) {
+                    const int nv = std::min(65535, hi - v0);
+                    const bcn_status es = launch_expand_i64(c, src_d + (size_t)v0 * c->N, nv, lp.level,
+                                                            reinterpret_cast<uint32_t *>(p) + (size_t)v0 * lp.level * c->N,
+                                                            cs);
+                    if (es != BCN_OK) return cleanup(es, bcn_last_error());
+                }
+                cudaEvent_t e;
+                if (!new_event(&e) || cudaEventRecord(e, cs) != cudaSuccess)
+                    return cleanup(BCN_E_CUDA, "bcn_eval_host: event failed");
+                ready[0].push_back(e);
+                if (l != 0) ready[l].push_back(e);
+            }
+        }
         pts_d.push_back(reinterpret_cast<const uint32_t *>(p));
         p += align_up(b);
         a++;

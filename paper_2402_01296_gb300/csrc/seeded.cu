@@ -1,3 +1,7 @@
+// Compact uploads.  Integer plaintexts: a plaintext whose coefficients are
+// below 2^63 in magnitude travels as those integers (8 bytes a coefficient
+// instead of 4 per prime) and the device reduces them mod each prime.
+//
 // Seeded ciphertexts: the second polynomial of a secret-key ciphertext,
 // c1 = a, is uniform noise the client draws from a seed, so the client can
 // send c0 and the seed instead of (c0, c1) and the server draws the same a
@@ -11,6 +15,7 @@
 // floor(2^32 / q_i) q_i, reduced mod q_i.  Every draw is computed from its
 // counter alone, so a block takes 512 draws at a time, keeps the accepted
 // ones in order with a block-wide prefix count, and stops once N are kept.
+#include <algorithm>
 #include <cuda_runtime.h>
 
 #include "device_api.h"
@@ -70,7 +75,32 @@ __global__ void __launch_bounds__(kThreads) k_expand_c1(uint32_t *__restrict__ c
     if (tid == 0) atomicOr(status, kStatusDraws);
 }
 
+// plaintexts given as their integer coefficients (|m| < 2^63): coeffs [n][N]
+// -> pts [n][level][N], m mod q_i.  grid (ceil(N / 256), n)
+__global__ void __launch_bounds__(256) k_expand_i64(const int64_t *__restrict__ coeffs, uint32_t *__restrict__ pts,
+                                                    int level, int N, const PrimeConst *__restrict__ pc) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    const int v = blockIdx.y;
+    const int64_t m = __ldg(reinterpret_cast<const long long *>(coeffs) + (size_t)v * N + j);
+    const uint64_t a = m < 0 ? (uint64_t)0 - (uint64_t)m : (uint64_t)m;
+    uint32_t *out = pts + (size_t)v * level * N + j;
+    for (int i = 0; i < level; i++) {
+        const uint32_t q = pc[i].q, r = barrett_reduce64(a, q, pc[i].barrett);
+        out[(size_t)i * N] = m < 0 && r != 0 ? q - r : r;
+    }
+}
+
 }  // namespace
+
+bcn_status launch_expand_i64(const bcn_ctx *c, const int64_t *coeffs, int n, int level, uint32_t *pts,
+                             cudaStream_t st) {
+    if (n <= 0) return BCN_OK;
+    if (n > 65535) return fail(BCN_E_INVAL, "integer plaintexts: more than 65535 in one call");
+    k_expand_i64<<<dim3((unsigned)((c->N + 255) / 256), (unsigned)n), 256, 0, st>>>(coeffs, pts, level, c->N,
+                                                                                   c->d_pc);
+    return check_launch("k_expand_i64");
+}
 
 bcn_status launch_expand_c1(const bcn_ctx *c, uint32_t *cts, int n_ct, int level, uint64_t seed, int ct_base,
                             cudaStream_t st) {
@@ -100,4 +130,20 @@ extern "C" bcn_status bcn_expand_seeded(const bcn_ctx *c, const uint32_t *c0_dev
         cudaSuccess)
         return fail(BCN_E_CUDA, "bcn_expand_seeded: copy of c0 failed");
     return launch_expand_c1(c, cts_dev, n_ct, level, seed, ct_base, st);
+}
+
+extern "C" bcn_status bcn_expand_i64(const bcn_ctx *c, const int64_t *coeffs_dev, int n, int level, uint32_t *pts_dev,
+                                     void *stream) {
+    if (!c || c->device < 0) return fail(BCN_E_INVAL, "bcn_expand_i64: no device context");
+    if (level < 1 || level > c->L || n < 0) return fail(BCN_E_INVAL, "bcn_expand_i64: bad level or count");
+    if (n == 0) return BCN_OK;
+    if (!coeffs_dev || !pts_dev || ((uintptr_t)coeffs_dev & 15) || ((uintptr_t)pts_dev & 15))
+        return fail(BCN_E_INVAL, "bcn_expand_i64: null or unaligned buffer");
+    const char *a0 = reinterpret_cast<const char *>(coeffs_dev), *a1 = a0 + (size_t)n * c->N * 8;
+    const char *b0 = reinterpret_cast<const char *>(pts_dev), *b1 = b0 + (size_t)n * level * c->N * 4;
+    if (a0 < b1 && b0 < a1) return fail(BCN_E_INVAL, "bcn_expand_i64: buffers overlap");
+    for (int v0 = 0; v0 < n; v0 += 65535)
+        BCN_TRY(launch_expand_i64(c, coeffs_dev + (size_t)v0 * c->N, std::min(65535, n - v0), level,
+                                  pts_dev + (size_t)v0 * level * c->N, (cudaStream_t)stream));
+    return BCN_OK;
 }

@@ -55,3 +55,39 @@ def test_eval_from_seeded_equals_full():
         torch.cuda.synchronize()
         assert np.array_equal(a, b)
     assert ctx.device_status() == 0
+
+
+def test_eval_from_integer_features_equals_residues():
+    """The compact upload (c0, the seed, the features' integer coefficients)
+    gives the same outputs as the full upload of the same encodings, twice in a
+    row on one workspace; bcn_expand_i64 alone equals the host encoder."""
+    cfg = workloads.with_batch(workloads.get_config("cryptonets"), 64)
+    ctx = bcn.Context.from_config(cfg)
+    wq = [bcn.quantize(w) for w in workloads.cipher_weights(cfg)]
+    model = bcn.Model(ctx, cfg["cipher"], [a for a, _ in wq], [s for _, s in wq])
+    sk, evk = ctx.keygen(5)
+    evk_eval = ctx.evk_prepare(bcn.to_device(evk))
+    imgs = workloads.images(cfg)
+    scale = 2.0 ** cfg["log_scale"]
+    full = ctx.encrypt_segment(sk, imgs, cfg["segment"], scale, 9)
+    c0 = np.ascontiguousarray(full[:, 0])
+    adds, _ = model.scales(scale)
+    rng = np.random.default_rng(3)
+    vals = [rng.uniform(-1, 1, (s[0], 64)) for s in model.pt_shapes()]
+    pts = [ctx.encode(v, s[1], sc) for v, s, sc in zip(vals, model.pt_shapes(), adds)]
+    feats = [ctx.encode_i64(v, sc) for v, sc in zip(vals, adds)]
+    dev = torch.from_numpy(feats[0]).cuda()
+    got = torch.zeros((feats[0].shape[0], pts[0].shape[1], ctx.N), dtype=torch.int32, device="cuda")
+    ctx.expand_i64(dev, feats[0].shape[0], pts[0].shape[1], got)
+    assert np.array_equal(bcn.to_host_u32(got), pts[0])
+    ws = model.alloc_workspace(host=True)
+    a = np.zeros(model.out_shape(), dtype=np.uint32)
+    b = np.zeros(model.out_shape(), dtype=np.uint32)
+    model.eval_host_async(evk_eval, full, pts, a, ws)
+    torch.cuda.synchronize()
+    for _ in range(2):
+        b[:] = 0
+        model.eval_host_compact_async(evk_eval, c0, 9, feats, b, ws)
+        torch.cuda.synchronize()
+        assert np.array_equal(a, b)
+    assert ctx.device_status() == 0

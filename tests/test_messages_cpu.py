@@ -99,3 +99,17 @@ def test_seeded_encryption_c0_equals_full(ctx):
     seg = (1, 2, 4, 5)
     assert np.array_equal(ctx.encrypt_segment_seeded(sk, imgs, seg, 2.0**20, 12),
                           ctx.encrypt_segment(sk, imgs, seg, 2.0**20, 12)[:, 0])
+
+
+def test_integer_encoding_reduces_to_the_residues(ctx):
+    """bcn_encode_i64's coefficients, reduced mod each prime, are bcn_encode's
+    residues, below and above 2^52 in magnitude; a coefficient at 2^63 or more
+    is refused."""
+    v = np.random.default_rng(4).uniform(-3, 3, (4, ctx.N // 2))
+    for scale in (2.0**30, 2.0**58):
+        co = ctx.encode_i64(v, scale)
+        q = np.array(ctx.q, dtype=np.int64)[None, :, None]
+        assert np.array_equal((co[:, None, :] % q).astype(np.uint32), ctx.encode(v, ctx.L, scale))
+    assert np.abs(ctx.encode_i64(v, 2.0**58)).max() > 2**53
+    with pytest.raises(bcn.BcnError, match="2\\^63"):
+        ctx.encode_i64(v, 2.0**70)
