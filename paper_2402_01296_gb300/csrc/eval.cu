@@ -882,7 +882,7 @@ bcn_status debug_index(const bcn_ctx *c, const int32_t *v, size_t n, int lo, int
 }
 
 // wait for the checks; a set bit refuses the call (and is cleared)
-bcn_status debug_verdict(const bcn_ctx *c, cudaStream_t st, const char *who) {
+bcn_status debug_outcome(const bcn_ctx *c, cudaStream_t st, const char *who) {
     uint32_t s = 0;
     if (cudaStreamSynchronize(st) != cudaSuccess || cudaMemcpy(&s, c->d_status, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
         return fail(BCN_E_CUDA, std::string(who) + ": reading the debug checks failed");
@@ -902,7 +902,7 @@ bcn_status debug_check_input(const bcn_ctx *c, const uint32_t *a, size_t n_poly,
                              const char *who) {
     if (!debug_on(c, st)) return BCN_OK;
     BCN_TRY(debug_residues(c, a, n_poly, level, st));
-    return debug_verdict(c, st, who);
+    return debug_outcome(c, st, who);
 }
 }  // namespace bcn
 }
@@ -1106,7 +1106,7 @@ static bcn_status eval_impl(const bcn_model *m, const uint32_t *evk, const uint3
             BCN_TRY(debug_index(c, p.d_gidx, (size_t)p.n_groups * p.K, -1, p.n_in, st));
             BCN_TRY(debug_index(c, p.d_gout, (size_t)p.n_groups * p.n_go, 0, p.n_out, st));
         }
-        BCN_TRY(debug_verdict(c, st, "bcn_eval"));
+        BCN_TRY(debug_outcome(c, st, "bcn_eval"));
     }
     cudaStream_t aux = nullptr;
     bool any_pt_ntt = false;
@@ -1530,7 +1530,7 @@ bcn_status bcn_op_mac(const bcn_ctx *c, int level, int n_in, int n_out, int K, c
     if (debug_on(c, (cudaStream_t)stream)) {
         BCN_TRY(debug_residues(c, in, 2 * (size_t)n_in, level, (cudaStream_t)stream));
         BCN_TRY(debug_residues(c, pt, (size_t)n_out, level, (cudaStream_t)stream));
-        BCN_TRY(debug_verdict(c, (cudaStream_t)stream, "bcn_op_mac"));
+        BCN_TRY(debug_outcome(c, (cudaStream_t)stream, "bcn_op_mac"));
     }
     // every output is a group of one with its own taps
     return launch_mac(c, level, K, n_out, 1, idx, w, nullptr, in, pt, out, (cudaStream_t)stream);

@@ -331,7 +331,7 @@ def test_keyswitch_noise_bound(cfg):
 
 def _ks_by_definition(q_data, p_special, alpha, level, x, evk):
     """Hybrid key switching written out with Python integers (App. A Mult(c1, c2)
-    relinearisation; the variant read for this build): for each digit j (primes
+    relinearisation; the hybrid variant the library implements): for each digit j (primes
     q_{j alpha} .. q_{min((j+1) alpha, level) - 1}) the digit value is the
     integer v_j = sum_i [x_i Dhat_i^-1]_{q_i} Dhat_i with centred residues
     [.]_q in (-q/2, q/2] and Dhat_i the product of the digit's other primes;
