@@ -762,7 +762,7 @@ def run_uneven(args, rank, world, local_rank):
     torch.cuda.synchronize()
     # the NTT-based kernels' block shape per ring degree, timed on each
     # context's first evaluation (the context keeps the faster)
-    shape_note = {}
+    shape_note, chunk_note = {}, {}
     for log_n, cx in ctxs.items():
         m0, ev0, c0, p0, o0 = next(it for it, cf in zip(items, cfgs) if cf["log_n"] == log_n)
         ws0 = m0.alloc_workspace()
@@ -770,6 +770,12 @@ def run_uneven(args, rank, world, local_rank):
         shape_note[str(log_n)] = {"chosen": best, "residues_per_thread": cx.ntt_shape()[1],
                                   "ms": {str(k): round(v, 3) for k, v in res.items()}}
         del ws0
+        # the key-switching chunk, on the same representative, for every model of the ring degree
+        ch, _, res = tuner.tune_chunk(m0, ev0, c0, p0, o0)
+        chunk_note[str(log_n)] = {"chosen": ch, "ms": {str(k): round(v, 3) for k, v in res.items()}}
+        for it, cf in zip(items, cfgs):
+            if cf["log_n"] == log_n:
+                it[0].set_chunk(ch)
     torch.cuda.empty_cache()
     free, total = torch.cuda.mem_get_info()
     budget = max(0, free - (8 << 30))
@@ -842,7 +848,7 @@ def run_uneven(args, rank, world, local_rank):
                    "counts": {str(k): sum(1 for c in cfgs if c["log_n"] == k) for k in (12, 13, 14)}},
         "p50_ms": statistics.median(ms), "p99_ms": float(np.percentile(ms, 99)),
         "tuning": {"lanes_ms": {str(k): round(v, 3) for k, v in lane_res.items()}, "alpha_ms": alpha_note,
-                   "ntt_shape": shape_note},
+                   "ntt_shape": shape_note, "chunk": chunk_note},
         "plain_sequential": {"value": images / (min(plain_ms) / 1e3), "ms_per_step": min(plain_ms),
                              "path": "each evaluation alone, every kernel in order on one stream, the "
                                      "configuration's digit size and the default chunk, no graph"},
