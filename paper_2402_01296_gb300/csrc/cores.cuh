@@ -246,8 +246,9 @@ __global__ void __launch_bounds__((1 << LOGN) / R, IN_NTT ? SqnOcc<(1 << LOGN) /
 // centred fast basis conversion
 //     sum_u r_u * Dhat_u - #{u : r_u > (q_u-1)/2} * D_j,  r_u = [x_u Dhat_u^{-1}]_{q_u},
 // which for one-prime digits is d mod t, less q_j mod t when d > (q_j-1)/2.
-// With LAZY (t a data prime) one-prime digits leave d + (t - q_j mod t) < 3t,
-// a valid lazy NTT input; otherwise the residue is canonical.  With PRE the
+// With LAZY (t a data prime) one-prime digits leave d + (t - q_j mod t) < 3t
+// and digits of two primes a residue below 4t, valid lazy NTT inputs;
+// otherwise the residue is canonical.  With PRE the
 // limbs of multi-prime digits already hold r_u = [x_u Dhat_u^{-1}]_{q_u} (the
 // square kernel's output for the key switch: computed there once instead of
 // once per target prime); the digit's own primes are then never read here.
@@ -280,6 +281,40 @@ __device__ __forceinline__ void modup_residue(uint32_t (&x)[R], const uint32_t *
                 uint32_t y = reduce_once(d, P.q);  // d < q_j < 2t
                 if (d > half) y = sub_mod(y, dp, P.q);
                 x[u] = y;
+            }
+        }
+    } else if (LAZY && hi - lo <= 2) {
+        // digits of two primes (and a last digit of one) on a data prime, lazily:
+        // the Shoup products' sum (below 4t) folded once into [0, 2t), then
+        // t - (D_j mod t) added once per centred correction, which keeps the
+        // residue below 4t, a valid lazy NTT input congruent to the canonical one
+        const size_t jb = (size_t)(n * ks.dnum_max + j);
+        const uint32_t tmq = P.q - ks.dprod[jb * ks.P + pt], q2 = 2 * P.q;
+        const uint32_t q0 = pc[lo].q, half0 = pc[lo].half;
+        const uint2 di0 = ks.dhat_inv[jb * A], dh0 = ks.dhat[(jb * A) * ks.P + pt];
+        const uint32_t *x0 = x2 + (size_t)lo * N;
+        if (hi - lo == 2) {
+            const uint32_t q1 = pc[lo + 1].q, half1 = pc[lo + 1].half;
+            const uint2 di1 = ks.dhat_inv[jb * A + 1], dh1 = ks.dhat[(jb * A + 1) * ks.P + pt];
+            const uint32_t *x1 = x0 + N;
+#pragma unroll
+            for (int u = 0; u < R; u++) {
+                const int e = C::nat_elem(u, tid);
+                const uint32_t a0 = __ldg(x0 + e), a1 = __ldg(x1 + e);
+                const uint32_t r0 = PRE ? a0 : shoup_mul(a0, di0.x, di0.y, q0);
+                const uint32_t r1 = PRE ? a1 : shoup_mul(a1, di1.x, di1.y, q1);
+                uint32_t y = shoup_mul_lazy(r0, dh0.x, dh0.y, P.q) + shoup_mul_lazy(r1, dh1.x, dh1.y, P.q);
+                y = min(y, y - q2);
+                y += r0 > half0 ? tmq : 0u;
+                y += r1 > half1 ? tmq : 0u;
+                x[u] = y;
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < R; u++) {
+                const uint32_t a0 = __ldg(x0 + C::nat_elem(u, tid));
+                const uint32_t r0 = PRE ? a0 : shoup_mul(a0, di0.x, di0.y, q0);
+                x[u] = shoup_mul_lazy(r0, dh0.x, dh0.y, P.q) + (r0 > half0 ? tmq : 0u);  // < 3t
             }
         }
     } else {
@@ -680,21 +715,39 @@ __global__ void __launch_bounds__((1 << LOGN) / R, NP == 1 ? MdOcc<(1 << LOGN) /
             // correction below a chain of selects: no branch, so the loads of
             // all R elements can be issued together
             uint32_t conv_i = 0;
-            int cnt = 0;
+            if constexpr (K <= 2) {
+                // lazily: the Shoup products' sum folded once into [0, 2q), plus
+                // q - (P mod q_i) per centred correction (below 4q), times P^{-1}
+                // up to one q, plus the lift: below 3q, a valid lazy NTT input
+                // congruent to the canonical value
+                uint32_t corr = 0;
 #pragma unroll
-            for (int m = 0; m < K; m++) {
-                const uint32_t ph2 = pc[ks.L + m].half;
-                const uint2 phi = ks.phat[(size_t)m * ks.L + i];
-                // a_m Phat_m^{-1}: the prepared key's special-prime limbs carry Phat_m^{-1}
-                const uint32_t r = __ldg(row[p] + (size_t)(n + m) * N + e);
-                cnt += r > ph2;
-                conv_i = add_mod(conv_i, shoup_mul(r, phi.x, phi.y, P.q), P.q);
+                for (int m = 0; m < K; m++) {
+                    const uint2 phi = ks.phat[(size_t)m * ks.L + i];
+                    // a_m Phat_m^{-1}: the prepared key's special-prime limbs carry Phat_m^{-1}
+                    const uint32_t r = __ldg(row[p] + (size_t)(n + m) * N + e);
+                    conv_i += shoup_mul_lazy(r, phi.x, phi.y, P.q);
+                    if (m > 0) conv_i = min(conv_i, conv_i - 2 * P.q);
+                    corr += r > pc[ks.L + m].half ? P.q - pmod_i : 0u;
+                }
+                const uint32_t y = __ldg(row[p] + (size_t)top * N + e);  // c_top (k_md_top)
+                x[p][u] = shoup_mul_lazy(conv_i + corr, pi.x, pi.y, P.q) + (y > htop ? y + tmq : y);
+            } else {
+                int cnt = 0;
+#pragma unroll
+                for (int m = 0; m < K; m++) {
+                    const uint32_t ph2 = pc[ks.L + m].half;
+                    const uint2 phi = ks.phat[(size_t)m * ks.L + i];
+                    const uint32_t r = __ldg(row[p] + (size_t)(n + m) * N + e);
+                    cnt += r > ph2;
+                    conv_i = add_mod(conv_i, shoup_mul(r, phi.x, phi.y, P.q), P.q);
+                }
+#pragma unroll
+                for (int c = 0; c < K; c++) conv_i = c < cnt ? sub_mod(conv_i, pmod_i, P.q) : conv_i;
+                const uint32_t y = __ldg(row[p] + (size_t)top * N + e);  // c_top (k_md_top)
+                const uint32_t lift = y > htop ? y + tmq : y;
+                x[p][u] = add_mod(shoup_mul(conv_i, pi.x, pi.y, P.q), lift, P.q);
             }
-#pragma unroll
-            for (int c = 0; c < K; c++) conv_i = c < cnt ? sub_mod(conv_i, pmod_i, P.q) : conv_i;
-            const uint32_t y = __ldg(row[p] + (size_t)top * N + e);  // c_top (k_md_top)
-            const uint32_t lift = y > htop ? y + tmq : y;
-            x[p][u] = add_mod(shoup_mul(conv_i, pi.x, pi.y, P.q), lift, P.q);
         }
     }
     C::template forward_n<NP>(x, sm, tid, ModQ(P.q, kFmaOne<LOGN, R> ? P.one : 1u), twf + (size_t)i * N);  // [0, 4q)
