@@ -181,6 +181,14 @@ bcn_status bcn_ctx_create(const bcn_params *p, int device, bcn_ctx **out) {
         delete c;
         return fail(BCN_E_INVAL, "not enough NTT-friendly primes for this N");
     }
+    // the device reduces MAC sums with a quotient estimate that wants the data
+    // primes above 2^29 (they are the largest below 2^30 that are 1 mod 2N)
+    for (int t = 0; t < c->L; t++) {
+        if (c->primes[t] <= (1ull << 29)) {
+            delete c;
+            return fail(BCN_E_INVAL, "data primes must lie between 2^29 and 2^30");
+        }
+    }
     const int P = c->L + c->K, N = c->N;
     c->h_tw_fwd.resize(P);
     c->h_tw_inv.resize(P);

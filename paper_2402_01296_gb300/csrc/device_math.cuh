@@ -56,4 +56,16 @@ __device__ __forceinline__ uint32_t barrett_reduce64(uint64_t x, uint32_t q, uin
     return reduce_once(r, q);
 }
 
+// x mod q for x < 2^59 and a data prime 2^29 < q < 2^30, with 32-bit
+// multiplies (mu = floor(2^64 / q) as for barrett_reduce64): the quotient
+// estimate floor(floor(x / 2^29) floor(2^61 / q) / 2^32) is at most 2 below
+// floor(x / q) (x / 2^61 < 1/4 and 2^29 / q < 1) and never above it, so
+// x - estimate q lies in [0, 3q) and fits 32 bits
+__device__ __forceinline__ uint32_t reduce59(uint64_t x, uint32_t q, uint64_t mu) {
+    const uint32_t qe = __umulhi((uint32_t)(x >> 29), (uint32_t)(mu >> 3));
+    uint32_t r = (uint32_t)x - qe * q;  // [0, 3q)
+    r = min(r, r - 2 * q);              // [0, 2q)
+    return reduce_once(r, q);
+}
+
 }  // namespace bcn

@@ -71,10 +71,14 @@ __global__ void __launch_bounds__(kMacThreads, OT <= 5 ? 3 : 2) k_mac_grouped(co
     const size_t cols = (size_t)2 * level * N;
     const size_t col = ((size_t)blockIdx.y * blockDim.x + threadIdx.x) * 4;
     const bool active = col < cols;
-    // residues are below 2^31, so signed 32 x 32 -> 64 products are exact
+    // residues are below 2^30, so signed 32 x 32 -> 64 products are exact; the
+    // sums start at the limb's offset (a multiple of q >= 2^58), which keeps
+    // them positive and below 2^59 (|sum of products| < 2^57 at the 2^20-tap limit)
+    const int lim = active ? (int)((col / N) % level) : 0;
+    const long long off0 = (long long)pc[lim].mac_offset;
     long long acc[OT][4];
 #pragma unroll
-    for (int o = 0; o < OT; o++) acc[o][0] = acc[o][1] = acc[o][2] = acc[o][3] = 0;
+    for (int o = 0; o < OT; o++) acc[o][0] = acc[o][1] = acc[o][2] = acc[o][3] = off0;
     const uint32_t *base = in + (active ? col : 0);
     for (int t0 = 0; t0 < K; t0 += kca) {  // taps in chunks that fit shared memory
         const int KC = min(kca, K - t0);
@@ -134,10 +138,9 @@ __global__ void __launch_bounds__(kMacThreads, OT <= 5 ? 3 : 2) k_mac_grouped(co
         }
     }
     if (!active) return;
-    const int poly = (int)(col / ((size_t)level * N)), i = (int)((col / N) % level);
+    const int poly = (int)(col / ((size_t)level * N)), i = lim;
     const uint32_t q = pc[i].q;
     const uint64_t mu = pc[i].barrett;
-    const long long off = (long long)pc[i].mac_offset;
     // every output's index and feature word are requested before any is used
     // (independent loads, one round trip)
     int og[OT];
@@ -145,10 +148,10 @@ __global__ void __launch_bounds__(kMacThreads, OT <= 5 ? 3 : 2) k_mac_grouped(co
 #pragma unroll
     for (int o = 0; o < OT; o++) {
         og[o] = o < no ? (gout != nullptr ? gout[(size_t)g * n_go + o0 + o] : g * n_go + o0 + o) : 0;
-        r[o].x = barrett_reduce64((uint64_t)(acc[o][0] + off), q, mu);
-        r[o].y = barrett_reduce64((uint64_t)(acc[o][1] + off), q, mu);
-        r[o].z = barrett_reduce64((uint64_t)(acc[o][2] + off), q, mu);
-        r[o].w = barrett_reduce64((uint64_t)(acc[o][3] + off), q, mu);
+        r[o].x = reduce59((uint64_t)acc[o][0], q, mu);
+        r[o].y = reduce59((uint64_t)acc[o][1], q, mu);
+        r[o].z = reduce59((uint64_t)acc[o][2], q, mu);
+        r[o].w = reduce59((uint64_t)acc[o][3], q, mu);
     }
     if (pt != nullptr && poly == 0) {
         uint4 p[OT];

@@ -316,7 +316,8 @@ __global__ void __launch_bounds__(kThreads, MINB) k_mac_tc(const uint32_t *__res
 #pragma unroll
                     for (int b = 0; b < kPlanes; b++)
                         v += (long long)__float2int_rn(__uint_as_float(f[b][o]) * 16777216.0f) << (8 * b);
-                    const uint32_t res = add_mod(barrett_reduce64((uint64_t)v, q, mu), pv[o], q);
+                    // offs >= 2^58 and |sum| < 2^48: v is positive and below 2^59
+                    const uint32_t res = add_mod(reduce59((uint64_t)v, q, mu), pv[o], q);
                     const int os = store_natural ? sgo[ob + o] : (g - g_base) * n_go + o0 + ob + o;
                     out[(size_t)os * cols + col] = res;
                 }
