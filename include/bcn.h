@@ -67,7 +67,7 @@ typedef struct bcn_plain_model bcn_plain_model;
 
 typedef struct {
     uint32_t log_n;        /* N = 2^log_n, 4 <= log_n <= 14 */
-    uint32_t n_data;       /* L data primes (< 2^30), 1 <= L <= 24 */
+    uint32_t n_data;       /* L data primes (between 2^29 and 2^30), 1 <= L <= 24 */
     uint32_t n_special;    /* K special primes (< 2^31), 1 <= K <= 4 */
     uint32_t alpha;        /* primes per key-switching digit, 1 <= alpha <= K */
 } bcn_params;
@@ -81,8 +81,10 @@ typedef struct {
 const char *bcn_last_error(void);
 
 /* ---------------------------------------------------------------- context */
-/* Builds the prime chain and the NTT / basis-conversion tables; with
- * device >= 0 also uploads the device tables to that GPU. */
+/* Builds the prime chain (the largest primes below 2^30, then below 2^31,
+ * that are 1 mod 2N) and the NTT / basis-conversion tables; with device >= 0
+ * also uploads the device tables to that GPU.  BCN_E_INVAL if the parameters
+ * are out of range or the chain cannot be built (a data prime not above 2^29). */
 bcn_status bcn_ctx_create(const bcn_params *params, int device, bcn_ctx **out);
 bcn_status bcn_ctx_destroy(bcn_ctx *ctx);
 bcn_status bcn_ctx_get_info(const bcn_ctx *ctx, bcn_ctx_info *out);
