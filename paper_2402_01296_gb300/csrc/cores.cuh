@@ -703,6 +703,16 @@ __global__ void __launch_bounds__((1 << LOGN) / R, NP == 1 ? MdOcc<(1 << LOGN) /
     const uint32_t *row[NP];
 #pragma unroll
     for (int p = 0; p < NP; p++) row[p] = acc + ((size_t)ct * 2 + b0 + p) * nb * N;
+    // the epilogue's rows A_i and D_i, requested into L2 now: the prologue and
+    // the transform run meanwhile (measured at N = 16384: ModDown 9.50 to 9.20
+    // ms per CIFAR-shaped evaluation; no gain at N = 8192)
+    if constexpr (N >= 16384) {
+#pragma unroll
+        for (int p = 0; p < NP; p++) {
+            prefetch_row_l2(row[p] + (size_t)i * N, N, tid, C::T);
+            prefetch_row_l2(D + (((size_t)ct * 3 + b0 + p) * n + i) * N, N, tid, C::T);
+        }
+    }
     // coefficient form: conv_i(a_P) P^{-1} + [c_top] (mod q_i), with
     // c_top = acc_top - conv_top(a_P) P^{-1} (mod q_top) formed by k_md_top
     uint32_t x[NP][R];

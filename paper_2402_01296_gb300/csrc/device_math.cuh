@@ -56,6 +56,12 @@ __device__ __forceinline__ uint32_t barrett_reduce64(uint64_t x, uint32_t q, uin
     return reduce_once(r, q);
 }
 
+// L2 prefetch hint for the 32-bit words [0, n_words) of a row: one 128-byte
+// line per thread, the block's nthreads threads striding over the row
+__device__ __forceinline__ void prefetch_row_l2(const uint32_t *row, int n_words, int tid, int nthreads) {
+    for (int w = tid * 32; w < n_words; w += nthreads * 32) asm volatile("prefetch.global.L2 [%0];" ::"l"(row + w));
+}
+
 // x mod q for x < 2^59 and a data prime 2^29 < q < 2^30, with 32-bit
 // multiplies (mu = floor(2^64 / q) as for barrett_reduce64): the quotient
 // estimate floor(floor(x / 2^29) floor(2^61 / q) / 2^32) is at most 2 below
