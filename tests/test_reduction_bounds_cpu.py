@@ -48,7 +48,7 @@ def test_mac_reduction_quotient_estimate(name):
     for q in ctx.q:
         assert (1 << 29) < q < (1 << 30)
         off = ((1 << 58) // q + 1) * q
-        span = (1 << 20) * 127 * (q - 1)  # the largest |sum of products|
+        span = (1 << 20) * 128 * (q - 1)  # the largest |sum of products| (int8 weights, 2^20 taps)
         assert 0 < off - span and off + span < (1 << 59)
         xs = [0, 1, q - 1, q, off - span, off + span, (1 << 59) - 1, off]
         xs += [int(v) for v in rng.integers(0, 1 << 59, size=200, dtype=np.uint64)]
